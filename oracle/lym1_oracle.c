@@ -1,0 +1,922 @@
+/*
+ * lym1_oracle.c -- plain, slow FP64 reference ("oracle") for one substep of the
+ * Lydion M1 method for Lyman-alpha transfer on a 2D Cartesian grid
+ * (arXiv 2606.02711).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * benchmark's CPU-baseline arm may load this file's library.  The GPU product
+ * path does not link, import or call it, and this file shares no code with the
+ * GPU path (its own constants, its own exp/expm1, its own Dawson function).
+ *
+ * What it computes, in the paper's order (Sec. 2.1, "overall update scheme"):
+ *   A0  frequency grid (Sec. 2.1, grid paragraph), bin-averaged Voigt profile
+ *       <H>_k (App. A, bin-averaged Voigt eq. and the I(x,a) integral),
+ *       emission fractions from phi_nu = H/sqrt(pi) (Sec. 2.1 step 2).
+ *   A1  linear reconstruction of J and f = H/J with MinMod; |f| > 1 rescaled
+ *       (Sec. 2.1 step 1 and its footnote); M1 closure (Levermore closure eq.).
+ *   A2  asymptotic-preserving GLF flux for J (corrected GLF flux eq.), the
+ *       interpolation factor eps and face optical depth (Sec. 2.1 step 1),
+ *       the modified GLF flux for K, upwind advection of uJ/c and uH/c.
+ *   A3  explicit forward-Euler update including the -grad(u):K/c work term.
+ *   A4  implicit emission/absorption/destruction (absorption step eqs.).
+ *   A5  radiation force from the change of H in A4 (Sec. 2.3 force eq.).
+ *   A6  implicit (BDF1) frequency diffusion + recoil + Doppler solve per cell
+ *       with the exponential scheme (App. A), then H = (J_new/J_old) H.
+ *   A7  energy bookkeeping with compensated (Neumaier) sums.
+ *
+ * Readings where the paper is silent (each also listed in the design notes):
+ *   - Cartesian geometry: face optical depth tau = aF_i dx/2 + aF_{i+1} dx/2,
+ *     D:grad u = Dxx dux/dx + Dyy duy/dy + Dxy (dux/dy + duy/dx).
+ *   - outflow boundaries = two ghost layers copying the edge cell (all fields).
+ *   - face velocity = mean of the two cells; the upwind donor is the
+ *     reconstructed state on the upwind side.
+ *   - velocity gradients by central differences over the two neighbours.
+ *   - the K-flux dissipation term uses the jump of the same H component.
+ *   - the diffusion part of the J flux is (1-eps)(J_{i+1}-J_i)/(3 tau), and 0
+ *     where tau = 0 (then eps = 1).
+ *   - A6: the exponential-scheme leakage coefficients are evaluated with a
+ *     common exponential factor taken out so that nothing overflows at large
+ *     Peclet numbers, and the tridiagonal system is eliminated in its
+ *     conservative (flux) form carrying the diagonal-dominance margin, which
+ *     keeps every step free of subtraction.  Both are exact rearrangements of
+ *     the App. A equations.
+ *   - phi and chi are evaluated with this file's own exp/expm1 (Cody-Waite
+ *     argument reduction + Taylor polynomial), not lookup tables.
+ *   - no FMA contraction: build with -ffp-contract=off.
+ *
+ * Parity pins (tests/test_oracle_*.py): printed N_nu = 194, sigma0 and a_v
+ * scalings, Dawson vs scipy, <H> vs quadrature, closure and eps limits,
+ * conservation of energy to round-off, realisability, free-streaming beam,
+ * Gaussian diffusion closed form, thin-slab force multiplier, step-3 vs dense
+ * and exact-rational solves, recoil-only equilibrium, central-difference
+ * limit vs a banded solver.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* ---- physical constants, cgs (CODATA 2018) ---- */
+#define O_PI 3.14159265358979323846
+#define O_SQRTPI 1.772453850905516
+#define O_C 2.99792458e10          /* speed of light, cm/s */
+#define O_HPL 6.62607015e-27       /* Planck constant, erg s */
+#define O_KB 1.380649e-16          /* Boltzmann constant, erg/K */
+#define O_ME 9.1093837015e-28      /* electron mass, g */
+#define O_QE 4.803204712570263e-10 /* elementary charge, esu */
+#define O_MH 1.67353284e-24        /* hydrogen atom mass, g */
+#define O_NU_LYA (O_C / 1215.67e-8) /* Lya line-centre frequency, Hz */
+#define O_NU_LYC 3.28805e15        /* H ionisation threshold frequency, Hz */
+#define O_A_LYA 6.265e8            /* Lya Einstein A, 1/s */
+#define O_F12 0.4162               /* Lya oscillator strength */
+
+/* ======================================================================
+ * Own exp / expm1: Cody-Waite argument reduction x = n ln2 + r, |r| <= ln2/2,
+ * then a degree-13 Taylor polynomial for expm1(r) (remainder < 1.2e-17 |r|).
+ * ln2 is split into a 32-significant-bit head (so n*LN2_HI is exact for
+ * |n| < 2^20) and the rounded tail.
+ * ====================================================================== */
+static const double O_LN2_HI = 0x1.62e42feep-1;
+static const double O_LN2_LO = 0x1.a39ef35793c76p-33;
+static const double O_INV_LN2 = 0x1.71547652b82fep+0;
+
+static double o_pow2i(int n) /* exact 2^n for -1022 <= n <= 1023 */
+{
+    uint64_t b = (uint64_t)(n + 1023) << 52;
+    double d;
+    memcpy(&d, &b, sizeof d);
+    return d;
+}
+
+static double o_expm1_poly(double r)
+{
+    double q = 1.0 / 6227020800.0; /* 1/13! */
+    q = q * r + 1.0 / 479001600.0; /* 1/12! */
+    q = q * r + 1.0 / 39916800.0;  /* 1/11! */
+    q = q * r + 1.0 / 3628800.0;   /* 1/10! */
+    q = q * r + 1.0 / 362880.0;    /* 1/9! */
+    q = q * r + 1.0 / 40320.0;     /* 1/8! */
+    q = q * r + 1.0 / 5040.0;      /* 1/7! */
+    q = q * r + 1.0 / 720.0;       /* 1/6! */
+    q = q * r + 1.0 / 120.0;       /* 1/5! */
+    q = q * r + 1.0 / 24.0;        /* 1/4! */
+    q = q * r + 1.0 / 6.0;         /* 1/3! */
+    q = q * r + 1.0 / 2.0;         /* 1/2! */
+    return r + (r * r) * q;
+}
+
+static void o_reduce(double x, int *n, double *r)
+{
+    double t = floor(x * O_INV_LN2 + 0.5);
+    *n = (int)t;
+    *r = (x - t * O_LN2_HI) - t * O_LN2_LO;
+}
+
+double lym1o_exp(double x)
+{
+    if (x != x) return x;
+    if (x > 709.782712893384) return INFINITY;
+    if (x < -745.2) return 0.0;
+    int n;
+    double r;
+    o_reduce(x, &n, &r);
+    double s = 1.0 + o_expm1_poly(r);
+    if (n > 1023) return (s * 2.0) * o_pow2i(n - 1);
+    if (n >= -1022) return s * o_pow2i(n);
+    return (s * o_pow2i(n + 1022)) * o_pow2i(-1022);
+}
+
+double lym1o_expm1(double x)
+{
+    if (x != x) return x;
+    if (x > 709.782712893384) return INFINITY;
+    if (x < -745.2) return -1.0;
+    int n;
+    double r;
+    o_reduce(x, &n, &r);
+    double p = o_expm1_poly(r);
+    if (n == 0) return p;
+    if (n < -1022) return -1.0;
+    if (n > 1023) return (p + 1.0) * 2.0 * o_pow2i(n - 1);
+    double t = o_pow2i(n);
+    return t * p + (t - 1.0);
+}
+
+/* ======================================================================
+ * Dawson's integral F(x) = exp(-x^2) int_0^x exp(y^2) dy, needed by the
+ * bin-averaged Voigt profile (App. A, I(x,a) integral).
+ *   |x| < 0.2 : Maclaurin series  F = sum_n (-2)^n x^(2n+1) / (2n+1)!!
+ *   |x| < 10  : Rybicki (1989) sampling-theorem sum
+ *               F(x) ~ pi^(-1/2) sum_{n odd} exp(-(x - n h)^2) / n, h = 0.2,
+ *               whose error is of order exp(-(pi/2h)^2) ~ 1e-27
+ *   |x| >= 10 : asymptotic series F ~ (1/2x) sum_n (2n-1)!! / (2x^2)^n
+ * ====================================================================== */
+double lym1o_dawson(double x)
+{
+    double ax = fabs(x), f;
+    if (ax < 0.2) {
+        double x2 = ax * ax, term = ax;
+        f = ax;
+        for (int n = 1; n <= 12; ++n) {
+            term = (term * (-2.0 * x2)) / (2.0 * n + 1.0);
+            f += term;
+        }
+    } else if (ax < 10.0) {
+        const double h = 0.2;
+        int n_lo = (int)ceil((ax - 8.0) / h), n_hi = (int)floor((ax + 8.0) / h);
+        double s = 0.0;
+        for (int n = n_lo; n <= n_hi; ++n) {
+            if ((n & 1) == 0) continue;
+            double d = ax - n * h;
+            s += exp(-d * d) / n;
+        }
+        f = s / O_SQRTPI;
+    } else {
+        double y = 1.0 / (2.0 * ax * ax), term = 1.0, s = 1.0;
+        for (int n = 1; n <= 20; ++n) {
+            term = term * ((2.0 * n - 1.0) * y);
+            s += term;
+        }
+        f = s / (2.0 * ax);
+    }
+    return (x < 0.0) ? -f : f;
+}
+
+/* ---- line constants at temperature T (Sec. 2.1 grid paragraph) ---- */
+void lym1o_line(double T, double *out3 /* dnuD, a_v, sigma0 */)
+{
+    double dnuD = (O_NU_LYA * sqrt((2.0 * O_KB * T) / O_MH)) / O_C;
+    out3[0] = dnuD;
+    out3[1] = O_A_LYA / ((4.0 * O_PI) * dnuD);
+    out3[2] = ((O_SQRTPI * (O_QE * O_QE)) * O_F12) / ((O_ME * O_C) * dnuD);
+}
+
+/*
+ * Frequency grid (Sec. 2.1, grid paragraph): symmetric in dnu = nu - nu_Lya,
+ * the two central bins of width dnu_D(T_min), widths growing by q outwards,
+ * |dnu| <= min(1e5 dnu_D(T_min), 0.99 nu_Lya, nu_LyC - nu_Lya).  The last bin on
+ * each side is the one that crosses the limit, truncated at it.  Writes the
+ * 2M+1 ascending edges and returns N = 2M (or -1 if max_edges is too small).
+ */
+int lym1o_freq_grid(double T_min, double q, double *edges, int max_edges)
+{
+    double ln[3];
+    lym1o_line(T_min, ln);
+    double w0 = ln[0];
+    double lim = 1e5 * w0;
+    if (0.99 * O_NU_LYA < lim) lim = 0.99 * O_NU_LYA;
+    if (O_NU_LYC - O_NU_LYA < lim) lim = O_NU_LYC - O_NU_LYA;
+    /* positive-side edges e_0 = 0 < e_1 < ... < e_M = lim */
+    double *pos = (double *)malloc(100000 * sizeof(double));
+    int M = 0;
+    double e = 0.0, w = w0;
+    pos[0] = 0.0;
+    while (1) {
+        double next = e + w;
+        M += 1;
+        if (M >= 100000) {
+            free(pos);
+            return -1;
+        }
+        if (next >= lim) {
+            pos[M] = lim;
+            break;
+        }
+        pos[M] = next;
+        e = next;
+        w = w * q;
+    }
+    if (2 * M + 1 > max_edges) {
+        free(pos);
+        return -1;
+    }
+    for (int j = 0; j <= M; ++j) {
+        edges[M + j] = pos[j];
+        edges[M - j] = -pos[j];
+    }
+    edges[M] = 0.0;
+    free(pos);
+    return 2 * M;
+}
+
+/* part of I(x,a) (App. A) other than the erf term */
+static double o_I_rest(double x, double a)
+{
+    return -((2.0 * a) / O_SQRTPI) * lym1o_dawson(x) + ((a * a) * x) * exp(-(x * x));
+}
+
+/*
+ * Bin-averaged Voigt profile over [xa, xb] in Doppler units (App. A):
+ * <H> = [I(xb,a) - I(xa,a)] / dx_k.  The erf difference is taken through erfc
+ * on the side away from line centre so that wing bins keep full precision.
+ */
+static double o_bin_H(double xa, double xb, double a, double dxk)
+{
+    double derf;
+    if (xa >= 0.0)
+        derf = (O_SQRTPI / 2.0) * (erfc(xa) - erfc(xb));
+    else if (xb <= 0.0)
+        derf = (O_SQRTPI / 2.0) * (erfc(-xb) - erfc(-xa));
+    else
+        derf = (O_SQRTPI / 2.0) * (erf(xb) - erf(xa));
+    return (derf + (o_I_rest(xb, a) - o_I_rest(xa, a))) / dxk;
+}
+
+/*
+ * Per-bin tables for n bins with the given dnu edges at temperature T:
+ * dnu_k (width, Hz), nubar_k (absolute centre frequency, bin midpoint, App. A
+ * footnote), Havg_k (bin-averaged Voigt), w_k (emitted fraction, from
+ * phi_nu = H/sqrt(pi), renormalised to sum 1 so the grid conserves photons).
+ * Returns eta = sum_k w_k Havg_k (the gray-group overlap factor).
+ */
+double lym1o_bin_tables(int n, const double *edges, double T, double *dnu, double *nubar,
+                        double *Havg, double *w)
+{
+    double ln[3];
+    lym1o_line(T, ln);
+    double dnuD = ln[0], a = ln[1];
+    double S = 0.0;
+    for (int k = 0; k < n; ++k) {
+        dnu[k] = edges[k + 1] - edges[k];
+        nubar[k] = O_NU_LYA + 0.5 * (edges[k] + edges[k + 1]);
+        double xa = edges[k] / dnuD, xb = edges[k + 1] / dnuD, dxk = dnu[k] / dnuD;
+        Havg[k] = o_bin_H(xa, xb, a, dxk);
+        w[k] = Havg[k] * dxk;
+        S += w[k];
+    }
+    double eta = 0.0;
+    for (int k = 0; k < n; ++k) {
+        w[k] = w[k] / S;
+        eta += w[k] * Havg[k];
+    }
+    return eta;
+}
+
+/* ======================================================================
+ * Problem and context
+ * ====================================================================== */
+typedef struct {
+    int nx, ny;          /* cells */
+    int nbins;           /* bins of the frequency grid given by edges */
+    int gray;            /* 1: one gray group (opacity alpha*eta), no step 3 */
+    int recoil;          /* 1: atomic recoil in step 3 */
+    int freq_step;       /* 1: run step 3 (ignored if gray) */
+    double dx;           /* cell width (cm); the slab depth is also dx */
+    double T;            /* gas temperature (K), uniform */
+    double c_tilde;      /* (reduced) speed of light (cm/s) */
+    double cfl;          /* CFL_RT (0.4 in the paper) */
+    double kappa_abs;    /* dust absorption opacity kappa_ext(1-omega) (cm^2/g) */
+    double kappa_F;      /* dust flux opacity kappa_ext(1-omega g) (cm^2/g) */
+    const double *edges; /* nbins+1 ascending dnu edges (Hz) */
+    const double *n_hi;  /* [ny][nx] cm^-3 */
+    const double *rho_d; /* [ny][nx] g cm^-3 */
+    const double *p_d;   /* [ny][nx] */
+    const double *ux;    /* [ny][nx] cm/s */
+    const double *uy;    /* [ny][nx] cm/s */
+    const double *lum;   /* [ny][nx] erg/s emitted in the cell */
+} lym1o_problem;
+
+typedef struct {
+    double e_before, e_after;                  /* Lya energy in the domain, erg */
+    double emitted, absorbed, outflow, work;   /* erg over the substep */
+    double residual;                           /* e_after-e_before-(em-abs-out-work) */
+    double max_f;                              /* max |H|/J after the substep */
+    double n_unrealisable;                     /* (cell,bin) with |H| > J(1+1e-12) */
+    double force_abs;                          /* sum |f| dV, dyn */
+    double force_radial;                       /* sum f.rhat dV, dyn */
+} lym1o_diag;
+
+typedef struct {
+    lym1o_problem p;
+    int nb; /* state bins */
+    double dnuD, a_v, sigma0, hkT, eta, dt_cfl;
+    double *dnu, *nubar, *Havg, *gem, *Rk, *half;
+    double *alpha, *gxx, *gyy, *gsh;
+} lym1o_ctx;
+
+static int o_cl(int i, int n) { return i < 0 ? 0 : (i >= n ? n - 1 : i); }
+
+void lym1o_destroy(lym1o_ctx *c)
+{
+    if (!c) return;
+    free(c->dnu); free(c->nubar); free(c->Havg); free(c->gem); free(c->Rk); free(c->half);
+    free(c->alpha); free(c->gxx); free(c->gyy); free(c->gsh);
+    free(c);
+}
+
+lym1o_ctx *lym1o_create(const lym1o_problem *p)
+{
+    if (p->nx < 1 || p->ny < 1 || p->nbins < 1 || p->dx <= 0.0) return NULL;
+    lym1o_ctx *c = (lym1o_ctx *)calloc(1, sizeof *c);
+    c->p = *p;
+    int nx = p->nx, ny = p->ny, N = p->nbins;
+    double ln[3];
+    lym1o_line(p->T, ln);
+    c->dnuD = ln[0];
+    c->a_v = ln[1];
+    c->sigma0 = ln[2];
+    c->hkT = O_HPL / (O_KB * p->T);
+    double *dnu = malloc(N * sizeof(double)), *nub = malloc(N * sizeof(double));
+    double *Hv = malloc(N * sizeof(double)), *w = malloc(N * sizeof(double));
+    c->eta = lym1o_bin_tables(N, p->edges, p->T, dnu, nub, Hv, w);
+    c->nb = p->gray ? 1 : N;
+    int nb = c->nb;
+    c->dnu = malloc(nb * sizeof(double));
+    c->nubar = malloc(nb * sizeof(double));
+    c->Havg = malloc(nb * sizeof(double));
+    c->gem = malloc(nb * sizeof(double));
+    c->Rk = malloc(nb * sizeof(double));
+    c->half = malloc(nb * sizeof(double));
+    double V = (p->dx * p->dx) * p->dx;
+    double fourpiV = (4.0 * O_PI) * V;
+    if (p->gray) {
+        c->dnu[0] = 1.0;
+        c->nubar[0] = O_NU_LYA;
+        c->Havg[0] = c->eta;
+        c->gem[0] = 1.0 / fourpiV;
+        c->Rk[0] = 0.0;
+        c->half[0] = 0.5;
+    } else {
+        for (int k = 0; k < N; ++k) {
+            c->dnu[k] = dnu[k];
+            c->nubar[k] = nub[k];
+            c->Havg[k] = Hv[k];
+            c->gem[k] = w[k] / (fourpiV * dnu[k]);
+            c->Rk[k] = p->recoil ? (c->hkT - 2.0 / nub[k]) : 0.0;
+            c->half[k] = 0.5 * dnu[k];
+        }
+    }
+    free(dnu); free(nub); free(Hv); free(w);
+    size_t nc = (size_t)nx * ny;
+    c->alpha = malloc(nc * sizeof(double));
+    c->gxx = malloc(nc * sizeof(double));
+    c->gyy = malloc(nc * sizeof(double));
+    c->gsh = malloc(nc * sizeof(double));
+    double umax = 0.0;
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            size_t id = (size_t)j * nx + i;
+            c->alpha[id] = p->n_hi[id] * c->sigma0;
+            const double *ux = p->ux, *uy = p->uy;
+            size_t xm = (size_t)j * nx + o_cl(i - 1, nx), xp = (size_t)j * nx + o_cl(i + 1, nx);
+            size_t ym = (size_t)o_cl(j - 1, ny) * nx + i, yp = (size_t)o_cl(j + 1, ny) * nx + i;
+            double h2 = 2.0 * p->dx;
+            c->gxx[id] = (ux[xp] - ux[xm]) / h2;
+            c->gyy[id] = (uy[yp] - uy[ym]) / h2;
+            c->gsh[id] = (ux[yp] - ux[ym]) / h2 + (uy[xp] - uy[xm]) / h2;
+            double um = sqrt(ux[id] * ux[id] + uy[id] * uy[id]);
+            if (um > umax) umax = um;
+        }
+    /* RT time step (Sec. 2.1, CFL condition, D = 2 dimensions) */
+    c->dt_cfl = (p->cfl / 2.0) * (p->dx / (p->c_tilde + umax));
+    return c;
+}
+
+double lym1o_dt_cfl(const lym1o_ctx *c) { return c->dt_cfl; }
+double lym1o_eta(const lym1o_ctx *c) { return c->eta; }
+int lym1o_nb(const lym1o_ctx *c) { return c->nb; }
+void lym1o_tables(const lym1o_ctx *c, double *dnu, double *nubar, double *Havg, double *gem)
+{
+    for (int k = 0; k < c->nb; ++k) {
+        dnu[k] = c->dnu[k];
+        nubar[k] = c->nubar[k];
+        Havg[k] = c->Havg[k];
+        gem[k] = c->gem[k];
+    }
+}
+
+/* ======================================================================
+ * A1: closure and reconstruction helpers
+ * ====================================================================== */
+/* Levermore M1 closure (Sec. 2.1): D = (1-chi)/2 I + (3chi-1)/2 h h, returns
+ * the normal-normal and normal-tangential components for f = (fn, ft). */
+static void o_closure(double fn, double ft, double *Dnn, double *Dnt, double *Dtt)
+{
+    double f2 = fn * fn + ft * ft;
+    double chi = (3.0 + 4.0 * f2) / (5.0 + 2.0 * sqrt(4.0 - 3.0 * f2));
+    double dA = (1.0 - chi) / 2.0, dB = (3.0 * chi - 1.0) / 2.0;
+    if (f2 > 0.0) {
+        *Dnn = dA + (dB * (fn * fn)) / f2;
+        *Dnt = (dB * (fn * ft)) / f2;
+        *Dtt = dA + (dB * (ft * ft)) / f2;
+    } else {
+        *Dnn = dA;
+        *Dnt = 0.0;
+        *Dtt = dA;
+    }
+}
+
+void lym1o_closure(double fx, double fy, double *D3 /* Dxx, Dxy, Dyy */)
+{
+    o_closure(fx, fy, &D3[0], &D3[1], &D3[2]);
+}
+
+/* interpolation factor between GLF and diffusion fluxes (Sec. 2.1) */
+double lym1o_eps(double tau) { return (0.2 + tau) / ((0.2 + tau) + tau * tau); }
+
+static double o_minmod(double a, double b)
+{
+    if (a > 0.0 && b > 0.0) return a < b ? a : b;
+    if (a < 0.0 && b < 0.0) return a > b ? a : b;
+    return 0.0;
+}
+
+/* primitive state of one cell: J and the reduced flux components (n, t) */
+typedef struct { double J, fn, ft; } o_prim;
+
+static o_prim o_make_prim(double J, double Hn, double Ht)
+{
+    o_prim q;
+    q.J = J;
+    if (J > 0.0) {
+        q.fn = Hn / J;
+        q.ft = Ht / J;
+    } else {
+        q.fn = 0.0;
+        q.ft = 0.0;
+    }
+    return q;
+}
+
+/*
+ * A1+A2: flux across the face between cells "0" and "1" (normal direction n,
+ * tangential t).  qm, q0, q1, q2 are the cells at offsets -1, 0, +1, +2 along
+ * the normal.  Returns the flux of J (FJ), of H_n (Fn) and of H_t (Ft).
+ */
+static void o_face(o_prim qm, o_prim q0, o_prim q1, o_prim q2, double aF0, double aF1,
+                   double un0, double un1, double half_dx, double *FJ, double *Fn, double *Ft)
+{
+    /* MinMod-limited linear reconstruction of J, f_n, f_t */
+    double sJ0 = o_minmod(q0.J - qm.J, q1.J - q0.J), sJ1 = o_minmod(q1.J - q0.J, q2.J - q1.J);
+    double sn0 = o_minmod(q0.fn - qm.fn, q1.fn - q0.fn), sn1 = o_minmod(q1.fn - q0.fn, q2.fn - q1.fn);
+    double st0 = o_minmod(q0.ft - qm.ft, q1.ft - q0.ft), st1 = o_minmod(q1.ft - q0.ft, q2.ft - q1.ft);
+    double JL = q0.J + 0.5 * sJ0, fnL = q0.fn + 0.5 * sn0, ftL = q0.ft + 0.5 * st0;
+    double JR = q1.J - 0.5 * sJ1, fnR = q1.fn - 0.5 * sn1, ftR = q1.ft - 0.5 * st1;
+    /* |f| > 1 at the interface: scale the components down */
+    double f2L = fnL * fnL + ftL * ftL;
+    if (f2L > 1.0) {
+        double r = sqrt(f2L);
+        fnL = fnL / r;
+        ftL = ftL / r;
+    }
+    double f2R = fnR * fnR + ftR * ftR;
+    if (f2R > 1.0) {
+        double r = sqrt(f2R);
+        fnR = fnR / r;
+        ftR = ftR / r;
+    }
+    double HnL = JL * fnL, HtL = JL * ftL, HnR = JR * fnR, HtR = JR * ftR;
+    double DnnL, DntL, DttL, DnnR, DntR, DttR;
+    o_closure(fnL, ftL, &DnnL, &DntL, &DttL);
+    o_closure(fnR, ftR, &DnnR, &DntR, &DttR);
+    double KnnL = DnnL * JL, KntL = DntL * JL, KnnR = DnnR * JR, KntR = DntR * JR;
+    /* flux optical depth (Cartesian: centroid at the centre) and eps */
+    double tau = aF0 * half_dx + aF1 * half_dx;
+    double eps = (0.2 + tau) / ((0.2 + tau) + tau * tau);
+    double dif = (tau > 0.0) ? ((1.0 - eps) * (q1.J - q0.J)) / (3.0 * tau) : 0.0;
+    /* corrected GLF flux for J, modified GLF flux for K */
+    double fJ = (eps * (0.5 * (HnL + HnR)) - eps * (0.5 * (JR - JL))) - dif;
+    double fn = 0.5 * (KnnL + KnnR) - eps * (0.5 * (HnR - HnL));
+    double ft = 0.5 * (KntL + KntR) - eps * (0.5 * (HtR - HtL));
+    /* upwind advection of uJ/c and uH/c with the face velocity */
+    double uf = 0.5 * (un0 + un1);
+    if (uf > 0.0) {
+        fJ = fJ + (uf * JL) / O_C;
+        fn = fn + (uf * HnL) / O_C;
+        ft = ft + (uf * HtL) / O_C;
+    } else if (uf < 0.0) {
+        fJ = fJ + (uf * JR) / O_C;
+        fn = fn + (uf * HnR) / O_C;
+        ft = ft + (uf * HtR) / O_C;
+    }
+    *FJ = fJ;
+    *Fn = fn;
+    *Ft = ft;
+}
+
+/* exported for unit pins: flux across one face from 4 cells along the normal */
+void lym1o_face_flux(const double *J4, const double *Hn4, const double *Ht4, double aF0, double aF1,
+                     double un0, double un1, double dx, double *out3)
+{
+    o_prim q[4];
+    for (int m = 0; m < 4; ++m) q[m] = o_make_prim(J4[m], Hn4[m], Ht4[m]);
+    o_face(q[0], q[1], q[2], q[3], aF0, aF1, un0, un1, 0.5 * dx, &out3[0], &out3[1], &out3[2]);
+}
+
+/* ======================================================================
+ * A6: frequency step for one cell (App. A)
+ * ====================================================================== */
+/*
+ * Solves (J_k - Jin_k)/(ct dt) = F+_k J_{k+1} - F_k J_k + F-_k J_{k-1} with
+ * zero-flux ends, K_k = dnuD^2 alpha <H>_k / 2, C_k = K_k R_k + (nubar_k/c)
+ * DdU_k, P_k = C_k dlt_k / K_k (dlt_k = half bin width, midpoint centres).
+ *
+ * Leakage coefficients (App. A) written per interface k+1/2 as
+ *   A = (1 - phiL(P_k)) / den,   B = (1 - phiR(P_{k+1})) / den,
+ *   den = chiL(P_k) dlt_k/K_k - chiR(P_{k+1}) dlt_{k+1}/K_{k+1},
+ * so that dnu_k F+_k = B_{k+1/2}, dnu_k F-_k = A_{k-1/2},
+ * dnu_k F_k = A_{k+1/2} + B_{k-1/2}.  With E(z) = expm1(z)/z (z <= 0, E(0) = 1):
+ *   chiL(P) = exp(max(-P,0)) E(-|P|),  -chiR(P) = exp(max(P,0)) E(-|P|),
+ * and the common factor exp(m), m = max(0, -P_k, P_{k+1}), is divided out of
+ * numerators and denominator, so all exponentials have non-positive arguments.
+ *
+ * Elimination in conservative form (row k times dnu_k, s_k = dnu_k/(ct dt)):
+ *   (s_k + A_{k+1/2} + B_{k-1/2}) J_k - B_{k+1/2} J_{k+1} - A_{k-1/2} J_{k-1} = s_k Jin_k.
+ * Forward: E_0 = s_0, E_k = s_k + B_{k-1/2} q_{k-1}, D'_k = E_k + A_{k+1/2},
+ *   r_k = s_k Jin_k + A_{k-1/2} g_{k-1}, with inv = 1/D'_k, q_k = E_k inv,
+ *   g_k = r_k inv, h_k = B_{k+1/2} inv.
+ * Back: J_{N-1} = g_{N-1}, J_k = g_k + h_k J_{k+1}.
+ * Every quantity is a sum or product of non-negative terms for Jin >= 0.
+ */
+static void o_freq_cell(int N, const double *dnu, const double *half, const double *Havg,
+                        const double *Rk, const double *nubar_c, double Kc, const double *DdU,
+                        double cdt, const double *Jin, double *Jout, double *scr /* 6N */)
+{
+    double *P = scr, *a = scr + N, *e = scr + 2 * N, *g = scr + 3 * N, *hh = scr + 4 * N;
+    for (int k = 0; k < N; ++k) {
+        double K = Kc * Havg[k];
+        double C = K * Rk[k] + nubar_c[k] * DdU[k];
+        P[k] = (C * half[k]) / K;
+        a[k] = half[k] / K;
+        double z = -fabs(P[k]);
+        e[k] = (z == 0.0) ? 1.0 : lym1o_expm1(z) / z;
+    }
+    double Eprev = 0.0, qprev = 0.0, gprev = 0.0, Bprev = 0.0, Aprev = 0.0;
+    for (int k = 0; k < N; ++k) {
+        double Ak = 0.0, Bk = 0.0; /* interface k+1/2 */
+        if (k + 1 < N) {
+            double p = P[k], q = P[k + 1];
+            double d1 = (-p > 0.0) ? -p : 0.0, d2 = (q > 0.0) ? q : 0.0;
+            double m = (d1 > d2) ? d1 : d2;
+            double den = lym1o_exp(d1 - m) * (e[k] * a[k]) + lym1o_exp(d2 - m) * (e[k + 1] * a[k + 1]);
+            Ak = lym1o_exp(-p - m) / den;
+            Bk = lym1o_exp(q - m) / den;
+        }
+        double s = dnu[k] / cdt;
+        double E = (k == 0) ? s : s + Bprev * qprev;
+        double r = (k == 0) ? s * Jin[k] : s * Jin[k] + Aprev * gprev;
+        double Dp = E + Ak;
+        double inv = 1.0 / Dp;
+        g[k] = r * inv;
+        hh[k] = Bk * inv;
+        qprev = E * inv;
+        gprev = g[k];
+        Eprev = E;
+        Bprev = Bk;
+        Aprev = Ak;
+    }
+    (void)Eprev;
+    Jout[N - 1] = g[N - 1];
+    for (int k = N - 2; k >= 0; --k) Jout[k] = g[k] + hh[k] * Jout[k + 1];
+}
+
+/* exported for pins: one cell's frequency step with given per-bin D:grad(u) */
+void lym1o_freq_solve(int N, const double *edges, double T, double alpha, int recoil,
+                      const double *DdU, double cdt, const double *Jin, double *Jout)
+{
+    double ln[3];
+    lym1o_line(T, ln);
+    double *dnu = malloc(N * sizeof(double)), *nub = malloc(N * sizeof(double));
+    double *Hv = malloc(N * sizeof(double)), *w = malloc(N * sizeof(double));
+    double *half = malloc(N * sizeof(double)), *Rk = malloc(N * sizeof(double));
+    double *nbc = malloc(N * sizeof(double)), *scr = malloc(6 * N * sizeof(double));
+    lym1o_bin_tables(N, edges, T, dnu, nub, Hv, w);
+    double hkT = O_HPL / (O_KB * T);
+    for (int k = 0; k < N; ++k) {
+        half[k] = 0.5 * dnu[k];
+        Rk[k] = recoil ? (hkT - 2.0 / nub[k]) : 0.0;
+        nbc[k] = nub[k] / O_C;
+    }
+    double Kc = (0.5 * (ln[0] * ln[0])) * alpha;
+    o_freq_cell(N, dnu, half, Hv, Rk, nbc, Kc, DdU, cdt, Jin, Jout, scr);
+    free(dnu); free(nub); free(Hv); free(w); free(half); free(Rk); free(nbc); free(scr);
+}
+
+/* exported for pins: leakage coefficients A_{k+1/2}, B_{k+1/2} (N-1 each) */
+void lym1o_leakage(int N, const double *edges, double T, double alpha, int recoil,
+                   const double *DdU, double *Aout, double *Bout)
+{
+    double ln[3];
+    lym1o_line(T, ln);
+    double *dnu = malloc(N * sizeof(double)), *nub = malloc(N * sizeof(double));
+    double *Hv = malloc(N * sizeof(double)), *w = malloc(N * sizeof(double));
+    double *P = malloc(N * sizeof(double)), *a = malloc(N * sizeof(double)), *e = malloc(N * sizeof(double));
+    lym1o_bin_tables(N, edges, T, dnu, nub, Hv, w);
+    double hkT = O_HPL / (O_KB * T);
+    double Kc = (0.5 * (ln[0] * ln[0])) * alpha;
+    for (int k = 0; k < N; ++k) {
+        double half = 0.5 * dnu[k], K = Kc * Hv[k];
+        double Rk = recoil ? (hkT - 2.0 / nub[k]) : 0.0;
+        double C = K * Rk + (nub[k] / O_C) * DdU[k];
+        P[k] = (C * half) / K;
+        a[k] = half / K;
+        double z = -fabs(P[k]);
+        e[k] = (z == 0.0) ? 1.0 : lym1o_expm1(z) / z;
+    }
+    for (int k = 0; k + 1 < N; ++k) {
+        double p = P[k], q = P[k + 1];
+        double d1 = (-p > 0.0) ? -p : 0.0, d2 = (q > 0.0) ? q : 0.0;
+        double m = (d1 > d2) ? d1 : d2;
+        double den = lym1o_exp(d1 - m) * (e[k] * a[k]) + lym1o_exp(d2 - m) * (e[k + 1] * a[k + 1]);
+        Aout[k] = lym1o_exp(-p - m) / den;
+        Bout[k] = lym1o_exp(q - m) / den;
+    }
+    free(dnu); free(nub); free(Hv); free(w); free(P); free(a); free(e);
+}
+
+/* ======================================================================
+ * Neumaier compensated sum
+ * ====================================================================== */
+typedef struct { double s, c; } o_ksum;
+static void o_kadd(o_ksum *a, double v)
+{
+    double t = a->s + v;
+    if (fabs(a->s) >= fabs(v))
+        a->c += (a->s - t) + v;
+    else
+        a->c += (v - t) + a->s;
+    a->s = t;
+}
+static double o_kval(const o_ksum *a) { return a->s + a->c; }
+
+static double o_energy(const lym1o_ctx *c, const double *J)
+{
+    size_t nc = (size_t)c->p.nx * c->p.ny;
+    o_ksum S = {0.0, 0.0};
+    for (int k = 0; k < c->nb; ++k)
+        for (size_t id = 0; id < nc; ++id) o_kadd(&S, c->dnu[k] * J[(size_t)k * nc + id]);
+    double V = (c->p.dx * c->p.dx) * c->p.dx;
+    return ((4.0 * O_PI) / O_C) * V * o_kval(&S);
+}
+
+double lym1o_energy(const lym1o_ctx *c, const double *J) { return o_energy(c, J); }
+
+/* ======================================================================
+ * One substep of length dt: state (J, Hx, Hy) [k][y][x] -> (Jo, Hxo, Hyo),
+ * force (fx, fy) [y][x] in dyn cm^-3.  Input and output may not alias.
+ * ====================================================================== */
+int lym1o_substep(const lym1o_ctx *c, double dt, const double *J, const double *Hx,
+                  const double *Hy, double *Jo, double *Hxo, double *Hyo, double *fx,
+                  double *fy, lym1o_diag *dg)
+{
+    const lym1o_problem *p = &c->p;
+    const int nx = p->nx, ny = p->ny, nb = c->nb;
+    const size_t nc = (size_t)nx * ny;
+    const double dx = p->dx, half_dx = 0.5 * dx, cdt = p->c_tilde * dt;
+    const double V = (dx * dx) * dx;
+    const double eunit = ((4.0 * O_PI) / O_C) * V; /* erg per (Hz-weighted J) per cell */
+    lym1o_diag d;
+    memset(&d, 0, sizeof d);
+    d.e_before = o_energy(c, J);
+    o_ksum s_em = {0, 0}, s_ab = {0, 0}, s_out = {0, 0}, s_wk = {0, 0};
+
+    /* per-bin work arrays */
+    double *FJx = malloc((size_t)(nx + 1) * ny * sizeof(double));
+    double *FHxx = malloc((size_t)(nx + 1) * ny * sizeof(double));
+    double *FHyx = malloc((size_t)(nx + 1) * ny * sizeof(double));
+    double *FJy = malloc((size_t)nx * (ny + 1) * sizeof(double));
+    double *FHxy = malloc((size_t)nx * (ny + 1) * sizeof(double));
+    double *FHyy = malloc((size_t)nx * (ny + 1) * sizeof(double));
+    double *Wk = malloc(nc * sizeof(double));
+    double *ax = malloc(nc * sizeof(double)), *ay = malloc(nc * sizeof(double));
+    for (size_t id = 0; id < nc; ++id) {
+        ax[id] = 0.0;
+        ay[id] = 0.0;
+    }
+
+    for (int k = 0; k < nb; ++k) {
+        const double *Jk = J + (size_t)k * nc, *Hxk = Hx + (size_t)k * nc, *Hyk = Hy + (size_t)k * nc;
+        const double Hk = c->Havg[k];
+#define AF(id) (c->alpha[id] * Hk + p->rho_d[id] * p->kappa_F)
+        /* x faces: face i sits between cells i-1 and i, i = 0..nx */
+#pragma omp parallel for schedule(static)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i <= nx; ++i) {
+                size_t im = (size_t)j * nx + o_cl(i - 2, nx), i0 = (size_t)j * nx + o_cl(i - 1, nx);
+                size_t i1 = (size_t)j * nx + o_cl(i, nx), i2 = (size_t)j * nx + o_cl(i + 1, nx);
+                o_prim qm = o_make_prim(Jk[im], Hxk[im], Hyk[im]);
+                o_prim q0 = o_make_prim(Jk[i0], Hxk[i0], Hyk[i0]);
+                o_prim q1 = o_make_prim(Jk[i1], Hxk[i1], Hyk[i1]);
+                o_prim q2 = o_make_prim(Jk[i2], Hxk[i2], Hyk[i2]);
+                size_t f = (size_t)j * (nx + 1) + i;
+                o_face(qm, q0, q1, q2, AF(i0), AF(i1), p->ux[i0], p->ux[i1], half_dx, &FJx[f],
+                       &FHxx[f], &FHyx[f]);
+            }
+        /* y faces: face j sits between rows j-1 and j, j = 0..ny */
+#pragma omp parallel for schedule(static)
+        for (int j = 0; j <= ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                size_t im = (size_t)o_cl(j - 2, ny) * nx + i, i0 = (size_t)o_cl(j - 1, ny) * nx + i;
+                size_t i1 = (size_t)o_cl(j, ny) * nx + i, i2 = (size_t)o_cl(j + 1, ny) * nx + i;
+                o_prim qm = o_make_prim(Jk[im], Hyk[im], Hxk[im]);
+                o_prim q0 = o_make_prim(Jk[i0], Hyk[i0], Hxk[i0]);
+                o_prim q1 = o_make_prim(Jk[i1], Hyk[i1], Hxk[i1]);
+                o_prim q2 = o_make_prim(Jk[i2], Hyk[i2], Hxk[i2]);
+                size_t f = (size_t)j * nx + i;
+                o_face(qm, q0, q1, q2, AF(i0), AF(i1), p->uy[i0], p->uy[i1], half_dx, &FJy[f],
+                       &FHyy[f], &FHxy[f]);
+            }
+        /* A3 explicit update, A4 implicit source, A5 force accumulation */
+#pragma omp parallel for schedule(static)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                size_t id = (size_t)j * nx + i, kid = (size_t)k * nc + id;
+                o_prim q = o_make_prim(Jk[id], Hxk[id], Hyk[id]);
+                double fxc = q.fn, fyc = q.ft, f2 = fxc * fxc + fyc * fyc;
+                if (f2 > 1.0) {
+                    double r = sqrt(f2);
+                    fxc = fxc / r;
+                    fyc = fyc / r;
+                }
+                double Dxx, Dxy, Dyy;
+                o_closure(fxc, fyc, &Dxx, &Dxy, &Dyy);
+                double W = ((Dxx * Jk[id]) * c->gxx[id] + (Dyy * Jk[id]) * c->gyy[id]) +
+                           (Dxy * Jk[id]) * c->gsh[id];
+                Wk[id] = W;
+                size_t fxl = (size_t)j * (nx + 1) + i, fyl = (size_t)j * nx + i;
+                double divJ = (FJx[fxl + 1] - FJx[fxl]) + (FJy[fyl + nx] - FJy[fyl]);
+                double divHx = (FHxx[fxl + 1] - FHxx[fxl]) + (FHxy[fyl + nx] - FHxy[fyl]);
+                double divHy = (FHyx[fxl + 1] - FHyx[fxl]) + (FHyy[fyl + nx] - FHyy[fyl]);
+                double J1 = Jk[id] - cdt * (divJ / dx + W / O_C);
+                double Hx1 = Hxk[id] - cdt * (divHx / dx);
+                double Hy1 = Hyk[id] - cdt * (divHy / dx);
+                /* A4: (J''-J')/(ct dt) = j - kappa J'', (H''-H')/(ct dt) = -aF H'' */
+                double aH = c->alpha[id] * Hk;
+                double kap = p->rho_d[id] * p->kappa_abs + p->p_d[id] * aH;
+                double aF = aH + p->rho_d[id] * p->kappa_F;
+                double js = p->lum[id] * c->gem[k];
+                double J2 = (J1 + cdt * js) / (1.0 + cdt * kap);
+                double Hx2 = Hx1 / (1.0 + cdt * aF);
+                double Hy2 = Hy1 / (1.0 + cdt * aF);
+                Jo[kid] = J2;
+                Hxo[kid] = Hx2;
+                Hyo[kid] = Hy2;
+                ax[id] = ax[id] + c->dnu[k] * (Hx1 - Hx2);
+                ay[id] = ay[id] + c->dnu[k] * (Hy1 - Hy2);
+            }
+        /* bookkeeping for this bin (serial, fixed order) */
+        for (size_t id = 0; id < nc; ++id) {
+            size_t kid = (size_t)k * nc + id;
+            double aH = c->alpha[id] * Hk;
+            double kap = p->rho_d[id] * p->kappa_abs + p->p_d[id] * aH;
+            double js = p->lum[id] * c->gem[k];
+            o_kadd(&s_em, c->dnu[k] * (cdt * js));
+            o_kadd(&s_ab, c->dnu[k] * (cdt * (kap * Jo[kid])));
+            o_kadd(&s_wk, c->dnu[k] * (cdt * (Wk[id] / O_C)));
+        }
+        for (int j = 0; j < ny; ++j) {
+            o_kadd(&s_out, c->dnu[k] * (cdt * (-FJx[(size_t)j * (nx + 1)] / dx)));
+            o_kadd(&s_out, c->dnu[k] * (cdt * (FJx[(size_t)j * (nx + 1) + nx] / dx)));
+        }
+        for (int i = 0; i < nx; ++i) {
+            o_kadd(&s_out, c->dnu[k] * (cdt * (-FJy[i] / dx)));
+            o_kadd(&s_out, c->dnu[k] * (cdt * (FJy[(size_t)ny * nx + i] / dx)));
+        }
+#undef AF
+    }
+    /* A5: f = 4 pi / (c ct dt) sum_k dnu_k (H' - H'') */
+    const double fcoef = (4.0 * O_PI) / ((O_C * p->c_tilde) * dt);
+    for (size_t id = 0; id < nc; ++id) {
+        fx[id] = fcoef * ax[id];
+        fy[id] = fcoef * ay[id];
+    }
+
+    /* A6: frequency step per cell, in place on (Jo, Hxo, Hyo) */
+    if (!p->gray && p->freq_step) {
+        const double Kc0 = 0.5 * (c->dnuD * c->dnuD);
+        double *nbc = malloc(nb * sizeof(double));
+        for (int k = 0; k < nb; ++k) nbc[k] = c->nubar[k] / O_C;
+#pragma omp parallel
+        {
+            double *scr = malloc((size_t)6 * nb * sizeof(double));
+            double *Jin = malloc(nb * sizeof(double)), *Jn = malloc(nb * sizeof(double));
+            double *DdU = malloc(nb * sizeof(double));
+#pragma omp for schedule(static)
+            for (long long idl = 0; idl < (long long)nc; ++idl) {
+                size_t id = (size_t)idl;
+                if (!(c->alpha[id] > 0.0)) continue;
+                for (int k = 0; k < nb; ++k) {
+                    size_t kid = (size_t)k * nc + id;
+                    o_prim q = o_make_prim(Jo[kid], Hxo[kid], Hyo[kid]);
+                    double fxc = q.fn, fyc = q.ft, f2 = fxc * fxc + fyc * fyc;
+                    if (f2 > 1.0) {
+                        double r = sqrt(f2);
+                        fxc = fxc / r;
+                        fyc = fyc / r;
+                    }
+                    double Dxx, Dxy, Dyy;
+                    o_closure(fxc, fyc, &Dxx, &Dxy, &Dyy);
+                    DdU[k] = (Dxx * c->gxx[id] + Dyy * c->gyy[id]) + Dxy * c->gsh[id];
+                    Jin[k] = Jo[kid];
+                }
+                o_freq_cell(nb, c->dnu, c->half, c->Havg, c->Rk, nbc, Kc0 * c->alpha[id], DdU, cdt,
+                            Jin, Jn, scr);
+                for (int k = 0; k < nb; ++k) {
+                    size_t kid = (size_t)k * nc + id;
+                    double ratio = (Jin[k] > 0.0) ? Jn[k] / Jin[k] : 0.0;
+                    Jo[kid] = Jn[k];
+                    Hxo[kid] = ratio * Hxo[kid];
+                    Hyo[kid] = ratio * Hyo[kid];
+                }
+            }
+            free(scr); free(Jin); free(Jn); free(DdU);
+        }
+        free(nbc);
+    }
+
+    /* A7: diagnostics */
+    d.e_after = o_energy(c, Jo);
+    d.emitted = eunit * o_kval(&s_em);
+    d.absorbed = eunit * o_kval(&s_ab);
+    d.outflow = eunit * o_kval(&s_out);
+    d.work = eunit * o_kval(&s_wk);
+    d.residual = (d.e_after - d.e_before) - (((d.emitted - d.absorbed) - d.outflow) - d.work);
+    double maxf = 0.0, nbad = 0.0;
+    for (int k = 0; k < nb; ++k)
+        for (size_t id = 0; id < nc; ++id) {
+            size_t kid = (size_t)k * nc + id;
+            double hn = sqrt(Hxo[kid] * Hxo[kid] + Hyo[kid] * Hyo[kid]);
+            if (Jo[kid] > 0.0) {
+                double f = hn / Jo[kid];
+                if (f > maxf) maxf = f;
+            }
+            if (hn > Jo[kid] * (1.0 + 1e-12) && hn > 0.0) nbad += 1.0;
+        }
+    d.max_f = maxf;
+    d.n_unrealisable = nbad;
+    o_ksum fa = {0, 0}, fr = {0, 0};
+    double cx = 0.5 * nx * dx, cy = 0.5 * ny * dx;
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            size_t id = (size_t)j * nx + i;
+            double x = (i + 0.5) * dx - cx, y = (j + 0.5) * dx - cy, r = sqrt(x * x + y * y);
+            o_kadd(&fa, sqrt(fx[id] * fx[id] + fy[id] * fy[id]) * V);
+            if (r > 0.0) o_kadd(&fr, ((fx[id] * x + fy[id] * y) / r) * V);
+        }
+    d.force_abs = o_kval(&fa);
+    d.force_radial = o_kval(&fr);
+    if (dg) *dg = d;
+    free(FJx); free(FHxx); free(FHyx); free(FJy); free(FHxy); free(FHyy); free(Wk); free(ax); free(ay);
+    return 0;
+}
+
+void lym1o_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
+int lym1o_get_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

@@ -1,0 +1,19 @@
+"""Shared pytest configuration: the `gpu` marker and small helpers."""
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def pytest_configure(config):
+    config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300) and the built CUDA library")
+
+
+@pytest.fixture(scope="session")
+def paper_edges():
+    import oracle
+    return oracle.freq_grid(30.0, 1.1)

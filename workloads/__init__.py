@@ -1,0 +1,176 @@
+"""Seeded synthetic inputs for the Lya M1 substep: clouds shaped like the paper's setups.
+
+This module is shared by the GPU path's tests/bench and by the oracle's tests.
+It only draws and lays out input fields (densities, dust, velocities, sources);
+it holds none of the M1 method's arithmetic.  All randomness comes from
+numpy's counter-based Philox generator with an explicit seed.
+
+Physical setup readings (each cites the paper, arXiv 2606.02711):
+  * dust-to-gas: D/D_sun = Z/Z_sun with D_sun = 1/162 (Sec. 5 cluster setup and the
+    dust-to-gas normalisation), gas mass density rho = 1.333 m_H n_H;
+  * Lya dust opacities: mass-fraction-weighted Table 1 Lya row with f_Sil =
+    0.7264, f_C = 0.2517, f_PAH = 0.0218 (Table 1 caption);
+  * all hydrogen neutral (n_HI = n_H), T = 1e4 K;
+  * a point source is spread equally over the central 2x2 cells;
+  * velocity u = v_edge (r / r_edge) r_hat about the box centre.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+L_SUN = 3.828e33          # erg/s
+PC = 3.0857e18            # cm
+M_H = 1.67353284e-24      # g
+KM = 1.0e5                # cm
+C_LIGHT = 2.99792458e10   # cm/s
+
+# Table 1, Lya row (cm^2 per g of dust in the bin) and dust mass fractions
+_F_BIN = (0.7264, 0.2517, 0.0218)
+_KABS = (1.84e4, 2.48e4, 3.31e5)
+_KF = (2.22e4, 2.84e4, 3.31e5)
+KAPPA_ABS = sum(f * k for f, k in zip(_F_BIN, _KABS))
+KAPPA_F = sum(f * k for f, k in zip(_F_BIN, _KF))
+DUST_TO_GAS_SUN = 1.0 / 162.0
+
+
+def rng(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.Philox(int(seed)))
+
+
+def gaussian_field(nx: int, ny: int, seed: int, slope: float = -4.0) -> np.ndarray:
+    """Unit-variance Gaussian random field with 2D power spectrum P(k) ~ |k|^slope
+    (k != 0), built by filtering seeded white noise with numpy's FFT."""
+    g = rng(seed)
+    white = g.standard_normal((ny, nx))
+    Wk = np.fft.rfft2(white)
+    ky = np.fft.fftfreq(ny)[:, None]
+    kx = np.fft.rfftfreq(nx)[None, :]
+    k2 = kx * kx + ky * ky
+    amp = np.zeros_like(k2)
+    amp[k2 > 0] = k2[k2 > 0] ** (slope / 4.0)   # sqrt(P) = |k|^(slope/2)
+    f = np.fft.irfft2(Wk * amp, s=(ny, nx))
+    f -= f.mean()
+    sd = f.std()
+    return f / sd if sd > 0 else f
+
+
+def lognormal_density(nx, ny, mean, sigma_ln, seed) -> np.ndarray:
+    """n = mean * exp(sigma g - sigma^2/2), rescaled to sample mean `mean`."""
+    g = gaussian_field(nx, ny, seed)
+    n = np.exp(sigma_ln * g - 0.5 * sigma_ln * sigma_ln)
+    return n * (mean / n.mean())
+
+
+def radial_velocity(nx, ny, dx, v_edge=10 * KM, r_edge=1.0 * PC):
+    x = (np.arange(nx) + 0.5) * dx - 0.5 * nx * dx
+    y = (np.arange(ny) + 0.5) * dx - 0.5 * ny * dx
+    X, Y = np.meshgrid(x, y)
+    s = v_edge / r_edge
+    return s * X, s * Y
+
+
+def central_source(nx, ny, L) -> np.ndarray:
+    lum = np.zeros((ny, nx))
+    i0, j0 = nx // 2 - 1, ny // 2 - 1
+    lum[j0:j0 + 2, i0:i0 + 2] = L / 4.0
+    return lum
+
+
+def dust_density(n_h, Z_over_Zsun) -> np.ndarray:
+    return (Z_over_Zsun * DUST_TO_GAS_SUN) * (1.333 * M_H) * n_h
+
+
+@dataclass
+class Cloud:
+    """Inputs of one solve: grid, groups, opacities and sources."""
+    name: str
+    nx: int
+    ny: int
+    dx: float
+    n_hi: np.ndarray
+    rho_d: np.ndarray
+    p_d: np.ndarray
+    ux: np.ndarray
+    uy: np.ndarray
+    lum: np.ndarray
+    T: float = 1.0e4
+    gray: bool = False
+    recoil: bool = True
+    freq_step: bool = True
+    kappa_abs: float = KAPPA_ABS
+    kappa_F: float = KAPPA_F
+    c_tilde: float = C_LIGHT
+    cfl: float = 0.4
+    substeps: int = 1
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def L_total(self) -> float:
+        return float(self.lum.sum())
+
+    def kwargs(self) -> dict:
+        """Keyword arguments common to the oracle and the GPU binding."""
+        return dict(nx=self.nx, ny=self.ny, dx=self.dx, T=self.T, n_hi=self.n_hi,
+                    rho_d=self.rho_d, p_d=self.p_d, ux=self.ux, uy=self.uy, lum=self.lum,
+                    kappa_abs=self.kappa_abs, kappa_F=self.kappa_F, c_tilde=self.c_tilde,
+                    cfl=self.cfl, gray=self.gray, recoil=self.recoil,
+                    freq_step=self.freq_step)
+
+
+def uniform_gray(nx=64, ny=64, box_pc=2.0, n_h=1e3, L_sun=1e6, name="uniform-gray"):
+    """Static uniform neutral cloud, one gray group, central point source, no
+    dust, no velocity, p_d = 0 (64x64, 2 pc, n_H = 1e3, 1e6 L_sun at full size)."""
+    dx = box_pc * PC / nx
+    z = np.zeros((ny, nx))
+    return Cloud(name, nx, ny, dx, np.full((ny, nx), float(n_h)), z.copy(), z.copy(), z.copy(),
+                 z.copy(), central_source(nx, ny, L_sun * L_SUN), gray=True, substeps=2000)
+
+
+def lognormal_cloud(nx=512, ny=512, box_pc=2.0, mean_nh=1e3, sigma_ln=1.0, Z=0.01, L_sun=1e6,
+                    seed=1, p_d=1e-12, v_edge_kms=10.0, name="lognormal", substeps=500):
+    """Lognormal n_H (k^-4 spectrum), dust at Z/Z_sun, v ~ r with v_edge at 1 pc,
+    central source, 194 frequency bins at T = 1e4 K."""
+    dx = box_pc * PC / nx
+    n_h = lognormal_density(nx, ny, mean_nh, sigma_ln, seed)
+    ux, uy = radial_velocity(nx, ny, dx, v_edge_kms * KM, 1.0 * PC)
+    return Cloud(name, nx, ny, dx, n_h, dust_density(n_h, Z), np.full((ny, nx), float(p_d)), ux,
+                 uy, central_source(nx, ny, L_sun * L_SUN), substeps=substeps,
+                 meta={"seed": seed, "sigma_ln": sigma_ln, "mean_nh": mean_nh, "Z": Z})
+
+
+def config_lognormal_512(seed=1):
+    """512x512, 194 bins, sigma_ln = 1.0, mean n_H 1e3, Z = 0.01 Z_sun, 1e6 L_sun."""
+    return lognormal_cloud(512, 512, mean_nh=1e3, sigma_ln=1.0, Z=0.01, L_sun=1e6, seed=seed,
+                           name="lognormal-512", substeps=500)
+
+
+def config_lognormal_2048(seed=1):
+    """2048x2048, 194 bins, sigma_ln = 1.5, mean n_H 1e4, Z = 1e-3 Z_sun, 1e7 L_sun."""
+    return lognormal_cloud(2048, 2048, mean_nh=1e4, sigma_ln=1.5, Z=1e-3, L_sun=1e7, seed=seed,
+                           name="lognormal-2048", substeps=5000)
+
+
+def batch_clouds(n=256, base_seed=1000, side_lo=64, side_hi=512):
+    """Independent clouds for a batched sweep: side log-uniform in
+    [side_lo, side_hi] rounded to a multiple of 16, mean n_H log-uniform
+    [1e2, 1e5], L log-uniform [1e4, 1e7] L_sun, Z in {0, 1e-3, 1e-2} Z_sun."""
+    g = rng(base_seed)
+    out = []
+    for i in range(n):
+        side = int(round(math.exp(g.uniform(math.log(side_lo), math.log(side_hi))) / 16.0)) * 16
+        side = max(16, side)
+        mean = 10 ** g.uniform(2, 5)
+        L = 10 ** g.uniform(4, 7)
+        Z = (0.0, 1e-3, 1e-2)[int(g.integers(0, 3))]
+        out.append(lognormal_cloud(side, side, mean_nh=mean, sigma_ln=1.0, Z=Z, L_sun=L,
+                                   seed=base_seed + 1 + i, name=f"batch-{i}", substeps=1000))
+    return out
+
+
+def poisson_arrivals(n=1000, rate=50.0, seed=7):
+    """Seeded Poisson arrival times (s) for a request stream."""
+    g = rng(seed)
+    return np.cumsum(g.exponential(1.0 / rate, size=n))
