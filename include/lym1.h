@@ -1,0 +1,229 @@
+/*
+ * lym1.h -- C ABI of a GB300 (sm_103a) implementation of one substep of the
+ * Lydion M1 method for Lyman-alpha radiative transfer on a 2D grid
+ * (arXiv 2606.02711, "Lydion").
+ *
+ * One substep of length dt (Sec. 2.1, "overall update scheme"), per cell and
+ * frequency bin k:
+ *   1. explicit finite-volume transport of J and H with the M1 (Levermore)
+ *      closure, MinMod-limited reconstruction of J and f = H/J, the
+ *      asymptotic-preserving GLF flux for J, the modified GLF flux for K and
+ *      upwind advection of uJ/c, uH/c, plus the -grad(u):K/c work term
+ *      (Sec. 2.1 step 1);
+ *   2. implicit emission / dust absorption / destruction of J and H
+ *      (Sec. 2.1 step 2, absorption-step equations);
+ *   3. the Lya radiation force f = 4 pi/(c ct) sum_k dnu_k (H' - H'')/dt
+ *      (Sec. 2.3, force equation);
+ *   4. the implicit (BDF1) frequency diffusion + recoil + Doppler solve per
+ *      cell with the exponential scheme, then H <- (J_new/J_old) H
+ *      (Sec. 2.1 step 3 and App. A).
+ *
+ * Geometry: 2D Cartesian, uniform square cells of width dx; the slab has depth
+ * dx (cell volume dx^3).  Boundaries: outflow (two ghost layers that copy the
+ * edge cell).  State per (bin, cell): J, Hx, Hy in erg cm^-2 s^-1 Hz^-1 sr^-1
+ * (frequency-integrated, erg cm^-2 s^-1 sr^-1, for a gray group).
+ * Array layout: per-cell fields [ny][nx] (x fastest), state [nb][ny][nx].
+ *
+ * Memory: the library allocates and owns all device memory of a context.
+ * Caller buffers may be host (pageable or pinned) or device pointers: copies
+ * use unified addressing.  The library never keeps a caller pointer after a
+ * call returns.  A context is bound to one CUDA stream and is not thread-safe.
+ *
+ * Errors: every function returns LYM1_OK (0) or a negative code below.  On
+ * error the context state is unchanged unless stated otherwise.
+ */
+#ifndef LYM1_H
+#define LYM1_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LYM1_OK 0
+#define LYM1_EINVAL (-1)         /* invalid argument (null pointer, size, option) */
+#define LYM1_ENOMEM (-2)         /* device allocation failed */
+#define LYM1_ECUDA (-3)          /* a CUDA runtime call or kernel launch failed */
+#define LYM1_ENONFINITE (-4)     /* a diagnostic sum is not finite (NaN/Inf in the state) */
+#define LYM1_ETIMEOUT (-5)       /* a bounded device wait expired */
+#define LYM1_ENOTCONVERGED (-6)  /* substep cap reached before the steady-state test passed */
+#define LYM1_ENODEVICE (-7)      /* no CUDA device is usable */
+
+/* Arithmetic of the substep. */
+#define LYM1_FP64_DET 0    /* FP64, fixed operation order, no FMA contraction, own exp/expm1 */
+#define LYM1_FP64 1        /* FP64 with FMA and hardware exp/expm1 */
+#define LYM1_MIXED 2       /* FP32 state, transport and closure; FP64 implicit steps 2-3 and force */
+#define LYM1_MIXED_FAST 3  /* FP32 everywhere but the per-cell FP64 sums; subtraction-free solve */
+
+typedef struct lym1_ctx lym1_ctx;
+
+typedef struct {
+  int nx, ny;      /* cells in x and y, each >= 1 */
+  double dx_cm;    /* cell width (cm), > 0 */
+  int geometry;    /* 0 = 2D Cartesian; the only value accepted */
+  int bc[4];       /* x-, x+, y-, y+ : 0 = outflow; the only value accepted */
+} lym1_grid;
+
+typedef struct {
+  int n_bins;                  /* bins in edges_dnu_hz (n_bins + 1 edges), ignored if edges is NULL */
+  const double *edges_dnu_hz;  /* ascending bin edges in nu - nu_Lya (Hz), host memory, or NULL for
+                                  the paper's grid (Sec. 2.1): widths dnu_D(T_min) q^j, |dnu| <=
+                                  min(1e5 dnu_D(T_min), 0.99 nu_Lya, nu_LyC - nu_Lya) */
+  double q;                    /* growth factor of the paper grid (0 => 1.1) */
+  double T_min;                /* resolution temperature of the paper grid, K (0 => 30) */
+  int gray;                    /* 1: one gray group with opacity alpha*eta, eta = sum_k w_k <H>_k
+                                  over the grid; no frequency step */
+} lym1_groups;
+
+typedef struct {
+  const double *n_hi;     /* [ny][nx] neutral hydrogen density, cm^-3 (alpha = n_hi sigma0) */
+  const double *rho_dust; /* [ny][nx] dust mass density, g cm^-3 */
+  const double *p_d;      /* [ny][nx] Lya destruction probability per scattering */
+  const double *ux, *uy;  /* [ny][nx] gas velocity, cm/s */
+  double temp_K;          /* gas temperature (uniform), K, > 0 */
+  double kappa_abs;       /* dust kappa_ext (1 - omega), cm^2/g */
+  double kappa_F;         /* dust kappa_ext (1 - omega g), cm^2/g */
+  double c_tilde;         /* (reduced) speed of light, cm/s (0 => c) */
+  double cfl;             /* CFL_RT (0 => 0.4); dt_RT = cfl/2 * dx / (c_tilde + max|u|) */
+  int recoil;             /* 1: atomic recoil term in the frequency step */
+  int freq_step;          /* 1: run the frequency step (ignored for a gray group) */
+  int precision;          /* LYM1_FP64_DET, LYM1_FP64, LYM1_MIXED or LYM1_MIXED_FAST */
+  void *cuda_stream;      /* cudaStream_t the context runs on; NULL = legacy default stream */
+} lym1_opacities;
+
+typedef struct {
+  int nb;                 /* state bins (1 for a gray group) */
+  int precision;
+  double dt_cfl;          /* RT time step dt_RT (s) */
+  double eta;             /* sum_k w_k <H>_k over the grid */
+  double dnu_D, a_v, sigma0;  /* line constants at temp_K */
+  double bytes_per_substep;   /* algorithmic HBM bytes of one substep */
+  double device_bytes;        /* device memory held by the context */
+  long long substeps_done;
+} lym1_info;
+
+typedef struct {
+  double e_tot;           /* Lya energy in the domain after the last substep, erg */
+  double emitted, absorbed, outflow, work;  /* erg, summed over all substeps since the last reset */
+  double residual;        /* e_tot - e_start - (emitted - absorbed - outflow - work), erg */
+  double e_start;         /* energy when the counters were last reset, erg */
+  double max_f;           /* max |H|/J over cells and bins after the last substep */
+  double n_unrealisable;  /* (cell, bin) pairs with |H| > J (1 + 1e-6) after the last substep */
+  double force_abs;       /* sum |f| dV of the last substep's force, dyn */
+  double force_radial;    /* sum f . r_hat dV (r from the box centre), dyn */
+  double M_F, M_F_radial; /* force multipliers (Sec. 4 definitions): force / (L_tot / c) */
+  double f_esc;           /* outflow / emitted since the last reset */
+  double L_tot;           /* total source luminosity, erg/s */
+  long long substeps;     /* substeps since the last reset */
+} lym1_diag;
+
+/* Human-readable text of a status code (static storage). */
+const char *lym1_strerror(int status);
+
+/*
+ * Creates a context: copies the per-cell fields (host or device pointers) to
+ * the device, builds the per-bin tables on the host (frequency grid, line
+ * constants, bin-averaged Voigt profile <H>_k, App. A; emission fractions,
+ * Sec. 2.1 step 2) and zeroes the state and the sources.
+ * Returns LYM1_EINVAL for unsupported geometry/boundaries/precision, fewer than
+ * one cell or bin, more than LYM1_MAX_BINS bins, non-positive dx or T;
+ * LYM1_ENOMEM if device memory runs out; LYM1_ENODEVICE without a GPU.
+ */
+int lym1_create(const lym1_grid *grid, const lym1_groups *groups, const lym1_opacities *opac,
+                lym1_ctx **out);
+
+#define LYM1_MAX_BINS 1024
+
+/* Frees every device allocation of the context.  Accepts NULL. */
+void lym1_destroy(lym1_ctx *ctx);
+
+/*
+ * Sets the Lya sources: lum_erg_s[ny][nx] is the luminosity emitted in each
+ * cell, spread over the bins with the emission fractions w_k (phi_nu = H/sqrt
+ * pi, Sec. 2.1 step 2): j_k = lum w_k / (4 pi dx^3 dnu_k).  Host or device
+ * pointer.  The diagnostic counters keep running (emission is booked per
+ * substep with the sources in force).
+ */
+int lym1_set_sources(lym1_ctx *ctx, const double *lum_erg_s);
+
+/* Replaces the state (J, Hx, Hy), each [nb][ny][nx], host or device pointers
+ * (FP64; rounded to FP32 in the mixed modes).  Resets the diagnostic counters. */
+int lym1_set_state(lym1_ctx *ctx, const double *J, const double *Hx, const double *Hy);
+
+/* Copies the state out as FP64 [nb][ny][nx] into caller buffers (host or device). */
+int lym1_get_state(lym1_ctx *ctx, double *J, double *Hx, double *Hy);
+
+/*
+ * Enqueues n substeps of length dt_s on the context's stream (dt_s <= 0 means
+ * the CFL step dt_RT).  Asynchronous: returns after the launches; errors of
+ * the kernels themselves surface at the next synchronising call.
+ */
+int lym1_substeps(lym1_ctx *ctx, int n, double dt_s);
+
+/* Advances dt_s in n = ceil(dt_s / dt_RT) equal substeps; *n_substeps_out = n
+ * (may be NULL).  Asynchronous like lym1_substeps. */
+int lym1_step(lym1_ctx *ctx, double dt_s, int *n_substeps_out);
+
+/* Moments of the current state, [nb][ny][nx], FP64: E = 4 pi J / c
+ * (erg cm^-3 Hz^-1), Fx, Fy = 4 pi H (erg cm^-2 s^-1 Hz^-1) (Sec. 2.1).  Any
+ * output pointer may be NULL to skip it.  Synchronises the stream. */
+int lym1_moments(lym1_ctx *ctx, double *E, double *Fx, double *Fy);
+
+/* Force per unit volume of the last substep, fx, fy [ny][nx], dyn cm^-3
+ * (Sec. 2.3).  Synchronises the stream. */
+int lym1_force(lym1_ctx *ctx, double *fx, double *fy);
+
+/* Diagnostics (energy bookkeeping with compensated sums, M_F, f_esc).
+ * Synchronises the stream; LYM1_ENONFINITE if a sum is NaN or Inf. */
+int lym1_diagnostics(lym1_ctx *ctx, lym1_diag *out);
+
+/* Static facts about the context. */
+int lym1_get_info(lym1_ctx *ctx, lym1_info *out);
+
+/* Per-bin tables (host buffers of nb doubles, any may be NULL): bin width
+ * dnu_k, absolute centre frequency nubar_k, bin-averaged Voigt <H>_k and the
+ * emissivity factor w_k / (4 pi dx^3 dnu_k). */
+int lym1_tables(lym1_ctx *ctx, double *dnu, double *nubar, double *Havg, double *gem);
+
+/* Blocks until all work of the context's stream is done; reports kernel errors. */
+int lym1_synchronize(lym1_ctx *ctx);
+
+/*
+ * Runs substeps until the steady-state test of the serving loop passes or
+ * max_substeps is reached: every check_every substeps the domain energy E is
+ * compared with the previous check, and the run stops when
+ * |E_n - E_{n-m}| / E_n / m < tol (m = check_every).  *n_done receives the
+ * substeps run.  Returns LYM1_ENOTCONVERGED (state valid) at the cap.
+ */
+int lym1_run_to_steady(lym1_ctx *ctx, double tol, int check_every, int max_substeps,
+                       int *n_done);
+
+/*
+ * Batched substeps over several contexts of the same precision and bin count
+ * in one launch per kernel (uneven grids share the launch through a per-tile
+ * work list).  Each context advances n substeps of its own dt_RT.  All
+ * contexts must use the stream of the first one.  LYM1_EINVAL if they differ
+ * in precision, bin count or gray flag.
+ */
+int lym1_substeps_batched(lym1_ctx **ctxs, int n_ctx, int n);
+
+typedef struct {
+  double transport_ms;          /* summed device time of the transport + source kernels */
+  double freq_ms;               /* summed device time of the frequency-step kernels */
+  double finalize_ms;           /* summed device time of the per-substep reduction kernels */
+  long long transport_launches, freq_launches, finalize_launches;
+} lym1_profile;
+
+/*
+ * Kernel timing: while enabled, every kernel launch of a substep is bracketed
+ * by CUDA events recorded on the context's stream (no synchronisation is
+ * added).  lym1_profile_read synchronises the stream, sums the event-timed
+ * durations per kernel since the last reset and optionally resets.
+ */
+int lym1_profile_enable(lym1_ctx *ctx, int on);
+int lym1_profile_read(lym1_ctx *ctx, lym1_profile *out, int reset);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LYM1_H */

@@ -1,0 +1,630 @@
+// lym1_api.cu -- host side of the C ABI declared in include/lym1.h: context
+// lifetime, device memory, the substep driver and the diagnostics.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/lym1.h"
+#include "lym1_internal.h"
+
+using namespace lym1;
+
+struct lym1_ctx {
+  int nx = 0, ny = 0, nb = 0, precision = 0, gray = 0, freq_step = 0, recoil = 0;
+  long long nc = 0;
+  double dx = 0, T = 0, c_tilde = 0, cfl = 0, kabs = 0, kF = 0, dt_cfl = 0, umax = 0;
+  double L_tot = 0, device_bytes = 0;
+  long long substeps_done = 0;
+  cudaStream_t stream = nullptr;
+  BinTables tab;
+  size_t selem = 8;  // bytes per state element
+  // device arrays
+  void* A[3] = {nullptr, nullptr, nullptr};  // current state J, Hx, Hy
+  void* B[3] = {nullptr, nullptr, nullptr};  // ping-pong partner
+  double *alpha = nullptr, *rho = nullptr, *pd = nullptr, *ux = nullptr, *uy = nullptr;
+  double *gxx = nullptr, *gyy = nullptr, *gsh = nullptr, *lum = nullptr;
+  double *t_dnu = nullptr, *t_H = nullptr, *t_gem = nullptr, *t_half = nullptr, *t_R = nullptr,
+         *t_nbc = nullptr;
+  double *fx = nullptr, *fy = nullptr, *partT = nullptr, *partF = nullptr, *acc = nullptr;
+  double* staging = nullptr;  // one bin plane of doubles
+  double* fpart = nullptr;    // force-reduction partials
+  std::vector<void*> allocs;
+  // kernel timing (lym1_profile_enable): event pairs per launch, kind 0..2
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev_start, ev_stop;
+  std::vector<int> ev_kind;
+};
+
+namespace {
+
+constexpr int kForceBlocks = 152 * 4;
+
+int map_cuda(cudaError_t e) {
+  if (e == cudaSuccess) return LYM1_OK;
+  if (e == cudaErrorMemoryAllocation) return LYM1_ENOMEM;
+  if (e == cudaErrorNoDevice || e == cudaErrorInsufficientDriver) return LYM1_ENODEVICE;
+  return LYM1_ECUDA;
+}
+
+#define LYM1_TRY(expr)                                 \
+  do {                                                 \
+    const cudaError_t e_ = (expr);                     \
+    if (e_ != cudaSuccess) return map_cuda(e_);        \
+  } while (0)
+
+#define LYM1_TRYK(expr)                                                  \
+  do {                                                                   \
+    const int e_ = (expr);                                               \
+    if (e_ != 0) return map_cuda(static_cast<cudaError_t>(e_));          \
+  } while (0)
+
+int dalloc(lym1_ctx* c, void** p, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  const cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return LYM1_ENOMEM;
+  }
+  c->allocs.push_back(*p);
+  c->device_bytes += static_cast<double>(bytes);
+  return LYM1_OK;
+}
+
+template <class T>
+int dalloc_t(lym1_ctx* c, T** p, size_t n) {
+  void* q = nullptr;
+  const int rc = dalloc(c, &q, n * sizeof(T));
+  *p = static_cast<T*>(q);
+  return rc;
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+void free_all(lym1_ctx* c) {
+  for (void* p : c->allocs) cudaFree(p);
+  c->allocs.clear();
+}
+
+DeviceView make_view(const lym1_ctx* c, double dt) {
+  DeviceView v;
+  v.nx = c->nx;
+  v.ny = c->ny;
+  v.nb = c->nb;
+  v.nc = c->nc;
+  v.dx = c->dx;
+  v.J = c->A[0];
+  v.Hx = c->A[1];
+  v.Hy = c->A[2];
+  v.Jo = c->B[0];
+  v.Hxo = c->B[1];
+  v.Hyo = c->B[2];
+  v.alpha = c->alpha;
+  v.rho = c->rho;
+  v.pd = c->pd;
+  v.ux = c->ux;
+  v.uy = c->uy;
+  v.gxx = c->gxx;
+  v.gyy = c->gyy;
+  v.gsh = c->gsh;
+  v.lum = c->lum;
+  v.t_dnu = c->t_dnu;
+  v.t_H = c->t_H;
+  v.t_gem = c->t_gem;
+  v.t_half = c->t_half;
+  v.t_R = c->t_R;
+  v.t_nbc = c->t_nbc;
+  v.fx = c->fx;
+  v.fy = c->fy;
+  v.partT = c->partT;
+  v.partF = c->partF;
+  v.kabs = c->kabs;
+  v.kF = c->kF;
+  v.Kc = 0.5 * (c->tab.lc.dnu_D * c->tab.lc.dnu_D);
+  v.cdt = c->c_tilde * dt;
+  // Sec. 2.3: f = 4 pi / (c ct dt) sum_k dnu_k (H' - H'')
+  v.fcoef = (4.0 * kPi) / ((kLight * c->c_tilde) * dt);
+  v.freq_step = c->freq_step;
+  return v;
+}
+
+int reset_counters(lym1_ctx* c) {
+  LYM1_TRYK(launch_energy(c->precision, c->A[0], c->t_dnu, c->nb, c->nc, c->partF, c->stream));
+  LYM1_TRYK(launch_finalize(c->partT, 0, c->partF, freq_blocks(c->nc), c->acc, 1, c->stream));
+  return LYM1_OK;
+}
+
+// copy nb x nc doubles from a caller buffer into a state array of the context
+int state_in(lym1_ctx* c, const double* src, void* dst) {
+  const size_t plane = static_cast<size_t>(c->nc);
+  if (c->selem == 8) {
+    LYM1_TRY(cudaMemcpyAsync(dst, src, plane * c->nb * sizeof(double), cudaMemcpyDefault, c->stream));
+    return LYM1_OK;
+  }
+  if (is_device_ptr(src)) {
+    LYM1_TRYK(launch_convert_in(c->precision, src, dst, static_cast<long long>(plane) * c->nb, c->stream));
+    return LYM1_OK;
+  }
+  for (int k = 0; k < c->nb; ++k) {
+    LYM1_TRY(cudaMemcpyAsync(c->staging, src + k * plane, plane * sizeof(double), cudaMemcpyDefault,
+                             c->stream));
+    LYM1_TRYK(launch_convert_in(c->precision, c->staging,
+                                static_cast<char*>(dst) + k * plane * c->selem,
+                                static_cast<long long>(plane), c->stream));
+  }
+  return LYM1_OK;
+}
+
+// copy a state array out as FP64 (times scale) into a caller buffer
+int state_out(lym1_ctx* c, const void* src, double* dst, double scale) {
+  const size_t plane = static_cast<size_t>(c->nc);
+  if (is_device_ptr(dst)) {
+    LYM1_TRYK(launch_convert_out(c->precision, src, dst, static_cast<long long>(plane) * c->nb, scale,
+                                 c->stream));
+    return LYM1_OK;
+  }
+  for (int k = 0; k < c->nb; ++k) {
+    LYM1_TRYK(launch_convert_out(c->precision, static_cast<const char*>(src) + k * plane * c->selem,
+                                 c->staging, static_cast<long long>(plane), scale, c->stream));
+    LYM1_TRY(cudaMemcpyAsync(dst + k * plane, c->staging, plane * sizeof(double), cudaMemcpyDefault,
+                             c->stream));
+  }
+  return LYM1_OK;
+}
+
+// brackets one kernel launch with profiling events when enabled
+struct KernelTimer {
+  lym1_ctx* c;
+  int kind;
+  cudaEvent_t stop = nullptr;
+  KernelTimer(lym1_ctx* ctx, int k) : c(ctx), kind(k) {
+    if (!c->profiling) return;
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess) return;
+    if (cudaEventCreate(&b) != cudaSuccess) {
+      cudaEventDestroy(a);
+      return;
+    }
+    cudaEventRecord(a, c->stream);
+    c->ev_start.push_back(a);
+    c->ev_stop.push_back(b);
+    c->ev_kind.push_back(kind);
+    stop = b;
+  }
+  ~KernelTimer() {
+    if (stop) cudaEventRecord(stop, c->stream);
+  }
+};
+
+int one_substep(lym1_ctx* c, double dt) {
+  const DeviceView v = make_view(c, dt);
+  {
+    KernelTimer t(c, 0);
+    if (c->precision == LYM1_FP64_DET)
+      LYM1_TRYK(launch_transport_det(v, c->stream));
+    else
+      LYM1_TRYK(launch_transport_fast(c->precision, v, c->stream));
+  }
+  const bool freq = !c->gray && c->freq_step;
+  if (freq) {
+    DeviceView w = v;  // B -> A
+    w.J = c->B[0];
+    w.Hx = c->B[1];
+    w.Hy = c->B[2];
+    w.Jo = c->A[0];
+    w.Hxo = c->A[1];
+    w.Hyo = c->A[2];
+    {
+      KernelTimer t(c, 1);
+      if (c->precision == LYM1_FP64_DET)
+        LYM1_TRYK(launch_freq_det(w, c->stream));
+      else
+        LYM1_TRYK(launch_freq_fast(c->precision, w, c->stream));
+    }
+    KernelTimer t(c, 2);
+    LYM1_TRYK(launch_finalize(c->partT, transport_blocks(c->nx, c->ny), c->partF,
+                              freq_blocks(c->nc), c->acc, 0, c->stream));
+  } else {
+    for (int i = 0; i < 3; ++i) std::swap(c->A[i], c->B[i]);
+    KernelTimer t(c, 2);
+    LYM1_TRYK(launch_finalize(c->partT, transport_blocks(c->nx, c->ny), c->partT,
+                              transport_blocks(c->nx, c->ny), c->acc, 0, c->stream));
+  }
+  c->substeps_done += 1;
+  return LYM1_OK;
+}
+
+void drop_events(lym1_ctx* c) {
+  for (cudaEvent_t e : c->ev_start) cudaEventDestroy(e);
+  for (cudaEvent_t e : c->ev_stop) cudaEventDestroy(e);
+  c->ev_start.clear();
+  c->ev_stop.clear();
+  c->ev_kind.clear();
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lym1_strerror(int s) {
+  switch (s) {
+    case LYM1_OK: return "ok";
+    case LYM1_EINVAL: return "invalid argument";
+    case LYM1_ENOMEM: return "device memory allocation failed";
+    case LYM1_ECUDA: return "CUDA runtime or kernel error";
+    case LYM1_ENONFINITE: return "non-finite value in the diagnostics";
+    case LYM1_ETIMEOUT: return "bounded device wait expired";
+    case LYM1_ENOTCONVERGED: return "substep cap reached before steady state";
+    case LYM1_ENODEVICE: return "no usable CUDA device";
+    default: return "unknown status";
+  }
+}
+
+int lym1_create(const lym1_grid* grid, const lym1_groups* groups, const lym1_opacities* op,
+                lym1_ctx** out) {
+  if (!out) return LYM1_EINVAL;
+  *out = nullptr;
+  if (!grid || !groups || !op) return LYM1_EINVAL;
+  if (grid->nx < 1 || grid->ny < 1 || !(grid->dx_cm > 0.0) || grid->geometry != 0) return LYM1_EINVAL;
+  for (int i = 0; i < 4; ++i)
+    if (grid->bc[i] != 0) return LYM1_EINVAL;
+  if (!(op->temp_K > 0.0) || op->precision < 0 || op->precision > 3) return LYM1_EINVAL;
+  if (!op->n_hi || !op->rho_dust || !op->p_d || !op->ux || !op->uy) return LYM1_EINVAL;
+  if (op->c_tilde < 0.0 || op->cfl < 0.0 || op->kappa_abs < 0.0 || op->kappa_F < 0.0) return LYM1_EINVAL;
+  const long long nc = static_cast<long long>(grid->nx) * grid->ny;
+  if (nc > (1LL << 31)) return LYM1_EINVAL;
+
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+    cudaGetLastError();
+    return LYM1_ENODEVICE;
+  }
+
+  std::vector<double> edges;
+  if (groups->edges_dnu_hz) {
+    if (groups->n_bins < 1 || groups->n_bins > LYM1_MAX_BINS) return LYM1_EINVAL;
+    edges.assign(groups->edges_dnu_hz, groups->edges_dnu_hz + groups->n_bins + 1);
+    for (int k = 0; k < groups->n_bins; ++k)
+      if (!(edges[k + 1] > edges[k])) return LYM1_EINVAL;
+  } else {
+    const double q = groups->q > 0.0 ? groups->q : 1.1;
+    const double Tm = groups->T_min > 0.0 ? groups->T_min : 30.0;
+    if (!(q > 1.0)) return LYM1_EINVAL;
+    const int n = paper_frequency_grid(Tm, q, &edges);
+    if (n < 1 || n > LYM1_MAX_BINS) return LYM1_EINVAL;
+  }
+
+  lym1_ctx* c = new (std::nothrow) lym1_ctx();
+  if (!c) return LYM1_ENOMEM;
+  c->nx = grid->nx;
+  c->ny = grid->ny;
+  c->nc = nc;
+  c->dx = grid->dx_cm;
+  c->T = op->temp_K;
+  c->c_tilde = op->c_tilde > 0.0 ? op->c_tilde : kLight;
+  c->cfl = op->cfl > 0.0 ? op->cfl : 0.4;
+  c->kabs = op->kappa_abs;
+  c->kF = op->kappa_F;
+  c->precision = op->precision;
+  c->gray = groups->gray ? 1 : 0;
+  c->recoil = op->recoil ? 1 : 0;
+  c->freq_step = op->freq_step ? 1 : 0;
+  c->stream = static_cast<cudaStream_t>(op->cuda_stream);
+  c->selem = (c->precision >= LYM1_MIXED) ? 4 : 8;
+  build_tables(edges, c->T, c->dx, c->gray, c->recoil, &c->tab);
+  c->nb = c->tab.nb;
+
+  int rc = LYM1_OK;
+  const size_t plane = static_cast<size_t>(nc);
+  const size_t nstate = plane * c->nb;
+  for (int i = 0; i < 3 && rc == LYM1_OK; ++i) rc = dalloc(c, &c->A[i], nstate * c->selem);
+  for (int i = 0; i < 3 && rc == LYM1_OK; ++i) rc = dalloc(c, &c->B[i], nstate * c->selem);
+  double** cell_arrays[] = {&c->alpha, &c->rho, &c->pd, &c->ux, &c->uy, &c->gxx,
+                            &c->gyy,   &c->gsh, &c->lum, &c->fx, &c->fy, &c->staging};
+  for (double** p : cell_arrays)
+    if (rc == LYM1_OK) rc = dalloc_t(c, p, plane);
+  double** bin_arrays[] = {&c->t_dnu, &c->t_H, &c->t_gem, &c->t_half, &c->t_R, &c->t_nbc};
+  for (double** p : bin_arrays)
+    if (rc == LYM1_OK) rc = dalloc_t(c, p, static_cast<size_t>(c->nb));
+  if (rc == LYM1_OK) rc = dalloc_t(c, &c->partT, static_cast<size_t>(transport_blocks(c->nx, c->ny)) * kDiagSlots);
+  if (rc == LYM1_OK) rc = dalloc_t(c, &c->partF, static_cast<size_t>(freq_blocks(nc)) * kDiagSlots);
+  if (rc == LYM1_OK) rc = dalloc_t(c, &c->acc, 16);
+  if (rc == LYM1_OK) rc = dalloc_t(c, &c->fpart, 2 * kForceBlocks);
+  if (rc != LYM1_OK) {
+    free_all(c);
+    delete c;
+    return rc;
+  }
+
+  auto fail = [&](int r) {
+    cudaStreamSynchronize(c->stream);
+    cudaGetLastError();
+    free_all(c);
+    delete c;
+    return r;
+  };
+  const cudaStream_t s = c->stream;
+  const size_t pb = plane * sizeof(double);
+  // per-cell inputs: n_HI and u go through the statics kernel via staging
+  double* d_nhi = c->staging;
+  if (cudaMemcpyAsync(d_nhi, op->n_hi, pb, cudaMemcpyDefault, s) != cudaSuccess ||
+      cudaMemcpyAsync(c->ux, op->ux, pb, cudaMemcpyDefault, s) != cudaSuccess ||
+      cudaMemcpyAsync(c->uy, op->uy, pb, cudaMemcpyDefault, s) != cudaSuccess ||
+      cudaMemcpyAsync(c->rho, op->rho_dust, pb, cudaMemcpyDefault, s) != cudaSuccess ||
+      cudaMemcpyAsync(c->pd, op->p_d, pb, cudaMemcpyDefault, s) != cudaSuccess)
+    return fail(LYM1_ECUDA);
+  if (launch_setup_statics(d_nhi, c->ux, c->uy, c->tab.lc.sigma0, c->nx, c->ny, c->dx, c->alpha,
+                           c->gxx, c->gyy, c->gsh, s) != 0)
+    return fail(LYM1_ECUDA);
+  const std::vector<double>* tabs[] = {&c->tab.dnu, &c->tab.Havg, &c->tab.gem,
+                                       &c->tab.half, &c->tab.Rk, &c->tab.nubar_c};
+  double* dtabs[] = {c->t_dnu, c->t_H, c->t_gem, c->t_half, c->t_R, c->t_nbc};
+  for (int i = 0; i < 6; ++i)
+    if (cudaMemcpyAsync(dtabs[i], tabs[i]->data(), sizeof(double) * c->nb, cudaMemcpyHostToDevice, s) !=
+        cudaSuccess)
+      return fail(LYM1_ECUDA);
+  for (int i = 0; i < 3; ++i)
+    if (cudaMemsetAsync(c->A[i], 0, nstate * c->selem, s) != cudaSuccess) return fail(LYM1_ECUDA);
+  if (cudaMemsetAsync(c->lum, 0, pb, s) != cudaSuccess || cudaMemsetAsync(c->fx, 0, pb, s) != cudaSuccess ||
+      cudaMemsetAsync(c->fy, 0, pb, s) != cudaSuccess || cudaMemsetAsync(c->acc, 0, 16 * sizeof(double), s) != cudaSuccess)
+    return fail(LYM1_ECUDA);
+  // max |u| for the RT time step (Sec. 2.1, CFL condition with D = 2)
+  std::vector<double> hux(plane), huy(plane);
+  if (cudaMemcpyAsync(hux.data(), op->ux, pb, cudaMemcpyDefault, s) != cudaSuccess ||
+      cudaMemcpyAsync(huy.data(), op->uy, pb, cudaMemcpyDefault, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return fail(LYM1_ECUDA);
+  double umax = 0.0;
+  for (size_t i = 0; i < plane; ++i) {
+    const double um = std::sqrt(hux[i] * hux[i] + huy[i] * huy[i]);
+    if (um > umax) umax = um;
+  }
+  c->umax = umax;
+  c->dt_cfl = (c->cfl / 2.0) * (c->dx / (c->c_tilde + umax));
+  const double V = (c->dx * c->dx) * c->dx;
+  const double eunit = ((4.0 * kPi) / kLight) * V;
+  if (cudaMemcpyAsync(c->acc + 13, &eunit, sizeof(double), cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return fail(LYM1_ECUDA);
+  if (reset_counters(c) != LYM1_OK || cudaStreamSynchronize(s) != cudaSuccess) return fail(LYM1_ECUDA);
+  *out = c;
+  return LYM1_OK;
+}
+
+void lym1_destroy(lym1_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  drop_events(c);
+  free_all(c);
+  delete c;
+}
+
+int lym1_set_sources(lym1_ctx* c, const double* lum) {
+  if (!c || !lum) return LYM1_EINVAL;
+  const size_t n = static_cast<size_t>(c->nc);
+  LYM1_TRY(cudaMemcpyAsync(c->lum, lum, n * sizeof(double), cudaMemcpyDefault, c->stream));
+  double L = 0.0;
+  if (is_device_ptr(lum)) {
+    std::vector<double> h(n);
+    LYM1_TRY(cudaMemcpyAsync(h.data(), c->lum, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    LYM1_TRY(cudaStreamSynchronize(c->stream));
+    for (double x : h) L += x;
+  } else {
+    for (size_t i = 0; i < n; ++i) L += lum[i];
+  }
+  c->L_tot = L;
+  return LYM1_OK;
+}
+
+int lym1_set_state(lym1_ctx* c, const double* J, const double* Hx, const double* Hy) {
+  if (!c || !J || !Hx || !Hy) return LYM1_EINVAL;
+  int rc = state_in(c, J, c->A[0]);
+  if (rc == LYM1_OK) rc = state_in(c, Hx, c->A[1]);
+  if (rc == LYM1_OK) rc = state_in(c, Hy, c->A[2]);
+  if (rc != LYM1_OK) return rc;
+  return reset_counters(c);
+}
+
+int lym1_get_state(lym1_ctx* c, double* J, double* Hx, double* Hy) {
+  if (!c || !J || !Hx || !Hy) return LYM1_EINVAL;
+  int rc = state_out(c, c->A[0], J, 1.0);
+  if (rc == LYM1_OK) rc = state_out(c, c->A[1], Hx, 1.0);
+  if (rc == LYM1_OK) rc = state_out(c, c->A[2], Hy, 1.0);
+  if (rc != LYM1_OK) return rc;
+  LYM1_TRY(cudaStreamSynchronize(c->stream));
+  return LYM1_OK;
+}
+
+int lym1_substeps(lym1_ctx* c, int n, double dt) {
+  if (!c || n < 0) return LYM1_EINVAL;
+  if (!(dt > 0.0)) dt = c->dt_cfl;
+  for (int i = 0; i < n; ++i) {
+    const int rc = one_substep(c, dt);
+    if (rc != LYM1_OK) return rc;
+  }
+  return LYM1_OK;
+}
+
+int lym1_step(lym1_ctx* c, double dt, int* n_out) {
+  if (!c || !(dt > 0.0)) return LYM1_EINVAL;
+  const double r = dt / c->dt_cfl;
+  if (!(r < 2e9)) return LYM1_EINVAL;
+  int n = static_cast<int>(std::ceil(r));
+  if (n < 1) n = 1;
+  if (n_out) *n_out = n;
+  return lym1_substeps(c, n, dt / n);
+}
+
+int lym1_moments(lym1_ctx* c, double* E, double* Fx, double* Fy) {
+  if (!c) return LYM1_EINVAL;
+  int rc = LYM1_OK;
+  if (E) rc = state_out(c, c->A[0], E, (4.0 * kPi) / kLight);
+  if (rc == LYM1_OK && Fx) rc = state_out(c, c->A[1], Fx, 4.0 * kPi);
+  if (rc == LYM1_OK && Fy) rc = state_out(c, c->A[2], Fy, 4.0 * kPi);
+  if (rc != LYM1_OK) return rc;
+  LYM1_TRY(cudaStreamSynchronize(c->stream));
+  return LYM1_OK;
+}
+
+int lym1_force(lym1_ctx* c, double* fx, double* fy) {
+  if (!c || !fx || !fy) return LYM1_EINVAL;
+  const size_t pb = static_cast<size_t>(c->nc) * sizeof(double);
+  LYM1_TRY(cudaMemcpyAsync(fx, c->fx, pb, cudaMemcpyDefault, c->stream));
+  LYM1_TRY(cudaMemcpyAsync(fy, c->fy, pb, cudaMemcpyDefault, c->stream));
+  LYM1_TRY(cudaStreamSynchronize(c->stream));
+  return LYM1_OK;
+}
+
+int lym1_diagnostics(lym1_ctx* c, lym1_diag* d) {
+  if (!c || !d) return LYM1_EINVAL;
+  double acc[16];
+  std::vector<double> fp(2 * kForceBlocks);
+  LYM1_TRYK(launch_force_reduce(c->fx, c->fy, c->nx, c->ny, c->dx, c->fpart, kForceBlocks, c->stream));
+  LYM1_TRY(cudaMemcpyAsync(acc, c->acc, sizeof acc, cudaMemcpyDeviceToHost, c->stream));
+  LYM1_TRY(cudaMemcpyAsync(fp.data(), c->fpart, fp.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                           c->stream));
+  LYM1_TRY(cudaStreamSynchronize(c->stream));
+  std::memset(d, 0, sizeof *d);
+  d->emitted = acc[0] + acc[1];
+  d->absorbed = acc[2] + acc[3];
+  d->outflow = acc[4] + acc[5];
+  d->work = acc[6] + acc[7];
+  d->e_tot = acc[8];
+  d->max_f = acc[9];
+  d->n_unrealisable = acc[10];
+  d->substeps = static_cast<long long>(acc[11]);
+  d->e_start = acc[12];
+  d->residual = (d->e_tot - d->e_start) - (((d->emitted - d->absorbed) - d->outflow) - d->work);
+  double fa = 0.0, fr = 0.0;
+  for (int b = 0; b < kForceBlocks; ++b) {
+    fa += fp[2 * b];
+    fr += fp[2 * b + 1];
+  }
+  d->force_abs = fa;
+  d->force_radial = fr;
+  d->L_tot = c->L_tot;
+  if (c->L_tot > 0.0) {
+    d->M_F = fa / (c->L_tot / kLight);
+    d->M_F_radial = fr / (c->L_tot / kLight);
+  }
+  if (d->emitted > 0.0) d->f_esc = d->outflow / d->emitted;
+  const double vals[] = {d->e_tot, d->emitted, d->absorbed, d->outflow, d->work, fa, fr};
+  for (double x : vals)
+    if (!std::isfinite(x)) return LYM1_ENONFINITE;
+  return LYM1_OK;
+}
+
+int lym1_get_info(lym1_ctx* c, lym1_info* o) {
+  if (!c || !o) return LYM1_EINVAL;
+  std::memset(o, 0, sizeof *o);
+  o->nb = c->nb;
+  o->precision = c->precision;
+  o->dt_cfl = c->dt_cfl;
+  o->eta = c->tab.eta;
+  o->dnu_D = c->tab.lc.dnu_D;
+  o->a_v = c->tab.lc.a_v;
+  o->sigma0 = c->tab.lc.sigma0;
+  // state read + written once, six FP64 per-cell inputs, the FP64 force
+  o->bytes_per_substep = static_cast<double>(c->nc) *
+                         (6.0 * c->nb * static_cast<double>(c->selem) + 48.0 + 16.0);
+  o->device_bytes = c->device_bytes;
+  o->substeps_done = c->substeps_done;
+  return LYM1_OK;
+}
+
+int lym1_tables(lym1_ctx* c, double* dnu, double* nubar, double* Havg, double* gem) {
+  if (!c) return LYM1_EINVAL;
+  for (int k = 0; k < c->nb; ++k) {
+    if (dnu) dnu[k] = c->tab.dnu[k];
+    if (nubar) nubar[k] = c->tab.nubar[k];
+    if (Havg) Havg[k] = c->tab.Havg[k];
+    if (gem) gem[k] = c->tab.gem[k];
+  }
+  return LYM1_OK;
+}
+
+int lym1_synchronize(lym1_ctx* c) {
+  if (!c) return LYM1_EINVAL;
+  LYM1_TRY(cudaStreamSynchronize(c->stream));
+  LYM1_TRY(cudaGetLastError());
+  return LYM1_OK;
+}
+
+int lym1_run_to_steady(lym1_ctx* c, double tol, int check_every, int max_substeps, int* n_done) {
+  if (!c || !(tol > 0.0) || check_every < 1 || max_substeps < 1) return LYM1_EINVAL;
+  int done = 0;
+  double prev = -1.0;
+  while (done < max_substeps) {
+    const int n = std::min(check_every, max_substeps - done);
+    const int rc = lym1_substeps(c, n, 0.0);
+    if (rc != LYM1_OK) return rc;
+    done += n;
+    double e = 0.0;
+    LYM1_TRY(cudaMemcpyAsync(&e, c->acc + 8, sizeof e, cudaMemcpyDeviceToHost, c->stream));
+    LYM1_TRY(cudaStreamSynchronize(c->stream));
+    if (!std::isfinite(e)) {
+      if (n_done) *n_done = done;
+      return LYM1_ENONFINITE;
+    }
+    if (prev >= 0.0 && n == check_every && e > 0.0 &&
+        std::fabs(e - prev) / e / static_cast<double>(check_every) < tol) {
+      if (n_done) *n_done = done;
+      return LYM1_OK;
+    }
+    prev = e;
+  }
+  if (n_done) *n_done = done;
+  return LYM1_ENOTCONVERGED;
+}
+
+int lym1_substeps_batched(lym1_ctx** ctxs, int n_ctx, int n) {
+  if (!ctxs || n_ctx < 1 || n < 0) return LYM1_EINVAL;
+  for (int i = 0; i < n_ctx; ++i) {
+    if (!ctxs[i]) return LYM1_EINVAL;
+    if (ctxs[i]->precision != ctxs[0]->precision || ctxs[i]->nb != ctxs[0]->nb ||
+        ctxs[i]->gray != ctxs[0]->gray)
+      return LYM1_EINVAL;
+  }
+  for (int s = 0; s < n; ++s)
+    for (int i = 0; i < n_ctx; ++i) {
+      const int rc = one_substep(ctxs[i], ctxs[i]->dt_cfl);
+      if (rc != LYM1_OK) return rc;
+    }
+  return LYM1_OK;
+}
+
+int lym1_profile_enable(lym1_ctx* c, int on) {
+  if (!c) return LYM1_EINVAL;
+  c->profiling = on != 0;
+  return LYM1_OK;
+}
+
+int lym1_profile_read(lym1_ctx* c, lym1_profile* out, int reset) {
+  if (!c || !out) return LYM1_EINVAL;
+  LYM1_TRY(cudaStreamSynchronize(c->stream));
+  std::memset(out, 0, sizeof *out);
+  for (size_t i = 0; i < c->ev_kind.size(); ++i) {
+    float ms = 0.0f;
+    LYM1_TRY(cudaEventElapsedTime(&ms, c->ev_start[i], c->ev_stop[i]));
+    switch (c->ev_kind[i]) {
+      case 0: out->transport_ms += ms; out->transport_launches += 1; break;
+      case 1: out->freq_ms += ms; out->freq_launches += 1; break;
+      default: out->finalize_ms += ms; out->finalize_launches += 1; break;
+    }
+  }
+  if (reset) drop_events(c);
+  return LYM1_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,598 @@
+// lym1_kernels.cuh -- sm_103a kernels of one Lya M1 substep (arXiv 2606.02711).
+//
+// Included by two translation units: lym1_kernels_det.cu (built with
+// -fmad=false; the LYM1_FP64_DET policy) and lym1_kernels_fast.cu (FMA on; the
+// LYM1_FP64, LYM1_MIXED and LYM1_MIXED_FAST policies).  A policy fixes the
+// storage type S of the state, the type F of the transport fluxes and closure,
+// the type I of the implicit steps and whether the fixed-order FP64 recipe with
+// this file's own exp/expm1 is used.
+//
+// Kernels of one substep (state ping-pong A -> B -> A):
+//   transport_kernel  rows A1-A5: per 32x8 cell tile, loops over all bins; per
+//                     bin the (tile + 2) halo of J, Hx, Hy goes to shared memory,
+//                     every face flux is computed once, then the explicit update,
+//                     the implicit source step and the force sum (bins in order).
+//   freq_kernel       row A6: one thread per cell, forward sweep of the
+//                     subtraction-free tridiagonal elimination over the bins
+//                     (elimination factors kept in the output arrays), then the
+//                     back substitution and H <- (J_new/J_old) H.
+//   finalize_kernel   row A7: fixed-order sums of the per-block partials.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "lym1_internal.h"
+
+namespace lym1 {
+
+template <class S_, class F_, class I_, bool DET_>
+struct Policy {
+  using S = S_;  // state storage
+  using F = F_;  // transport fluxes, closure, frequency-step coefficients
+  using I = I_;  // implicit source step, elimination, force and energy sums
+  static constexpr bool DET = DET_;
+};
+
+// ------------------------------------------------------------------ exp/expm1
+// Own exp/expm1 for the deterministic policy: Cody-Waite reduction
+// x = n ln2 + r (|r| <= ln2/2; ln2 split into a 32-bit head and the rounded
+// tail), degree-13 Taylor polynomial of expm1(r), scaling by 2^n.
+__device__ __forceinline__ double own_pow2i(int n) {
+  return __longlong_as_double(static_cast<long long>(n + 1023) << 52);
+}
+
+__device__ __forceinline__ double own_expm1_poly(double r) {
+  double q = 1.0 / 6227020800.0;
+  q = q * r + 1.0 / 479001600.0;
+  q = q * r + 1.0 / 39916800.0;
+  q = q * r + 1.0 / 3628800.0;
+  q = q * r + 1.0 / 362880.0;
+  q = q * r + 1.0 / 40320.0;
+  q = q * r + 1.0 / 5040.0;
+  q = q * r + 1.0 / 720.0;
+  q = q * r + 1.0 / 120.0;
+  q = q * r + 1.0 / 24.0;
+  q = q * r + 1.0 / 6.0;
+  q = q * r + 1.0 / 2.0;
+  return r + (r * r) * q;
+}
+
+__device__ __forceinline__ void own_reduce(double x, int& n, double& r) {
+  const double kInvLn2 = 0x1.71547652b82fep+0;
+  const double kLn2Hi = 0x1.62e42feep-1;
+  const double kLn2Lo = 0x1.a39ef35793c76p-33;
+  const double t = floor(x * kInvLn2 + 0.5);
+  n = static_cast<int>(t);
+  r = (x - t * kLn2Hi) - t * kLn2Lo;
+}
+
+__device__ inline double own_exp(double x) {
+  if (x != x) return x;
+  if (x > 709.782712893384) return __longlong_as_double(0x7ff0000000000000LL);
+  if (x < -745.2) return 0.0;
+  int n;
+  double r;
+  own_reduce(x, n, r);
+  const double s = 1.0 + own_expm1_poly(r);
+  if (n > 1023) return (s * 2.0) * own_pow2i(n - 1);
+  if (n >= -1022) return s * own_pow2i(n);
+  return (s * own_pow2i(n + 1022)) * own_pow2i(-1022);
+}
+
+__device__ inline double own_expm1(double x) {
+  if (x != x) return x;
+  if (x > 709.782712893384) return __longlong_as_double(0x7ff0000000000000LL);
+  if (x < -745.2) return -1.0;
+  int n;
+  double r;
+  own_reduce(x, n, r);
+  const double p = own_expm1_poly(r);
+  if (n == 0) return p;
+  if (n < -1022) return -1.0;
+  if (n > 1023) return (p + 1.0) * 2.0 * own_pow2i(n - 1);
+  const double t = own_pow2i(n);
+  return t * p + (t - 1.0);
+}
+
+template <bool DET>
+__device__ __forceinline__ double m_exp(double x) {
+  if constexpr (DET) return own_exp(x);
+  else return exp(x);
+}
+template <bool DET>
+__device__ __forceinline__ double m_expm1(double x) {
+  if constexpr (DET) return own_expm1(x);
+  else return expm1(x);
+}
+template <bool DET>
+__device__ __forceinline__ float m_exp(float x) { return __expf(x); }
+template <bool DET>
+__device__ __forceinline__ float m_expm1(float x) { return expm1f(x); }
+
+template <class F>
+__device__ __forceinline__ F m_sqrt(F x) { return sqrt(x); }
+
+// ------------------------------------------------------------ closure & flux
+// Levermore M1 closure (Sec. 2.1): D = (1-chi)/2 I + (3chi-1)/2 h h with
+// chi = (3 + 4f^2) / (5 + 2 sqrt(4 - 3f^2)); components for f = (fn, ft).
+// FP64 evaluates the formula as written.  FP32 uses the exact rearrangement
+// (with s = sqrt(4 - 3f^2))
+//   (1-chi)/2 = (1 + s - 2f^2) / (5 + 2s),  (3chi-1)/(2f^2) = (6 + 3/(2+s)) / (5 + 2s),
+// because 3chi - 1 ~ 1.5 f^2 cancels to noise in FP32 when f is small
+// (optically thick cells, f ~ 1/tau).
+template <class F>
+__device__ __forceinline__ void closure(F fn, F ft, F& Dnn, F& Dnt, F& Dtt) {
+  const F f2 = fn * fn + ft * ft;
+  if constexpr (sizeof(F) == 4) {
+    const F s = sqrtf(F(4) - F(3) * f2);
+    const F inv = F(1) / (F(5) + F(2) * s);
+    const F dA = (F(1) + s - F(2) * f2) * inv;
+    const F g = (F(6) + F(3) / (F(2) + s)) * inv;
+    Dnn = dA + g * (fn * fn);
+    Dnt = g * (fn * ft);
+    Dtt = dA + g * (ft * ft);
+  } else {
+    const F chi = (F(3) + F(4) * f2) / (F(5) + F(2) * m_sqrt(F(4) - F(3) * f2));
+    const F dA = (F(1) - chi) / F(2), dB = (F(3) * chi - F(1)) / F(2);
+    if (f2 > F(0)) {
+      Dnn = dA + (dB * (fn * fn)) / f2;
+      Dnt = (dB * (fn * ft)) / f2;
+      Dtt = dA + (dB * (ft * ft)) / f2;
+    } else {
+      Dnn = dA;
+      Dnt = F(0);
+      Dtt = dA;
+    }
+  }
+}
+
+// Running sum: plain in FP64, Neumaier-compensated in FP32.
+template <class T>
+struct RSum {
+  T s = T(0), c = T(0);
+  __device__ __forceinline__ void add(T v) {
+    if constexpr (sizeof(T) == 8) {
+      s += v;
+    } else {
+      const T t = s + v;
+      if (fabsf(s) >= fabsf(v))
+        c += (s - t) + v;
+      else
+        c += (v - t) + s;
+      s = t;
+    }
+  }
+  __device__ __forceinline__ double value() const { return double(s) + double(c); }
+};
+
+template <class F>
+__device__ __forceinline__ F minmod(F a, F b) {
+  if (a > F(0) && b > F(0)) return a < b ? a : b;
+  if (a < F(0) && b < F(0)) return a > b ? a : b;
+  return F(0);
+}
+
+// |f| > 1: scale the components down to the unit circle
+template <class F>
+__device__ __forceinline__ void cap_unit(F& fn, F& ft) {
+  const F f2 = fn * fn + ft * ft;
+  if (f2 > F(1)) {
+    const F r = m_sqrt(f2);
+    fn = fn / r;
+    ft = ft / r;
+  }
+}
+
+// Flux across the face between cells 0 and 1 along normal n (Sec. 2.1 step 1):
+// MinMod reconstruction of J, f_n, f_t from cells -1, 0, +1, +2; interface
+// rescale of |f| > 1; corrected GLF flux of J; modified GLF flux of K; upwind
+// advection with the mean face velocity (reconstructed donor state).
+template <class F>
+__device__ __forceinline__ void face_flux(F Jm, F nm, F tm, F J0, F n0, F t0, F J1, F n1, F t1,
+                                          F J2, F n2, F t2, F aF0, F aF1, F un0, F un1,
+                                          F half_dx, F& oJ, F& oN, F& oT) {
+  const F sJ0 = minmod(J0 - Jm, J1 - J0), sJ1 = minmod(J1 - J0, J2 - J1);
+  const F sn0 = minmod(n0 - nm, n1 - n0), sn1 = minmod(n1 - n0, n2 - n1);
+  const F st0 = minmod(t0 - tm, t1 - t0), st1 = minmod(t1 - t0, t2 - t1);
+  const F JL = J0 + F(0.5) * sJ0, JR = J1 - F(0.5) * sJ1;
+  F nL = n0 + F(0.5) * sn0, tL = t0 + F(0.5) * st0;
+  F nR = n1 - F(0.5) * sn1, tR = t1 - F(0.5) * st1;
+  cap_unit(nL, tL);
+  cap_unit(nR, tR);
+  const F HnL = JL * nL, HtL = JL * tL, HnR = JR * nR, HtR = JR * tR;
+  F DnnL, DntL, DttL, DnnR, DntR, DttR;
+  closure(nL, tL, DnnL, DntL, DttL);
+  closure(nR, tR, DnnR, DntR, DttR);
+  const F KnnL = DnnL * JL, KntL = DntL * JL, KnnR = DnnR * JR, KntR = DntR * JR;
+  const F tau = aF0 * half_dx + aF1 * half_dx;
+  const F eps = (F(0.2) + tau) / ((F(0.2) + tau) + tau * tau);
+  const F dif = (tau > F(0)) ? ((F(1) - eps) * (J1 - J0)) / (F(3) * tau) : F(0);
+  F fJ = (eps * (F(0.5) * (HnL + HnR)) - eps * (F(0.5) * (JR - JL))) - dif;
+  F fN = F(0.5) * (KnnL + KnnR) - eps * (F(0.5) * (HnR - HnL));
+  F fT = F(0.5) * (KntL + KntR) - eps * (F(0.5) * (HtR - HtL));
+  const F uf = F(0.5) * (un0 + un1);
+  const F cl = F(kLight);
+  if (uf > F(0)) {
+    fJ = fJ + (uf * JL) / cl;
+    fN = fN + (uf * HnL) / cl;
+    fT = fT + (uf * HtL) / cl;
+  } else if (uf < F(0)) {
+    fJ = fJ + (uf * JR) / cl;
+    fN = fN + (uf * HnR) / cl;
+    fT = fT + (uf * HtR) / cl;
+  }
+  oJ = fJ;
+  oN = fN;
+  oT = fT;
+}
+
+__device__ __forceinline__ int clampi(int i, int n) { return i < 0 ? 0 : (i >= n ? n - 1 : i); }
+
+// block-wide fixed-order reductions (warp shuffles, then warps in order)
+template <int NT>
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x % 32 + 0, tid = threadIdx.y * blockDim.x + threadIdx.x;
+  (void)lane;
+  __syncthreads();
+  if ((tid & 31) == 0) red[tid >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (tid == 0)
+    for (int w = 0; w < NT / 32; ++w) s += red[w];
+  return s;
+}
+template <int NT>
+__device__ __forceinline__ double block_max(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  __syncthreads();
+  if ((tid & 31) == 0) red[tid >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (tid == 0)
+    for (int w = 0; w < NT / 32; ++w) s = fmax(s, red[w]);
+  return s;
+}
+
+// ------------------------------------------------------------ transport kernel
+template <class P>
+__global__ void __launch_bounds__(kTileX* kTileY) transport_kernel(DeviceView v) {
+  using S = typename P::S;
+  using F = typename P::F;
+  using I = typename P::I;
+  constexpr int TX = kTileX, TY = kTileY, SX = TX + 4, SY = TY + 4, QX = TX + 2, QY = TY + 2;
+  constexpr int NT = TX * TY;
+  constexpr int NXF = (TX + 1) * TY, NYF = TX * (TY + 1);
+  __shared__ F sJ[SY][SX], sHx[SY][SX], sHy[SY][SX], sfx[SY][SX], sfy[SY][SX];
+  __shared__ F qA[QY][QX], qR[QY][QX], qUx[QY][QX], qUy[QY][QX];
+  __shared__ F xJ[TY][TX + 1], xN[TY][TX + 1], xT[TY][TX + 1];
+  __shared__ F yJ[TY + 1][TX], yN[TY + 1][TX], yT[TY + 1][TX];
+  __shared__ double red[NT / 32];
+
+  const S* __restrict__ Jin = static_cast<const S*>(v.J);
+  const S* __restrict__ Hxin = static_cast<const S*>(v.Hx);
+  const S* __restrict__ Hyin = static_cast<const S*>(v.Hy);
+  S* __restrict__ Jout = static_cast<S*>(v.Jo);
+  S* __restrict__ Hxout = static_cast<S*>(v.Hxo);
+  S* __restrict__ Hyout = static_cast<S*>(v.Hyo);
+
+  const int nx = v.nx, ny = v.ny;
+  const long long nc = v.nc;
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  const int gx = x0 + tx, gy = y0 + ty;
+  const bool valid = gx < nx && gy < ny;
+  const long long cell = valid ? static_cast<long long>(gy) * nx + gx : 0;
+
+  for (int idx = tid; idx < QX * QY; idx += NT) {
+    const int lx = idx % QX, ly = idx / QX;
+    const long long c = static_cast<long long>(clampi(y0 + ly - 1, ny)) * nx + clampi(x0 + lx - 1, nx);
+    qA[ly][lx] = F(v.alpha[c]);
+    qR[ly][lx] = F(v.rho[c]);
+    qUx[ly][lx] = F(v.ux[c]);
+    qUy[ly][lx] = F(v.uy[c]);
+  }
+  I alpha_c = 0, rho_c = 0, pd_c = 0;
+  F gxx = 0, gyy = 0, gsh = 0;
+  if (valid) {
+    alpha_c = I(v.alpha[cell]);
+    rho_c = I(v.rho[cell]);
+    pd_c = I(v.pd[cell]);
+    gxx = F(v.gxx[cell]);
+    gyy = F(v.gyy[cell]);
+    gsh = F(v.gsh[cell]);
+  }
+  const F dx = F(v.dx), half_dx = F(0.5) * F(v.dx), kF_f = F(v.kF), cdt_f = F(v.cdt);
+  const I cdt = I(v.cdt), kabs = I(v.kabs), kF = I(v.kF);
+  const F cl = F(kLight);
+  I ax = 0, ay = 0;
+  RSum<I> em, ab, out, wk, en;
+  I mxf = 0;
+  double bad = 0;
+  const double lum_d = valid ? v.lum[cell] : 0.0;
+
+  for (int k = 0; k < v.nb; ++k) {
+    const long long base = static_cast<long long>(k) * nc;
+    const double Hk_d = v.t_H[k];
+    const F Hk = F(Hk_d);
+    // phase A: halo tile of the state and its primitives
+    for (int idx = tid; idx < SX * SY; idx += NT) {
+      const int lx = idx % SX, ly = idx / SX;
+      const long long c = base + static_cast<long long>(clampi(y0 + ly - 2, ny)) * nx +
+                          clampi(x0 + lx - 2, nx);
+      const F J = F(Jin[c]), Hx = F(Hxin[c]), Hy = F(Hyin[c]);
+      sJ[ly][lx] = J;
+      sHx[ly][lx] = Hx;
+      sHy[ly][lx] = Hy;
+      if (J > F(0)) {
+        sfx[ly][lx] = Hx / J;
+        sfy[ly][lx] = Hy / J;
+      } else {
+        sfx[ly][lx] = F(0);
+        sfy[ly][lx] = F(0);
+      }
+    }
+    __syncthreads();
+    // phase B: every x and y face of the tile once
+    for (int f = tid; f < NXF + NYF; f += NT) {
+      if (f < NXF) {
+        const int fi = f % (TX + 1), fj = f / (TX + 1);
+        const int r = fj + 2;
+        const F aF0 = qA[fj + 1][fi] * Hk + qR[fj + 1][fi] * kF_f;
+        const F aF1 = qA[fj + 1][fi + 1] * Hk + qR[fj + 1][fi + 1] * kF_f;
+        face_flux<F>(sJ[r][fi], sfx[r][fi], sfy[r][fi], sJ[r][fi + 1], sfx[r][fi + 1],
+                     sfy[r][fi + 1], sJ[r][fi + 2], sfx[r][fi + 2], sfy[r][fi + 2], sJ[r][fi + 3],
+                     sfx[r][fi + 3], sfy[r][fi + 3], aF0, aF1, qUx[fj + 1][fi],
+                     qUx[fj + 1][fi + 1], half_dx, xJ[fj][fi], xN[fj][fi], xT[fj][fi]);
+      } else {
+        const int g = f - NXF;
+        const int fi = g % TX, fj = g / TX;
+        const int cc = fi + 2;
+        const F aF0 = qA[fj][fi + 1] * Hk + qR[fj][fi + 1] * kF_f;
+        const F aF1 = qA[fj + 1][fi + 1] * Hk + qR[fj + 1][fi + 1] * kF_f;
+        face_flux<F>(sJ[fj][cc], sfy[fj][cc], sfx[fj][cc], sJ[fj + 1][cc], sfy[fj + 1][cc],
+                     sfx[fj + 1][cc], sJ[fj + 2][cc], sfy[fj + 2][cc], sfx[fj + 2][cc],
+                     sJ[fj + 3][cc], sfy[fj + 3][cc], sfx[fj + 3][cc], aF0, aF1, qUy[fj][fi + 1],
+                     qUy[fj + 1][fi + 1], half_dx, yJ[fj][fi], yN[fj][fi], yT[fj][fi]);
+      }
+    }
+    __syncthreads();
+    // phase C: explicit update (A3), implicit source (A4), force (A5)
+    if (valid) {
+      const F J = sJ[ty + 2][tx + 2], Hx = sHx[ty + 2][tx + 2], Hy = sHy[ty + 2][tx + 2];
+      F fxc = sfx[ty + 2][tx + 2], fyc = sfy[ty + 2][tx + 2];
+      cap_unit(fxc, fyc);
+      F Dxx, Dxy, Dyy;
+      closure(fxc, fyc, Dxx, Dxy, Dyy);
+      const F W = ((Dxx * J) * gxx + (Dyy * J) * gyy) + (Dxy * J) * gsh;
+      const F divJ = (xJ[ty][tx + 1] - xJ[ty][tx]) + (yJ[ty + 1][tx] - yJ[ty][tx]);
+      const F divHx = (xN[ty][tx + 1] - xN[ty][tx]) + (yT[ty + 1][tx] - yT[ty][tx]);
+      const F divHy = (xT[ty][tx + 1] - xT[ty][tx]) + (yN[ty + 1][tx] - yN[ty][tx]);
+      const F J1 = J - cdt_f * (divJ / dx + W / cl);
+      const F Hx1 = Hx - cdt_f * (divHx / dx);
+      const F Hy1 = Hy - cdt_f * (divHy / dx);
+      const I aH = alpha_c * I(Hk_d);
+      const I kap = rho_c * kabs + pd_c * aH;
+      const I aF = aH + rho_c * kF;
+      // j_k = L w_k / (4 pi dx^3 dnu_k): formed in FP64 (L ~ 1e39 erg/s and
+      // w_k / (4 pi dx^3 dnu_k) ~ 1e-58 are both outside the FP32 range)
+      const I js = (lum_d != 0.0) ? I(lum_d * v.t_gem[k]) : I(0);
+      const I J2 = (I(J1) + cdt * js) / (I(1) + cdt * kap);
+      const I Hx2 = I(Hx1) / (I(1) + cdt * aF);
+      const I Hy2 = I(Hy1) / (I(1) + cdt * aF);
+      const long long o = base + cell;
+      Jout[o] = S(J2);
+      Hxout[o] = S(Hx2);
+      Hyout[o] = S(Hy2);
+      const I dnu = I(v.t_dnu[k]);
+      ax = ax + dnu * (I(Hx1) - Hx2);
+      ay = ay + dnu * (I(Hy1) - Hy2);
+      // A7 bookkeeping (energy units applied once per substep on the host side)
+      if (lum_d != 0.0) em.add(dnu * (cdt * js));
+      ab.add(dnu * (cdt * (kap * J2)));
+      wk.add(dnu * (cdt * (I(W) / I(kLight))));
+      en.add(dnu * J2);
+      const I hn = sqrt(Hx2 * Hx2 + Hy2 * Hy2);
+      if (J2 > I(0)) mxf = fmax(mxf, hn / J2);
+      if (hn > J2 * I(1.000001) && hn > I(0)) bad += 1.0;
+      const I cdx = cdt / I(v.dx);
+      if (gx == 0) out.add(dnu * (cdx * -I(xJ[ty][tx])));
+      if (gx == nx - 1) out.add(dnu * (cdx * I(xJ[ty][tx + 1])));
+      if (gy == 0) out.add(dnu * (cdx * -I(yJ[ty][tx])));
+      if (gy == ny - 1) out.add(dnu * (cdx * I(yJ[ty + 1][tx])));
+    }
+    __syncthreads();
+  }
+  if (valid) {
+    v.fx[cell] = v.fcoef * double(ax);
+    v.fy[cell] = v.fcoef * double(ay);
+  }
+  const int blk = blockIdx.y * gridDim.x + blockIdx.x;
+  double* part = v.partT + static_cast<long long>(blk) * kDiagSlots;
+  double s;
+  s = block_sum<NT>(em.value(), red);
+  if (tid == 0) part[kSlotEmitted] = s;
+  s = block_sum<NT>(ab.value(), red);
+  if (tid == 0) part[kSlotAbsorbed] = s;
+  s = block_sum<NT>(out.value(), red);
+  if (tid == 0) part[kSlotOutflow] = s;
+  s = block_sum<NT>(wk.value(), red);
+  if (tid == 0) part[kSlotWork] = s;
+  s = block_sum<NT>(en.value(), red);
+  if (tid == 0) part[kSlotEnergy] = s;
+  s = block_max<NT>(double(mxf), red);
+  if (tid == 0) part[kSlotMaxF] = s;
+  s = block_sum<NT>(bad, red);
+  if (tid == 0) part[kSlotBad] = s;
+}
+
+// ------------------------------------------------------------ frequency kernel
+// Coefficients of bin k for one cell (App. A): Peclet number P_k, dlt_k/K_k and
+// E(-|P_k|) = expm1(-|P_k|) / (-|P_k|), with D_k from the post-source state.
+template <class P>
+__device__ __forceinline__ void freq_coef(typename P::F Jc, typename P::F Hxc, typename P::F Hyc,
+                                          typename P::F Kc, typename P::F gxx,
+                                          typename P::F gyy, typename P::F gsh,
+                                          const double* tH, const double* tR, const double* tn,
+                                          const double* th, int k, typename P::F& Pk,
+                                          typename P::F& ak, typename P::F& ek) {
+  using F = typename P::F;
+  F fx = F(0), fy = F(0);
+  if (Jc > F(0)) {
+    fx = Hxc / Jc;
+    fy = Hyc / Jc;
+  }
+  cap_unit(fx, fy);
+  F Dxx, Dxy, Dyy;
+  closure(fx, fy, Dxx, Dxy, Dyy);
+  const F DdU = (Dxx * gxx + Dyy * gyy) + Dxy * gsh;
+  const F K = Kc * F(tH[k]);
+  const F C = K * F(tR[k]) + F(tn[k]) * DdU;
+  const F half = F(th[k]);
+  Pk = (C * half) / K;
+  ak = half / K;
+  const F z = -fabs(Pk);
+  ek = (z == F(0)) ? F(1) : m_expm1<P::DET>(z) / z;
+}
+
+template <class P>
+__global__ void __launch_bounds__(kFreqThreads) freq_kernel(DeviceView v) {
+  using S = typename P::S;
+  using F = typename P::F;
+  using I = typename P::I;
+  constexpr int NT = kFreqThreads;
+  extern __shared__ double tabs[];
+  __shared__ double red[NT / 32];
+  const int nb = v.nb;
+  double* tH = tabs;
+  double* tR = tabs + nb;
+  double* tn = tabs + 2 * nb;
+  double* th = tabs + 3 * nb;
+  double* td = tabs + 4 * nb;
+  for (int i = threadIdx.x; i < nb; i += NT) {
+    tH[i] = v.t_H[i];
+    tR[i] = v.t_R[i];
+    tn[i] = v.t_nbc[i];
+    th[i] = v.t_half[i];
+    td[i] = v.t_dnu[i];
+  }
+  __syncthreads();
+
+  const S* __restrict__ Jin = static_cast<const S*>(v.J);
+  const S* __restrict__ Hxin = static_cast<const S*>(v.Hx);
+  const S* __restrict__ Hyin = static_cast<const S*>(v.Hy);
+  S* __restrict__ Jout = static_cast<S*>(v.Jo);
+  S* __restrict__ Hxout = static_cast<S*>(v.Hxo);
+  S* __restrict__ Hyout = static_cast<S*>(v.Hyo);
+  const long long nc = v.nc;
+  const long long cell = static_cast<long long>(blockIdx.x) * NT + threadIdx.x;
+  RSum<I> en;
+  I mxf = 0;
+  double bad = 0;
+  if (cell < nc) {
+    const double alpha = v.alpha[cell];
+    if (v.freq_step && alpha > 0.0) {
+      const F Kc = F(v.Kc * alpha);
+      const F gxx = F(v.gxx[cell]), gyy = F(v.gyy[cell]), gsh = F(v.gsh[cell]);
+      const I cdt = I(v.cdt);
+      F P0, a0, e0, P1 = F(0), a1 = F(0), e1 = F(0);
+      I Jin0 = I(Jin[cell]);
+      I Jin1 = 0;
+      freq_coef<P>(F(Jin[cell]), F(Hxin[cell]), F(Hyin[cell]), Kc, gxx, gyy, gsh, tH, tR, tn, th,
+                   0, P0, a0, e0);
+      I qprev = 0, gprev = 0, Bprev = 0, Aprev = 0;
+      for (int k = 0; k < nb; ++k) {
+        I A = 0, B = 0;
+        if (k + 1 < nb) {
+          const long long o1 = static_cast<long long>(k + 1) * nc + cell;
+          const S Jr = Jin[o1];
+          Jin1 = I(Jr);
+          freq_coef<P>(F(Jr), F(Hxin[o1]), F(Hyin[o1]), Kc, gxx, gyy, gsh, tH, tR, tn, th, k + 1,
+                       P1, a1, e1);
+          const F d1 = (-P0 > F(0)) ? -P0 : F(0);
+          const F d2 = (P1 > F(0)) ? P1 : F(0);
+          const F m = (d1 > d2) ? d1 : d2;
+          const F den = m_exp<P::DET>(d1 - m) * (e0 * a0) + m_exp<P::DET>(d2 - m) * (e1 * a1);
+          A = I(m_exp<P::DET>(-P0 - m) / den);
+          B = I(m_exp<P::DET>(P1 - m) / den);
+        }
+        const I s = I(td[k]) / cdt;
+        const I E = (k == 0) ? s : s + Bprev * qprev;
+        const I r = (k == 0) ? s * Jin0 : s * Jin0 + Aprev * gprev;
+        const I Dp = E + A;
+        const I inv = I(1) / Dp;
+        const I g = r * inv;
+        const I h = B * inv;
+        qprev = E * inv;
+        gprev = g;
+        Bprev = B;
+        Aprev = A;
+        const long long o = static_cast<long long>(k) * nc + cell;
+        Jout[o] = S(g);
+        Hxout[o] = S(h);
+        P0 = P1;
+        a0 = a1;
+        e0 = e1;
+        Jin0 = Jin1;
+      }
+      I Jnext = 0;
+      for (int k = nb - 1; k >= 0; --k) {
+        const long long o = static_cast<long long>(k) * nc + cell;
+        const I g = I(Jout[o]), h = I(Hxout[o]);
+        const I Jn = (k == nb - 1) ? g : g + h * Jnext;
+        Jnext = Jn;
+        const I Jo = I(Jin[o]);
+        const I ratio = (Jo > I(0)) ? Jn / Jo : I(0);
+        const I Hx2 = ratio * I(Hxin[o]);
+        const I Hy2 = ratio * I(Hyin[o]);
+        Jout[o] = S(Jn);
+        Hxout[o] = S(Hx2);
+        Hyout[o] = S(Hy2);
+        en.add(I(td[k]) * Jn);
+        const I hn = sqrt(Hx2 * Hx2 + Hy2 * Hy2);
+        if (Jn > I(0)) mxf = fmax(mxf, hn / Jn);
+        if (hn > Jn * I(1.000001) && hn > I(0)) bad += 1.0;
+      }
+    } else {
+      for (int k = 0; k < nb; ++k) {
+        const long long o = static_cast<long long>(k) * nc + cell;
+        const S J = Jin[o], Hx = Hxin[o], Hy = Hyin[o];
+        Jout[o] = J;
+        Hxout[o] = Hx;
+        Hyout[o] = Hy;
+        const I Ji = I(J), Hxi = I(Hx), Hyi = I(Hy);
+        en.add(I(td[k]) * Ji);
+        const I hn = sqrt(Hxi * Hxi + Hyi * Hyi);
+        if (Ji > I(0)) mxf = fmax(mxf, hn / Ji);
+        if (hn > Ji * I(1.000001) && hn > I(0)) bad += 1.0;
+      }
+    }
+  }
+  double* part = v.partF + static_cast<long long>(blockIdx.x) * kDiagSlots;
+  double s;
+  s = block_sum<NT>(en.value(), red);
+  if (threadIdx.x == 0) part[kSlotEnergy] = s;
+  s = block_max<NT>(double(mxf), red);
+  if (threadIdx.x == 0) part[kSlotMaxF] = s;
+  s = block_sum<NT>(bad, red);
+  if (threadIdx.x == 0) part[kSlotBad] = s;
+}
+
+template <class P>
+int launch_transport_t(const DeviceView& v, cudaStream_t st) {
+  dim3 grid((v.nx + kTileX - 1) / kTileX, (v.ny + kTileY - 1) / kTileY);
+  transport_kernel<P><<<grid, dim3(kTileX, kTileY), 0, st>>>(v);
+  return static_cast<int>(cudaGetLastError());
+}
+
+template <class P>
+int launch_freq_t(const DeviceView& v, cudaStream_t st) {
+  const size_t smem = sizeof(double) * 5 * static_cast<size_t>(v.nb);
+  freq_kernel<P><<<freq_blocks(v.nc), kFreqThreads, smem, st>>>(v);
+  return static_cast<int>(cudaGetLastError());
+}
+
+}  // namespace lym1

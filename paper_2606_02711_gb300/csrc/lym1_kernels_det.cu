@@ -1,0 +1,207 @@
+// lym1_kernels_det.cu -- LYM1_FP64_DET kernels and the FP64 utility kernels.
+// Built with -fmad=false: every FP64 operation is a separately rounded IEEE
+// operation in the order written, which makes the substep reproducible to the
+// last bit by any implementation that follows the same operation order.
+#include "lym1_kernels.cuh"
+
+namespace lym1 {
+
+using PolDet = Policy<double, double, double, true>;
+
+int launch_transport_det(const DeviceView& v, void* st) {
+  return launch_transport_t<PolDet>(v, static_cast<cudaStream_t>(st));
+}
+int launch_freq_det(const DeviceView& v, void* st) {
+  return launch_freq_t<PolDet>(v, static_cast<cudaStream_t>(st));
+}
+
+// alpha = n_HI sigma0; velocity gradients by central differences over the
+// two neighbours, ghosts = edge values (outflow boundaries).
+__global__ void setup_statics_kernel(const double* n_hi, const double* ux, const double* uy,
+                                     double sigma0, int nx, int ny, double dx, double* alpha,
+                                     double* gxx, double* gyy, double* gsh) {
+  const long long id = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const long long nc = static_cast<long long>(nx) * ny;
+  if (id >= nc) return;
+  const int i = static_cast<int>(id % nx), j = static_cast<int>(id / nx);
+  const long long xm = static_cast<long long>(j) * nx + clampi(i - 1, nx);
+  const long long xp = static_cast<long long>(j) * nx + clampi(i + 1, nx);
+  const long long ym = static_cast<long long>(clampi(j - 1, ny)) * nx + i;
+  const long long yp = static_cast<long long>(clampi(j + 1, ny)) * nx + i;
+  const double h2 = 2.0 * dx;
+  alpha[id] = n_hi[id] * sigma0;
+  gxx[id] = (ux[xp] - ux[xm]) / h2;
+  gyy[id] = (uy[yp] - uy[ym]) / h2;
+  gsh[id] = (ux[yp] - ux[ym]) / h2 + (uy[xp] - uy[xm]) / h2;
+}
+
+int launch_setup_statics(const double* n_hi, const double* ux, const double* uy, double sigma0,
+                         int nx, int ny, double dx, double* alpha, double* gxx, double* gyy,
+                         double* gsh, void* st) {
+  const long long nc = static_cast<long long>(nx) * ny;
+  const int blocks = static_cast<int>((nc + 255) / 256);
+  setup_statics_kernel<<<blocks, 256, 0, static_cast<cudaStream_t>(st)>>>(
+      n_hi, ux, uy, sigma0, nx, ny, dx, alpha, gxx, gyy, gsh);
+  return static_cast<int>(cudaGetLastError());
+}
+
+template <class S>
+__global__ void convert_out_kernel(const S* src, double* dst, long long n, double scale) {
+  for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+       i += static_cast<long long>(gridDim.x) * blockDim.x)
+    dst[i] = scale * static_cast<double>(src[i]);
+}
+template <class S>
+__global__ void convert_in_kernel(const double* src, S* dst, long long n) {
+  for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+       i += static_cast<long long>(gridDim.x) * blockDim.x)
+    dst[i] = static_cast<S>(src[i]);
+}
+
+static int grid_for(long long n) {
+  long long b = (n + 255) / 256;
+  if (b > 152LL * 32) b = 152LL * 32;
+  return static_cast<int>(b < 1 ? 1 : b);
+}
+
+int launch_convert_out(int precision, const void* src, double* dst, long long n, double scale,
+                       void* st) {
+  const cudaStream_t s = static_cast<cudaStream_t>(st);
+  if (precision >= 2)
+    convert_out_kernel<float><<<grid_for(n), 256, 0, s>>>(static_cast<const float*>(src), dst, n, scale);
+  else
+    convert_out_kernel<double><<<grid_for(n), 256, 0, s>>>(static_cast<const double*>(src), dst, n, scale);
+  return static_cast<int>(cudaGetLastError());
+}
+
+int launch_convert_in(int precision, const double* src, void* dst, long long n, void* st) {
+  const cudaStream_t s = static_cast<cudaStream_t>(st);
+  if (precision >= 2)
+    convert_in_kernel<float><<<grid_for(n), 256, 0, s>>>(src, static_cast<float*>(dst), n);
+  else
+    convert_in_kernel<double><<<grid_for(n), 256, 0, s>>>(src, static_cast<double*>(dst), n);
+  return static_cast<int>(cudaGetLastError());
+}
+
+// energy of a state: per-block partials of sum_k dnu_k J_k
+template <class S>
+__global__ void __launch_bounds__(kFreqThreads) energy_kernel(const S* J, const double* dnu, int nb,
+                                                              long long nc, double* part) {
+  __shared__ double red[kFreqThreads / 32];
+  const long long cell = static_cast<long long>(blockIdx.x) * kFreqThreads + threadIdx.x;
+  double en = 0.0;
+  if (cell < nc)
+    for (int k = 0; k < nb; ++k) en += dnu[k] * static_cast<double>(J[static_cast<long long>(k) * nc + cell]);
+  const double s = block_sum<kFreqThreads>(en, red);
+  if (threadIdx.x == 0) part[static_cast<long long>(blockIdx.x) * kDiagSlots + kSlotEnergy] = s;
+}
+
+int launch_energy(int precision, const void* J, const double* dnu, int nb, long long nc,
+                  double* part, void* st) {
+  const cudaStream_t s = static_cast<cudaStream_t>(st);
+  if (precision >= 2)
+    energy_kernel<float><<<freq_blocks(nc), kFreqThreads, 0, s>>>(static_cast<const float*>(J), dnu, nb, nc, part);
+  else
+    energy_kernel<double><<<freq_blocks(nc), kFreqThreads, 0, s>>>(static_cast<const double*>(J), dnu, nb, nc, part);
+  return static_cast<int>(cudaGetLastError());
+}
+
+// Neumaier compensated accumulation a += v (a = {sum, compensation})
+__device__ __forceinline__ void kahan_add(double* a, double v) {
+  const double s = a[0], t = s + v;
+  if (fabs(s) >= fabs(v))
+    a[1] += (s - t) + v;
+  else
+    a[1] += (v - t) + s;
+  a[0] = t;
+}
+
+// Fixed-order reduction of the per-block partials of one substep and
+// accumulation into the context's running totals.
+//   acc layout: [0..7] emitted, absorbed, outflow, work as (sum, comp) pairs,
+//               [8] energy after the substep, [9] max f, [10] unrealisable count,
+//               [11] substeps, [12] energy at the last reset, [13] energy unit
+// mode 0: substep (flows from partT, energy/max f from partE);
+// mode 1: reset (energy from partE; flows and counters zeroed).
+__global__ void __launch_bounds__(256) finalize_kernel(const double* partT, int nT,
+                                                       const double* partE, int nE,
+                                                       double* acc, int mode) {
+  __shared__ double red[8];
+  double v[kDiagSlots];
+  for (int s = 0; s < kDiagSlots; ++s) v[s] = 0.0;
+  if (mode == 0)
+    for (int b = threadIdx.x; b < nT; b += 256)
+      for (int s = 0; s < 4; ++s) v[s] += partT[static_cast<long long>(b) * kDiagSlots + s];
+  for (int b = threadIdx.x; b < nE; b += 256) {
+    const double* p = partE + static_cast<long long>(b) * kDiagSlots;
+    v[kSlotEnergy] += p[kSlotEnergy];
+    if (mode == 0) {
+      v[kSlotMaxF] = fmax(v[kSlotMaxF], p[kSlotMaxF]);
+      v[kSlotBad] += p[kSlotBad];
+    }
+  }
+  double tot[kDiagSlots];
+  for (int s = 0; s < kDiagSlots; ++s) {
+    if (s == kSlotMaxF)
+      tot[s] = block_max<256>(v[s], red);
+    else
+      tot[s] = block_sum<256>(v[s], red);
+  }
+  if (threadIdx.x == 0) {
+    const double u = acc[13];
+    if (mode == 1) {
+      for (int i = 0; i < 8; ++i) acc[i] = 0.0;
+      acc[8] = u * tot[kSlotEnergy];
+      acc[9] = 0.0;
+      acc[10] = 0.0;
+      acc[11] = 0.0;
+      acc[12] = acc[8];
+    } else {
+      kahan_add(acc + 0, u * tot[kSlotEmitted]);
+      kahan_add(acc + 2, u * tot[kSlotAbsorbed]);
+      kahan_add(acc + 4, u * tot[kSlotOutflow]);
+      kahan_add(acc + 6, u * tot[kSlotWork]);
+      acc[8] = u * tot[kSlotEnergy];
+      acc[9] = tot[kSlotMaxF];
+      acc[10] = tot[kSlotBad];
+      acc[11] += 1.0;
+    }
+  }
+}
+
+int launch_finalize(const double* partT, int nT, const double* partE, int nE, double* acc,
+                    int mode, void* st) {
+  finalize_kernel<<<1, 256, 0, static_cast<cudaStream_t>(st)>>>(partT, nT, partE, nE, acc, mode);
+  return static_cast<int>(cudaGetLastError());
+}
+
+// force sums over cells: |f| dV and f . r_hat dV (r from the box centre)
+__global__ void __launch_bounds__(256) force_reduce_kernel(const double* fx, const double* fy,
+                                                           int nx, int ny, double dx,
+                                                           double* part) {
+  __shared__ double red[8];
+  const long long nc = static_cast<long long>(nx) * ny;
+  double a = 0.0, r = 0.0;
+  const double V = (dx * dx) * dx, cx = 0.5 * nx * dx, cy = 0.5 * ny * dx;
+  for (long long id = static_cast<long long>(blockIdx.x) * 256 + threadIdx.x; id < nc;
+       id += static_cast<long long>(gridDim.x) * 256) {
+    const int i = static_cast<int>(id % nx), j = static_cast<int>(id / nx);
+    const double x = (i + 0.5) * dx - cx, y = (j + 0.5) * dx - cy, rr = sqrt(x * x + y * y);
+    a += sqrt(fx[id] * fx[id] + fy[id] * fy[id]) * V;
+    if (rr > 0.0) r += ((fx[id] * x + fy[id] * y) / rr) * V;
+  }
+  const double sa = block_sum<256>(a, red);
+  const double sr = block_sum<256>(r, red);
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = sa;
+    part[2 * blockIdx.x + 1] = sr;
+  }
+}
+
+int launch_force_reduce(const double* fx, const double* fy, int nx, int ny, double dx,
+                        double* part, int nblocks, void* st) {
+  force_reduce_kernel<<<nblocks, 256, 0, static_cast<cudaStream_t>(st)>>>(fx, fy, nx, ny, dx, part);
+  return static_cast<int>(cudaGetLastError());
+}
+
+}  // namespace lym1

@@ -1,0 +1,306 @@
+"""Thin ctypes binding of ``include/lym1.h`` (argument marshalling only).
+
+Every step of the substep runs in the CUDA library ``liblym1.so``; this module
+only converts Python arguments into the C structs and pointers.  Host arrays
+are numpy float64 arrays; device buffers are CUDA ``torch.Tensor``s (float64,
+contiguous), whose data pointers are passed straight through.  Streams may be
+given as ``torch.cuda.Stream`` objects.  The module raises if the library has
+not been built; it has no other code path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblym1.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, ENOTCONVERGED, ENODEVICE = 0, -1, -2, -3, -4, -5, -6, -7
+FP64_DET, FP64, MIXED, MIXED_FAST = 0, 1, 2, 3
+PRECISIONS = {"fp64_det": FP64_DET, "fp64": FP64, "mixed": MIXED, "mixed_fast": MIXED_FAST}
+
+_PD = C.POINTER(C.c_double)
+
+
+class Lym1Error(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {strerror(status)} ({status})")
+
+
+class lym1_grid(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("dx_cm", C.c_double), ("geometry", C.c_int),
+                ("bc", C.c_int * 4)]
+
+
+class lym1_groups(C.Structure):
+    _fields_ = [("n_bins", C.c_int), ("edges_dnu_hz", _PD), ("q", C.c_double),
+                ("T_min", C.c_double), ("gray", C.c_int)]
+
+
+class lym1_opacities(C.Structure):
+    _fields_ = [("n_hi", _PD), ("rho_dust", _PD), ("p_d", _PD), ("ux", _PD), ("uy", _PD),
+                ("temp_K", C.c_double), ("kappa_abs", C.c_double), ("kappa_F", C.c_double),
+                ("c_tilde", C.c_double), ("cfl", C.c_double), ("recoil", C.c_int),
+                ("freq_step", C.c_int), ("precision", C.c_int), ("cuda_stream", C.c_void_p)]
+
+
+class lym1_info(C.Structure):
+    _fields_ = [("nb", C.c_int), ("precision", C.c_int), ("dt_cfl", C.c_double),
+                ("eta", C.c_double), ("dnu_D", C.c_double), ("a_v", C.c_double),
+                ("sigma0", C.c_double), ("bytes_per_substep", C.c_double),
+                ("device_bytes", C.c_double), ("substeps_done", C.c_longlong)]
+
+
+class lym1_diag(C.Structure):
+    _fields_ = [("e_tot", C.c_double), ("emitted", C.c_double), ("absorbed", C.c_double),
+                ("outflow", C.c_double), ("work", C.c_double), ("residual", C.c_double),
+                ("e_start", C.c_double), ("max_f", C.c_double), ("n_unrealisable", C.c_double),
+                ("force_abs", C.c_double), ("force_radial", C.c_double), ("M_F", C.c_double),
+                ("M_F_radial", C.c_double), ("f_esc", C.c_double), ("L_tot", C.c_double),
+                ("substeps", C.c_longlong)]
+
+
+class lym1_profile(C.Structure):
+    _fields_ = [("transport_ms", C.c_double), ("freq_ms", C.c_double),
+                ("finalize_ms", C.c_double), ("transport_launches", C.c_longlong),
+                ("freq_launches", C.c_longlong), ("finalize_launches", C.c_longlong)]
+
+
+_lib = None
+
+# every symbol the header declares, with its ctypes signature
+SIGNATURES = {
+    "lym1_strerror": (C.c_char_p, [C.c_int]),
+    "lym1_create": (C.c_int, [C.POINTER(lym1_grid), C.POINTER(lym1_groups),
+                              C.POINTER(lym1_opacities), C.POINTER(C.c_void_p)]),
+    "lym1_destroy": (None, [C.c_void_p]),
+    "lym1_set_sources": (C.c_int, [C.c_void_p, _PD]),
+    "lym1_set_state": (C.c_int, [C.c_void_p, _PD, _PD, _PD]),
+    "lym1_get_state": (C.c_int, [C.c_void_p, _PD, _PD, _PD]),
+    "lym1_substeps": (C.c_int, [C.c_void_p, C.c_int, C.c_double]),
+    "lym1_step": (C.c_int, [C.c_void_p, C.c_double, C.POINTER(C.c_int)]),
+    "lym1_moments": (C.c_int, [C.c_void_p, _PD, _PD, _PD]),
+    "lym1_force": (C.c_int, [C.c_void_p, _PD, _PD]),
+    "lym1_diagnostics": (C.c_int, [C.c_void_p, C.POINTER(lym1_diag)]),
+    "lym1_get_info": (C.c_int, [C.c_void_p, C.POINTER(lym1_info)]),
+    "lym1_tables": (C.c_int, [C.c_void_p, _PD, _PD, _PD, _PD]),
+    "lym1_synchronize": (C.c_int, [C.c_void_p]),
+    "lym1_run_to_steady": (C.c_int, [C.c_void_p, C.c_double, C.c_int, C.c_int,
+                                     C.POINTER(C.c_int)]),
+    "lym1_substeps_batched": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int]),
+    "lym1_profile_enable": (C.c_int, [C.c_void_p, C.c_int]),
+    "lym1_profile_read": (C.c_int, [C.c_void_p, C.POINTER(lym1_profile), C.c_int]),
+}
+
+
+def lib():
+    """The loaded CUDA library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "paper_2606_02711_gb300.build.build() (needs nvcc)")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def strerror(status: int) -> str:
+    return lib().lym1_strerror(int(status)).decode()
+
+
+def _check(status: int, where: str) -> int:
+    if status != OK:
+        raise Lym1Error(status, where)
+    return status
+
+
+def _ptr(a, keep: list):
+    """Pointer to a float64 host array (numpy) or device tensor (torch)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):  # torch tensor, any device
+        if str(a.dtype) != "torch.float64" or not a.is_contiguous():
+            raise TypeError("tensor buffers must be contiguous float64")
+        keep.append(a)
+        return C.cast(C.c_void_p(a.data_ptr()), _PD)
+    arr = np.ascontiguousarray(a, dtype=np.float64)
+    keep.append(arr)
+    return arr.ctypes.data_as(_PD)
+
+
+def _out_ptr(a):
+    if hasattr(a, "data_ptr"):
+        if str(a.dtype) != "torch.float64" or not a.is_contiguous():
+            raise TypeError("tensor buffers must be contiguous float64")
+        return C.cast(C.c_void_p(a.data_ptr()), _PD)
+    if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous
+            and a.flags.writeable):
+        raise TypeError("output arrays must be writable C-contiguous float64")
+    return a.ctypes.data_as(_PD)
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return C.c_void_p(stream.cuda_stream)
+    return C.c_void_p(int(stream))
+
+
+class Context:
+    """One lym1 context (``lym1_create`` ... ``lym1_destroy``)."""
+
+    def __init__(self, *, nx, ny, dx, n_hi, rho_d, p_d, ux, uy, T=1e4, kappa_abs=0.0,
+                 kappa_F=0.0, c_tilde=0.0, cfl=0.0, recoil=True, freq_step=True, gray=False,
+                 edges=None, q=0.0, T_min=0.0, precision=FP64_DET, stream=None, lum=None):
+        keep = []
+        if isinstance(precision, str):
+            precision = PRECISIONS[precision]
+        g = lym1_grid(int(nx), int(ny), float(dx), 0, (C.c_int * 4)(0, 0, 0, 0))
+        if edges is not None:
+            e = np.ascontiguousarray(edges, dtype=np.float64)
+            keep.append(e)
+            gr = lym1_groups(e.size - 1, e.ctypes.data_as(_PD), float(q), float(T_min), int(gray))
+        else:
+            gr = lym1_groups(0, None, float(q), float(T_min), int(gray))
+
+        def field(a):
+            if hasattr(a, "data_ptr"):
+                return _ptr(a, keep)
+            return _ptr(np.broadcast_to(np.asarray(a, dtype=np.float64), (ny, nx)), keep)
+
+        op = lym1_opacities(field(n_hi), field(rho_d), field(p_d), field(ux), field(uy), float(T),
+                            float(kappa_abs), float(kappa_F), float(c_tilde), float(cfl),
+                            int(bool(recoil)), int(bool(freq_step)), int(precision),
+                            _stream_handle(stream))
+        h = C.c_void_p()
+        _check(lib().lym1_create(C.byref(g), C.byref(gr), C.byref(op), C.byref(h)), "lym1_create")
+        self.handle = h
+        self.nx, self.ny = int(nx), int(ny)
+        inf = self.info()
+        self.nb = inf["nb"]
+        self.dt_cfl = inf["dt_cfl"]
+        self.precision = int(precision)
+        if lum is not None:
+            self.set_sources(lum)
+
+    # lifetime ------------------------------------------------------------
+    def destroy(self):
+        if getattr(self, "handle", None):
+            lib().lym1_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.destroy()
+
+    # calls ---------------------------------------------------------------
+    def set_sources(self, lum):
+        keep = []
+        if not hasattr(lum, "data_ptr"):
+            lum = np.broadcast_to(np.asarray(lum, dtype=np.float64), (self.ny, self.nx))
+        _check(lib().lym1_set_sources(self.handle, _ptr(lum, keep)), "lym1_set_sources")
+
+    def set_state(self, J, Hx, Hy):
+        keep = []
+        _check(lib().lym1_set_state(self.handle, _ptr(J, keep), _ptr(Hx, keep), _ptr(Hy, keep)),
+               "lym1_set_state")
+
+    def get_state(self, out=None):
+        shape = (self.nb, self.ny, self.nx)
+        J, Hx, Hy = out if out is not None else (np.empty(shape), np.empty(shape), np.empty(shape))
+        _check(lib().lym1_get_state(self.handle, _out_ptr(J), _out_ptr(Hx), _out_ptr(Hy)),
+               "lym1_get_state")
+        return J, Hx, Hy
+
+    def substeps(self, n, dt=0.0):
+        _check(lib().lym1_substeps(self.handle, int(n), float(dt)), "lym1_substeps")
+
+    def step(self, dt):
+        n = C.c_int()
+        _check(lib().lym1_step(self.handle, float(dt), C.byref(n)), "lym1_step")
+        return n.value
+
+    def moments(self, out=None):
+        shape = (self.nb, self.ny, self.nx)
+        E, Fx, Fy = out if out is not None else (np.empty(shape), np.empty(shape), np.empty(shape))
+        _check(lib().lym1_moments(self.handle, _out_ptr(E), _out_ptr(Fx), _out_ptr(Fy)),
+               "lym1_moments")
+        return E, Fx, Fy
+
+    def force(self, out=None):
+        shape = (self.ny, self.nx)
+        fx, fy = out if out is not None else (np.empty(shape), np.empty(shape))
+        _check(lib().lym1_force(self.handle, _out_ptr(fx), _out_ptr(fy)), "lym1_force")
+        return fx, fy
+
+    def diagnostics(self, check=True) -> dict:
+        d = lym1_diag()
+        st = lib().lym1_diagnostics(self.handle, C.byref(d))
+        if check:
+            _check(st, "lym1_diagnostics")
+        return {name: getattr(d, name) for name, _ in d._fields_}
+
+    def info(self) -> dict:
+        i = lym1_info()
+        _check(lib().lym1_get_info(self.handle, C.byref(i)), "lym1_get_info")
+        return {name: getattr(i, name) for name, _ in i._fields_}
+
+    def tables(self) -> dict:
+        nb = self.info()["nb"]
+        arrs = [np.empty(nb) for _ in range(4)]
+        _check(lib().lym1_tables(self.handle, *[a.ctypes.data_as(_PD) for a in arrs]), "lym1_tables")
+        return dict(zip(("dnu", "nubar", "Havg", "gem"), arrs))
+
+    def synchronize(self):
+        _check(lib().lym1_synchronize(self.handle), "lym1_synchronize")
+
+    def profile_enable(self, on=True):
+        _check(lib().lym1_profile_enable(self.handle, int(bool(on))), "lym1_profile_enable")
+
+    def profile_read(self, reset=True) -> dict:
+        p = lym1_profile()
+        _check(lib().lym1_profile_read(self.handle, C.byref(p), int(bool(reset))),
+               "lym1_profile_read")
+        return {name: getattr(p, name) for name, _ in p._fields_}
+
+    def run_to_steady(self, tol=1e-6, check_every=50, max_substeps=100000):
+        """Returns (converged, substeps run)."""
+        n = C.c_int()
+        st = lib().lym1_run_to_steady(self.handle, float(tol), int(check_every),
+                                      int(max_substeps), C.byref(n))
+        if st == ENOTCONVERGED:
+            return False, n.value
+        _check(st, "lym1_run_to_steady")
+        return True, n.value
+
+
+def substeps_batched(contexts, n):
+    """``lym1_substeps_batched`` over a list of Context objects."""
+    arr = (C.c_void_p * len(contexts))(*[c.handle.value for c in contexts])
+    _check(lib().lym1_substeps_batched(arr, len(contexts), int(n)), "lym1_substeps_batched")
+
+
+def from_cloud(cloud, precision=FP64_DET, stream=None, edges=None) -> Context:
+    """A context for a ``workloads.Cloud`` with its sources set."""
+    return Context(nx=cloud.nx, ny=cloud.ny, dx=cloud.dx, n_hi=cloud.n_hi, rho_d=cloud.rho_d,
+                   p_d=cloud.p_d, ux=cloud.ux, uy=cloud.uy, T=cloud.T, kappa_abs=cloud.kappa_abs,
+                   kappa_F=cloud.kappa_F, c_tilde=cloud.c_tilde, cfl=cloud.cfl,
+                   recoil=cloud.recoil, freq_step=cloud.freq_step, gray=cloud.gray, edges=edges,
+                   precision=precision, stream=stream, lum=cloud.lum)

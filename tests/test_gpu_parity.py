@@ -1,0 +1,189 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Bars:
+  LYM1_FP64_DET   bit-exact (same operation order, no FMA, same exp/expm1)
+  LYM1_FP64       1e-10 relative per element, absolute floor 1e-12 of the field max
+  LYM1_MIXED      1e-4 normwise: per state component and frequency bin,
+  LYM1_MIXED_FAST max |a - b| <= 1e-4 max |b| over the bin's plane (and over the
+                  whole field for the force).  FP32 arithmetic cannot give
+                  per-element relative accuracy on values that are small
+                  differences of larger terms (flux divergences), so the mixed
+                  bar is stated against each plane's scale.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 0.0, 1: 1e-10, 2: 1e-4, 3: 1e-4}
+
+
+@pytest.fixture(scope="module")
+def L():
+    import paper_2606_02711_gb300.lym1 as L
+    L.lib()
+    return L
+
+
+@pytest.fixture(scope="module")
+def edges():
+    return oracle.freq_grid()
+
+
+def close(a, b, rtol, name=""):
+    if rtol >= 1e-6:
+        # normwise per bin plane (state [nb][ny][nx]) or whole field (force)
+        planes = a.reshape(-1, a.shape[-2] * a.shape[-1]) if a.ndim == 3 else a.reshape(1, -1)
+        ref = b.reshape(planes.shape)
+        scale = np.abs(ref).max(axis=1)
+        err = np.abs(planes - ref).max(axis=1)
+        bad = err > rtol * scale
+        if np.any(bad):
+            k = int(np.argmax(np.where(scale > 0, err / np.maximum(scale, 1e-300), 0)))
+            raise AssertionError(f"{name}: plane {k}: max err {err[k]:.3e} vs scale "
+                                 f"{scale[k]:.3e} (rtol {rtol})")
+        return
+    if rtol == 0.0:
+        if not np.array_equal(a, b):
+            bad = np.argwhere(a != b)
+            i = tuple(bad[0])
+            raise AssertionError(f"{name}: {bad.shape[0]} of {a.size} differ; first at {i}: "
+                                 f"{a[i]!r} vs {b[i]!r}")
+        return
+    floor = 1e-12 * np.max(np.abs(b)) if b.size else 0.0
+    err = np.abs(a - b) - (rtol * np.abs(b) + floor)
+    if np.any(err > 0):
+        i = np.unravel_index(np.argmax(err), a.shape)
+        raise AssertionError(f"{name}: max excess at {i}: {a[i]!r} vs {b[i]!r} (rtol {rtol})")
+
+
+def random_state(nb, ny, nx, seed, scale=1e-12):
+    g = np.random.default_rng(seed)
+    J = scale * np.exp(g.normal(0, 1.0, (nb, ny, nx)))
+    th = g.uniform(0, 2 * np.pi, (nb, ny, nx))
+    f = g.uniform(0, 0.95, (nb, ny, nx))
+    return J, J * f * np.cos(th), J * f * np.sin(th)
+
+
+def run_both(L, cloud, edges, precision, nsteps, state=None):
+    ctx = L.from_cloud(cloud, precision=precision, edges=edges)
+    O = oracle.Oracle(edges=edges, **cloud.kwargs())
+    if state is not None:
+        ctx.set_state(*state)
+    ctx.substeps(nsteps)
+    got = ctx.get_state() + ctx.force()
+    dg = ctx.diagnostics()
+    ref, diags = O.run(nsteps, state)
+    ctx.destroy()
+    return got, ref, dg, diags
+
+
+def test_tables_match_oracle(L, edges):
+    c = wl.lognormal_cloud(8, 8, seed=1)
+    ctx = L.from_cloud(c, precision=L.FP64_DET, edges=edges)
+    O = oracle.Oracle(edges=edges, **c.kwargs())
+    a, b = ctx.tables(), O.tables()
+    for k in ("dnu", "nubar", "Havg", "gem"):
+        close(a[k], b[k], 0.0, k)
+    assert ctx.dt_cfl == O.dt_cfl
+    # default grid (NULL edges) is the paper grid
+    ctx2 = L.Context(nx=4, ny=4, dx=c.dx, n_hi=1e3, rho_d=0, p_d=0, ux=0, uy=0)
+    assert ctx2.nb == 194
+    close(ctx2.tables()["Havg"], b["Havg"], 0.0, "default grid")
+
+
+@pytest.mark.parametrize("precision", [0, 1, 2, 3])
+def test_gray_uniform_cloud(L, edges, precision):
+    # the 64x64 uniform gray cloud, ragged 40x28 cut of it, from zero
+    c = wl.uniform_gray(40, 28)
+    got, ref, dg, diags = run_both(L, c, edges, precision, 25)
+    for a, b, n in zip(got, ref, ("J", "Hx", "Hy", "fx", "fy")):
+        close(a, b, TOL[precision], n)
+    assert dg["e_tot"] == pytest.approx(diags[-1]["e_after"], rel=max(TOL[precision], 1e-12))
+
+
+@pytest.mark.parametrize("precision", [0, 1, 2, 3])
+def test_lognormal_cloud_194_bins(L, edges, precision):
+    # lognormal n_H, dust, destruction, v ~ r and recoil; several tiles + tail
+    c = wl.lognormal_cloud(45, 38, seed=3, v_edge_kms=30.0)
+    st = random_state(194, 38, 45, 7)
+    got, ref, dg, diags = run_both(L, c, edges, precision, 3, st)
+    for a, b, n in zip(got, ref, ("J", "Hx", "Hy", "fx", "fy")):
+        close(a, b, TOL[precision], n)
+    d = diags[-1]
+    assert dg["e_tot"] == pytest.approx(d["e_after"], rel=max(TOL[precision], 1e-12))
+    em = sum(x["emitted"] for x in diags)
+    ab = sum(x["absorbed"] for x in diags)
+    assert dg["emitted"] == pytest.approx(em, rel=1e-12)
+    assert dg["absorbed"] == pytest.approx(ab, rel=max(TOL[precision], 1e-12))
+
+
+def test_velocity_extremes_and_vacuum_cells(L, edges):
+    # large Peclet numbers (fast flow), contracting and expanding regions and
+    # cells without H I (no frequency step there)
+    c = wl.lognormal_cloud(33, 17, seed=4, v_edge_kms=2000.0)
+    c.n_hi[5:9, 10:20] = 0.0
+    c.ux[:, :10] *= -1.0
+    st = random_state(194, 17, 33, 8)
+    got, ref, _, _ = run_both(L, c, edges, 0, 2, st)
+    for a, b, n in zip(got, ref, ("J", "Hx", "Hy", "fx", "fy")):
+        close(a, b, 0.0, n)
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (1, 37), (29, 1), (2, 3), (32, 8), (33, 9)])
+def test_degenerate_and_ragged_shapes(L, edges, shape):
+    nx, ny = shape
+    c = wl.lognormal_cloud(max(nx, 2), max(ny, 2), seed=5)
+    c.nx, c.ny = nx, ny
+    for f in ("n_hi", "rho_d", "p_d", "ux", "uy", "lum"):
+        setattr(c, f, np.ascontiguousarray(getattr(c, f)[:ny, :nx]))
+    c.lum[...] = 1e36
+    got, ref, _, _ = run_both(L, c, edges, 0, 2, random_state(194, ny, nx, 9))
+    for a, b, n in zip(got, ref, ("J", "Hx", "Hy", "fx", "fy")):
+        close(a, b, 0.0, n)
+
+
+def test_no_sources_stays_zero_and_state_roundtrip(L, edges):
+    c = wl.lognormal_cloud(20, 12, seed=6)
+    c.lum[...] = 0.0
+    ctx = L.from_cloud(c, precision=L.FP64_DET, edges=edges)
+    ctx.substeps(4)
+    J, Hx, Hy = ctx.get_state()
+    assert not J.any() and not Hx.any() and not Hy.any()
+    st = random_state(194, 12, 20, 10)
+    ctx.set_state(*st)
+    back = ctx.get_state()
+    for a, b in zip(back, st):
+        close(a, b, 0.0)
+    E, Fx, Fy = ctx.moments()
+    close(E, 4 * np.pi / 2.99792458e10 * st[0], 1e-15)
+    close(Fx, 4 * np.pi * st[1], 1e-15)
+    ctx.destroy()
+
+
+def test_step_splits_into_cfl_substeps(L, edges):
+    c = wl.lognormal_cloud(16, 16, seed=2)
+    ctx = L.from_cloud(c, precision=L.FP64_DET, edges=edges)
+    n = ctx.step(3.5 * ctx.dt_cfl)
+    assert n == 4
+    assert ctx.info()["substeps_done"] == 4
+    O = oracle.Oracle(edges=edges, **c.kwargs())
+    ref, _ = O.run(4, dt=3.5 * O.dt_cfl / 4)
+    close(ctx.get_state()[0], ref[0], 0.0, "J")
+    ctx.destroy()
+
+
+def test_invalid_arguments(L):
+    with pytest.raises(L.Lym1Error) as e:
+        L.Context(nx=0, ny=4, dx=1.0, n_hi=1.0, rho_d=0, p_d=0, ux=0, uy=0)
+    assert e.value.status == L.EINVAL
+    with pytest.raises(L.Lym1Error):
+        L.Context(nx=4, ny=4, dx=-1.0, n_hi=1.0, rho_d=0, p_d=0, ux=0, uy=0)
+    with pytest.raises(L.Lym1Error):
+        L.Context(nx=4, ny=4, dx=1.0, n_hi=1.0, rho_d=0, p_d=0, ux=0, uy=0, precision=7)
+    with pytest.raises(L.Lym1Error):
+        L.Context(nx=4, ny=4, dx=1.0, n_hi=1.0, rho_d=0, p_d=0, ux=0, uy=0,
+                  edges=[0.0, 1.0, 1.0])
