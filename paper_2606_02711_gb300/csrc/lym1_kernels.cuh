@@ -429,33 +429,349 @@ __global__ void __launch_bounds__(kTileX* kTileY) transport_kernel(DeviceView v)
   if (tid == 0) part[kSlotBad] = s;
 }
 
+
+// ------------------------------------------------------- FP32 fast-path math
+// The FP32 policies use the SFU reciprocal / reciprocal square root (a few ulp)
+// and fold divisions by constants into multiplications; their results are
+// checked against the FP64 oracle at the mixed-precision bar.
+__device__ __forceinline__ float frcp(float b) { return __fdividef(1.0f, b); }
+__device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
+// J below this is treated as zero when forming f = H/J in FP32: the SFU
+// reciprocal flushes subnormal inputs, and such J are ~1e-30 of any field's
+// scale (the far wings of the line far from the sources).
+constexpr float kTinyJ = 1e-30f;
+
+// Levermore closure in the cancellation-free FP32 form (see closure()).
+__device__ __forceinline__ void closure_f32(float fn, float ft, float& Dnn, float& Dnt, float& Dtt) {
+  const float f2 = fn * fn + ft * ft;
+  const float y = 4.0f - 3.0f * f2;
+  const float s = y * rsqrtf(y);
+  const float inv = frcp(5.0f + 2.0f * s);
+  const float dA = (1.0f + s - 2.0f * f2) * inv;
+  const float g = (6.0f + fdiv(3.0f, 2.0f + s)) * inv;
+  Dnn = dA + g * (fn * fn);
+  Dnt = g * (fn * ft);
+  Dtt = dA + g * (ft * ft);
+}
+
+__device__ __forceinline__ void cap_unit_f32(float& fn, float& ft) {
+  const float f2 = fn * fn + ft * ft;
+  if (f2 > 1.0f) {
+    const float r = rsqrtf(f2);
+    fn *= r;
+    ft *= r;
+  }
+}
+
+// Face flux (same scheme as face_flux) with w = u/c stored per cell and the
+// interpolation factor and diffusion coefficient sharing one reciprocal:
+//   eps = (0.2 + tau) / d,  (1 - eps) / (3 tau) = tau / (3 d),  d = 0.2 + tau + tau^2.
+__device__ __forceinline__ void face_flux_f32(float Jm, float nm, float tm, float J0, float n0,
+                                              float t0, float J1, float n1, float t1, float J2,
+                                              float n2, float t2, float aF0, float aF1, float w0,
+                                              float w1, float half_dx, float& oJ, float& oN,
+                                              float& oT) {
+  const float sJ0 = minmod(J0 - Jm, J1 - J0), sJ1 = minmod(J1 - J0, J2 - J1);
+  const float sn0 = minmod(n0 - nm, n1 - n0), sn1 = minmod(n1 - n0, n2 - n1);
+  const float st0 = minmod(t0 - tm, t1 - t0), st1 = minmod(t1 - t0, t2 - t1);
+  const float JL = J0 + 0.5f * sJ0, JR = J1 - 0.5f * sJ1;
+  float nL = n0 + 0.5f * sn0, tL = t0 + 0.5f * st0;
+  float nR = n1 - 0.5f * sn1, tR = t1 - 0.5f * st1;
+  cap_unit_f32(nL, tL);
+  cap_unit_f32(nR, tR);
+  const float HnL = JL * nL, HtL = JL * tL, HnR = JR * nR, HtR = JR * tR;
+  float DnnL, DntL, DttL, DnnR, DntR, DttR;
+  closure_f32(nL, tL, DnnL, DntL, DttL);
+  closure_f32(nR, tR, DnnR, DntR, DttR);
+  const float tau = (aF0 + aF1) * half_dx;
+  const float a = 0.2f + tau;
+  const float rden = frcp(a + tau * tau);
+  const float eps = a * rden;
+  const float dcoef = tau * rden * (1.0f / 3.0f);
+  float fJ = 0.5f * eps * ((HnL + HnR) - (JR - JL)) - dcoef * (J1 - J0);
+  float fN = 0.5f * ((DnnL * JL + DnnR * JR) - eps * (HnR - HnL));
+  float fT = 0.5f * ((DntL * JL + DntR * JR) - eps * (HtR - HtL));
+  const float wf = 0.5f * (w0 + w1);
+  if (wf > 0.0f) {
+    fJ += wf * JL;
+    fN += wf * HnL;
+    fT += wf * HtL;
+  } else if (wf < 0.0f) {
+    fJ += wf * JR;
+    fN += wf * HnR;
+    fT += wf * HtR;
+  }
+  oJ = fJ;
+  oN = fN;
+  oT = fT;
+}
+
+// ------------------------------------------------ FP32 transport kernel
+// Same rows A1-A5 as transport_kernel for FP32 state and fluxes.  The halo
+// tile is double-buffered: each thread prefetches its (at most two) halo
+// entries of bin k+1 into registers while bin k is computed, so one substep
+// needs two block barriers per bin.  The implicit source step runs in type I
+// (FP64 for LYM1_MIXED, FP32 for LYM1_MIXED_FAST).
+template <class P>
+__global__ void __launch_bounds__(kTileX* kTileY) transport_kernel_f32(DeviceView v) {
+  using I = typename P::I;
+  constexpr int TX = kTileX, TY = kTileY, SX = TX + 4, SY = TY + 4, QX = TX + 2, QY = TY + 2;
+  constexpr int NT = TX * TY;
+  constexpr int NXF = (TX + 1) * TY, NYF = TX * (TY + 1);
+  static_assert(SX * SY <= 2 * NT, "two halo entries per thread at most");
+  __shared__ float sJ[2][SY][SX], sHx[2][SY][SX], sHy[2][SY][SX], sfx[2][SY][SX], sfy[2][SY][SX];
+  __shared__ float qA[QY][QX], qR[QY][QX], qWx[QY][QX], qWy[QY][QX];
+  __shared__ float xJ[TY][TX + 1], xN[TY][TX + 1], xT[TY][TX + 1];
+  __shared__ float yJ[TY + 1][TX], yN[TY + 1][TX], yT[TY + 1][TX];
+  __shared__ double red[NT / 32];
+  extern __shared__ float tabf[];  // <H>_k, dnu_k as FP32 (2 nb)
+  float* tH = tabf;
+  float* tD = tabf + v.nb;
+
+  const float* __restrict__ Jin = static_cast<const float*>(v.J);
+  const float* __restrict__ Hxin = static_cast<const float*>(v.Hx);
+  const float* __restrict__ Hyin = static_cast<const float*>(v.Hy);
+  float* __restrict__ Jout = static_cast<float*>(v.Jo);
+  float* __restrict__ Hxout = static_cast<float*>(v.Hxo);
+  float* __restrict__ Hyout = static_cast<float*>(v.Hyo);
+
+  const int nx = v.nx, ny = v.ny, nb = v.nb;
+  const long long nc = v.nc;
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  const int gx = x0 + tx, gy = y0 + ty;
+  const bool valid = gx < nx && gy < ny;
+  const long long cell = valid ? static_cast<long long>(gy) * nx + gx : 0;
+  const float inv_c = 1.0f / float(kLight);
+
+  for (int i = tid; i < nb; i += NT) {
+    tH[i] = float(v.t_H[i]);
+    tD[i] = float(v.t_dnu[i]);
+  }
+  for (int idx = tid; idx < QX * QY; idx += NT) {
+    const int lx = idx % QX, ly = idx / QX;
+    const long long c = static_cast<long long>(clampi(y0 + ly - 1, ny)) * nx + clampi(x0 + lx - 1, nx);
+    qA[ly][lx] = float(v.alpha[c]);
+    qR[ly][lx] = float(v.rho[c]);
+    qWx[ly][lx] = float(v.ux[c]) * inv_c;
+    qWy[ly][lx] = float(v.uy[c]) * inv_c;
+  }
+  // halo entries owned by this thread (plane offsets)
+  const int e0 = tid, e1 = tid + NT;
+  const bool has1 = e1 < SX * SY;
+  const int ex0 = e0 % SX, ey0 = e0 / SX, ex1 = e1 % SX, ey1 = e1 / SX;
+  const long long off0 = static_cast<long long>(clampi(y0 + ey0 - 2, ny)) * nx + clampi(x0 + ex0 - 2, nx);
+  const long long off1 = has1 ? static_cast<long long>(clampi(y0 + ey1 - 2, ny)) * nx + clampi(x0 + ex1 - 2, nx) : 0;
+
+  I alpha_c = 0, rho_c = 0, pd_c = 0;
+  float gxx = 0, gyy = 0, gsh = 0;
+  double lum_d = 0.0;
+  if (valid) {
+    alpha_c = I(v.alpha[cell]);
+    rho_c = I(v.rho[cell]);
+    pd_c = I(v.pd[cell]);
+    lum_d = v.lum[cell];
+    gxx = float(v.gxx[cell]);
+    gyy = float(v.gyy[cell]);
+    gsh = float(v.gsh[cell]);
+  }
+  const float half_dx = 0.5f * float(v.dx), kF_f = float(v.kF), cdt_f = float(v.cdt);
+  const float inv_dx = 1.0f / float(v.dx);
+  const float cdt_dx = float(v.cdt / v.dx);
+  const I cdt = I(v.cdt), kabs = I(v.kabs), kF = I(v.kF), cdx = I(v.cdt / v.dx);
+  I ax = 0, ay = 0;
+  RSum<I> em, ab, out, wk, en;
+  float mxf2 = 0.0f;
+  double bad = 0.0;
+
+  float pJ0 = Jin[off0], pX0 = Hxin[off0], pY0 = Hyin[off0];
+  float pJ1 = 0.f, pX1 = 0.f, pY1 = 0.f;
+  if (has1) {
+    pJ1 = Jin[off1];
+    pX1 = Hxin[off1];
+    pY1 = Hyin[off1];
+  }
+  for (int k = 0; k < nb; ++k) {
+    const int b = k & 1;
+    {  // halo entries of bin k: registers -> shared, with primitives
+      const float r0 = pJ0 > kTinyJ ? frcp(pJ0) : 0.0f;
+      sJ[b][ey0][ex0] = pJ0;
+      sHx[b][ey0][ex0] = pX0;
+      sHy[b][ey0][ex0] = pY0;
+      sfx[b][ey0][ex0] = pX0 * r0;
+      sfy[b][ey0][ex0] = pY0 * r0;
+      if (has1) {
+        const float r1 = pJ1 > kTinyJ ? frcp(pJ1) : 0.0f;
+        sJ[b][ey1][ex1] = pJ1;
+        sHx[b][ey1][ex1] = pX1;
+        sHy[b][ey1][ex1] = pY1;
+        sfx[b][ey1][ex1] = pX1 * r1;
+        sfy[b][ey1][ex1] = pY1 * r1;
+      }
+    }
+    if (k + 1 < nb) {  // prefetch bin k+1
+      const long long base = static_cast<long long>(k + 1) * nc;
+      pJ0 = Jin[base + off0];
+      pX0 = Hxin[base + off0];
+      pY0 = Hyin[base + off0];
+      if (has1) {
+        pJ1 = Jin[base + off1];
+        pX1 = Hxin[base + off1];
+        pY1 = Hyin[base + off1];
+      }
+    }
+    __syncthreads();
+    const float Hk = tH[k];
+    for (int f = tid; f < NXF + NYF; f += NT) {
+      if (f < NXF) {
+        const int fi = f % (TX + 1), fj = f / (TX + 1);
+        const int r = fj + 2;
+        const float aF0 = qA[fj + 1][fi] * Hk + qR[fj + 1][fi] * kF_f;
+        const float aF1 = qA[fj + 1][fi + 1] * Hk + qR[fj + 1][fi + 1] * kF_f;
+        face_flux_f32(sJ[b][r][fi], sfx[b][r][fi], sfy[b][r][fi], sJ[b][r][fi + 1],
+                      sfx[b][r][fi + 1], sfy[b][r][fi + 1], sJ[b][r][fi + 2], sfx[b][r][fi + 2],
+                      sfy[b][r][fi + 2], sJ[b][r][fi + 3], sfx[b][r][fi + 3], sfy[b][r][fi + 3],
+                      aF0, aF1, qWx[fj + 1][fi], qWx[fj + 1][fi + 1], half_dx, xJ[fj][fi],
+                      xN[fj][fi], xT[fj][fi]);
+      } else {
+        const int g = f - NXF;
+        const int fi = g % TX, fj = g / TX;
+        const int cc = fi + 2;
+        const float aF0 = qA[fj][fi + 1] * Hk + qR[fj][fi + 1] * kF_f;
+        const float aF1 = qA[fj + 1][fi + 1] * Hk + qR[fj + 1][fi + 1] * kF_f;
+        face_flux_f32(sJ[b][fj][cc], sfy[b][fj][cc], sfx[b][fj][cc], sJ[b][fj + 1][cc],
+                      sfy[b][fj + 1][cc], sfx[b][fj + 1][cc], sJ[b][fj + 2][cc],
+                      sfy[b][fj + 2][cc], sfx[b][fj + 2][cc], sJ[b][fj + 3][cc],
+                      sfy[b][fj + 3][cc], sfx[b][fj + 3][cc], aF0, aF1, qWy[fj][fi + 1],
+                      qWy[fj + 1][fi + 1], half_dx, yJ[fj][fi], yN[fj][fi], yT[fj][fi]);
+      }
+    }
+    __syncthreads();
+    if (valid) {
+      const float J = sJ[b][ty + 2][tx + 2], Hx = sHx[b][ty + 2][tx + 2], Hy = sHy[b][ty + 2][tx + 2];
+      float fxc = sfx[b][ty + 2][tx + 2], fyc = sfy[b][ty + 2][tx + 2];
+      cap_unit_f32(fxc, fyc);
+      float Dxx, Dxy, Dyy;
+      closure_f32(fxc, fyc, Dxx, Dxy, Dyy);
+      const float W = J * ((Dxx * gxx + Dyy * gyy) + Dxy * gsh);
+      const float divJ = (xJ[ty][tx + 1] - xJ[ty][tx]) + (yJ[ty + 1][tx] - yJ[ty][tx]);
+      const float divHx = (xN[ty][tx + 1] - xN[ty][tx]) + (yT[ty + 1][tx] - yT[ty][tx]);
+      const float divHy = (xT[ty][tx + 1] - xT[ty][tx]) + (yN[ty + 1][tx] - yN[ty][tx]);
+      const float J1 = J - cdt_f * (divJ * inv_dx + W * inv_c);
+      const float Hx1 = Hx - cdt_dx * divHx;
+      const float Hy1 = Hy - cdt_dx * divHy;
+      I aH, dnu;
+      if constexpr (sizeof(I) == 8) {
+        aH = alpha_c * v.t_H[k];
+        dnu = v.t_dnu[k];
+      } else {
+        aH = alpha_c * Hk;
+        dnu = tD[k];
+      }
+      const I kap = rho_c * kabs + pd_c * aH;
+      const I aF = aH + rho_c * kF;
+      // j_k = L w_k / (4 pi dx^3 dnu_k), formed in FP64 (outside the FP32 range)
+      const I js = (lum_d != 0.0) ? I(lum_d * v.t_gem[k]) : I(0);
+      I J2, Hx2, Hy2;
+      if constexpr (sizeof(I) == 8) {
+        J2 = (I(J1) + cdt * js) / (I(1) + cdt * kap);
+        const I ra = I(1) / (I(1) + cdt * aF);
+        Hx2 = I(Hx1) * ra;
+        Hy2 = I(Hy1) * ra;
+      } else {
+        J2 = (J1 + cdt * js) * frcp(1.0f + cdt * kap);
+        const float ra = frcp(1.0f + cdt * aF);
+        Hx2 = Hx1 * ra;
+        Hy2 = Hy1 * ra;
+      }
+      const long long o = static_cast<long long>(k) * nc + cell;
+      Jout[o] = float(J2);
+      Hxout[o] = float(Hx2);
+      Hyout[o] = float(Hy2);
+      ax = ax + dnu * (I(Hx1) - Hx2);
+      ay = ay + dnu * (I(Hy1) - Hy2);
+      // A7 bookkeeping (energy units applied once per substep)
+      if (lum_d != 0.0) em.add(dnu * (cdt * js));
+      ab.add(dnu * (cdt * (kap * J2)));
+      wk.add(dnu * (cdt * (I(W) * I(inv_c))));
+      en.add(dnu * J2);
+      const float j2f = float(J2), h2 = float(Hx2) * float(Hx2) + float(Hy2) * float(Hy2);
+      const float jj = j2f * j2f;
+      if (j2f > 1e-18f) mxf2 = fmaxf(mxf2, fdiv(h2, jj));
+      if (h2 > jj * 1.000002f && h2 > 0.0f) bad += 1.0;
+      if (gx == 0) out.add(dnu * (cdx * -I(xJ[ty][tx])));
+      if (gx == nx - 1) out.add(dnu * (cdx * I(xJ[ty][tx + 1])));
+      if (gy == 0) out.add(dnu * (cdx * -I(yJ[ty][tx])));
+      if (gy == ny - 1) out.add(dnu * (cdx * I(yJ[ty + 1][tx])));
+    }
+  }
+  if (valid) {
+    v.fx[cell] = v.fcoef * double(ax);
+    v.fy[cell] = v.fcoef * double(ay);
+  }
+  const int blk = blockIdx.y * gridDim.x + blockIdx.x;
+  double* part = v.partT + static_cast<long long>(blk) * kDiagSlots;
+  double s;
+  s = block_sum<NT>(em.value(), red);
+  if (tid == 0) part[kSlotEmitted] = s;
+  s = block_sum<NT>(ab.value(), red);
+  if (tid == 0) part[kSlotAbsorbed] = s;
+  s = block_sum<NT>(out.value(), red);
+  if (tid == 0) part[kSlotOutflow] = s;
+  s = block_sum<NT>(wk.value(), red);
+  if (tid == 0) part[kSlotWork] = s;
+  s = block_sum<NT>(en.value(), red);
+  if (tid == 0) part[kSlotEnergy] = s;
+  s = block_max<NT>(sqrt(double(mxf2)), red);
+  if (tid == 0) part[kSlotMaxF] = s;
+  s = block_sum<NT>(bad, red);
+  if (tid == 0) part[kSlotBad] = s;
+}
+
 // ------------------------------------------------------------ frequency kernel
 // Coefficients of bin k for one cell (App. A): Peclet number P_k, dlt_k/K_k and
 // E(-|P_k|) = expm1(-|P_k|) / (-|P_k|), with D_k from the post-source state.
-template <class P>
+template <class P, class T>
 __device__ __forceinline__ void freq_coef(typename P::F Jc, typename P::F Hxc, typename P::F Hyc,
                                           typename P::F Kc, typename P::F gxx,
-                                          typename P::F gyy, typename P::F gsh,
-                                          const double* tH, const double* tR, const double* tn,
-                                          const double* th, int k, typename P::F& Pk,
-                                          typename P::F& ak, typename P::F& ek) {
+                                          typename P::F gyy, typename P::F gsh, const T* tH,
+                                          const T* tR, const T* tn, const T* th, int k,
+                                          typename P::F& Pk, typename P::F& ak,
+                                          typename P::F& ek) {
   using F = typename P::F;
-  F fx = F(0), fy = F(0);
-  if (Jc > F(0)) {
-    fx = Hxc / Jc;
-    fy = Hyc / Jc;
+  if constexpr (sizeof(F) == 4) {
+    const float r = Jc > kTinyJ ? frcp(Jc) : 0.0f;
+    float fx = Hxc * r, fy = Hyc * r;
+    cap_unit_f32(fx, fy);
+    float Dxx, Dxy, Dyy;
+    closure_f32(fx, fy, Dxx, Dxy, Dyy);
+    const float DdU = (Dxx * gxx + Dyy * gyy) + Dxy * gsh;
+    const float K = Kc * tH[k];
+    const float rK = frcp(K);
+    const float C = K * tR[k] + tn[k] * DdU;
+    const float half = th[k];
+    ak = half * rK;
+    Pk = C * ak;
+    const float z = -fabsf(Pk);
+    ek = (z == 0.0f) ? 1.0f : fdiv(expm1f(z), z);
+  } else {
+    F fx = F(0), fy = F(0);
+    if (Jc > F(0)) {
+      fx = Hxc / Jc;
+      fy = Hyc / Jc;
+    }
+    cap_unit(fx, fy);
+    F Dxx, Dxy, Dyy;
+    closure(fx, fy, Dxx, Dxy, Dyy);
+    const F DdU = (Dxx * gxx + Dyy * gyy) + Dxy * gsh;
+    const F K = Kc * F(tH[k]);
+    const F C = K * F(tR[k]) + F(tn[k]) * DdU;
+    const F half = F(th[k]);
+    Pk = (C * half) / K;
+    ak = half / K;
+    const F z = -fabs(Pk);
+    ek = (z == F(0)) ? F(1) : m_expm1<P::DET>(z) / z;
   }
-  cap_unit(fx, fy);
-  F Dxx, Dxy, Dyy;
-  closure(fx, fy, Dxx, Dxy, Dyy);
-  const F DdU = (Dxx * gxx + Dyy * gyy) + Dxy * gsh;
-  const F K = Kc * F(tH[k]);
-  const F C = K * F(tR[k]) + F(tn[k]) * DdU;
-  const F half = F(th[k]);
-  Pk = (C * half) / K;
-  ak = half / K;
-  const F z = -fabs(Pk);
-  ek = (z == F(0)) ? F(1) : m_expm1<P::DET>(z) / z;
 }
 
 template <class P>
@@ -463,21 +779,25 @@ __global__ void __launch_bounds__(kFreqThreads) freq_kernel(DeviceView v) {
   using S = typename P::S;
   using F = typename P::F;
   using I = typename P::I;
+  using T = F;  // table type in shared memory
   constexpr int NT = kFreqThreads;
-  extern __shared__ double tabs[];
+  extern __shared__ double tabs_raw[];
+  T* tabs = reinterpret_cast<T*>(tabs_raw);
   __shared__ double red[NT / 32];
   const int nb = v.nb;
-  double* tH = tabs;
-  double* tR = tabs + nb;
-  double* tn = tabs + 2 * nb;
-  double* th = tabs + 3 * nb;
-  double* td = tabs + 4 * nb;
+  T* tH = tabs;
+  T* tR = tabs + nb;
+  T* tn = tabs + 2 * nb;
+  T* th = tabs + 3 * nb;
+  T* td = tabs + 4 * nb;
+  I* tdi = reinterpret_cast<I*>(tabs_raw + 5 * nb);  // dnu_k in the elimination type
   for (int i = threadIdx.x; i < nb; i += NT) {
-    tH[i] = v.t_H[i];
-    tR[i] = v.t_R[i];
-    tn[i] = v.t_nbc[i];
-    th[i] = v.t_half[i];
-    td[i] = v.t_dnu[i];
+    tH[i] = T(v.t_H[i]);
+    tR[i] = T(v.t_R[i]);
+    tn[i] = T(v.t_nbc[i]);
+    th[i] = T(v.t_half[i]);
+    td[i] = T(v.t_dnu[i]);
+    tdi[i] = I(v.t_dnu[i]);
   }
   __syncthreads();
 
@@ -498,6 +818,8 @@ __global__ void __launch_bounds__(kFreqThreads) freq_kernel(DeviceView v) {
       const F Kc = F(v.Kc * alpha);
       const F gxx = F(v.gxx[cell]), gyy = F(v.gyy[cell]), gsh = F(v.gsh[cell]);
       const I cdt = I(v.cdt);
+      const float rcdt = float(1.0 / v.cdt);
+      (void)rcdt;
       F P0, a0, e0, P1 = F(0), a1 = F(0), e1 = F(0);
       I Jin0 = I(Jin[cell]);
       I Jin1 = 0;
@@ -516,14 +838,29 @@ __global__ void __launch_bounds__(kFreqThreads) freq_kernel(DeviceView v) {
           const F d2 = (P1 > F(0)) ? P1 : F(0);
           const F m = (d1 > d2) ? d1 : d2;
           const F den = m_exp<P::DET>(d1 - m) * (e0 * a0) + m_exp<P::DET>(d2 - m) * (e1 * a1);
-          A = I(m_exp<P::DET>(-P0 - m) / den);
-          B = I(m_exp<P::DET>(P1 - m) / den);
+          if constexpr (sizeof(F) == 4) {
+            const float rden = frcp(den);
+            A = I(m_exp<P::DET>(-P0 - m) * rden);
+            B = I(m_exp<P::DET>(P1 - m) * rden);
+          } else {
+            A = I(m_exp<P::DET>(-P0 - m) / den);
+            B = I(m_exp<P::DET>(P1 - m) / den);
+          }
         }
-        const I s = I(td[k]) / cdt;
+        I s, inv_dummy = 0;
+        (void)inv_dummy;
+        if constexpr (sizeof(I) == 4)
+          s = tdi[k] * rcdt;
+        else
+          s = tdi[k] / cdt;
         const I E = (k == 0) ? s : s + Bprev * qprev;
         const I r = (k == 0) ? s * Jin0 : s * Jin0 + Aprev * gprev;
         const I Dp = E + A;
-        const I inv = I(1) / Dp;
+        I inv;
+        if constexpr (sizeof(I) == 4)
+          inv = frcp(Dp);
+        else
+          inv = I(1) / Dp;
         const I g = r * inv;
         const I h = B * inv;
         qprev = E * inv;
@@ -545,13 +882,17 @@ __global__ void __launch_bounds__(kFreqThreads) freq_kernel(DeviceView v) {
         const I Jn = (k == nb - 1) ? g : g + h * Jnext;
         Jnext = Jn;
         const I Jo = I(Jin[o]);
-        const I ratio = (Jo > I(0)) ? Jn / Jo : I(0);
+        I ratio;
+        if constexpr (sizeof(I) == 4)
+          ratio = (Jo > kTinyJ) ? fdiv(Jn, Jo) : 0.0f;
+        else
+          ratio = (Jo > I(0)) ? Jn / Jo : I(0);
         const I Hx2 = ratio * I(Hxin[o]);
         const I Hy2 = ratio * I(Hyin[o]);
         Jout[o] = S(Jn);
         Hxout[o] = S(Hx2);
         Hyout[o] = S(Hy2);
-        en.add(I(td[k]) * Jn);
+        en.add(tdi[k] * Jn);
         const I hn = sqrt(Hx2 * Hx2 + Hy2 * Hy2);
         if (Jn > I(0)) mxf = fmax(mxf, hn / Jn);
         if (hn > Jn * I(1.000001) && hn > I(0)) bad += 1.0;
@@ -564,7 +905,7 @@ __global__ void __launch_bounds__(kFreqThreads) freq_kernel(DeviceView v) {
         Hxout[o] = Hx;
         Hyout[o] = Hy;
         const I Ji = I(J), Hxi = I(Hx), Hyi = I(Hy);
-        en.add(I(td[k]) * Ji);
+        en.add(tdi[k] * Ji);
         const I hn = sqrt(Hxi * Hxi + Hyi * Hyi);
         if (Ji > I(0)) mxf = fmax(mxf, hn / Ji);
         if (hn > Ji * I(1.000001) && hn > I(0)) bad += 1.0;
@@ -584,13 +925,18 @@ __global__ void __launch_bounds__(kFreqThreads) freq_kernel(DeviceView v) {
 template <class P>
 int launch_transport_t(const DeviceView& v, cudaStream_t st) {
   dim3 grid((v.nx + kTileX - 1) / kTileX, (v.ny + kTileY - 1) / kTileY);
-  transport_kernel<P><<<grid, dim3(kTileX, kTileY), 0, st>>>(v);
+  if constexpr (sizeof(typename P::S) == 4) {
+    const size_t smem = sizeof(float) * 2 * static_cast<size_t>(v.nb);
+    transport_kernel_f32<P><<<grid, dim3(kTileX, kTileY), smem, st>>>(v);
+  } else {
+    transport_kernel<P><<<grid, dim3(kTileX, kTileY), 0, st>>>(v);
+  }
   return static_cast<int>(cudaGetLastError());
 }
 
 template <class P>
 int launch_freq_t(const DeviceView& v, cudaStream_t st) {
-  const size_t smem = sizeof(double) * 5 * static_cast<size_t>(v.nb);
+  const size_t smem = sizeof(double) * 6 * static_cast<size_t>(v.nb);
   freq_kernel<P><<<freq_blocks(v.nc), kFreqThreads, smem, st>>>(v);
   return static_cast<int>(cudaGetLastError());
 }
