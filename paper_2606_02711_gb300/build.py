@@ -36,6 +36,10 @@ def _cmd(src: str) -> list[str]:
            "-Xcompiler", "-ffp-contract=off", *inc, "-c", path, "-o", obj]
     if src == "lym1_kernels_det.cu":
         cmd.insert(1, "-fmad=false")
+    if src == "lym1_kernels_fast.cu":
+        # FP32 policies: flush subnormals, approximate FP32 divide/sqrt (FP64
+        # arithmetic is not affected by these flags)
+        cmd[1:1] = ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"]
     return cmd
 
 

@@ -9,7 +9,7 @@
 #include <new>
 #include <vector>
 
-#include "../../include/lym1.h"
+#include "lym1.h"
 #include "lym1_internal.h"
 
 using namespace lym1;
@@ -18,7 +18,7 @@ struct lym1_ctx {
   int nx = 0, ny = 0, nb = 0, precision = 0, gray = 0, freq_step = 0, recoil = 0;
   long long nc = 0;
   double dx = 0, T = 0, c_tilde = 0, cfl = 0, kabs = 0, kF = 0, dt_cfl = 0, umax = 0;
-  double L_tot = 0, device_bytes = 0;
+  double L_tot = 0, device_bytes = 0, gem_max = 1;
   long long substeps_done = 0;
   cudaStream_t stream = nullptr;
   BinTables tab;
@@ -137,6 +137,7 @@ DeviceView make_view(const lym1_ctx* c, double dt) {
   // Sec. 2.3: f = 4 pi / (c ct dt) sum_k dnu_k (H' - H'')
   v.fcoef = (4.0 * kPi) / ((kLight * c->c_tilde) * dt);
   v.freq_step = c->freq_step;
+  v.gem_max = c->gem_max;
   return v;
 }
 
@@ -325,6 +326,9 @@ int lym1_create(const lym1_grid* grid, const lym1_groups* groups, const lym1_opa
   c->selem = (c->precision >= LYM1_MIXED) ? 4 : 8;
   build_tables(edges, c->T, c->dx, c->gray, c->recoil, &c->tab);
   c->nb = c->tab.nb;
+  c->gem_max = 0.0;
+  for (double g : c->tab.gem) c->gem_max = std::max(c->gem_max, g);
+  if (!(c->gem_max > 0.0)) c->gem_max = 1.0;
 
   int rc = LYM1_OK;
   const size_t plane = static_cast<size_t>(nc);

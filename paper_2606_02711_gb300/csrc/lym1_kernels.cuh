@@ -463,20 +463,27 @@ __device__ __forceinline__ void cap_unit_f32(float& fn, float& ft) {
   }
 }
 
-// Face flux (same scheme as face_flux) with w = u/c stored per cell and the
-// interpolation factor and diffusion coefficient sharing one reciprocal:
+// MinMod without branches: the smaller magnitude with the common sign, zero
+// when the signs differ (sign bits compared, so tiny slopes are kept).
+__device__ __forceinline__ float minmod_f32(float a, float b) {
+  const float m = copysignf(fminf(fabsf(a), fabsf(b)), a);
+  return ((__float_as_uint(a) ^ __float_as_uint(b)) & 0x80000000u) ? 0.0f : m;
+}
+
+// Face flux (same scheme as face_flux) from packed primitives q = (J, f_n, f_t)
+// of cells -1, 0, +1, +2, with w = u/c per cell; the interpolation factor and
+// the diffusion coefficient share one reciprocal:
 //   eps = (0.2 + tau) / d,  (1 - eps) / (3 tau) = tau / (3 d),  d = 0.2 + tau + tau^2.
 __device__ __forceinline__ void face_flux_f32(float Jm, float nm, float tm, float J0, float n0,
                                               float t0, float J1, float n1, float t1, float J2,
                                               float n2, float t2, float aF0, float aF1, float w0,
                                               float w1, float half_dx, float& oJ, float& oN,
                                               float& oT) {
-  const float sJ0 = minmod(J0 - Jm, J1 - J0), sJ1 = minmod(J1 - J0, J2 - J1);
-  const float sn0 = minmod(n0 - nm, n1 - n0), sn1 = minmod(n1 - n0, n2 - n1);
-  const float st0 = minmod(t0 - tm, t1 - t0), st1 = minmod(t1 - t0, t2 - t1);
-  const float JL = J0 + 0.5f * sJ0, JR = J1 - 0.5f * sJ1;
-  float nL = n0 + 0.5f * sn0, tL = t0 + 0.5f * st0;
-  float nR = n1 - 0.5f * sn1, tR = t1 - 0.5f * st1;
+  const float d0 = J0 - Jm, d1 = J1 - J0, d2 = J2 - J1;
+  const float JL = J0 + 0.5f * minmod_f32(d0, d1), JR = J1 - 0.5f * minmod_f32(d1, d2);
+  const float e1 = n1 - n0, g1 = t1 - t0;
+  float nL = n0 + 0.5f * minmod_f32(n0 - nm, e1), tL = t0 + 0.5f * minmod_f32(t0 - tm, g1);
+  float nR = n1 - 0.5f * minmod_f32(e1, n2 - n1), tR = t1 - 0.5f * minmod_f32(g1, t2 - t1);
   cap_unit_f32(nL, tL);
   cap_unit_f32(nR, tR);
   const float HnL = JL * nL, HtL = JL * tL, HnR = JR * nR, HtR = JR * tR;
@@ -488,45 +495,40 @@ __device__ __forceinline__ void face_flux_f32(float Jm, float nm, float tm, floa
   const float rden = frcp(a + tau * tau);
   const float eps = a * rden;
   const float dcoef = tau * rden * (1.0f / 3.0f);
-  float fJ = 0.5f * eps * ((HnL + HnR) - (JR - JL)) - dcoef * (J1 - J0);
-  float fN = 0.5f * ((DnnL * JL + DnnR * JR) - eps * (HnR - HnL));
-  float fT = 0.5f * ((DntL * JL + DntR * JR) - eps * (HtR - HtL));
   const float wf = 0.5f * (w0 + w1);
-  if (wf > 0.0f) {
-    fJ += wf * JL;
-    fN += wf * HnL;
-    fT += wf * HtL;
-  } else if (wf < 0.0f) {
-    fJ += wf * JR;
-    fN += wf * HnR;
-    fT += wf * HtR;
-  }
-  oJ = fJ;
-  oN = fN;
-  oT = fT;
+  const bool up = wf > 0.0f;  // upwind donor: reconstructed state on the upwind side
+  const float Jd = up ? JL : JR, Hnd = up ? HnL : HnR, Htd = up ? HtL : HtR;
+  oJ = 0.5f * eps * ((HnL + HnR) - (JR - JL)) - dcoef * d1 + wf * Jd;
+  oN = 0.5f * ((DnnL * JL + DnnR * JR) - eps * (HnR - HnL)) + wf * Hnd;
+  oT = 0.5f * ((DntL * JL + DntR * JR) - eps * (HtR - HtL)) + wf * Htd;
 }
 
 // ------------------------------------------------ FP32 transport kernel
 // Same rows A1-A5 as transport_kernel for FP32 state and fluxes.  The halo
-// tile is double-buffered: each thread prefetches its (at most two) halo
-// entries of bin k+1 into registers while bin k is computed, so one substep
-// needs two block barriers per bin.  The implicit source step runs in type I
-// (FP64 for LYM1_MIXED, FP32 for LYM1_MIXED_FAST).
+// tile is double-buffered and packed as float4 (J, f_x, f_y, -) per cell; each
+// thread prefetches its (at most two) halo entries of bin k+1 into registers
+// while bin k is computed, so one bin needs two block barriers.  Faces are
+// mapped to threads without division: every thread computes the left x-face
+// and the bottom y-face of its cell, warp 0 the top row of y-faces and part
+// of warp 1 the right column of x-faces.  The implicit source step runs in
+// type I (FP64 for LYM1_MIXED, FP32 for LYM1_MIXED_FAST).
 template <class P>
-__global__ void __launch_bounds__(kTileX* kTileY) transport_kernel_f32(DeviceView v) {
+__global__ void __launch_bounds__(kTileX* kTileY, 3) transport_kernel_f32(DeviceView v) {
   using I = typename P::I;
   constexpr int TX = kTileX, TY = kTileY, SX = TX + 4, SY = TY + 4, QX = TX + 2, QY = TY + 2;
   constexpr int NT = TX * TY;
-  constexpr int NXF = (TX + 1) * TY, NYF = TX * (TY + 1);
   static_assert(SX * SY <= 2 * NT, "two halo entries per thread at most");
-  __shared__ float sJ[2][SY][SX], sHx[2][SY][SX], sHy[2][SY][SX], sfx[2][SY][SX], sfy[2][SY][SX];
-  __shared__ float qA[QY][QX], qR[QY][QX], qWx[QY][QX], qWy[QY][QX];
+  static_assert(TY <= 32, "right-column faces are computed by one warp");
+  __shared__ float4 sq[2][SY][SX];  // (J, f_x, f_y, unused)
+  __shared__ float sHx[2][SY][SX], sHy[2][SY][SX];
+  __shared__ float4 qc[QY][QX];  // (alpha, rho_d, u_x/c, u_y/c)
   __shared__ float xJ[TY][TX + 1], xN[TY][TX + 1], xT[TY][TX + 1];
   __shared__ float yJ[TY + 1][TX], yN[TY + 1][TX], yT[TY + 1][TX];
   __shared__ double red[NT / 32];
-  extern __shared__ float tabf[];  // <H>_k, dnu_k as FP32 (2 nb)
+  extern __shared__ float tabf[];  // <H>_k, dnu_k, gem_k / gem_max as FP32 (3 nb)
   float* tH = tabf;
   float* tD = tabf + v.nb;
+  float* tG = tabf + 2 * v.nb;
 
   const float* __restrict__ Jin = static_cast<const float*>(v.J);
   const float* __restrict__ Hxin = static_cast<const float*>(v.Hx);
@@ -547,14 +549,13 @@ __global__ void __launch_bounds__(kTileX* kTileY) transport_kernel_f32(DeviceVie
   for (int i = tid; i < nb; i += NT) {
     tH[i] = float(v.t_H[i]);
     tD[i] = float(v.t_dnu[i]);
+    tG[i] = float(v.t_gem[i] / v.gem_max);
   }
   for (int idx = tid; idx < QX * QY; idx += NT) {
     const int lx = idx % QX, ly = idx / QX;
     const long long c = static_cast<long long>(clampi(y0 + ly - 1, ny)) * nx + clampi(x0 + lx - 1, nx);
-    qA[ly][lx] = float(v.alpha[c]);
-    qR[ly][lx] = float(v.rho[c]);
-    qWx[ly][lx] = float(v.ux[c]) * inv_c;
-    qWy[ly][lx] = float(v.uy[c]) * inv_c;
+    qc[ly][lx] = make_float4(float(v.alpha[c]), float(v.rho[c]), float(v.ux[c]) * inv_c,
+                             float(v.uy[c]) * inv_c);
   }
   // halo entries owned by this thread (plane offsets)
   const int e0 = tid, e1 = tid + NT;
@@ -562,6 +563,8 @@ __global__ void __launch_bounds__(kTileX* kTileY) transport_kernel_f32(DeviceVie
   const int ex0 = e0 % SX, ey0 = e0 / SX, ex1 = e1 % SX, ey1 = e1 / SX;
   const long long off0 = static_cast<long long>(clampi(y0 + ey0 - 2, ny)) * nx + clampi(x0 + ex0 - 2, nx);
   const long long off1 = has1 ? static_cast<long long>(clampi(y0 + ey1 - 2, ny)) * nx + clampi(x0 + ex1 - 2, nx) : 0;
+  // extra faces: warp 0 -> top row of y-faces, warp 1 (lanes < TY) -> right column of x-faces
+  const bool xtra_y = ty == 0, xtra_x = ty == 1 && tx < TY;
 
   I alpha_c = 0, rho_c = 0, pd_c = 0;
   float gxx = 0, gyy = 0, gsh = 0;
@@ -580,9 +583,17 @@ __global__ void __launch_bounds__(kTileX* kTileY) transport_kernel_f32(DeviceVie
   const float cdt_dx = float(v.cdt / v.dx);
   const I cdt = I(v.cdt), kabs = I(v.kabs), kF = I(v.kF), cdx = I(v.cdt / v.dx);
   I ax = 0, ay = 0;
-  RSum<I> em, ab, out, wk, en;
+  // per-cell bookkeeping sums over the bins: FP64 (compensation-free, exact
+  // enough at 194 terms) for LYM1_MIXED, plain FP32 for LYM1_MIXED_FAST; the
+  // sums over cells are FP64 in both
+  I em = 0, ab = 0, out = 0, wk = 0, en = 0;
   float mxf2 = 0.0f;
-  double bad = 0.0;
+  int bad = 0;
+  // emissivity j_k = (L_cell gem_max) (gem_k / gem_max): both factors lie in
+  // the FP32 range, unlike L_cell (~1e39 erg/s) and gem_k (~1e-58) alone
+  const bool src = lum_d != 0.0;
+  const float jsc = float(lum_d * v.gem_max);
+  const bool bnd = valid && (gx == 0 || gx == nx - 1 || gy == 0 || gy == ny - 1);
 
   float pJ0 = Jin[off0], pX0 = Hxin[off0], pY0 = Hyin[off0];
   float pJ1 = 0.f, pX1 = 0.f, pY1 = 0.f;
@@ -595,18 +606,14 @@ __global__ void __launch_bounds__(kTileX* kTileY) transport_kernel_f32(DeviceVie
     const int b = k & 1;
     {  // halo entries of bin k: registers -> shared, with primitives
       const float r0 = pJ0 > kTinyJ ? frcp(pJ0) : 0.0f;
-      sJ[b][ey0][ex0] = pJ0;
+      sq[b][ey0][ex0] = make_float4(pJ0, pX0 * r0, pY0 * r0, 0.0f);
       sHx[b][ey0][ex0] = pX0;
       sHy[b][ey0][ex0] = pY0;
-      sfx[b][ey0][ex0] = pX0 * r0;
-      sfy[b][ey0][ex0] = pY0 * r0;
       if (has1) {
         const float r1 = pJ1 > kTinyJ ? frcp(pJ1) : 0.0f;
-        sJ[b][ey1][ex1] = pJ1;
+        sq[b][ey1][ex1] = make_float4(pJ1, pX1 * r1, pY1 * r1, 0.0f);
         sHx[b][ey1][ex1] = pX1;
         sHy[b][ey1][ex1] = pY1;
-        sfx[b][ey1][ex1] = pX1 * r1;
-        sfy[b][ey1][ex1] = pY1 * r1;
       }
     }
     if (k + 1 < nb) {  // prefetch bin k+1
@@ -622,34 +629,33 @@ __global__ void __launch_bounds__(kTileX* kTileY) transport_kernel_f32(DeviceVie
     }
     __syncthreads();
     const float Hk = tH[k];
-    for (int f = tid; f < NXF + NYF; f += NT) {
-      if (f < NXF) {
-        const int fi = f % (TX + 1), fj = f / (TX + 1);
-        const int r = fj + 2;
-        const float aF0 = qA[fj + 1][fi] * Hk + qR[fj + 1][fi] * kF_f;
-        const float aF1 = qA[fj + 1][fi + 1] * Hk + qR[fj + 1][fi + 1] * kF_f;
-        face_flux_f32(sJ[b][r][fi], sfx[b][r][fi], sfy[b][r][fi], sJ[b][r][fi + 1],
-                      sfx[b][r][fi + 1], sfy[b][r][fi + 1], sJ[b][r][fi + 2], sfx[b][r][fi + 2],
-                      sfy[b][r][fi + 2], sJ[b][r][fi + 3], sfx[b][r][fi + 3], sfy[b][r][fi + 3],
-                      aF0, aF1, qWx[fj + 1][fi], qWx[fj + 1][fi + 1], half_dx, xJ[fj][fi],
-                      xN[fj][fi], xT[fj][fi]);
-      } else {
-        const int g = f - NXF;
-        const int fi = g % TX, fj = g / TX;
-        const int cc = fi + 2;
-        const float aF0 = qA[fj][fi + 1] * Hk + qR[fj][fi + 1] * kF_f;
-        const float aF1 = qA[fj + 1][fi + 1] * Hk + qR[fj + 1][fi + 1] * kF_f;
-        face_flux_f32(sJ[b][fj][cc], sfy[b][fj][cc], sfx[b][fj][cc], sJ[b][fj + 1][cc],
-                      sfy[b][fj + 1][cc], sfx[b][fj + 1][cc], sJ[b][fj + 2][cc],
-                      sfy[b][fj + 2][cc], sfx[b][fj + 2][cc], sJ[b][fj + 3][cc],
-                      sfy[b][fj + 3][cc], sfx[b][fj + 3][cc], aF0, aF1, qWy[fj][fi + 1],
-                      qWy[fj + 1][fi + 1], half_dx, yJ[fj][fi], yN[fj][fi], yT[fj][fi]);
-      }
-    }
+    auto xface = [&](int fi, int fj) {  // between tile cells (fi-1, fj) and (fi, fj)
+      const int r = fj + 2;
+      const float4 qm = sq[b][r][fi], q0 = sq[b][r][fi + 1], q1 = sq[b][r][fi + 2],
+                   q2 = sq[b][r][fi + 3];
+      const float4 c0 = qc[fj + 1][fi], c1 = qc[fj + 1][fi + 1];
+      face_flux_f32(qm.x, qm.y, qm.z, q0.x, q0.y, q0.z, q1.x, q1.y, q1.z, q2.x, q2.y, q2.z,
+                    c0.x * Hk + c0.y * kF_f, c1.x * Hk + c1.y * kF_f, c0.z, c1.z, half_dx,
+                    xJ[fj][fi], xN[fj][fi], xT[fj][fi]);
+    };
+    auto yface = [&](int fi, int fj) {  // between tile cells (fi, fj-1) and (fi, fj)
+      const int cc = fi + 2;
+      const float4 qm = sq[b][fj][cc], q0 = sq[b][fj + 1][cc], q1 = sq[b][fj + 2][cc],
+                   q2 = sq[b][fj + 3][cc];
+      const float4 c0 = qc[fj][fi + 1], c1 = qc[fj + 1][fi + 1];
+      face_flux_f32(qm.x, qm.z, qm.y, q0.x, q0.z, q0.y, q1.x, q1.z, q1.y, q2.x, q2.z, q2.y,
+                    c0.x * Hk + c0.y * kF_f, c1.x * Hk + c1.y * kF_f, c0.w, c1.w, half_dx,
+                    yJ[fj][fi], yN[fj][fi], yT[fj][fi]);
+    };
+    xface(tx, ty);
+    yface(tx, ty);
+    if (xtra_y) yface(tx, TY);
+    if (xtra_x) xface(TX, tx);
     __syncthreads();
     if (valid) {
-      const float J = sJ[b][ty + 2][tx + 2], Hx = sHx[b][ty + 2][tx + 2], Hy = sHy[b][ty + 2][tx + 2];
-      float fxc = sfx[b][ty + 2][tx + 2], fyc = sfy[b][ty + 2][tx + 2];
+      const float4 qs = sq[b][ty + 2][tx + 2];
+      const float J = qs.x, Hx = sHx[b][ty + 2][tx + 2], Hy = sHy[b][ty + 2][tx + 2];
+      float fxc = qs.y, fyc = qs.z;
       cap_unit_f32(fxc, fyc);
       float Dxx, Dxy, Dyy;
       closure_f32(fxc, fyc, Dxx, Dxy, Dyy);
@@ -670,8 +676,11 @@ __global__ void __launch_bounds__(kTileX* kTileY) transport_kernel_f32(DeviceVie
       }
       const I kap = rho_c * kabs + pd_c * aH;
       const I aF = aH + rho_c * kF;
-      // j_k = L w_k / (4 pi dx^3 dnu_k), formed in FP64 (outside the FP32 range)
-      const I js = (lum_d != 0.0) ? I(lum_d * v.t_gem[k]) : I(0);
+      I js;
+      if constexpr (sizeof(I) == 8)
+        js = src ? lum_d * v.t_gem[k] : 0.0;
+      else
+        js = src ? jsc * tG[k] : 0.0f;
       I J2, Hx2, Hy2;
       if constexpr (sizeof(I) == 8) {
         J2 = (I(J1) + cdt * js) / (I(1) + cdt * kap);
@@ -688,21 +697,27 @@ __global__ void __launch_bounds__(kTileX* kTileY) transport_kernel_f32(DeviceVie
       Jout[o] = float(J2);
       Hxout[o] = float(Hx2);
       Hyout[o] = float(Hy2);
-      ax = ax + dnu * (I(Hx1) - Hx2);
-      ay = ay + dnu * (I(Hy1) - Hy2);
+      ax += dnu * (I(Hx1) - Hx2);
+      ay += dnu * (I(Hy1) - Hy2);
       // A7 bookkeeping (energy units applied once per substep)
-      if (lum_d != 0.0) em.add(dnu * (cdt * js));
-      ab.add(dnu * (cdt * (kap * J2)));
-      wk.add(dnu * (cdt * (I(W) * I(inv_c))));
-      en.add(dnu * J2);
+      if (src) em += dnu * (cdt * js);
+      ab += dnu * (cdt * (kap * J2));
+      wk += dnu * (cdt * (I(W) * I(inv_c)));
+      en += dnu * J2;
       const float j2f = float(J2), h2 = float(Hx2) * float(Hx2) + float(Hy2) * float(Hy2);
       const float jj = j2f * j2f;
-      if (j2f > 1e-18f) mxf2 = fmaxf(mxf2, fdiv(h2, jj));
-      if (h2 > jj * 1.000002f && h2 > 0.0f) bad += 1.0;
-      if (gx == 0) out.add(dnu * (cdx * -I(xJ[ty][tx])));
-      if (gx == nx - 1) out.add(dnu * (cdx * I(xJ[ty][tx + 1])));
-      if (gy == 0) out.add(dnu * (cdx * -I(yJ[ty][tx])));
-      if (gy == ny - 1) out.add(dnu * (cdx * I(yJ[ty + 1][tx])));
+      if (j2f > 1e-18f) {  // |H|/J is only meaningful well above the FP32 range floor
+        mxf2 = fmaxf(mxf2, fdiv(h2, jj));
+        bad += (h2 > jj * 1.000002f) ? 1 : 0;
+      }
+      if (bnd) {
+        I o2 = 0;
+        if (gx == 0) o2 -= I(xJ[ty][tx]);
+        if (gx == nx - 1) o2 += I(xJ[ty][tx + 1]);
+        if (gy == 0) o2 -= I(yJ[ty][tx]);
+        if (gy == ny - 1) o2 += I(yJ[ty + 1][tx]);
+        out += dnu * (cdx * o2);
+      }
     }
   }
   if (valid) {
@@ -712,19 +727,19 @@ __global__ void __launch_bounds__(kTileX* kTileY) transport_kernel_f32(DeviceVie
   const int blk = blockIdx.y * gridDim.x + blockIdx.x;
   double* part = v.partT + static_cast<long long>(blk) * kDiagSlots;
   double s;
-  s = block_sum<NT>(em.value(), red);
+  s = block_sum<NT>(double(em), red);
   if (tid == 0) part[kSlotEmitted] = s;
-  s = block_sum<NT>(ab.value(), red);
+  s = block_sum<NT>(double(ab), red);
   if (tid == 0) part[kSlotAbsorbed] = s;
-  s = block_sum<NT>(out.value(), red);
+  s = block_sum<NT>(double(out), red);
   if (tid == 0) part[kSlotOutflow] = s;
-  s = block_sum<NT>(wk.value(), red);
+  s = block_sum<NT>(double(wk), red);
   if (tid == 0) part[kSlotWork] = s;
-  s = block_sum<NT>(en.value(), red);
+  s = block_sum<NT>(double(en), red);
   if (tid == 0) part[kSlotEnergy] = s;
   s = block_max<NT>(sqrt(double(mxf2)), red);
   if (tid == 0) part[kSlotMaxF] = s;
-  s = block_sum<NT>(bad, red);
+  s = block_sum<NT>(double(bad), red);
   if (tid == 0) part[kSlotBad] = s;
 }
 
@@ -811,7 +826,7 @@ __global__ void __launch_bounds__(kFreqThreads) freq_kernel(DeviceView v) {
   const long long cell = static_cast<long long>(blockIdx.x) * NT + threadIdx.x;
   RSum<I> en;
   I mxf = 0;
-  double bad = 0;
+  int bad = 0;
   if (cell < nc) {
     const double alpha = v.alpha[cell];
     if (v.freq_step && alpha > 0.0) {
@@ -826,14 +841,26 @@ __global__ void __launch_bounds__(kFreqThreads) freq_kernel(DeviceView v) {
       freq_coef<P>(F(Jin[cell]), F(Hxin[cell]), F(Hyin[cell]), Kc, gxx, gyy, gsh, tH, tR, tn, th,
                    0, P0, a0, e0);
       I qprev = 0, gprev = 0, Bprev = 0, Aprev = 0;
+      // two-deep software pipeline: (nJ, nX, nY) hold bin k+1, loads for k+2 are in flight
+      S nJ = S(0), nX = S(0), nY = S(0);
+      if (nb > 1) {
+        const long long o1 = nc + cell;
+        nJ = Jin[o1];
+        nX = Hxin[o1];
+        nY = Hyin[o1];
+      }
       for (int k = 0; k < nb; ++k) {
         I A = 0, B = 0;
         if (k + 1 < nb) {
-          const long long o1 = static_cast<long long>(k + 1) * nc + cell;
-          const S Jr = Jin[o1];
+          const S Jr = nJ, Xr = nX, Yr = nY;
+          if (k + 2 < nb) {
+            const long long o2 = static_cast<long long>(k + 2) * nc + cell;
+            nJ = Jin[o2];
+            nX = Hxin[o2];
+            nY = Hyin[o2];
+          }
           Jin1 = I(Jr);
-          freq_coef<P>(F(Jr), F(Hxin[o1]), F(Hyin[o1]), Kc, gxx, gyy, gsh, tH, tR, tn, th, k + 1,
-                       P1, a1, e1);
+          freq_coef<P>(F(Jr), F(Xr), F(Yr), Kc, gxx, gyy, gsh, tH, tR, tn, th, k + 1, P1, a1, e1);
           const F d1 = (-P0 > F(0)) ? -P0 : F(0);
           const F d2 = (P1 > F(0)) ? P1 : F(0);
           const F m = (d1 > d2) ? d1 : d2;
@@ -876,26 +903,41 @@ __global__ void __launch_bounds__(kFreqThreads) freq_kernel(DeviceView v) {
         Jin0 = Jin1;
       }
       I Jnext = 0;
+      long long o = static_cast<long long>(nb - 1) * nc + cell;
+      S cg = Jout[o], ch = Hxout[o], cJ = Jin[o], cX = Hxin[o], cY = Hyin[o];
       for (int k = nb - 1; k >= 0; --k) {
-        const long long o = static_cast<long long>(k) * nc + cell;
-        const I g = I(Jout[o]), h = I(Hxout[o]);
+        const S gS = cg, hS = ch, JS = cJ, XS = cX, YS = cY;
+        const long long oc = o;
+        if (k > 0) {  // prefetch bin k-1
+          o -= nc;
+          cg = Jout[o];
+          ch = Hxout[o];
+          cJ = Jin[o];
+          cX = Hxin[o];
+          cY = Hyin[o];
+        }
+        const I g = I(gS), h = I(hS);
         const I Jn = (k == nb - 1) ? g : g + h * Jnext;
         Jnext = Jn;
-        const I Jo = I(Jin[o]);
+        const I Jo = I(JS);
         I ratio;
         if constexpr (sizeof(I) == 4)
           ratio = (Jo > kTinyJ) ? fdiv(Jn, Jo) : 0.0f;
         else
           ratio = (Jo > I(0)) ? Jn / Jo : I(0);
-        const I Hx2 = ratio * I(Hxin[o]);
-        const I Hy2 = ratio * I(Hyin[o]);
-        Jout[o] = S(Jn);
-        Hxout[o] = S(Hx2);
-        Hyout[o] = S(Hy2);
+        const I Hx2 = ratio * I(XS);
+        const I Hy2 = ratio * I(YS);
+        Jout[oc] = S(Jn);
+        Hxout[oc] = S(Hx2);
+        Hyout[oc] = S(Hy2);
         en.add(tdi[k] * Jn);
-        const I hn = sqrt(Hx2 * Hx2 + Hy2 * Hy2);
-        if (Jn > I(0)) mxf = fmax(mxf, hn / Jn);
-        if (hn > Jn * I(1.000001) && hn > I(0)) bad += 1.0;
+        // |H|/J is only meaningful above the FP32 tiny-J threshold
+        const I jmin = (sizeof(I) == 4) ? I(kTinyJ) : I(0);
+        if (Jn > jmin) {
+          const I hn = sqrt(Hx2 * Hx2 + Hy2 * Hy2);
+          mxf = fmax(mxf, hn / Jn);
+          bad += (hn > Jn * I(1.000001)) ? 1 : 0;
+        }
       }
     } else {
       for (int k = 0; k < nb; ++k) {
@@ -906,9 +948,12 @@ __global__ void __launch_bounds__(kFreqThreads) freq_kernel(DeviceView v) {
         Hyout[o] = Hy;
         const I Ji = I(J), Hxi = I(Hx), Hyi = I(Hy);
         en.add(tdi[k] * Ji);
-        const I hn = sqrt(Hxi * Hxi + Hyi * Hyi);
-        if (Ji > I(0)) mxf = fmax(mxf, hn / Ji);
-        if (hn > Ji * I(1.000001) && hn > I(0)) bad += 1.0;
+        const I jmin = (sizeof(I) == 4) ? I(kTinyJ) : I(0);
+        if (Ji > jmin) {
+          const I hn = sqrt(Hxi * Hxi + Hyi * Hyi);
+          mxf = fmax(mxf, hn / Ji);
+          bad += (hn > Ji * I(1.000001)) ? 1 : 0;
+        }
       }
     }
   }
@@ -918,7 +963,7 @@ __global__ void __launch_bounds__(kFreqThreads) freq_kernel(DeviceView v) {
   if (threadIdx.x == 0) part[kSlotEnergy] = s;
   s = block_max<NT>(double(mxf), red);
   if (threadIdx.x == 0) part[kSlotMaxF] = s;
-  s = block_sum<NT>(bad, red);
+  s = block_sum<NT>(double(bad), red);
   if (threadIdx.x == 0) part[kSlotBad] = s;
 }
 
@@ -926,7 +971,7 @@ template <class P>
 int launch_transport_t(const DeviceView& v, cudaStream_t st) {
   dim3 grid((v.nx + kTileX - 1) / kTileX, (v.ny + kTileY - 1) / kTileY);
   if constexpr (sizeof(typename P::S) == 4) {
-    const size_t smem = sizeof(float) * 2 * static_cast<size_t>(v.nb);
+    const size_t smem = sizeof(float) * 3 * static_cast<size_t>(v.nb);
     transport_kernel_f32<P><<<grid, dim3(kTileX, kTileY), smem, st>>>(v);
   } else {
     transport_kernel<P><<<grid, dim3(kTileX, kTileY), 0, st>>>(v);
