@@ -92,6 +92,7 @@ struct DeviceView {
   double* partF = nullptr;  // frequency-kernel block partials [blocks][kDiagSlots]
   // scalars
   double kabs = 0, kF = 0, Kc = 0, cdt = 0, fcoef = 0;
+  double gem_max = 1;  // max_k gem_k (FP32 emissivity scaling)
   int freq_step = 0;
 };
 
