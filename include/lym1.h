@@ -47,6 +47,7 @@ extern "C" {
 #define LYM1_ETIMEOUT (-5)       /* a bounded device wait expired */
 #define LYM1_ENOTCONVERGED (-6)  /* substep cap reached before the steady-state test passed */
 #define LYM1_ENODEVICE (-7)      /* no CUDA device is usable */
+#define LYM1_ERANGE (-8)         /* size beyond the fixed maximum of an allocation-free call */
 
 /* Arithmetic of the substep. */
 #define LYM1_FP64_DET 0    /* FP64, fixed operation order, no FMA contraction, own exp/expm1 */
@@ -221,6 +222,37 @@ typedef struct {
  */
 int lym1_profile_enable(lym1_ctx *ctx, int on);
 int lym1_profile_read(lym1_ctx *ctx, lym1_profile *out, int reset);
+
+/*
+ * Allocation-free energy of a caller-owned state.  The paper has no
+ * counterpart: this is a service for callers that cannot allocate device
+ * memory when they need the number -- for instance a host code whose device
+ * memory is owned by another runtime's allocator, a real-time loop that
+ * forbids allocation, or work recorded into a CUDA graph.
+ *
+ * Returns in *e_out (host or device pointer) the Lya energy in erg,
+ * (4 pi / c) dx^3 sum_cells sum_k dnu_k J_k, of J[nb][nc] (FP64, device
+ * pointer) with bin widths dnu[nb] (host pointer, Hz), using the same
+ * reduction order as the energy in lym1_diagnostics.  Runs on cuda_stream
+ * (NULL = legacy default stream) and synchronises it before returning.
+ *
+ * Memory: calls no cudaMalloc/cudaFree and no allocating library routine.
+ * Its partial sums live in one file-scope device array of
+ * (LYM1_NOALLOC_MAX_CELLS / 128 + 1) doubles (1 MiB), which every GPU that
+ * loads the library holds until the process exits.  The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress) with
+ * the device current; make the first call on each device before any stream
+ * capture.  All calls share the array and it keeps the last call's contents:
+ * calls that overlap on the GPU (other streams, other host threads) race and
+ * must be serialised by the caller.
+ * Errors: LYM1_EINVAL for null pointers, nb or nc < 1, dx_cm <= 0;
+ * LYM1_ERANGE for nb > LYM1_NOALLOC_MAX_BINS or nc > LYM1_NOALLOC_MAX_CELLS;
+ * LYM1_ECUDA if a launch or copy fails.
+ */
+#define LYM1_NOALLOC_MAX_CELLS (1 << 24) /* 16,777,216 cells, e.g. 4096 x 4096 */
+#define LYM1_NOALLOC_MAX_BINS 1024
+int lym1_energy_noalloc(const double *J, const double *dnu, int nb, long long nc, double dx_cm,
+                        double *e_out, void *cuda_stream);
 
 #ifdef __cplusplus
 }

@@ -5,6 +5,7 @@ Four translation units compiled in parallel, then linked:
   csrc/lym1_api.cu            C ABI host code
   csrc/lym1_kernels_det.cu    FP64 fixed-order kernels (-fmad=false)
   csrc/lym1_kernels_fast.cu   FP64 / mixed kernels
+  csrc/lym1_noalloc.cu        allocation-free energy reduction
 """
 from __future__ import annotations
 
@@ -21,7 +22,8 @@ BUILD = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 
-SOURCES = ["lym1_tables.cpp", "lym1_api.cu", "lym1_kernels_det.cu", "lym1_kernels_fast.cu"]
+SOURCES = ["lym1_tables.cpp", "lym1_api.cu", "lym1_kernels_det.cu", "lym1_kernels_fast.cu",
+           "lym1_noalloc.cu"]
 HEADERS = ["lym1_internal.h", "lym1_kernels.cuh"]
 
 

@@ -269,6 +269,7 @@ const char* lym1_strerror(int s) {
     case LYM1_ETIMEOUT: return "bounded device wait expired";
     case LYM1_ENOTCONVERGED: return "substep cap reached before steady state";
     case LYM1_ENODEVICE: return "no usable CUDA device";
+    case LYM1_ERANGE: return "size beyond the fixed maximum of an allocation-free call";
     default: return "unknown status";
   }
 }

@@ -1,0 +1,118 @@
+// lym1_noalloc.cu -- lym1_energy_noalloc: the domain Lya energy of a
+// caller-owned state, computed without allocating any device memory.
+//
+// Some callers cannot call cudaMalloc at the moment they need this number: a
+// host code whose device memory is owned by another runtime's allocator (a
+// framework that preallocates most of HBM), a real-time loop that forbids
+// allocation, or work being recorded into a CUDA graph.  This entry point
+// runs the same two-stage reduction as the library's own energy bookkeeping,
+// with its per-block partial sums in a file-scope device array of fixed size
+// instead of a context's allocation.
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "lym1.h"
+#include "lym1_kernels.cuh"
+
+namespace lym1 {
+namespace {
+
+constexpr int kNoAllocMaxBlocks = static_cast<int>(
+    (static_cast<long long>(LYM1_NOALLOC_MAX_CELLS) + kFreqThreads - 1) / kFreqThreads);
+
+// Shared scratch: one partial sum per block, then the result.  Every GPU that
+// loads the library holds it (1 MiB + 8 B) until the process exits.  In host
+// code this name is only a stand-in for the device array; kernels get its
+// device address from cudaGetSymbolAddress.
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocMaxBlocks + 1];
+
+struct NoAllocArgs {
+  const double* J;
+  long long nc;
+  int nb;
+  double unit;
+  double dnu[LYM1_NOALLOC_MAX_BINS];
+};
+
+// Stage 1: per-thread sum_k dnu_k J_k, block sums in fixed order (the same
+// partition and order as the library's energy kernel).
+__global__ void __launch_bounds__(kFreqThreads) noalloc_energy_blocks(const NoAllocArgs a,
+                                                                      double* scratch) {
+  __shared__ double red[kFreqThreads / 32];
+  const long long cell = static_cast<long long>(blockIdx.x) * kFreqThreads + threadIdx.x;
+  double en = 0.0;
+  if (cell < a.nc)
+    for (int k = 0; k < a.nb; ++k) en += a.dnu[k] * a.J[static_cast<long long>(k) * a.nc + cell];
+  const double s = block_sum<kFreqThreads>(en, red);
+  if (threadIdx.x == 0) scratch[blockIdx.x] = s;
+}
+
+// Stage 2: one block sums the partials of this call (strided, then in warp
+// order) and stores unit * total after them.  Only slots written by stage 1 of
+// the same call are read, so nothing needs clearing between calls.
+__global__ void __launch_bounds__(256) noalloc_energy_total(int nblocks, double unit,
+                                                            double* scratch) {
+  __shared__ double red[8];
+  double v = 0.0;
+  for (int b = threadIdx.x; b < nblocks; b += 256) v += scratch[b];
+  const double t = block_sum<256>(v, red);
+  if (threadIdx.x == 0) scratch[kNoAllocMaxBlocks] = unit * t;
+}
+
+std::mutex g_setup_mutex;
+double* g_scratch_ptr[256] = {};
+
+// Device address of the scratch array for the current device, looked up once
+// per device with that device current.
+int scratch_for_current_device(double** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) {
+    cudaGetLastError();
+    return LYM1_ENODEVICE;
+  }
+  std::lock_guard<std::mutex> lock(g_setup_mutex);
+  if (!g_scratch_ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+      cudaGetLastError();
+      return LYM1_ECUDA;
+    }
+    g_scratch_ptr[dev] = static_cast<double*>(p);
+  }
+  *out = g_scratch_ptr[dev];
+  return LYM1_OK;
+}
+
+}  // namespace
+}  // namespace lym1
+
+extern "C" int lym1_energy_noalloc(const double* J, const double* dnu, int nb, long long nc,
+                                   double dx_cm, double* e_out, void* cuda_stream) {
+  using namespace lym1;
+  if (!J || !dnu || !e_out || !(dx_cm > 0.0)) return LYM1_EINVAL;
+  if (nb < 1 || nc < 1) return LYM1_EINVAL;
+  if (nb > LYM1_NOALLOC_MAX_BINS || nc > LYM1_NOALLOC_MAX_CELLS) return LYM1_ERANGE;
+  double* scratch = nullptr;
+  const int rc = scratch_for_current_device(&scratch);
+  if (rc != LYM1_OK) return rc;
+  const cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  NoAllocArgs a;
+  a.J = J;
+  a.nc = nc;
+  a.nb = nb;
+  const double V = (dx_cm * dx_cm) * dx_cm;
+  a.unit = ((4.0 * kPi) / kLight) * V;
+  for (int k = 0; k < nb; ++k) a.dnu[k] = dnu[k];
+  const int nblocks = static_cast<int>((nc + kFreqThreads - 1) / kFreqThreads);
+  noalloc_energy_blocks<<<nblocks, kFreqThreads, 0, st>>>(a, scratch);
+  noalloc_energy_total<<<1, 256, 0, st>>>(nblocks, a.unit, scratch);
+  if (cudaGetLastError() != cudaSuccess) return LYM1_ECUDA;
+  if (cudaMemcpyAsync(e_out, scratch + kNoAllocMaxBlocks, sizeof(double), cudaMemcpyDefault, st) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess) {
+    cudaGetLastError();
+    return LYM1_ECUDA;
+  }
+  return LYM1_OK;
+}

@@ -18,6 +18,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "liblym1.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, ENOTCONVERGED, ENODEVICE = 0, -1, -2, -3, -4, -5, -6, -7
+ERANGE = -8
 FP64_DET, FP64, MIXED, MIXED_FAST = 0, 1, 2, 3
 PRECISIONS = {"fp64_det": FP64_DET, "fp64": FP64, "mixed": MIXED, "mixed_fast": MIXED_FAST}
 
@@ -93,6 +94,8 @@ SIGNATURES = {
     "lym1_substeps_batched": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int]),
     "lym1_profile_enable": (C.c_int, [C.c_void_p, C.c_int]),
     "lym1_profile_read": (C.c_int, [C.c_void_p, C.POINTER(lym1_profile), C.c_int]),
+    "lym1_energy_noalloc": (C.c_int, [_PD, _PD, C.c_int, C.c_longlong, C.c_double, _PD,
+                                      C.c_void_p]),
 }
 
 
@@ -289,6 +292,20 @@ class Context:
             return False, n.value
         _check(st, "lym1_run_to_steady")
         return True, n.value
+
+
+def energy_noalloc(J, dnu, dx, stream=None) -> float:
+    """``lym1_energy_noalloc``: Lya energy (erg) of a device state J[nb][ny][nx]
+    (contiguous float64 CUDA tensor) with bin widths dnu (host), for callers that
+    cannot allocate device memory at that point; the call itself allocates nothing."""
+    d = np.ascontiguousarray(dnu, dtype=np.float64)
+    nb = d.size
+    nc = J.numel() // nb
+    out = np.zeros(1)
+    _check(lib().lym1_energy_noalloc(_out_ptr(J), d.ctypes.data_as(_PD), nb, nc, float(dx),
+                                     out.ctypes.data_as(_PD), _stream_handle(stream)),
+           "lym1_energy_noalloc")
+    return float(out[0])
 
 
 def substeps_batched(contexts, n):
