@@ -107,8 +107,10 @@ typedef struct {
   double emitted, absorbed, outflow, work;  /* erg, summed over all substeps since the last reset */
   double residual;        /* e_tot - e_start - (emitted - absorbed - outflow - work), erg */
   double e_start;         /* energy when the counters were last reset, erg */
-  double max_f;           /* max |H|/J over cells and bins after the last substep */
-  double n_unrealisable;  /* (cell, bin) pairs with |H| > J (1 + 1e-6) after the last substep */
+  double max_f;           /* max |H|/J over cells and bins after the last substep (FP32 policies:
+                             over (cell, bin) pairs holding >= 1e-8 of the domain energy) */
+  double n_unrealisable;  /* (cell, bin) pairs with |H| > J (1 + 1e-6) after the last substep,
+                             counted over the same pairs */
   double force_abs;       /* sum |f| dV of the last substep's force, dyn */
   double force_radial;    /* sum f . r_hat dV (r from the box centre), dyn */
   double M_F, M_F_radial; /* force multipliers (Sec. 4 definitions): force / (L_tot / c) */

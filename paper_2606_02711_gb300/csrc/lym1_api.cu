@@ -138,6 +138,7 @@ DeviceView make_view(const lym1_ctx* c, double dt) {
   v.fcoef = (4.0 * kPi) / ((kLight * c->c_tilde) * dt);
   v.freq_step = c->freq_step;
   v.gem_max = c->gem_max;
+  v.acc = c->acc;
   return v;
 }
 

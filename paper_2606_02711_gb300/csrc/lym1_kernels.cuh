@@ -440,6 +440,9 @@ __device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b
 // reciprocal flushes subnormal inputs, and such J are ~1e-30 of any field's
 // scale (the far wings of the line far from the sources).
 constexpr float kTinyJ = 1e-30f;
+// share of the domain energy above which a (cell, bin) pair enters the FP32
+// realisability diagnostics
+constexpr double kActiveShare = 1e-8;
 
 // Levermore closure in the cancellation-free FP32 form (see closure()).
 __device__ __forceinline__ void closure_f32(float fn, float ft, float& Dnn, float& Dnt, float& Dtt) {
@@ -525,10 +528,11 @@ __global__ void __launch_bounds__(kTileX* kTileY, 3) transport_kernel_f32(Device
   __shared__ float xJ[TY][TX + 1], xN[TY][TX + 1], xT[TY][TX + 1];
   __shared__ float yJ[TY + 1][TX], yN[TY + 1][TX], yT[TY + 1][TX];
   __shared__ double red[NT / 32];
-  extern __shared__ float tabf[];  // <H>_k, dnu_k, gem_k / gem_max as FP32 (3 nb)
+  extern __shared__ float tabf[];  // <H>_k, dnu_k, gem_k / gem_max, J_act,k as FP32 (4 nb)
   float* tH = tabf;
   float* tD = tabf + v.nb;
   float* tG = tabf + 2 * v.nb;
+  float* tA = tabf + 3 * v.nb;
 
   const float* __restrict__ Jin = static_cast<const float*>(v.J);
   const float* __restrict__ Hxin = static_cast<const float*>(v.Hx);
@@ -546,10 +550,16 @@ __global__ void __launch_bounds__(kTileX* kTileY, 3) transport_kernel_f32(Device
   const long long cell = valid ? static_cast<long long>(gy) * nx + gx : 0;
   const float inv_c = 1.0f / float(kLight);
 
+  // realisability is checked on (cell, bin) pairs holding at least kActiveShare
+  // of the domain energy of the previous substep (FP32 rounding makes |H|/J
+  // meaningless far below a bin plane's scale)
+  const double e_prev = v.acc[8], e_unit = v.acc[13];
   for (int i = tid; i < nb; i += NT) {
     tH[i] = float(v.t_H[i]);
     tD[i] = float(v.t_dnu[i]);
     tG[i] = float(v.t_gem[i] / v.gem_max);
+    const double ja = kActiveShare * e_prev / (e_unit * v.t_dnu[i]);
+    tA[i] = float(fmax(fmin(ja, 1e30), 1e-30));
   }
   for (int idx = tid; idx < QX * QY; idx += NT) {
     const int lx = idx % QX, ly = idx / QX;
@@ -706,7 +716,7 @@ __global__ void __launch_bounds__(kTileX* kTileY, 3) transport_kernel_f32(Device
       en += dnu * J2;
       const float j2f = float(J2), h2 = float(Hx2) * float(Hx2) + float(Hy2) * float(Hy2);
       const float jj = j2f * j2f;
-      if (j2f > 1e-18f) {  // |H|/J is only meaningful well above the FP32 range floor
+      if (j2f > tA[k]) {
         mxf2 = fmaxf(mxf2, fdiv(h2, jj));
         bad += (h2 > jj * 1.000002f) ? 1 : 0;
       }
@@ -806,7 +816,15 @@ __global__ void __launch_bounds__(kFreqThreads) freq_kernel(DeviceView v) {
   T* th = tabs + 3 * nb;
   T* td = tabs + 4 * nb;
   I* tdi = reinterpret_cast<I*>(tabs_raw + 5 * nb);  // dnu_k in the elimination type
+  I* tact = reinterpret_cast<I*>(tabs_raw + 6 * nb);  // J above which |H|/J is checked
+  const double e_prev = v.acc[8], e_unit = v.acc[13];
   for (int i = threadIdx.x; i < nb; i += NT) {
+    if constexpr (sizeof(F) == 4) {
+      const double ja = kActiveShare * e_prev / (e_unit * v.t_dnu[i]);
+      tact[i] = I(fmax(fmin(ja, 1e30), 1e-30));
+    } else {
+      tact[i] = I(0);
+    }
     tH[i] = T(v.t_H[i]);
     tR[i] = T(v.t_R[i]);
     tn[i] = T(v.t_nbc[i]);
@@ -931,9 +949,7 @@ __global__ void __launch_bounds__(kFreqThreads) freq_kernel(DeviceView v) {
         Hxout[oc] = S(Hx2);
         Hyout[oc] = S(Hy2);
         en.add(tdi[k] * Jn);
-        // |H|/J is only meaningful above the FP32 tiny-J threshold
-        const I jmin = (sizeof(I) == 4) ? I(kTinyJ) : I(0);
-        if (Jn > jmin) {
+        if (Jn > tact[k]) {
           const I hn = sqrt(Hx2 * Hx2 + Hy2 * Hy2);
           mxf = fmax(mxf, hn / Jn);
           bad += (hn > Jn * I(1.000001)) ? 1 : 0;
@@ -948,8 +964,7 @@ __global__ void __launch_bounds__(kFreqThreads) freq_kernel(DeviceView v) {
         Hyout[o] = Hy;
         const I Ji = I(J), Hxi = I(Hx), Hyi = I(Hy);
         en.add(tdi[k] * Ji);
-        const I jmin = (sizeof(I) == 4) ? I(kTinyJ) : I(0);
-        if (Ji > jmin) {
+        if (Ji > tact[k]) {
           const I hn = sqrt(Hxi * Hxi + Hyi * Hyi);
           mxf = fmax(mxf, hn / Ji);
           bad += (hn > Ji * I(1.000001)) ? 1 : 0;
@@ -971,7 +986,7 @@ template <class P>
 int launch_transport_t(const DeviceView& v, cudaStream_t st) {
   dim3 grid((v.nx + kTileX - 1) / kTileX, (v.ny + kTileY - 1) / kTileY);
   if constexpr (sizeof(typename P::S) == 4) {
-    const size_t smem = sizeof(float) * 3 * static_cast<size_t>(v.nb);
+    const size_t smem = sizeof(float) * 4 * static_cast<size_t>(v.nb);
     transport_kernel_f32<P><<<grid, dim3(kTileX, kTileY), smem, st>>>(v);
   } else {
     transport_kernel<P><<<grid, dim3(kTileX, kTileY), 0, st>>>(v);
@@ -981,7 +996,7 @@ int launch_transport_t(const DeviceView& v, cudaStream_t st) {
 
 template <class P>
 int launch_freq_t(const DeviceView& v, cudaStream_t st) {
-  const size_t smem = sizeof(double) * 6 * static_cast<size_t>(v.nb);
+  const size_t smem = sizeof(double) * 7 * static_cast<size_t>(v.nb);
   freq_kernel<P><<<freq_blocks(v.nc), kFreqThreads, smem, st>>>(v);
   return static_cast<int>(cudaGetLastError());
 }
