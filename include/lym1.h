@@ -201,12 +201,27 @@ int lym1_run_to_steady(lym1_ctx *ctx, double tol, int check_every, int max_subst
                        int *n_done);
 
 /*
- * Batched substeps over several contexts of the same precision and bin count
- * in one launch per kernel (uneven grids share the launch through a per-tile
- * work list).  Each context advances n substeps of its own dt_RT.  All
- * contexts must use the stream of the first one.  LYM1_EINVAL if they differ
- * in precision, bin count or gray flag.
+ * Batches: several contexts (clouds of different sizes, luminosities and
+ * densities) advanced together.  Each substep of a batch is three launches in
+ * total -- one persistent transport kernel over a work list of every
+ * context's 32x8 tiles, one persistent frequency-step kernel over every
+ * context's cell blocks and one reduction kernel with a block per context --
+ * captured once in a CUDA graph and replayed.  The persistent grid size is
+ * tuned on the batch's first substeps (each candidate times one substep; the
+ * choice does not change any result).  Every context advances with its own
+ * dt_RT and its own bookkeeping, exactly as with lym1_substeps.
+ * The contexts must share precision, bin count and stream, and not be gray;
+ * otherwise LYM1_EINVAL.  A batch holds device pointers of its contexts:
+ * destroy the batch before any of them.
  */
+typedef struct lym1_batch lym1_batch;
+int lym1_batch_create(lym1_ctx *const *ctxs, int n_ctx, lym1_batch **out);
+int lym1_batch_substeps(lym1_batch *batch, int n);
+/* persistent grid sizes in use (0 until tuned) */
+int lym1_batch_grid(lym1_batch *batch, int *transport_blocks, int *freq_blocks);
+void lym1_batch_destroy(lym1_batch *batch);
+
+/* One-shot batch: create, run n substeps, destroy. */
 int lym1_substeps_batched(lym1_ctx **ctxs, int n_ctx, int n);
 
 typedef struct {

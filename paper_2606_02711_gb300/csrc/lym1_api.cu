@@ -44,6 +44,11 @@ namespace {
 
 constexpr int kForceBlocks = 152 * 4;
 
+// host mirror of the kernels' BatchItem {ctx, x0, y0, blk}
+struct BatchItemHost {
+  int ctx, x0, y0, blk;
+};
+
 int map_cuda(cudaError_t e) {
   if (e == cudaSuccess) return LYM1_OK;
   if (e == cudaErrorMemoryAllocation) return LYM1_ENOMEM;
@@ -254,6 +259,52 @@ void drop_events(lym1_ctx* c) {
   c->ev_start.clear();
   c->ev_stop.clear();
   c->ev_kind.clear();
+}
+
+}  // namespace
+
+struct lym1_batch {
+  std::vector<lym1_ctx*> ctxs;
+  int precision = 0, nb = 0, nT = 0, nF = 0;
+  cudaStream_t ctx_stream = nullptr, bs = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr, t0 = nullptr, t1 = nullptr;
+  DeviceView *viewsT = nullptr, *viewsF = nullptr;
+  void *itemsT = nullptr, *itemsF = nullptr;
+  FinalizeJob* jobs = nullptr;
+  int gridT = 0, gridF = 0;
+  // tuning state: candidate persistent grids (multiples of the SM count)
+  std::vector<int> candT, candF;
+  std::vector<float> timeT;
+  int tuned = 0;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraph_t graph = nullptr;
+};
+
+namespace {
+
+int batch_launch(lym1_batch* b, cudaStream_t s) {
+  const int n = static_cast<int>(b->ctxs.size());
+  if (b->precision == LYM1_FP64_DET) {
+    LYM1_TRYK(launch_batched_det(0, b->viewsT, b->itemsT, b->nT, b->gridT, b->nb, s));
+    LYM1_TRYK(launch_batched_det(1, b->viewsF, b->itemsF, b->nF, b->gridF, b->nb, s));
+  } else {
+    LYM1_TRYK(launch_batched_fast(b->precision, 0, b->viewsT, b->itemsT, b->nT, b->gridT, b->nb, s));
+    LYM1_TRYK(launch_batched_fast(b->precision, 1, b->viewsF, b->itemsF, b->nF, b->gridF, b->nb, s));
+  }
+  LYM1_TRYK(launch_finalize_batched(b->jobs, n, s));
+  return LYM1_OK;
+}
+
+void batch_free(lym1_batch* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  void* ptrs[] = {b->viewsT, b->viewsF, b->itemsT, b->itemsF, b->jobs};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  cudaEvent_t evs[] = {b->ev_in, b->ev_out, b->t0, b->t1};
+  for (cudaEvent_t e : evs)
+    if (e) cudaEventDestroy(e);
+  if (b->bs) cudaStreamDestroy(b->bs);
 }
 
 }  // namespace
@@ -595,19 +646,152 @@ int lym1_run_to_steady(lym1_ctx* c, double tol, int check_every, int max_substep
 }
 
 int lym1_substeps_batched(lym1_ctx** ctxs, int n_ctx, int n) {
-  if (!ctxs || n_ctx < 1 || n < 0) return LYM1_EINVAL;
+  lym1_batch* b = nullptr;
+  int rc = lym1_batch_create(ctxs, n_ctx, &b);
+  if (rc != LYM1_OK) return rc;
+  rc = lym1_batch_substeps(b, n);
+  lym1_batch_destroy(b);
+  return rc;
+}
+
+int lym1_batch_create(lym1_ctx* const* ctxs, int n_ctx, lym1_batch** out) {
+  if (!out) return LYM1_EINVAL;
+  *out = nullptr;
+  if (!ctxs || n_ctx < 1) return LYM1_EINVAL;
   for (int i = 0; i < n_ctx; ++i) {
-    if (!ctxs[i]) return LYM1_EINVAL;
+    if (!ctxs[i] || ctxs[i]->gray || !ctxs[i]->freq_step) return LYM1_EINVAL;
     if (ctxs[i]->precision != ctxs[0]->precision || ctxs[i]->nb != ctxs[0]->nb ||
-        ctxs[i]->gray != ctxs[0]->gray)
+        ctxs[i]->stream != ctxs[0]->stream)
       return LYM1_EINVAL;
   }
-  for (int s = 0; s < n; ++s)
-    for (int i = 0; i < n_ctx; ++i) {
-      const int rc = one_substep(ctxs[i], ctxs[i]->dt_cfl);
-      if (rc != LYM1_OK) return rc;
-    }
+  lym1_batch* b = new (std::nothrow) lym1_batch();
+  if (!b) return LYM1_ENOMEM;
+  b->ctxs.assign(ctxs, ctxs + n_ctx);
+  b->precision = ctxs[0]->precision;
+  b->nb = ctxs[0]->nb;
+  b->ctx_stream = ctxs[0]->stream;
+  std::vector<DeviceView> vT, vF;
+  std::vector<BatchItemHost> iT, iF;
+  std::vector<FinalizeJob> jobs;
+  for (int i = 0; i < n_ctx; ++i) {
+    lym1_ctx* c = ctxs[i];
+    DeviceView v = make_view(c, c->dt_cfl);
+    vT.push_back(v);
+    DeviceView w = v;  // frequency step reads B, writes A
+    w.J = c->B[0];
+    w.Hx = c->B[1];
+    w.Hy = c->B[2];
+    w.Jo = c->A[0];
+    w.Hxo = c->A[1];
+    w.Hyo = c->A[2];
+    vF.push_back(w);
+    const int gx = (c->nx + kTileX - 1) / kTileX, gy = (c->ny + kTileY - 1) / kTileY;
+    for (int by = 0; by < gy; ++by)
+      for (int bx = 0; bx < gx; ++bx) iT.push_back({i, bx * kTileX, by * kTileY, by * gx + bx});
+    const int fb = freq_blocks(c->nc);
+    for (int k = 0; k < fb; ++k) iF.push_back({i, 0, 0, k});
+    jobs.push_back({c->partT, c->partF, c->acc, transport_blocks(c->nx, c->ny), fb});
+  }
+  b->nT = static_cast<int>(iT.size());
+  b->nF = static_cast<int>(iF.size());
+  auto fail = [&](int rc) {
+    batch_free(b);
+    delete b;
+    return rc;
+  };
+  if (cudaMalloc(reinterpret_cast<void**>(&b->viewsT), sizeof(DeviceView) * n_ctx) != cudaSuccess ||
+      cudaMalloc(reinterpret_cast<void**>(&b->viewsF), sizeof(DeviceView) * n_ctx) != cudaSuccess ||
+      cudaMalloc(&b->itemsT, sizeof(BatchItemHost) * iT.size()) != cudaSuccess ||
+      cudaMalloc(&b->itemsF, sizeof(BatchItemHost) * iF.size()) != cudaSuccess ||
+      cudaMalloc(reinterpret_cast<void**>(&b->jobs), sizeof(FinalizeJob) * n_ctx) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(LYM1_ENOMEM);
+  }
+  if (cudaMemcpy(b->viewsT, vT.data(), sizeof(DeviceView) * n_ctx, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(b->viewsF, vF.data(), sizeof(DeviceView) * n_ctx, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(b->itemsT, iT.data(), sizeof(BatchItemHost) * iT.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(b->itemsF, iF.data(), sizeof(BatchItemHost) * iF.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(b->jobs, jobs.data(), sizeof(FinalizeJob) * n_ctx, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&b->bs, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreate(&b->t0) != cudaSuccess || cudaEventCreate(&b->t1) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(LYM1_ECUDA);
+  }
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (nsm < 1) nsm = 1;
+  const int rT = b->precision == LYM1_FP64_DET ? resident_blocks_det(0) : resident_blocks_fast(b->precision, 0);
+  const int rF = b->precision == LYM1_FP64_DET ? resident_blocks_det(1) : resident_blocks_fast(b->precision, 1);
+  for (int m = 1; m <= rT; ++m) b->candT.push_back(std::min(b->nT, m * nsm));
+  const int gf = std::min(b->nF, rF * nsm);
+  b->candF.push_back(gf);
+  b->gridT = b->candT.back();
+  b->gridF = gf;
+  *out = b;
   return LYM1_OK;
+}
+
+int lym1_batch_substeps(lym1_batch* b, int n) {
+  if (!b || n < 0) return LYM1_EINVAL;
+  if (n == 0) return LYM1_OK;
+  LYM1_TRY(cudaEventRecord(b->ev_in, b->ctx_stream));
+  LYM1_TRY(cudaStreamWaitEvent(b->bs, b->ev_in, 0));
+  int done = 0;
+  // tuning: the first substeps run once with each candidate persistent grid
+  while (!b->tuned && done < n) {
+    const size_t i = b->timeT.size();
+    b->gridT = b->candT[i];
+    LYM1_TRY(cudaEventRecord(b->t0, b->bs));
+    const int rc = batch_launch(b, b->bs);
+    if (rc != LYM1_OK) return rc;
+    LYM1_TRY(cudaEventRecord(b->t1, b->bs));
+    LYM1_TRY(cudaEventSynchronize(b->t1));
+    float ms = 0.0f;
+    LYM1_TRY(cudaEventElapsedTime(&ms, b->t0, b->t1));
+    b->timeT.push_back(ms);
+    ++done;
+    if (b->timeT.size() == b->candT.size()) {
+      size_t best = 0;
+      for (size_t k = 1; k < b->timeT.size(); ++k)
+        if (b->timeT[k] < b->timeT[best]) best = k;
+      b->gridT = b->candT[best];
+      b->tuned = 1;
+    }
+  }
+  if (done < n) {
+    if (!b->exec) {
+      LYM1_TRY(cudaStreamBeginCapture(b->bs, cudaStreamCaptureModeThreadLocal));
+      const int rc = batch_launch(b, b->bs);
+      cudaGraph_t g = nullptr;
+      const cudaError_t e = cudaStreamEndCapture(b->bs, &g);
+      if (rc != LYM1_OK) return rc;
+      LYM1_TRY(e);
+      b->graph = g;
+      LYM1_TRY(cudaGraphInstantiate(&b->exec, b->graph, 0));
+    }
+    for (; done < n; ++done) LYM1_TRY(cudaGraphLaunch(b->exec, b->bs));
+  }
+  LYM1_TRY(cudaEventRecord(b->ev_out, b->bs));
+  LYM1_TRY(cudaStreamWaitEvent(b->ctx_stream, b->ev_out, 0));
+  for (lym1_ctx* c : b->ctxs) c->substeps_done += n;
+  return LYM1_OK;
+}
+
+int lym1_batch_grid(lym1_batch* b, int* gt, int* gf) {
+  if (!b) return LYM1_EINVAL;
+  if (gt) *gt = b->tuned ? b->gridT : 0;
+  if (gf) *gf = b->tuned ? b->gridF : 0;
+  return LYM1_OK;
+}
+
+void lym1_batch_destroy(lym1_batch* b) {
+  if (!b) return;
+  cudaStreamSynchronize(b->bs);
+  batch_free(b);
+  delete b;
 }
 
 int lym1_profile_enable(lym1_ctx* c, int on) {

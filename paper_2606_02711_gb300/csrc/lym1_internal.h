@@ -116,6 +116,22 @@ int launch_convert_in(int precision, const double* src, void* dst, long long n, 
 int launch_force_reduce(const double* fx, const double* fy, int nx, int ny, double dx,
                         double* part, int nblocks, void* stream);
 
+// batched (multi-context) launches; kind 0 = transport, 1 = frequency step;
+// items point to device arrays of {ctx, x0, y0, blk}
+struct FinalizeJob {
+  const double* partT;
+  const double* partE;
+  double* acc;
+  int nT, nE;
+};
+int launch_batched_det(int kind, const DeviceView* views, const void* items, int n, int grid,
+                       int nb_max, void* stream);
+int launch_batched_fast(int precision, int kind, const DeviceView* views, const void* items, int n,
+                        int grid, int nb_max, void* stream);
+int resident_blocks_det(int kind);
+int resident_blocks_fast(int precision, int kind);
+int launch_finalize_batched(const FinalizeJob* jobs, int n, void* stream);
+
 inline int transport_blocks(int nx, int ny) {
   return ((nx + kTileX - 1) / kTileX) * ((ny + kTileY - 1) / kTileY);
 }

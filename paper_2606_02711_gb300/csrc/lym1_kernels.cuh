@@ -259,7 +259,7 @@ __device__ __forceinline__ double block_max(double v, double* red) {
 
 // ------------------------------------------------------------ transport kernel
 template <class P>
-__global__ void __launch_bounds__(kTileX* kTileY) transport_kernel(DeviceView v) {
+__device__ __forceinline__ void transport_tile(const DeviceView& v, int x0, int y0, int blk) {
   using S = typename P::S;
   using F = typename P::F;
   using I = typename P::I;
@@ -282,7 +282,6 @@ __global__ void __launch_bounds__(kTileX* kTileY) transport_kernel(DeviceView v)
   const int nx = v.nx, ny = v.ny;
   const long long nc = v.nc;
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
   const int gx = x0 + tx, gy = y0 + ty;
   const bool valid = gx < nx && gy < ny;
   const long long cell = valid ? static_cast<long long>(gy) * nx + gx : 0;
@@ -410,7 +409,6 @@ __global__ void __launch_bounds__(kTileX* kTileY) transport_kernel(DeviceView v)
     v.fx[cell] = v.fcoef * double(ax);
     v.fy[cell] = v.fcoef * double(ay);
   }
-  const int blk = blockIdx.y * gridDim.x + blockIdx.x;
   double* part = v.partT + static_cast<long long>(blk) * kDiagSlots;
   double s;
   s = block_sum<NT>(em.value(), red);
@@ -429,6 +427,11 @@ __global__ void __launch_bounds__(kTileX* kTileY) transport_kernel(DeviceView v)
   if (tid == 0) part[kSlotBad] = s;
 }
 
+
+template <class P>
+__global__ void __launch_bounds__(kTileX* kTileY) transport_kernel(DeviceView v) {
+  transport_tile<P>(v, blockIdx.x * kTileX, blockIdx.y * kTileY, blockIdx.y * gridDim.x + blockIdx.x);
+}
 
 // ------------------------------------------------------- FP32 fast-path math
 // The FP32 policies use the SFU reciprocal / reciprocal square root (a few ulp)
@@ -516,7 +519,7 @@ __device__ __forceinline__ void face_flux_f32(float Jm, float nm, float tm, floa
 // of warp 1 the right column of x-faces.  The implicit source step runs in
 // type I (FP64 for LYM1_MIXED, FP32 for LYM1_MIXED_FAST).
 template <class P>
-__global__ void __launch_bounds__(kTileX* kTileY, 3) transport_kernel_f32(DeviceView v) {
+__device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, int y0, int blk) {
   using I = typename P::I;
   constexpr int TX = kTileX, TY = kTileY, SX = TX + 4, SY = TY + 4, QX = TX + 2, QY = TY + 2;
   constexpr int NT = TX * TY;
@@ -544,7 +547,6 @@ __global__ void __launch_bounds__(kTileX* kTileY, 3) transport_kernel_f32(Device
   const int nx = v.nx, ny = v.ny, nb = v.nb;
   const long long nc = v.nc;
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
   const int gx = x0 + tx, gy = y0 + ty;
   const bool valid = gx < nx && gy < ny;
   const long long cell = valid ? static_cast<long long>(gy) * nx + gx : 0;
@@ -734,7 +736,6 @@ __global__ void __launch_bounds__(kTileX* kTileY, 3) transport_kernel_f32(Device
     v.fx[cell] = v.fcoef * double(ax);
     v.fy[cell] = v.fcoef * double(ay);
   }
-  const int blk = blockIdx.y * gridDim.x + blockIdx.x;
   double* part = v.partT + static_cast<long long>(blk) * kDiagSlots;
   double s;
   s = block_sum<NT>(double(em), red);
@@ -751,6 +752,12 @@ __global__ void __launch_bounds__(kTileX* kTileY, 3) transport_kernel_f32(Device
   if (tid == 0) part[kSlotMaxF] = s;
   s = block_sum<NT>(double(bad), red);
   if (tid == 0) part[kSlotBad] = s;
+}
+
+template <class P>
+__global__ void __launch_bounds__(kTileX* kTileY, 3) transport_kernel_f32(DeviceView v) {
+  transport_tile_f32<P>(v, blockIdx.x * kTileX, blockIdx.y * kTileY,
+                        blockIdx.y * gridDim.x + blockIdx.x);
 }
 
 // ------------------------------------------------------------ frequency kernel
@@ -800,7 +807,7 @@ __device__ __forceinline__ void freq_coef(typename P::F Jc, typename P::F Hxc, t
 }
 
 template <class P>
-__global__ void __launch_bounds__(kFreqThreads) freq_kernel(DeviceView v) {
+__device__ __forceinline__ void freq_block(const DeviceView& v, int blk) {
   using S = typename P::S;
   using F = typename P::F;
   using I = typename P::I;
@@ -841,7 +848,7 @@ __global__ void __launch_bounds__(kFreqThreads) freq_kernel(DeviceView v) {
   S* __restrict__ Hxout = static_cast<S*>(v.Hxo);
   S* __restrict__ Hyout = static_cast<S*>(v.Hyo);
   const long long nc = v.nc;
-  const long long cell = static_cast<long long>(blockIdx.x) * NT + threadIdx.x;
+  const long long cell = static_cast<long long>(blk) * NT + threadIdx.x;
   RSum<I> en;
   I mxf = 0;
   int bad = 0;
@@ -972,7 +979,7 @@ __global__ void __launch_bounds__(kFreqThreads) freq_kernel(DeviceView v) {
       }
     }
   }
-  double* part = v.partF + static_cast<long long>(blockIdx.x) * kDiagSlots;
+  double* part = v.partF + static_cast<long long>(blk) * kDiagSlots;
   double s;
   s = block_sum<NT>(en.value(), red);
   if (threadIdx.x == 0) part[kSlotEnergy] = s;
@@ -980,6 +987,92 @@ __global__ void __launch_bounds__(kFreqThreads) freq_kernel(DeviceView v) {
   if (threadIdx.x == 0) part[kSlotMaxF] = s;
   s = block_sum<NT>(double(bad), red);
   if (threadIdx.x == 0) part[kSlotBad] = s;
+}
+
+template <class P>
+__global__ void __launch_bounds__(kFreqThreads) freq_kernel(DeviceView v) {
+  freq_block<P>(v, blockIdx.x);
+}
+
+// ------------------------------------------------------------ batched launches
+// Persistent kernels over a work list that spans several contexts (clouds of
+// different sizes): each item names a context and a tile (transport) or a
+// block of cells (frequency step); blocks walk the list with a grid stride.
+struct BatchItem {
+  int ctx, x0, y0, blk;
+};
+
+template <class P>
+__global__ void __launch_bounds__(kTileX* kTileY) transport_batched(const DeviceView* views,
+                                                                    const BatchItem* items, int n) {
+  for (int i = blockIdx.x; i < n; i += gridDim.x) {
+    const BatchItem it = items[i];
+    const DeviceView v = views[it.ctx];
+    transport_tile<P>(v, it.x0, it.y0, it.blk);
+    __syncthreads();
+  }
+}
+
+template <class P>
+__global__ void __launch_bounds__(kTileX* kTileY, 3) transport_batched_f32(const DeviceView* views,
+                                                                           const BatchItem* items,
+                                                                           int n) {
+  for (int i = blockIdx.x; i < n; i += gridDim.x) {
+    const BatchItem it = items[i];
+    const DeviceView v = views[it.ctx];
+    transport_tile_f32<P>(v, it.x0, it.y0, it.blk);
+    __syncthreads();
+  }
+}
+
+template <class P>
+__global__ void __launch_bounds__(kFreqThreads) freq_batched(const DeviceView* views,
+                                                            const BatchItem* items, int n) {
+  for (int i = blockIdx.x; i < n; i += gridDim.x) {
+    const BatchItem it = items[i];
+    const DeviceView v = views[it.ctx];
+    freq_block<P>(v, it.blk);
+    __syncthreads();
+  }
+}
+
+template <class P>
+int launch_transport_batched_t(const DeviceView* views, const BatchItem* items, int n, int grid,
+                               int nb_max, cudaStream_t st) {
+  if constexpr (sizeof(typename P::S) == 4) {
+    const size_t smem = sizeof(float) * 4 * static_cast<size_t>(nb_max);
+    transport_batched_f32<P><<<grid, dim3(kTileX, kTileY), smem, st>>>(views, items, n);
+  } else {
+    transport_batched<P><<<grid, dim3(kTileX, kTileY), 0, st>>>(views, items, n);
+  }
+  return static_cast<int>(cudaGetLastError());
+}
+
+template <class P>
+int launch_freq_batched_t(const DeviceView* views, const BatchItem* items, int n, int grid,
+                          int nb_max, cudaStream_t st) {
+  const size_t smem = sizeof(double) * 7 * static_cast<size_t>(nb_max);
+  freq_batched<P><<<grid, kFreqThreads, smem, st>>>(views, items, n);
+  return static_cast<int>(cudaGetLastError());
+}
+
+template <class P>
+int max_resident_transport() {
+  int nblk = 0;
+  if constexpr (sizeof(typename P::S) == 4)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nblk, transport_batched_f32<P>, kTileX * kTileY,
+                                                  sizeof(float) * 4 * 194);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nblk, transport_batched<P>, kTileX * kTileY, 0);
+  return nblk < 1 ? 1 : nblk;
+}
+
+template <class P>
+int max_resident_freq() {
+  int nblk = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nblk, freq_batched<P>, kFreqThreads,
+                                                sizeof(double) * 7 * 194);
+  return nblk < 1 ? 1 : nblk;
 }
 
 template <class P>

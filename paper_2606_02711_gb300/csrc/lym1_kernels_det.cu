@@ -15,6 +15,19 @@ int launch_freq_det(const DeviceView& v, void* st) {
   return launch_freq_t<PolDet>(v, static_cast<cudaStream_t>(st));
 }
 
+int launch_batched_det(int kind, const DeviceView* views, const void* items, int n, int grid,
+                       int nb_max, void* st) {
+  const cudaStream_t s = static_cast<cudaStream_t>(st);
+  const BatchItem* it = static_cast<const BatchItem*>(items);
+  if (kind == 0) return launch_transport_batched_t<PolDet>(views, it, n, grid, nb_max, s);
+  return launch_freq_batched_t<PolDet>(views, it, n, grid, nb_max, s);
+}
+
+int resident_blocks_det(int kind) {
+  return kind == 0 ? max_resident_transport<PolDet>() : max_resident_freq<PolDet>();
+}
+
+
 // alpha = n_HI sigma0; velocity gradients by central differences over the
 // two neighbours, ghosts = edge values (outflow boundaries).
 __global__ void setup_statics_kernel(const double* n_hi, const double* ux, const double* uy,
@@ -123,9 +136,8 @@ __device__ __forceinline__ void kahan_add(double* a, double v) {
 //               [11] substeps, [12] energy at the last reset, [13] energy unit
 // mode 0: substep (flows from partT, energy/max f from partE);
 // mode 1: reset (energy from partE; flows and counters zeroed).
-__global__ void __launch_bounds__(256) finalize_kernel(const double* partT, int nT,
-                                                       const double* partE, int nE,
-                                                       double* acc, int mode) {
+__device__ __forceinline__ void finalize_body(const double* partT, int nT, const double* partE,
+                                              int nE, double* acc, int mode) {
   __shared__ double red[8];
   double v[kDiagSlots];
   for (int s = 0; s < kDiagSlots; ++s) v[s] = 0.0;
@@ -169,6 +181,12 @@ __global__ void __launch_bounds__(256) finalize_kernel(const double* partT, int 
   }
 }
 
+__global__ void __launch_bounds__(256) finalize_kernel(const double* partT, int nT,
+                                                       const double* partE, int nE,
+                                                       double* acc, int mode) {
+  finalize_body(partT, nT, partE, nE, acc, mode);
+}
+
 int launch_finalize(const double* partT, int nT, const double* partE, int nE, double* acc,
                     int mode, void* st) {
   finalize_kernel<<<1, 256, 0, static_cast<cudaStream_t>(st)>>>(partT, nT, partE, nE, acc, mode);
@@ -201,6 +219,17 @@ __global__ void __launch_bounds__(256) force_reduce_kernel(const double* fx, con
 int launch_force_reduce(const double* fx, const double* fy, int nx, int ny, double dx,
                         double* part, int nblocks, void* st) {
   force_reduce_kernel<<<nblocks, 256, 0, static_cast<cudaStream_t>(st)>>>(fx, fy, nx, ny, dx, part);
+  return static_cast<int>(cudaGetLastError());
+}
+
+// one block per context: the per-substep reduction of finalize_kernel for a batch
+__global__ void __launch_bounds__(256) finalize_batched_kernel(const FinalizeJob* jobs) {
+  const FinalizeJob j = jobs[blockIdx.x];
+  finalize_body(j.partT, j.nT, j.partE, j.nE, j.acc, 0);
+}
+
+int launch_finalize_batched(const FinalizeJob* jobs, int n, void* st) {
+  finalize_batched_kernel<<<n, 256, 0, static_cast<cudaStream_t>(st)>>>(jobs);
   return static_cast<int>(cudaGetLastError());
 }
 

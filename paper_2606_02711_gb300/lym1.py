@@ -94,6 +94,10 @@ SIGNATURES = {
     "lym1_substeps_batched": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int]),
     "lym1_profile_enable": (C.c_int, [C.c_void_p, C.c_int]),
     "lym1_profile_read": (C.c_int, [C.c_void_p, C.POINTER(lym1_profile), C.c_int]),
+    "lym1_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_void_p)]),
+    "lym1_batch_substeps": (C.c_int, [C.c_void_p, C.c_int]),
+    "lym1_batch_grid": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "lym1_batch_destroy": (None, [C.c_void_p]),
     "lym1_energy_noalloc": (C.c_int, [_PD, _PD, C.c_int, C.c_longlong, C.c_double, _PD,
                                       C.c_void_p]),
 }
@@ -306,6 +310,37 @@ def energy_noalloc(J, dnu, dx, stream=None) -> float:
                                      out.ctypes.data_as(_PD), _stream_handle(stream)),
            "lym1_energy_noalloc")
     return float(out[0])
+
+
+class Batch:
+    """``lym1_batch_*``: several contexts advanced by one graph-replayed set of
+    persistent launches per substep.  Destroy it before its contexts."""
+
+    def __init__(self, contexts):
+        self.contexts = list(contexts)
+        arr = (C.c_void_p * len(self.contexts))(*[c.handle.value for c in self.contexts])
+        h = C.c_void_p()
+        _check(lib().lym1_batch_create(arr, len(self.contexts), C.byref(h)), "lym1_batch_create")
+        self.handle = h
+
+    def substeps(self, n):
+        _check(lib().lym1_batch_substeps(self.handle, int(n)), "lym1_batch_substeps")
+
+    def grid(self):
+        a, b = C.c_int(), C.c_int()
+        _check(lib().lym1_batch_grid(self.handle, C.byref(a), C.byref(b)), "lym1_batch_grid")
+        return a.value, b.value
+
+    def destroy(self):
+        if getattr(self, "handle", None):
+            lib().lym1_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
 
 
 def substeps_batched(contexts, n):
