@@ -44,7 +44,8 @@ extern "C" {
 #define LYM1_ENOMEM (-2)         /* device allocation failed */
 #define LYM1_ECUDA (-3)          /* a CUDA runtime call or kernel launch failed */
 #define LYM1_ENONFINITE (-4)     /* a diagnostic sum is not finite (NaN/Inf in the state) */
-#define LYM1_ETIMEOUT (-5)       /* a bounded device wait expired */
+#define LYM1_ETIMEOUT (-5)       /* a kernel's bounded wait on its own bulk copies expired (sticky,
+                                    reported by lym1_synchronize and lym1_diagnostics) */
 #define LYM1_ENOTCONVERGED (-6)  /* substep cap reached before the steady-state test passed */
 #define LYM1_ENODEVICE (-7)      /* no CUDA device is usable */
 #define LYM1_ERANGE (-8)         /* size beyond the fixed maximum of an allocation-free call */

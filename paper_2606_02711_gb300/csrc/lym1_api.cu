@@ -33,7 +33,10 @@ struct lym1_ctx {
   double *fx = nullptr, *fy = nullptr, *partT = nullptr, *partF = nullptr, *acc = nullptr;
   double* staging = nullptr;  // one bin plane of doubles
   double* fpart = nullptr;    // force-reduction partials
+  int* status = nullptr;      // set by a kernel whose bounded wait expired
   std::vector<void*> allocs;
+  // persistent graph-replayed path for CFL substeps (a batch of this context alone)
+  lym1_batch* self_batch = nullptr;
   // kernel timing (lym1_profile_enable): event pairs per launch, kind 0..2
   bool profiling = false;
   std::vector<cudaEvent_t> ev_start, ev_stop;
@@ -144,6 +147,7 @@ DeviceView make_view(const lym1_ctx* c, double dt) {
   v.freq_step = c->freq_step;
   v.gem_max = c->gem_max;
   v.acc = c->acc;
+  v.status = c->status;
   return v;
 }
 
@@ -295,6 +299,37 @@ int batch_launch(lym1_batch* b, cudaStream_t s) {
   return LYM1_OK;
 }
 
+// the persistent launches of one substep on the context's stream, each
+// bracketed by profiling events (no graph)
+int batch_launch_timed(lym1_batch* b, lym1_ctx* c) {
+  const int n = static_cast<int>(b->ctxs.size());
+  {
+    KernelTimer t(c, 0);
+    if (b->precision == LYM1_FP64_DET)
+      LYM1_TRYK(launch_batched_det(0, b->viewsT, b->itemsT, b->nT, b->gridT, b->nb, c->stream));
+    else
+      LYM1_TRYK(launch_batched_fast(b->precision, 0, b->viewsT, b->itemsT, b->nT, b->gridT, b->nb,
+                                    c->stream));
+  }
+  {
+    KernelTimer t(c, 1);
+    if (b->precision == LYM1_FP64_DET)
+      LYM1_TRYK(launch_batched_det(1, b->viewsF, b->itemsF, b->nF, b->gridF, b->nb, c->stream));
+    else
+      LYM1_TRYK(launch_batched_fast(b->precision, 1, b->viewsF, b->itemsF, b->nF, b->gridF, b->nb,
+                                    c->stream));
+  }
+  KernelTimer t(c, 2);
+  LYM1_TRYK(launch_finalize_batched(b->jobs, n, c->stream));
+  return LYM1_OK;
+}
+
+int device_status(lym1_ctx* c) {
+  int st = 0;
+  LYM1_TRY(cudaMemcpy(&st, c->status, sizeof st, cudaMemcpyDeviceToHost));
+  return st != 0 ? LYM1_ETIMEOUT : LYM1_OK;
+}
+
 void batch_free(lym1_batch* b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
@@ -399,6 +434,7 @@ int lym1_create(const lym1_grid* grid, const lym1_groups* groups, const lym1_opa
   if (rc == LYM1_OK) rc = dalloc_t(c, &c->partF, static_cast<size_t>(freq_blocks(nc)) * kDiagSlots);
   if (rc == LYM1_OK) rc = dalloc_t(c, &c->acc, 16);
   if (rc == LYM1_OK) rc = dalloc_t(c, &c->fpart, 2 * kForceBlocks);
+  if (rc == LYM1_OK) rc = dalloc_t(c, &c->status, 4);
   if (rc != LYM1_OK) {
     free_all(c);
     delete c;
@@ -435,7 +471,8 @@ int lym1_create(const lym1_grid* grid, const lym1_groups* groups, const lym1_opa
   for (int i = 0; i < 3; ++i)
     if (cudaMemsetAsync(c->A[i], 0, nstate * c->selem, s) != cudaSuccess) return fail(LYM1_ECUDA);
   if (cudaMemsetAsync(c->lum, 0, pb, s) != cudaSuccess || cudaMemsetAsync(c->fx, 0, pb, s) != cudaSuccess ||
-      cudaMemsetAsync(c->fy, 0, pb, s) != cudaSuccess || cudaMemsetAsync(c->acc, 0, 16 * sizeof(double), s) != cudaSuccess)
+      cudaMemsetAsync(c->fy, 0, pb, s) != cudaSuccess || cudaMemsetAsync(c->acc, 0, 16 * sizeof(double), s) != cudaSuccess ||
+      cudaMemsetAsync(c->status, 0, 4 * sizeof(int), s) != cudaSuccess)
     return fail(LYM1_ECUDA);
   // max |u| for the RT time step (Sec. 2.1, CFL condition with D = 2)
   std::vector<double> hux(plane), huy(plane);
@@ -462,6 +499,8 @@ int lym1_create(const lym1_grid* grid, const lym1_groups* groups, const lym1_opa
 void lym1_destroy(lym1_ctx* c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
+  if (c->self_batch) lym1_batch_destroy(c->self_batch);
+  c->self_batch = nullptr;
   drop_events(c);
   free_all(c);
   delete c;
@@ -506,6 +545,28 @@ int lym1_get_state(lym1_ctx* c, double* J, double* Hx, double* Hy) {
 int lym1_substeps(lym1_ctx* c, int n, double dt) {
   if (!c || n < 0) return LYM1_EINVAL;
   if (!(dt > 0.0)) dt = c->dt_cfl;
+  if (n > 0 && dt == c->dt_cfl && !c->gray && c->freq_step) {
+    // CFL substeps: the persistent work-list kernels, graph-replayed
+    if (!c->self_batch) {
+      lym1_ctx* one[1] = {c};
+      const int rc = lym1_batch_create(one, 1, &c->self_batch);
+      if (rc != LYM1_OK) return rc;
+    }
+    if (!c->profiling) return lym1_batch_substeps(c->self_batch, n);
+    lym1_batch* b = c->self_batch;
+    int done = 0;
+    if (!b->tuned) {  // the tuning substeps (untimed) count toward n
+      done = std::min(n, static_cast<int>(b->candT.size()));
+      const int rc = lym1_batch_substeps(b, done);
+      if (rc != LYM1_OK) return rc;
+    }
+    for (; done < n; ++done) {
+      const int rc = batch_launch_timed(b, c);
+      if (rc != LYM1_OK) return rc;
+      c->substeps_done += 1;
+    }
+    return LYM1_OK;
+  }
   for (int i = 0; i < n; ++i) {
     const int rc = one_substep(c, dt);
     if (rc != LYM1_OK) return rc;
@@ -579,7 +640,7 @@ int lym1_diagnostics(lym1_ctx* c, lym1_diag* d) {
   const double vals[] = {d->e_tot, d->emitted, d->absorbed, d->outflow, d->work, fa, fr};
   for (double x : vals)
     if (!std::isfinite(x)) return LYM1_ENONFINITE;
-  return LYM1_OK;
+  return device_status(c);
 }
 
 int lym1_get_info(lym1_ctx* c, lym1_info* o) {
@@ -615,7 +676,7 @@ int lym1_synchronize(lym1_ctx* c) {
   if (!c) return LYM1_EINVAL;
   LYM1_TRY(cudaStreamSynchronize(c->stream));
   LYM1_TRY(cudaGetLastError());
-  return LYM1_OK;
+  return device_status(c);
 }
 
 int lym1_run_to_steady(lym1_ctx* c, double tol, int check_every, int max_substeps, int* n_done) {

@@ -94,6 +94,7 @@ struct DeviceView {
   double kabs = 0, kF = 0, Kc = 0, cdt = 0, fcoef = 0;
   double gem_max = 1;  // max_k gem_k (FP32 emissivity scaling)
   const double* acc = nullptr;  // running totals: [8] energy of the last substep, [13] energy unit
+  int* status = nullptr;        // device status word: nonzero after a bounded wait expired
   int freq_step = 0;
 };
 

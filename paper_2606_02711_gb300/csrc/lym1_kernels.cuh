@@ -989,9 +989,314 @@ __device__ __forceinline__ void freq_block(const DeviceView& v, int blk) {
   if (threadIdx.x == 0) part[kSlotBad] = s;
 }
 
+
+// ------------------------------------------- bulk-copy pipeline (FP32 state)
+// Shared-memory ring fed by cp.async.bulk (one thread issues, an mbarrier per
+// stage counts the bytes).  Every wait is bounded: past kMaxSpins polls the
+// block records LYM1_ETIMEOUT in the context's status word and gives up.
+constexpr int kBulkDepth = 8;
+constexpr long long kMaxSpins = 100000000;          // backstop on the number of polls
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s per wait
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes,
+                                          unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  for (long long i = 0; i < kMaxSpins; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 255) == 0 && global_ns() - t0 > kWaitLimitNs) return false;
+  }
+  return false;
+}
+__device__ __forceinline__ void fence_proxy_async_global() {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Frequency step of one block of kFreqThreads cells with every bin row
+// streamed through the ring (cell count a multiple of 4, so that every row
+// segment starts on a 16-byte boundary and is a whole number of 16 bytes).
+// Same arithmetic, in the same order, as freq_block.
 template <class P>
-__global__ void __launch_bounds__(kFreqThreads) freq_kernel(DeviceView v) {
-  freq_block<P>(v, blockIdx.x);
+__device__ __forceinline__ void freq_block_bulk(const DeviceView& v, int blk) {
+  using F = typename P::F;
+  using I = typename P::I;
+  using T = F;
+  constexpr int NT = kFreqThreads, D = kBulkDepth;
+  __shared__ __align__(128) float ring[D][5][NT];
+  __shared__ __align__(8) unsigned long long barF[D], barB[D];
+  __shared__ double red[NT / 32];
+  __shared__ int failed;
+  extern __shared__ double tabs_raw[];
+  T* tabs = reinterpret_cast<T*>(tabs_raw);
+  const int nb = v.nb;
+  T* tH = tabs;
+  T* tR = tabs + nb;
+  T* tn = tabs + 2 * nb;
+  T* th = tabs + 3 * nb;
+  I* tdi = reinterpret_cast<I*>(tabs_raw + 5 * nb);
+  I* tact = reinterpret_cast<I*>(tabs_raw + 6 * nb);
+  const int tid = threadIdx.x;
+  const double e_prev = v.acc[8], e_unit = v.acc[13];
+  for (int i = tid; i < nb; i += NT) {
+    tH[i] = T(v.t_H[i]);
+    tR[i] = T(v.t_R[i]);
+    tn[i] = T(v.t_nbc[i]);
+    th[i] = T(v.t_half[i]);
+    tdi[i] = I(v.t_dnu[i]);
+    const double ja = kActiveShare * e_prev / (e_unit * v.t_dnu[i]);
+    tact[i] = I(fmax(fmin(ja, 1e30), 1e-30));
+  }
+  if (tid == 0) {
+    failed = 0;
+    for (int s = 0; s < D; ++s) {
+      mbar_init(&barF[s], 1);
+      mbar_init(&barB[s], 1);
+    }
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  const float* __restrict__ Jin = static_cast<const float*>(v.J);
+  const float* __restrict__ Hxin = static_cast<const float*>(v.Hx);
+  const float* __restrict__ Hyin = static_cast<const float*>(v.Hy);
+  float* __restrict__ Jout = static_cast<float*>(v.Jo);
+  float* __restrict__ Hxout = static_cast<float*>(v.Hxo);
+  float* __restrict__ Hyout = static_cast<float*>(v.Hyo);
+  const long long nc = v.nc;
+  const long long c0 = static_cast<long long>(blk) * NT;
+  const int ncell = static_cast<int>(nc - c0 < NT ? nc - c0 : NT);
+  const unsigned rowb = static_cast<unsigned>(ncell) * 4u;
+  const long long cell = c0 + tid;
+  const bool valid = tid < ncell;
+  const double alpha = valid ? v.alpha[cell] : 0.0;
+  const bool act = valid && alpha > 0.0;
+  const F Kc = F(v.Kc * alpha);
+  const F gxx = valid ? F(v.gxx[cell]) : F(0), gyy = valid ? F(v.gyy[cell]) : F(0),
+          gsh = valid ? F(v.gsh[cell]) : F(0);
+  const I cdt = I(v.cdt);
+  const float rcdt = float(1.0 / v.cdt);
+  (void)rcdt;
+
+  auto issue_fwd = [&](int k) {
+    const int s = k % D;
+    const long long off = static_cast<long long>(k) * nc + c0;
+    mbar_expect_tx(&barF[s], 3u * rowb);
+    bulk_load(&ring[s][0][0], Jin + off, rowb, &barF[s]);
+    bulk_load(&ring[s][1][0], Hxin + off, rowb, &barF[s]);
+    bulk_load(&ring[s][2][0], Hyin + off, rowb, &barF[s]);
+  };
+  auto issue_bwd = [&](int j) {  // j-th bin from the top
+    const int s = j % D, k = nb - 1 - j;
+    const long long off = static_cast<long long>(k) * nc + c0;
+    mbar_expect_tx(&barB[s], 5u * rowb);
+    bulk_load(&ring[s][0][0], Jout + off, rowb, &barB[s]);
+    bulk_load(&ring[s][1][0], Hxout + off, rowb, &barB[s]);
+    bulk_load(&ring[s][2][0], Jin + off, rowb, &barB[s]);
+    bulk_load(&ring[s][3][0], Hxin + off, rowb, &barB[s]);
+    bulk_load(&ring[s][4][0], Hyin + off, rowb, &barB[s]);
+  };
+  // bounded failure: record the status, let the copies in flight land, stop
+  auto give_up = [&](unsigned long long* bars, int issued_upto, int consumed) {
+    if (tid == 0) {
+      atomicExch(v.status, 1);
+      for (int j = consumed; j < issued_upto; ++j) mbar_wait_bounded(&bars[j % D], (j / D) & 1);
+    }
+  };
+
+  if (tid == 0)
+    for (int k = 0; k < nb && k < D; ++k) issue_fwd(k);
+  // forward sweep, one bin behind the data: iteration k forms the
+  // coefficients of bin k and eliminates row k-1
+  F Pp = F(0), ap = F(0), ep = F(0);
+  I Jp = 0, qprev = 0, gprev = 0, Bprev = 0, Aprev = 0;
+  for (int k = 0; k < nb; ++k) {
+    const int s = k % D;
+    if (!mbar_wait_bounded(&barF[s], (k / D) & 1)) failed = 1;
+    __syncthreads();
+    if (failed) {
+      give_up(barF, nb < k + D ? nb : k + D, k);
+      return;
+    }
+    if (act) {
+      const F Jc = F(ring[s][0][tid]), Xc = F(ring[s][1][tid]), Yc = F(ring[s][2][tid]);
+      F Pk, ak, ek;
+      freq_coef<P>(Jc, Xc, Yc, Kc, gxx, gyy, gsh, tH, tR, tn, th, k, Pk, ak, ek);
+      if (k > 0) {
+        const F d1 = (-Pp > F(0)) ? -Pp : F(0);
+        const F d2 = (Pk > F(0)) ? Pk : F(0);
+        const F m = (d1 > d2) ? d1 : d2;
+        const F den = m_exp<P::DET>(d1 - m) * (ep * ap) + m_exp<P::DET>(d2 - m) * (ek * ak);
+        const float rden = frcp(den);
+        const I A = I(m_exp<P::DET>(-Pp - m) * rden);
+        const I B = I(m_exp<P::DET>(Pk - m) * rden);
+        // row k-1
+        I sk;
+        if constexpr (sizeof(I) == 4)
+          sk = tdi[k - 1] * rcdt;
+        else
+          sk = tdi[k - 1] / cdt;
+        const I E = (k == 1) ? sk : sk + Bprev * qprev;
+        const I r = (k == 1) ? sk * Jp : sk * Jp + Aprev * gprev;
+        const I Dp = E + A;
+        I inv;
+        if constexpr (sizeof(I) == 4)
+          inv = frcp(Dp);
+        else
+          inv = I(1) / Dp;
+        const I g = r * inv;
+        const I h = B * inv;
+        qprev = E * inv;
+        gprev = g;
+        Bprev = B;
+        Aprev = A;
+        const long long o = static_cast<long long>(k - 1) * nc + cell;
+        Jout[o] = float(g);
+        Hxout[o] = float(h);
+      }
+      Pp = Pk;
+      ap = ak;
+      ep = ek;
+      Jp = I(Jc);
+    }
+    __syncthreads();  // stage s consumed
+    if (tid == 0 && k + D < nb) issue_fwd(k + D);
+  }
+  if (act) {  // last row: no interface above
+    I sk;
+    if constexpr (sizeof(I) == 4)
+      sk = tdi[nb - 1] * rcdt;
+    else
+      sk = tdi[nb - 1] / cdt;
+    const I E = (nb == 1) ? sk : sk + Bprev * qprev;
+    const I r = (nb == 1) ? sk * Jp : sk * Jp + Aprev * gprev;
+    I inv;
+    if constexpr (sizeof(I) == 4)
+      inv = frcp(E);
+    else
+      inv = I(1) / E;
+    const long long o = static_cast<long long>(nb - 1) * nc + cell;
+    Jout[o] = float(r * inv);
+    Hxout[o] = 0.0f;
+  }
+  // the elimination factors go back through the async proxy
+  fence_proxy_async_global();
+  __syncthreads();
+  if (tid == 0)
+    for (int j = 0; j < nb && j < D; ++j) issue_bwd(j);
+  RSum<I> en;
+  I mxf = 0;
+  int bad = 0;
+  I Jnext = 0;
+  for (int j = 0; j < nb; ++j) {
+    const int s = j % D, k = nb - 1 - j;
+    if (!mbar_wait_bounded(&barB[s], (j / D) & 1)) failed = 1;
+    __syncthreads();
+    if (failed) {
+      give_up(barB, nb < j + D ? nb : j + D, j);
+      return;
+    }
+    if (valid) {
+      const long long o = static_cast<long long>(k) * nc + cell;
+      const float Jo = ring[s][2][tid], Xo = ring[s][3][tid], Yo = ring[s][4][tid];
+      if (act) {
+        const I g = I(ring[s][0][tid]), h = I(ring[s][1][tid]);
+        const I Jn = (j == 0) ? g : g + h * Jnext;
+        Jnext = Jn;
+        I ratio;
+        if constexpr (sizeof(I) == 4)
+          ratio = (Jo > kTinyJ) ? fdiv(Jn, Jo) : 0.0f;
+        else
+          ratio = (I(Jo) > I(0)) ? Jn / I(Jo) : I(0);
+        const I Hx2 = ratio * I(Xo), Hy2 = ratio * I(Yo);
+        Jout[o] = float(Jn);
+        Hxout[o] = float(Hx2);
+        Hyout[o] = float(Hy2);
+        en.add(tdi[k] * Jn);
+        if (Jn > tact[k]) {
+          const I hn = sqrt(Hx2 * Hx2 + Hy2 * Hy2);
+          mxf = fmax(mxf, hn / Jn);
+          bad += (hn > Jn * I(1.000001)) ? 1 : 0;
+        }
+      } else {
+        Jout[o] = Jo;
+        Hxout[o] = Xo;
+        Hyout[o] = Yo;
+        const I Ji = I(Jo), Hxi = I(Xo), Hyi = I(Yo);
+        en.add(tdi[k] * Ji);
+        if (Ji > tact[k]) {
+          const I hn = sqrt(Hxi * Hxi + Hyi * Hyi);
+          mxf = fmax(mxf, hn / Ji);
+          bad += (hn > Ji * I(1.000001)) ? 1 : 0;
+        }
+      }
+    }
+    __syncthreads();
+    if (tid == 0 && j + D < nb) issue_bwd(j + D);
+  }
+  double* part = v.partF + static_cast<long long>(blk) * kDiagSlots;
+  double sres;
+  sres = block_sum<NT>(en.value(), red);
+  if (tid == 0) part[kSlotEnergy] = sres;
+  sres = block_max<NT>(double(mxf), red);
+  if (tid == 0) part[kSlotMaxF] = sres;
+  sres = block_sum<NT>(double(bad), red);
+  if (tid == 0) part[kSlotBad] = sres;
+}
+
+// FP32 state with a cell count that is a multiple of 4 takes the bulk-copy
+// pipeline; everything else the register-prefetch sweep
+template <class P>
+__device__ __forceinline__ void freq_dispatch(const DeviceView& v, int blk) {
+  if constexpr (sizeof(typename P::S) == 4) {
+    if ((v.nc & 3) == 0) {
+      freq_block_bulk<P>(v, blk);
+      return;
+    }
+  }
+  freq_block<P>(v, blk);
+}
+
+// FP32 state: at most 64 registers so that 8 blocks (32 warps) per SM keep
+// enough loads in flight for the latency-bound bin sweeps
+template <class P>
+__global__ void __launch_bounds__(kFreqThreads, sizeof(typename P::S) == 4 ? 8 : 1)
+    freq_kernel(DeviceView v) {
+  freq_dispatch<P>(v, blockIdx.x);
 }
 
 // ------------------------------------------------------------ batched launches
@@ -1026,12 +1331,12 @@ __global__ void __launch_bounds__(kTileX* kTileY, 3) transport_batched_f32(const
 }
 
 template <class P>
-__global__ void __launch_bounds__(kFreqThreads) freq_batched(const DeviceView* views,
-                                                            const BatchItem* items, int n) {
+__global__ void __launch_bounds__(kFreqThreads, sizeof(typename P::S) == 4 ? 8 : 1)
+    freq_batched(const DeviceView* views, const BatchItem* items, int n) {
   for (int i = blockIdx.x; i < n; i += gridDim.x) {
     const BatchItem it = items[i];
     const DeviceView v = views[it.ctx];
-    freq_block<P>(v, it.blk);
+    freq_dispatch<P>(v, it.blk);
     __syncthreads();
   }
 }
