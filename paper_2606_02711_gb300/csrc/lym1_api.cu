@@ -34,6 +34,8 @@ struct lym1_ctx {
   double* staging = nullptr;  // one bin plane of doubles
   double* fpart = nullptr;    // force-reduction partials
   int* status = nullptr;      // set by a kernel whose bounded wait expired
+  float *f_H = nullptr, *f_dnu = nullptr, *f_G = nullptr, *f_R = nullptr, *f_nbc = nullptr,
+        *f_half = nullptr;
   std::vector<void*> allocs;
   // persistent graph-replayed path for CFL substeps (a batch of this context alone)
   lym1_batch* self_batch = nullptr;
@@ -148,6 +150,12 @@ DeviceView make_view(const lym1_ctx* c, double dt) {
   v.gem_max = c->gem_max;
   v.acc = c->acc;
   v.status = c->status;
+  v.f_H = c->f_H;
+  v.f_dnu = c->f_dnu;
+  v.f_G = c->f_G;
+  v.f_R = c->f_R;
+  v.f_nbc = c->f_nbc;
+  v.f_half = c->f_half;
   return v;
 }
 
@@ -435,6 +443,9 @@ int lym1_create(const lym1_grid* grid, const lym1_groups* groups, const lym1_opa
   if (rc == LYM1_OK) rc = dalloc_t(c, &c->acc, 16);
   if (rc == LYM1_OK) rc = dalloc_t(c, &c->fpart, 2 * kForceBlocks);
   if (rc == LYM1_OK) rc = dalloc_t(c, &c->status, 4);
+  float** ftabs[] = {&c->f_H, &c->f_dnu, &c->f_G, &c->f_R, &c->f_nbc, &c->f_half};
+  for (float** p : ftabs)
+    if (rc == LYM1_OK) rc = dalloc_t(c, p, static_cast<size_t>(c->nb));
   if (rc != LYM1_OK) {
     free_all(c);
     delete c;
@@ -467,6 +478,20 @@ int lym1_create(const lym1_grid* grid, const lym1_groups* groups, const lym1_opa
   for (int i = 0; i < 6; ++i)
     if (cudaMemcpyAsync(dtabs[i], tabs[i]->data(), sizeof(double) * c->nb, cudaMemcpyHostToDevice, s) !=
         cudaSuccess)
+      return fail(LYM1_ECUDA);
+  // FP32 table copies (the emissivity factor scaled by its maximum)
+  std::vector<float> fh[6];
+  for (int k = 0; k < c->nb; ++k) {
+    fh[0].push_back(static_cast<float>(c->tab.Havg[k]));
+    fh[1].push_back(static_cast<float>(c->tab.dnu[k]));
+    fh[2].push_back(static_cast<float>(c->tab.gem[k] / c->gem_max));
+    fh[3].push_back(static_cast<float>(c->tab.Rk[k]));
+    fh[4].push_back(static_cast<float>(c->tab.nubar_c[k]));
+    fh[5].push_back(static_cast<float>(c->tab.half[k]));
+  }
+  float* fd[] = {c->f_H, c->f_dnu, c->f_G, c->f_R, c->f_nbc, c->f_half};
+  for (int i = 0; i < 6; ++i)
+    if (cudaMemcpy(fd[i], fh[i].data(), sizeof(float) * c->nb, cudaMemcpyHostToDevice) != cudaSuccess)
       return fail(LYM1_ECUDA);
   for (int i = 0; i < 3; ++i)
     if (cudaMemsetAsync(c->A[i], 0, nstate * c->selem, s) != cudaSuccess) return fail(LYM1_ECUDA);

@@ -95,6 +95,14 @@ struct DeviceView {
   double gem_max = 1;  // max_k gem_k (FP32 emissivity scaling)
   const double* acc = nullptr;  // running totals: [8] energy of the last substep, [13] energy unit
   int* status = nullptr;        // device status word: nonzero after a bounded wait expired
+  // FP32 copies of the per-bin tables for the FP32 policies: <H>_k, dnu_k,
+  // gem_k / gem_max, R_k, nubar_k / c, half width
+  const float* f_H = nullptr;
+  const float* f_dnu = nullptr;
+  const float* f_G = nullptr;
+  const float* f_R = nullptr;
+  const float* f_nbc = nullptr;
+  const float* f_half = nullptr;
   int freq_step = 0;
 };
 

@@ -444,7 +444,8 @@ __device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b
 // scale (the far wings of the line far from the sources).
 constexpr float kTinyJ = 1e-30f;
 // share of the domain energy above which a (cell, bin) pair enters the FP32
-// realisability diagnostics
+// realisability diagnostics (the reduction of each substep stores
+// kActiveShare E / unit for the next one)
 constexpr double kActiveShare = 1e-8;
 
 // Levermore closure in the cancellation-free FP32 form (see closure()).
@@ -555,13 +556,13 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
   // realisability is checked on (cell, bin) pairs holding at least kActiveShare
   // of the domain energy of the previous substep (FP32 rounding makes |H|/J
   // meaningless far below a bin plane's scale)
-  const double e_prev = v.acc[8], e_unit = v.acc[13];
+  // J dnu_k above thr = kActiveShare E_prev / unit (set by the previous substep's reduction)
+  const float thr = float(v.acc[14]);
   for (int i = tid; i < nb; i += NT) {
-    tH[i] = float(v.t_H[i]);
-    tD[i] = float(v.t_dnu[i]);
-    tG[i] = float(v.t_gem[i] / v.gem_max);
-    const double ja = kActiveShare * e_prev / (e_unit * v.t_dnu[i]);
-    tA[i] = float(fmax(fmin(ja, 1e30), 1e-30));
+    tH[i] = v.f_H[i];
+    tD[i] = v.f_dnu[i];
+    tG[i] = v.f_G[i];
+    tA[i] = fmaxf(thr, 1e-30f) / v.f_dnu[i];
   }
   for (int idx = tid; idx < QX * QY; idx += NT) {
     const int lx = idx % QX, ly = idx / QX;
@@ -824,20 +825,30 @@ __device__ __forceinline__ void freq_block(const DeviceView& v, int blk) {
   T* td = tabs + 4 * nb;
   I* tdi = reinterpret_cast<I*>(tabs_raw + 5 * nb);  // dnu_k in the elimination type
   I* tact = reinterpret_cast<I*>(tabs_raw + 6 * nb);  // J above which |H|/J is checked
-  const double e_prev = v.acc[8], e_unit = v.acc[13];
-  for (int i = threadIdx.x; i < nb; i += NT) {
-    if constexpr (sizeof(F) == 4) {
-      const double ja = kActiveShare * e_prev / (e_unit * v.t_dnu[i]);
-      tact[i] = I(fmax(fmin(ja, 1e30), 1e-30));
-    } else {
-      tact[i] = I(0);
+  if constexpr (sizeof(F) == 4) {
+    const float thr = float(v.acc[14]);
+    for (int i = threadIdx.x; i < nb; i += NT) {
+      tact[i] = I(fmaxf(thr, 1e-30f) / v.f_dnu[i]);
+      tH[i] = v.f_H[i];
+      tR[i] = v.f_R[i];
+      tn[i] = v.f_nbc[i];
+      th[i] = v.f_half[i];
+      td[i] = v.f_dnu[i];
+      if constexpr (sizeof(I) == 4)
+        tdi[i] = v.f_dnu[i];
+      else
+        tdi[i] = v.t_dnu[i];
     }
-    tH[i] = T(v.t_H[i]);
-    tR[i] = T(v.t_R[i]);
-    tn[i] = T(v.t_nbc[i]);
-    th[i] = T(v.t_half[i]);
-    td[i] = T(v.t_dnu[i]);
-    tdi[i] = I(v.t_dnu[i]);
+  } else {
+    for (int i = threadIdx.x; i < nb; i += NT) {
+      tact[i] = I(0);
+      tH[i] = T(v.t_H[i]);
+      tR[i] = T(v.t_R[i]);
+      tn[i] = T(v.t_nbc[i]);
+      th[i] = T(v.t_half[i]);
+      td[i] = T(v.t_dnu[i]);
+      tdi[i] = I(v.t_dnu[i]);
+    }
   }
   __syncthreads();
 
@@ -1071,15 +1082,17 @@ __device__ __forceinline__ void freq_block_bulk(const DeviceView& v, int blk) {
   I* tdi = reinterpret_cast<I*>(tabs_raw + 5 * nb);
   I* tact = reinterpret_cast<I*>(tabs_raw + 6 * nb);
   const int tid = threadIdx.x;
-  const double e_prev = v.acc[8], e_unit = v.acc[13];
+  const float thr = float(v.acc[14]);
   for (int i = tid; i < nb; i += NT) {
-    tH[i] = T(v.t_H[i]);
-    tR[i] = T(v.t_R[i]);
-    tn[i] = T(v.t_nbc[i]);
-    th[i] = T(v.t_half[i]);
-    tdi[i] = I(v.t_dnu[i]);
-    const double ja = kActiveShare * e_prev / (e_unit * v.t_dnu[i]);
-    tact[i] = I(fmax(fmin(ja, 1e30), 1e-30));
+    tH[i] = v.f_H[i];
+    tR[i] = v.f_R[i];
+    tn[i] = v.f_nbc[i];
+    th[i] = v.f_half[i];
+    if constexpr (sizeof(I) == 4)
+      tdi[i] = v.f_dnu[i];
+    else
+      tdi[i] = v.t_dnu[i];
+    tact[i] = I(fmaxf(thr, 1e-30f) / v.f_dnu[i]);
   }
   if (tid == 0) {
     failed = 0;

@@ -168,6 +168,7 @@ __device__ __forceinline__ void finalize_body(const double* partT, int nT, const
       acc[10] = 0.0;
       acc[11] = 0.0;
       acc[12] = acc[8];
+      acc[14] = 1e-8 * tot[kSlotEnergy];
     } else {
       kahan_add(acc + 0, u * tot[kSlotEmitted]);
       kahan_add(acc + 2, u * tot[kSlotAbsorbed]);
@@ -177,6 +178,7 @@ __device__ __forceinline__ void finalize_body(const double* partT, int nT, const
       acc[9] = tot[kSlotMaxF];
       acc[10] = tot[kSlotBad];
       acc[11] += 1.0;
+      acc[14] = 1e-8 * tot[kSlotEnergy];  // FP32 realisability threshold on J dnu_k
     }
   }
 }
