@@ -239,6 +239,17 @@ typedef struct {
  * durations per kernel since the last reset and optionally resets.
  */
 int lym1_profile_enable(lym1_ctx *ctx, int on);
+
+/*
+ * Test hook for the failure path of the bounded waits.  The next
+ * frequency-step launch arms one bulk-copy stage without issuing its copies,
+ * so its wait runs out after ~2 s.  The kernel records the expiry and returns,
+ * and the next lym1_synchronize reports LYM1_ETIMEOUT once and clears it.  The
+ * state of that substep is not meaningful; the context stays usable.  Only
+ * for FP32 contexts whose cell count is a multiple of 4 (LYM1_EINVAL
+ * otherwise).
+ */
+int lym1_debug_expire_wait(lym1_ctx *ctx);
 int lym1_profile_read(lym1_ctx *ctx, lym1_profile *out, int reset);
 
 /*

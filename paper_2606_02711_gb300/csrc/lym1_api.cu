@@ -332,10 +332,13 @@ int batch_launch_timed(lym1_batch* b, lym1_ctx* c) {
   return LYM1_OK;
 }
 
+// reports an expired bounded wait once, then clears the status words
 int device_status(lym1_ctx* c) {
-  int st = 0;
-  LYM1_TRY(cudaMemcpy(&st, c->status, sizeof st, cudaMemcpyDeviceToHost));
-  return st != 0 ? LYM1_ETIMEOUT : LYM1_OK;
+  int st[2] = {0, 0};
+  LYM1_TRY(cudaMemcpy(st, c->status, sizeof st, cudaMemcpyDeviceToHost));
+  if (st[0] == 0 && st[1] == 0) return LYM1_OK;
+  LYM1_TRY(cudaMemset(c->status, 0, 2 * sizeof(int)));
+  return st[0] != 0 ? LYM1_ETIMEOUT : LYM1_OK;
 }
 
 void batch_free(lym1_batch* b) {
@@ -878,6 +881,15 @@ void lym1_batch_destroy(lym1_batch* b) {
   cudaStreamSynchronize(b->bs);
   batch_free(b);
   delete b;
+}
+
+int lym1_debug_expire_wait(lym1_ctx* c) {
+  if (!c) return LYM1_EINVAL;
+  if (c->precision < LYM1_MIXED || (c->nc & 3) != 0 || c->gray || !c->freq_step) return LYM1_EINVAL;
+  const int one = 1;
+  LYM1_TRY(cudaMemcpyAsync(c->status + 1, &one, sizeof one, cudaMemcpyHostToDevice, c->stream));
+  LYM1_TRY(cudaStreamSynchronize(c->stream));
+  return LYM1_OK;
 }
 
 int lym1_profile_enable(lym1_ctx* c, int on) {

@@ -1151,8 +1151,16 @@ __device__ __forceinline__ void freq_block_bulk(const DeviceView& v, int blk) {
     }
   };
 
+  // status[1] == 1 (set only by lym1_debug_expire_wait) arms stage 0 without
+  // issuing its copies, so that its bounded wait runs out
+  const bool expire = v.status[1] == 1;
   if (tid == 0)
-    for (int k = 0; k < nb && k < D; ++k) issue_fwd(k);
+    for (int k = 0; k < nb && k < D; ++k) {
+      if (k == 0 && expire)
+        mbar_expect_tx(&barF[0], 3u * rowb);
+      else
+        issue_fwd(k);
+    }
   // forward sweep, one bin behind the data: iteration k forms the
   // coefficients of bin k and eliminates row k-1
   F Pp = F(0), ap = F(0), ep = F(0);

@@ -98,6 +98,7 @@ SIGNATURES = {
     "lym1_batch_substeps": (C.c_int, [C.c_void_p, C.c_int]),
     "lym1_batch_grid": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "lym1_batch_destroy": (None, [C.c_void_p]),
+    "lym1_debug_expire_wait": (C.c_int, [C.c_void_p]),
     "lym1_energy_noalloc": (C.c_int, [_PD, _PD, C.c_int, C.c_longlong, C.c_double, _PD,
                                       C.c_void_p]),
 }
@@ -277,6 +278,14 @@ class Context:
 
     def synchronize(self):
         _check(lib().lym1_synchronize(self.handle), "lym1_synchronize")
+
+    def synchronize_status(self) -> int:
+        """``lym1_synchronize`` returning the status code instead of raising."""
+        return lib().lym1_synchronize(self.handle)
+
+    def debug_expire_wait(self):
+        """Test hook: make the next frequency-step launch's bounded wait run out."""
+        _check(lib().lym1_debug_expire_wait(self.handle), "lym1_debug_expire_wait")
 
     def profile_enable(self, on=True):
         _check(lib().lym1_profile_enable(self.handle, int(bool(on))), "lym1_profile_enable")
