@@ -1,7 +1,7 @@
 /*
  * lym1_oracle.c -- plain, slow FP64 reference ("oracle") for one substep of the
- * Lydion M1 method for Lyman-alpha transfer on a 2D Cartesian grid
- * (arXiv 2606.02711).
+ * Lydion M1 method for Lyman-alpha transfer on a 2D Cartesian grid or an
+ * axisymmetric (R, Z) grid (arXiv 2606.02711).
  *
  * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
  * benchmark's CPU-baseline arm may load this file's library.  The GPU product
@@ -43,6 +43,17 @@
  *   - phi and chi are evaluated with this file's own exp/expm1 (Cody-Waite
  *     argument reduction + Taylor polynomial), not lookup tables.
  *   - no FMA contraction: build with -ffp-contract=off.
+ *   - axisymmetric (R, Z) geometry (the paper's test and RHD set-ups, Sec. 4):
+ *     finite volumes per radian with R faces of area R dZ and Z faces of area
+ *     (R+^2 - R-^2)/2; the R component of div K carries the hoop source
+ *     K_phiphi <1/R> with <1/R> = dR dZ / Vol, which makes a uniform isotropic
+ *     field exactly steady; the work term and step 3's D:grad u add
+ *     D_phiphi <u_R/R>, with <u_R/R> from the two R-face velocities; the face
+ *     optical depth uses the centroid-to-face distances (Sec. 2.1 step 1);
+ *     the axis and the midplane are mirrors (H_R, u_R flip across the axis,
+ *     H_Z, u_Z across the midplane), the outer edges outflow; MinMod slopes
+ *     use cell indices (uniform geometric centres); the cell luminosity is
+ *     emitted into the full ring volume 2 pi Vol.
  *
  * Parity pins (tests/test_oracle_*.py): printed N_nu = 194, sigma0 and a_v
  * scalings, Dawson vs scipy, <H> vs quadrature, closure and eps limits,
@@ -317,6 +328,8 @@ typedef struct {
     const double *ux;    /* [ny][nx] cm/s */
     const double *uy;    /* [ny][nx] cm/s */
     const double *lum;   /* [ny][nx] erg/s emitted in the cell */
+    int geometry;        /* 0: 2D Cartesian slab; 1: axisymmetric cylindrical (R = x, Z = y) with
+                            the axis at R = 0 and the midplane at Z = 0 mirrored */
 } lym1o_problem;
 
 typedef struct {
@@ -335,6 +348,12 @@ typedef struct {
     double dnuD, a_v, sigma0, hkT, eta, dt_cfl;
     double *dnu, *nubar, *Havg, *gem, *Rk, *half;
     double *alpha, *gxx, *gyy, *gsh;
+    /* cylindrical geometry (per radian): R-face areas AR[nx+1], Z-face areas
+     * AZ[nx], volumes Vol[nx], centroids Rbar[nx], centroid-to-face distances
+     * dlL/dlR[nx+1] on the two sides of each R face, <1/R> = dR dZ / Vol,
+     * full volumes 2 pi Vol, the emission factor w_k / (4 pi dnu_k) and
+     * <u_R/R> per cell */
+    double *AR, *AZ, *Vol, *Rbar, *dlL, *dlR, *invR, *V2pi, *gemc, *gphi;
 } lym1o_ctx;
 
 static int o_cl(int i, int n) { return i < 0 ? 0 : (i >= n ? n - 1 : i); }
@@ -344,7 +363,21 @@ void lym1o_destroy(lym1o_ctx *c)
     if (!c) return;
     free(c->dnu); free(c->nubar); free(c->Havg); free(c->gem); free(c->Rk); free(c->half);
     free(c->alpha); free(c->gxx); free(c->gyy); free(c->gsh);
+    free(c->AR); free(c->AZ); free(c->Vol); free(c->Rbar); free(c->dlL); free(c->dlR);
+    free(c->invR); free(c->V2pi); free(c->gemc); free(c->gphi);
     free(c);
+}
+
+/* index along one axis with the low side mirrored (axis R = 0 or midplane
+ * Z = 0) and the high side copied (outflow); *flip = 1 for a mirrored cell */
+static int o_mir(int i, int n, int *flip)
+{
+    if (i < 0) {
+        *flip = 1;
+        return -1 - i;
+    }
+    *flip = 0;
+    return i >= n ? n - 1 : i;
 }
 
 lym1o_ctx *lym1o_create(const lym1o_problem *p)
@@ -372,6 +405,7 @@ lym1o_ctx *lym1o_create(const lym1o_problem *p)
     c->half = malloc(nb * sizeof(double));
     double V = (p->dx * p->dx) * p->dx;
     double fourpiV = (4.0 * O_PI) * V;
+    size_t nc = (size_t)nx * ny;
     if (p->gray) {
         c->dnu[0] = 1.0;
         c->nubar[0] = O_NU_LYA;
@@ -390,16 +424,77 @@ lym1o_ctx *lym1o_create(const lym1o_problem *p)
         }
     }
     free(dnu); free(nub); free(Hv); free(w);
-    size_t nc = (size_t)nx * ny;
     c->alpha = malloc(nc * sizeof(double));
     c->gxx = malloc(nc * sizeof(double));
     c->gyy = malloc(nc * sizeof(double));
     c->gsh = malloc(nc * sizeof(double));
     double umax = 0.0;
+    if (p->geometry == 1) {
+        const double dx = p->dx;
+        c->AR = malloc((nx + 1) * sizeof(double));
+        c->dlL = malloc((nx + 1) * sizeof(double));
+        c->dlR = malloc((nx + 1) * sizeof(double));
+        c->AZ = malloc(nx * sizeof(double));
+        c->Vol = malloc(nx * sizeof(double));
+        c->Rbar = malloc(nx * sizeof(double));
+        c->invR = malloc(nx * sizeof(double));
+        c->V2pi = malloc(nx * sizeof(double));
+        c->gphi = malloc(nc * sizeof(double));
+        c->gemc = malloc(nb * sizeof(double));
+        for (int i = 0; i < nx; ++i) {
+            double Rm = i * dx, Rp = (i + 1) * dx;
+            c->AZ[i] = 0.5 * (Rp * Rp - Rm * Rm);
+            c->Vol[i] = c->AZ[i] * dx;
+            c->Rbar[i] = (2.0 / 3.0) * ((Rp * Rp * Rp - Rm * Rm * Rm) / (Rp * Rp - Rm * Rm));
+            c->invR[i] = (dx * dx) / c->Vol[i];
+            c->V2pi[i] = (2.0 * O_PI) * c->Vol[i];
+        }
+        for (int i = 0; i <= nx; ++i) {
+            double Rf = i * dx;
+            c->AR[i] = Rf * dx;
+            double left = (i == 0) ? -c->Rbar[0] : c->Rbar[i - 1];
+            double right = (i == nx) ? c->Rbar[nx - 1] + dx : c->Rbar[i];
+            c->dlL[i] = Rf - left;
+            c->dlR[i] = right - Rf;
+        }
+        if (p->gray) {
+            c->gemc[0] = 1.0 / (4.0 * O_PI);
+        } else {
+            /* j_k = (L_cell / (2 pi Vol)) w_k / (4 pi dnu_k) */
+            double *t1 = malloc(N * sizeof(double)), *t2 = malloc(N * sizeof(double));
+            double *t3 = malloc(N * sizeof(double)), *t4 = malloc(N * sizeof(double));
+            lym1o_bin_tables(N, p->edges, p->T, t1, t2, t3, t4);
+            for (int k = 0; k < N; ++k) c->gemc[k] = t4[k] / ((4.0 * O_PI) * t1[k]);
+            free(t1); free(t2); free(t3); free(t4);
+        }
+    }
     for (int j = 0; j < ny; ++j)
         for (int i = 0; i < nx; ++i) {
             size_t id = (size_t)j * nx + i;
             c->alpha[id] = p->n_hi[id] * c->sigma0;
+            if (p->geometry == 1) {
+                /* mirrored ghosts: across the axis u_R flips, across the midplane u_Z flips */
+                const double *ux = p->ux, *uy = p->uy;
+                int fm, fp, gm, gp;
+                int im = o_mir(i - 1, nx, &fm), ip = o_mir(i + 1, nx, &fp);
+                int jm = o_mir(j - 1, ny, &gm), jp = o_mir(j + 1, ny, &gp);
+                double uRm = ux[(size_t)j * nx + im] * (fm ? -1.0 : 1.0);
+                double uRp = ux[(size_t)j * nx + ip];
+                double uZm = uy[(size_t)jm * nx + i] * (gm ? -1.0 : 1.0);
+                double uZp = uy[(size_t)jp * nx + i];
+                double uZl = uy[(size_t)j * nx + im], uZr = uy[(size_t)j * nx + ip];
+                double uRd = ux[(size_t)jm * nx + i], uRu = ux[(size_t)jp * nx + i];
+                double h2 = 2.0 * p->dx;
+                c->gxx[id] = (uRp - uRm) / h2;
+                c->gyy[id] = (uZp - uZm) / h2;
+                c->gsh[id] = (uRu - uRd) / h2 + (uZr - uZl) / h2;
+                /* <u_R / R> from the face velocities (mean of the two cells) */
+                double fL = 0.5 * (uRm + ux[id]), fR = 0.5 * (ux[id] + uRp);
+                c->gphi[id] = (fR + fL) / ((i + 1) * p->dx + i * p->dx);
+                double um = sqrt(ux[id] * ux[id] + uy[id] * uy[id]);
+                if (um > umax) umax = um;
+                continue;
+            }
             const double *ux = p->ux, *uy = p->uy;
             size_t xm = (size_t)j * nx + o_cl(i - 1, nx), xp = (size_t)j * nx + o_cl(i + 1, nx);
             size_t ym = (size_t)o_cl(j - 1, ny) * nx + i, yp = (size_t)o_cl(j + 1, ny) * nx + i;
@@ -487,7 +582,8 @@ static o_prim o_make_prim(double J, double Hn, double Ht)
  * the normal.  Returns the flux of J (FJ), of H_n (Fn) and of H_t (Ft).
  */
 static void o_face(o_prim qm, o_prim q0, o_prim q1, o_prim q2, double aF0, double aF1,
-                   double un0, double un1, double half_dx, double *FJ, double *Fn, double *Ft)
+                   double un0, double un1, double dl0, double dl1, double *FJ, double *Fn,
+                   double *Ft)
 {
     /* MinMod-limited linear reconstruction of J, f_n, f_t */
     double sJ0 = o_minmod(q0.J - qm.J, q1.J - q0.J), sJ1 = o_minmod(q1.J - q0.J, q2.J - q1.J);
@@ -513,8 +609,8 @@ static void o_face(o_prim qm, o_prim q0, o_prim q1, o_prim q2, double aF0, doubl
     o_closure(fnL, ftL, &DnnL, &DntL, &DttL);
     o_closure(fnR, ftR, &DnnR, &DntR, &DttR);
     double KnnL = DnnL * JL, KntL = DntL * JL, KnnR = DnnR * JR, KntR = DntR * JR;
-    /* flux optical depth (Cartesian: centroid at the centre) and eps */
-    double tau = aF0 * half_dx + aF1 * half_dx;
+    /* flux optical depth: alpha_F times the centroid-to-face distance on each side */
+    double tau = aF0 * dl0 + aF1 * dl1;
     double eps = (0.2 + tau) / ((0.2 + tau) + tau * tau);
     double dif = (tau > 0.0) ? ((1.0 - eps) * (q1.J - q0.J)) / (3.0 * tau) : 0.0;
     /* corrected GLF flux for J, modified GLF flux for K */
@@ -543,7 +639,8 @@ void lym1o_face_flux(const double *J4, const double *Hn4, const double *Ht4, dou
 {
     o_prim q[4];
     for (int m = 0; m < 4; ++m) q[m] = o_make_prim(J4[m], Hn4[m], Ht4[m]);
-    o_face(q[0], q[1], q[2], q[3], aF0, aF1, un0, un1, 0.5 * dx, &out3[0], &out3[1], &out3[2]);
+    o_face(q[0], q[1], q[2], q[3], aF0, aF1, un0, un1, 0.5 * dx, 0.5 * dx, &out3[0], &out3[1],
+           &out3[2]);
 }
 
 /* ======================================================================
@@ -698,10 +795,15 @@ double lym1o_energy(const lym1o_ctx *c, const double *J) { return o_energy(c, J)
  * One substep of length dt: state (J, Hx, Hy) [k][y][x] -> (Jo, Hxo, Hyo),
  * force (fx, fy) [y][x] in dyn cm^-3.  Input and output may not alias.
  * ====================================================================== */
+int lym1o_substep_cyl(const lym1o_ctx *c, double dt, const double *J, const double *Hx,
+                      const double *Hy, double *Jo, double *Hxo, double *Hyo, double *fx,
+                      double *fy, lym1o_diag *dg);
+
 int lym1o_substep(const lym1o_ctx *c, double dt, const double *J, const double *Hx,
                   const double *Hy, double *Jo, double *Hxo, double *Hyo, double *fx,
                   double *fy, lym1o_diag *dg)
 {
+    if (c->p.geometry == 1) return lym1o_substep_cyl(c, dt, J, Hx, Hy, Jo, Hxo, Hyo, fx, fy, dg);
     const lym1o_problem *p = &c->p;
     const int nx = p->nx, ny = p->ny, nb = c->nb;
     const size_t nc = (size_t)nx * ny;
@@ -742,8 +844,8 @@ int lym1o_substep(const lym1o_ctx *c, double dt, const double *J, const double *
                 o_prim q1 = o_make_prim(Jk[i1], Hxk[i1], Hyk[i1]);
                 o_prim q2 = o_make_prim(Jk[i2], Hxk[i2], Hyk[i2]);
                 size_t f = (size_t)j * (nx + 1) + i;
-                o_face(qm, q0, q1, q2, AF(i0), AF(i1), p->ux[i0], p->ux[i1], half_dx, &FJx[f],
-                       &FHxx[f], &FHyx[f]);
+                o_face(qm, q0, q1, q2, AF(i0), AF(i1), p->ux[i0], p->ux[i1], half_dx, half_dx,
+                       &FJx[f], &FHxx[f], &FHyx[f]);
             }
         /* y faces: face j sits between rows j-1 and j, j = 0..ny */
 #pragma omp parallel for schedule(static)
@@ -756,8 +858,8 @@ int lym1o_substep(const lym1o_ctx *c, double dt, const double *J, const double *
                 o_prim q1 = o_make_prim(Jk[i1], Hyk[i1], Hxk[i1]);
                 o_prim q2 = o_make_prim(Jk[i2], Hyk[i2], Hxk[i2]);
                 size_t f = (size_t)j * nx + i;
-                o_face(qm, q0, q1, q2, AF(i0), AF(i1), p->uy[i0], p->uy[i1], half_dx, &FJy[f],
-                       &FHyy[f], &FHxy[f]);
+                o_face(qm, q0, q1, q2, AF(i0), AF(i1), p->uy[i0], p->uy[i1], half_dx, half_dx,
+                       &FJy[f], &FHyy[f], &FHxy[f]);
             }
         /* A3 explicit update, A4 implicit source, A5 force accumulation */
 #pragma omp parallel for schedule(static)
@@ -895,6 +997,230 @@ int lym1o_substep(const lym1o_ctx *c, double dt, const double *J, const double *
             double x = (i + 0.5) * dx - cx, y = (j + 0.5) * dx - cy, r = sqrt(x * x + y * y);
             o_kadd(&fa, sqrt(fx[id] * fx[id] + fy[id] * fy[id]) * V);
             if (r > 0.0) o_kadd(&fr, ((fx[id] * x + fy[id] * y) / r) * V);
+        }
+    d.force_abs = o_kval(&fa);
+    d.force_radial = o_kval(&fr);
+    if (dg) *dg = d;
+    free(FJx); free(FHxx); free(FHyx); free(FJy); free(FHxy); free(FHyy); free(Wk); free(ax); free(ay);
+    return 0;
+}
+
+
+/* ======================================================================
+ * One substep in axisymmetric cylindrical geometry (R = x index, Z = y
+ * index): finite volumes per radian, R faces of area R dZ, Z faces of area
+ * (R+^2 - R-^2)/2, the hoop-stress source +K_phiphi <1/R> in the H_R
+ * equation (the R component of div K in cylindrical coordinates), the
+ * D_phiphi <u_R/R> parts of the work term and of D:grad(u) in step 3 (App. A),
+ * mirrored ghosts at R = 0 and Z = 0 (H_R and u_R flip across the axis, H_Z
+ * and u_Z across the midplane), outflow ghosts outside.
+ * ====================================================================== */
+int lym1o_substep_cyl(const lym1o_ctx *c, double dt, const double *J, const double *Hx,
+                      const double *Hy, double *Jo, double *Hxo, double *Hyo, double *fx,
+                      double *fy, lym1o_diag *dg)
+{
+    const lym1o_problem *p = &c->p;
+    const int nx = p->nx, ny = p->ny, nb = c->nb;
+    const size_t nc = (size_t)nx * ny;
+    const double dx = p->dx, half_dx = 0.5 * dx, cdt = p->c_tilde * dt;
+    lym1o_diag d;
+    memset(&d, 0, sizeof d);
+    o_ksum s_e0 = {0, 0}, s_e1 = {0, 0}, s_em = {0, 0}, s_ab = {0, 0}, s_out = {0, 0}, s_wk = {0, 0};
+    for (int k = 0; k < nb; ++k)
+        for (size_t id = 0; id < nc; ++id)
+            o_kadd(&s_e0, c->V2pi[id % nx] * (c->dnu[k] * J[(size_t)k * nc + id]));
+    double *FJx = malloc((size_t)(nx + 1) * ny * sizeof(double));
+    double *FHxx = malloc((size_t)(nx + 1) * ny * sizeof(double));
+    double *FHyx = malloc((size_t)(nx + 1) * ny * sizeof(double));
+    double *FJy = malloc((size_t)nx * (ny + 1) * sizeof(double));
+    double *FHxy = malloc((size_t)nx * (ny + 1) * sizeof(double));
+    double *FHyy = malloc((size_t)nx * (ny + 1) * sizeof(double));
+    double *Wk = malloc(nc * sizeof(double));
+    double *ax = calloc(nc, sizeof(double)), *ay = calloc(nc, sizeof(double));
+
+    for (int k = 0; k < nb; ++k) {
+        const double *Jk = J + (size_t)k * nc, *Hxk = Hx + (size_t)k * nc, *Hyk = Hy + (size_t)k * nc;
+        const double Hk = c->Havg[k];
+#define AFC(id) (c->alpha[id] * Hk + p->rho_d[id] * p->kappa_F)
+        /* R faces: face i between cells i-1 and i */
+#pragma omp parallel for schedule(static)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i <= nx; ++i) {
+                int fl[4];
+                int ii[4];
+                for (int m = 0; m < 4; ++m) ii[m] = o_mir(i - 2 + m, nx, &fl[m]);
+                o_prim q[4];
+                double ur[2];
+                for (int m = 0; m < 4; ++m) {
+                    size_t id = (size_t)j * nx + ii[m];
+                    double sg = fl[m] ? -1.0 : 1.0;
+                    q[m] = o_make_prim(Jk[id], Hxk[id] * sg, Hyk[id]);
+                    if (m == 1 || m == 2) ur[m - 1] = p->ux[id] * sg;
+                }
+                size_t i0 = (size_t)j * nx + ii[1], i1 = (size_t)j * nx + ii[2];
+                size_t f = (size_t)j * (nx + 1) + i;
+                o_face(q[0], q[1], q[2], q[3], AFC(i0), AFC(i1), ur[0], ur[1], c->dlL[i], c->dlR[i],
+                       &FJx[f], &FHxx[f], &FHyx[f]);
+            }
+        /* Z faces: face j between rows j-1 and j */
+#pragma omp parallel for schedule(static)
+        for (int j = 0; j <= ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                int fl[4];
+                int jj[4];
+                for (int m = 0; m < 4; ++m) jj[m] = o_mir(j - 2 + m, ny, &fl[m]);
+                o_prim q[4];
+                double uz[2];
+                for (int m = 0; m < 4; ++m) {
+                    size_t id = (size_t)jj[m] * nx + i;
+                    double sg = fl[m] ? -1.0 : 1.0;
+                    q[m] = o_make_prim(Jk[id], Hyk[id] * sg, Hxk[id]);
+                    if (m == 1 || m == 2) uz[m - 1] = p->uy[id] * sg;
+                }
+                size_t i0 = (size_t)jj[1] * nx + i, i1 = (size_t)jj[2] * nx + i;
+                size_t f = (size_t)j * nx + i;
+                o_face(q[0], q[1], q[2], q[3], AFC(i0), AFC(i1), uz[0], uz[1], half_dx, half_dx,
+                       &FJy[f], &FHyy[f], &FHxy[f]);
+            }
+#pragma omp parallel for schedule(static)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                size_t id = (size_t)j * nx + i, kid = (size_t)k * nc + id;
+                o_prim q = o_make_prim(Jk[id], Hxk[id], Hyk[id]);
+                double fxc = q.fn, fyc = q.ft, f2 = fxc * fxc + fyc * fyc;
+                if (f2 > 1.0) {
+                    double r = sqrt(f2);
+                    fxc = fxc / r;
+                    fyc = fyc / r;
+                }
+                double Dxx, Dxy, Dyy;
+                o_closure(fxc, fyc, &Dxx, &Dxy, &Dyy);
+                double f2c = fxc * fxc + fyc * fyc;
+                double chi = (3.0 + 4.0 * f2c) / (5.0 + 2.0 * sqrt(4.0 - 3.0 * f2c));
+                double Dpp = (1.0 - chi) / 2.0;
+                double W = (((Dxx * Jk[id]) * c->gxx[id] + (Dyy * Jk[id]) * c->gyy[id]) +
+                            (Dxy * Jk[id]) * c->gsh[id]) +
+                           (Dpp * Jk[id]) * c->gphi[id];
+                Wk[id] = W;
+                size_t fxl = (size_t)j * (nx + 1) + i, fyl = (size_t)j * nx + i;
+                double divJ = ((c->AR[i + 1] * FJx[fxl + 1] - c->AR[i] * FJx[fxl]) +
+                               c->AZ[i] * (FJy[fyl + nx] - FJy[fyl])) / c->Vol[i];
+                double divHx = ((c->AR[i + 1] * FHxx[fxl + 1] - c->AR[i] * FHxx[fxl]) +
+                                c->AZ[i] * (FHxy[fyl + nx] - FHxy[fyl])) / c->Vol[i] -
+                               (Dpp * Jk[id]) * c->invR[i];
+                double divHy = ((c->AR[i + 1] * FHyx[fxl + 1] - c->AR[i] * FHyx[fxl]) +
+                                c->AZ[i] * (FHyy[fyl + nx] - FHyy[fyl])) / c->Vol[i];
+                double J1 = Jk[id] - cdt * (divJ + W / O_C);
+                double Hx1 = Hxk[id] - cdt * divHx;
+                double Hy1 = Hyk[id] - cdt * divHy;
+                double aH = c->alpha[id] * Hk;
+                double kap = p->rho_d[id] * p->kappa_abs + p->p_d[id] * aH;
+                double aF = aH + p->rho_d[id] * p->kappa_F;
+                double js = (p->lum[id] / c->V2pi[i]) * c->gemc[k];
+                double J2 = (J1 + cdt * js) / (1.0 + cdt * kap);
+                double Hx2 = Hx1 / (1.0 + cdt * aF);
+                double Hy2 = Hy1 / (1.0 + cdt * aF);
+                Jo[kid] = J2;
+                Hxo[kid] = Hx2;
+                Hyo[kid] = Hy2;
+                ax[id] = ax[id] + c->dnu[k] * (Hx1 - Hx2);
+                ay[id] = ay[id] + c->dnu[k] * (Hy1 - Hy2);
+            }
+        for (size_t id = 0; id < nc; ++id) {
+            size_t kid = (size_t)k * nc + id;
+            int i = (int)(id % nx);
+            double aH = c->alpha[id] * Hk;
+            double kap = p->rho_d[id] * p->kappa_abs + p->p_d[id] * aH;
+            double js = (p->lum[id] / c->V2pi[i]) * c->gemc[k];
+            o_kadd(&s_em, c->V2pi[i] * (c->dnu[k] * (cdt * js)));
+            o_kadd(&s_ab, c->V2pi[i] * (c->dnu[k] * (cdt * (kap * Jo[kid]))));
+            o_kadd(&s_wk, c->V2pi[i] * (c->dnu[k] * (cdt * (Wk[id] / O_C))));
+        }
+        /* outflow through the outer R and Z faces (the axis and midplane are mirrors) */
+        for (int j = 0; j < ny; ++j)
+            o_kadd(&s_out, (2.0 * O_PI) * (c->AR[nx] * (c->dnu[k] * (cdt * FJx[(size_t)j * (nx + 1) + nx]))));
+        for (int i = 0; i < nx; ++i)
+            o_kadd(&s_out, (2.0 * O_PI) * (c->AZ[i] * (c->dnu[k] * (cdt * FJy[(size_t)ny * nx + i]))));
+#undef AFC
+    }
+    const double fcoef = (4.0 * O_PI) / ((O_C * p->c_tilde) * dt);
+    for (size_t id = 0; id < nc; ++id) {
+        fx[id] = fcoef * ax[id];
+        fy[id] = fcoef * ay[id];
+    }
+    if (!p->gray && p->freq_step) {
+        const double Kc0 = 0.5 * (c->dnuD * c->dnuD);
+        double *nbc = malloc(nb * sizeof(double));
+        for (int k = 0; k < nb; ++k) nbc[k] = c->nubar[k] / O_C;
+#pragma omp parallel
+        {
+            double *scr = malloc((size_t)6 * nb * sizeof(double));
+            double *Jin = malloc(nb * sizeof(double)), *Jn = malloc(nb * sizeof(double));
+            double *DdU = malloc(nb * sizeof(double));
+#pragma omp for schedule(static)
+            for (long long idl = 0; idl < (long long)nc; ++idl) {
+                size_t id = (size_t)idl;
+                if (!(c->alpha[id] > 0.0)) continue;
+                for (int k = 0; k < nb; ++k) {
+                    size_t kid = (size_t)k * nc + id;
+                    o_prim q = o_make_prim(Jo[kid], Hxo[kid], Hyo[kid]);
+                    double fxc = q.fn, fyc = q.ft, f2 = fxc * fxc + fyc * fyc;
+                    if (f2 > 1.0) {
+                        double r = sqrt(f2);
+                        fxc = fxc / r;
+                        fyc = fyc / r;
+                    }
+                    double Dxx, Dxy, Dyy;
+                    o_closure(fxc, fyc, &Dxx, &Dxy, &Dyy);
+                    double f2c = fxc * fxc + fyc * fyc;
+                    double chi = (3.0 + 4.0 * f2c) / (5.0 + 2.0 * sqrt(4.0 - 3.0 * f2c));
+                    double Dpp = (1.0 - chi) / 2.0;
+                    DdU[k] = ((Dxx * c->gxx[id] + Dyy * c->gyy[id]) + Dxy * c->gsh[id]) +
+                             Dpp * c->gphi[id];
+                    Jin[k] = Jo[kid];
+                }
+                o_freq_cell(nb, c->dnu, c->half, c->Havg, c->Rk, nbc, Kc0 * c->alpha[id], DdU, cdt,
+                            Jin, Jn, scr);
+                for (int k = 0; k < nb; ++k) {
+                    size_t kid = (size_t)k * nc + id;
+                    double ratio = (Jin[k] > 0.0) ? Jn[k] / Jin[k] : 0.0;
+                    Jo[kid] = Jn[k];
+                    Hxo[kid] = ratio * Hxo[kid];
+                    Hyo[kid] = ratio * Hyo[kid];
+                }
+            }
+            free(scr); free(Jin); free(Jn); free(DdU);
+        }
+        free(nbc);
+    }
+    for (int k = 0; k < nb; ++k)
+        for (size_t id = 0; id < nc; ++id)
+            o_kadd(&s_e1, c->V2pi[id % nx] * (c->dnu[k] * Jo[(size_t)k * nc + id]));
+    const double eu = (4.0 * O_PI) / O_C;
+    d.e_before = eu * o_kval(&s_e0);
+    d.e_after = eu * o_kval(&s_e1);
+    d.emitted = eu * o_kval(&s_em);
+    d.absorbed = eu * o_kval(&s_ab);
+    d.outflow = eu * o_kval(&s_out);
+    d.work = eu * o_kval(&s_wk);
+    d.residual = (d.e_after - d.e_before) - (((d.emitted - d.absorbed) - d.outflow) - d.work);
+    double maxf = 0.0, nbad = 0.0;
+    for (int k = 0; k < nb; ++k)
+        for (size_t id = 0; id < nc; ++id) {
+            size_t kid = (size_t)k * nc + id;
+            double hn = sqrt(Hxo[kid] * Hxo[kid] + Hyo[kid] * Hyo[kid]);
+            if (Jo[kid] > 0.0 && hn / Jo[kid] > maxf) maxf = hn / Jo[kid];
+            if (hn > Jo[kid] * (1.0 + 1e-12) && hn > 0.0) nbad += 1.0;
+        }
+    d.max_f = maxf;
+    d.n_unrealisable = nbad;
+    o_ksum fa = {0, 0}, fr = {0, 0};
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            size_t id = (size_t)j * nx + i;
+            double R = (i + 0.5) * dx, Z = (j + 0.5) * dx, r = sqrt(R * R + Z * Z);
+            o_kadd(&fa, sqrt(fx[id] * fx[id] + fy[id] * fy[id]) * c->V2pi[i]);
+            o_kadd(&fr, ((fx[id] * R + fy[id] * Z) / r) * c->V2pi[i]);
         }
     d.force_abs = o_kval(&fa);
     d.force_radial = o_kval(&fr);

@@ -105,6 +105,7 @@ class Cloud:
     c_tilde: float = C_LIGHT
     cfl: float = 0.4
     substeps: int = 1
+    geometry: int = 0        # 0: 2D Cartesian slab; 1: axisymmetric (R = x, Z = y)
     meta: dict = field(default_factory=dict)
 
     @property
@@ -117,7 +118,7 @@ class Cloud:
                     rho_d=self.rho_d, p_d=self.p_d, ux=self.ux, uy=self.uy, lum=self.lum,
                     kappa_abs=self.kappa_abs, kappa_F=self.kappa_F, c_tilde=self.c_tilde,
                     cfl=self.cfl, gray=self.gray, recoil=self.recoil,
-                    freq_step=self.freq_step)
+                    freq_step=self.freq_step, geometry=self.geometry)
 
 
 def uniform_gray(nx=64, ny=64, box_pc=2.0, n_h=1e3, L_sun=1e6, name="uniform-gray"):
@@ -174,3 +175,69 @@ def poisson_arrivals(n=1000, rate=50.0, seed=7):
     """Seeded Poisson arrival times (s) for a request stream."""
     g = rng(seed)
     return np.cumsum(g.exponential(1.0 / rate, size=n))
+
+
+# Line-centre Lya cross-section at 1e4 K (cm^2), used only to turn a quoted
+# optical depth into a density; it scales as T^-1/2 through the Doppler width.
+SIGMA0_1E4K = 5.898e-14
+
+
+def _sigma0(T: float) -> float:
+    return SIGMA0_1E4K * math.sqrt(1.0e4 / T)
+
+
+def _rz_grid(n, R_cl, extent=1.1):
+    """Cell centres (R, Z) of an n x n axisymmetric grid covering [0, extent R_cl]^2."""
+    dx = extent * R_cl / n
+    c = (np.arange(n) + 0.5) * dx
+    R, Z = np.meshgrid(c, c)          # [ny][nx]: Z rows, R columns
+    vol = 2.0 * math.pi * 0.5 * (((np.arange(n) + 1) * dx) ** 2 - (np.arange(n) * dx) ** 2) * dx
+    return dx, R, Z, np.broadcast_to(vol, (n, n))
+
+
+def uniform_sphere(n=64, tau_cl=0.1, T=1.0e4, R_cl_pc=1.0, L_sun=1e6, gray=False, recoil=False,
+                   freq_step=True, sigma0=None, name="uniform-sphere"):
+    """Static dust-free uniform sphere in axisymmetric (R, Z) coordinates with
+    the midplane mirrored (Sec. 4.1, Test 1): line-centre optical depth
+    tau_cl = n_HI sigma0 R_cl inside r <= R_cl, vacuum outside, box 1.1 R_cl,
+    emission uniform per unit volume inside the sphere (the upper half emits
+    L/2 of a total L), c_tilde = c."""
+    R_cl = R_cl_pc * PC
+    dx, R, Z, vol = _rz_grid(n, R_cl)
+    inside = np.sqrt(R * R + Z * Z) <= R_cl
+    s0 = _sigma0(T) if sigma0 is None else sigma0
+    n_hi = np.where(inside, tau_cl / (s0 * R_cl), 0.0)
+    z = np.zeros((n, n))
+    lum = np.where(inside, vol, 0.0)
+    lum = lum * (0.5 * L_sun * L_SUN / lum.sum())
+    return Cloud(name, n, n, dx, n_hi, z.copy(), z.copy(), z.copy(), z.copy(), lum, T=T, gray=gray,
+                 recoil=recoil, freq_step=freq_step, kappa_abs=0.0, kappa_F=0.0, geometry=1,
+                 meta={"tau_cl": tau_cl, "R_cl": R_cl})
+
+
+def cone_cloud(n=256, tau_cl=1e8, tau_cone=1e5, T=1.0e4, R_cl_pc=1.0, L_sun=1e6,
+               mu_cone=1.0 / math.sqrt(2.0), dmu=0.025, eps_core=1e-4, sigma0=None,
+               name="cone"):
+    """Anisotropic escape test (Sec. 4.2, Test 6): a uniform sphere with a bipolar
+    low-opacity cone about the Z axis.  n_H = n_cone + (n_cl - n_cone)/2
+    [1 - tanh((mu - mu_cone)/dmu)], mu = |Z|/r; n_HI = eps n_H with eps = 1 in the
+    shell 0.5 R_cl < r <= R_cl and eps_core inside 0.5 R_cl (the emission
+    region, emitting uniformly per unit volume); vacuum outside R_cl; recoil
+    on; no dust or destruction; static gas; 256^2 cells over 1.1 R_cl;
+    n_cl, n_cone from tau = n sigma0 R_cl."""
+    R_cl = R_cl_pc * PC
+    dx, R, Z, vol = _rz_grid(n, R_cl)
+    r = np.sqrt(R * R + Z * Z)
+    mu = np.abs(Z) / r
+    s0 = _sigma0(T) if sigma0 is None else sigma0
+    n_cl, n_cn = tau_cl / (s0 * R_cl), tau_cone / (s0 * R_cl)
+    n_h = n_cn + 0.5 * (n_cl - n_cn) * (1.0 - np.tanh((mu - mu_cone) / dmu))
+    eps = np.where(r <= 0.5 * R_cl, eps_core, 1.0)
+    n_hi = np.where(r <= R_cl, eps * n_h, 0.0)
+    z = np.zeros((n, n))
+    lum = np.where(r <= 0.5 * R_cl, vol, 0.0)
+    lum = lum * (0.5 * L_sun * L_SUN / lum.sum())
+    t_max = 4.0 * max((4.7e-4 * math.sqrt(1e4 / T) * tau_cl) ** (1.0 / 3.0), 3.0) * R_cl / C_LIGHT
+    return Cloud(name, n, n, dx, n_hi, z.copy(), z.copy(), z.copy(), z.copy(), lum, T=T,
+                 recoil=True, freq_step=True, kappa_abs=0.0, kappa_F=0.0, geometry=1,
+                 meta={"tau_cl": tau_cl, "tau_cone": tau_cone, "R_cl": R_cl, "t_max": t_max})
