@@ -61,8 +61,16 @@ typedef struct lym1_ctx lym1_ctx;
 typedef struct {
   int nx, ny;      /* cells in x and y, each >= 1 */
   double dx_cm;    /* cell width (cm), > 0 */
-  int geometry;    /* 0 = 2D Cartesian; the only value accepted */
-  int bc[4];       /* x-, x+, y-, y+ : 0 = outflow; the only value accepted */
+  int geometry;    /* 0 = 2D Cartesian slab of depth dx, outflow on all four sides;
+                      1 = axisymmetric (R, Z) as in the paper's tests and RHD runs (Sec. 4):
+                      x = R from the axis (R = 0 at the left edge), y = Z from the midplane
+                      (Z = 0 at the bottom edge); the axis reflects (H_R, u_R mirrored), the
+                      midplane is a mirror (H_Z, u_Z mirrored), the outer R and Z edges are
+                      outflow; finite volumes per radian with the hoop source of div K; a
+                      cell's lum is emitted into its full ring volume 2 pi Vol; energies and
+                      force integrals cover the ring volumes of the half-space Z > 0 */
+  int bc[4];       /* x-, x+, y-, y+ : 0 = the boundaries of the geometry; the only value
+                      accepted */
 } lym1_grid;
 
 typedef struct {
@@ -128,6 +136,7 @@ const char *lym1_strerror(int status);
  * the device, builds the per-bin tables on the host (frequency grid, line
  * constants, bin-averaged Voigt profile <H>_k, App. A; emission fractions,
  * Sec. 2.1 step 2) and zeroes the state and the sources.
+ * Contexts of different geometries cannot share a batch (lym1_batch_create).
  * Returns LYM1_EINVAL for unsupported geometry/boundaries/precision, fewer than
  * one cell or bin, more than LYM1_MAX_BINS bins, non-positive dx or T;
  * LYM1_ENOMEM if device memory runs out; LYM1_ENODEVICE without a GPU.

@@ -60,7 +60,8 @@
  * conservation of energy to round-off, realisability, free-streaming beam,
  * Gaussian diffusion closed form, thin-slab force multiplier, step-3 vs dense
  * and exact-rational solves, recoil-only equilibrium, central-difference
- * limit vs a banded solver.
+ * limit vs a banded solver; in (R, Z): the thin-sphere force multiplier
+ * tau eta / 4, a steady uniform isotropic field, the Hubble-flow work term.
  */
 #include <math.h>
 #include <stdint.h>
@@ -374,7 +375,7 @@ static int o_mir(int i, int n, int *flip)
 {
     if (i < 0) {
         *flip = 1;
-        return -1 - i;
+        return (-1 - i >= n) ? n - 1 : -1 - i;
     }
     *flip = 0;
     return i >= n ? n - 1 : i;

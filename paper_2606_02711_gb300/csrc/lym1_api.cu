@@ -7,6 +7,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <utility>
 #include <vector>
 
 #include "lym1.h"
@@ -15,7 +16,7 @@
 using namespace lym1;
 
 struct lym1_ctx {
-  int nx = 0, ny = 0, nb = 0, precision = 0, gray = 0, freq_step = 0, recoil = 0;
+  int nx = 0, ny = 0, nb = 0, precision = 0, gray = 0, freq_step = 0, recoil = 0, geometry = 0;
   long long nc = 0;
   double dx = 0, T = 0, c_tilde = 0, cfl = 0, kabs = 0, kF = 0, dt_cfl = 0, umax = 0;
   double L_tot = 0, device_bytes = 0, gem_max = 1;
@@ -36,6 +37,12 @@ struct lym1_ctx {
   int* status = nullptr;      // set by a kernel whose bounded wait expired
   float *f_H = nullptr, *f_dnu = nullptr, *f_G = nullptr, *f_R = nullptr, *f_nbc = nullptr,
         *f_half = nullptr;
+  // axisymmetric grid (geometry 1): <u_R/R> per cell and the per-column tables
+  double *gphi = nullptr, *g_AR = nullptr, *g_AZ = nullptr, *g_Vol = nullptr, *g_invR = nullptr,
+         *g_dlL = nullptr, *g_dlR = nullptr, *g_wv = nullptr, *g_V2pi = nullptr;
+  float *gf_r0 = nullptr, *gf_r1 = nullptr, *gf_hoop = nullptr, *gf_dlL = nullptr,
+        *gf_dlR = nullptr, *gf_wv = nullptr;
+  double g_wR = 0;
   std::vector<void*> allocs;
   // persistent graph-replayed path for CFL substeps (a batch of this context alone)
   lym1_batch* self_batch = nullptr;
@@ -156,11 +163,28 @@ DeviceView make_view(const lym1_ctx* c, double dt) {
   v.f_R = c->f_R;
   v.f_nbc = c->f_nbc;
   v.f_half = c->f_half;
+  v.geometry = c->geometry;
+  v.gphi = c->gphi;
+  v.g_AR = c->g_AR;
+  v.g_AZ = c->g_AZ;
+  v.g_Vol = c->g_Vol;
+  v.g_invR = c->g_invR;
+  v.g_dlL = c->g_dlL;
+  v.g_dlR = c->g_dlR;
+  v.g_wv = c->g_wv;
+  v.gf_r0 = c->gf_r0;
+  v.gf_r1 = c->gf_r1;
+  v.gf_hoop = c->gf_hoop;
+  v.gf_dlL = c->gf_dlL;
+  v.gf_dlR = c->gf_dlR;
+  v.gf_wv = c->gf_wv;
+  v.g_wR = c->g_wR;
   return v;
 }
 
 int reset_counters(lym1_ctx* c) {
-  LYM1_TRYK(launch_energy(c->precision, c->A[0], c->t_dnu, c->nb, c->nc, c->partF, c->stream));
+  LYM1_TRYK(launch_energy(c->precision, c->A[0], c->t_dnu, c->nb, c->nc, c->partF,
+                          c->geometry == 1 ? c->g_wv : nullptr, c->nx, c->stream));
   LYM1_TRYK(launch_finalize(c->partT, 0, c->partF, freq_blocks(c->nc), c->acc, 1, c->stream));
   return LYM1_OK;
 }
@@ -277,7 +301,7 @@ void drop_events(lym1_ctx* c) {
 
 struct lym1_batch {
   std::vector<lym1_ctx*> ctxs;
-  int precision = 0, nb = 0, nT = 0, nF = 0;
+  int precision = 0, nb = 0, nT = 0, nF = 0, geometry = 0;
   cudaStream_t ctx_stream = nullptr, bs = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr, t0 = nullptr, t1 = nullptr;
   DeviceView *viewsT = nullptr, *viewsF = nullptr;
@@ -297,11 +321,13 @@ namespace {
 int batch_launch(lym1_batch* b, cudaStream_t s) {
   const int n = static_cast<int>(b->ctxs.size());
   if (b->precision == LYM1_FP64_DET) {
-    LYM1_TRYK(launch_batched_det(0, b->viewsT, b->itemsT, b->nT, b->gridT, b->nb, s));
-    LYM1_TRYK(launch_batched_det(1, b->viewsF, b->itemsF, b->nF, b->gridF, b->nb, s));
+    LYM1_TRYK(launch_batched_det(0, b->geometry, b->viewsT, b->itemsT, b->nT, b->gridT, b->nb, s));
+    LYM1_TRYK(launch_batched_det(1, b->geometry, b->viewsF, b->itemsF, b->nF, b->gridF, b->nb, s));
   } else {
-    LYM1_TRYK(launch_batched_fast(b->precision, 0, b->viewsT, b->itemsT, b->nT, b->gridT, b->nb, s));
-    LYM1_TRYK(launch_batched_fast(b->precision, 1, b->viewsF, b->itemsF, b->nF, b->gridF, b->nb, s));
+    LYM1_TRYK(launch_batched_fast(b->precision, 0, b->geometry, b->viewsT, b->itemsT, b->nT, b->gridT,
+                                  b->nb, s));
+    LYM1_TRYK(launch_batched_fast(b->precision, 1, b->geometry, b->viewsF, b->itemsF, b->nF, b->gridF,
+                                  b->nb, s));
   }
   LYM1_TRYK(launch_finalize_batched(b->jobs, n, s));
   return LYM1_OK;
@@ -314,18 +340,20 @@ int batch_launch_timed(lym1_batch* b, lym1_ctx* c) {
   {
     KernelTimer t(c, 0);
     if (b->precision == LYM1_FP64_DET)
-      LYM1_TRYK(launch_batched_det(0, b->viewsT, b->itemsT, b->nT, b->gridT, b->nb, c->stream));
+      LYM1_TRYK(launch_batched_det(0, b->geometry, b->viewsT, b->itemsT, b->nT, b->gridT, b->nb,
+                                   c->stream));
     else
-      LYM1_TRYK(launch_batched_fast(b->precision, 0, b->viewsT, b->itemsT, b->nT, b->gridT, b->nb,
-                                    c->stream));
+      LYM1_TRYK(launch_batched_fast(b->precision, 0, b->geometry, b->viewsT, b->itemsT, b->nT,
+                                    b->gridT, b->nb, c->stream));
   }
   {
     KernelTimer t(c, 1);
     if (b->precision == LYM1_FP64_DET)
-      LYM1_TRYK(launch_batched_det(1, b->viewsF, b->itemsF, b->nF, b->gridF, b->nb, c->stream));
+      LYM1_TRYK(launch_batched_det(1, b->geometry, b->viewsF, b->itemsF, b->nF, b->gridF, b->nb,
+                                   c->stream));
     else
-      LYM1_TRYK(launch_batched_fast(b->precision, 1, b->viewsF, b->itemsF, b->nF, b->gridF, b->nb,
-                                    c->stream));
+      LYM1_TRYK(launch_batched_fast(b->precision, 1, b->geometry, b->viewsF, b->itemsF, b->nF,
+                                    b->gridF, b->nb, c->stream));
   }
   KernelTimer t(c, 2);
   LYM1_TRYK(launch_finalize_batched(b->jobs, n, c->stream));
@@ -377,7 +405,8 @@ int lym1_create(const lym1_grid* grid, const lym1_groups* groups, const lym1_opa
   if (!out) return LYM1_EINVAL;
   *out = nullptr;
   if (!grid || !groups || !op) return LYM1_EINVAL;
-  if (grid->nx < 1 || grid->ny < 1 || !(grid->dx_cm > 0.0) || grid->geometry != 0) return LYM1_EINVAL;
+  if (grid->nx < 1 || grid->ny < 1 || !(grid->dx_cm > 0.0)) return LYM1_EINVAL;
+  if (grid->geometry != 0 && grid->geometry != 1) return LYM1_EINVAL;
   for (int i = 0; i < 4; ++i)
     if (grid->bc[i] != 0) return LYM1_EINVAL;
   if (!(op->temp_K > 0.0) || op->precision < 0 || op->precision > 3) return LYM1_EINVAL;
@@ -423,7 +452,8 @@ int lym1_create(const lym1_grid* grid, const lym1_groups* groups, const lym1_opa
   c->freq_step = op->freq_step ? 1 : 0;
   c->stream = static_cast<cudaStream_t>(op->cuda_stream);
   c->selem = (c->precision >= LYM1_MIXED) ? 4 : 8;
-  build_tables(edges, c->T, c->dx, c->gray, c->recoil, &c->tab);
+  c->geometry = grid->geometry;
+  build_tables(edges, c->T, c->dx, c->gray, c->recoil, &c->tab, c->geometry);
   c->nb = c->tab.nb;
   c->gem_max = 0.0;
   for (double g : c->tab.gem) c->gem_max = std::max(c->gem_max, g);
@@ -449,6 +479,25 @@ int lym1_create(const lym1_grid* grid, const lym1_groups* groups, const lym1_opa
   float** ftabs[] = {&c->f_H, &c->f_dnu, &c->f_G, &c->f_R, &c->f_nbc, &c->f_half};
   for (float** p : ftabs)
     if (rc == LYM1_OK) rc = dalloc_t(c, p, static_cast<size_t>(c->nb));
+  CylTables cyl;
+  const size_t ncol = static_cast<size_t>(c->nx);
+  if (c->geometry == 1) {
+    build_cyl_tables(c->nx, c->dx, &cyl);
+    c->g_wR = cyl.wR;
+    if (rc == LYM1_OK) rc = dalloc_t(c, &c->gphi, plane);
+    double** cd[] = {&c->g_AR, &c->g_dlL, &c->g_dlR};
+    for (double** p : cd)
+      if (rc == LYM1_OK) rc = dalloc_t(c, p, ncol + 1);
+    double** cc[] = {&c->g_AZ, &c->g_Vol, &c->g_invR, &c->g_wv, &c->g_V2pi};
+    for (double** p : cc)
+      if (rc == LYM1_OK) rc = dalloc_t(c, p, ncol);
+    float** fd1[] = {&c->gf_dlL, &c->gf_dlR};
+    for (float** p : fd1)
+      if (rc == LYM1_OK) rc = dalloc_t(c, p, ncol + 1);
+    float** fc[] = {&c->gf_r0, &c->gf_r1, &c->gf_hoop, &c->gf_wv};
+    for (float** p : fc)
+      if (rc == LYM1_OK) rc = dalloc_t(c, p, ncol);
+  }
   if (rc != LYM1_OK) {
     free_all(c);
     delete c;
@@ -473,8 +522,24 @@ int lym1_create(const lym1_grid* grid, const lym1_groups* groups, const lym1_opa
       cudaMemcpyAsync(c->pd, op->p_d, pb, cudaMemcpyDefault, s) != cudaSuccess)
     return fail(LYM1_ECUDA);
   if (launch_setup_statics(d_nhi, c->ux, c->uy, c->tab.lc.sigma0, c->nx, c->ny, c->dx, c->alpha,
-                           c->gxx, c->gyy, c->gsh, s) != 0)
+                           c->gxx, c->gyy, c->gsh, c->geometry, c->gphi, s) != 0)
     return fail(LYM1_ECUDA);
+  if (c->geometry == 1) {
+    const std::pair<double*, const std::vector<double>*> dt[] = {
+        {c->g_AR, &cyl.AR},     {c->g_dlL, &cyl.dlL}, {c->g_dlR, &cyl.dlR},   {c->g_AZ, &cyl.AZ},
+        {c->g_Vol, &cyl.Vol},   {c->g_invR, &cyl.invR}, {c->g_wv, &cyl.wv}, {c->g_V2pi, &cyl.V2pi}};
+    for (const auto& e : dt)
+      if (cudaMemcpy(e.first, e.second->data(), sizeof(double) * e.second->size(),
+                     cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail(LYM1_ECUDA);
+    const std::pair<float*, const std::vector<float>*> ft[] = {
+        {c->gf_dlL, &cyl.fdlL}, {c->gf_dlR, &cyl.fdlR}, {c->gf_r0, &cyl.r0},
+        {c->gf_r1, &cyl.r1},    {c->gf_hoop, &cyl.hoop}, {c->gf_wv, &cyl.fwv}};
+    for (const auto& e : ft)
+      if (cudaMemcpy(e.first, e.second->data(), sizeof(float) * e.second->size(),
+                     cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail(LYM1_ECUDA);
+  }
   const std::vector<double>* tabs[] = {&c->tab.dnu, &c->tab.Havg, &c->tab.gem,
                                        &c->tab.half, &c->tab.Rk, &c->tab.nubar_c};
   double* dtabs[] = {c->t_dnu, c->t_H, c->t_gem, c->t_half, c->t_R, c->t_nbc};
@@ -538,10 +603,13 @@ int lym1_set_sources(lym1_ctx* c, const double* lum) {
   if (!c || !lum) return LYM1_EINVAL;
   const size_t n = static_cast<size_t>(c->nc);
   LYM1_TRY(cudaMemcpyAsync(c->lum, lum, n * sizeof(double), cudaMemcpyDefault, c->stream));
+  // axisymmetric grid: the kernels take the luminosity per unit ring volume
+  if (c->geometry == 1)
+    LYM1_TRYK(launch_scale_columns(c->lum, c->g_V2pi, c->nx, c->nc, c->stream));
   double L = 0.0;
   if (is_device_ptr(lum)) {
     std::vector<double> h(n);
-    LYM1_TRY(cudaMemcpyAsync(h.data(), c->lum, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    LYM1_TRY(cudaMemcpyAsync(h.data(), lum, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     LYM1_TRY(cudaStreamSynchronize(c->stream));
     for (double x : h) L += x;
   } else {
@@ -636,7 +704,8 @@ int lym1_diagnostics(lym1_ctx* c, lym1_diag* d) {
   if (!c || !d) return LYM1_EINVAL;
   double acc[16];
   std::vector<double> fp(2 * kForceBlocks);
-  LYM1_TRYK(launch_force_reduce(c->fx, c->fy, c->nx, c->ny, c->dx, c->fpart, kForceBlocks, c->stream));
+  LYM1_TRYK(launch_force_reduce(c->fx, c->fy, c->nx, c->ny, c->dx, c->geometry, c->fpart,
+                                kForceBlocks, c->stream));
   LYM1_TRY(cudaMemcpyAsync(acc, c->acc, sizeof acc, cudaMemcpyDeviceToHost, c->stream));
   LYM1_TRY(cudaMemcpyAsync(fp.data(), c->fpart, fp.size() * sizeof(double), cudaMemcpyDeviceToHost,
                            c->stream));
@@ -750,13 +819,14 @@ int lym1_batch_create(lym1_ctx* const* ctxs, int n_ctx, lym1_batch** out) {
   for (int i = 0; i < n_ctx; ++i) {
     if (!ctxs[i] || ctxs[i]->gray || !ctxs[i]->freq_step) return LYM1_EINVAL;
     if (ctxs[i]->precision != ctxs[0]->precision || ctxs[i]->nb != ctxs[0]->nb ||
-        ctxs[i]->stream != ctxs[0]->stream)
+        ctxs[i]->stream != ctxs[0]->stream || ctxs[i]->geometry != ctxs[0]->geometry)
       return LYM1_EINVAL;
   }
   lym1_batch* b = new (std::nothrow) lym1_batch();
   if (!b) return LYM1_ENOMEM;
   b->ctxs.assign(ctxs, ctxs + n_ctx);
   b->precision = ctxs[0]->precision;
+  b->geometry = ctxs[0]->geometry;
   b->nb = ctxs[0]->nb;
   b->ctx_stream = ctxs[0]->stream;
   std::vector<DeviceView> vT, vF;
@@ -812,8 +882,10 @@ int lym1_batch_create(lym1_ctx* const* ctxs, int n_ctx, lym1_batch** out) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   if (nsm < 1) nsm = 1;
-  const int rT = b->precision == LYM1_FP64_DET ? resident_blocks_det(0) : resident_blocks_fast(b->precision, 0);
-  const int rF = b->precision == LYM1_FP64_DET ? resident_blocks_det(1) : resident_blocks_fast(b->precision, 1);
+  const int rT = b->precision == LYM1_FP64_DET ? resident_blocks_det(0, b->geometry)
+                                               : resident_blocks_fast(b->precision, 0, b->geometry);
+  const int rF = b->precision == LYM1_FP64_DET ? resident_blocks_det(1, b->geometry)
+                                               : resident_blocks_fast(b->precision, 1, b->geometry);
   for (int m = 1; m <= rT; ++m) b->candT.push_back(std::min(b->nT, m * nsm));
   const int gf = std::min(b->nF, rF * nsm);
   b->candF.push_back(gf);

@@ -33,10 +33,27 @@ struct BinTables {
   std::vector<double> dnu, nubar, Havg, gem, Rk, half, nubar_c;
 };
 
+// Per-column tables of the axisymmetric (R, Z) grid, per radian: R-face areas
+// AR[i] = R_i dZ (nx+1), Z-face areas AZ = (R+^2 - R-^2)/2, volumes Vol = AZ dZ,
+// <1/R> = dR dZ / Vol, ring volumes 2 pi Vol, centroid-to-face distances on
+// the two sides of each R face (nx+1; the axis face mirrors the first
+// centroid, the outer face sits half a cell from a ghost at Rbar + dx), and
+// the dimensionless factors the FP32 kernels use: AR[i] dx / Vol, AR[i+1] dx /
+// Vol, dx^3 / Vol (the hoop factor), 2 pi Vol / dx^3 (energy weight).
+struct CylTables {
+  std::vector<double> AR, AZ, Vol, invR, V2pi, dlL, dlR, wv;
+  std::vector<float> r0, r1, hoop, fdlL, fdlR, fwv;
+  double wR = 0;  // 2 pi AR[nx] / dx^2: outflow weight of the outer R face
+};
+
 LineConstants line_constants(double T);
 int paper_frequency_grid(double T_min, double q, std::vector<double>* edges);
+// cell volume dx^3 in the emissivity factor gem_k for geometry 0; 1 for the
+// axisymmetric grid, whose per-cell luminosity is divided by 2 pi Vol on the
+// device
 void build_tables(const std::vector<double>& edges, double T, double dx, int gray, int recoil,
-                  BinTables* t);
+                  BinTables* t, int geometry = 0);
+void build_cyl_tables(int nx, double dx, CylTables* g);
 
 // ---------------------------------------------------------------- kernel side
 constexpr int kTileX = 32;   // transport tile: one thread per cell
@@ -104,6 +121,24 @@ struct DeviceView {
   const float* f_nbc = nullptr;
   const float* f_half = nullptr;
   int freq_step = 0;
+  // axisymmetric (R, Z) grid (geometry 1): per-cell <u_R / R> and the
+  // per-column tables of CylTables (nullptr for geometry 0)
+  int geometry = 0;
+  const double* gphi = nullptr;
+  const double* g_AR = nullptr;
+  const double* g_AZ = nullptr;
+  const double* g_Vol = nullptr;
+  const double* g_invR = nullptr;
+  const double* g_dlL = nullptr;
+  const double* g_dlR = nullptr;
+  const double* g_wv = nullptr;
+  const float* gf_r0 = nullptr;
+  const float* gf_r1 = nullptr;
+  const float* gf_hoop = nullptr;
+  const float* gf_dlL = nullptr;
+  const float* gf_dlR = nullptr;
+  const float* gf_wv = nullptr;
+  double g_wR = 0;
 };
 
 // Launchers (defined in the kernel translation units); each returns a
@@ -112,18 +147,21 @@ int launch_transport_det(const DeviceView& v, void* stream);
 int launch_freq_det(const DeviceView& v, void* stream);
 int launch_transport_fast(int precision, const DeviceView& v, void* stream);
 int launch_freq_fast(int precision, const DeviceView& v, void* stream);
+// wcol: per-column energy weights (nullptr = 1), nx columns
 int launch_energy(int precision, const void* J, const double* dnu, int nb, long long nc,
-                  double* part, void* stream);
+                  double* part, const double* wcol, int nx, void* stream);
 int launch_finalize(const double* partT, int nT, const double* partE, int nE, double* acc,
                     int mode, void* stream);
 int launch_setup_statics(const double* n_hi, const double* ux, const double* uy, double sigma0,
                          int nx, int ny, double dx, double* alpha, double* gxx, double* gyy,
-                         double* gsh, void* stream);
+                         double* gsh, int geometry, double* gphi, void* stream);
+// lum[j][i] /= V2pi[i] (axisymmetric grid: per-volume luminosity density)
+int launch_scale_columns(double* lum, const double* V2pi, int nx, long long nc, void* stream);
 int launch_convert_out(int precision, const void* src, double* dst, long long n, double scale,
                        void* stream);
 int launch_convert_in(int precision, const double* src, void* dst, long long n, void* stream);
 int launch_force_reduce(const double* fx, const double* fy, int nx, int ny, double dx,
-                        double* part, int nblocks, void* stream);
+                        int geometry, double* part, int nblocks, void* stream);
 
 // batched (multi-context) launches; kind 0 = transport, 1 = frequency step;
 // items point to device arrays of {ctx, x0, y0, blk}
@@ -133,12 +171,13 @@ struct FinalizeJob {
   double* acc;
   int nT, nE;
 };
-int launch_batched_det(int kind, const DeviceView* views, const void* items, int n, int grid,
-                       int nb_max, void* stream);
-int launch_batched_fast(int precision, int kind, const DeviceView* views, const void* items, int n,
-                        int grid, int nb_max, void* stream);
-int resident_blocks_det(int kind);
-int resident_blocks_fast(int precision, int kind);
+// every context of one batched launch has the same geometry
+int launch_batched_det(int kind, int geometry, const DeviceView* views, const void* items, int n,
+                       int grid, int nb_max, void* stream);
+int launch_batched_fast(int precision, int kind, int geometry, const DeviceView* views,
+                        const void* items, int n, int grid, int nb_max, void* stream);
+int resident_blocks_det(int kind, int geometry);
+int resident_blocks_fast(int precision, int kind, int geometry);
 int launch_finalize_batched(const FinalizeJob* jobs, int n, void* stream);
 
 inline int transport_blocks(int nx, int ny) {

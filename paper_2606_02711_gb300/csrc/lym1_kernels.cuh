@@ -122,8 +122,10 @@ __device__ __forceinline__ F m_sqrt(F x) { return sqrt(x); }
 //   (1-chi)/2 = (1 + s - 2f^2) / (5 + 2s),  (3chi-1)/(2f^2) = (6 + 3/(2+s)) / (5 + 2s),
 // because 3chi - 1 ~ 1.5 f^2 cancels to noise in FP32 when f is small
 // (optically thick cells, f ~ 1/tau).
+// Dpp = (1-chi)/2 is the component along any direction normal to f (the
+// azimuthal one on the axisymmetric grid).
 template <class F>
-__device__ __forceinline__ void closure(F fn, F ft, F& Dnn, F& Dnt, F& Dtt) {
+__device__ __forceinline__ void closure(F fn, F ft, F& Dnn, F& Dnt, F& Dtt, F& Dpp) {
   const F f2 = fn * fn + ft * ft;
   if constexpr (sizeof(F) == 4) {
     const F s = sqrtf(F(4) - F(3) * f2);
@@ -133,9 +135,11 @@ __device__ __forceinline__ void closure(F fn, F ft, F& Dnn, F& Dnt, F& Dtt) {
     Dnn = dA + g * (fn * fn);
     Dnt = g * (fn * ft);
     Dtt = dA + g * (ft * ft);
+    Dpp = dA;
   } else {
     const F chi = (F(3) + F(4) * f2) / (F(5) + F(2) * m_sqrt(F(4) - F(3) * f2));
     const F dA = (F(1) - chi) / F(2), dB = (F(3) * chi - F(1)) / F(2);
+    Dpp = dA;
     if (f2 > F(0)) {
       Dnn = dA + (dB * (fn * fn)) / f2;
       Dnt = (dB * (fn * ft)) / f2;
@@ -146,6 +150,12 @@ __device__ __forceinline__ void closure(F fn, F ft, F& Dnn, F& Dnt, F& Dtt) {
       Dtt = dA;
     }
   }
+}
+
+template <class F>
+__device__ __forceinline__ void closure(F fn, F ft, F& Dnn, F& Dnt, F& Dtt) {
+  F Dpp;
+  closure(fn, ft, Dnn, Dnt, Dtt, Dpp);
 }
 
 // Running sum: plain in FP64, Neumaier-compensated in FP32.
@@ -192,7 +202,7 @@ __device__ __forceinline__ void cap_unit(F& fn, F& ft) {
 template <class F>
 __device__ __forceinline__ void face_flux(F Jm, F nm, F tm, F J0, F n0, F t0, F J1, F n1, F t1,
                                           F J2, F n2, F t2, F aF0, F aF1, F un0, F un1,
-                                          F half_dx, F& oJ, F& oN, F& oT) {
+                                          F dl0, F dl1, F& oJ, F& oN, F& oT) {
   const F sJ0 = minmod(J0 - Jm, J1 - J0), sJ1 = minmod(J1 - J0, J2 - J1);
   const F sn0 = minmod(n0 - nm, n1 - n0), sn1 = minmod(n1 - n0, n2 - n1);
   const F st0 = minmod(t0 - tm, t1 - t0), st1 = minmod(t1 - t0, t2 - t1);
@@ -206,7 +216,8 @@ __device__ __forceinline__ void face_flux(F Jm, F nm, F tm, F J0, F n0, F t0, F 
   closure(nL, tL, DnnL, DntL, DttL);
   closure(nR, tR, DnnR, DntR, DttR);
   const F KnnL = DnnL * JL, KntL = DntL * JL, KnnR = DnnR * JR, KntR = DntR * JR;
-  const F tau = aF0 * half_dx + aF1 * half_dx;
+  // face optical depth from the two cells' centres (centroids) to the face
+  const F tau = aF0 * dl0 + aF1 * dl1;
   const F eps = (F(0.2) + tau) / ((F(0.2) + tau) + tau * tau);
   const F dif = (tau > F(0)) ? ((F(1) - eps) * (J1 - J0)) / (F(3) * tau) : F(0);
   F fJ = (eps * (F(0.5) * (HnL + HnR)) - eps * (F(0.5) * (JR - JL))) - dif;
@@ -229,6 +240,23 @@ __device__ __forceinline__ void face_flux(F Jm, F nm, F tm, F J0, F n0, F t0, F 
 }
 
 __device__ __forceinline__ int clampi(int i, int n) { return i < 0 ? 0 : (i >= n ? n - 1 : i); }
+
+// Ghost cell index along one axis.  Geometry 0: outflow on both sides (copy
+// of the edge cell).  Geometry 1: the low side (R = 0 axis, Z = 0 midplane)
+// is a mirror, where the normal components of H and u change sign (flip =
+// true); the high side is outflow.
+template <int G>
+__device__ __forceinline__ int ghost(int i, int n, bool& flip) {
+  if constexpr (G == 1) {
+    if (i < 0) {
+      flip = true;
+      const int m = -1 - i;
+      return m >= n ? n - 1 : m;
+    }
+  }
+  flip = false;
+  return clampi(i, n);
+}
 
 // block-wide fixed-order reductions (warp shuffles, then warps in order)
 template <int NT>
@@ -258,7 +286,7 @@ __device__ __forceinline__ double block_max(double v, double* red) {
 }
 
 // ------------------------------------------------------------ transport kernel
-template <class P>
+template <class P, int G>
 __device__ __forceinline__ void transport_tile(const DeviceView& v, int x0, int y0, int blk) {
   using S = typename P::S;
   using F = typename P::F;
@@ -270,6 +298,7 @@ __device__ __forceinline__ void transport_tile(const DeviceView& v, int x0, int 
   __shared__ F qA[QY][QX], qR[QY][QX], qUx[QY][QX], qUy[QY][QX];
   __shared__ F xJ[TY][TX + 1], xN[TY][TX + 1], xT[TY][TX + 1];
   __shared__ F yJ[TY + 1][TX], yN[TY + 1][TX], yT[TY + 1][TX];
+  __shared__ F sdl[2][G == 1 ? TX + 1 : 1];  // axisymmetric: centroid distances per R face
   __shared__ double red[NT / 32];
 
   const S* __restrict__ Jin = static_cast<const S*>(v.J);
@@ -288,14 +317,25 @@ __device__ __forceinline__ void transport_tile(const DeviceView& v, int x0, int 
 
   for (int idx = tid; idx < QX * QY; idx += NT) {
     const int lx = idx % QX, ly = idx / QX;
-    const long long c = static_cast<long long>(clampi(y0 + ly - 1, ny)) * nx + clampi(x0 + lx - 1, nx);
+    bool fxg, fyg;
+    const int ix = ghost<G>(x0 + lx - 1, nx, fxg), iy = ghost<G>(y0 + ly - 1, ny, fyg);
+    const long long c = static_cast<long long>(iy) * nx + ix;
     qA[ly][lx] = F(v.alpha[c]);
     qR[ly][lx] = F(v.rho[c]);
-    qUx[ly][lx] = F(v.ux[c]);
-    qUy[ly][lx] = F(v.uy[c]);
+    qUx[ly][lx] = fxg ? -F(v.ux[c]) : F(v.ux[c]);
+    qUy[ly][lx] = fyg ? -F(v.uy[c]) : F(v.uy[c]);
+  }
+  if constexpr (G == 1) {
+    for (int f = tid; f <= TX; f += NT) {
+      const int gf = x0 + f <= nx ? x0 + f : nx;
+      sdl[0][f] = F(v.g_dlL[gf]);
+      sdl[1][f] = F(v.g_dlR[gf]);
+    }
   }
   I alpha_c = 0, rho_c = 0, pd_c = 0;
-  F gxx = 0, gyy = 0, gsh = 0;
+  F gxx = 0, gyy = 0, gsh = 0, gphi = 0;
+  F ARm = 0, ARp = 0, AZc = 0, Volc = 0, invRc = 0;
+  double wcell = 1.0;
   if (valid) {
     alpha_c = I(v.alpha[cell]);
     rho_c = I(v.rho[cell]);
@@ -303,6 +343,15 @@ __device__ __forceinline__ void transport_tile(const DeviceView& v, int x0, int 
     gxx = F(v.gxx[cell]);
     gyy = F(v.gyy[cell]);
     gsh = F(v.gsh[cell]);
+    if constexpr (G == 1) {
+      gphi = F(v.gphi[cell]);
+      ARm = F(v.g_AR[gx]);
+      ARp = F(v.g_AR[gx + 1]);
+      AZc = F(v.g_AZ[gx]);
+      Volc = F(v.g_Vol[gx]);
+      invRc = F(v.g_invR[gx]);
+      wcell = v.g_wv[gx];
+    }
   }
   const F dx = F(v.dx), half_dx = F(0.5) * F(v.dx), kF_f = F(v.kF), cdt_f = F(v.cdt);
   const I cdt = I(v.cdt), kabs = I(v.kabs), kF = I(v.kF);
@@ -320,9 +369,12 @@ __device__ __forceinline__ void transport_tile(const DeviceView& v, int x0, int 
     // phase A: halo tile of the state and its primitives
     for (int idx = tid; idx < SX * SY; idx += NT) {
       const int lx = idx % SX, ly = idx / SX;
-      const long long c = base + static_cast<long long>(clampi(y0 + ly - 2, ny)) * nx +
-                          clampi(x0 + lx - 2, nx);
-      const F J = F(Jin[c]), Hx = F(Hxin[c]), Hy = F(Hyin[c]);
+      bool fxg, fyg;
+      const int ix = ghost<G>(x0 + lx - 2, nx, fxg), iy = ghost<G>(y0 + ly - 2, ny, fyg);
+      const long long c = base + static_cast<long long>(iy) * nx + ix;
+      const F J = F(Jin[c]);
+      const F Hx = fxg ? -F(Hxin[c]) : F(Hxin[c]);
+      const F Hy = fyg ? -F(Hyin[c]) : F(Hyin[c]);
       sJ[ly][lx] = J;
       sHx[ly][lx] = Hx;
       sHy[ly][lx] = Hy;
@@ -342,10 +394,15 @@ __device__ __forceinline__ void transport_tile(const DeviceView& v, int x0, int 
         const int r = fj + 2;
         const F aF0 = qA[fj + 1][fi] * Hk + qR[fj + 1][fi] * kF_f;
         const F aF1 = qA[fj + 1][fi + 1] * Hk + qR[fj + 1][fi + 1] * kF_f;
+        F dl0 = half_dx, dl1 = half_dx;
+        if constexpr (G == 1) {
+          dl0 = sdl[0][fi];
+          dl1 = sdl[1][fi];
+        }
         face_flux<F>(sJ[r][fi], sfx[r][fi], sfy[r][fi], sJ[r][fi + 1], sfx[r][fi + 1],
                      sfy[r][fi + 1], sJ[r][fi + 2], sfx[r][fi + 2], sfy[r][fi + 2], sJ[r][fi + 3],
                      sfx[r][fi + 3], sfy[r][fi + 3], aF0, aF1, qUx[fj + 1][fi],
-                     qUx[fj + 1][fi + 1], half_dx, xJ[fj][fi], xN[fj][fi], xT[fj][fi]);
+                     qUx[fj + 1][fi + 1], dl0, dl1, xJ[fj][fi], xN[fj][fi], xT[fj][fi]);
       } else {
         const int g = f - NXF;
         const int fi = g % TX, fj = g / TX;
@@ -355,7 +412,7 @@ __device__ __forceinline__ void transport_tile(const DeviceView& v, int x0, int 
         face_flux<F>(sJ[fj][cc], sfy[fj][cc], sfx[fj][cc], sJ[fj + 1][cc], sfy[fj + 1][cc],
                      sfx[fj + 1][cc], sJ[fj + 2][cc], sfy[fj + 2][cc], sfx[fj + 2][cc],
                      sJ[fj + 3][cc], sfy[fj + 3][cc], sfx[fj + 3][cc], aF0, aF1, qUy[fj][fi + 1],
-                     qUy[fj + 1][fi + 1], half_dx, yJ[fj][fi], yN[fj][fi], yT[fj][fi]);
+                     qUy[fj + 1][fi + 1], half_dx, half_dx, yJ[fj][fi], yN[fj][fi], yT[fj][fi]);
       }
     }
     __syncthreads();
@@ -364,20 +421,34 @@ __device__ __forceinline__ void transport_tile(const DeviceView& v, int x0, int 
       const F J = sJ[ty + 2][tx + 2], Hx = sHx[ty + 2][tx + 2], Hy = sHy[ty + 2][tx + 2];
       F fxc = sfx[ty + 2][tx + 2], fyc = sfy[ty + 2][tx + 2];
       cap_unit(fxc, fyc);
-      F Dxx, Dxy, Dyy;
-      closure(fxc, fyc, Dxx, Dxy, Dyy);
-      const F W = ((Dxx * J) * gxx + (Dyy * J) * gyy) + (Dxy * J) * gsh;
-      const F divJ = (xJ[ty][tx + 1] - xJ[ty][tx]) + (yJ[ty + 1][tx] - yJ[ty][tx]);
-      const F divHx = (xN[ty][tx + 1] - xN[ty][tx]) + (yT[ty + 1][tx] - yT[ty][tx]);
-      const F divHy = (xT[ty][tx + 1] - xT[ty][tx]) + (yN[ty + 1][tx] - yN[ty][tx]);
-      const F J1 = J - cdt_f * (divJ / dx + W / cl);
-      const F Hx1 = Hx - cdt_f * (divHx / dx);
-      const F Hy1 = Hy - cdt_f * (divHy / dx);
+      F Dxx, Dxy, Dyy, Dpp;
+      closure(fxc, fyc, Dxx, Dxy, Dyy, Dpp);
+      F J1, Hx1, Hy1, W;
+      if constexpr (G == 1) {
+        // finite volumes per radian; hoop source K_phiphi <1/R> in the R equation
+        W = (((Dxx * J) * gxx + (Dyy * J) * gyy) + (Dxy * J) * gsh) + (Dpp * J) * gphi;
+        const F divJ = ((ARp * xJ[ty][tx + 1] - ARm * xJ[ty][tx]) + AZc * (yJ[ty + 1][tx] - yJ[ty][tx])) / Volc;
+        const F divHx = ((ARp * xN[ty][tx + 1] - ARm * xN[ty][tx]) + AZc * (yT[ty + 1][tx] - yT[ty][tx])) / Volc -
+                        (Dpp * J) * invRc;
+        const F divHy = ((ARp * xT[ty][tx + 1] - ARm * xT[ty][tx]) + AZc * (yN[ty + 1][tx] - yN[ty][tx])) / Volc;
+        J1 = J - cdt_f * (divJ + W / cl);
+        Hx1 = Hx - cdt_f * divHx;
+        Hy1 = Hy - cdt_f * divHy;
+      } else {
+        W = ((Dxx * J) * gxx + (Dyy * J) * gyy) + (Dxy * J) * gsh;
+        const F divJ = (xJ[ty][tx + 1] - xJ[ty][tx]) + (yJ[ty + 1][tx] - yJ[ty][tx]);
+        const F divHx = (xN[ty][tx + 1] - xN[ty][tx]) + (yT[ty + 1][tx] - yT[ty][tx]);
+        const F divHy = (xT[ty][tx + 1] - xT[ty][tx]) + (yN[ty + 1][tx] - yN[ty][tx]);
+        J1 = J - cdt_f * (divJ / dx + W / cl);
+        Hx1 = Hx - cdt_f * (divHx / dx);
+        Hy1 = Hy - cdt_f * (divHy / dx);
+      }
       const I aH = alpha_c * I(Hk_d);
       const I kap = rho_c * kabs + pd_c * aH;
       const I aF = aH + rho_c * kF;
-      // j_k = L w_k / (4 pi dx^3 dnu_k): formed in FP64 (L ~ 1e39 erg/s and
-      // w_k / (4 pi dx^3 dnu_k) ~ 1e-58 are both outside the FP32 range)
+      // j_k = L w_k / (4 pi V dnu_k): formed in FP64 (L ~ 1e39 erg/s and
+      // w_k / (4 pi V dnu_k) ~ 1e-58 are both outside the FP32 range); on the
+      // axisymmetric grid lum already holds L / (2 pi Vol) and gem_k has V = 1
       const I js = (lum_d != 0.0) ? I(lum_d * v.t_gem[k]) : I(0);
       const I J2 = (I(J1) + cdt * js) / (I(1) + cdt * kap);
       const I Hx2 = I(Hx1) / (I(1) + cdt * aF);
@@ -398,10 +469,15 @@ __device__ __forceinline__ void transport_tile(const DeviceView& v, int x0, int 
       if (J2 > I(0)) mxf = fmax(mxf, hn / J2);
       if (hn > J2 * I(1.000001) && hn > I(0)) bad += 1.0;
       const I cdx = cdt / I(v.dx);
-      if (gx == 0) out.add(dnu * (cdx * -I(xJ[ty][tx])));
-      if (gx == nx - 1) out.add(dnu * (cdx * I(xJ[ty][tx + 1])));
-      if (gy == 0) out.add(dnu * (cdx * -I(yJ[ty][tx])));
-      if (gy == ny - 1) out.add(dnu * (cdx * I(yJ[ty + 1][tx])));
+      if constexpr (G == 1) {  // outflow through the outer R and Z faces only
+        if (gx == nx - 1) out.add(dnu * (cdx * (I(v.g_wR) * I(xJ[ty][tx + 1]))));
+        if (gy == ny - 1) out.add(dnu * (cdx * (I(wcell) * I(yJ[ty + 1][tx]))));
+      } else {
+        if (gx == 0) out.add(dnu * (cdx * -I(xJ[ty][tx])));
+        if (gx == nx - 1) out.add(dnu * (cdx * I(xJ[ty][tx + 1])));
+        if (gy == 0) out.add(dnu * (cdx * -I(yJ[ty][tx])));
+        if (gy == ny - 1) out.add(dnu * (cdx * I(yJ[ty + 1][tx])));
+      }
     }
     __syncthreads();
   }
@@ -411,15 +487,15 @@ __device__ __forceinline__ void transport_tile(const DeviceView& v, int x0, int 
   }
   double* part = v.partT + static_cast<long long>(blk) * kDiagSlots;
   double s;
-  s = block_sum<NT>(em.value(), red);
+  s = block_sum<NT>(em.value() * wcell, red);
   if (tid == 0) part[kSlotEmitted] = s;
-  s = block_sum<NT>(ab.value(), red);
+  s = block_sum<NT>(ab.value() * wcell, red);
   if (tid == 0) part[kSlotAbsorbed] = s;
   s = block_sum<NT>(out.value(), red);
   if (tid == 0) part[kSlotOutflow] = s;
-  s = block_sum<NT>(wk.value(), red);
+  s = block_sum<NT>(wk.value() * wcell, red);
   if (tid == 0) part[kSlotWork] = s;
-  s = block_sum<NT>(en.value(), red);
+  s = block_sum<NT>(en.value() * wcell, red);
   if (tid == 0) part[kSlotEnergy] = s;
   s = block_max<NT>(double(mxf), red);
   if (tid == 0) part[kSlotMaxF] = s;
@@ -428,9 +504,9 @@ __device__ __forceinline__ void transport_tile(const DeviceView& v, int x0, int 
 }
 
 
-template <class P>
+template <class P, int G>
 __global__ void __launch_bounds__(kTileX* kTileY) transport_kernel(DeviceView v) {
-  transport_tile<P>(v, blockIdx.x * kTileX, blockIdx.y * kTileY, blockIdx.y * gridDim.x + blockIdx.x);
+  transport_tile<P, G>(v, blockIdx.x * kTileX, blockIdx.y * kTileY, blockIdx.y * gridDim.x + blockIdx.x);
 }
 
 // ------------------------------------------------------- FP32 fast-path math
@@ -448,8 +524,10 @@ constexpr float kTinyJ = 1e-30f;
 // kActiveShare E / unit for the next one)
 constexpr double kActiveShare = 1e-8;
 
-// Levermore closure in the cancellation-free FP32 form (see closure()).
-__device__ __forceinline__ void closure_f32(float fn, float ft, float& Dnn, float& Dnt, float& Dtt) {
+// Levermore closure in the cancellation-free FP32 form (see closure());
+// Dpp = (1 - chi)/2.
+__device__ __forceinline__ void closure_f32(float fn, float ft, float& Dnn, float& Dnt, float& Dtt,
+                                            float& Dpp) {
   const float f2 = fn * fn + ft * ft;
   const float y = 4.0f - 3.0f * f2;
   const float s = y * rsqrtf(y);
@@ -459,6 +537,12 @@ __device__ __forceinline__ void closure_f32(float fn, float ft, float& Dnn, floa
   Dnn = dA + g * (fn * fn);
   Dnt = g * (fn * ft);
   Dtt = dA + g * (ft * ft);
+  Dpp = dA;
+}
+
+__device__ __forceinline__ void closure_f32(float fn, float ft, float& Dnn, float& Dnt, float& Dtt) {
+  float Dpp;
+  closure_f32(fn, ft, Dnn, Dnt, Dtt, Dpp);
 }
 
 __device__ __forceinline__ void cap_unit_f32(float& fn, float& ft) {
@@ -479,12 +563,12 @@ __device__ __forceinline__ float minmod_f32(float a, float b) {
 
 // Face flux (same scheme as face_flux) from packed primitives q = (J, f_n, f_t)
 // of cells -1, 0, +1, +2, with w = u/c per cell; the interpolation factor and
-// the diffusion coefficient share one reciprocal:
+// the diffusion coefficient share one reciprocal (tau: the face optical depth):
 //   eps = (0.2 + tau) / d,  (1 - eps) / (3 tau) = tau / (3 d),  d = 0.2 + tau + tau^2.
 __device__ __forceinline__ void face_flux_f32(float Jm, float nm, float tm, float J0, float n0,
                                               float t0, float J1, float n1, float t1, float J2,
                                               float n2, float t2, float aF0, float aF1, float w0,
-                                              float w1, float half_dx, float& oJ, float& oN,
+                                              float w1, float tau, float& oJ, float& oN,
                                               float& oT) {
   const float d0 = J0 - Jm, d1 = J1 - J0, d2 = J2 - J1;
   const float JL = J0 + 0.5f * minmod_f32(d0, d1), JR = J1 - 0.5f * minmod_f32(d1, d2);
@@ -497,7 +581,6 @@ __device__ __forceinline__ void face_flux_f32(float Jm, float nm, float tm, floa
   float DnnL, DntL, DttL, DnnR, DntR, DttR;
   closure_f32(nL, tL, DnnL, DntL, DttL);
   closure_f32(nR, tR, DnnR, DntR, DttR);
-  const float tau = (aF0 + aF1) * half_dx;
   const float a = 0.2f + tau;
   const float rden = frcp(a + tau * tau);
   const float eps = a * rden;
@@ -519,7 +602,7 @@ __device__ __forceinline__ void face_flux_f32(float Jm, float nm, float tm, floa
 // and the bottom y-face of its cell, warp 0 the top row of y-faces and part
 // of warp 1 the right column of x-faces.  The implicit source step runs in
 // type I (FP64 for LYM1_MIXED, FP32 for LYM1_MIXED_FAST).
-template <class P>
+template <class P, int G>
 __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, int y0, int blk) {
   using I = typename P::I;
   constexpr int TX = kTileX, TY = kTileY, SX = TX + 4, SY = TY + 4, QX = TX + 2, QY = TY + 2;
@@ -531,6 +614,7 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
   __shared__ float4 qc[QY][QX];  // (alpha, rho_d, u_x/c, u_y/c)
   __shared__ float xJ[TY][TX + 1], xN[TY][TX + 1], xT[TY][TX + 1];
   __shared__ float yJ[TY + 1][TX], yN[TY + 1][TX], yT[TY + 1][TX];
+  __shared__ float sdl[2][G == 1 ? TX + 1 : 1];  // axisymmetric: centroid distances per R face
   __shared__ double red[NT / 32];
   extern __shared__ float tabf[];  // <H>_k, dnu_k, gem_k / gem_max, J_act,k as FP32 (4 nb)
   float* tH = tabf;
@@ -566,21 +650,37 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
   }
   for (int idx = tid; idx < QX * QY; idx += NT) {
     const int lx = idx % QX, ly = idx / QX;
-    const long long c = static_cast<long long>(clampi(y0 + ly - 1, ny)) * nx + clampi(x0 + lx - 1, nx);
-    qc[ly][lx] = make_float4(float(v.alpha[c]), float(v.rho[c]), float(v.ux[c]) * inv_c,
-                             float(v.uy[c]) * inv_c);
+    bool fxg, fyg;
+    const int ix = ghost<G>(x0 + lx - 1, nx, fxg), iy = ghost<G>(y0 + ly - 1, ny, fyg);
+    const long long c = static_cast<long long>(iy) * nx + ix;
+    const float wx = float(v.ux[c]) * inv_c, wy = float(v.uy[c]) * inv_c;
+    qc[ly][lx] = make_float4(float(v.alpha[c]), float(v.rho[c]), fxg ? -wx : wx, fyg ? -wy : wy);
   }
-  // halo entries owned by this thread (plane offsets)
+  if constexpr (G == 1) {
+    for (int f = tid; f <= TX; f += NT) {
+      const int gf = x0 + f <= nx ? x0 + f : nx;
+      sdl[0][f] = v.gf_dlL[gf];
+      sdl[1][f] = v.gf_dlR[gf];
+    }
+  }
+  // halo entries owned by this thread (plane offsets; sign of H_x, H_y)
   const int e0 = tid, e1 = tid + NT;
   const bool has1 = e1 < SX * SY;
   const int ex0 = e0 % SX, ey0 = e0 / SX, ex1 = e1 % SX, ey1 = e1 / SX;
-  const long long off0 = static_cast<long long>(clampi(y0 + ey0 - 2, ny)) * nx + clampi(x0 + ex0 - 2, nx);
-  const long long off1 = has1 ? static_cast<long long>(clampi(y0 + ey1 - 2, ny)) * nx + clampi(x0 + ex1 - 2, nx) : 0;
+  bool fx0, fy0, fx1 = false, fy1 = false;
+  const long long off0 = static_cast<long long>(ghost<G>(y0 + ey0 - 2, ny, fy0)) * nx +
+                         ghost<G>(x0 + ex0 - 2, nx, fx0);
+  const long long off1 = has1 ? static_cast<long long>(ghost<G>(y0 + ey1 - 2, ny, fy1)) * nx +
+                                    ghost<G>(x0 + ex1 - 2, nx, fx1)
+                              : 0;
+  const float sx0 = fx0 ? -1.0f : 1.0f, sy0 = fy0 ? -1.0f : 1.0f;
+  const float sx1 = fx1 ? -1.0f : 1.0f, sy1 = fy1 ? -1.0f : 1.0f;
   // extra faces: warp 0 -> top row of y-faces, warp 1 (lanes < TY) -> right column of x-faces
   const bool xtra_y = ty == 0, xtra_x = ty == 1 && tx < TY;
 
   I alpha_c = 0, rho_c = 0, pd_c = 0;
-  float gxx = 0, gyy = 0, gsh = 0;
+  float gxx = 0, gyy = 0, gsh = 0, gphi = 0;
+  float r0c = 0, r1c = 0, hoopc = 0, wvf = 1.0f;
   double lum_d = 0.0;
   if (valid) {
     alpha_c = I(v.alpha[cell]);
@@ -590,11 +690,19 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
     gxx = float(v.gxx[cell]);
     gyy = float(v.gyy[cell]);
     gsh = float(v.gsh[cell]);
+    if constexpr (G == 1) {
+      gphi = float(v.gphi[cell]);
+      r0c = v.gf_r0[gx];
+      r1c = v.gf_r1[gx];
+      hoopc = v.gf_hoop[gx];
+      wvf = v.gf_wv[gx];
+    }
   }
   const float half_dx = 0.5f * float(v.dx), kF_f = float(v.kF), cdt_f = float(v.cdt);
   const float inv_dx = 1.0f / float(v.dx);
   const float cdt_dx = float(v.cdt / v.dx);
   const I cdt = I(v.cdt), kabs = I(v.kabs), kF = I(v.kF), cdx = I(v.cdt / v.dx);
+  const I wR = I(v.g_wR), wcell = I(wvf);
   I ax = 0, ay = 0;
   // per-cell bookkeeping sums over the bins: FP64 (compensation-free, exact
   // enough at 194 terms) for LYM1_MIXED, plain FP32 for LYM1_MIXED_FAST; the
@@ -606,7 +714,8 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
   // the FP32 range, unlike L_cell (~1e39 erg/s) and gem_k (~1e-58) alone
   const bool src = lum_d != 0.0;
   const float jsc = float(lum_d * v.gem_max);
-  const bool bnd = valid && (gx == 0 || gx == nx - 1 || gy == 0 || gy == ny - 1);
+  const bool bnd = valid && (G == 1 ? (gx == nx - 1 || gy == ny - 1)
+                                     : (gx == 0 || gx == nx - 1 || gy == 0 || gy == ny - 1));
 
   float pJ0 = Jin[off0], pX0 = Hxin[off0], pY0 = Hyin[off0];
   float pJ1 = 0.f, pX1 = 0.f, pY1 = 0.f;
@@ -618,15 +727,22 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
   for (int k = 0; k < nb; ++k) {
     const int b = k & 1;
     {  // halo entries of bin k: registers -> shared, with primitives
+      float X0 = pX0, Y0 = pY0, X1 = pX1, Y1 = pY1;
+      if constexpr (G == 1) {
+        X0 *= sx0;
+        Y0 *= sy0;
+        X1 *= sx1;
+        Y1 *= sy1;
+      }
       const float r0 = pJ0 > kTinyJ ? frcp(pJ0) : 0.0f;
-      sq[b][ey0][ex0] = make_float4(pJ0, pX0 * r0, pY0 * r0, 0.0f);
-      sHx[b][ey0][ex0] = pX0;
-      sHy[b][ey0][ex0] = pY0;
+      sq[b][ey0][ex0] = make_float4(pJ0, X0 * r0, Y0 * r0, 0.0f);
+      sHx[b][ey0][ex0] = X0;
+      sHy[b][ey0][ex0] = Y0;
       if (has1) {
         const float r1 = pJ1 > kTinyJ ? frcp(pJ1) : 0.0f;
-        sq[b][ey1][ex1] = make_float4(pJ1, pX1 * r1, pY1 * r1, 0.0f);
-        sHx[b][ey1][ex1] = pX1;
-        sHy[b][ey1][ex1] = pY1;
+        sq[b][ey1][ex1] = make_float4(pJ1, X1 * r1, Y1 * r1, 0.0f);
+        sHx[b][ey1][ex1] = X1;
+        sHy[b][ey1][ex1] = Y1;
       }
     }
     if (k + 1 < nb) {  // prefetch bin k+1
@@ -647,18 +763,24 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
       const float4 qm = sq[b][r][fi], q0 = sq[b][r][fi + 1], q1 = sq[b][r][fi + 2],
                    q2 = sq[b][r][fi + 3];
       const float4 c0 = qc[fj + 1][fi], c1 = qc[fj + 1][fi + 1];
+      const float aF0 = c0.x * Hk + c0.y * kF_f, aF1 = c1.x * Hk + c1.y * kF_f;
+      float tau;
+      if constexpr (G == 1)
+        tau = aF0 * sdl[0][fi] + aF1 * sdl[1][fi];
+      else
+        tau = (aF0 + aF1) * half_dx;
       face_flux_f32(qm.x, qm.y, qm.z, q0.x, q0.y, q0.z, q1.x, q1.y, q1.z, q2.x, q2.y, q2.z,
-                    c0.x * Hk + c0.y * kF_f, c1.x * Hk + c1.y * kF_f, c0.z, c1.z, half_dx,
-                    xJ[fj][fi], xN[fj][fi], xT[fj][fi]);
+                    aF0, aF1, c0.z, c1.z, tau, xJ[fj][fi], xN[fj][fi], xT[fj][fi]);
     };
     auto yface = [&](int fi, int fj) {  // between tile cells (fi, fj-1) and (fi, fj)
       const int cc = fi + 2;
       const float4 qm = sq[b][fj][cc], q0 = sq[b][fj + 1][cc], q1 = sq[b][fj + 2][cc],
                    q2 = sq[b][fj + 3][cc];
       const float4 c0 = qc[fj][fi + 1], c1 = qc[fj + 1][fi + 1];
+      const float aF0 = c0.x * Hk + c0.y * kF_f, aF1 = c1.x * Hk + c1.y * kF_f;
       face_flux_f32(qm.x, qm.z, qm.y, q0.x, q0.z, q0.y, q1.x, q1.z, q1.y, q2.x, q2.z, q2.y,
-                    c0.x * Hk + c0.y * kF_f, c1.x * Hk + c1.y * kF_f, c0.w, c1.w, half_dx,
-                    yJ[fj][fi], yN[fj][fi], yT[fj][fi]);
+                    aF0, aF1, c0.w, c1.w, (aF0 + aF1) * half_dx, yJ[fj][fi], yN[fj][fi],
+                    yT[fj][fi]);
     };
     xface(tx, ty);
     yface(tx, ty);
@@ -670,12 +792,23 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
       const float J = qs.x, Hx = sHx[b][ty + 2][tx + 2], Hy = sHy[b][ty + 2][tx + 2];
       float fxc = qs.y, fyc = qs.z;
       cap_unit_f32(fxc, fyc);
-      float Dxx, Dxy, Dyy;
-      closure_f32(fxc, fyc, Dxx, Dxy, Dyy);
-      const float W = J * ((Dxx * gxx + Dyy * gyy) + Dxy * gsh);
-      const float divJ = (xJ[ty][tx + 1] - xJ[ty][tx]) + (yJ[ty + 1][tx] - yJ[ty][tx]);
-      const float divHx = (xN[ty][tx + 1] - xN[ty][tx]) + (yT[ty + 1][tx] - yT[ty][tx]);
-      const float divHy = (xT[ty][tx + 1] - xT[ty][tx]) + (yN[ty + 1][tx] - yN[ty][tx]);
+      float Dxx, Dxy, Dyy, Dpp;
+      closure_f32(fxc, fyc, Dxx, Dxy, Dyy, Dpp);
+      float W, divJ, divHx, divHy;
+      if constexpr (G == 1) {
+        // per-radian finite volumes in units of dx (r0, r1 = R-face areas x dx /
+        // Vol, hoop = dx^3 / Vol); hoop source K_phiphi <1/R> in the R equation
+        W = J * (((Dxx * gxx + Dyy * gyy) + Dxy * gsh) + Dpp * gphi);
+        divJ = (r1c * xJ[ty][tx + 1] - r0c * xJ[ty][tx]) + (yJ[ty + 1][tx] - yJ[ty][tx]);
+        divHx = ((r1c * xN[ty][tx + 1] - r0c * xN[ty][tx]) + (yT[ty + 1][tx] - yT[ty][tx])) -
+                hoopc * (Dpp * J);
+        divHy = (r1c * xT[ty][tx + 1] - r0c * xT[ty][tx]) + (yN[ty + 1][tx] - yN[ty][tx]);
+      } else {
+        W = J * ((Dxx * gxx + Dyy * gyy) + Dxy * gsh);
+        divJ = (xJ[ty][tx + 1] - xJ[ty][tx]) + (yJ[ty + 1][tx] - yJ[ty][tx]);
+        divHx = (xN[ty][tx + 1] - xN[ty][tx]) + (yT[ty + 1][tx] - yT[ty][tx]);
+        divHy = (xT[ty][tx + 1] - xT[ty][tx]) + (yN[ty + 1][tx] - yN[ty][tx]);
+      }
       const float J1 = J - cdt_f * (divJ * inv_dx + W * inv_c);
       const float Hx1 = Hx - cdt_dx * divHx;
       const float Hy1 = Hy - cdt_dx * divHy;
@@ -719,16 +852,21 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
       en += dnu * J2;
       const float j2f = float(J2), h2 = float(Hx2) * float(Hx2) + float(Hy2) * float(Hy2);
       const float jj = j2f * j2f;
-      if (j2f > tA[k]) {
+      if ((G == 1 ? j2f * wvf : j2f) > tA[k]) {
         mxf2 = fmaxf(mxf2, fdiv(h2, jj));
         bad += (h2 > jj * 1.000002f) ? 1 : 0;
       }
       if (bnd) {
         I o2 = 0;
-        if (gx == 0) o2 -= I(xJ[ty][tx]);
-        if (gx == nx - 1) o2 += I(xJ[ty][tx + 1]);
-        if (gy == 0) o2 -= I(yJ[ty][tx]);
-        if (gy == ny - 1) o2 += I(yJ[ty + 1][tx]);
+        if constexpr (G == 1) {
+          if (gx == nx - 1) o2 += wR * I(xJ[ty][tx + 1]);
+          if (gy == ny - 1) o2 += wcell * I(yJ[ty + 1][tx]);
+        } else {
+          if (gx == 0) o2 -= I(xJ[ty][tx]);
+          if (gx == nx - 1) o2 += I(xJ[ty][tx + 1]);
+          if (gy == 0) o2 -= I(yJ[ty][tx]);
+          if (gy == ny - 1) o2 += I(yJ[ty + 1][tx]);
+        }
         out += dnu * (cdx * o2);
       }
     }
@@ -739,15 +877,16 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
   }
   double* part = v.partT + static_cast<long long>(blk) * kDiagSlots;
   double s;
-  s = block_sum<NT>(double(em), red);
+  const double wd = G == 1 ? double(wvf) : 1.0;
+  s = block_sum<NT>(double(em) * wd, red);
   if (tid == 0) part[kSlotEmitted] = s;
-  s = block_sum<NT>(double(ab), red);
+  s = block_sum<NT>(double(ab) * wd, red);
   if (tid == 0) part[kSlotAbsorbed] = s;
   s = block_sum<NT>(double(out), red);
   if (tid == 0) part[kSlotOutflow] = s;
-  s = block_sum<NT>(double(wk), red);
+  s = block_sum<NT>(double(wk) * wd, red);
   if (tid == 0) part[kSlotWork] = s;
-  s = block_sum<NT>(double(en), red);
+  s = block_sum<NT>(double(en) * wd, red);
   if (tid == 0) part[kSlotEnergy] = s;
   s = block_max<NT>(sqrt(double(mxf2)), red);
   if (tid == 0) part[kSlotMaxF] = s;
@@ -755,19 +894,20 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
   if (tid == 0) part[kSlotBad] = s;
 }
 
-template <class P>
+template <class P, int G>
 __global__ void __launch_bounds__(kTileX* kTileY, 3) transport_kernel_f32(DeviceView v) {
-  transport_tile_f32<P>(v, blockIdx.x * kTileX, blockIdx.y * kTileY,
+  transport_tile_f32<P, G>(v, blockIdx.x * kTileX, blockIdx.y * kTileY,
                         blockIdx.y * gridDim.x + blockIdx.x);
 }
 
 // ------------------------------------------------------------ frequency kernel
 // Coefficients of bin k for one cell (App. A): Peclet number P_k, dlt_k/K_k and
 // E(-|P_k|) = expm1(-|P_k|) / (-|P_k|), with D_k from the post-source state.
-template <class P, class T>
+template <class P, int G, class T>
 __device__ __forceinline__ void freq_coef(typename P::F Jc, typename P::F Hxc, typename P::F Hyc,
                                           typename P::F Kc, typename P::F gxx,
-                                          typename P::F gyy, typename P::F gsh, const T* tH,
+                                          typename P::F gyy, typename P::F gsh,
+                                          typename P::F gphi, const T* tH,
                                           const T* tR, const T* tn, const T* th, int k,
                                           typename P::F& Pk, typename P::F& ak,
                                           typename P::F& ek) {
@@ -776,9 +916,10 @@ __device__ __forceinline__ void freq_coef(typename P::F Jc, typename P::F Hxc, t
     const float r = Jc > kTinyJ ? frcp(Jc) : 0.0f;
     float fx = Hxc * r, fy = Hyc * r;
     cap_unit_f32(fx, fy);
-    float Dxx, Dxy, Dyy;
-    closure_f32(fx, fy, Dxx, Dxy, Dyy);
-    const float DdU = (Dxx * gxx + Dyy * gyy) + Dxy * gsh;
+    float Dxx, Dxy, Dyy, Dpp;
+    closure_f32(fx, fy, Dxx, Dxy, Dyy, Dpp);
+    float DdU = (Dxx * gxx + Dyy * gyy) + Dxy * gsh;
+    if constexpr (G == 1) DdU = DdU + Dpp * gphi;
     const float K = Kc * tH[k];
     const float rK = frcp(K);
     const float C = K * tR[k] + tn[k] * DdU;
@@ -794,9 +935,10 @@ __device__ __forceinline__ void freq_coef(typename P::F Jc, typename P::F Hxc, t
       fy = Hyc / Jc;
     }
     cap_unit(fx, fy);
-    F Dxx, Dxy, Dyy;
-    closure(fx, fy, Dxx, Dxy, Dyy);
-    const F DdU = (Dxx * gxx + Dyy * gyy) + Dxy * gsh;
+    F Dxx, Dxy, Dyy, Dpp;
+    closure(fx, fy, Dxx, Dxy, Dyy, Dpp);
+    F DdU = (Dxx * gxx + Dyy * gyy) + Dxy * gsh;
+    if constexpr (G == 1) DdU = DdU + Dpp * gphi;  // D_phiphi <u_R / R>
     const F K = Kc * F(tH[k]);
     const F C = K * F(tR[k]) + F(tn[k]) * DdU;
     const F half = F(th[k]);
@@ -807,7 +949,7 @@ __device__ __forceinline__ void freq_coef(typename P::F Jc, typename P::F Hxc, t
   }
 }
 
-template <class P>
+template <class P, int G>
 __device__ __forceinline__ void freq_block(const DeviceView& v, int blk) {
   using S = typename P::S;
   using F = typename P::F;
@@ -863,19 +1005,25 @@ __device__ __forceinline__ void freq_block(const DeviceView& v, int blk) {
   RSum<I> en;
   I mxf = 0;
   int bad = 0;
+  // axisymmetric grid: energy weight 2 pi Vol / dx^3 of the cell's column
+  double wcell = 1.0;
+  if constexpr (G == 1)
+    if (cell < nc) wcell = v.g_wv[cell % v.nx];
+  const I wI = I(wcell);
   if (cell < nc) {
     const double alpha = v.alpha[cell];
     if (v.freq_step && alpha > 0.0) {
       const F Kc = F(v.Kc * alpha);
       const F gxx = F(v.gxx[cell]), gyy = F(v.gyy[cell]), gsh = F(v.gsh[cell]);
+      const F gphi = G == 1 ? F(v.gphi[cell]) : F(0);
       const I cdt = I(v.cdt);
       const float rcdt = float(1.0 / v.cdt);
       (void)rcdt;
       F P0, a0, e0, P1 = F(0), a1 = F(0), e1 = F(0);
       I Jin0 = I(Jin[cell]);
       I Jin1 = 0;
-      freq_coef<P>(F(Jin[cell]), F(Hxin[cell]), F(Hyin[cell]), Kc, gxx, gyy, gsh, tH, tR, tn, th,
-                   0, P0, a0, e0);
+      freq_coef<P, G>(F(Jin[cell]), F(Hxin[cell]), F(Hyin[cell]), Kc, gxx, gyy, gsh, gphi, tH, tR,
+                      tn, th, 0, P0, a0, e0);
       I qprev = 0, gprev = 0, Bprev = 0, Aprev = 0;
       // two-deep software pipeline: (nJ, nX, nY) hold bin k+1, loads for k+2 are in flight
       S nJ = S(0), nX = S(0), nY = S(0);
@@ -896,7 +1044,8 @@ __device__ __forceinline__ void freq_block(const DeviceView& v, int blk) {
             nY = Hyin[o2];
           }
           Jin1 = I(Jr);
-          freq_coef<P>(F(Jr), F(Xr), F(Yr), Kc, gxx, gyy, gsh, tH, tR, tn, th, k + 1, P1, a1, e1);
+          freq_coef<P, G>(F(Jr), F(Xr), F(Yr), Kc, gxx, gyy, gsh, gphi, tH, tR, tn, th, k + 1, P1,
+                          a1, e1);
           const F d1 = (-P0 > F(0)) ? -P0 : F(0);
           const F d2 = (P1 > F(0)) ? P1 : F(0);
           const F m = (d1 > d2) ? d1 : d2;
@@ -967,7 +1116,7 @@ __device__ __forceinline__ void freq_block(const DeviceView& v, int blk) {
         Hxout[oc] = S(Hx2);
         Hyout[oc] = S(Hy2);
         en.add(tdi[k] * Jn);
-        if (Jn > tact[k]) {
+        if ((G == 1 ? Jn * wI : Jn) > tact[k]) {
           const I hn = sqrt(Hx2 * Hx2 + Hy2 * Hy2);
           mxf = fmax(mxf, hn / Jn);
           bad += (hn > Jn * I(1.000001)) ? 1 : 0;
@@ -982,7 +1131,7 @@ __device__ __forceinline__ void freq_block(const DeviceView& v, int blk) {
         Hyout[o] = Hy;
         const I Ji = I(J), Hxi = I(Hx), Hyi = I(Hy);
         en.add(tdi[k] * Ji);
-        if (Ji > tact[k]) {
+        if ((G == 1 ? Ji * wI : Ji) > tact[k]) {
           const I hn = sqrt(Hxi * Hxi + Hyi * Hyi);
           mxf = fmax(mxf, hn / Ji);
           bad += (hn > Ji * I(1.000001)) ? 1 : 0;
@@ -992,7 +1141,7 @@ __device__ __forceinline__ void freq_block(const DeviceView& v, int blk) {
   }
   double* part = v.partF + static_cast<long long>(blk) * kDiagSlots;
   double s;
-  s = block_sum<NT>(en.value(), red);
+  s = block_sum<NT>(en.value() * wcell, red);
   if (threadIdx.x == 0) part[kSlotEnergy] = s;
   s = block_max<NT>(double(mxf), red);
   if (threadIdx.x == 0) part[kSlotMaxF] = s;
@@ -1062,7 +1211,7 @@ __device__ __forceinline__ void fence_mbar_init() {
 // streamed through the ring (cell count a multiple of 4, so that every row
 // segment starts on a 16-byte boundary and is a whole number of 16 bytes).
 // Same arithmetic, in the same order, as freq_block.
-template <class P>
+template <class P, int G>
 __device__ __forceinline__ void freq_block_bulk(const DeviceView& v, int blk) {
   using F = typename P::F;
   using I = typename P::I;
@@ -1121,6 +1270,14 @@ __device__ __forceinline__ void freq_block_bulk(const DeviceView& v, int blk) {
   const F Kc = F(v.Kc * alpha);
   const F gxx = valid ? F(v.gxx[cell]) : F(0), gyy = valid ? F(v.gyy[cell]) : F(0),
           gsh = valid ? F(v.gsh[cell]) : F(0);
+  F gphi = F(0);
+  double wcell = 1.0;  // axisymmetric grid: energy weight of the cell's column
+  if constexpr (G == 1)
+    if (valid) {
+      gphi = F(v.gphi[cell]);
+      wcell = v.g_wv[cell % v.nx];
+    }
+  const I wI = I(wcell);
   const I cdt = I(v.cdt);
   const float rcdt = float(1.0 / v.cdt);
   (void)rcdt;
@@ -1176,7 +1333,7 @@ __device__ __forceinline__ void freq_block_bulk(const DeviceView& v, int blk) {
     if (act) {
       const F Jc = F(ring[s][0][tid]), Xc = F(ring[s][1][tid]), Yc = F(ring[s][2][tid]);
       F Pk, ak, ek;
-      freq_coef<P>(Jc, Xc, Yc, Kc, gxx, gyy, gsh, tH, tR, tn, th, k, Pk, ak, ek);
+      freq_coef<P, G>(Jc, Xc, Yc, Kc, gxx, gyy, gsh, gphi, tH, tR, tn, th, k, Pk, ak, ek);
       if (k > 0) {
         const F d1 = (-Pp > F(0)) ? -Pp : F(0);
         const F d2 = (Pk > F(0)) ? Pk : F(0);
@@ -1268,7 +1425,7 @@ __device__ __forceinline__ void freq_block_bulk(const DeviceView& v, int blk) {
         Hxout[o] = float(Hx2);
         Hyout[o] = float(Hy2);
         en.add(tdi[k] * Jn);
-        if (Jn > tact[k]) {
+        if ((G == 1 ? Jn * wI : Jn) > tact[k]) {
           const I hn = sqrt(Hx2 * Hx2 + Hy2 * Hy2);
           mxf = fmax(mxf, hn / Jn);
           bad += (hn > Jn * I(1.000001)) ? 1 : 0;
@@ -1279,7 +1436,7 @@ __device__ __forceinline__ void freq_block_bulk(const DeviceView& v, int blk) {
         Hyout[o] = Yo;
         const I Ji = I(Jo), Hxi = I(Xo), Hyi = I(Yo);
         en.add(tdi[k] * Ji);
-        if (Ji > tact[k]) {
+        if ((G == 1 ? Ji * wI : Ji) > tact[k]) {
           const I hn = sqrt(Hxi * Hxi + Hyi * Hyi);
           mxf = fmax(mxf, hn / Ji);
           bad += (hn > Ji * I(1.000001)) ? 1 : 0;
@@ -1291,7 +1448,7 @@ __device__ __forceinline__ void freq_block_bulk(const DeviceView& v, int blk) {
   }
   double* part = v.partF + static_cast<long long>(blk) * kDiagSlots;
   double sres;
-  sres = block_sum<NT>(en.value(), red);
+  sres = block_sum<NT>(en.value() * wcell, red);
   if (tid == 0) part[kSlotEnergy] = sres;
   sres = block_max<NT>(double(mxf), red);
   if (tid == 0) part[kSlotMaxF] = sres;
@@ -1301,123 +1458,158 @@ __device__ __forceinline__ void freq_block_bulk(const DeviceView& v, int blk) {
 
 // FP32 state with a cell count that is a multiple of 4 takes the bulk-copy
 // pipeline; everything else the register-prefetch sweep
-template <class P>
+template <class P, int G>
 __device__ __forceinline__ void freq_dispatch(const DeviceView& v, int blk) {
   if constexpr (sizeof(typename P::S) == 4) {
     if ((v.nc & 3) == 0) {
-      freq_block_bulk<P>(v, blk);
+      freq_block_bulk<P, G>(v, blk);
       return;
     }
   }
-  freq_block<P>(v, blk);
+  freq_block<P, G>(v, blk);
 }
 
 // FP32 state: at most 64 registers so that 8 blocks (32 warps) per SM keep
 // enough loads in flight for the latency-bound bin sweeps
-template <class P>
+template <class P, int G>
 __global__ void __launch_bounds__(kFreqThreads, sizeof(typename P::S) == 4 ? 8 : 1)
     freq_kernel(DeviceView v) {
-  freq_dispatch<P>(v, blockIdx.x);
+  freq_dispatch<P, G>(v, blockIdx.x);
 }
 
 // ------------------------------------------------------------ batched launches
 // Persistent kernels over a work list that spans several contexts (clouds of
-// different sizes): each item names a context and a tile (transport) or a
-// block of cells (frequency step); blocks walk the list with a grid stride.
+// different sizes, one geometry): each item names a context and a tile
+// (transport) or a block of cells (frequency step); blocks walk the list with
+// a grid stride.
 struct BatchItem {
   int ctx, x0, y0, blk;
 };
 
-template <class P>
+template <class P, int G>
 __global__ void __launch_bounds__(kTileX* kTileY) transport_batched(const DeviceView* views,
                                                                     const BatchItem* items, int n) {
   for (int i = blockIdx.x; i < n; i += gridDim.x) {
     const BatchItem it = items[i];
     const DeviceView v = views[it.ctx];
-    transport_tile<P>(v, it.x0, it.y0, it.blk);
+    transport_tile<P, G>(v, it.x0, it.y0, it.blk);
     __syncthreads();
   }
 }
 
-template <class P>
+template <class P, int G>
 __global__ void __launch_bounds__(kTileX* kTileY, 3) transport_batched_f32(const DeviceView* views,
                                                                            const BatchItem* items,
                                                                            int n) {
   for (int i = blockIdx.x; i < n; i += gridDim.x) {
     const BatchItem it = items[i];
     const DeviceView v = views[it.ctx];
-    transport_tile_f32<P>(v, it.x0, it.y0, it.blk);
+    transport_tile_f32<P, G>(v, it.x0, it.y0, it.blk);
     __syncthreads();
   }
 }
 
-template <class P>
+template <class P, int G>
 __global__ void __launch_bounds__(kFreqThreads, sizeof(typename P::S) == 4 ? 8 : 1)
     freq_batched(const DeviceView* views, const BatchItem* items, int n) {
   for (int i = blockIdx.x; i < n; i += gridDim.x) {
     const BatchItem it = items[i];
     const DeviceView v = views[it.ctx];
-    freq_dispatch<P>(v, it.blk);
+    freq_dispatch<P, G>(v, it.blk);
     __syncthreads();
   }
 }
 
-template <class P>
-int launch_transport_batched_t(const DeviceView* views, const BatchItem* items, int n, int grid,
+template <class P, int G>
+int launch_transport_batched_g(const DeviceView* views, const BatchItem* items, int n, int grid,
                                int nb_max, cudaStream_t st) {
   if constexpr (sizeof(typename P::S) == 4) {
     const size_t smem = sizeof(float) * 4 * static_cast<size_t>(nb_max);
-    transport_batched_f32<P><<<grid, dim3(kTileX, kTileY), smem, st>>>(views, items, n);
+    transport_batched_f32<P, G><<<grid, dim3(kTileX, kTileY), smem, st>>>(views, items, n);
   } else {
-    transport_batched<P><<<grid, dim3(kTileX, kTileY), 0, st>>>(views, items, n);
+    transport_batched<P, G><<<grid, dim3(kTileX, kTileY), 0, st>>>(views, items, n);
   }
   return static_cast<int>(cudaGetLastError());
 }
 
-template <class P>
-int launch_freq_batched_t(const DeviceView* views, const BatchItem* items, int n, int grid,
+template <class P, int G>
+int launch_freq_batched_g(const DeviceView* views, const BatchItem* items, int n, int grid,
                           int nb_max, cudaStream_t st) {
   const size_t smem = sizeof(double) * 7 * static_cast<size_t>(nb_max);
-  freq_batched<P><<<grid, kFreqThreads, smem, st>>>(views, items, n);
+  freq_batched<P, G><<<grid, kFreqThreads, smem, st>>>(views, items, n);
   return static_cast<int>(cudaGetLastError());
 }
 
 template <class P>
-int max_resident_transport() {
-  int nblk = 0;
-  if constexpr (sizeof(typename P::S) == 4)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nblk, transport_batched_f32<P>, kTileX * kTileY,
-                                                  sizeof(float) * 4 * 194);
-  else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nblk, transport_batched<P>, kTileX * kTileY, 0);
-  return nblk < 1 ? 1 : nblk;
+int launch_transport_batched_t(int geometry, const DeviceView* views, const BatchItem* items, int n,
+                               int grid, int nb_max, cudaStream_t st) {
+  return geometry == 1 ? launch_transport_batched_g<P, 1>(views, items, n, grid, nb_max, st)
+                       : launch_transport_batched_g<P, 0>(views, items, n, grid, nb_max, st);
 }
 
 template <class P>
-int max_resident_freq() {
+int launch_freq_batched_t(int geometry, const DeviceView* views, const BatchItem* items, int n,
+                          int grid, int nb_max, cudaStream_t st) {
+  return geometry == 1 ? launch_freq_batched_g<P, 1>(views, items, n, grid, nb_max, st)
+                       : launch_freq_batched_g<P, 0>(views, items, n, grid, nb_max, st);
+}
+
+template <class P, int G>
+int max_resident_transport_g() {
   int nblk = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nblk, freq_batched<P>, kFreqThreads,
+  if constexpr (sizeof(typename P::S) == 4)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nblk, transport_batched_f32<P, G>,
+                                                  kTileX * kTileY, sizeof(float) * 4 * 194);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nblk, transport_batched<P, G>, kTileX * kTileY, 0);
+  return nblk < 1 ? 1 : nblk;
+}
+
+template <class P, int G>
+int max_resident_freq_g() {
+  int nblk = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nblk, freq_batched<P, G>, kFreqThreads,
                                                 sizeof(double) * 7 * 194);
   return nblk < 1 ? 1 : nblk;
 }
 
 template <class P>
-int launch_transport_t(const DeviceView& v, cudaStream_t st) {
+int max_resident_transport(int geometry) {
+  return geometry == 1 ? max_resident_transport_g<P, 1>() : max_resident_transport_g<P, 0>();
+}
+
+template <class P>
+int max_resident_freq(int geometry) {
+  return geometry == 1 ? max_resident_freq_g<P, 1>() : max_resident_freq_g<P, 0>();
+}
+
+template <class P, int G>
+int launch_transport_g(const DeviceView& v, cudaStream_t st) {
   dim3 grid((v.nx + kTileX - 1) / kTileX, (v.ny + kTileY - 1) / kTileY);
   if constexpr (sizeof(typename P::S) == 4) {
     const size_t smem = sizeof(float) * 4 * static_cast<size_t>(v.nb);
-    transport_kernel_f32<P><<<grid, dim3(kTileX, kTileY), smem, st>>>(v);
+    transport_kernel_f32<P, G><<<grid, dim3(kTileX, kTileY), smem, st>>>(v);
   } else {
-    transport_kernel<P><<<grid, dim3(kTileX, kTileY), 0, st>>>(v);
+    transport_kernel<P, G><<<grid, dim3(kTileX, kTileY), 0, st>>>(v);
   }
   return static_cast<int>(cudaGetLastError());
 }
 
+template <class P, int G>
+int launch_freq_g(const DeviceView& v, cudaStream_t st) {
+  const size_t smem = sizeof(double) * 7 * static_cast<size_t>(v.nb);
+  freq_kernel<P, G><<<freq_blocks(v.nc), kFreqThreads, smem, st>>>(v);
+  return static_cast<int>(cudaGetLastError());
+}
+
+template <class P>
+int launch_transport_t(const DeviceView& v, cudaStream_t st) {
+  return v.geometry == 1 ? launch_transport_g<P, 1>(v, st) : launch_transport_g<P, 0>(v, st);
+}
+
 template <class P>
 int launch_freq_t(const DeviceView& v, cudaStream_t st) {
-  const size_t smem = sizeof(double) * 7 * static_cast<size_t>(v.nb);
-  freq_kernel<P><<<freq_blocks(v.nc), kFreqThreads, smem, st>>>(v);
-  return static_cast<int>(cudaGetLastError());
+  return v.geometry == 1 ? launch_freq_g<P, 1>(v, st) : launch_freq_g<P, 0>(v, st);
 }
 
 }  // namespace lym1

@@ -15,34 +15,57 @@ int launch_freq_det(const DeviceView& v, void* st) {
   return launch_freq_t<PolDet>(v, static_cast<cudaStream_t>(st));
 }
 
-int launch_batched_det(int kind, const DeviceView* views, const void* items, int n, int grid,
-                       int nb_max, void* st) {
+int launch_batched_det(int kind, int geometry, const DeviceView* views, const void* items, int n,
+                       int grid, int nb_max, void* st) {
   const cudaStream_t s = static_cast<cudaStream_t>(st);
   const BatchItem* it = static_cast<const BatchItem*>(items);
-  if (kind == 0) return launch_transport_batched_t<PolDet>(views, it, n, grid, nb_max, s);
-  return launch_freq_batched_t<PolDet>(views, it, n, grid, nb_max, s);
+  if (kind == 0) return launch_transport_batched_t<PolDet>(geometry, views, it, n, grid, nb_max, s);
+  return launch_freq_batched_t<PolDet>(geometry, views, it, n, grid, nb_max, s);
 }
 
-int resident_blocks_det(int kind) {
-  return kind == 0 ? max_resident_transport<PolDet>() : max_resident_freq<PolDet>();
+int resident_blocks_det(int kind, int geometry) {
+  return kind == 0 ? max_resident_transport<PolDet>(geometry) : max_resident_freq<PolDet>(geometry);
 }
 
 
 // alpha = n_HI sigma0; velocity gradients by central differences over the
-// two neighbours, ghosts = edge values (outflow boundaries).
+// two neighbours.  Geometry 0: ghosts = edge values (outflow boundaries).
+// Geometry 1 (R = x, Z = y): the ghost across the axis (midplane) mirrors the
+// first column (row) with u_R (u_Z) negated; <u_R / R> from the mean of the
+// two R-face velocities over the mean face radius.
 __global__ void setup_statics_kernel(const double* n_hi, const double* ux, const double* uy,
                                      double sigma0, int nx, int ny, double dx, double* alpha,
-                                     double* gxx, double* gyy, double* gsh) {
+                                     double* gxx, double* gyy, double* gsh, int geometry,
+                                     double* gphi) {
   const long long id = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
   const long long nc = static_cast<long long>(nx) * ny;
   if (id >= nc) return;
   const int i = static_cast<int>(id % nx), j = static_cast<int>(id / nx);
+  const double h2 = 2.0 * dx;
+  alpha[id] = n_hi[id] * sigma0;
+  if (geometry == 1) {
+    bool fm, fp, gm, gp;
+    const int im = ghost<1>(i - 1, nx, fm), ip = ghost<1>(i + 1, nx, fp);
+    const int jm = ghost<1>(j - 1, ny, gm), jp = ghost<1>(j + 1, ny, gp);
+    const long long row = static_cast<long long>(j) * nx;
+    const double uRm = ux[row + im] * (fm ? -1.0 : 1.0);
+    const double uRp = ux[row + ip];
+    const double uZm = uy[static_cast<long long>(jm) * nx + i] * (gm ? -1.0 : 1.0);
+    const double uZp = uy[static_cast<long long>(jp) * nx + i];
+    const double uZl = uy[row + im], uZr = uy[row + ip];
+    const double uRd = ux[static_cast<long long>(jm) * nx + i];
+    const double uRu = ux[static_cast<long long>(jp) * nx + i];
+    gxx[id] = (uRp - uRm) / h2;
+    gyy[id] = (uZp - uZm) / h2;
+    gsh[id] = (uRu - uRd) / h2 + (uZr - uZl) / h2;
+    const double fL = 0.5 * (uRm + ux[id]), fR = 0.5 * (ux[id] + uRp);
+    gphi[id] = (fR + fL) / ((i + 1) * dx + i * dx);
+    return;
+  }
   const long long xm = static_cast<long long>(j) * nx + clampi(i - 1, nx);
   const long long xp = static_cast<long long>(j) * nx + clampi(i + 1, nx);
   const long long ym = static_cast<long long>(clampi(j - 1, ny)) * nx + i;
   const long long yp = static_cast<long long>(clampi(j + 1, ny)) * nx + i;
-  const double h2 = 2.0 * dx;
-  alpha[id] = n_hi[id] * sigma0;
   gxx[id] = (ux[xp] - ux[xm]) / h2;
   gyy[id] = (uy[yp] - uy[ym]) / h2;
   gsh[id] = (ux[yp] - ux[ym]) / h2 + (uy[xp] - uy[xm]) / h2;
@@ -50,12 +73,18 @@ __global__ void setup_statics_kernel(const double* n_hi, const double* ux, const
 
 int launch_setup_statics(const double* n_hi, const double* ux, const double* uy, double sigma0,
                          int nx, int ny, double dx, double* alpha, double* gxx, double* gyy,
-                         double* gsh, void* st) {
+                         double* gsh, int geometry, double* gphi, void* st) {
   const long long nc = static_cast<long long>(nx) * ny;
   const int blocks = static_cast<int>((nc + 255) / 256);
   setup_statics_kernel<<<blocks, 256, 0, static_cast<cudaStream_t>(st)>>>(
-      n_hi, ux, uy, sigma0, nx, ny, dx, alpha, gxx, gyy, gsh);
+      n_hi, ux, uy, sigma0, nx, ny, dx, alpha, gxx, gyy, gsh, geometry, gphi);
   return static_cast<int>(cudaGetLastError());
+}
+
+__global__ void scale_columns_kernel(double* a, const double* w, int nx, long long nc) {
+  for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < nc;
+       i += static_cast<long long>(gridDim.x) * blockDim.x)
+    a[i] = a[i] / w[i % nx];
 }
 
 template <class S>
@@ -77,6 +106,11 @@ static int grid_for(long long n) {
   return static_cast<int>(b < 1 ? 1 : b);
 }
 
+int launch_scale_columns(double* lum, const double* V2pi, int nx, long long nc, void* st) {
+  scale_columns_kernel<<<grid_for(nc), 256, 0, static_cast<cudaStream_t>(st)>>>(lum, V2pi, nx, nc);
+  return static_cast<int>(cudaGetLastError());
+}
+
 int launch_convert_out(int precision, const void* src, double* dst, long long n, double scale,
                        void* st) {
   const cudaStream_t s = static_cast<cudaStream_t>(st);
@@ -96,26 +130,32 @@ int launch_convert_in(int precision, const double* src, void* dst, long long n, 
   return static_cast<int>(cudaGetLastError());
 }
 
-// energy of a state: per-block partials of sum_k dnu_k J_k
+// energy of a state: per-block partials of sum_k dnu_k J_k (times the
+// column weight on the axisymmetric grid)
 template <class S>
 __global__ void __launch_bounds__(kFreqThreads) energy_kernel(const S* J, const double* dnu, int nb,
-                                                              long long nc, double* part) {
+                                                              long long nc, double* part,
+                                                              const double* wcol, int nx) {
   __shared__ double red[kFreqThreads / 32];
   const long long cell = static_cast<long long>(blockIdx.x) * kFreqThreads + threadIdx.x;
   double en = 0.0;
-  if (cell < nc)
+  if (cell < nc) {
     for (int k = 0; k < nb; ++k) en += dnu[k] * static_cast<double>(J[static_cast<long long>(k) * nc + cell]);
+    if (wcol) en *= wcol[cell % nx];
+  }
   const double s = block_sum<kFreqThreads>(en, red);
   if (threadIdx.x == 0) part[static_cast<long long>(blockIdx.x) * kDiagSlots + kSlotEnergy] = s;
 }
 
 int launch_energy(int precision, const void* J, const double* dnu, int nb, long long nc,
-                  double* part, void* st) {
+                  double* part, const double* wcol, int nx, void* st) {
   const cudaStream_t s = static_cast<cudaStream_t>(st);
   if (precision >= 2)
-    energy_kernel<float><<<freq_blocks(nc), kFreqThreads, 0, s>>>(static_cast<const float*>(J), dnu, nb, nc, part);
+    energy_kernel<float><<<freq_blocks(nc), kFreqThreads, 0, s>>>(static_cast<const float*>(J), dnu, nb, nc,
+                                                                  part, wcol, nx);
   else
-    energy_kernel<double><<<freq_blocks(nc), kFreqThreads, 0, s>>>(static_cast<const double*>(J), dnu, nb, nc, part);
+    energy_kernel<double><<<freq_blocks(nc), kFreqThreads, 0, s>>>(static_cast<const double*>(J), dnu, nb,
+                                                                   nc, part, wcol, nx);
   return static_cast<int>(cudaGetLastError());
 }
 
@@ -195,17 +235,24 @@ int launch_finalize(const double* partT, int nT, const double* partE, int nE, do
   return static_cast<int>(cudaGetLastError());
 }
 
-// force sums over cells: |f| dV and f . r_hat dV (r from the box centre)
+// force sums over cells: |f| dV and f . r_hat dV.  Geometry 0: r from the box
+// centre, dV = dx^3.  Geometry 1: r from the origin (R, Z) = (0, 0), dV the
+// ring volume 2 pi Vol of the cell.
 __global__ void __launch_bounds__(256) force_reduce_kernel(const double* fx, const double* fy,
                                                            int nx, int ny, double dx,
-                                                           double* part) {
+                                                           int geometry, double* part) {
   __shared__ double red[8];
   const long long nc = static_cast<long long>(nx) * ny;
   double a = 0.0, r = 0.0;
-  const double V = (dx * dx) * dx, cx = 0.5 * nx * dx, cy = 0.5 * ny * dx;
+  const double cx = geometry == 1 ? 0.0 : 0.5 * nx * dx, cy = geometry == 1 ? 0.0 : 0.5 * ny * dx;
   for (long long id = static_cast<long long>(blockIdx.x) * 256 + threadIdx.x; id < nc;
        id += static_cast<long long>(gridDim.x) * 256) {
     const int i = static_cast<int>(id % nx), j = static_cast<int>(id / nx);
+    double V = (dx * dx) * dx;
+    if (geometry == 1) {
+      const double Rm = i * dx, Rp = (i + 1) * dx;
+      V = (2.0 * kPi) * ((0.5 * (Rp * Rp - Rm * Rm)) * dx);
+    }
     const double x = (i + 0.5) * dx - cx, y = (j + 0.5) * dx - cy, rr = sqrt(x * x + y * y);
     a += sqrt(fx[id] * fx[id] + fy[id] * fy[id]) * V;
     if (rr > 0.0) r += ((fx[id] * x + fy[id] * y) / rr) * V;
@@ -219,8 +266,9 @@ __global__ void __launch_bounds__(256) force_reduce_kernel(const double* fx, con
 }
 
 int launch_force_reduce(const double* fx, const double* fy, int nx, int ny, double dx,
-                        double* part, int nblocks, void* st) {
-  force_reduce_kernel<<<nblocks, 256, 0, static_cast<cudaStream_t>(st)>>>(fx, fy, nx, ny, dx, part);
+                        int geometry, double* part, int nblocks, void* st) {
+  force_reduce_kernel<<<nblocks, 256, 0, static_cast<cudaStream_t>(st)>>>(fx, fy, nx, ny, dx,
+                                                                          geometry, part);
   return static_cast<int>(cudaGetLastError());
 }
 

@@ -120,7 +120,7 @@ int paper_frequency_grid(double T_min, double q, std::vector<double>* edges) {
 // carries <H> = eta = sum_k w_k <H>_k over the given grid, width 1 (so J is the
 // frequency-integrated mean intensity) and no frequency step.
 void build_tables(const std::vector<double>& edges, double T, double dx, int gray, int recoil,
-                  BinTables* t) {
+                  BinTables* t, int geometry) {
   const int n = static_cast<int>(edges.size()) - 1;
   const LineConstants lc = line_constants(T);
   std::vector<double> dnu(n), nubar(n), Hv(n), w(n);
@@ -142,7 +142,7 @@ void build_tables(const std::vector<double>& edges, double T, double dx, int gra
   t->lc = lc;
   t->eta = eta;
   t->hkT = kPlanck / (kBoltzmann * T);
-  const double V = (dx * dx) * dx;
+  const double V = geometry == 1 ? 1.0 : (dx * dx) * dx;
   const double fourpiV = (4.0 * kPi) * V;
   const int nb = gray ? 1 : n;
   t->nb = nb;
@@ -170,6 +170,59 @@ void build_tables(const std::vector<double>& edges, double T, double dx, int gra
     t->Rk[k] = recoil ? (t->hkT - 2.0 / nubar[k]) : 0.0;
     t->half[k] = 0.5 * dnu[k];
     t->nubar_c[k] = nubar[k] / kLight;
+  }
+}
+
+}  // namespace lym1
+
+namespace lym1 {
+
+// Axisymmetric finite-volume geometry, per radian (cells [i dx, (i+1) dx] in R).
+void build_cyl_tables(int nx, double dx, CylTables* g) {
+  g->AR.assign(nx + 1, 0.0);
+  g->dlL.assign(nx + 1, 0.0);
+  g->dlR.assign(nx + 1, 0.0);
+  g->AZ.assign(nx, 0.0);
+  g->Vol.assign(nx, 0.0);
+  g->invR.assign(nx, 0.0);
+  g->V2pi.assign(nx, 0.0);
+  g->wv.assign(nx, 0.0);
+  std::vector<double> Rbar(nx);
+  const double dx3 = (dx * dx) * dx;
+  for (int i = 0; i < nx; ++i) {
+    const double Rm = i * dx, Rp = (i + 1) * dx;
+    g->AZ[i] = 0.5 * (Rp * Rp - Rm * Rm);
+    g->Vol[i] = g->AZ[i] * dx;
+    // centroid of the annulus: int R^2 dR / int R dR
+    Rbar[i] = (2.0 / 3.0) * ((Rp * Rp * Rp - Rm * Rm * Rm) / (Rp * Rp - Rm * Rm));
+    g->invR[i] = (dx * dx) / g->Vol[i];
+    g->V2pi[i] = (2.0 * kPi) * g->Vol[i];
+    g->wv[i] = g->V2pi[i] / dx3;
+  }
+  for (int i = 0; i <= nx; ++i) {
+    const double Rf = i * dx;
+    g->AR[i] = Rf * dx;
+    const double left = (i == 0) ? -Rbar[0] : Rbar[i - 1];
+    const double right = (i == nx) ? Rbar[nx - 1] + dx : Rbar[i];
+    g->dlL[i] = Rf - left;
+    g->dlR[i] = right - Rf;
+  }
+  g->wR = (2.0 * kPi) * g->AR[nx] / (dx * dx);
+  g->r0.resize(nx);
+  g->r1.resize(nx);
+  g->hoop.resize(nx);
+  g->fwv.resize(nx);
+  g->fdlL.resize(nx + 1);
+  g->fdlR.resize(nx + 1);
+  for (int i = 0; i < nx; ++i) {
+    g->r0[i] = static_cast<float>(g->AR[i] * dx / g->Vol[i]);
+    g->r1[i] = static_cast<float>(g->AR[i + 1] * dx / g->Vol[i]);
+    g->hoop[i] = static_cast<float>(g->invR[i] * dx);
+    g->fwv[i] = static_cast<float>(g->wv[i]);
+  }
+  for (int i = 0; i <= nx; ++i) {
+    g->fdlL[i] = static_cast<float>(g->dlL[i]);
+    g->fdlR[i] = static_cast<float>(g->dlR[i]);
   }
 }
 

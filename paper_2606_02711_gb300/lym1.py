@@ -168,11 +168,12 @@ class Context:
 
     def __init__(self, *, nx, ny, dx, n_hi, rho_d, p_d, ux, uy, T=1e4, kappa_abs=0.0,
                  kappa_F=0.0, c_tilde=0.0, cfl=0.0, recoil=True, freq_step=True, gray=False,
-                 edges=None, q=0.0, T_min=0.0, precision=FP64_DET, stream=None, lum=None):
+                 edges=None, q=0.0, T_min=0.0, precision=FP64_DET, stream=None, lum=None,
+                 geometry=0):
         keep = []
         if isinstance(precision, str):
             precision = PRECISIONS[precision]
-        g = lym1_grid(int(nx), int(ny), float(dx), 0, (C.c_int * 4)(0, 0, 0, 0))
+        g = lym1_grid(int(nx), int(ny), float(dx), int(geometry), (C.c_int * 4)(0, 0, 0, 0))
         if edges is not None:
             e = np.ascontiguousarray(edges, dtype=np.float64)
             keep.append(e)
@@ -364,4 +365,5 @@ def from_cloud(cloud, precision=FP64_DET, stream=None, edges=None) -> Context:
                    p_d=cloud.p_d, ux=cloud.ux, uy=cloud.uy, T=cloud.T, kappa_abs=cloud.kappa_abs,
                    kappa_F=cloud.kappa_F, c_tilde=cloud.c_tilde, cfl=cloud.cfl,
                    recoil=cloud.recoil, freq_step=cloud.freq_step, gray=cloud.gray, edges=edges,
-                   precision=precision, stream=stream, lum=cloud.lum)
+                   precision=precision, stream=stream, lum=cloud.lum,
+                   geometry=getattr(cloud, "geometry", 0))
