@@ -69,8 +69,11 @@ typedef struct {
                       outflow; finite volumes per radian with the hoop source of div K; a
                       cell's lum is emitted into its full ring volume 2 pi Vol; energies and
                       force integrals cover the ring volumes of the half-space Z > 0 */
-  int bc[4];       /* x-, x+, y-, y+ : 0 = the boundaries of the geometry; the only value
-                      accepted */
+  int bc[4];       /* x-, x+, y-, y+ outflow kind: 0 = zero gradient (two ghost layers copying
+                      the edge cell); 1 = outflow into vacuum (the ghosts carry no radiation,
+                      opacities and velocities are copied: radiation leaves and never enters,
+                      for clouds surrounded by vacuum as in Sec. 4).  The mirrored sides of
+                      geometry 1 (x- and y-) ignore their entry. */
 } lym1_grid;
 
 typedef struct {

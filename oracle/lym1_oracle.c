@@ -27,7 +27,12 @@
  * Readings where the paper is silent (each also listed in the design notes):
  *   - Cartesian geometry: face optical depth tau = aF_i dx/2 + aF_{i+1} dx/2,
  *     D:grad u = Dxx dux/dx + Dyy duy/dy + Dxy (dux/dy + duy/dx).
- *   - outflow boundaries = two ghost layers copying the edge cell (all fields).
+ *   - outflow boundaries: two ghost layers per side, either copying the edge
+ *     cell (zero gradient, the default) or, for a cloud surrounded by vacuum
+ *     (Sec. 4 test set-ups), holding no radiation while the opacities and
+ *     velocities are copied, so that radiation leaves but never enters.  The
+ *     zero-gradient ghosts let an inward flux at the edge feed the edge cell,
+ *     which grew without bound in the vacuum gap of the 256^2 cone test.
  *   - face velocity = mean of the two cells; the upwind donor is the
  *     reconstructed state on the upwind side.
  *   - velocity gradients by central differences over the two neighbours.
@@ -331,6 +336,10 @@ typedef struct {
     const double *lum;   /* [ny][nx] erg/s emitted in the cell */
     int geometry;        /* 0: 2D Cartesian slab; 1: axisymmetric cylindrical (R = x, Z = y) with
                             the axis at R = 0 and the midplane at Z = 0 mirrored */
+    int bc[4];           /* x-, x+, y-, y+ outflow kind: 0 = ghosts copy the edge cell
+                            (zero gradient); 1 = outflow into vacuum (ghosts carry no
+                            radiation; opacities and velocities are still copied); the
+                            mirrored sides of geometry 1 ignore their entry */
 } lym1o_problem;
 
 typedef struct {
@@ -359,6 +368,12 @@ typedef struct {
 
 static int o_cl(int i, int n) { return i < 0 ? 0 : (i >= n ? n - 1 : i); }
 
+/* 1 where index i lies beyond an edge whose outflow kind is vacuum */
+static int o_vac(int i, int n, int bc_lo, int bc_hi)
+{
+    return (i < 0 && bc_lo == 1) || (i >= n && bc_hi == 1);
+}
+
 void lym1o_destroy(lym1o_ctx *c)
 {
     if (!c) return;
@@ -384,6 +399,8 @@ static int o_mir(int i, int n, int *flip)
 lym1o_ctx *lym1o_create(const lym1o_problem *p)
 {
     if (p->nx < 1 || p->ny < 1 || p->nbins < 1 || p->dx <= 0.0) return NULL;
+    for (int s = 0; s < 4; ++s)
+        if (p->bc[s] != 0 && p->bc[s] != 1) return NULL;
     lym1o_ctx *c = (lym1o_ctx *)calloc(1, sizeof *c);
     c->p = *p;
     int nx = p->nx, ny = p->ny, N = p->nbins;
@@ -552,6 +569,24 @@ void lym1o_closure(double fx, double fy, double *D3 /* Dxx, Dxy, Dyy */)
 
 /* interpolation factor between GLF and diffusion fluxes (Sec. 2.1) */
 double lym1o_eps(double tau) { return (0.2 + tau) / ((0.2 + tau) + tau * tau); }
+
+/* Step 3 leaves every cell causal (Sec. 2.1 step 3: |H|/J <= 1 with H
+ * rescaled by J_new/J_old): an H longer than J is shortened to J along its
+ * direction, and H = 0 where J <= 0. */
+static void o_causal(double J, double *Hx, double *Hy)
+{
+    double hn = sqrt((*Hx) * (*Hx) + (*Hy) * (*Hy));
+    if (hn > J) {
+        if (J > 0.0) {
+            double s = J / hn;
+            *Hx = (*Hx) * s;
+            *Hy = (*Hy) * s;
+        } else {
+            *Hx = 0.0;
+            *Hy = 0.0;
+        }
+    }
+}
 
 static double o_minmod(double a, double b)
 {
@@ -838,28 +873,32 @@ int lym1o_substep(const lym1o_ctx *c, double dt, const double *J, const double *
 #pragma omp parallel for schedule(static)
         for (int j = 0; j < ny; ++j)
             for (int i = 0; i <= nx; ++i) {
-                size_t im = (size_t)j * nx + o_cl(i - 2, nx), i0 = (size_t)j * nx + o_cl(i - 1, nx);
-                size_t i1 = (size_t)j * nx + o_cl(i, nx), i2 = (size_t)j * nx + o_cl(i + 1, nx);
-                o_prim qm = o_make_prim(Jk[im], Hxk[im], Hyk[im]);
-                o_prim q0 = o_make_prim(Jk[i0], Hxk[i0], Hyk[i0]);
-                o_prim q1 = o_make_prim(Jk[i1], Hxk[i1], Hyk[i1]);
-                o_prim q2 = o_make_prim(Jk[i2], Hxk[i2], Hyk[i2]);
+                o_prim q[4];
+                for (int m = 0; m < 4; ++m) {
+                    int ii = i - 2 + m;
+                    size_t id = (size_t)j * nx + o_cl(ii, nx);
+                    q[m] = o_vac(ii, nx, p->bc[0], p->bc[1]) ? o_make_prim(0.0, 0.0, 0.0)
+                                                              : o_make_prim(Jk[id], Hxk[id], Hyk[id]);
+                }
+                size_t i0 = (size_t)j * nx + o_cl(i - 1, nx), i1 = (size_t)j * nx + o_cl(i, nx);
                 size_t f = (size_t)j * (nx + 1) + i;
-                o_face(qm, q0, q1, q2, AF(i0), AF(i1), p->ux[i0], p->ux[i1], half_dx, half_dx,
+                o_face(q[0], q[1], q[2], q[3], AF(i0), AF(i1), p->ux[i0], p->ux[i1], half_dx, half_dx,
                        &FJx[f], &FHxx[f], &FHyx[f]);
             }
         /* y faces: face j sits between rows j-1 and j, j = 0..ny */
 #pragma omp parallel for schedule(static)
         for (int j = 0; j <= ny; ++j)
             for (int i = 0; i < nx; ++i) {
-                size_t im = (size_t)o_cl(j - 2, ny) * nx + i, i0 = (size_t)o_cl(j - 1, ny) * nx + i;
-                size_t i1 = (size_t)o_cl(j, ny) * nx + i, i2 = (size_t)o_cl(j + 1, ny) * nx + i;
-                o_prim qm = o_make_prim(Jk[im], Hyk[im], Hxk[im]);
-                o_prim q0 = o_make_prim(Jk[i0], Hyk[i0], Hxk[i0]);
-                o_prim q1 = o_make_prim(Jk[i1], Hyk[i1], Hxk[i1]);
-                o_prim q2 = o_make_prim(Jk[i2], Hyk[i2], Hxk[i2]);
+                o_prim q[4];
+                for (int m = 0; m < 4; ++m) {
+                    int jj = j - 2 + m;
+                    size_t id = (size_t)o_cl(jj, ny) * nx + i;
+                    q[m] = o_vac(jj, ny, p->bc[2], p->bc[3]) ? o_make_prim(0.0, 0.0, 0.0)
+                                                              : o_make_prim(Jk[id], Hyk[id], Hxk[id]);
+                }
+                size_t i0 = (size_t)o_cl(j - 1, ny) * nx + i, i1 = (size_t)o_cl(j, ny) * nx + i;
                 size_t f = (size_t)j * nx + i;
-                o_face(qm, q0, q1, q2, AF(i0), AF(i1), p->uy[i0], p->uy[i1], half_dx, half_dx,
+                o_face(q[0], q[1], q[2], q[3], AF(i0), AF(i1), p->uy[i0], p->uy[i1], half_dx, half_dx,
                        &FJy[f], &FHyy[f], &FHxy[f]);
             }
         /* A3 explicit update, A4 implicit source, A5 force accumulation */
@@ -940,7 +979,13 @@ int lym1o_substep(const lym1o_ctx *c, double dt, const double *J, const double *
 #pragma omp for schedule(static)
             for (long long idl = 0; idl < (long long)nc; ++idl) {
                 size_t id = (size_t)idl;
-                if (!(c->alpha[id] > 0.0)) continue;
+                if (!(c->alpha[id] > 0.0)) {
+                    for (int k = 0; k < nb; ++k) {
+                        size_t kid = (size_t)k * nc + id;
+                        o_causal(Jo[kid], &Hxo[kid], &Hyo[kid]);
+                    }
+                    continue;
+                }
                 for (int k = 0; k < nb; ++k) {
                     size_t kid = (size_t)k * nc + id;
                     o_prim q = o_make_prim(Jo[kid], Hxo[kid], Hyo[kid]);
@@ -963,6 +1008,7 @@ int lym1o_substep(const lym1o_ctx *c, double dt, const double *J, const double *
                     Jo[kid] = Jn[k];
                     Hxo[kid] = ratio * Hxo[kid];
                     Hyo[kid] = ratio * Hyo[kid];
+                    o_causal(Jo[kid], &Hxo[kid], &Hyo[kid]);
                 }
             }
             free(scr); free(Jin); free(Jn); free(DdU);
@@ -1055,7 +1101,8 @@ int lym1o_substep_cyl(const lym1o_ctx *c, double dt, const double *J, const doub
                 for (int m = 0; m < 4; ++m) {
                     size_t id = (size_t)j * nx + ii[m];
                     double sg = fl[m] ? -1.0 : 1.0;
-                    q[m] = o_make_prim(Jk[id], Hxk[id] * sg, Hyk[id]);
+                    q[m] = o_vac(i - 2 + m, nx, 0, p->bc[1]) ? o_make_prim(0.0, 0.0, 0.0)
+                                                             : o_make_prim(Jk[id], Hxk[id] * sg, Hyk[id]);
                     if (m == 1 || m == 2) ur[m - 1] = p->ux[id] * sg;
                 }
                 size_t i0 = (size_t)j * nx + ii[1], i1 = (size_t)j * nx + ii[2];
@@ -1075,7 +1122,8 @@ int lym1o_substep_cyl(const lym1o_ctx *c, double dt, const double *J, const doub
                 for (int m = 0; m < 4; ++m) {
                     size_t id = (size_t)jj[m] * nx + i;
                     double sg = fl[m] ? -1.0 : 1.0;
-                    q[m] = o_make_prim(Jk[id], Hyk[id] * sg, Hxk[id]);
+                    q[m] = o_vac(j - 2 + m, ny, 0, p->bc[3]) ? o_make_prim(0.0, 0.0, 0.0)
+                                                             : o_make_prim(Jk[id], Hyk[id] * sg, Hxk[id]);
                     if (m == 1 || m == 2) uz[m - 1] = p->uy[id] * sg;
                 }
                 size_t i0 = (size_t)jj[1] * nx + i, i1 = (size_t)jj[2] * nx + i;
@@ -1161,7 +1209,13 @@ int lym1o_substep_cyl(const lym1o_ctx *c, double dt, const double *J, const doub
 #pragma omp for schedule(static)
             for (long long idl = 0; idl < (long long)nc; ++idl) {
                 size_t id = (size_t)idl;
-                if (!(c->alpha[id] > 0.0)) continue;
+                if (!(c->alpha[id] > 0.0)) {
+                    for (int k = 0; k < nb; ++k) {
+                        size_t kid = (size_t)k * nc + id;
+                        o_causal(Jo[kid], &Hxo[kid], &Hyo[kid]);
+                    }
+                    continue;
+                }
                 for (int k = 0; k < nb; ++k) {
                     size_t kid = (size_t)k * nc + id;
                     o_prim q = o_make_prim(Jo[kid], Hxo[kid], Hyo[kid]);
@@ -1188,6 +1242,7 @@ int lym1o_substep_cyl(const lym1o_ctx *c, double dt, const double *J, const doub
                     Jo[kid] = Jn[k];
                     Hxo[kid] = ratio * Hxo[kid];
                     Hyo[kid] = ratio * Hyo[kid];
+                    o_causal(Jo[kid], &Hxo[kid], &Hyo[kid]);
                 }
             }
             free(scr); free(Jin); free(Jn); free(DdU);

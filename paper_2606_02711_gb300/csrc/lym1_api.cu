@@ -17,6 +17,7 @@ using namespace lym1;
 
 struct lym1_ctx {
   int nx = 0, ny = 0, nb = 0, precision = 0, gray = 0, freq_step = 0, recoil = 0, geometry = 0;
+  int vac = 0;  // outflow sides into vacuum, bit 0 x-, 1 x+, 2 y-, 3 y+
   long long nc = 0;
   double dx = 0, T = 0, c_tilde = 0, cfl = 0, kabs = 0, kF = 0, dt_cfl = 0, umax = 0;
   double L_tot = 0, device_bytes = 0, gem_max = 1;
@@ -164,6 +165,7 @@ DeviceView make_view(const lym1_ctx* c, double dt) {
   v.f_nbc = c->f_nbc;
   v.f_half = c->f_half;
   v.geometry = c->geometry;
+  v.vac = c->vac;
   v.gphi = c->gphi;
   v.g_AR = c->g_AR;
   v.g_AZ = c->g_AZ;
@@ -408,7 +410,7 @@ int lym1_create(const lym1_grid* grid, const lym1_groups* groups, const lym1_opa
   if (grid->nx < 1 || grid->ny < 1 || !(grid->dx_cm > 0.0)) return LYM1_EINVAL;
   if (grid->geometry != 0 && grid->geometry != 1) return LYM1_EINVAL;
   for (int i = 0; i < 4; ++i)
-    if (grid->bc[i] != 0) return LYM1_EINVAL;
+    if (grid->bc[i] != 0 && grid->bc[i] != 1) return LYM1_EINVAL;
   if (!(op->temp_K > 0.0) || op->precision < 0 || op->precision > 3) return LYM1_EINVAL;
   if (!op->n_hi || !op->rho_dust || !op->p_d || !op->ux || !op->uy) return LYM1_EINVAL;
   if (op->c_tilde < 0.0 || op->cfl < 0.0 || op->kappa_abs < 0.0 || op->kappa_F < 0.0) return LYM1_EINVAL;
@@ -453,6 +455,8 @@ int lym1_create(const lym1_grid* grid, const lym1_groups* groups, const lym1_opa
   c->stream = static_cast<cudaStream_t>(op->cuda_stream);
   c->selem = (c->precision >= LYM1_MIXED) ? 4 : 8;
   c->geometry = grid->geometry;
+  for (int i = 0; i < 4; ++i)
+    if (grid->bc[i] == 1 && !(c->geometry == 1 && (i == 0 || i == 2))) c->vac |= 1 << i;
   build_tables(edges, c->T, c->dx, c->gray, c->recoil, &c->tab, c->geometry);
   c->nb = c->tab.nb;
   c->gem_max = 0.0;

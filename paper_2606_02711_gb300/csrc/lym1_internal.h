@@ -124,6 +124,9 @@ struct DeviceView {
   // axisymmetric (R, Z) grid (geometry 1): per-cell <u_R / R> and the
   // per-column tables of CylTables (nullptr for geometry 0)
   int geometry = 0;
+  // outflow sides into vacuum (bit 0 x-, 1 x+, 2 y-, 3 y+): ghost cells there
+  // carry no radiation; the other outflow sides copy the edge cell
+  int vac = 0;
   const double* gphi = nullptr;
   const double* g_AR = nullptr;
   const double* g_AZ = nullptr;

@@ -158,6 +158,38 @@ __device__ __forceinline__ void closure(F fn, F ft, F& Dnn, F& Dnt, F& Dtt) {
   closure(fn, ft, Dnn, Dnt, Dtt, Dpp);
 }
 
+// Causality after the frequency step (Sec. 2.1 step 3: |H|/J <= 1 with H
+// rescaled by J_new/J_old): an H longer than J is shortened to J along its
+// direction; H = 0 where J <= 0.
+template <class I>
+__device__ __forceinline__ void causal(I J, I& Hx, I& Hy) {
+  if constexpr (sizeof(I) == 8) {
+    const I hn = sqrt(Hx * Hx + Hy * Hy);
+    if (hn > J) {
+      if (J > I(0)) {
+        const I s = J / hn;
+        Hx = Hx * s;
+        Hy = Hy * s;
+      } else {
+        Hx = I(0);
+        Hy = I(0);
+      }
+    }
+  } else {
+    const float h2 = Hx * Hx + Hy * Hy;
+    if (h2 > J * J) {
+      if (J > 0.0f) {
+        const float s = J * rsqrtf(h2);
+        Hx *= s;
+        Hy *= s;
+      } else {
+        Hx = 0.0f;
+        Hy = 0.0f;
+      }
+    }
+  }
+}
+
 // Running sum: plain in FP64, Neumaier-compensated in FP32.
 template <class T>
 struct RSum {
@@ -256,6 +288,14 @@ __device__ __forceinline__ int ghost(int i, int n, bool& flip) {
   }
   flip = false;
   return clampi(i, n);
+}
+
+// Ghost cell (x, y) outside an outflow side into vacuum (DeviceView::vac):
+// its radiation state is zero.  The low sides of geometry 1 are mirrors.
+template <int G>
+__device__ __forceinline__ bool vac_ghost(int x, int y, int nx, int ny, int vac) {
+  return (G == 0 && x < 0 && (vac & 1)) || (x >= nx && (vac & 2)) ||
+         (G == 0 && y < 0 && (vac & 4)) || (y >= ny && (vac & 8));
 }
 
 // block-wide fixed-order reductions (warp shuffles, then warps in order)
@@ -370,11 +410,15 @@ __device__ __forceinline__ void transport_tile(const DeviceView& v, int x0, int 
     for (int idx = tid; idx < SX * SY; idx += NT) {
       const int lx = idx % SX, ly = idx / SX;
       bool fxg, fyg;
-      const int ix = ghost<G>(x0 + lx - 2, nx, fxg), iy = ghost<G>(y0 + ly - 2, ny, fyg);
+      const int xx = x0 + lx - 2, yy = y0 + ly - 2;
+      const int ix = ghost<G>(xx, nx, fxg), iy = ghost<G>(yy, ny, fyg);
       const long long c = base + static_cast<long long>(iy) * nx + ix;
-      const F J = F(Jin[c]);
-      const F Hx = fxg ? -F(Hxin[c]) : F(Hxin[c]);
-      const F Hy = fyg ? -F(Hyin[c]) : F(Hyin[c]);
+      const bool vz = vac_ghost<G>(xx, yy, nx, ny, v.vac);
+      const F J = vz ? F(0) : F(Jin[c]);
+      F Hx = vz ? F(0) : F(Hxin[c]);
+      F Hy = vz ? F(0) : F(Hyin[c]);
+      if (fxg) Hx = -Hx;
+      if (fyg) Hy = -Hy;
       sJ[ly][lx] = J;
       sHx[ly][lx] = Hx;
       sHy[ly][lx] = Hy;
@@ -675,6 +719,9 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
                               : 0;
   const float sx0 = fx0 ? -1.0f : 1.0f, sy0 = fy0 ? -1.0f : 1.0f;
   const float sx1 = fx1 ? -1.0f : 1.0f, sy1 = fy1 ? -1.0f : 1.0f;
+  // ghosts beyond an outflow side into vacuum hold no radiation
+  const bool vz0 = vac_ghost<G>(x0 + ex0 - 2, y0 + ey0 - 2, nx, ny, v.vac);
+  const bool vz1 = has1 && vac_ghost<G>(x0 + ex1 - 2, y0 + ey1 - 2, nx, ny, v.vac);
   // extra faces: warp 0 -> top row of y-faces, warp 1 (lanes < TY) -> right column of x-faces
   const bool xtra_y = ty == 0, xtra_x = ty == 1 && tx < TY;
 
@@ -727,20 +774,22 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
   for (int k = 0; k < nb; ++k) {
     const int b = k & 1;
     {  // halo entries of bin k: registers -> shared, with primitives
-      float X0 = pX0, Y0 = pY0, X1 = pX1, Y1 = pY1;
+      float J0 = pJ0, X0 = pX0, Y0 = pY0, J1 = pJ1, X1 = pX1, Y1 = pY1;
+      if (vz0) J0 = X0 = Y0 = 0.0f;
+      if (vz1) J1 = X1 = Y1 = 0.0f;
       if constexpr (G == 1) {
         X0 *= sx0;
         Y0 *= sy0;
         X1 *= sx1;
         Y1 *= sy1;
       }
-      const float r0 = pJ0 > kTinyJ ? frcp(pJ0) : 0.0f;
-      sq[b][ey0][ex0] = make_float4(pJ0, X0 * r0, Y0 * r0, 0.0f);
+      const float r0 = J0 > kTinyJ ? frcp(J0) : 0.0f;
+      sq[b][ey0][ex0] = make_float4(J0, X0 * r0, Y0 * r0, 0.0f);
       sHx[b][ey0][ex0] = X0;
       sHy[b][ey0][ex0] = Y0;
       if (has1) {
-        const float r1 = pJ1 > kTinyJ ? frcp(pJ1) : 0.0f;
-        sq[b][ey1][ex1] = make_float4(pJ1, X1 * r1, Y1 * r1, 0.0f);
+        const float r1 = J1 > kTinyJ ? frcp(J1) : 0.0f;
+        sq[b][ey1][ex1] = make_float4(J1, X1 * r1, Y1 * r1, 0.0f);
         sHx[b][ey1][ex1] = X1;
         sHy[b][ey1][ex1] = Y1;
       }
@@ -1110,8 +1159,9 @@ __device__ __forceinline__ void freq_block(const DeviceView& v, int blk) {
           ratio = (Jo > kTinyJ) ? fdiv(Jn, Jo) : 0.0f;
         else
           ratio = (Jo > I(0)) ? Jn / Jo : I(0);
-        const I Hx2 = ratio * I(XS);
-        const I Hy2 = ratio * I(YS);
+        I Hx2 = ratio * I(XS);
+        I Hy2 = ratio * I(YS);
+        causal(Jn, Hx2, Hy2);
         Jout[oc] = S(Jn);
         Hxout[oc] = S(Hx2);
         Hyout[oc] = S(Hy2);
@@ -1125,11 +1175,13 @@ __device__ __forceinline__ void freq_block(const DeviceView& v, int blk) {
     } else {
       for (int k = 0; k < nb; ++k) {
         const long long o = static_cast<long long>(k) * nc + cell;
-        const S J = Jin[o], Hx = Hxin[o], Hy = Hyin[o];
+        const S J = Jin[o];
+        const I Ji = I(J);
+        I Hxi = I(Hxin[o]), Hyi = I(Hyin[o]);
+        causal(Ji, Hxi, Hyi);
         Jout[o] = J;
-        Hxout[o] = Hx;
-        Hyout[o] = Hy;
-        const I Ji = I(J), Hxi = I(Hx), Hyi = I(Hy);
+        Hxout[o] = S(Hxi);
+        Hyout[o] = S(Hyi);
         en.add(tdi[k] * Ji);
         if ((G == 1 ? Ji * wI : Ji) > tact[k]) {
           const I hn = sqrt(Hxi * Hxi + Hyi * Hyi);
@@ -1420,7 +1472,8 @@ __device__ __forceinline__ void freq_block_bulk(const DeviceView& v, int blk) {
           ratio = (Jo > kTinyJ) ? fdiv(Jn, Jo) : 0.0f;
         else
           ratio = (I(Jo) > I(0)) ? Jn / I(Jo) : I(0);
-        const I Hx2 = ratio * I(Xo), Hy2 = ratio * I(Yo);
+        I Hx2 = ratio * I(Xo), Hy2 = ratio * I(Yo);
+        causal(Jn, Hx2, Hy2);
         Jout[o] = float(Jn);
         Hxout[o] = float(Hx2);
         Hyout[o] = float(Hy2);
@@ -1431,10 +1484,12 @@ __device__ __forceinline__ void freq_block_bulk(const DeviceView& v, int blk) {
           bad += (hn > Jn * I(1.000001)) ? 1 : 0;
         }
       } else {
+        const I Ji = I(Jo);
+        I Hxi = I(Xo), Hyi = I(Yo);
+        causal(Ji, Hxi, Hyi);
         Jout[o] = Jo;
-        Hxout[o] = Xo;
-        Hyout[o] = Yo;
-        const I Ji = I(Jo), Hxi = I(Xo), Hyi = I(Yo);
+        Hxout[o] = float(Hxi);
+        Hyout[o] = float(Hyi);
         en.add(tdi[k] * Ji);
         if ((G == 1 ? Ji * wI : Ji) > tact[k]) {
           const I hn = sqrt(Hxi * Hxi + Hyi * Hyi);

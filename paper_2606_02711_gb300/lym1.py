@@ -169,11 +169,12 @@ class Context:
     def __init__(self, *, nx, ny, dx, n_hi, rho_d, p_d, ux, uy, T=1e4, kappa_abs=0.0,
                  kappa_F=0.0, c_tilde=0.0, cfl=0.0, recoil=True, freq_step=True, gray=False,
                  edges=None, q=0.0, T_min=0.0, precision=FP64_DET, stream=None, lum=None,
-                 geometry=0):
+                 geometry=0, bc=(0, 0, 0, 0)):
         keep = []
         if isinstance(precision, str):
             precision = PRECISIONS[precision]
-        g = lym1_grid(int(nx), int(ny), float(dx), int(geometry), (C.c_int * 4)(0, 0, 0, 0))
+        g = lym1_grid(int(nx), int(ny), float(dx), int(geometry),
+                      (C.c_int * 4)(*[int(b) for b in bc]))
         if edges is not None:
             e = np.ascontiguousarray(edges, dtype=np.float64)
             keep.append(e)
@@ -366,4 +367,4 @@ def from_cloud(cloud, precision=FP64_DET, stream=None, edges=None) -> Context:
                    kappa_F=cloud.kappa_F, c_tilde=cloud.c_tilde, cfl=cloud.cfl,
                    recoil=cloud.recoil, freq_step=cloud.freq_step, gray=cloud.gray, edges=edges,
                    precision=precision, stream=stream, lum=cloud.lum,
-                   geometry=getattr(cloud, "geometry", 0))
+                   geometry=getattr(cloud, "geometry", 0), bc=getattr(cloud, "bc", (0, 0, 0, 0)))

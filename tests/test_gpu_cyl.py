@@ -159,3 +159,12 @@ def test_cyl_thin_sphere_force_multiplier(L, edges, precision):
     mf = d["force_abs"] / (s.L_total / C)
     assert abs(mf / (tau * eta / 4.0) - 1.0) < 0.02
     assert abs(d["force_radial"] / d["force_abs"] - 1.0) < 2e-3
+
+
+@pytest.mark.parametrize("precision", [0, 3])
+def test_cyl_vacuum_outer_edges(L, edges, precision):
+    c = cyl_cloud(37, 29, seed=33)
+    c.bc = (0, 1, 0, 1)
+    got, ref, _, _ = run_both(L, c, edges, precision, 3, random_state(194, 29, 37, 34))
+    for a, b, n in zip(got, ref, ("J", "Hx", "Hy", "fx", "fy")):
+        close(a, b, TOL[precision], n)

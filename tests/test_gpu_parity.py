@@ -187,3 +187,35 @@ def test_invalid_arguments(L):
     with pytest.raises(L.Lym1Error):
         L.Context(nx=4, ny=4, dx=1.0, n_hi=1.0, rho_d=0, p_d=0, ux=0, uy=0,
                   edges=[0.0, 1.0, 1.0])
+
+
+@pytest.mark.parametrize("precision", [0, 1, 2, 3])
+def test_causality_cap_on_unrealisable_input(L, edges, precision):
+    # states with |H|/J up to 3 (Sec. 2.1 step 3 leaves |H| <= J in every
+    # cell, with or without H I); parity with the oracle at each policy's bar
+    c = wl.lognormal_cloud(37, 21, seed=12, v_edge_kms=50.0)
+    c.n_hi[3:7, 4:12] = 0.0
+    J, Hx, Hy = random_state(194, 21, 37, 23)
+    g = np.random.default_rng(24)
+    boost = np.where(g.uniform(size=J.shape) < 0.3, g.uniform(1.0, 3.0 / 0.95, J.shape), 1.0)
+    st = (J, Hx * boost, Hy * boost)
+    got, ref, dg, _ = run_both(L, c, edges, precision, 1, st)
+    for a, b, n in zip(got, ref, ("J", "Hx", "Hy", "fx", "fy")):
+        close(a, b, TOL[precision], n)
+    Jg, Hxg, Hyg = got[:3]
+    assert np.all(np.hypot(Hxg, Hyg) <= Jg * (1 + (1e-6 if precision >= 2 else 1e-15)))
+
+
+@pytest.mark.parametrize("bc", [(1, 1, 1, 1), (1, 0, 0, 1)])
+@pytest.mark.parametrize("precision", [0, 3])
+def test_vacuum_outflow_sides(L, edges, bc, precision):
+    # outflow into vacuum on some sides (ghosts without radiation), with an
+    # inward-pointing random state at the edges
+    c = wl.lognormal_cloud(41, 19, seed=31, v_edge_kms=40.0)
+    c.bc = bc
+    st = random_state(194, 19, 41, 32)
+    got, ref, dg, diags = run_both(L, c, edges, precision, 2, st)
+    for a, b, n in zip(got, ref, ("J", "Hx", "Hy", "fx", "fy")):
+        close(a, b, TOL[precision], n)
+    out = sum(d["outflow"] for d in diags)
+    assert dg["outflow"] == pytest.approx(out, rel=max(TOL[precision], 1e-10))

@@ -147,3 +147,68 @@ def test_thin_slab_force_multiplier(paper_edges):
     # steady state reached: what is emitted escapes; realisable everywhere
     assert d["outflow"] == pytest.approx(d["emitted"], rel=1e-2)
     assert d["max_f"] <= 1 + 1e-12
+
+
+def test_step3_causality_cap(paper_edges):
+    # Sec. 2.1 step 3: H is rescaled with J_new/J_old and must satisfy
+    # |H| <= J.  One cell with copy ghosts (no transport change), a thin
+    # medium (no damping to speak of), two bins with |H|/J = 3 and one with
+    # |H|/J = 0.5: the first two leave with |H| = J along the same direction,
+    # the last keeps H = (J_new/J_old) H'' exactly.
+    nb = paper_edges.size - 1
+    O = oracle.Oracle(nx=1, ny=1, dx=1e14, edges=paper_edges, T=1e4, n_hi=1e-6, rho_d=0.0,
+                      p_d=0.0, ux=0.0, uy=0.0, lum=0.0)
+    J = np.full((nb, 1, 1), 1e-10)
+    Hx = np.zeros_like(J)
+    Hy = np.zeros_like(J)
+    k1, k2, k3 = nb // 2, nb // 2 + 1, nb // 2 - 3
+    Hx[k1], Hy[k1] = 3e-10 * 0.6, 3e-10 * 0.8
+    Hx[k2], Hy[k2] = -3e-10, 0.0
+    Hx[k3], Hy[k3] = 0.3e-10, 0.4e-10
+    Jo, Hxo, Hyo, _, _, _ = O.substep(J, Hx, Hy)
+    for k, (cx, cy) in ((k1, (0.6, 0.8)), (k2, (-1.0, 0.0))):
+        hn = math.hypot(Hxo[k, 0, 0], Hyo[k, 0, 0])
+        assert hn == pytest.approx(Jo[k, 0, 0], rel=1e-15)
+        assert Hxo[k, 0, 0] / hn == pytest.approx(cx, abs=1e-15)
+        assert Hyo[k, 0, 0] / hn == pytest.approx(cy, abs=1e-15)
+    # the uncapped bin: f after step 3 equals f after the source step
+    # (H'' = H / (1 + ct dt aF) with J unchanged by transport)
+    tab = O.tables()
+    a = 1e-6 * oracle.line_constants(1e4)["sigma0"] * tab["Havg"][k3]
+    damp = 1.0 / (1.0 + 2.99792458e10 * O.dt_cfl * a)
+    f3 = math.hypot(Hxo[k3, 0, 0], Hyo[k3, 0, 0]) / Jo[k3, 0, 0]
+    assert f3 == pytest.approx(0.5 * damp, rel=1e-12)
+    assert np.all(np.hypot(Hxo, Hyo) <= Jo * (1 + 1e-15))
+
+
+def test_vacuum_outflow_never_admits_radiation():
+    # outflow into vacuum (ghosts without radiation): for any realisable
+    # state in a static medium the boundary flux is eps/2 (J_L + H_L,n) +
+    # (1 - eps) J / (3 tau) >= 0 on every face, so no energy enters.  The
+    # zero-gradient kind passes the edge cell's own H_n, which admits
+    # radiation when that flux points inward.
+    nx, ny = 10, 8
+    g = np.random.default_rng(3)
+    J = g.uniform(0.5, 1.5, (1, ny, nx))
+    f = g.uniform(0.0, 1.0, (1, ny, nx))
+    th = g.uniform(0, 2 * np.pi, (1, ny, nx))
+    Hx, Hy = J * f * np.cos(th), J * f * np.sin(th)
+    # edges flowing inward
+    Hx[..., 0], Hx[..., -1] = 0.9 * J[..., 0], -0.9 * J[..., -1]
+    Hy[:, 0, :], Hy[:, -1, :] = 0.9 * J[:, 0, :], -0.9 * J[:, -1, :]
+    for n_hi in (0.0, 1e-3):
+        vac = _gray(nx, ny, 1e16, n_hi, bc=(1, 1, 1, 1))
+        cp = _gray(nx, ny, 1e16, n_hi, bc=(0, 0, 0, 0))
+        dv = vac.substep(J, Hx, Hy)[5]
+        dc = cp.substep(J, Hx, Hy)[5]
+        assert dv["outflow"] > 0
+        assert dc["outflow"] < 0
+        assert abs(dv["residual"]) <= 1e-13 * dv["e_before"]
+    # per face: an outward beam leaves the vacuum edge unchanged in flux
+    Jb = np.ones((1, 2, 6))
+    st = (Jb, Jb.copy(), np.zeros_like(Jb))
+    vac = _gray(6, 2, 1e16, 0.0, bc=(1, 1, 0, 0))
+    d = vac.substep(*st)[5]
+    # x+ face: flux J (f = 1, eps = 1); x- face: (H_R - J_R)/2 = 0
+    assert d["outflow"] == pytest.approx(2 * vac.dt_cfl * C / 1e16 * 1.0 * (4 * math.pi / C)
+                                         * (1e16) ** 3, rel=1e-12)

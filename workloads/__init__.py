@@ -106,6 +106,7 @@ class Cloud:
     cfl: float = 0.4
     substeps: int = 1
     geometry: int = 0        # 0: 2D Cartesian slab; 1: axisymmetric (R = x, Z = y)
+    bc: tuple = (0, 0, 0, 0)  # x-, x+, y-, y+: 0 = zero-gradient outflow, 1 = vacuum outflow
     meta: dict = field(default_factory=dict)
 
     @property
@@ -118,7 +119,7 @@ class Cloud:
                     rho_d=self.rho_d, p_d=self.p_d, ux=self.ux, uy=self.uy, lum=self.lum,
                     kappa_abs=self.kappa_abs, kappa_F=self.kappa_F, c_tilde=self.c_tilde,
                     cfl=self.cfl, gray=self.gray, recoil=self.recoil,
-                    freq_step=self.freq_step, geometry=self.geometry)
+                    freq_step=self.freq_step, geometry=self.geometry, bc=self.bc)
 
 
 def uniform_gray(nx=64, ny=64, box_pc=2.0, n_h=1e3, L_sun=1e6, name="uniform-gray"):
@@ -201,7 +202,7 @@ def uniform_sphere(n=64, tau_cl=0.1, T=1.0e4, R_cl_pc=1.0, L_sun=1e6, gray=False
     the midplane mirrored (Sec. 4.1, Test 1): line-centre optical depth
     tau_cl = n_HI sigma0 R_cl inside r <= R_cl, vacuum outside, box 1.1 R_cl,
     emission uniform per unit volume inside the sphere (the upper half emits
-    L/2 of a total L), c_tilde = c."""
+    L/2 of a total L), c_tilde = c; vacuum outflow at the outer R and Z edges."""
     R_cl = R_cl_pc * PC
     dx, R, Z, vol = _rz_grid(n, R_cl)
     inside = np.sqrt(R * R + Z * Z) <= R_cl
@@ -212,7 +213,7 @@ def uniform_sphere(n=64, tau_cl=0.1, T=1.0e4, R_cl_pc=1.0, L_sun=1e6, gray=False
     lum = lum * (0.5 * L_sun * L_SUN / lum.sum())
     return Cloud(name, n, n, dx, n_hi, z.copy(), z.copy(), z.copy(), z.copy(), lum, T=T, gray=gray,
                  recoil=recoil, freq_step=freq_step, kappa_abs=0.0, kappa_F=0.0, geometry=1,
-                 meta={"tau_cl": tau_cl, "R_cl": R_cl})
+                 bc=(0, 1, 0, 1), meta={"tau_cl": tau_cl, "R_cl": R_cl})
 
 
 def cone_cloud(n=256, tau_cl=1e8, tau_cone=1e5, T=1.0e4, R_cl_pc=1.0, L_sun=1e6,
@@ -224,7 +225,7 @@ def cone_cloud(n=256, tau_cl=1e8, tau_cone=1e5, T=1.0e4, R_cl_pc=1.0, L_sun=1e6,
     shell 0.5 R_cl < r <= R_cl and eps_core inside 0.5 R_cl (the emission
     region, emitting uniformly per unit volume); vacuum outside R_cl; recoil
     on; no dust or destruction; static gas; 256^2 cells over 1.1 R_cl;
-    n_cl, n_cone from tau = n sigma0 R_cl."""
+    n_cl, n_cone from tau = n sigma0 R_cl; vacuum outflow at the outer edges."""
     R_cl = R_cl_pc * PC
     dx, R, Z, vol = _rz_grid(n, R_cl)
     r = np.sqrt(R * R + Z * Z)
@@ -240,4 +241,4 @@ def cone_cloud(n=256, tau_cl=1e8, tau_cone=1e5, T=1.0e4, R_cl_pc=1.0, L_sun=1e6,
     t_max = 4.0 * max((4.7e-4 * math.sqrt(1e4 / T) * tau_cl) ** (1.0 / 3.0), 3.0) * R_cl / C_LIGHT
     return Cloud(name, n, n, dx, n_hi, z.copy(), z.copy(), z.copy(), z.copy(), lum, T=T,
                  recoil=True, freq_step=True, kappa_abs=0.0, kappa_F=0.0, geometry=1,
-                 meta={"tau_cl": tau_cl, "tau_cone": tau_cone, "R_cl": R_cl, "t_max": t_max})
+                 bc=(0, 1, 0, 1), meta={"tau_cl": tau_cl, "tau_cone": tau_cone, "R_cl": R_cl, "t_max": t_max})
