@@ -155,6 +155,7 @@ DeviceView make_view(const lym1_ctx* c, double dt) {
   // Sec. 2.3: f = 4 pi / (c ct dt) sum_k dnu_k (H' - H'')
   v.fcoef = (4.0 * kPi) / ((kLight * c->c_tilde) * dt);
   v.freq_step = c->freq_step;
+  v.tdiag = (!c->gray && c->freq_step) ? 0 : 1;
   v.gem_max = c->gem_max;
   v.acc = c->acc;
   v.status = c->status;

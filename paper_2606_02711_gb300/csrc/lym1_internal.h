@@ -121,6 +121,9 @@ struct DeviceView {
   const float* f_nbc = nullptr;
   const float* f_half = nullptr;
   int freq_step = 0;
+  // 1: the transport kernel produces the energy and realisability partials
+  // (no frequency step follows it in this substep)
+  int tdiag = 1;
   // axisymmetric (R, Z) grid (geometry 1): per-cell <u_R / R> and the
   // per-column tables of CylTables (nullptr for geometry 0)
   int geometry = 0;

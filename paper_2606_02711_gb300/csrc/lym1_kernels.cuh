@@ -161,31 +161,38 @@ __device__ __forceinline__ void closure(F fn, F ft, F& Dnn, F& Dnt, F& Dtt) {
 // Causality after the frequency step (Sec. 2.1 step 3: |H|/J <= 1 with H
 // rescaled by J_new/J_old): an H longer than J is shortened to J along its
 // direction; H = 0 where J <= 0.
+// FP64: the square root is taken only when |H|^2 > J^2, which leaves the
+// decision |H| > J unchanged (sqrt(fl(J J)) = J for a correctly rounded
+// product and square root in binary arithmetic without under/overflow) and
+// keeps the result bit-identical to the plain form.
 template <class I>
 __device__ __forceinline__ void causal(I J, I& Hx, I& Hy) {
   if constexpr (sizeof(I) == 8) {
-    const I hn = sqrt(Hx * Hx + Hy * Hy);
-    if (hn > J) {
-      if (J > I(0)) {
-        const I s = J / hn;
-        Hx = Hx * s;
-        Hy = Hy * s;
-      } else {
-        Hx = I(0);
-        Hy = I(0);
+    if (J > I(0)) {
+      const I h2 = Hx * Hx + Hy * Hy;
+      if (h2 > J * J) {
+        const I hn = sqrt(h2);
+        if (hn > J) {
+          const I s = J / hn;
+          Hx = Hx * s;
+          Hy = Hy * s;
+        }
       }
+    } else {
+      Hx = I(0);
+      Hy = I(0);
     }
   } else {
-    const float h2 = Hx * Hx + Hy * Hy;
-    if (h2 > J * J) {
-      if (J > 0.0f) {
+    if (J > 0.0f) {
+      const float h2 = Hx * Hx + Hy * Hy;
+      if (h2 > J * J) {
         const float s = J * rsqrtf(h2);
         Hx *= s;
         Hy *= s;
-      } else {
-        Hx = 0.0f;
-        Hy = 0.0f;
       }
+    } else {
+      Hx = 0.0f;
+      Hy = 0.0f;
     }
   }
 }
@@ -508,10 +515,12 @@ __device__ __forceinline__ void transport_tile(const DeviceView& v, int x0, int 
       if (lum_d != 0.0) em.add(dnu * (cdt * js));
       ab.add(dnu * (cdt * (kap * J2)));
       wk.add(dnu * (cdt * (I(W) / I(kLight))));
-      en.add(dnu * J2);
-      const I hn = sqrt(Hx2 * Hx2 + Hy2 * Hy2);
-      if (J2 > I(0)) mxf = fmax(mxf, hn / J2);
-      if (hn > J2 * I(1.000001) && hn > I(0)) bad += 1.0;
+      if (v.tdiag) {  // the frequency step recomputes these when it follows
+        en.add(dnu * J2);
+        const I hn = sqrt(Hx2 * Hx2 + Hy2 * Hy2);
+        if (J2 > I(0)) mxf = fmax(mxf, hn / J2);
+        if (hn > J2 * I(1.000001) && hn > I(0)) bad += 1.0;
+      }
       const I cdx = cdt / I(v.dx);
       if constexpr (G == 1) {  // outflow through the outer R and Z faces only
         if (gx == nx - 1) out.add(dnu * (cdx * (I(v.g_wR) * I(xJ[ty][tx + 1]))));
@@ -539,12 +548,14 @@ __device__ __forceinline__ void transport_tile(const DeviceView& v, int x0, int 
   if (tid == 0) part[kSlotOutflow] = s;
   s = block_sum<NT>(wk.value() * wcell, red);
   if (tid == 0) part[kSlotWork] = s;
-  s = block_sum<NT>(en.value() * wcell, red);
-  if (tid == 0) part[kSlotEnergy] = s;
-  s = block_max<NT>(double(mxf), red);
-  if (tid == 0) part[kSlotMaxF] = s;
-  s = block_sum<NT>(bad, red);
-  if (tid == 0) part[kSlotBad] = s;
+  if (v.tdiag) {
+    s = block_sum<NT>(en.value() * wcell, red);
+    if (tid == 0) part[kSlotEnergy] = s;
+    s = block_max<NT>(double(mxf), red);
+    if (tid == 0) part[kSlotMaxF] = s;
+    s = block_sum<NT>(bad, red);
+    if (tid == 0) part[kSlotBad] = s;
+  }
 }
 
 
@@ -568,20 +579,27 @@ constexpr float kTinyJ = 1e-30f;
 // kActiveShare E / unit for the next one)
 constexpr double kActiveShare = 1e-8;
 
-// Levermore closure in the cancellation-free FP32 form (see closure());
-// Dpp = (1 - chi)/2.
-__device__ __forceinline__ void closure_f32(float fn, float ft, float& Dnn, float& Dnt, float& Dtt,
-                                            float& Dpp) {
-  const float f2 = fn * fn + ft * ft;
+// Levermore closure for FP32 from f = (fn, ft) and f2 = |f|^2.  With
+// s = sqrt(4 - 3 f2) (so f2 = (4 - s^2)/3) the printed chi reduces exactly to
+// chi = (5 - 2s)/3, hence
+//   (1 - chi)/2 = (s - 1)/3   and   (3 chi - 1)/(2 f2) = (2 - s)/f2 = 3/(2 + s),
+// both free of cancellation at small f (where the printed 3 chi - 1 ~ 1.5 f2
+// loses every digit in FP32).  Dpp = (1 - chi)/2.
+__device__ __forceinline__ void closure_f32q(float fn, float ft, float f2, float& Dnn, float& Dnt,
+                                             float& Dtt, float& Dpp) {
   const float y = 4.0f - 3.0f * f2;
   const float s = y * rsqrtf(y);
-  const float inv = frcp(5.0f + 2.0f * s);
-  const float dA = (1.0f + s - 2.0f * f2) * inv;
-  const float g = (6.0f + fdiv(3.0f, 2.0f + s)) * inv;
+  const float dA = (s - 1.0f) * (1.0f / 3.0f);
+  const float g = 3.0f * frcp(2.0f + s);
   Dnn = dA + g * (fn * fn);
   Dnt = g * (fn * ft);
   Dtt = dA + g * (ft * ft);
   Dpp = dA;
+}
+
+__device__ __forceinline__ void closure_f32(float fn, float ft, float& Dnn, float& Dnt, float& Dtt,
+                                            float& Dpp) {
+  closure_f32q(fn, ft, fn * fn + ft * ft, Dnn, Dnt, Dtt, Dpp);
 }
 
 __device__ __forceinline__ void closure_f32(float fn, float ft, float& Dnn, float& Dnt, float& Dtt) {
@@ -589,47 +607,46 @@ __device__ __forceinline__ void closure_f32(float fn, float ft, float& Dnn, floa
   closure_f32(fn, ft, Dnn, Dnt, Dtt, Dpp);
 }
 
-__device__ __forceinline__ void cap_unit_f32(float& fn, float& ft) {
+// |f| > 1: scale to the unit circle (without a branch: the factor is
+// rsqrt(max(|f|^2, 1)), 1 for |f| <= 1); returns |f|^2 after the scaling
+__device__ __forceinline__ float cap_unit_f32(float& fn, float& ft) {
   const float f2 = fn * fn + ft * ft;
-  if (f2 > 1.0f) {
-    const float r = rsqrtf(f2);
-    fn *= r;
-    ft *= r;
-  }
+  const float r = rsqrtf(fmaxf(f2, 1.0f));
+  fn *= r;
+  ft *= r;
+  return fminf(f2, 1.0f);
 }
 
-// MinMod without branches: the smaller magnitude with the common sign, zero
-// when the signs differ (sign bits compared, so tiny slopes are kept).
+// MinMod as the median of (a, b, 0): the smaller magnitude when a and b share
+// a sign, zero otherwise (pure selection, so tiny slopes are kept).
 __device__ __forceinline__ float minmod_f32(float a, float b) {
-  const float m = copysignf(fminf(fabsf(a), fabsf(b)), a);
-  return ((__float_as_uint(a) ^ __float_as_uint(b)) & 0x80000000u) ? 0.0f : m;
+  return fmaxf(fminf(a, b), fminf(fmaxf(a, b), 0.0f));
 }
 
 // Face flux (same scheme as face_flux) from packed primitives q = (J, f_n, f_t)
-// of cells -1, 0, +1, +2, with w = u/c per cell; the interpolation factor and
-// the diffusion coefficient share one reciprocal (tau: the face optical depth):
+// of cells -1, 0, +1, +2, the face optical depth tau and the face velocity
+// wf = (u_0 + u_1) / (2c); the interpolation factor and the diffusion
+// coefficient share one reciprocal:
 //   eps = (0.2 + tau) / d,  (1 - eps) / (3 tau) = tau / (3 d),  d = 0.2 + tau + tau^2.
 __device__ __forceinline__ void face_flux_f32(float Jm, float nm, float tm, float J0, float n0,
                                               float t0, float J1, float n1, float t1, float J2,
-                                              float n2, float t2, float aF0, float aF1, float w0,
-                                              float w1, float tau, float& oJ, float& oN,
-                                              float& oT) {
+                                              float n2, float t2, float tau, float wf, float& oJ,
+                                              float& oN, float& oT) {
   const float d0 = J0 - Jm, d1 = J1 - J0, d2 = J2 - J1;
   const float JL = J0 + 0.5f * minmod_f32(d0, d1), JR = J1 - 0.5f * minmod_f32(d1, d2);
   const float e1 = n1 - n0, g1 = t1 - t0;
   float nL = n0 + 0.5f * minmod_f32(n0 - nm, e1), tL = t0 + 0.5f * minmod_f32(t0 - tm, g1);
   float nR = n1 - 0.5f * minmod_f32(e1, n2 - n1), tR = t1 - 0.5f * minmod_f32(g1, t2 - t1);
-  cap_unit_f32(nL, tL);
-  cap_unit_f32(nR, tR);
+  const float f2L = cap_unit_f32(nL, tL);
+  const float f2R = cap_unit_f32(nR, tR);
   const float HnL = JL * nL, HtL = JL * tL, HnR = JR * nR, HtR = JR * tR;
-  float DnnL, DntL, DttL, DnnR, DntR, DttR;
-  closure_f32(nL, tL, DnnL, DntL, DttL);
-  closure_f32(nR, tR, DnnR, DntR, DttR);
+  float DnnL, DntL, DttL, DppL, DnnR, DntR, DttR, DppR;
+  closure_f32q(nL, tL, f2L, DnnL, DntL, DttL, DppL);
+  closure_f32q(nR, tR, f2R, DnnR, DntR, DttR, DppR);
   const float a = 0.2f + tau;
   const float rden = frcp(a + tau * tau);
   const float eps = a * rden;
   const float dcoef = tau * rden * (1.0f / 3.0f);
-  const float wf = 0.5f * (w0 + w1);
   const bool up = wf > 0.0f;  // upwind donor: reconstructed state on the upwind side
   const float Jd = up ? JL : JR, Hnd = up ? HnL : HnR, Htd = up ? HtL : HtR;
   oJ = 0.5f * eps * ((HnL + HnR) - (JR - JL)) - dcoef * d1 + wf * Jd;
@@ -639,26 +656,27 @@ __device__ __forceinline__ void face_flux_f32(float Jm, float nm, float tm, floa
 
 // ------------------------------------------------ FP32 transport kernel
 // Same rows A1-A5 as transport_kernel for FP32 state and fluxes.  The halo
-// tile is double-buffered and packed as float4 (J, f_x, f_y, -) per cell; each
-// thread prefetches its (at most two) halo entries of bin k+1 into registers
-// while bin k is computed, so one bin needs two block barriers.  Faces are
-// mapped to threads without division: every thread computes the left x-face
-// and the bottom y-face of its cell, warp 0 the top row of y-faces and part
-// of warp 1 the right column of x-faces.  The implicit source step runs in
-// type I (FP64 for LYM1_MIXED, FP32 for LYM1_MIXED_FAST).
+// tile is double-buffered and packed as float4 (J, f_x, f_y, alpha_F,k) per
+// cell; each thread owns at most two halo entries, keeps their opacities in
+// registers and prefetches their state of bin k+1 while bin k is computed, so
+// one bin needs two block barriers.  Faces are mapped to threads without
+// division: every thread computes the left x-face and the bottom y-face of
+// its cell, warp 0 the top row of y-faces and part of warp 1 the right column
+// of x-faces; the face velocities (and on the axisymmetric grid the centroid
+// distances) of a thread's faces do not depend on the bin and stay in
+// registers.  The implicit source step runs in type I (FP64 for LYM1_MIXED,
+// FP32 for LYM1_MIXED_FAST).
 template <class P, int G>
 __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, int y0, int blk) {
   using I = typename P::I;
-  constexpr int TX = kTileX, TY = kTileY, SX = TX + 4, SY = TY + 4, QX = TX + 2, QY = TY + 2;
+  constexpr int TX = kTileX, TY = kTileY, SX = TX + 4, SY = TY + 4;
   constexpr int NT = TX * TY;
   static_assert(SX * SY <= 2 * NT, "two halo entries per thread at most");
   static_assert(TY <= 32, "right-column faces are computed by one warp");
-  __shared__ float4 sq[2][SY][SX];  // (J, f_x, f_y, unused)
+  __shared__ float4 sq[2][SY][SX];  // (J, f_x, f_y, alpha_F of the bin)
   __shared__ float sHx[2][SY][SX], sHy[2][SY][SX];
-  __shared__ float4 qc[QY][QX];  // (alpha, rho_d, u_x/c, u_y/c)
   __shared__ float xJ[TY][TX + 1], xN[TY][TX + 1], xT[TY][TX + 1];
   __shared__ float yJ[TY + 1][TX], yN[TY + 1][TX], yT[TY + 1][TX];
-  __shared__ float sdl[2][G == 1 ? TX + 1 : 1];  // axisymmetric: centroid distances per R face
   __shared__ double red[NT / 32];
   extern __shared__ float tabf[];  // <H>_k, dnu_k, gem_k / gem_max, J_act,k as FP32 (4 nb)
   float* tH = tabf;
@@ -680,6 +698,7 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
   const bool valid = gx < nx && gy < ny;
   const long long cell = valid ? static_cast<long long>(gy) * nx + gx : 0;
   const float inv_c = 1.0f / float(kLight);
+  const bool tdiag = v.tdiag != 0;
 
   // realisability is checked on (cell, bin) pairs holding at least kActiveShare
   // of the domain energy of the previous substep (FP32 rounding makes |H|/J
@@ -692,22 +711,8 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
     tG[i] = v.f_G[i];
     tA[i] = fmaxf(thr, 1e-30f) / v.f_dnu[i];
   }
-  for (int idx = tid; idx < QX * QY; idx += NT) {
-    const int lx = idx % QX, ly = idx / QX;
-    bool fxg, fyg;
-    const int ix = ghost<G>(x0 + lx - 1, nx, fxg), iy = ghost<G>(y0 + ly - 1, ny, fyg);
-    const long long c = static_cast<long long>(iy) * nx + ix;
-    const float wx = float(v.ux[c]) * inv_c, wy = float(v.uy[c]) * inv_c;
-    qc[ly][lx] = make_float4(float(v.alpha[c]), float(v.rho[c]), fxg ? -wx : wx, fyg ? -wy : wy);
-  }
-  if constexpr (G == 1) {
-    for (int f = tid; f <= TX; f += NT) {
-      const int gf = x0 + f <= nx ? x0 + f : nx;
-      sdl[0][f] = v.gf_dlL[gf];
-      sdl[1][f] = v.gf_dlR[gf];
-    }
-  }
-  // halo entries owned by this thread (plane offsets; sign of H_x, H_y)
+  // halo entries owned by this thread (plane offsets; sign of H_x, H_y;
+  // opacity alpha and rho_d kappa_F of the ghost-mapped cell)
   const int e0 = tid, e1 = tid + NT;
   const bool has1 = e1 < SX * SY;
   const int ex0 = e0 % SX, ey0 = e0 / SX, ex1 = e1 % SX, ey1 = e1 / SX;
@@ -722,8 +727,39 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
   // ghosts beyond an outflow side into vacuum hold no radiation
   const bool vz0 = vac_ghost<G>(x0 + ex0 - 2, y0 + ey0 - 2, nx, ny, v.vac);
   const bool vz1 = has1 && vac_ghost<G>(x0 + ex1 - 2, y0 + ey1 - 2, nx, ny, v.vac);
-  // extra faces: warp 0 -> top row of y-faces, warp 1 (lanes < TY) -> right column of x-faces
+  const float kF_f = float(v.kF);
+  const float al0 = float(v.alpha[off0]), rk0 = float(v.rho[off0]) * kF_f;
+  const float al1 = has1 ? float(v.alpha[off1]) : 0.0f;
+  const float rk1 = has1 ? float(v.rho[off1]) * kF_f : 0.0f;
+  // this thread's faces: x-face (tx, ty), y-face (tx, ty) and the extra
+  // ones; velocity u/c of each adjacent cell with the mirror flips
+  auto wcell = [&](int x, int y, bool xdir) {
+    bool fxg, fyg;
+    const int ix = ghost<G>(x, nx, fxg), iy = ghost<G>(y, ny, fyg);
+    const long long c = static_cast<long long>(iy) * nx + ix;
+    const float w = float(xdir ? v.ux[c] : v.uy[c]) * inv_c;
+    return (xdir ? fxg : fyg) ? -w : w;
+  };
   const bool xtra_y = ty == 0, xtra_x = ty == 1 && tx < TY;
+  const float wfx = 0.5f * (wcell(gx - 1, gy, true) + wcell(gx, gy, true));
+  const float wfy = 0.5f * (wcell(gx, gy - 1, false) + wcell(gx, gy, false));
+  float wfx2 = 0.0f, wfy2 = 0.0f;
+  if (xtra_y) wfy2 = 0.5f * (wcell(gx, y0 + TY - 1, false) + wcell(gx, y0 + TY, false));
+  if (xtra_x) wfx2 = 0.5f * (wcell(x0 + TX - 1, y0 + tx, true) + wcell(x0 + TX, y0 + tx, true));
+  // face optical depth = aF_0 dl_0 + aF_1 dl_1 (centroid distances, geometry
+  // 1) or (aF_0 + aF_1) dx/2 (geometry 0)
+  const float half_dx = 0.5f * float(v.dx);
+  float dlA0 = half_dx, dlA1 = half_dx, dlB0 = half_dx, dlB1 = half_dx;
+  if constexpr (G == 1) {
+    const int fa = gx <= nx ? gx : nx;
+    dlA0 = v.gf_dlL[fa];
+    dlA1 = v.gf_dlR[fa];
+    if (xtra_x) {
+      const int fb = x0 + TX <= nx ? x0 + TX : nx;
+      dlB0 = v.gf_dlL[fb];
+      dlB1 = v.gf_dlR[fb];
+    }
+  }
 
   I alpha_c = 0, rho_c = 0, pd_c = 0;
   float gxx = 0, gyy = 0, gsh = 0, gphi = 0;
@@ -745,11 +781,11 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
       wvf = v.gf_wv[gx];
     }
   }
-  const float half_dx = 0.5f * float(v.dx), kF_f = float(v.kF), cdt_f = float(v.cdt);
+  const float cdt_f = float(v.cdt);
   const float inv_dx = 1.0f / float(v.dx);
   const float cdt_dx = float(v.cdt / v.dx);
   const I cdt = I(v.cdt), kabs = I(v.kabs), kF = I(v.kF), cdx = I(v.cdt / v.dx);
-  const I wR = I(v.g_wR), wcell = I(wvf);
+  const I wR = I(v.g_wR), wcol = I(wvf);
   I ax = 0, ay = 0;
   // per-cell bookkeeping sums over the bins: FP64 (compensation-free, exact
   // enough at 194 terms) for LYM1_MIXED, plain FP32 for LYM1_MIXED_FAST; the
@@ -771,9 +807,11 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
     pX1 = Hxin[off1];
     pY1 = Hyin[off1];
   }
+  long long base = 0;  // k * nc
   for (int k = 0; k < nb; ++k) {
     const int b = k & 1;
-    {  // halo entries of bin k: registers -> shared, with primitives
+    const float Hk = tH[k];
+    {  // halo entries of bin k: registers -> shared, with primitives and alpha_F
       float J0 = pJ0, X0 = pX0, Y0 = pY0, J1 = pJ1, X1 = pX1, Y1 = pY1;
       if (vz0) J0 = X0 = Y0 = 0.0f;
       if (vz1) J1 = X1 = Y1 = 0.0f;
@@ -784,65 +822,56 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
         Y1 *= sy1;
       }
       const float r0 = J0 > kTinyJ ? frcp(J0) : 0.0f;
-      sq[b][ey0][ex0] = make_float4(J0, X0 * r0, Y0 * r0, 0.0f);
+      sq[b][ey0][ex0] = make_float4(J0, X0 * r0, Y0 * r0, al0 * Hk + rk0);
       sHx[b][ey0][ex0] = X0;
       sHy[b][ey0][ex0] = Y0;
       if (has1) {
         const float r1 = J1 > kTinyJ ? frcp(J1) : 0.0f;
-        sq[b][ey1][ex1] = make_float4(J1, X1 * r1, Y1 * r1, 0.0f);
+        sq[b][ey1][ex1] = make_float4(J1, X1 * r1, Y1 * r1, al1 * Hk + rk1);
         sHx[b][ey1][ex1] = X1;
         sHy[b][ey1][ex1] = Y1;
       }
     }
+    const long long nbase = base + nc;
     if (k + 1 < nb) {  // prefetch bin k+1
-      const long long base = static_cast<long long>(k + 1) * nc;
-      pJ0 = Jin[base + off0];
-      pX0 = Hxin[base + off0];
-      pY0 = Hyin[base + off0];
+      pJ0 = Jin[nbase + off0];
+      pX0 = Hxin[nbase + off0];
+      pY0 = Hyin[nbase + off0];
       if (has1) {
-        pJ1 = Jin[base + off1];
-        pX1 = Hxin[base + off1];
-        pY1 = Hyin[base + off1];
+        pJ1 = Jin[nbase + off1];
+        pX1 = Hxin[nbase + off1];
+        pY1 = Hyin[nbase + off1];
       }
     }
     __syncthreads();
-    const float Hk = tH[k];
-    auto xface = [&](int fi, int fj) {  // between tile cells (fi-1, fj) and (fi, fj)
+    auto xface = [&](int fi, int fj, float wf, float dl0, float dl1) {
+      // between tile cells (fi-1, fj) and (fi, fj)
       const int r = fj + 2;
       const float4 qm = sq[b][r][fi], q0 = sq[b][r][fi + 1], q1 = sq[b][r][fi + 2],
                    q2 = sq[b][r][fi + 3];
-      const float4 c0 = qc[fj + 1][fi], c1 = qc[fj + 1][fi + 1];
-      const float aF0 = c0.x * Hk + c0.y * kF_f, aF1 = c1.x * Hk + c1.y * kF_f;
-      float tau;
-      if constexpr (G == 1)
-        tau = aF0 * sdl[0][fi] + aF1 * sdl[1][fi];
-      else
-        tau = (aF0 + aF1) * half_dx;
-      face_flux_f32(qm.x, qm.y, qm.z, q0.x, q0.y, q0.z, q1.x, q1.y, q1.z, q2.x, q2.y, q2.z,
-                    aF0, aF1, c0.z, c1.z, tau, xJ[fj][fi], xN[fj][fi], xT[fj][fi]);
+      const float tau = (G == 1) ? q0.w * dl0 + q1.w * dl1 : (q0.w + q1.w) * dl0;
+      face_flux_f32(qm.x, qm.y, qm.z, q0.x, q0.y, q0.z, q1.x, q1.y, q1.z, q2.x, q2.y, q2.z, tau,
+                    wf, xJ[fj][fi], xN[fj][fi], xT[fj][fi]);
     };
-    auto yface = [&](int fi, int fj) {  // between tile cells (fi, fj-1) and (fi, fj)
+    auto yface = [&](int fi, int fj, float wf) {  // between tile cells (fi, fj-1) and (fi, fj)
       const int cc = fi + 2;
       const float4 qm = sq[b][fj][cc], q0 = sq[b][fj + 1][cc], q1 = sq[b][fj + 2][cc],
                    q2 = sq[b][fj + 3][cc];
-      const float4 c0 = qc[fj][fi + 1], c1 = qc[fj + 1][fi + 1];
-      const float aF0 = c0.x * Hk + c0.y * kF_f, aF1 = c1.x * Hk + c1.y * kF_f;
       face_flux_f32(qm.x, qm.z, qm.y, q0.x, q0.z, q0.y, q1.x, q1.z, q1.y, q2.x, q2.z, q2.y,
-                    aF0, aF1, c0.w, c1.w, (aF0 + aF1) * half_dx, yJ[fj][fi], yN[fj][fi],
-                    yT[fj][fi]);
+                    (q0.w + q1.w) * half_dx, wf, yJ[fj][fi], yN[fj][fi], yT[fj][fi]);
     };
-    xface(tx, ty);
-    yface(tx, ty);
-    if (xtra_y) yface(tx, TY);
-    if (xtra_x) xface(TX, tx);
+    xface(tx, ty, wfx, dlA0, dlA1);
+    yface(tx, ty, wfy);
+    if (xtra_y) yface(tx, TY, wfy2);
+    if (xtra_x) xface(TX, tx, wfx2, dlB0, dlB1);
     __syncthreads();
     if (valid) {
       const float4 qs = sq[b][ty + 2][tx + 2];
       const float J = qs.x, Hx = sHx[b][ty + 2][tx + 2], Hy = sHy[b][ty + 2][tx + 2];
       float fxc = qs.y, fyc = qs.z;
-      cap_unit_f32(fxc, fyc);
+      const float f2c = cap_unit_f32(fxc, fyc);
       float Dxx, Dxy, Dyy, Dpp;
-      closure_f32(fxc, fyc, Dxx, Dxy, Dyy, Dpp);
+      closure_f32q(fxc, fyc, f2c, Dxx, Dxy, Dyy, Dpp);
       float W, divJ, divHx, divHy;
       if constexpr (G == 1) {
         // per-radian finite volumes in units of dx (r0, r1 = R-face areas x dx /
@@ -888,28 +917,31 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
         Hx2 = Hx1 * ra;
         Hy2 = Hy1 * ra;
       }
-      const long long o = static_cast<long long>(k) * nc + cell;
+      const long long o = base + cell;
       Jout[o] = float(J2);
       Hxout[o] = float(Hx2);
       Hyout[o] = float(Hy2);
       ax += dnu * (I(Hx1) - Hx2);
       ay += dnu * (I(Hy1) - Hy2);
-      // A7 bookkeeping (energy units applied once per substep)
-      if (src) em += dnu * (cdt * js);
-      ab += dnu * (cdt * (kap * J2));
-      wk += dnu * (cdt * (I(W) * I(inv_c)));
-      en += dnu * J2;
-      const float j2f = float(J2), h2 = float(Hx2) * float(Hx2) + float(Hy2) * float(Hy2);
-      const float jj = j2f * j2f;
-      if ((G == 1 ? j2f * wvf : j2f) > tA[k]) {
-        mxf2 = fmaxf(mxf2, fdiv(h2, jj));
-        bad += (h2 > jj * 1.000002f) ? 1 : 0;
+      // A7 bookkeeping (energy units applied once per substep; the factors
+      // c_tilde dt and 1/c once per cell after the bin loop)
+      if (src) em += dnu * js;
+      ab += dnu * (kap * J2);
+      wk += dnu * I(W);
+      if (tdiag) {  // the frequency step recomputes these when it follows
+        en += dnu * J2;
+        const float j2f = float(J2), h2 = float(Hx2) * float(Hx2) + float(Hy2) * float(Hy2);
+        const float jj = j2f * j2f;
+        if ((G == 1 ? j2f * wvf : j2f) > tA[k]) {
+          mxf2 = fmaxf(mxf2, fdiv(h2, jj));
+          bad += (h2 > jj * 1.000002f) ? 1 : 0;
+        }
       }
       if (bnd) {
         I o2 = 0;
         if constexpr (G == 1) {
           if (gx == nx - 1) o2 += wR * I(xJ[ty][tx + 1]);
-          if (gy == ny - 1) o2 += wcell * I(yJ[ty + 1][tx]);
+          if (gy == ny - 1) o2 += wcol * I(yJ[ty + 1][tx]);
         } else {
           if (gx == 0) o2 -= I(xJ[ty][tx]);
           if (gx == nx - 1) o2 += I(xJ[ty][tx + 1]);
@@ -919,6 +951,7 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
         out += dnu * (cdx * o2);
       }
     }
+    base = nbase;
   }
   if (valid) {
     v.fx[cell] = v.fcoef * double(ax);
@@ -927,26 +960,28 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
   double* part = v.partT + static_cast<long long>(blk) * kDiagSlots;
   double s;
   const double wd = G == 1 ? double(wvf) : 1.0;
-  s = block_sum<NT>(double(em) * wd, red);
+  s = block_sum<NT>(double(em) * (v.cdt * wd), red);
   if (tid == 0) part[kSlotEmitted] = s;
-  s = block_sum<NT>(double(ab) * wd, red);
+  s = block_sum<NT>(double(ab) * (v.cdt * wd), red);
   if (tid == 0) part[kSlotAbsorbed] = s;
   s = block_sum<NT>(double(out), red);
   if (tid == 0) part[kSlotOutflow] = s;
-  s = block_sum<NT>(double(wk) * wd, red);
+  s = block_sum<NT>(double(wk) * ((v.cdt / kLight) * wd), red);
   if (tid == 0) part[kSlotWork] = s;
-  s = block_sum<NT>(double(en) * wd, red);
-  if (tid == 0) part[kSlotEnergy] = s;
-  s = block_max<NT>(sqrt(double(mxf2)), red);
-  if (tid == 0) part[kSlotMaxF] = s;
-  s = block_sum<NT>(double(bad), red);
-  if (tid == 0) part[kSlotBad] = s;
+  if (tdiag) {
+    s = block_sum<NT>(double(en) * wd, red);
+    if (tid == 0) part[kSlotEnergy] = s;
+    s = block_max<NT>(sqrt(double(mxf2)), red);
+    if (tid == 0) part[kSlotMaxF] = s;
+    s = block_sum<NT>(double(bad), red);
+    if (tid == 0) part[kSlotBad] = s;
+  }
 }
 
 template <class P, int G>
 __global__ void __launch_bounds__(kTileX* kTileY, 3) transport_kernel_f32(DeviceView v) {
   transport_tile_f32<P, G>(v, blockIdx.x * kTileX, blockIdx.y * kTileY,
-                        blockIdx.y * gridDim.x + blockIdx.x);
+                           blockIdx.y * gridDim.x + blockIdx.x);
 }
 
 // ------------------------------------------------------------ frequency kernel
@@ -976,7 +1011,12 @@ __device__ __forceinline__ void freq_coef(typename P::F Jc, typename P::F Hxc, t
     ak = half * rK;
     Pk = C * ak;
     const float z = -fabsf(Pk);
-    ek = (z == 0.0f) ? 1.0f : fdiv(expm1f(z), z);
+    // E(z) = expm1(z)/z: its Taylor polynomial to z^6 on [-0.5, 0] (truncation
+    // below 2e-7 relative), (e^z - 1)/z below, where the subtraction loses at
+    // most a factor 2.5 of e^z's relative error
+    const float poly =
+        1.0f + z * (0.5f + z * (1.0f / 6 + z * (1.0f / 24 + z * (1.0f / 120 + z * (1.0f / 720 + z * (1.0f / 5040))))));
+    ek = (z > -0.5f) ? poly : (__expf(z) - 1.0f) * frcp(z);
   } else {
     F fx = F(0), fy = F(0);
     if (Jc > F(0)) {
@@ -1374,7 +1414,8 @@ __device__ __forceinline__ void freq_block_bulk(const DeviceView& v, int blk) {
   // coefficients of bin k and eliminates row k-1
   F Pp = F(0), ap = F(0), ep = F(0);
   I Jp = 0, qprev = 0, gprev = 0, Bprev = 0, Aprev = 0;
-  for (int k = 0; k < nb; ++k) {
+  long long ofw = cell - nc;  // plane offset of row k - 1
+  for (int k = 0; k < nb; ++k, ofw += nc) {
     const int s = k % D;
     if (!mbar_wait_bounded(&barF[s], (k / D) & 1)) failed = 1;
     __syncthreads();
@@ -1414,7 +1455,7 @@ __device__ __forceinline__ void freq_block_bulk(const DeviceView& v, int blk) {
         gprev = g;
         Bprev = B;
         Aprev = A;
-        const long long o = static_cast<long long>(k - 1) * nc + cell;
+        const long long o = ofw;
         Jout[o] = float(g);
         Hxout[o] = float(h);
       }
@@ -1452,7 +1493,8 @@ __device__ __forceinline__ void freq_block_bulk(const DeviceView& v, int blk) {
   I mxf = 0;
   int bad = 0;
   I Jnext = 0;
-  for (int j = 0; j < nb; ++j) {
+  long long obw = static_cast<long long>(nb - 1) * nc + cell;  // plane offset of row k
+  for (int j = 0; j < nb; ++j, obw -= nc) {
     const int s = j % D, k = nb - 1 - j;
     if (!mbar_wait_bounded(&barB[s], (j / D) & 1)) failed = 1;
     __syncthreads();
@@ -1461,7 +1503,7 @@ __device__ __forceinline__ void freq_block_bulk(const DeviceView& v, int blk) {
       return;
     }
     if (valid) {
-      const long long o = static_cast<long long>(k) * nc + cell;
+      const long long o = obw;
       const float Jo = ring[s][2][tid], Xo = ring[s][3][tid], Yo = ring[s][4][tid];
       if (act) {
         const I g = I(ring[s][0][tid]), h = I(ring[s][1][tid]);
