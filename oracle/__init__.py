@@ -50,7 +50,7 @@ class Problem(C.Structure):
                 ("c_tilde", _D), ("cfl", _D), ("kappa_abs", _D), ("kappa_F", _D),
                 ("edges", _PD), ("n_hi", _PD), ("rho_d", _PD), ("p_d", _PD),
                 ("ux", _PD), ("uy", _PD), ("lum", _PD), ("geometry", C.c_int),
-                ("bc", C.c_int * 4)]
+                ("bc", C.c_int * 4), ("temp", _PD)]
 
 
 class Diag(C.Structure):
@@ -206,15 +206,21 @@ class Oracle:
 
     def __init__(self, *, nx, ny, dx, edges, T, n_hi, rho_d, p_d, ux, uy, lum,
                  kappa_abs=0.0, kappa_F=0.0, c_tilde=2.99792458e10, cfl=0.4,
-                 gray=False, recoil=True, freq_step=True, geometry=0, bc=(0, 0, 0, 0)):
+                 gray=False, recoil=True, freq_step=True, geometry=0, bc=(0, 0, 0, 0),
+                 temp=None):
         self._keep = [_f64(edges)] + [_f64(np.broadcast_to(a, (ny, nx)))
                                       for a in (n_hi, rho_d, p_d, ux, uy, lum)]
         e, n_hi, rho_d, p_d, ux, uy, lum = self._keep
+        tp = None
+        if temp is not None:
+            tp = _f64(np.broadcast_to(temp, (ny, nx)))
+            self._keep.append(tp)
         self.nx, self.ny = int(nx), int(ny)
         self.prob = Problem(self.nx, self.ny, e.size - 1, int(gray), int(recoil), int(freq_step),
                             float(dx), float(T), float(c_tilde), float(cfl), float(kappa_abs),
                             float(kappa_F), _p(e), _p(n_hi), _p(rho_d), _p(p_d), _p(ux), _p(uy),
-                            _p(lum), int(geometry), (C.c_int * 4)(*[int(b) for b in bc]))
+                            _p(lum), int(geometry), (C.c_int * 4)(*[int(b) for b in bc]),
+                            _p(tp) if tp is not None else None)
         self.ctx = lib().lym1o_create(C.byref(self.prob))
         if not self.ctx:
             raise ValueError("invalid oracle problem")

@@ -48,6 +48,10 @@
  *   - phi and chi are evaluated with this file's own exp/expm1 (Cody-Waite
  *     argument reduction + Taylor polynomial), not lookup tables.
  *   - no FMA contraction: build with -ffp-contract=off.
+ *   - a per-cell gas temperature (App. A evaluates <H>_k, the Doppler width and a_v
+ *     at each cell): A0 runs once per cell at its own T with the same routine
+ *     as for a uniform T; alpha = n_HI sigma0(T), the recoil factor h/(k_B T)
+ *     and the step-3 prefactor dnu_D^2/2 are per cell.
  *   - axisymmetric (R, Z) geometry (the paper's test and RHD set-ups, Sec. 4):
  *     finite volumes per radian with R faces of area R dZ and Z faces of area
  *     (R+^2 - R-^2)/2; the R component of div K carries the hoop source
@@ -66,7 +70,9 @@
  * Gaussian diffusion closed form, thin-slab force multiplier, step-3 vs dense
  * and exact-rational solves, recoil-only equilibrium, central-difference
  * limit vs a banded solver; in (R, Z): the thin-sphere force multiplier
- * tau eta / 4, a steady uniform isotropic field, the Hubble-flow work term.
+ * tau eta / 4, a steady uniform isotropic field, the Hubble-flow work term;
+ * under a temperature field: a uniform field equals the scalar T bit for bit,
+ * and cells at two temperatures equal one-cell runs at their own T.
  */
 #include <math.h>
 #include <stdint.h>
@@ -340,6 +346,7 @@ typedef struct {
                             (zero gradient); 1 = outflow into vacuum (ghosts carry no
                             radiation; opacities and velocities are still copied); the
                             mirrored sides of geometry 1 ignore their entry */
+    const double *temp;  /* [ny][nx] gas temperature (K) per cell, or NULL for the uniform T */
 } lym1o_problem;
 
 typedef struct {
@@ -364,6 +371,10 @@ typedef struct {
      * full volumes 2 pi Vol, the emission factor w_k / (4 pi dnu_k) and
      * <u_R/R> per cell */
     double *AR, *AZ, *Vol, *Rbar, *dlL, *dlR, *invR, *V2pi, *gemc, *gphi;
+    /* per-cell temperature (p.temp != NULL): <H>_k and the emission factor per
+     * [k][cell] (A0 at the cell's T), the recoil factor h/(k_B T) and the
+     * frequency-diffusion prefactor dnu_D^2/2 per cell; NULL otherwise */
+    double *Hc, *Gc, *hkTc, *Kcc;
 } lym1o_ctx;
 
 static int o_cl(int i, int n) { return i < 0 ? 0 : (i >= n ? n - 1 : i); }
@@ -381,6 +392,7 @@ void lym1o_destroy(lym1o_ctx *c)
     free(c->alpha); free(c->gxx); free(c->gyy); free(c->gsh);
     free(c->AR); free(c->AZ); free(c->Vol); free(c->Rbar); free(c->dlL); free(c->dlR);
     free(c->invR); free(c->V2pi); free(c->gemc); free(c->gphi);
+    free(c->Hc); free(c->Gc); free(c->hkTc); free(c->Kcc);
     free(c);
 }
 
@@ -490,6 +502,11 @@ lym1o_ctx *lym1o_create(const lym1o_problem *p)
         for (int i = 0; i < nx; ++i) {
             size_t id = (size_t)j * nx + i;
             c->alpha[id] = p->n_hi[id] * c->sigma0;
+            if (p->temp) {
+                double lc[3];
+                lym1o_line(p->temp[id], lc);
+                c->alpha[id] = p->n_hi[id] * lc[2];
+            }
             if (p->geometry == 1) {
                 /* mirrored ghosts: across the axis u_R flips, across the midplane u_Z flips */
                 const double *ux = p->ux, *uy = p->uy;
@@ -525,6 +542,38 @@ lym1o_ctx *lym1o_create(const lym1o_problem *p)
         }
     /* RT time step (Sec. 2.1, CFL condition, D = 2 dimensions) */
     c->dt_cfl = (p->cfl / 2.0) * (p->dx / (p->c_tilde + umax));
+    if (p->temp) {
+        /* A0 at every cell's own temperature (App. A: <H>_k, the Doppler width
+         * and a_v at T; Sec. 2.1 step 2: emission fractions) */
+        c->Hc = malloc((size_t)nb * nc * sizeof(double));
+        c->Gc = malloc((size_t)nb * nc * sizeof(double));
+        c->hkTc = malloc(nc * sizeof(double));
+        c->Kcc = malloc(nc * sizeof(double));
+        double *d1 = malloc(N * sizeof(double)), *d2 = malloc(N * sizeof(double));
+        double *d3 = malloc(N * sizeof(double)), *d4 = malloc(N * sizeof(double));
+        for (size_t id = 0; id < nc; ++id) {
+            const double Tc = p->temp[id];
+            double lc[3];
+            lym1o_line(Tc, lc);
+            c->hkTc[id] = O_HPL / (O_KB * Tc);
+            c->Kcc[id] = 0.5 * (lc[0] * lc[0]);
+            double etac = lym1o_bin_tables(N, p->edges, Tc, d1, d2, d3, d4);
+            int i = (int)(id % nx);
+            for (int k = 0; k < nb; ++k) {
+                size_t kid = (size_t)k * nc + id;
+                if (p->gray) {
+                    c->Hc[kid] = etac;
+                    c->Gc[kid] = (p->geometry == 1) ? 1.0 / (4.0 * O_PI) : 1.0 / fourpiV;
+                } else {
+                    c->Hc[kid] = d3[k];
+                    c->Gc[kid] = (p->geometry == 1) ? d4[k] / ((4.0 * O_PI) * d1[k])
+                                                    : d4[k] / (fourpiV * d1[k]);
+                }
+            }
+            (void)i;
+        }
+        free(d1); free(d2); free(d3); free(d4);
+    }
     return c;
 }
 
@@ -835,6 +884,31 @@ int lym1o_substep_cyl(const lym1o_ctx *c, double dt, const double *J, const doub
                       const double *Hy, double *Jo, double *Hxo, double *Hyo, double *fx,
                       double *fy, lym1o_diag *dg);
 
+/* per-bin table entry, or the cell's own entry under a temperature field */
+#define HAV(k, id) (c->Hc ? c->Hc[(size_t)(k) * nc + (id)] : c->Havg[k])
+#define GEMK(k, id) (c->Gc ? c->Gc[(size_t)(k) * nc + (id)] : c->gem[k])
+#define GEMC(k, id) (c->Gc ? c->Gc[(size_t)(k) * nc + (id)] : c->gemc[k])
+
+/* step 3 of one cell: the per-bin tables or the cell's own (temperature field) */
+static void o_freq_of_cell(const lym1o_ctx *c, size_t id, size_t nc, const double *nbc,
+                           const double *DdU, double cdt, const double *Jin, double *Jn,
+                           double *scr, double *Hcell, double *Rcell)
+{
+    const int nb = c->nb;
+    if (!c->Hc) {
+        const double Kc0 = 0.5 * (c->dnuD * c->dnuD);
+        o_freq_cell(nb, c->dnu, c->half, c->Havg, c->Rk, nbc, Kc0 * c->alpha[id], DdU, cdt, Jin, Jn,
+                    scr);
+        return;
+    }
+    for (int k = 0; k < nb; ++k) {
+        Hcell[k] = c->Hc[(size_t)k * nc + id];
+        Rcell[k] = c->p.recoil ? (c->hkTc[id] - 2.0 / c->nubar[k]) : 0.0;
+    }
+    o_freq_cell(nb, c->dnu, c->half, Hcell, Rcell, nbc, c->Kcc[id] * c->alpha[id], DdU, cdt, Jin, Jn,
+                scr);
+}
+
 int lym1o_substep(const lym1o_ctx *c, double dt, const double *J, const double *Hx,
                   const double *Hy, double *Jo, double *Hxo, double *Hyo, double *fx,
                   double *fy, lym1o_diag *dg)
@@ -867,8 +941,7 @@ int lym1o_substep(const lym1o_ctx *c, double dt, const double *J, const double *
 
     for (int k = 0; k < nb; ++k) {
         const double *Jk = J + (size_t)k * nc, *Hxk = Hx + (size_t)k * nc, *Hyk = Hy + (size_t)k * nc;
-        const double Hk = c->Havg[k];
-#define AF(id) (c->alpha[id] * Hk + p->rho_d[id] * p->kappa_F)
+#define AF(id) (c->alpha[id] * HAV(k, id) + p->rho_d[id] * p->kappa_F)
         /* x faces: face i sits between cells i-1 and i, i = 0..nx */
 #pragma omp parallel for schedule(static)
         for (int j = 0; j < ny; ++j)
@@ -926,10 +999,10 @@ int lym1o_substep(const lym1o_ctx *c, double dt, const double *J, const double *
                 double Hx1 = Hxk[id] - cdt * (divHx / dx);
                 double Hy1 = Hyk[id] - cdt * (divHy / dx);
                 /* A4: (J''-J')/(ct dt) = j - kappa J'', (H''-H')/(ct dt) = -aF H'' */
-                double aH = c->alpha[id] * Hk;
+                double aH = c->alpha[id] * HAV(k, id);
                 double kap = p->rho_d[id] * p->kappa_abs + p->p_d[id] * aH;
                 double aF = aH + p->rho_d[id] * p->kappa_F;
-                double js = p->lum[id] * c->gem[k];
+                double js = p->lum[id] * GEMK(k, id);
                 double J2 = (J1 + cdt * js) / (1.0 + cdt * kap);
                 double Hx2 = Hx1 / (1.0 + cdt * aF);
                 double Hy2 = Hy1 / (1.0 + cdt * aF);
@@ -942,9 +1015,9 @@ int lym1o_substep(const lym1o_ctx *c, double dt, const double *J, const double *
         /* bookkeeping for this bin (serial, fixed order) */
         for (size_t id = 0; id < nc; ++id) {
             size_t kid = (size_t)k * nc + id;
-            double aH = c->alpha[id] * Hk;
+            double aH = c->alpha[id] * HAV(k, id);
             double kap = p->rho_d[id] * p->kappa_abs + p->p_d[id] * aH;
-            double js = p->lum[id] * c->gem[k];
+            double js = p->lum[id] * GEMK(k, id);
             o_kadd(&s_em, c->dnu[k] * (cdt * js));
             o_kadd(&s_ab, c->dnu[k] * (cdt * (kap * Jo[kid])));
             o_kadd(&s_wk, c->dnu[k] * (cdt * (Wk[id] / O_C)));
@@ -968,7 +1041,6 @@ int lym1o_substep(const lym1o_ctx *c, double dt, const double *J, const double *
 
     /* A6: frequency step per cell, in place on (Jo, Hxo, Hyo) */
     if (!p->gray && p->freq_step) {
-        const double Kc0 = 0.5 * (c->dnuD * c->dnuD);
         double *nbc = malloc(nb * sizeof(double));
         for (int k = 0; k < nb; ++k) nbc[k] = c->nubar[k] / O_C;
 #pragma omp parallel
@@ -976,6 +1048,7 @@ int lym1o_substep(const lym1o_ctx *c, double dt, const double *J, const double *
             double *scr = malloc((size_t)6 * nb * sizeof(double));
             double *Jin = malloc(nb * sizeof(double)), *Jn = malloc(nb * sizeof(double));
             double *DdU = malloc(nb * sizeof(double));
+            double *Hcell = malloc(nb * sizeof(double)), *Rcell = malloc(nb * sizeof(double));
 #pragma omp for schedule(static)
             for (long long idl = 0; idl < (long long)nc; ++idl) {
                 size_t id = (size_t)idl;
@@ -1000,8 +1073,7 @@ int lym1o_substep(const lym1o_ctx *c, double dt, const double *J, const double *
                     DdU[k] = (Dxx * c->gxx[id] + Dyy * c->gyy[id]) + Dxy * c->gsh[id];
                     Jin[k] = Jo[kid];
                 }
-                o_freq_cell(nb, c->dnu, c->half, c->Havg, c->Rk, nbc, Kc0 * c->alpha[id], DdU, cdt,
-                            Jin, Jn, scr);
+                o_freq_of_cell(c, id, nc, nbc, DdU, cdt, Jin, Jn, scr, Hcell, Rcell);
                 for (int k = 0; k < nb; ++k) {
                     size_t kid = (size_t)k * nc + id;
                     double ratio = (Jin[k] > 0.0) ? Jn[k] / Jin[k] : 0.0;
@@ -1011,7 +1083,7 @@ int lym1o_substep(const lym1o_ctx *c, double dt, const double *J, const double *
                     o_causal(Jo[kid], &Hxo[kid], &Hyo[kid]);
                 }
             }
-            free(scr); free(Jin); free(Jn); free(DdU);
+            free(scr); free(Jin); free(Jn); free(DdU); free(Hcell); free(Rcell);
         }
         free(nbc);
     }
@@ -1087,8 +1159,7 @@ int lym1o_substep_cyl(const lym1o_ctx *c, double dt, const double *J, const doub
 
     for (int k = 0; k < nb; ++k) {
         const double *Jk = J + (size_t)k * nc, *Hxk = Hx + (size_t)k * nc, *Hyk = Hy + (size_t)k * nc;
-        const double Hk = c->Havg[k];
-#define AFC(id) (c->alpha[id] * Hk + p->rho_d[id] * p->kappa_F)
+#define AFC(id) (c->alpha[id] * HAV(k, id) + p->rho_d[id] * p->kappa_F)
         /* R faces: face i between cells i-1 and i */
 #pragma omp parallel for schedule(static)
         for (int j = 0; j < ny; ++j)
@@ -1162,10 +1233,10 @@ int lym1o_substep_cyl(const lym1o_ctx *c, double dt, const double *J, const doub
                 double J1 = Jk[id] - cdt * (divJ + W / O_C);
                 double Hx1 = Hxk[id] - cdt * divHx;
                 double Hy1 = Hyk[id] - cdt * divHy;
-                double aH = c->alpha[id] * Hk;
+                double aH = c->alpha[id] * HAV(k, id);
                 double kap = p->rho_d[id] * p->kappa_abs + p->p_d[id] * aH;
                 double aF = aH + p->rho_d[id] * p->kappa_F;
-                double js = (p->lum[id] / c->V2pi[i]) * c->gemc[k];
+                double js = (p->lum[id] / c->V2pi[i]) * GEMC(k, id);
                 double J2 = (J1 + cdt * js) / (1.0 + cdt * kap);
                 double Hx2 = Hx1 / (1.0 + cdt * aF);
                 double Hy2 = Hy1 / (1.0 + cdt * aF);
@@ -1178,9 +1249,9 @@ int lym1o_substep_cyl(const lym1o_ctx *c, double dt, const double *J, const doub
         for (size_t id = 0; id < nc; ++id) {
             size_t kid = (size_t)k * nc + id;
             int i = (int)(id % nx);
-            double aH = c->alpha[id] * Hk;
+            double aH = c->alpha[id] * HAV(k, id);
             double kap = p->rho_d[id] * p->kappa_abs + p->p_d[id] * aH;
-            double js = (p->lum[id] / c->V2pi[i]) * c->gemc[k];
+            double js = (p->lum[id] / c->V2pi[i]) * GEMC(k, id);
             o_kadd(&s_em, c->V2pi[i] * (c->dnu[k] * (cdt * js)));
             o_kadd(&s_ab, c->V2pi[i] * (c->dnu[k] * (cdt * (kap * Jo[kid]))));
             o_kadd(&s_wk, c->V2pi[i] * (c->dnu[k] * (cdt * (Wk[id] / O_C))));
@@ -1198,7 +1269,6 @@ int lym1o_substep_cyl(const lym1o_ctx *c, double dt, const double *J, const doub
         fy[id] = fcoef * ay[id];
     }
     if (!p->gray && p->freq_step) {
-        const double Kc0 = 0.5 * (c->dnuD * c->dnuD);
         double *nbc = malloc(nb * sizeof(double));
         for (int k = 0; k < nb; ++k) nbc[k] = c->nubar[k] / O_C;
 #pragma omp parallel
@@ -1206,6 +1276,7 @@ int lym1o_substep_cyl(const lym1o_ctx *c, double dt, const double *J, const doub
             double *scr = malloc((size_t)6 * nb * sizeof(double));
             double *Jin = malloc(nb * sizeof(double)), *Jn = malloc(nb * sizeof(double));
             double *DdU = malloc(nb * sizeof(double));
+            double *Hcell = malloc(nb * sizeof(double)), *Rcell = malloc(nb * sizeof(double));
 #pragma omp for schedule(static)
             for (long long idl = 0; idl < (long long)nc; ++idl) {
                 size_t id = (size_t)idl;
@@ -1234,8 +1305,7 @@ int lym1o_substep_cyl(const lym1o_ctx *c, double dt, const double *J, const doub
                              Dpp * c->gphi[id];
                     Jin[k] = Jo[kid];
                 }
-                o_freq_cell(nb, c->dnu, c->half, c->Havg, c->Rk, nbc, Kc0 * c->alpha[id], DdU, cdt,
-                            Jin, Jn, scr);
+                o_freq_of_cell(c, id, nc, nbc, DdU, cdt, Jin, Jn, scr, Hcell, Rcell);
                 for (int k = 0; k < nb; ++k) {
                     size_t kid = (size_t)k * nc + id;
                     double ratio = (Jin[k] > 0.0) ? Jn[k] / Jin[k] : 0.0;
@@ -1245,7 +1315,7 @@ int lym1o_substep_cyl(const lym1o_ctx *c, double dt, const double *J, const doub
                     o_causal(Jo[kid], &Hxo[kid], &Hyo[kid]);
                 }
             }
-            free(scr); free(Jin); free(Jn); free(DdU);
+            free(scr); free(Jin); free(Jn); free(DdU); free(Hcell); free(Rcell);
         }
         free(nbc);
     }

@@ -107,6 +107,7 @@ class Cloud:
     substeps: int = 1
     geometry: int = 0        # 0: 2D Cartesian slab; 1: axisymmetric (R = x, Z = y)
     bc: tuple = (0, 0, 0, 0)  # x-, x+, y-, y+: 0 = zero-gradient outflow, 1 = vacuum outflow
+    temp: object = None       # [ny][nx] gas temperature (K) per cell, or None for the uniform T
     meta: dict = field(default_factory=dict)
 
     @property
@@ -119,7 +120,8 @@ class Cloud:
                     rho_d=self.rho_d, p_d=self.p_d, ux=self.ux, uy=self.uy, lum=self.lum,
                     kappa_abs=self.kappa_abs, kappa_F=self.kappa_F, c_tilde=self.c_tilde,
                     cfl=self.cfl, gray=self.gray, recoil=self.recoil,
-                    freq_step=self.freq_step, geometry=self.geometry, bc=self.bc)
+                    freq_step=self.freq_step, geometry=self.geometry, bc=self.bc,
+                    temp=self.temp)
 
 
 def uniform_gray(nx=64, ny=64, box_pc=2.0, n_h=1e3, L_sun=1e6, name="uniform-gray"):
@@ -242,3 +244,16 @@ def cone_cloud(n=256, tau_cl=1e8, tau_cone=1e5, T=1.0e4, R_cl_pc=1.0, L_sun=1e6,
     return Cloud(name, n, n, dx, n_hi, z.copy(), z.copy(), z.copy(), z.copy(), lum, T=T,
                  recoil=True, freq_step=True, kappa_abs=0.0, kappa_F=0.0, geometry=1,
                  bc=(0, 1, 0, 1), meta={"tau_cl": tau_cl, "tau_cone": tau_cone, "R_cl": R_cl, "t_max": t_max})
+
+
+def two_phase_temperature(nx, ny, seed, T_cold=100.0, T_hot=1.0e4, frac_hot=0.5, smooth=True):
+    """Seeded temperature field with warm and cold phases (K): a k^-4 Gaussian
+    field thresholded at the quantile giving frac_hot of the cells the warm
+    phase, with a log-linear transition of width ~0.3 sigma when smooth."""
+    g = gaussian_field(nx, ny, seed)
+    t = np.quantile(g, 1.0 - frac_hot)
+    if smooth:
+        s = 0.5 * (1.0 + np.tanh((g - t) / 0.3))
+    else:
+        s = (g > t).astype(float)
+    return np.exp(np.log(T_cold) + s * (np.log(T_hot) - np.log(T_cold)))
