@@ -101,6 +101,14 @@ typedef struct {
   int freq_step;          /* 1: run the frequency step (ignored for a gray group) */
   int precision;          /* LYM1_FP64_DET, LYM1_FP64, LYM1_MIXED or LYM1_MIXED_FAST */
   void *cuda_stream;      /* cudaStream_t the context runs on; NULL = legacy default stream */
+  const double *temp_field; /* [ny][nx] gas temperature per cell, K, each > 0 (host or device
+                               pointer), or NULL for the uniform temp_K.  With a field the
+                               per-bin tables (App. A: <H>_k, Doppler width, a_v, sigma0; Sec. 2.1
+                               step 2: emission fractions; the recoil factor h/(k_B T)) are built
+                               for every cell's own temperature, once at creation, on the host
+                               (the routine of the uniform case, once per distinct value), and
+                               held per [bin][cell] on the device.  Contexts with and without a
+                               field cannot share a batch. */
 } lym1_opacities;
 
 typedef struct {

@@ -32,7 +32,7 @@ def _cmd(src: str) -> list[str]:
     obj = os.path.join(BUILD, src + ".o")
     inc = ["-I", os.path.join(ROOT, "include"), "-I", CSRC]
     if src.endswith(".cpp"):
-        return ["g++", "-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-fno-fast-math",
+        return ["g++", "-O2", "-std=c++17", "-fPIC", "-pthread", "-ffp-contract=off", "-fno-fast-math",
                 *inc, "-c", path, "-o", obj]
     cmd = [NVCC, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
            "-Xcompiler", "-ffp-contract=off", *inc, "-c", path, "-o", obj]
@@ -70,7 +70,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         list(ex.map(run, [_cmd(s) for s in SOURCES]))
     objs = [os.path.join(BUILD, s + ".o") for s in SOURCES]
-    run([NVCC, *ARCH, "-shared", "-o", LIB + ".tmp", *objs])
+    run([NVCC, *ARCH, "-shared", "-o", LIB + ".tmp", *objs, "-lpthread"])
     os.replace(LIB + ".tmp", LIB)
     return LIB
 

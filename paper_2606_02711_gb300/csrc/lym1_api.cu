@@ -18,6 +18,11 @@ using namespace lym1;
 struct lym1_ctx {
   int nx = 0, ny = 0, nb = 0, precision = 0, gray = 0, freq_step = 0, recoil = 0, geometry = 0;
   int vac = 0;  // outflow sides into vacuum, bit 0 x-, 1 x+, 2 y-, 3 y+
+  // temperature field: per [bin][cell] tables (state type) and per-cell constants
+  int pt = 0;
+  void *Hc = nullptr, *Gc = nullptr;
+  double *gmaxc = nullptr, *Kcc = nullptr, *hkTc = nullptr, *t_2nu = nullptr, *sig0c = nullptr;
+  float* f_2nu = nullptr;
   long long nc = 0;
   double dx = 0, T = 0, c_tilde = 0, cfl = 0, kabs = 0, kF = 0, dt_cfl = 0, umax = 0;
   double L_tot = 0, device_bytes = 0, gem_max = 1;
@@ -167,6 +172,14 @@ DeviceView make_view(const lym1_ctx* c, double dt) {
   v.f_half = c->f_half;
   v.geometry = c->geometry;
   v.vac = c->vac;
+  v.pt = c->pt;
+  v.Hc = c->Hc;
+  v.Gc = c->Gc;
+  v.gmaxc = c->gmaxc;
+  v.Kcc = c->Kcc;
+  v.hkTc = c->hkTc;
+  v.t_2nu = c->t_2nu;
+  v.f_2nu = c->f_2nu;
   v.gphi = c->gphi;
   v.g_AR = c->g_AR;
   v.g_AZ = c->g_AZ;
@@ -304,7 +317,7 @@ void drop_events(lym1_ctx* c) {
 
 struct lym1_batch {
   std::vector<lym1_ctx*> ctxs;
-  int precision = 0, nb = 0, nT = 0, nF = 0, geometry = 0;
+  int precision = 0, nb = 0, nT = 0, nF = 0, geometry = 0, pt = 0;
   cudaStream_t ctx_stream = nullptr, bs = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr, t0 = nullptr, t1 = nullptr;
   DeviceView *viewsT = nullptr, *viewsF = nullptr;
@@ -324,13 +337,13 @@ namespace {
 int batch_launch(lym1_batch* b, cudaStream_t s) {
   const int n = static_cast<int>(b->ctxs.size());
   if (b->precision == LYM1_FP64_DET) {
-    LYM1_TRYK(launch_batched_det(0, b->geometry, b->viewsT, b->itemsT, b->nT, b->gridT, b->nb, s));
-    LYM1_TRYK(launch_batched_det(1, b->geometry, b->viewsF, b->itemsF, b->nF, b->gridF, b->nb, s));
+    LYM1_TRYK(launch_batched_det(0, b->geometry, b->pt, b->viewsT, b->itemsT, b->nT, b->gridT, b->nb, s));
+    LYM1_TRYK(launch_batched_det(1, b->geometry, b->pt, b->viewsF, b->itemsF, b->nF, b->gridF, b->nb, s));
   } else {
-    LYM1_TRYK(launch_batched_fast(b->precision, 0, b->geometry, b->viewsT, b->itemsT, b->nT, b->gridT,
-                                  b->nb, s));
-    LYM1_TRYK(launch_batched_fast(b->precision, 1, b->geometry, b->viewsF, b->itemsF, b->nF, b->gridF,
-                                  b->nb, s));
+    LYM1_TRYK(launch_batched_fast(b->precision, 0, b->geometry, b->pt, b->viewsT, b->itemsT, b->nT,
+                                  b->gridT, b->nb, s));
+    LYM1_TRYK(launch_batched_fast(b->precision, 1, b->geometry, b->pt, b->viewsF, b->itemsF, b->nF,
+                                  b->gridF, b->nb, s));
   }
   LYM1_TRYK(launch_finalize_batched(b->jobs, n, s));
   return LYM1_OK;
@@ -343,19 +356,19 @@ int batch_launch_timed(lym1_batch* b, lym1_ctx* c) {
   {
     KernelTimer t(c, 0);
     if (b->precision == LYM1_FP64_DET)
-      LYM1_TRYK(launch_batched_det(0, b->geometry, b->viewsT, b->itemsT, b->nT, b->gridT, b->nb,
-                                   c->stream));
+      LYM1_TRYK(launch_batched_det(0, b->geometry, b->pt, b->viewsT, b->itemsT, b->nT, b->gridT,
+                                   b->nb, c->stream));
     else
-      LYM1_TRYK(launch_batched_fast(b->precision, 0, b->geometry, b->viewsT, b->itemsT, b->nT,
+      LYM1_TRYK(launch_batched_fast(b->precision, 0, b->geometry, b->pt, b->viewsT, b->itemsT, b->nT,
                                     b->gridT, b->nb, c->stream));
   }
   {
     KernelTimer t(c, 1);
     if (b->precision == LYM1_FP64_DET)
-      LYM1_TRYK(launch_batched_det(1, b->geometry, b->viewsF, b->itemsF, b->nF, b->gridF, b->nb,
-                                   c->stream));
+      LYM1_TRYK(launch_batched_det(1, b->geometry, b->pt, b->viewsF, b->itemsF, b->nF, b->gridF,
+                                   b->nb, c->stream));
     else
-      LYM1_TRYK(launch_batched_fast(b->precision, 1, b->geometry, b->viewsF, b->itemsF, b->nF,
+      LYM1_TRYK(launch_batched_fast(b->precision, 1, b->geometry, b->pt, b->viewsF, b->itemsF, b->nF,
                                     b->gridF, b->nb, c->stream));
   }
   KernelTimer t(c, 2);
@@ -484,6 +497,28 @@ int lym1_create(const lym1_grid* grid, const lym1_groups* groups, const lym1_opa
   float** ftabs[] = {&c->f_H, &c->f_dnu, &c->f_G, &c->f_R, &c->f_nbc, &c->f_half};
   for (float** p : ftabs)
     if (rc == LYM1_OK) rc = dalloc_t(c, p, static_cast<size_t>(c->nb));
+  CellTables ct;
+  if (op->temp_field) {
+    // per-cell A0 on the host (the field may live on the device)
+    std::vector<double> hT(plane);
+    if (cudaMemcpy(hT.data(), op->temp_field, plane * sizeof(double), cudaMemcpyDefault) != cudaSuccess) {
+      cudaGetLastError();
+      rc = LYM1_EINVAL;
+    }
+    for (size_t i = 0; rc == LYM1_OK && i < plane; ++i)
+      if (!(hT[i] > 0.0) || !std::isfinite(hT[i])) rc = LYM1_EINVAL;
+    if (rc == LYM1_OK) {
+      c->pt = 1;
+      build_cell_tables(edges, hT.data(), nc, c->dx, c->gray, c->recoil, grid->geometry, &ct);
+      if (rc == LYM1_OK) rc = dalloc(c, &c->Hc, nstate * c->selem);
+      if (rc == LYM1_OK) rc = dalloc(c, &c->Gc, nstate * c->selem);
+      double** pc[] = {&c->gmaxc, &c->Kcc, &c->hkTc, &c->sig0c};
+      for (double** q : pc)
+        if (rc == LYM1_OK) rc = dalloc_t(c, q, plane);
+      if (rc == LYM1_OK) rc = dalloc_t(c, &c->t_2nu, static_cast<size_t>(c->nb));
+      if (rc == LYM1_OK) rc = dalloc_t(c, &c->f_2nu, static_cast<size_t>(c->nb));
+    }
+  }
   CylTables cyl;
   const size_t ncol = static_cast<size_t>(c->nx);
   if (c->geometry == 1) {
@@ -526,8 +561,43 @@ int lym1_create(const lym1_grid* grid, const lym1_groups* groups, const lym1_opa
       cudaMemcpyAsync(c->rho, op->rho_dust, pb, cudaMemcpyDefault, s) != cudaSuccess ||
       cudaMemcpyAsync(c->pd, op->p_d, pb, cudaMemcpyDefault, s) != cudaSuccess)
     return fail(LYM1_ECUDA);
-  if (launch_setup_statics(d_nhi, c->ux, c->uy, c->tab.lc.sigma0, c->nx, c->ny, c->dx, c->alpha,
-                           c->gxx, c->gyy, c->gsh, c->geometry, c->gphi, s) != 0)
+  if (c->pt) {
+    // per-[bin][cell] tables in the state type (FP32 policies: G / gmax)
+    const size_t nsv = ct.H.size();
+    if (c->selem == 8) {
+      if (cudaMemcpy(c->Hc, ct.H.data(), nsv * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+          cudaMemcpy(c->Gc, ct.G.data(), nsv * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail(LYM1_ECUDA);
+    } else {
+      std::vector<float> hf(nsv), gf(nsv);
+      for (size_t q = 0; q < nsv; ++q) {
+        hf[q] = static_cast<float>(ct.H[q]);
+        gf[q] = static_cast<float>(ct.G[q] / ct.gmax[q % plane]);
+      }
+      if (cudaMemcpy(c->Hc, hf.data(), nsv * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
+          cudaMemcpy(c->Gc, gf.data(), nsv * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail(LYM1_ECUDA);
+    }
+    // the recoil factor R_k = h/(k_B T) - 2/nubar_k, zero without recoil
+    std::vector<double> hk(ct.hkT), t2(c->nb, 0.0);
+    std::vector<float> f2(c->nb, 0.0f);
+    if (c->recoil && !c->gray)
+      for (int k = 0; k < c->nb; ++k) {
+        t2[k] = 2.0 / c->tab.nubar[k];
+        f2[k] = static_cast<float>(t2[k]);
+      }
+    else
+      std::fill(hk.begin(), hk.end(), 0.0);
+    if (cudaMemcpy(c->gmaxc, ct.gmax.data(), pb, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(c->Kcc, ct.Kc.data(), pb, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(c->hkTc, hk.data(), pb, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(c->sig0c, ct.sigma0.data(), pb, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(c->t_2nu, t2.data(), sizeof(double) * c->nb, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(c->f_2nu, f2.data(), sizeof(float) * c->nb, cudaMemcpyHostToDevice) != cudaSuccess)
+      return fail(LYM1_ECUDA);
+  }
+  if (launch_setup_statics(d_nhi, c->ux, c->uy, c->tab.lc.sigma0, c->pt ? c->sig0c : nullptr, c->nx,
+                           c->ny, c->dx, c->alpha, c->gxx, c->gyy, c->gsh, c->geometry, c->gphi, s) != 0)
     return fail(LYM1_ECUDA);
   if (c->geometry == 1) {
     const std::pair<double*, const std::vector<double>*> dt[] = {
@@ -824,7 +894,8 @@ int lym1_batch_create(lym1_ctx* const* ctxs, int n_ctx, lym1_batch** out) {
   for (int i = 0; i < n_ctx; ++i) {
     if (!ctxs[i] || ctxs[i]->gray || !ctxs[i]->freq_step) return LYM1_EINVAL;
     if (ctxs[i]->precision != ctxs[0]->precision || ctxs[i]->nb != ctxs[0]->nb ||
-        ctxs[i]->stream != ctxs[0]->stream || ctxs[i]->geometry != ctxs[0]->geometry)
+        ctxs[i]->stream != ctxs[0]->stream || ctxs[i]->geometry != ctxs[0]->geometry ||
+        ctxs[i]->pt != ctxs[0]->pt)
       return LYM1_EINVAL;
   }
   lym1_batch* b = new (std::nothrow) lym1_batch();
@@ -832,6 +903,7 @@ int lym1_batch_create(lym1_ctx* const* ctxs, int n_ctx, lym1_batch** out) {
   b->ctxs.assign(ctxs, ctxs + n_ctx);
   b->precision = ctxs[0]->precision;
   b->geometry = ctxs[0]->geometry;
+  b->pt = ctxs[0]->pt;
   b->nb = ctxs[0]->nb;
   b->ctx_stream = ctxs[0]->stream;
   std::vector<DeviceView> vT, vF;
@@ -887,10 +959,10 @@ int lym1_batch_create(lym1_ctx* const* ctxs, int n_ctx, lym1_batch** out) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   if (nsm < 1) nsm = 1;
-  const int rT = b->precision == LYM1_FP64_DET ? resident_blocks_det(0, b->geometry)
-                                               : resident_blocks_fast(b->precision, 0, b->geometry);
-  const int rF = b->precision == LYM1_FP64_DET ? resident_blocks_det(1, b->geometry)
-                                               : resident_blocks_fast(b->precision, 1, b->geometry);
+  const int rT = b->precision == LYM1_FP64_DET ? resident_blocks_det(0, b->geometry, b->pt)
+                                               : resident_blocks_fast(b->precision, 0, b->geometry, b->pt);
+  const int rF = b->precision == LYM1_FP64_DET ? resident_blocks_det(1, b->geometry, b->pt)
+                                               : resident_blocks_fast(b->precision, 1, b->geometry, b->pt);
   for (int m = 1; m <= rT; ++m) b->candT.push_back(std::min(b->nT, m * nsm));
   const int gf = std::min(b->nF, rF * nsm);
   b->candF.push_back(gf);

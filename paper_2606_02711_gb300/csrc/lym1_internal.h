@@ -55,6 +55,16 @@ void build_tables(const std::vector<double>& edges, double T, double dx, int gra
                   BinTables* t, int geometry = 0);
 void build_cyl_tables(int nx, double dx, CylTables* g);
 
+// A0 at every cell's own temperature (per-cell gas temperature): <H>_k and the
+// emission factor per [k][cell] and the per-cell line constants.  The same
+// routine as build_tables runs once per distinct temperature value.
+struct CellTables {
+  std::vector<double> H, G;                // [nb][nc]
+  std::vector<double> sigma0, hkT, Kc, gmax;  // [nc]; Kc = dnu_D^2 / 2, gmax = max_k G
+};
+void build_cell_tables(const std::vector<double>& edges, const double* T, long long nc, double dx,
+                       int gray, int recoil, int geometry, CellTables* out);
+
 // ---------------------------------------------------------------- kernel side
 constexpr int kTileX = 32;   // transport tile: one thread per cell
 constexpr int kTileY = 8;
@@ -130,6 +140,17 @@ struct DeviceView {
   // outflow sides into vacuum (bit 0 x-, 1 x+, 2 y-, 3 y+): ghost cells there
   // carry no radiation; the other outflow sides copy the edge cell
   int vac = 0;
+  // per-cell gas temperature (pt = 1): <H>_k and the emission factor per
+  // [k][cell] in the state type (FP32 policies hold G / gmax), and the
+  // per-cell line constants; the per-bin tables above are then unused
+  int pt = 0;
+  const void* Hc = nullptr;
+  const void* Gc = nullptr;
+  const double* gmaxc = nullptr;
+  const double* Kcc = nullptr;
+  const double* hkTc = nullptr;
+  const double* t_2nu = nullptr;  // 2 / nubar_k
+  const float* f_2nu = nullptr;
   const double* gphi = nullptr;
   const double* g_AR = nullptr;
   const double* g_AZ = nullptr;
@@ -158,9 +179,11 @@ int launch_energy(int precision, const void* J, const double* dnu, int nb, long 
                   double* part, const double* wcol, int nx, void* stream);
 int launch_finalize(const double* partT, int nT, const double* partE, int nE, double* acc,
                     int mode, void* stream);
+// sigma0c: per-cell line-centre cross-sections (temperature field) or nullptr
 int launch_setup_statics(const double* n_hi, const double* ux, const double* uy, double sigma0,
-                         int nx, int ny, double dx, double* alpha, double* gxx, double* gyy,
-                         double* gsh, int geometry, double* gphi, void* stream);
+                         const double* sigma0c, int nx, int ny, double dx, double* alpha,
+                         double* gxx, double* gyy, double* gsh, int geometry, double* gphi,
+                         void* stream);
 // lum[j][i] /= V2pi[i] (axisymmetric grid: per-volume luminosity density)
 int launch_scale_columns(double* lum, const double* V2pi, int nx, long long nc, void* stream);
 int launch_convert_out(int precision, const void* src, double* dst, long long n, double scale,
@@ -178,12 +201,13 @@ struct FinalizeJob {
   int nT, nE;
 };
 // every context of one batched launch has the same geometry
-int launch_batched_det(int kind, int geometry, const DeviceView* views, const void* items, int n,
-                       int grid, int nb_max, void* stream);
-int launch_batched_fast(int precision, int kind, int geometry, const DeviceView* views,
+// every context of one batched launch has the same geometry and temperature mode
+int launch_batched_det(int kind, int geometry, int pt, const DeviceView* views, const void* items,
+                       int n, int grid, int nb_max, void* stream);
+int launch_batched_fast(int precision, int kind, int geometry, int pt, const DeviceView* views,
                         const void* items, int n, int grid, int nb_max, void* stream);
-int resident_blocks_det(int kind, int geometry);
-int resident_blocks_fast(int precision, int kind, int geometry);
+int resident_blocks_det(int kind, int geometry, int pt);
+int resident_blocks_fast(int precision, int kind, int geometry, int pt);
 int launch_finalize_batched(const FinalizeJob* jobs, int n, void* stream);
 
 inline int transport_blocks(int nx, int ny) {

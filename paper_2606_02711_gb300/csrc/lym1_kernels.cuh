@@ -333,7 +333,7 @@ __device__ __forceinline__ double block_max(double v, double* red) {
 }
 
 // ------------------------------------------------------------ transport kernel
-template <class P, int G>
+template <class P, int G, bool PT>
 __device__ __forceinline__ void transport_tile(const DeviceView& v, int x0, int y0, int blk) {
   using S = typename P::S;
   using F = typename P::F;
@@ -346,6 +346,9 @@ __device__ __forceinline__ void transport_tile(const DeviceView& v, int x0, int 
   __shared__ F xJ[TY][TX + 1], xN[TY][TX + 1], xT[TY][TX + 1];
   __shared__ F yJ[TY + 1][TX], yN[TY + 1][TX], yT[TY + 1][TX];
   __shared__ F sdl[2][G == 1 ? TX + 1 : 1];  // axisymmetric: centroid distances per R face
+  __shared__ F qH[PT ? QY : 1][PT ? QX : 1];  // temperature field: <H>_k of the one-cell halo
+  const S* __restrict__ Hcs = static_cast<const S*>(v.Hc);
+  const S* __restrict__ Gcs = static_cast<const S*>(v.Gc);
   __shared__ double red[NT / 32];
 
   const S* __restrict__ Jin = static_cast<const S*>(v.J);
@@ -413,6 +416,14 @@ __device__ __forceinline__ void transport_tile(const DeviceView& v, int x0, int 
     const long long base = static_cast<long long>(k) * nc;
     const double Hk_d = v.t_H[k];
     const F Hk = F(Hk_d);
+    if constexpr (PT) {  // <H>_k of the one-cell halo at each cell's temperature
+      for (int idx = tid; idx < QX * QY; idx += NT) {
+        const int lx = idx % QX, ly = idx / QX;
+        bool fxg, fyg;
+        const int ix = ghost<G>(x0 + lx - 1, nx, fxg), iy = ghost<G>(y0 + ly - 1, ny, fyg);
+        qH[ly][lx] = F(Hcs[base + static_cast<long long>(iy) * nx + ix]);
+      }
+    }
     // phase A: halo tile of the state and its primitives
     for (int idx = tid; idx < SX * SY; idx += NT) {
       const int lx = idx % SX, ly = idx / SX;
@@ -443,8 +454,8 @@ __device__ __forceinline__ void transport_tile(const DeviceView& v, int x0, int 
       if (f < NXF) {
         const int fi = f % (TX + 1), fj = f / (TX + 1);
         const int r = fj + 2;
-        const F aF0 = qA[fj + 1][fi] * Hk + qR[fj + 1][fi] * kF_f;
-        const F aF1 = qA[fj + 1][fi + 1] * Hk + qR[fj + 1][fi + 1] * kF_f;
+        const F aF0 = qA[fj + 1][fi] * (PT ? qH[fj + 1][fi] : Hk) + qR[fj + 1][fi] * kF_f;
+        const F aF1 = qA[fj + 1][fi + 1] * (PT ? qH[fj + 1][fi + 1] : Hk) + qR[fj + 1][fi + 1] * kF_f;
         F dl0 = half_dx, dl1 = half_dx;
         if constexpr (G == 1) {
           dl0 = sdl[0][fi];
@@ -458,8 +469,8 @@ __device__ __forceinline__ void transport_tile(const DeviceView& v, int x0, int 
         const int g = f - NXF;
         const int fi = g % TX, fj = g / TX;
         const int cc = fi + 2;
-        const F aF0 = qA[fj][fi + 1] * Hk + qR[fj][fi + 1] * kF_f;
-        const F aF1 = qA[fj + 1][fi + 1] * Hk + qR[fj + 1][fi + 1] * kF_f;
+        const F aF0 = qA[fj][fi + 1] * (PT ? qH[fj][fi + 1] : Hk) + qR[fj][fi + 1] * kF_f;
+        const F aF1 = qA[fj + 1][fi + 1] * (PT ? qH[fj + 1][fi + 1] : Hk) + qR[fj + 1][fi + 1] * kF_f;
         face_flux<F>(sJ[fj][cc], sfy[fj][cc], sfx[fj][cc], sJ[fj + 1][cc], sfy[fj + 1][cc],
                      sfx[fj + 1][cc], sJ[fj + 2][cc], sfy[fj + 2][cc], sfx[fj + 2][cc],
                      sJ[fj + 3][cc], sfy[fj + 3][cc], sfx[fj + 3][cc], aF0, aF1, qUy[fj][fi + 1],
@@ -494,13 +505,13 @@ __device__ __forceinline__ void transport_tile(const DeviceView& v, int x0, int 
         Hx1 = Hx - cdt_f * (divHx / dx);
         Hy1 = Hy - cdt_f * (divHy / dx);
       }
-      const I aH = alpha_c * I(Hk_d);
+      const I aH = alpha_c * (PT ? I(Hcs[base + cell]) : I(Hk_d));
       const I kap = rho_c * kabs + pd_c * aH;
       const I aF = aH + rho_c * kF;
       // j_k = L w_k / (4 pi V dnu_k): formed in FP64 (L ~ 1e39 erg/s and
       // w_k / (4 pi V dnu_k) ~ 1e-58 are both outside the FP32 range); on the
       // axisymmetric grid lum already holds L / (2 pi Vol) and gem_k has V = 1
-      const I js = (lum_d != 0.0) ? I(lum_d * v.t_gem[k]) : I(0);
+      const I js = (lum_d != 0.0) ? I(lum_d * (PT ? double(Gcs[base + cell]) : v.t_gem[k])) : I(0);
       const I J2 = (I(J1) + cdt * js) / (I(1) + cdt * kap);
       const I Hx2 = I(Hx1) / (I(1) + cdt * aF);
       const I Hy2 = I(Hy1) / (I(1) + cdt * aF);
@@ -559,9 +570,9 @@ __device__ __forceinline__ void transport_tile(const DeviceView& v, int x0, int 
 }
 
 
-template <class P, int G>
+template <class P, int G, bool PT>
 __global__ void __launch_bounds__(kTileX* kTileY) transport_kernel(DeviceView v) {
-  transport_tile<P, G>(v, blockIdx.x * kTileX, blockIdx.y * kTileY, blockIdx.y * gridDim.x + blockIdx.x);
+  transport_tile<P, G, PT>(v, blockIdx.x * kTileX, blockIdx.y * kTileY, blockIdx.y * gridDim.x + blockIdx.x);
 }
 
 // ------------------------------------------------------- FP32 fast-path math
@@ -666,7 +677,7 @@ __device__ __forceinline__ void face_flux_f32(float Jm, float nm, float tm, floa
 // distances) of a thread's faces do not depend on the bin and stay in
 // registers.  The implicit source step runs in type I (FP64 for LYM1_MIXED,
 // FP32 for LYM1_MIXED_FAST).
-template <class P, int G>
+template <class P, int G, bool PT>
 __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, int y0, int blk) {
   using I = typename P::I;
   constexpr int TX = kTileX, TY = kTileY, SX = TX + 4, SY = TY + 4;
@@ -690,6 +701,9 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
   float* __restrict__ Jout = static_cast<float*>(v.Jo);
   float* __restrict__ Hxout = static_cast<float*>(v.Hxo);
   float* __restrict__ Hyout = static_cast<float*>(v.Hyo);
+  // temperature field: <H>_k and gem_k / gmax per [k][cell]
+  const float* __restrict__ Hcf = static_cast<const float*>(v.Hc);
+  const float* __restrict__ Gcf = static_cast<const float*>(v.Gc);
 
   const int nx = v.nx, ny = v.ny, nb = v.nb;
   const long long nc = v.nc;
@@ -796,16 +810,22 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
   // emissivity j_k = (L_cell gem_max) (gem_k / gem_max): both factors lie in
   // the FP32 range, unlike L_cell (~1e39 erg/s) and gem_k (~1e-58) alone
   const bool src = lum_d != 0.0;
-  const float jsc = float(lum_d * v.gem_max);
+  const double gmax_c = PT ? (valid ? v.gmaxc[cell] : 1.0) : v.gem_max;
+  const float jsc = float(lum_d * gmax_c);
   const bool bnd = valid && (G == 1 ? (gx == nx - 1 || gy == ny - 1)
                                      : (gx == 0 || gx == nx - 1 || gy == 0 || gy == ny - 1));
 
   float pJ0 = Jin[off0], pX0 = Hxin[off0], pY0 = Hyin[off0];
   float pJ1 = 0.f, pX1 = 0.f, pY1 = 0.f;
+  float pH0 = 0.f, pH1 = 0.f;  // <H>_k of the halo entries (temperature field)
   if (has1) {
     pJ1 = Jin[off1];
     pX1 = Hxin[off1];
     pY1 = Hyin[off1];
+  }
+  if constexpr (PT) {
+    pH0 = Hcf[off0];
+    if (has1) pH1 = Hcf[off1];
   }
   long long base = 0;  // k * nc
   for (int k = 0; k < nb; ++k) {
@@ -822,12 +842,12 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
         Y1 *= sy1;
       }
       const float r0 = J0 > kTinyJ ? frcp(J0) : 0.0f;
-      sq[b][ey0][ex0] = make_float4(J0, X0 * r0, Y0 * r0, al0 * Hk + rk0);
+      sq[b][ey0][ex0] = make_float4(J0, X0 * r0, Y0 * r0, al0 * (PT ? pH0 : Hk) + rk0);
       sHx[b][ey0][ex0] = X0;
       sHy[b][ey0][ex0] = Y0;
       if (has1) {
         const float r1 = J1 > kTinyJ ? frcp(J1) : 0.0f;
-        sq[b][ey1][ex1] = make_float4(J1, X1 * r1, Y1 * r1, al1 * Hk + rk1);
+        sq[b][ey1][ex1] = make_float4(J1, X1 * r1, Y1 * r1, al1 * (PT ? pH1 : Hk) + rk1);
         sHx[b][ey1][ex1] = X1;
         sHy[b][ey1][ex1] = Y1;
       }
@@ -841,6 +861,10 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
         pJ1 = Jin[nbase + off1];
         pX1 = Hxin[nbase + off1];
         pY1 = Hyin[nbase + off1];
+      }
+      if constexpr (PT) {
+        pH0 = Hcf[nbase + off0];
+        if (has1) pH1 = Hcf[nbase + off1];
       }
     }
     __syncthreads();
@@ -892,19 +916,19 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
       const float Hy1 = Hy - cdt_dx * divHy;
       I aH, dnu;
       if constexpr (sizeof(I) == 8) {
-        aH = alpha_c * v.t_H[k];
+        aH = alpha_c * (PT ? double(Hcf[base + cell]) : v.t_H[k]);
         dnu = v.t_dnu[k];
       } else {
-        aH = alpha_c * Hk;
+        aH = alpha_c * (PT ? Hcf[base + cell] : Hk);
         dnu = tD[k];
       }
       const I kap = rho_c * kabs + pd_c * aH;
       const I aF = aH + rho_c * kF;
       I js;
       if constexpr (sizeof(I) == 8)
-        js = src ? lum_d * v.t_gem[k] : 0.0;
+        js = src ? lum_d * (PT ? gmax_c * double(Gcf[base + cell]) : v.t_gem[k]) : 0.0;
       else
-        js = src ? jsc * tG[k] : 0.0f;
+        js = src ? jsc * (PT ? Gcf[base + cell] : tG[k]) : 0.0f;
       I J2, Hx2, Hy2;
       if constexpr (sizeof(I) == 8) {
         J2 = (I(J1) + cdt * js) / (I(1) + cdt * kap);
@@ -978,9 +1002,9 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
   }
 }
 
-template <class P, int G>
+template <class P, int G, bool PT>
 __global__ void __launch_bounds__(kTileX* kTileY, 3) transport_kernel_f32(DeviceView v) {
-  transport_tile_f32<P, G>(v, blockIdx.x * kTileX, blockIdx.y * kTileY,
+  transport_tile_f32<P, G, PT>(v, blockIdx.x * kTileX, blockIdx.y * kTileY,
                            blockIdx.y * gridDim.x + blockIdx.x);
 }
 
@@ -991,8 +1015,8 @@ template <class P, int G, class T>
 __device__ __forceinline__ void freq_coef(typename P::F Jc, typename P::F Hxc, typename P::F Hyc,
                                           typename P::F Kc, typename P::F gxx,
                                           typename P::F gyy, typename P::F gsh,
-                                          typename P::F gphi, const T* tH,
-                                          const T* tR, const T* tn, const T* th, int k,
+                                          typename P::F gphi, typename P::F Hk,
+                                          typename P::F Rk, const T* tn, const T* th, int k,
                                           typename P::F& Pk, typename P::F& ak,
                                           typename P::F& ek) {
   using F = typename P::F;
@@ -1004,9 +1028,9 @@ __device__ __forceinline__ void freq_coef(typename P::F Jc, typename P::F Hxc, t
     closure_f32(fx, fy, Dxx, Dxy, Dyy, Dpp);
     float DdU = (Dxx * gxx + Dyy * gyy) + Dxy * gsh;
     if constexpr (G == 1) DdU = DdU + Dpp * gphi;
-    const float K = Kc * tH[k];
+    const float K = Kc * Hk;
     const float rK = frcp(K);
-    const float C = K * tR[k] + tn[k] * DdU;
+    const float C = K * Rk + tn[k] * DdU;
     const float half = th[k];
     ak = half * rK;
     Pk = C * ak;
@@ -1028,8 +1052,8 @@ __device__ __forceinline__ void freq_coef(typename P::F Jc, typename P::F Hxc, t
     closure(fx, fy, Dxx, Dxy, Dyy, Dpp);
     F DdU = (Dxx * gxx + Dyy * gyy) + Dxy * gsh;
     if constexpr (G == 1) DdU = DdU + Dpp * gphi;  // D_phiphi <u_R / R>
-    const F K = Kc * F(tH[k]);
-    const F C = K * F(tR[k]) + F(tn[k]) * DdU;
+    const F K = Kc * Hk;
+    const F C = K * Rk + F(tn[k]) * DdU;
     const F half = F(th[k]);
     Pk = (C * half) / K;
     ak = half / K;
@@ -1038,7 +1062,7 @@ __device__ __forceinline__ void freq_coef(typename P::F Jc, typename P::F Hxc, t
   }
 }
 
-template <class P, int G>
+template <class P, int G, bool PT>
 __device__ __forceinline__ void freq_block(const DeviceView& v, int blk) {
   using S = typename P::S;
   using F = typename P::F;
@@ -1102,16 +1126,34 @@ __device__ __forceinline__ void freq_block(const DeviceView& v, int blk) {
   if (cell < nc) {
     const double alpha = v.alpha[cell];
     if (v.freq_step && alpha > 0.0) {
-      const F Kc = F(v.Kc * alpha);
+      const F Kc = PT ? F(v.Kcc[cell] * alpha) : F(v.Kc * alpha);
       const F gxx = F(v.gxx[cell]), gyy = F(v.gyy[cell]), gsh = F(v.gsh[cell]);
       const F gphi = G == 1 ? F(v.gphi[cell]) : F(0);
+      // <H>_k and the recoil factor R_k of bin kk: per-bin tables, or the
+      // cell's own under a temperature field
+      const S* __restrict__ Hcs = static_cast<const S*>(v.Hc);
+      const double hkT_c = PT ? v.hkTc[cell] : 0.0;
+      auto HR = [&](int kk, F& Hk, F& Rk) {
+        if constexpr (PT) {
+          Hk = F(Hcs[static_cast<long long>(kk) * nc + cell]);
+          if constexpr (sizeof(F) == 8)
+            Rk = F(hkT_c - v.t_2nu[kk]);
+          else
+            Rk = float(hkT_c) - v.f_2nu[kk];
+        } else {
+          Hk = tH[kk];
+          Rk = tR[kk];
+        }
+      };
+      F H0, R0;
+      HR(0, H0, R0);
       const I cdt = I(v.cdt);
       const float rcdt = float(1.0 / v.cdt);
       (void)rcdt;
       F P0, a0, e0, P1 = F(0), a1 = F(0), e1 = F(0);
       I Jin0 = I(Jin[cell]);
       I Jin1 = 0;
-      freq_coef<P, G>(F(Jin[cell]), F(Hxin[cell]), F(Hyin[cell]), Kc, gxx, gyy, gsh, gphi, tH, tR,
+      freq_coef<P, G>(F(Jin[cell]), F(Hxin[cell]), F(Hyin[cell]), Kc, gxx, gyy, gsh, gphi, H0, R0,
                       tn, th, 0, P0, a0, e0);
       I qprev = 0, gprev = 0, Bprev = 0, Aprev = 0;
       // two-deep software pipeline: (nJ, nX, nY) hold bin k+1, loads for k+2 are in flight
@@ -1133,7 +1175,9 @@ __device__ __forceinline__ void freq_block(const DeviceView& v, int blk) {
             nY = Hyin[o2];
           }
           Jin1 = I(Jr);
-          freq_coef<P, G>(F(Jr), F(Xr), F(Yr), Kc, gxx, gyy, gsh, gphi, tH, tR, tn, th, k + 1, P1,
+          F H1, R1;
+          HR(k + 1, H1, R1);
+          freq_coef<P, G>(F(Jr), F(Xr), F(Yr), Kc, gxx, gyy, gsh, gphi, H1, R1, tn, th, k + 1, P1,
                           a1, e1);
           const F d1 = (-P0 > F(0)) ? -P0 : F(0);
           const F d2 = (P1 > F(0)) ? P1 : F(0);
@@ -1303,7 +1347,7 @@ __device__ __forceinline__ void fence_mbar_init() {
 // streamed through the ring (cell count a multiple of 4, so that every row
 // segment starts on a 16-byte boundary and is a whole number of 16 bytes).
 // Same arithmetic, in the same order, as freq_block.
-template <class P, int G>
+template <class P, int G, bool PT>
 __device__ __forceinline__ void freq_block_bulk(const DeviceView& v, int blk) {
   using F = typename P::F;
   using I = typename P::I;
@@ -1359,7 +1403,10 @@ __device__ __forceinline__ void freq_block_bulk(const DeviceView& v, int blk) {
   const bool valid = tid < ncell;
   const double alpha = valid ? v.alpha[cell] : 0.0;
   const bool act = valid && alpha > 0.0;
-  const F Kc = F(v.Kc * alpha);
+  const F Kc = PT ? F((valid ? v.Kcc[cell] : 0.0) * alpha) : F(v.Kc * alpha);
+  // temperature field: <H>_k rides the forward ring as a fourth row
+  const float* __restrict__ Hcf = static_cast<const float*>(v.Hc);
+  const float hkT_c = PT ? float(valid ? v.hkTc[cell] : 0.0) : 0.0f;
   const F gxx = valid ? F(v.gxx[cell]) : F(0), gyy = valid ? F(v.gyy[cell]) : F(0),
           gsh = valid ? F(v.gsh[cell]) : F(0);
   F gphi = F(0);
@@ -1377,10 +1424,11 @@ __device__ __forceinline__ void freq_block_bulk(const DeviceView& v, int blk) {
   auto issue_fwd = [&](int k) {
     const int s = k % D;
     const long long off = static_cast<long long>(k) * nc + c0;
-    mbar_expect_tx(&barF[s], 3u * rowb);
+    mbar_expect_tx(&barF[s], (PT ? 4u : 3u) * rowb);
     bulk_load(&ring[s][0][0], Jin + off, rowb, &barF[s]);
     bulk_load(&ring[s][1][0], Hxin + off, rowb, &barF[s]);
     bulk_load(&ring[s][2][0], Hyin + off, rowb, &barF[s]);
+    if constexpr (PT) bulk_load(&ring[s][3][0], Hcf + off, rowb, &barF[s]);
   };
   auto issue_bwd = [&](int j) {  // j-th bin from the top
     const int s = j % D, k = nb - 1 - j;
@@ -1426,7 +1474,9 @@ __device__ __forceinline__ void freq_block_bulk(const DeviceView& v, int blk) {
     if (act) {
       const F Jc = F(ring[s][0][tid]), Xc = F(ring[s][1][tid]), Yc = F(ring[s][2][tid]);
       F Pk, ak, ek;
-      freq_coef<P, G>(Jc, Xc, Yc, Kc, gxx, gyy, gsh, gphi, tH, tR, tn, th, k, Pk, ak, ek);
+      const F Hk = PT ? F(ring[s][3][tid]) : F(tH[k]);
+      const F Rk = PT ? F(hkT_c - v.f_2nu[k]) : F(tR[k]);
+      freq_coef<P, G>(Jc, Xc, Yc, Kc, gxx, gyy, gsh, gphi, Hk, Rk, tn, th, k, Pk, ak, ek);
       if (k > 0) {
         const F d1 = (-Pp > F(0)) ? -Pp : F(0);
         const F d2 = (Pk > F(0)) ? Pk : F(0);
@@ -1555,158 +1605,164 @@ __device__ __forceinline__ void freq_block_bulk(const DeviceView& v, int blk) {
 
 // FP32 state with a cell count that is a multiple of 4 takes the bulk-copy
 // pipeline; everything else the register-prefetch sweep
-template <class P, int G>
+template <class P, int G, bool PT>
 __device__ __forceinline__ void freq_dispatch(const DeviceView& v, int blk) {
   if constexpr (sizeof(typename P::S) == 4) {
     if ((v.nc & 3) == 0) {
-      freq_block_bulk<P, G>(v, blk);
+      freq_block_bulk<P, G, PT>(v, blk);
       return;
     }
   }
-  freq_block<P, G>(v, blk);
+  freq_block<P, G, PT>(v, blk);
 }
 
 // FP32 state: at most 64 registers so that 8 blocks (32 warps) per SM keep
 // enough loads in flight for the latency-bound bin sweeps
-template <class P, int G>
+template <class P, int G, bool PT>
 __global__ void __launch_bounds__(kFreqThreads, sizeof(typename P::S) == 4 ? 8 : 1)
     freq_kernel(DeviceView v) {
-  freq_dispatch<P, G>(v, blockIdx.x);
+  freq_dispatch<P, G, PT>(v, blockIdx.x);
 }
 
 // ------------------------------------------------------------ batched launches
 // Persistent kernels over a work list that spans several contexts (clouds of
-// different sizes, one geometry): each item names a context and a tile
-// (transport) or a block of cells (frequency step); blocks walk the list with
-// a grid stride.
+// different sizes, one geometry and temperature mode): each item names a
+// context and a tile (transport) or a block of cells (frequency step); blocks
+// walk the list with a grid stride.
 struct BatchItem {
   int ctx, x0, y0, blk;
 };
 
-template <class P, int G>
+template <class P, int G, bool PT>
 __global__ void __launch_bounds__(kTileX* kTileY) transport_batched(const DeviceView* views,
                                                                     const BatchItem* items, int n) {
   for (int i = blockIdx.x; i < n; i += gridDim.x) {
     const BatchItem it = items[i];
     const DeviceView v = views[it.ctx];
-    transport_tile<P, G>(v, it.x0, it.y0, it.blk);
+    transport_tile<P, G, PT>(v, it.x0, it.y0, it.blk);
     __syncthreads();
   }
 }
 
-template <class P, int G>
+template <class P, int G, bool PT>
 __global__ void __launch_bounds__(kTileX* kTileY, 3) transport_batched_f32(const DeviceView* views,
                                                                            const BatchItem* items,
                                                                            int n) {
   for (int i = blockIdx.x; i < n; i += gridDim.x) {
     const BatchItem it = items[i];
     const DeviceView v = views[it.ctx];
-    transport_tile_f32<P, G>(v, it.x0, it.y0, it.blk);
+    transport_tile_f32<P, G, PT>(v, it.x0, it.y0, it.blk);
     __syncthreads();
   }
 }
 
-template <class P, int G>
+template <class P, int G, bool PT>
 __global__ void __launch_bounds__(kFreqThreads, sizeof(typename P::S) == 4 ? 8 : 1)
     freq_batched(const DeviceView* views, const BatchItem* items, int n) {
   for (int i = blockIdx.x; i < n; i += gridDim.x) {
     const BatchItem it = items[i];
     const DeviceView v = views[it.ctx];
-    freq_dispatch<P, G>(v, it.blk);
+    freq_dispatch<P, G, PT>(v, it.blk);
     __syncthreads();
   }
 }
 
-template <class P, int G>
+template <class P, int G, bool PT>
 int launch_transport_batched_g(const DeviceView* views, const BatchItem* items, int n, int grid,
                                int nb_max, cudaStream_t st) {
   if constexpr (sizeof(typename P::S) == 4) {
     const size_t smem = sizeof(float) * 4 * static_cast<size_t>(nb_max);
-    transport_batched_f32<P, G><<<grid, dim3(kTileX, kTileY), smem, st>>>(views, items, n);
+    transport_batched_f32<P, G, PT><<<grid, dim3(kTileX, kTileY), smem, st>>>(views, items, n);
   } else {
-    transport_batched<P, G><<<grid, dim3(kTileX, kTileY), 0, st>>>(views, items, n);
+    transport_batched<P, G, PT><<<grid, dim3(kTileX, kTileY), 0, st>>>(views, items, n);
   }
   return static_cast<int>(cudaGetLastError());
 }
 
-template <class P, int G>
+template <class P, int G, bool PT>
 int launch_freq_batched_g(const DeviceView* views, const BatchItem* items, int n, int grid,
                           int nb_max, cudaStream_t st) {
   const size_t smem = sizeof(double) * 7 * static_cast<size_t>(nb_max);
-  freq_batched<P, G><<<grid, kFreqThreads, smem, st>>>(views, items, n);
+  freq_batched<P, G, PT><<<grid, kFreqThreads, smem, st>>>(views, items, n);
   return static_cast<int>(cudaGetLastError());
 }
 
+// (geometry, temperature mode) -> template instance
+#define LYM1_GPT(F_, ...)                                              \
+  (geometry == 1 ? (pt ? F_<P, 1, true>(__VA_ARGS__) : F_<P, 1, false>(__VA_ARGS__)) \
+                 : (pt ? F_<P, 0, true>(__VA_ARGS__) : F_<P, 0, false>(__VA_ARGS__)))
+
 template <class P>
-int launch_transport_batched_t(int geometry, const DeviceView* views, const BatchItem* items, int n,
-                               int grid, int nb_max, cudaStream_t st) {
-  return geometry == 1 ? launch_transport_batched_g<P, 1>(views, items, n, grid, nb_max, st)
-                       : launch_transport_batched_g<P, 0>(views, items, n, grid, nb_max, st);
+int launch_transport_batched_t(int geometry, int pt, const DeviceView* views, const BatchItem* items,
+                               int n, int grid, int nb_max, cudaStream_t st) {
+  return LYM1_GPT(launch_transport_batched_g, views, items, n, grid, nb_max, st);
 }
 
 template <class P>
-int launch_freq_batched_t(int geometry, const DeviceView* views, const BatchItem* items, int n,
-                          int grid, int nb_max, cudaStream_t st) {
-  return geometry == 1 ? launch_freq_batched_g<P, 1>(views, items, n, grid, nb_max, st)
-                       : launch_freq_batched_g<P, 0>(views, items, n, grid, nb_max, st);
+int launch_freq_batched_t(int geometry, int pt, const DeviceView* views, const BatchItem* items,
+                          int n, int grid, int nb_max, cudaStream_t st) {
+  return LYM1_GPT(launch_freq_batched_g, views, items, n, grid, nb_max, st);
 }
 
-template <class P, int G>
+template <class P, int G, bool PT>
 int max_resident_transport_g() {
   int nblk = 0;
   if constexpr (sizeof(typename P::S) == 4)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nblk, transport_batched_f32<P, G>,
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nblk, transport_batched_f32<P, G, PT>,
                                                   kTileX * kTileY, sizeof(float) * 4 * 194);
   else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nblk, transport_batched<P, G>, kTileX * kTileY, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nblk, transport_batched<P, G, PT>,
+                                                  kTileX * kTileY, 0);
   return nblk < 1 ? 1 : nblk;
 }
 
-template <class P, int G>
+template <class P, int G, bool PT>
 int max_resident_freq_g() {
   int nblk = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nblk, freq_batched<P, G>, kFreqThreads,
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nblk, freq_batched<P, G, PT>, kFreqThreads,
                                                 sizeof(double) * 7 * 194);
   return nblk < 1 ? 1 : nblk;
 }
 
 template <class P>
-int max_resident_transport(int geometry) {
-  return geometry == 1 ? max_resident_transport_g<P, 1>() : max_resident_transport_g<P, 0>();
+int max_resident_transport(int geometry, int pt) {
+  return LYM1_GPT(max_resident_transport_g);
 }
 
 template <class P>
-int max_resident_freq(int geometry) {
-  return geometry == 1 ? max_resident_freq_g<P, 1>() : max_resident_freq_g<P, 0>();
+int max_resident_freq(int geometry, int pt) {
+  return LYM1_GPT(max_resident_freq_g);
 }
 
-template <class P, int G>
+template <class P, int G, bool PT>
 int launch_transport_g(const DeviceView& v, cudaStream_t st) {
   dim3 grid((v.nx + kTileX - 1) / kTileX, (v.ny + kTileY - 1) / kTileY);
   if constexpr (sizeof(typename P::S) == 4) {
     const size_t smem = sizeof(float) * 4 * static_cast<size_t>(v.nb);
-    transport_kernel_f32<P, G><<<grid, dim3(kTileX, kTileY), smem, st>>>(v);
+    transport_kernel_f32<P, G, PT><<<grid, dim3(kTileX, kTileY), smem, st>>>(v);
   } else {
-    transport_kernel<P, G><<<grid, dim3(kTileX, kTileY), 0, st>>>(v);
+    transport_kernel<P, G, PT><<<grid, dim3(kTileX, kTileY), 0, st>>>(v);
   }
   return static_cast<int>(cudaGetLastError());
 }
 
-template <class P, int G>
+template <class P, int G, bool PT>
 int launch_freq_g(const DeviceView& v, cudaStream_t st) {
   const size_t smem = sizeof(double) * 7 * static_cast<size_t>(v.nb);
-  freq_kernel<P, G><<<freq_blocks(v.nc), kFreqThreads, smem, st>>>(v);
+  freq_kernel<P, G, PT><<<freq_blocks(v.nc), kFreqThreads, smem, st>>>(v);
   return static_cast<int>(cudaGetLastError());
 }
 
 template <class P>
 int launch_transport_t(const DeviceView& v, cudaStream_t st) {
-  return v.geometry == 1 ? launch_transport_g<P, 1>(v, st) : launch_transport_g<P, 0>(v, st);
+  const int geometry = v.geometry, pt = v.pt;
+  return LYM1_GPT(launch_transport_g, v, st);
 }
 
 template <class P>
 int launch_freq_t(const DeviceView& v, cudaStream_t st) {
-  return v.geometry == 1 ? launch_freq_g<P, 1>(v, st) : launch_freq_g<P, 0>(v, st);
+  const int geometry = v.geometry, pt = v.pt;
+  return LYM1_GPT(launch_freq_g, v, st);
 }
 
 }  // namespace lym1

@@ -15,16 +15,17 @@ int launch_freq_det(const DeviceView& v, void* st) {
   return launch_freq_t<PolDet>(v, static_cast<cudaStream_t>(st));
 }
 
-int launch_batched_det(int kind, int geometry, const DeviceView* views, const void* items, int n,
-                       int grid, int nb_max, void* st) {
+int launch_batched_det(int kind, int geometry, int pt, const DeviceView* views, const void* items,
+                       int n, int grid, int nb_max, void* st) {
   const cudaStream_t s = static_cast<cudaStream_t>(st);
   const BatchItem* it = static_cast<const BatchItem*>(items);
-  if (kind == 0) return launch_transport_batched_t<PolDet>(geometry, views, it, n, grid, nb_max, s);
-  return launch_freq_batched_t<PolDet>(geometry, views, it, n, grid, nb_max, s);
+  if (kind == 0) return launch_transport_batched_t<PolDet>(geometry, pt, views, it, n, grid, nb_max, s);
+  return launch_freq_batched_t<PolDet>(geometry, pt, views, it, n, grid, nb_max, s);
 }
 
-int resident_blocks_det(int kind, int geometry) {
-  return kind == 0 ? max_resident_transport<PolDet>(geometry) : max_resident_freq<PolDet>(geometry);
+int resident_blocks_det(int kind, int geometry, int pt) {
+  return kind == 0 ? max_resident_transport<PolDet>(geometry, pt)
+                   : max_resident_freq<PolDet>(geometry, pt);
 }
 
 
@@ -34,15 +35,15 @@ int resident_blocks_det(int kind, int geometry) {
 // first column (row) with u_R (u_Z) negated; <u_R / R> from the mean of the
 // two R-face velocities over the mean face radius.
 __global__ void setup_statics_kernel(const double* n_hi, const double* ux, const double* uy,
-                                     double sigma0, int nx, int ny, double dx, double* alpha,
-                                     double* gxx, double* gyy, double* gsh, int geometry,
-                                     double* gphi) {
+                                     double sigma0, const double* sigma0c, int nx, int ny,
+                                     double dx, double* alpha, double* gxx, double* gyy,
+                                     double* gsh, int geometry, double* gphi) {
   const long long id = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
   const long long nc = static_cast<long long>(nx) * ny;
   if (id >= nc) return;
   const int i = static_cast<int>(id % nx), j = static_cast<int>(id / nx);
   const double h2 = 2.0 * dx;
-  alpha[id] = n_hi[id] * sigma0;
+  alpha[id] = n_hi[id] * (sigma0c ? sigma0c[id] : sigma0);
   if (geometry == 1) {
     bool fm, fp, gm, gp;
     const int im = ghost<1>(i - 1, nx, fm), ip = ghost<1>(i + 1, nx, fp);
@@ -72,12 +73,13 @@ __global__ void setup_statics_kernel(const double* n_hi, const double* ux, const
 }
 
 int launch_setup_statics(const double* n_hi, const double* ux, const double* uy, double sigma0,
-                         int nx, int ny, double dx, double* alpha, double* gxx, double* gyy,
-                         double* gsh, int geometry, double* gphi, void* st) {
+                         const double* sigma0c, int nx, int ny, double dx, double* alpha,
+                         double* gxx, double* gyy, double* gsh, int geometry, double* gphi,
+                         void* st) {
   const long long nc = static_cast<long long>(nx) * ny;
   const int blocks = static_cast<int>((nc + 255) / 256);
   setup_statics_kernel<<<blocks, 256, 0, static_cast<cudaStream_t>(st)>>>(
-      n_hi, ux, uy, sigma0, nx, ny, dx, alpha, gxx, gyy, gsh, geometry, gphi);
+      n_hi, ux, uy, sigma0, sigma0c, nx, ny, dx, alpha, gxx, gyy, gsh, geometry, gphi);
   return static_cast<int>(cudaGetLastError());
 }
 

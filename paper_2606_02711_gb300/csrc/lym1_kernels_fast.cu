@@ -28,29 +28,29 @@ int launch_freq_fast(int precision, const DeviceView& v, void* st) {
   }
 }
 
-int launch_batched_fast(int precision, int kind, int geometry, const DeviceView* views,
+int launch_batched_fast(int precision, int kind, int geometry, int pt, const DeviceView* views,
                         const void* items, int n, int grid, int nb_max, void* st) {
   const cudaStream_t s = static_cast<cudaStream_t>(st);
   const BatchItem* it = static_cast<const BatchItem*>(items);
   switch (precision * 2 + kind) {
-    case 2: return launch_transport_batched_t<PolF64>(geometry, views, it, n, grid, nb_max, s);
-    case 3: return launch_freq_batched_t<PolF64>(geometry, views, it, n, grid, nb_max, s);
-    case 4: return launch_transport_batched_t<PolMix>(geometry, views, it, n, grid, nb_max, s);
-    case 5: return launch_freq_batched_t<PolMix>(geometry, views, it, n, grid, nb_max, s);
-    case 6: return launch_transport_batched_t<PolMixFast>(geometry, views, it, n, grid, nb_max, s);
-    case 7: return launch_freq_batched_t<PolMixFast>(geometry, views, it, n, grid, nb_max, s);
+    case 2: return launch_transport_batched_t<PolF64>(geometry, pt, views, it, n, grid, nb_max, s);
+    case 3: return launch_freq_batched_t<PolF64>(geometry, pt, views, it, n, grid, nb_max, s);
+    case 4: return launch_transport_batched_t<PolMix>(geometry, pt, views, it, n, grid, nb_max, s);
+    case 5: return launch_freq_batched_t<PolMix>(geometry, pt, views, it, n, grid, nb_max, s);
+    case 6: return launch_transport_batched_t<PolMixFast>(geometry, pt, views, it, n, grid, nb_max, s);
+    case 7: return launch_freq_batched_t<PolMixFast>(geometry, pt, views, it, n, grid, nb_max, s);
     default: return static_cast<int>(cudaErrorInvalidValue);
   }
 }
 
-int resident_blocks_fast(int precision, int kind, int geometry) {
+int resident_blocks_fast(int precision, int kind, int geometry, int pt) {
   switch (precision * 2 + kind) {
-    case 2: return max_resident_transport<PolF64>(geometry);
-    case 3: return max_resident_freq<PolF64>(geometry);
-    case 4: return max_resident_transport<PolMix>(geometry);
-    case 5: return max_resident_freq<PolMix>(geometry);
-    case 6: return max_resident_transport<PolMixFast>(geometry);
-    case 7: return max_resident_freq<PolMixFast>(geometry);
+    case 2: return max_resident_transport<PolF64>(geometry, pt);
+    case 3: return max_resident_freq<PolF64>(geometry, pt);
+    case 4: return max_resident_transport<PolMix>(geometry, pt);
+    case 5: return max_resident_freq<PolMix>(geometry, pt);
+    case 6: return max_resident_transport<PolMixFast>(geometry, pt);
+    case 7: return max_resident_freq<PolMixFast>(geometry, pt);
     default: return 1;
   }
 }

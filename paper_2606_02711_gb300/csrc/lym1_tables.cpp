@@ -11,6 +11,9 @@
 //   <H>_k, I(x, a) ............ App. A, bin-averaged Voigt profile and its integral
 //   phi_nu = H / sqrt(pi) ..... Sec. 2.1 step 2 (emission profile)
 //   bin centres = midpoints ... App. A footnote
+#include <cstring>
+#include <thread>
+#include <unordered_map>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -223,6 +226,61 @@ void build_cyl_tables(int nx, double dx, CylTables* g) {
   for (int i = 0; i <= nx; ++i) {
     g->fdlL[i] = static_cast<float>(g->dlL[i]);
     g->fdlR[i] = static_cast<float>(g->dlR[i]);
+  }
+}
+
+}  // namespace lym1
+
+namespace lym1 {
+
+void build_cell_tables(const std::vector<double>& edges, const double* T, long long nc, double dx,
+                       int gray, int recoil, int geometry, CellTables* out) {
+  // distinct temperatures, by bit pattern
+  std::unordered_map<unsigned long long, int> index;
+  std::vector<double> uniq;
+  std::vector<int> which(static_cast<size_t>(nc));
+  for (long long i = 0; i < nc; ++i) {
+    unsigned long long key;
+    std::memcpy(&key, &T[i], sizeof key);
+    auto it = index.find(key);
+    if (it == index.end()) {
+      it = index.emplace(key, static_cast<int>(uniq.size())).first;
+      uniq.push_back(T[i]);
+    }
+    which[static_cast<size_t>(i)] = it->second;
+  }
+  std::vector<BinTables> tabs(uniq.size());
+  unsigned nt = std::thread::hardware_concurrency();
+  if (nt < 1) nt = 1;
+  if (nt > uniq.size()) nt = static_cast<unsigned>(uniq.size());
+  std::vector<std::thread> pool;
+  for (unsigned t = 0; t < nt; ++t)
+    pool.emplace_back([&, t]() {
+      for (size_t u = t; u < uniq.size(); u += nt)
+        build_tables(edges, uniq[u], dx, gray, recoil, &tabs[u], geometry);
+    });
+  for (auto& th : pool) th.join();
+  const int nb = tabs.empty() ? 0 : tabs[0].nb;
+  const size_t n = static_cast<size_t>(nc);
+  out->H.assign(static_cast<size_t>(nb) * n, 0.0);
+  out->G.assign(static_cast<size_t>(nb) * n, 0.0);
+  out->sigma0.assign(n, 0.0);
+  out->hkT.assign(n, 0.0);
+  out->Kc.assign(n, 0.0);
+  out->gmax.assign(n, 0.0);
+  std::vector<double> gm(uniq.size(), 0.0);
+  for (size_t u = 0; u < uniq.size(); ++u)
+    for (double g : tabs[u].gem) gm[u] = std::max(gm[u], g);
+  for (size_t i = 0; i < n; ++i) {
+    const BinTables& t = tabs[static_cast<size_t>(which[i])];
+    for (int k = 0; k < nb; ++k) {
+      out->H[static_cast<size_t>(k) * n + i] = t.Havg[k];
+      out->G[static_cast<size_t>(k) * n + i] = t.gem[k];
+    }
+    out->sigma0[i] = t.lc.sigma0;
+    out->hkT[i] = t.hkT;
+    out->Kc[i] = 0.5 * (t.lc.dnu_D * t.lc.dnu_D);
+    out->gmax[i] = gm[static_cast<size_t>(which[i])] > 0.0 ? gm[static_cast<size_t>(which[i])] : 1.0;
   }
 }
 

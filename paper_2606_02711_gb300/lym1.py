@@ -45,7 +45,8 @@ class lym1_opacities(C.Structure):
     _fields_ = [("n_hi", _PD), ("rho_dust", _PD), ("p_d", _PD), ("ux", _PD), ("uy", _PD),
                 ("temp_K", C.c_double), ("kappa_abs", C.c_double), ("kappa_F", C.c_double),
                 ("c_tilde", C.c_double), ("cfl", C.c_double), ("recoil", C.c_int),
-                ("freq_step", C.c_int), ("precision", C.c_int), ("cuda_stream", C.c_void_p)]
+                ("freq_step", C.c_int), ("precision", C.c_int), ("cuda_stream", C.c_void_p),
+                ("temp_field", _PD)]
 
 
 class lym1_info(C.Structure):
@@ -169,7 +170,7 @@ class Context:
     def __init__(self, *, nx, ny, dx, n_hi, rho_d, p_d, ux, uy, T=1e4, kappa_abs=0.0,
                  kappa_F=0.0, c_tilde=0.0, cfl=0.0, recoil=True, freq_step=True, gray=False,
                  edges=None, q=0.0, T_min=0.0, precision=FP64_DET, stream=None, lum=None,
-                 geometry=0, bc=(0, 0, 0, 0)):
+                 geometry=0, bc=(0, 0, 0, 0), temp=None):
         keep = []
         if isinstance(precision, str):
             precision = PRECISIONS[precision]
@@ -190,7 +191,7 @@ class Context:
         op = lym1_opacities(field(n_hi), field(rho_d), field(p_d), field(ux), field(uy), float(T),
                             float(kappa_abs), float(kappa_F), float(c_tilde), float(cfl),
                             int(bool(recoil)), int(bool(freq_step)), int(precision),
-                            _stream_handle(stream))
+                            _stream_handle(stream), field(temp) if temp is not None else None)
         h = C.c_void_p()
         _check(lib().lym1_create(C.byref(g), C.byref(gr), C.byref(op), C.byref(h)), "lym1_create")
         self.handle = h
@@ -367,4 +368,5 @@ def from_cloud(cloud, precision=FP64_DET, stream=None, edges=None) -> Context:
                    kappa_F=cloud.kappa_F, c_tilde=cloud.c_tilde, cfl=cloud.cfl,
                    recoil=cloud.recoil, freq_step=cloud.freq_step, gray=cloud.gray, edges=edges,
                    precision=precision, stream=stream, lum=cloud.lum,
-                   geometry=getattr(cloud, "geometry", 0), bc=getattr(cloud, "bc", (0, 0, 0, 0)))
+                   geometry=getattr(cloud, "geometry", 0), bc=getattr(cloud, "bc", (0, 0, 0, 0)),
+                   temp=getattr(cloud, "temp", None))
