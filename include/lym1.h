@@ -303,6 +303,23 @@ int lym1_profile_read(lym1_ctx *ctx, lym1_profile *out, int reset);
 int lym1_energy_noalloc(const double *J, const double *dnu, int nb, long long nc, double dx_cm,
                         double *e_out, void *cuda_stream);
 
+/*
+ * Emergent spectrum (Sec. 4: the spectra of photons leaving the domain, Test 6
+ * at the outer R and Z boundaries; f_esc per bin).  lym1_spectrum_enable(ctx, 1)
+ * zeroes and starts the accumulation, over the following substeps, of the
+ * energy (erg) leaving through each outer boundary face in each bin: the
+ * per-face terms of the outflow bookkeeping of lym1_diagnostics.  Faces are
+ * ordered x- (by y), x+ (by y), y- (by x), y+ (by x) for geometry 0, and R outer
+ * (by Z), Z outer (by R) for geometry 1 (the axis and midplane are mirrors);
+ * the axisymmetric energies are those of the full rings.  (ctx, 0) stops it.
+ * Enable before adding the context to a lym1_batch.
+ * lym1_spectrum_read copies the [bin][face] array (nb x *n_faces doubles, host
+ * or device pointer; out = NULL only reports *n_faces).  LYM1_EINVAL if the
+ * spectrum was never enabled.
+ */
+int lym1_spectrum_enable(lym1_ctx *ctx, int on);
+int lym1_spectrum_read(lym1_ctx *ctx, double *out, int *n_faces);
+
 #ifdef __cplusplus
 }
 #endif

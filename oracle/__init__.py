@@ -104,6 +104,7 @@ def lib():
         L.lym1o_substep.argtypes = [C.c_void_p, _D, _PD, _PD, _PD, _PD, _PD, _PD, _PD, _PD,
                                     C.POINTER(Diag)]
         L.lym1o_set_threads.argtypes = [C.c_int]
+        L.lym1o_set_spectrum.argtypes = [C.c_void_p, _PD]
         L.lym1o_get_threads.restype = C.c_int
         _lib = L
     return _lib
@@ -249,6 +250,22 @@ class Oracle:
 
     def energy(self, J) -> float:
         return lib().lym1o_energy(self.ctx, _p(_f64(J)))
+
+    def n_faces(self) -> int:
+        """Outer faces of the emergent spectrum (x-, x+, y-, y+; R and Z outer
+        for the axisymmetric grid)."""
+        g = self.prob.geometry
+        return (self.nx + self.ny) if g == 1 else 2 * (self.nx + self.ny)
+
+    def spectrum_on(self, on: bool = True):
+        """Record the emergent spectrum (erg per [bin][face]) of each substep
+        in self.spectrum."""
+        if on:
+            self.spectrum = np.zeros((self.nb, self.n_faces()))
+            lib().lym1o_set_spectrum(self.ctx, _p(self.spectrum))
+        else:
+            lib().lym1o_set_spectrum(self.ctx, None)
+            self.spectrum = None
 
     def substep(self, J, Hx, Hy, dt=None):
         """Advance one substep; returns (J, Hx, Hy, fx, fy, diag dict)."""

@@ -375,6 +375,10 @@ typedef struct {
      * [k][cell] (A0 at the cell's T), the recoil factor h/(k_B T) and the
      * frequency-diffusion prefactor dnu_D^2/2 per cell; NULL otherwise */
     double *Hc, *Gc, *hkTc, *Kcc;
+    /* emergent spectrum of the last substep (NULL: off): escaping energy (erg)
+     * per [bin][outer face], faces ordered x- (j), x+ (j), y- (i), y+ (i) for
+     * geometry 0 and R outer (j), Z outer (i) for geometry 1 */
+    double *spec;
 } lym1o_ctx;
 
 static int o_cl(int i, int n) { return i < 0 ? 0 : (i >= n ? n - 1 : i); }
@@ -1022,13 +1026,26 @@ int lym1o_substep(const lym1o_ctx *c, double dt, const double *J, const double *
             o_kadd(&s_ab, c->dnu[k] * (cdt * (kap * Jo[kid])));
             o_kadd(&s_wk, c->dnu[k] * (cdt * (Wk[id] / O_C)));
         }
+        const int nf = 2 * (nx + ny);
         for (int j = 0; j < ny; ++j) {
-            o_kadd(&s_out, c->dnu[k] * (cdt * (-FJx[(size_t)j * (nx + 1)] / dx)));
-            o_kadd(&s_out, c->dnu[k] * (cdt * (FJx[(size_t)j * (nx + 1) + nx] / dx)));
+            double lo = c->dnu[k] * (cdt * (-FJx[(size_t)j * (nx + 1)] / dx));
+            double hi = c->dnu[k] * (cdt * (FJx[(size_t)j * (nx + 1) + nx] / dx));
+            o_kadd(&s_out, lo);
+            o_kadd(&s_out, hi);
+            if (c->spec) {
+                c->spec[(size_t)k * nf + j] = eunit * lo;
+                c->spec[(size_t)k * nf + ny + j] = eunit * hi;
+            }
         }
         for (int i = 0; i < nx; ++i) {
-            o_kadd(&s_out, c->dnu[k] * (cdt * (-FJy[i] / dx)));
-            o_kadd(&s_out, c->dnu[k] * (cdt * (FJy[(size_t)ny * nx + i] / dx)));
+            double lo = c->dnu[k] * (cdt * (-FJy[i] / dx));
+            double hi = c->dnu[k] * (cdt * (FJy[(size_t)ny * nx + i] / dx));
+            o_kadd(&s_out, lo);
+            o_kadd(&s_out, hi);
+            if (c->spec) {
+                c->spec[(size_t)k * nf + 2 * ny + i] = eunit * lo;
+                c->spec[(size_t)k * nf + 2 * ny + nx + i] = eunit * hi;
+            }
         }
 #undef AF
     }
@@ -1257,10 +1274,17 @@ int lym1o_substep_cyl(const lym1o_ctx *c, double dt, const double *J, const doub
             o_kadd(&s_wk, c->V2pi[i] * (c->dnu[k] * (cdt * (Wk[id] / O_C))));
         }
         /* outflow through the outer R and Z faces (the axis and midplane are mirrors) */
-        for (int j = 0; j < ny; ++j)
-            o_kadd(&s_out, (2.0 * O_PI) * (c->AR[nx] * (c->dnu[k] * (cdt * FJx[(size_t)j * (nx + 1) + nx]))));
-        for (int i = 0; i < nx; ++i)
-            o_kadd(&s_out, (2.0 * O_PI) * (c->AZ[i] * (c->dnu[k] * (cdt * FJy[(size_t)ny * nx + i]))));
+        const int nf = nx + ny;
+        for (int j = 0; j < ny; ++j) {
+            double o = (2.0 * O_PI) * (c->AR[nx] * (c->dnu[k] * (cdt * FJx[(size_t)j * (nx + 1) + nx])));
+            o_kadd(&s_out, o);
+            if (c->spec) c->spec[(size_t)k * nf + j] = ((4.0 * O_PI) / O_C) * o;
+        }
+        for (int i = 0; i < nx; ++i) {
+            double o = (2.0 * O_PI) * (c->AZ[i] * (c->dnu[k] * (cdt * FJy[(size_t)ny * nx + i])));
+            o_kadd(&s_out, o);
+            if (c->spec) c->spec[(size_t)k * nf + ny + i] = ((4.0 * O_PI) / O_C) * o;
+        }
 #undef AFC
     }
     const double fcoef = (4.0 * O_PI) / ((O_C * p->c_tilde) * dt);
@@ -1354,6 +1378,10 @@ int lym1o_substep_cyl(const lym1o_ctx *c, double dt, const double *J, const doub
     free(FJx); free(FHxx); free(FHyx); free(FJy); free(FHxy); free(FHyy); free(Wk); free(ax); free(ay);
     return 0;
 }
+
+/* emergent spectrum output of the following substeps (NULL: off); buf holds
+ * nb x (2 (nx + ny)) doubles for geometry 0, nb x (nx + ny) for geometry 1 */
+void lym1o_set_spectrum(lym1o_ctx *c, double *buf) { c->spec = buf; }
 
 void lym1o_set_threads(int n)
 {

@@ -23,6 +23,9 @@ struct lym1_ctx {
   void *Hc = nullptr, *Gc = nullptr;
   double *gmaxc = nullptr, *Kcc = nullptr, *hkTc = nullptr, *t_2nu = nullptr, *sig0c = nullptr;
   float* f_2nu = nullptr;
+  // emergent spectrum accumulation (lym1_spectrum_enable)
+  double* spec = nullptr;
+  int spec_on = 0;
   long long nc = 0;
   double dx = 0, T = 0, c_tilde = 0, cfl = 0, kabs = 0, kF = 0, dt_cfl = 0, umax = 0;
   double L_tot = 0, device_bytes = 0, gem_max = 1;
@@ -172,6 +175,9 @@ DeviceView make_view(const lym1_ctx* c, double dt) {
   v.f_half = c->f_half;
   v.geometry = c->geometry;
   v.vac = c->vac;
+  v.spec = c->spec_on ? c->spec : nullptr;
+  v.spec_unit = (4.0 * kPi) / kLight;
+  v.nf = c->geometry == 1 ? (c->nx + c->ny) : 2 * (c->nx + c->ny);
   v.pt = c->pt;
   v.Hc = c->Hc;
   v.Gc = c->Gc;
@@ -1065,3 +1071,36 @@ int lym1_profile_read(lym1_ctx* c, lym1_profile* out, int reset) {
 }
 
 }  // extern "C"
+
+int lym1_spectrum_enable(lym1_ctx* c, int on) {
+  if (!c) return LYM1_EINVAL;
+  const int nf = c->geometry == 1 ? (c->nx + c->ny) : 2 * (c->nx + c->ny);
+  const size_t bytes = sizeof(double) * static_cast<size_t>(nf) * c->nb;
+  if (on) {
+    if (!c->spec) {
+      const int rc = dalloc_t(c, &c->spec, bytes / sizeof(double));
+      if (rc != LYM1_OK) return rc;
+    }
+    LYM1_TRY(cudaMemsetAsync(c->spec, 0, bytes, c->stream));
+  }
+  c->spec_on = on ? 1 : 0;
+  // the graph-replayed path holds device copies of the views: rebuild it
+  if (c->self_batch) {
+    LYM1_TRY(cudaStreamSynchronize(c->stream));
+    lym1_batch_destroy(c->self_batch);
+    c->self_batch = nullptr;
+  }
+  return LYM1_OK;
+}
+
+int lym1_spectrum_read(lym1_ctx* c, double* out, int* n_faces) {
+  if (!c) return LYM1_EINVAL;
+  const int nf = c->geometry == 1 ? (c->nx + c->ny) : 2 * (c->nx + c->ny);
+  if (n_faces) *n_faces = nf;
+  if (!out) return LYM1_OK;
+  if (!c->spec) return LYM1_EINVAL;
+  const size_t bytes = sizeof(double) * static_cast<size_t>(nf) * c->nb;
+  LYM1_TRY(cudaMemcpyAsync(out, c->spec, bytes, cudaMemcpyDefault, c->stream));
+  LYM1_TRY(cudaStreamSynchronize(c->stream));
+  return LYM1_OK;
+}

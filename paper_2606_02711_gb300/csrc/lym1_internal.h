@@ -143,6 +143,12 @@ struct DeviceView {
   // per-cell gas temperature (pt = 1): <H>_k and the emission factor per
   // [k][cell] in the state type (FP32 policies hold G / gmax), and the
   // per-cell line constants; the per-bin tables above are then unused
+  // emergent spectrum (nullptr: off): escaping energy (erg) accumulated per
+  // [bin][outer face] (faces x-, x+, y-, y+ for geometry 0; R and Z outer for
+  // geometry 1); spec_unit = 4 pi / c
+  double* spec = nullptr;
+  double spec_unit = 0;
+  int nf = 0;
   int pt = 0;
   const void* Hc = nullptr;
   const void* Gc = nullptr;

@@ -542,6 +542,23 @@ __device__ __forceinline__ void transport_tile(const DeviceView& v, int x0, int 
         if (gy == 0) out.add(dnu * (cdx * -I(yJ[ty][tx])));
         if (gy == ny - 1) out.add(dnu * (cdx * I(yJ[ty + 1][tx])));
       }
+      if (v.spec && (gx == nx - 1 || gy == ny - 1 || (G == 0 && (gx == 0 || gy == 0)))) {
+        // emergent spectrum: the escaping energy of each outer face of this cell
+        double* sp = v.spec + static_cast<long long>(k) * v.nf;
+        const double cdt_d = v.cdt, dxd = v.dx, dnud = v.t_dnu[k];
+        if constexpr (G == 1) {
+          if (gx == nx - 1)
+            sp[gy] += v.spec_unit * ((2.0 * kPi) * (v.g_AR[nx] * (dnud * (cdt_d * double(xJ[ty][tx + 1])))));
+          if (gy == ny - 1)
+            sp[ny + gx] += v.spec_unit * ((2.0 * kPi) * (v.g_AZ[gx] * (dnud * (cdt_d * double(yJ[ty + 1][tx])))));
+        } else {
+          const double eu = v.spec_unit * ((dxd * dxd) * dxd);  // erg per unit of the sums
+          if (gx == 0) sp[gy] += eu * (dnud * (cdt_d * (-double(xJ[ty][tx]) / dxd)));
+          if (gx == nx - 1) sp[ny + gy] += eu * (dnud * (cdt_d * (double(xJ[ty][tx + 1]) / dxd)));
+          if (gy == 0) sp[2 * ny + gx] += eu * (dnud * (cdt_d * (-double(yJ[ty][tx]) / dxd)));
+          if (gy == ny - 1) sp[2 * ny + nx + gx] += eu * (dnud * (cdt_d * (double(yJ[ty + 1][tx]) / dxd)));
+        }
+      }
     }
     __syncthreads();
   }
@@ -973,6 +990,20 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
           if (gy == ny - 1) o2 += I(yJ[ty + 1][tx]);
         }
         out += dnu * (cdx * o2);
+        if (v.spec) {  // emergent spectrum: the escaping energy of each outer face
+          double* sp = v.spec + static_cast<long long>(k) * v.nf;
+          const double dxd = v.dx;
+          const double u = (v.spec_unit * ((dxd * dxd) * dxd)) * double(dnu * cdx);
+          if constexpr (G == 1) {
+            if (gx == nx - 1) sp[gy] += u * double(wR * I(xJ[ty][tx + 1]));
+            if (gy == ny - 1) sp[ny + gx] += u * double(wcol * I(yJ[ty + 1][tx]));
+          } else {
+            if (gx == 0) sp[gy] -= u * double(xJ[ty][tx]);
+            if (gx == nx - 1) sp[ny + gy] += u * double(xJ[ty][tx + 1]);
+            if (gy == 0) sp[2 * ny + gx] -= u * double(yJ[ty][tx]);
+            if (gy == ny - 1) sp[2 * ny + nx + gx] += u * double(yJ[ty + 1][tx]);
+          }
+        }
       }
     }
     base = nbase;

@@ -76,6 +76,8 @@ _lib = None
 # every symbol the header declares, with its ctypes signature
 SIGNATURES = {
     "lym1_strerror": (C.c_char_p, [C.c_int]),
+    "lym1_spectrum_enable": (C.c_int, [C.c_void_p, C.c_int]),
+    "lym1_spectrum_read": (C.c_int, [C.c_void_p, _PD, C.POINTER(C.c_int)]),
     "lym1_create": (C.c_int, [C.POINTER(lym1_grid), C.POINTER(lym1_groups),
                               C.POINTER(lym1_opacities), C.POINTER(C.c_void_p)]),
     "lym1_destroy": (None, [C.c_void_p]),
@@ -267,6 +269,19 @@ class Context:
         if check:
             _check(st, "lym1_diagnostics")
         return {name: getattr(d, name) for name, _ in d._fields_}
+
+    def spectrum_enable(self, on: bool = True):
+        """Start (zeroed) or stop accumulating the emergent spectrum."""
+        _check(lib().lym1_spectrum_enable(self.handle, int(bool(on))), "lym1_spectrum_enable")
+
+    def spectrum(self) -> np.ndarray:
+        """Escaping energy (erg) per [bin][outer face] since spectrum_enable."""
+        nf = C.c_int()
+        _check(lib().lym1_spectrum_read(self.handle, None, C.byref(nf)), "lym1_spectrum_read")
+        out = np.empty((self.nb, nf.value))
+        _check(lib().lym1_spectrum_read(self.handle, out.ctypes.data_as(_PD), C.byref(nf)),
+               "lym1_spectrum_read")
+        return out
 
     def info(self) -> dict:
         i = lym1_info()
