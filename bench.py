@@ -376,6 +376,28 @@ def main():
             c2.destroy()
         out["precisions"] = cmp
 
+        # the same cloud under a two-phase gas temperature (80 K / 2e4 K): the
+        # per-[bin][cell] <H>_k tables built at creation, then the headline policy
+        import copy
+        ctf = copy.copy(cloud)
+        ctf.temp = wl.two_phase_temperature(cloud.nx, cloud.ny, seed=7, T_cold=80.0, T_hot=2.0e4)
+        t0 = time.perf_counter()
+        c3 = L.from_cloud(ctf, precision=prec)
+        t_create = time.perf_counter() - t0
+        c3.substeps(4)
+        c3.synchronize()
+        n = 4 * args.fp64_steps
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        c3.substeps(n)
+        b.record()
+        torch.cuda.synchronize()
+        m = a.elapsed_time(b)
+        out["temperature_field"] = {"value": nc * n / (m * 1e-3), "unit": UNIT, "ms_per_step": m / n,
+                                    "steps": n, "create_s": t_create,
+                                    "field": "two-phase 80 K / 2e4 K (seeded k^-4 field)"}
+        c3.destroy()
+
         if rank == 0 and world == 1 and not args.no_cpu:
             out["cpu_baseline"] = cpu_baseline(cloud, seconds=args.cpu_seconds)
 
