@@ -66,8 +66,10 @@ void build_cell_tables(const std::vector<double>& edges, const double* T, long l
                        int gray, int recoil, int geometry, CellTables* out);
 
 // ---------------------------------------------------------------- kernel side
-constexpr int kTileX = 32;   // transport tile: one thread per cell
-constexpr int kTileY = 8;
+// transport tile: one thread per cell; 16 x 16 makes the 32 faces beyond
+// the per-thread left and bottom faces (top row, right column) one warp's work
+constexpr int kTileX = 16;
+constexpr int kTileY = 16;
 constexpr int kFreqThreads = 128;
 constexpr int kDiagSlots = 8;  // per-block partial sums written by the kernels
 

@@ -700,17 +700,15 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
   constexpr int TX = kTileX, TY = kTileY, SX = TX + 4, SY = TY + 4;
   constexpr int NT = TX * TY;
   static_assert(SX * SY <= 2 * NT, "two halo entries per thread at most");
-  static_assert(TY <= 32, "right-column faces are computed by one warp");
+  static_assert(TX + TY == 32, "the extra faces are one warp's work");
   __shared__ float4 sq[2][SY][SX];  // (J, f_x, f_y, alpha_F of the bin)
   __shared__ float sHx[2][SY][SX], sHy[2][SY][SX];
-  __shared__ float xJ[TY][TX + 1], xN[TY][TX + 1], xT[TY][TX + 1];
-  __shared__ float yJ[TY + 1][TX], yN[TY + 1][TX], yT[TY + 1][TX];
+  // face fluxes (J, normal K, tangential K, -): x faces (J, K_xx, K_xy), y faces
+  // (J, K_yy, K_yx)
+  __shared__ float4 xF[TY][TX + 1];
+  __shared__ float4 yF[TY + 1][TX];
   __shared__ double red[NT / 32];
-  extern __shared__ float tabf[];  // <H>_k, dnu_k, gem_k / gem_max, J_act,k as FP32 (4 nb)
-  float* tH = tabf;
-  float* tD = tabf + v.nb;
-  float* tG = tabf + 2 * v.nb;
-  float* tA = tabf + 3 * v.nb;
+  extern __shared__ float4 tab4[];  // per bin (<H>_k, dnu_k, gem_k / gem_max, J_act,k) as FP32
 
   const float* __restrict__ Jin = static_cast<const float*>(v.J);
   const float* __restrict__ Hxin = static_cast<const float*>(v.Hx);
@@ -736,23 +734,18 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
   // meaningless far below a bin plane's scale)
   // J dnu_k above thr = kActiveShare E_prev / unit (set by the previous substep's reduction)
   const float thr = float(v.acc[14]);
-  for (int i = tid; i < nb; i += NT) {
-    tH[i] = v.f_H[i];
-    tD[i] = v.f_dnu[i];
-    tG[i] = v.f_G[i];
-    tA[i] = fmaxf(thr, 1e-30f) / v.f_dnu[i];
-  }
+  for (int i = tid; i < nb; i += NT)
+    tab4[i] = make_float4(v.f_H[i], v.f_dnu[i], v.f_G[i], fmaxf(thr, 1e-30f) / v.f_dnu[i]);
   // halo entries owned by this thread (plane offsets; sign of H_x, H_y;
   // opacity alpha and rho_d kappa_F of the ghost-mapped cell)
   const int e0 = tid, e1 = tid + NT;
   const bool has1 = e1 < SX * SY;
   const int ex0 = e0 % SX, ey0 = e0 / SX, ex1 = e1 % SX, ey1 = e1 / SX;
   bool fx0, fy0, fx1 = false, fy1 = false;
-  const long long off0 = static_cast<long long>(ghost<G>(y0 + ey0 - 2, ny, fy0)) * nx +
-                         ghost<G>(x0 + ex0 - 2, nx, fx0);
-  const long long off1 = has1 ? static_cast<long long>(ghost<G>(y0 + ey1 - 2, ny, fy1)) * nx +
-                                    ghost<G>(x0 + ex1 - 2, nx, fx1)
-                              : 0;
+  // in-plane offsets fit in 32 bits (cells per plane <= 2^31, checked at creation)
+  const int off0 = ghost<G>(y0 + ey0 - 2, ny, fy0) * nx + ghost<G>(x0 + ex0 - 2, nx, fx0);
+  const int off1 = has1 ? ghost<G>(y0 + ey1 - 2, ny, fy1) * nx + ghost<G>(x0 + ex1 - 2, nx, fx1) : 0;
+  const int cell32 = static_cast<int>(cell);
   const float sx0 = fx0 ? -1.0f : 1.0f, sy0 = fy0 ? -1.0f : 1.0f;
   const float sx1 = fx1 ? -1.0f : 1.0f, sy1 = fy1 ? -1.0f : 1.0f;
   // ghosts beyond an outflow side into vacuum hold no radiation
@@ -771,12 +764,18 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
     const float w = float(xdir ? v.ux[c] : v.uy[c]) * inv_c;
     return (xdir ? fxg : fyg) ? -w : w;
   };
-  const bool xtra_y = ty == 0, xtra_x = ty == 1 && tx < TY;
   const float wfx = 0.5f * (wcell(gx - 1, gy, true) + wcell(gx, gy, true));
   const float wfy = 0.5f * (wcell(gx, gy - 1, false) + wcell(gx, gy, false));
-  float wfx2 = 0.0f, wfy2 = 0.0f;
-  if (xtra_y) wfy2 = 0.5f * (wcell(gx, y0 + TY - 1, false) + wcell(gx, y0 + TY, false));
-  if (xtra_x) wfx2 = 0.5f * (wcell(x0 + TX - 1, y0 + tx, true) + wcell(x0 + TX, y0 + tx, true));
+  // the 32 extra faces are one evaluation by warp 0: lanes 0..TX-1 take the
+  // top row of y faces (fi = lane, fj = TY), lanes TX..31 the right column of
+  // x faces (fi = TX, fj = lane - TX)
+  const bool xtra = tid < 32;
+  const bool xisx = tid >= TX;
+  const int xfi = xisx ? TX : tid, xfj = xisx ? tid - TX : TY;
+  float wf2 = 0.0f;
+  if (xtra)
+    wf2 = xisx ? 0.5f * (wcell(x0 + TX - 1, y0 + xfj, true) + wcell(x0 + TX, y0 + xfj, true))
+               : 0.5f * (wcell(x0 + xfi, y0 + TY - 1, false) + wcell(x0 + xfi, y0 + TY, false));
   // face optical depth = aF_0 dl_0 + aF_1 dl_1 (centroid distances, geometry
   // 1) or (aF_0 + aF_1) dx/2 (geometry 0)
   const float half_dx = 0.5f * float(v.dx);
@@ -785,7 +784,7 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
     const int fa = gx <= nx ? gx : nx;
     dlA0 = v.gf_dlL[fa];
     dlA1 = v.gf_dlR[fa];
-    if (xtra_x) {
+    if (xtra && xisx) {
       const int fb = x0 + TX <= nx ? x0 + TX : nx;
       dlB0 = v.gf_dlL[fb];
       dlB1 = v.gf_dlR[fb];
@@ -847,7 +846,8 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
   long long base = 0;  // k * nc
   for (int k = 0; k < nb; ++k) {
     const int b = k & 1;
-    const float Hk = tH[k];
+    const float4 tb = tab4[k];  // (<H>_k, dnu_k, gem_k / gem_max, J_act,k)
+    const float Hk = tb.x;
     {  // halo entries of bin k: registers -> shared, with primitives and alpha_F
       float J0 = pJ0, X0 = pX0, Y0 = pY0, J1 = pJ1, X1 = pX1, Y1 = pY1;
       if (vz0) J0 = X0 = Y0 = 0.0f;
@@ -871,13 +871,16 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
     }
     const long long nbase = base + nc;
     if (k + 1 < nb) {  // prefetch bin k+1
-      pJ0 = Jin[nbase + off0];
-      pX0 = Hxin[nbase + off0];
-      pY0 = Hyin[nbase + off0];
+      const float* Jn = Jin + nbase;
+      const float* Xn = Hxin + nbase;
+      const float* Yn = Hyin + nbase;
+      pJ0 = Jn[off0];
+      pX0 = Xn[off0];
+      pY0 = Yn[off0];
       if (has1) {
-        pJ1 = Jin[nbase + off1];
-        pX1 = Hxin[nbase + off1];
-        pY1 = Hyin[nbase + off1];
+        pJ1 = Jn[off1];
+        pX1 = Xn[off1];
+        pY1 = Yn[off1];
       }
       if constexpr (PT) {
         pH0 = Hcf[nbase + off0];
@@ -891,20 +894,34 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
       const float4 qm = sq[b][r][fi], q0 = sq[b][r][fi + 1], q1 = sq[b][r][fi + 2],
                    q2 = sq[b][r][fi + 3];
       const float tau = (G == 1) ? q0.w * dl0 + q1.w * dl1 : (q0.w + q1.w) * dl0;
+      float oJ, oN, oT;
       face_flux_f32(qm.x, qm.y, qm.z, q0.x, q0.y, q0.z, q1.x, q1.y, q1.z, q2.x, q2.y, q2.z, tau,
-                    wf, xJ[fj][fi], xN[fj][fi], xT[fj][fi]);
+                    wf, oJ, oN, oT);
+      xF[fj][fi] = make_float4(oJ, oN, oT, 0.0f);
     };
     auto yface = [&](int fi, int fj, float wf) {  // between tile cells (fi, fj-1) and (fi, fj)
       const int cc = fi + 2;
       const float4 qm = sq[b][fj][cc], q0 = sq[b][fj + 1][cc], q1 = sq[b][fj + 2][cc],
                    q2 = sq[b][fj + 3][cc];
+      float oJ, oN, oT;
       face_flux_f32(qm.x, qm.z, qm.y, q0.x, q0.z, q0.y, q1.x, q1.z, q1.y, q2.x, q2.z, q2.y,
-                    (q0.w + q1.w) * half_dx, wf, yJ[fj][fi], yN[fj][fi], yT[fj][fi]);
+                    (q0.w + q1.w) * half_dx, wf, oJ, oN, oT);
+      yF[fj][fi] = make_float4(oJ, oN, oT, 0.0f);
     };
     xface(tx, ty, wfx, dlA0, dlA1);
     yface(tx, ty, wfy);
-    if (xtra_y) yface(tx, TY, wfy2);
-    if (xtra_x) xface(TX, tx, wfx2, dlB0, dlB1);
+    if (xtra) {  // one evaluation for both kinds of extra face
+      const float4* q = xisx ? &sq[b][xfj + 2][xfi] : &sq[b][xfj][xfi + 2];
+      const int st = xisx ? 1 : SX;
+      const float4 qm = q[0], q0 = q[st], q1 = q[2 * st], q2 = q[3 * st];
+      const float tau = q0.w * dlB0 + q1.w * dlB1;
+      float oJ, oN, oT;
+      face_flux_f32(qm.x, xisx ? qm.y : qm.z, xisx ? qm.z : qm.y, q0.x, xisx ? q0.y : q0.z,
+                    xisx ? q0.z : q0.y, q1.x, xisx ? q1.y : q1.z, xisx ? q1.z : q1.y, q2.x,
+                    xisx ? q2.y : q2.z, xisx ? q2.z : q2.y, tau, wf2, oJ, oN, oT);
+      float4* dst = xisx ? &xF[xfj][TX] : &yF[TY][xfi];
+      *dst = make_float4(oJ, oN, oT, 0.0f);
+    }
     __syncthreads();
     if (valid) {
       const float4 qs = sq[b][ty + 2][tx + 2];
@@ -913,20 +930,20 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
       const float f2c = cap_unit_f32(fxc, fyc);
       float Dxx, Dxy, Dyy, Dpp;
       closure_f32q(fxc, fyc, f2c, Dxx, Dxy, Dyy, Dpp);
+      const float4 xl = xF[ty][tx], xr = xF[ty][tx + 1], yb = yF[ty][tx], yt = yF[ty + 1][tx];
       float W, divJ, divHx, divHy;
       if constexpr (G == 1) {
         // per-radian finite volumes in units of dx (r0, r1 = R-face areas x dx /
         // Vol, hoop = dx^3 / Vol); hoop source K_phiphi <1/R> in the R equation
         W = J * (((Dxx * gxx + Dyy * gyy) + Dxy * gsh) + Dpp * gphi);
-        divJ = (r1c * xJ[ty][tx + 1] - r0c * xJ[ty][tx]) + (yJ[ty + 1][tx] - yJ[ty][tx]);
-        divHx = ((r1c * xN[ty][tx + 1] - r0c * xN[ty][tx]) + (yT[ty + 1][tx] - yT[ty][tx])) -
-                hoopc * (Dpp * J);
-        divHy = (r1c * xT[ty][tx + 1] - r0c * xT[ty][tx]) + (yN[ty + 1][tx] - yN[ty][tx]);
+        divJ = (r1c * xr.x - r0c * xl.x) + (yt.x - yb.x);
+        divHx = ((r1c * xr.y - r0c * xl.y) + (yt.z - yb.z)) - hoopc * (Dpp * J);
+        divHy = (r1c * xr.z - r0c * xl.z) + (yt.y - yb.y);
       } else {
         W = J * ((Dxx * gxx + Dyy * gyy) + Dxy * gsh);
-        divJ = (xJ[ty][tx + 1] - xJ[ty][tx]) + (yJ[ty + 1][tx] - yJ[ty][tx]);
-        divHx = (xN[ty][tx + 1] - xN[ty][tx]) + (yT[ty + 1][tx] - yT[ty][tx]);
-        divHy = (xT[ty][tx + 1] - xT[ty][tx]) + (yN[ty + 1][tx] - yN[ty][tx]);
+        divJ = (xr.x - xl.x) + (yt.x - yb.x);
+        divHx = (xr.y - xl.y) + (yt.z - yb.z);
+        divHy = (xr.z - xl.z) + (yt.y - yb.y);
       }
       const float J1 = J - cdt_f * (divJ * inv_dx + W * inv_c);
       const float Hx1 = Hx - cdt_dx * divHx;
@@ -937,7 +954,7 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
         dnu = v.t_dnu[k];
       } else {
         aH = alpha_c * (PT ? Hcf[base + cell] : Hk);
-        dnu = tD[k];
+        dnu = tb.y;
       }
       const I kap = rho_c * kabs + pd_c * aH;
       const I aF = aH + rho_c * kF;
@@ -945,7 +962,7 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
       if constexpr (sizeof(I) == 8)
         js = src ? lum_d * (PT ? gmax_c * double(Gcf[base + cell]) : v.t_gem[k]) : 0.0;
       else
-        js = src ? jsc * (PT ? Gcf[base + cell] : tG[k]) : 0.0f;
+        js = src ? jsc * (PT ? Gcf[base + cell] : tb.z) : 0.0f;
       I J2, Hx2, Hy2;
       if constexpr (sizeof(I) == 8) {
         J2 = (I(J1) + cdt * js) / (I(1) + cdt * kap);
@@ -958,10 +975,9 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
         Hx2 = Hx1 * ra;
         Hy2 = Hy1 * ra;
       }
-      const long long o = base + cell;
-      Jout[o] = float(J2);
-      Hxout[o] = float(Hx2);
-      Hyout[o] = float(Hy2);
+      (Jout + base)[cell32] = float(J2);
+      (Hxout + base)[cell32] = float(Hx2);
+      (Hyout + base)[cell32] = float(Hy2);
       ax += dnu * (I(Hx1) - Hx2);
       ay += dnu * (I(Hy1) - Hy2);
       // A7 bookkeeping (energy units applied once per substep; the factors
@@ -973,7 +989,7 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
         en += dnu * J2;
         const float j2f = float(J2), h2 = float(Hx2) * float(Hx2) + float(Hy2) * float(Hy2);
         const float jj = j2f * j2f;
-        if ((G == 1 ? j2f * wvf : j2f) > tA[k]) {
+        if ((G == 1 ? j2f * wvf : j2f) > tb.w) {
           mxf2 = fmaxf(mxf2, fdiv(h2, jj));
           bad += (h2 > jj * 1.000002f) ? 1 : 0;
         }
@@ -981,13 +997,13 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
       if (bnd) {
         I o2 = 0;
         if constexpr (G == 1) {
-          if (gx == nx - 1) o2 += wR * I(xJ[ty][tx + 1]);
-          if (gy == ny - 1) o2 += wcol * I(yJ[ty + 1][tx]);
+          if (gx == nx - 1) o2 += wR * I(xr.x);
+          if (gy == ny - 1) o2 += wcol * I(yt.x);
         } else {
-          if (gx == 0) o2 -= I(xJ[ty][tx]);
-          if (gx == nx - 1) o2 += I(xJ[ty][tx + 1]);
-          if (gy == 0) o2 -= I(yJ[ty][tx]);
-          if (gy == ny - 1) o2 += I(yJ[ty + 1][tx]);
+          if (gx == 0) o2 -= I(xl.x);
+          if (gx == nx - 1) o2 += I(xr.x);
+          if (gy == 0) o2 -= I(yb.x);
+          if (gy == ny - 1) o2 += I(yt.x);
         }
         out += dnu * (cdx * o2);
         if (v.spec) {  // emergent spectrum: the escaping energy of each outer face
@@ -995,13 +1011,13 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
           const double dxd = v.dx;
           const double u = (v.spec_unit * ((dxd * dxd) * dxd)) * double(dnu * cdx);
           if constexpr (G == 1) {
-            if (gx == nx - 1) sp[gy] += u * double(wR * I(xJ[ty][tx + 1]));
-            if (gy == ny - 1) sp[ny + gx] += u * double(wcol * I(yJ[ty + 1][tx]));
+            if (gx == nx - 1) sp[gy] += u * double(wR * I(xr.x));
+            if (gy == ny - 1) sp[ny + gx] += u * double(wcol * I(yt.x));
           } else {
-            if (gx == 0) sp[gy] -= u * double(xJ[ty][tx]);
-            if (gx == nx - 1) sp[ny + gy] += u * double(xJ[ty][tx + 1]);
-            if (gy == 0) sp[2 * ny + gx] -= u * double(yJ[ty][tx]);
-            if (gy == ny - 1) sp[2 * ny + nx + gx] += u * double(yJ[ty + 1][tx]);
+            if (gx == 0) sp[gy] -= u * double(xl.x);
+            if (gx == nx - 1) sp[ny + gy] += u * double(xr.x);
+            if (gy == 0) sp[2 * ny + gx] -= u * double(yb.x);
+            if (gy == ny - 1) sp[2 * ny + nx + gx] += u * double(yt.x);
           }
         }
       }
