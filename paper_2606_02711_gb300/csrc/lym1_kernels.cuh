@@ -158,6 +158,28 @@ __device__ __forceinline__ void closure(F fn, F ft, F& Dnn, F& Dnt, F& Dtt) {
   closure(fn, ft, Dnn, Dnt, Dtt, Dpp);
 }
 
+// FP64 closure for the tuned policy: with s = sqrt(4 - 3f^2) the printed chi is
+// (5 - 2s)/3, so (1-chi)/2 = (s - 1)/3 and (3chi - 1)/(2f^2) = 3/(2 + s): one
+// square root and one division instead of the printed form's three divisions
+// (GB300's FP64 division is a multi-instruction sequence on a 1/64-rate pipe).
+// LYM1_FP64_DET keeps the printed form and its operation order.
+template <bool DET>
+__device__ __forceinline__ void closure_d(double fn, double ft, double& Dnn, double& Dnt,
+                                          double& Dtt, double& Dpp) {
+  if constexpr (DET) {
+    closure(fn, ft, Dnn, Dnt, Dtt, Dpp);
+  } else {
+    const double f2 = fn * fn + ft * ft;
+    const double s = sqrt(4.0 - 3.0 * f2);
+    const double dA = (s - 1.0) * (1.0 / 3.0);
+    const double g = 3.0 / (2.0 + s);
+    Dnn = dA + g * (fn * fn);
+    Dnt = g * (fn * ft);
+    Dtt = dA + g * (ft * ft);
+    Dpp = dA;
+  }
+}
+
 // Causality after the frequency step (Sec. 2.1 step 3: |H|/J <= 1 with H
 // rescaled by J_new/J_old): an H longer than J is shortened to J along its
 // direction; H = 0 where J <= 0.
@@ -238,7 +260,7 @@ __device__ __forceinline__ void cap_unit(F& fn, F& ft) {
 // MinMod reconstruction of J, f_n, f_t from cells -1, 0, +1, +2; interface
 // rescale of |f| > 1; corrected GLF flux of J; modified GLF flux of K; upwind
 // advection with the mean face velocity (reconstructed donor state).
-template <class F>
+template <class F, bool DET = true>
 __device__ __forceinline__ void face_flux(F Jm, F nm, F tm, F J0, F n0, F t0, F J1, F n1, F t1,
                                           F J2, F n2, F t2, F aF0, F aF1, F un0, F un1,
                                           F dl0, F dl1, F& oJ, F& oN, F& oT) {
@@ -251,27 +273,42 @@ __device__ __forceinline__ void face_flux(F Jm, F nm, F tm, F J0, F n0, F t0, F 
   cap_unit(nL, tL);
   cap_unit(nR, tR);
   const F HnL = JL * nL, HtL = JL * tL, HnR = JR * nR, HtR = JR * tR;
-  F DnnL, DntL, DttL, DnnR, DntR, DttR;
-  closure(nL, tL, DnnL, DntL, DttL);
-  closure(nR, tR, DnnR, DntR, DttR);
+  F DnnL, DntL, DttL, DnnR, DntR, DttR, DppL, DppR;
+  closure_d<DET>(nL, tL, DnnL, DntL, DttL, DppL);
+  closure_d<DET>(nR, tR, DnnR, DntR, DttR, DppR);
   const F KnnL = DnnL * JL, KntL = DntL * JL, KnnR = DnnR * JR, KntR = DntR * JR;
   // face optical depth from the two cells' centres (centroids) to the face
   const F tau = aF0 * dl0 + aF1 * dl1;
-  const F eps = (F(0.2) + tau) / ((F(0.2) + tau) + tau * tau);
-  const F dif = (tau > F(0)) ? ((F(1) - eps) * (J1 - J0)) / (F(3) * tau) : F(0);
+  F eps, dif;
+  if constexpr (DET) {
+    eps = (F(0.2) + tau) / ((F(0.2) + tau) + tau * tau);
+    dif = (tau > F(0)) ? ((F(1) - eps) * (J1 - J0)) / (F(3) * tau) : F(0);
+  } else {  // one division: (1 - eps)/(3 tau) = tau / (3 d), d = 0.2 + tau + tau^2
+    const F rd = F(1) / ((F(0.2) + tau) + tau * tau);
+    eps = (F(0.2) + tau) * rd;
+    dif = (tau * rd) * (F(1) / F(3)) * (J1 - J0);
+  }
   F fJ = (eps * (F(0.5) * (HnL + HnR)) - eps * (F(0.5) * (JR - JL))) - dif;
   F fN = F(0.5) * (KnnL + KnnR) - eps * (F(0.5) * (HnR - HnL));
   F fT = F(0.5) * (KntL + KntR) - eps * (F(0.5) * (HtR - HtL));
   const F uf = F(0.5) * (un0 + un1);
   const F cl = F(kLight);
-  if (uf > F(0)) {
-    fJ = fJ + (uf * JL) / cl;
-    fN = fN + (uf * HnL) / cl;
-    fT = fT + (uf * HtL) / cl;
-  } else if (uf < F(0)) {
-    fJ = fJ + (uf * JR) / cl;
-    fN = fN + (uf * HnR) / cl;
-    fT = fT + (uf * HtR) / cl;
+  if constexpr (DET) {
+    if (uf > F(0)) {
+      fJ = fJ + (uf * JL) / cl;
+      fN = fN + (uf * HnL) / cl;
+      fT = fT + (uf * HtL) / cl;
+    } else if (uf < F(0)) {
+      fJ = fJ + (uf * JR) / cl;
+      fN = fN + (uf * HnR) / cl;
+      fT = fT + (uf * HtR) / cl;
+    }
+  } else {
+    const F w = uf * (F(1) / cl);
+    const bool up = uf > F(0);
+    fJ = fJ + w * (up ? JL : JR);
+    fN = fN + w * (up ? HnL : HnR);
+    fT = fT + w * (up ? HtL : HtR);
   }
   oJ = fJ;
   oN = fN;
@@ -441,8 +478,14 @@ __device__ __forceinline__ void transport_tile(const DeviceView& v, int x0, int 
       sHx[ly][lx] = Hx;
       sHy[ly][lx] = Hy;
       if (J > F(0)) {
-        sfx[ly][lx] = Hx / J;
-        sfy[ly][lx] = Hy / J;
+        if constexpr (P::DET) {
+          sfx[ly][lx] = Hx / J;
+          sfy[ly][lx] = Hy / J;
+        } else {
+          const F rJ = F(1) / J;
+          sfx[ly][lx] = Hx * rJ;
+          sfy[ly][lx] = Hy * rJ;
+        }
       } else {
         sfx[ly][lx] = F(0);
         sfy[ly][lx] = F(0);
@@ -461,7 +504,7 @@ __device__ __forceinline__ void transport_tile(const DeviceView& v, int x0, int 
           dl0 = sdl[0][fi];
           dl1 = sdl[1][fi];
         }
-        face_flux<F>(sJ[r][fi], sfx[r][fi], sfy[r][fi], sJ[r][fi + 1], sfx[r][fi + 1],
+        face_flux<F, P::DET>(sJ[r][fi], sfx[r][fi], sfy[r][fi], sJ[r][fi + 1], sfx[r][fi + 1],
                      sfy[r][fi + 1], sJ[r][fi + 2], sfx[r][fi + 2], sfy[r][fi + 2], sJ[r][fi + 3],
                      sfx[r][fi + 3], sfy[r][fi + 3], aF0, aF1, qUx[fj + 1][fi],
                      qUx[fj + 1][fi + 1], dl0, dl1, xJ[fj][fi], xN[fj][fi], xT[fj][fi]);
@@ -471,7 +514,7 @@ __device__ __forceinline__ void transport_tile(const DeviceView& v, int x0, int 
         const int cc = fi + 2;
         const F aF0 = qA[fj][fi + 1] * (PT ? qH[fj][fi + 1] : Hk) + qR[fj][fi + 1] * kF_f;
         const F aF1 = qA[fj + 1][fi + 1] * (PT ? qH[fj + 1][fi + 1] : Hk) + qR[fj + 1][fi + 1] * kF_f;
-        face_flux<F>(sJ[fj][cc], sfy[fj][cc], sfx[fj][cc], sJ[fj + 1][cc], sfy[fj + 1][cc],
+        face_flux<F, P::DET>(sJ[fj][cc], sfy[fj][cc], sfx[fj][cc], sJ[fj + 1][cc], sfy[fj + 1][cc],
                      sfx[fj + 1][cc], sJ[fj + 2][cc], sfy[fj + 2][cc], sfx[fj + 2][cc],
                      sJ[fj + 3][cc], sfy[fj + 3][cc], sfx[fj + 3][cc], aF0, aF1, qUy[fj][fi + 1],
                      qUy[fj + 1][fi + 1], half_dx, half_dx, yJ[fj][fi], yN[fj][fi], yT[fj][fi]);
@@ -484,7 +527,7 @@ __device__ __forceinline__ void transport_tile(const DeviceView& v, int x0, int 
       F fxc = sfx[ty + 2][tx + 2], fyc = sfy[ty + 2][tx + 2];
       cap_unit(fxc, fyc);
       F Dxx, Dxy, Dyy, Dpp;
-      closure(fxc, fyc, Dxx, Dxy, Dyy, Dpp);
+      closure_d<P::DET>(fxc, fyc, Dxx, Dxy, Dyy, Dpp);
       F J1, Hx1, Hy1, W;
       if constexpr (G == 1) {
         // finite volumes per radian; hoop source K_phiphi <1/R> in the R equation
@@ -501,9 +544,16 @@ __device__ __forceinline__ void transport_tile(const DeviceView& v, int x0, int 
         const F divJ = (xJ[ty][tx + 1] - xJ[ty][tx]) + (yJ[ty + 1][tx] - yJ[ty][tx]);
         const F divHx = (xN[ty][tx + 1] - xN[ty][tx]) + (yT[ty + 1][tx] - yT[ty][tx]);
         const F divHy = (xT[ty][tx + 1] - xT[ty][tx]) + (yN[ty + 1][tx] - yN[ty][tx]);
-        J1 = J - cdt_f * (divJ / dx + W / cl);
-        Hx1 = Hx - cdt_f * (divHx / dx);
-        Hy1 = Hy - cdt_f * (divHy / dx);
+        if constexpr (P::DET) {
+          J1 = J - cdt_f * (divJ / dx + W / cl);
+          Hx1 = Hx - cdt_f * (divHx / dx);
+          Hy1 = Hy - cdt_f * (divHy / dx);
+        } else {  // constant reciprocals instead of divisions
+          const F cdx = cdt_f * (F(1) / dx);
+          J1 = J - (cdx * divJ + cdt_f * (W * (F(1) / cl)));
+          Hx1 = Hx - cdx * divHx;
+          Hy1 = Hy - cdx * divHy;
+        }
       }
       const I aH = alpha_c * (PT ? I(Hcs[base + cell]) : I(Hk_d));
       const I kap = rho_c * kabs + pd_c * aH;
@@ -512,9 +562,17 @@ __device__ __forceinline__ void transport_tile(const DeviceView& v, int x0, int 
       // w_k / (4 pi V dnu_k) ~ 1e-58 are both outside the FP32 range); on the
       // axisymmetric grid lum already holds L / (2 pi Vol) and gem_k has V = 1
       const I js = (lum_d != 0.0) ? I(lum_d * (PT ? double(Gcs[base + cell]) : v.t_gem[k])) : I(0);
-      const I J2 = (I(J1) + cdt * js) / (I(1) + cdt * kap);
-      const I Hx2 = I(Hx1) / (I(1) + cdt * aF);
-      const I Hy2 = I(Hy1) / (I(1) + cdt * aF);
+      I J2, Hx2, Hy2;
+      if constexpr (P::DET) {
+        J2 = (I(J1) + cdt * js) / (I(1) + cdt * kap);
+        Hx2 = I(Hx1) / (I(1) + cdt * aF);
+        Hy2 = I(Hy1) / (I(1) + cdt * aF);
+      } else {
+        J2 = (I(J1) + cdt * js) / (I(1) + cdt * kap);
+        const I ra = I(1) / (I(1) + cdt * aF);
+        Hx2 = I(Hx1) * ra;
+        Hy2 = I(Hy1) * ra;
+      }
       const long long o = base + cell;
       Jout[o] = S(J2);
       Hxout[o] = S(Hx2);
@@ -1091,19 +1149,30 @@ __device__ __forceinline__ void freq_coef(typename P::F Jc, typename P::F Hxc, t
   } else {
     F fx = F(0), fy = F(0);
     if (Jc > F(0)) {
-      fx = Hxc / Jc;
-      fy = Hyc / Jc;
+      if constexpr (P::DET) {
+        fx = Hxc / Jc;
+        fy = Hyc / Jc;
+      } else {
+        const F rJ = F(1) / Jc;
+        fx = Hxc * rJ;
+        fy = Hyc * rJ;
+      }
     }
     cap_unit(fx, fy);
     F Dxx, Dxy, Dyy, Dpp;
-    closure(fx, fy, Dxx, Dxy, Dyy, Dpp);
+    closure_d<P::DET>(fx, fy, Dxx, Dxy, Dyy, Dpp);
     F DdU = (Dxx * gxx + Dyy * gyy) + Dxy * gsh;
     if constexpr (G == 1) DdU = DdU + Dpp * gphi;  // D_phiphi <u_R / R>
     const F K = Kc * Hk;
     const F C = K * Rk + F(tn[k]) * DdU;
     const F half = F(th[k]);
-    Pk = (C * half) / K;
-    ak = half / K;
+    if constexpr (P::DET) {
+      Pk = (C * half) / K;
+      ak = half / K;
+    } else {
+      ak = half / K;
+      Pk = C * ak;
+    }
     const F z = -fabs(Pk);
     ek = (z == F(0)) ? F(1) : m_expm1<P::DET>(z) / z;
   }
@@ -1234,17 +1303,23 @@ __device__ __forceinline__ void freq_block(const DeviceView& v, int blk) {
             const float rden = frcp(den);
             A = I(m_exp<P::DET>(-P0 - m) * rden);
             B = I(m_exp<P::DET>(P1 - m) * rden);
-          } else {
+          } else if constexpr (P::DET) {
             A = I(m_exp<P::DET>(-P0 - m) / den);
             B = I(m_exp<P::DET>(P1 - m) / den);
+          } else {
+            const F rden = F(1) / den;
+            A = I(m_exp<P::DET>(-P0 - m) * rden);
+            B = I(m_exp<P::DET>(P1 - m) * rden);
           }
         }
         I s, inv_dummy = 0;
         (void)inv_dummy;
         if constexpr (sizeof(I) == 4)
           s = tdi[k] * rcdt;
-        else
+        else if constexpr (P::DET)
           s = tdi[k] / cdt;
+        else
+          s = tdi[k] * (I(1) / cdt);
         const I E = (k == 0) ? s : s + Bprev * qprev;
         const I r = (k == 0) ? s * Jin0 : s * Jin0 + Aprev * gprev;
         const I Dp = E + A;
