@@ -105,6 +105,9 @@ def lib():
                                     C.POINTER(Diag)]
         L.lym1o_set_threads.argtypes = [C.c_int]
         L.lym1o_set_spectrum.argtypes = [C.c_void_p, _PD]
+        L.lym1o_set_ctilde.argtypes = [C.c_void_p, _D]
+        L.lym1o_dynamic_ctilde.restype = _D
+        L.lym1o_dynamic_ctilde.argtypes = [C.c_void_p, _PD, _D, _D]
         L.lym1o_get_threads.restype = C.c_int
         _lib = L
     return _lib
@@ -256,6 +259,21 @@ class Oracle:
         for the axisymmetric grid)."""
         g = self.prob.geometry
         return (self.nx + self.ny) if g == 1 else 2 * (self.nx + self.ny)
+
+    def set_ctilde(self, ct: float):
+        """Reduced speed of light (cm/s) and the RT time step with it."""
+        lib().lym1o_set_ctilde(self.ctx, float(ct))
+        self.dt_cfl = lib().lym1o_dt_cfl(self.ctx)
+
+    def dynamic_ctilde(self, cs=None, eps_rsl=4.0, ct_min=1.0e7) -> float:
+        """Apply the dynamic reduced speed of light; returns the new value."""
+        buf = None
+        if cs is not None:
+            buf = _f64(np.broadcast_to(cs, (self.ny, self.nx)))
+        ct = lib().lym1o_dynamic_ctilde(self.ctx, _p(buf) if buf is not None else None,
+                                        float(eps_rsl), float(ct_min))
+        self.dt_cfl = lib().lym1o_dt_cfl(self.ctx)
+        return ct
 
     def spectrum_on(self, on: bool = True):
         """Record the emergent spectrum (erg per [bin][face]) of each substep

@@ -362,7 +362,7 @@ typedef struct {
 typedef struct {
     lym1o_problem p;
     int nb; /* state bins */
-    double dnuD, a_v, sigma0, hkT, eta, dt_cfl;
+    double dnuD, a_v, sigma0, hkT, eta, dt_cfl, umax;
     double *dnu, *nubar, *Havg, *gem, *Rk, *half;
     double *alpha, *gxx, *gyy, *gsh;
     /* cylindrical geometry (per radian): R-face areas AR[nx+1], Z-face areas
@@ -546,6 +546,7 @@ lym1o_ctx *lym1o_create(const lym1o_problem *p)
         }
     /* RT time step (Sec. 2.1, CFL condition, D = 2 dimensions) */
     c->dt_cfl = (p->cfl / 2.0) * (p->dx / (p->c_tilde + umax));
+    c->umax = umax;
     if (p->temp) {
         /* A0 at every cell's own temperature (App. A: <H>_k, the Doppler width
          * and a_v at T; Sec. 2.1 step 2: emission fractions) */
@@ -1377,6 +1378,50 @@ int lym1o_substep_cyl(const lym1o_ctx *c, double dt, const double *J, const doub
     if (dg) *dg = d;
     free(FJx); free(FHxx); free(FHyx); free(FJy); free(FHxy); free(FHyy); free(Wk); free(ax); free(ay);
     return 0;
+}
+
+/* ======================================================================
+ * Reduced speed of light.  lym1o_set_ctilde sets c_tilde and the RT time
+ * step (Sec. 2.1, CFL condition).  lym1o_dynamic_ctilde applies the dynamic
+ * choice of Sec. 2.1 (the dynamic-RSL equation and its f_abs factor):
+ *   c_dyn = eps_RSL max_cells { max[1, (a_v tau_0)^(1/3) f_abs] max[|u|, c_s] },
+ *   f_abs = 1 / (1 + (a_v tau_0)^(1/3) tau_c + 0.6 p_d tau_0),
+ * with tau_0 = alpha dx the cell's line-centre optical depth (square cells)
+ * and tau_c = rho_d kappa_abs dx its continuum absorption depth; then
+ * c_tilde = min[max(c_min, c_dyn), c], moved by at most -25 % or x4 from the
+ * current value.  cs: per-cell sound speed (cm/s), or NULL for that of
+ * neutral atomic gas at the cell's temperature (gamma = 5/3, mu = 1.22).
+ * Returns the new c_tilde.
+ * ====================================================================== */
+void lym1o_set_ctilde(lym1o_ctx *c, double ct)
+{
+    c->p.c_tilde = ct;
+    c->dt_cfl = (c->p.cfl / 2.0) * (c->p.dx / (ct + c->umax));
+}
+
+double lym1o_dynamic_ctilde(lym1o_ctx *c, const double *cs, double eps_rsl, double ct_min)
+{
+    const lym1o_problem *p = &c->p;
+    const size_t nc = (size_t)p->nx * p->ny;
+    double m = 0.0;
+    for (size_t id = 0; id < nc; ++id) {
+        const double T = p->temp ? p->temp[id] : p->T;
+        double lc[3];
+        lym1o_line(T, lc);
+        const double tau0 = c->alpha[id] * p->dx;
+        const double tauc = (p->rho_d[id] * p->kappa_abs) * p->dx;
+        const double X = cbrt(lc[1] * tau0);
+        const double fabs_ = 1.0 / ((1.0 + X * tauc) + (0.6 * p->p_d[id]) * tau0);
+        const double u = sqrt(p->ux[id] * p->ux[id] + p->uy[id] * p->uy[id]);
+        const double s = cs ? cs[id] : sqrt(((5.0 / 3.0) * (O_KB * T)) / (1.22 * O_MH));
+        const double term = fmax(1.0, X * fabs_) * fmax(u, s);
+        if (term > m) m = term;
+    }
+    double ct = fmin(fmax(ct_min, eps_rsl * m), O_C);
+    const double prev = p->c_tilde;
+    ct = fmin(fmax(ct, 0.75 * prev), 4.0 * prev);
+    lym1o_set_ctilde(c, ct);
+    return ct;
 }
 
 /* emergent spectrum output of the following substeps (NULL: off); buf holds
