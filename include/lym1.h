@@ -320,6 +320,35 @@ int lym1_energy_noalloc(const double *J, const double *dnu, int nb, long long nc
 int lym1_spectrum_enable(lym1_ctx *ctx, int on);
 int lym1_spectrum_read(lym1_ctx *ctx, double *out, int *n_faces);
 
+/*
+ * Reduced speed of light (Sec. 2.1).  lym1_set_ctilde sets c_tilde (cm/s,
+ * 0 < c_tilde <= c) and with it the RT time step dt_RT = cfl/2 dx /
+ * (c_tilde + max|u|) reported by lym1_get_info; later substeps use both.
+ *
+ * lym1_dynamic_ctilde applies the dynamic choice of Sec. 2.1 on the GPU:
+ *   c_dyn = eps_rsl max_cells { max[1, (a_v tau_0)^(1/3) f_abs] max[|u|, c_s] },
+ *   f_abs = 1 / (1 + (a_v tau_0)^(1/3) tau_c + 0.6 p_d tau_0),
+ *   c_tilde = min[max(ct_min, c_dyn), c],
+ * then moves c_tilde by at most -25 % (x 0.75) or x 4 from its current value,
+ * and sets it as lym1_set_ctilde does.  tau_0 = n_HI sigma0 dx is the cell's
+ * line-centre optical depth and tau_c = rho_dust kappa_abs dx its continuum
+ * absorption depth, with a_v and sigma0 at the cell's temperature.
+ * cs: per-cell sound speed, cm/s, [ny][nx] FP64, host or device pointer, read
+ * during the call; NULL takes that of neutral atomic gas at the cell's
+ * temperature, sqrt(gamma k_B T / (mu m_H)) with gamma = 5/3, mu = 1.22.
+ * The paper's defaults are eps_rsl = 4 and ct_min = 100 km/s = 1e7 cm/s.
+ * The new value is written to *c_tilde_out (host pointer, may be NULL).
+ * Runs on the context's stream and synchronises it.  A lym1_batch holding
+ * the context picks up the new c_tilde before its next substep.
+ * Errors: LYM1_EINVAL for a null ctx, eps_rsl <= 0 or not finite, ct_min < 0
+ * or > c, c_tilde outside (0, c]; LYM1_ENONFINITE if the reduction met only
+ * non-finite terms and left no valid value (c_tilde then stays unchanged);
+ * LYM1_ECUDA if a launch or copy fails.
+ */
+int lym1_set_ctilde(lym1_ctx *ctx, double c_tilde);
+int lym1_dynamic_ctilde(lym1_ctx *ctx, const double *cs, double eps_rsl, double ct_min,
+                        double *c_tilde_out);
+
 #ifdef __cplusplus
 }
 #endif

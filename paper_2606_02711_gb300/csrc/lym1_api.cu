@@ -21,7 +21,8 @@ struct lym1_ctx {
   // temperature field: per [bin][cell] tables (state type) and per-cell constants
   int pt = 0;
   void *Hc = nullptr, *Gc = nullptr;
-  double *gmaxc = nullptr, *Kcc = nullptr, *hkTc = nullptr, *t_2nu = nullptr, *sig0c = nullptr;
+  double *gmaxc = nullptr, *Kcc = nullptr, *hkTc = nullptr, *t_2nu = nullptr, *sig0c = nullptr,
+         *Tc = nullptr;
   float* f_2nu = nullptr;
   // emergent spectrum accumulation (lym1_spectrum_enable)
   double* spec = nullptr;
@@ -29,6 +30,10 @@ struct lym1_ctx {
   long long nc = 0;
   double dx = 0, T = 0, c_tilde = 0, cfl = 0, kabs = 0, kF = 0, dt_cfl = 0, umax = 0;
   double L_tot = 0, device_bytes = 0, gem_max = 1;
+  // bumped when a value baked into the device views changes (c_tilde): a
+  // batch holding this context re-uploads its views before the next launch
+  unsigned view_gen = 0;
+  unsigned long long* ctw = nullptr;  // dynamic c_tilde: running max, result
   long long substeps_done = 0;
   cudaStream_t stream = nullptr;
   BinTables tab;
@@ -329,6 +334,7 @@ struct lym1_batch {
   DeviceView *viewsT = nullptr, *viewsF = nullptr;
   void *itemsT = nullptr, *itemsF = nullptr;
   FinalizeJob* jobs = nullptr;
+  std::vector<unsigned> gens;  // view_gen of each context at the last upload
   int gridT = 0, gridF = 0;
   // tuning state: candidate persistent grids (multiples of the SM count)
   std::vector<int> candT, candF;
@@ -339,6 +345,36 @@ struct lym1_batch {
 };
 
 namespace {
+
+// the two views of a context in a batch: the transport step reads A and
+// writes B, the frequency step reads B and writes A
+void batch_views(const lym1_ctx* c, DeviceView* vT, DeviceView* vF) {
+  *vT = make_view(c, c->dt_cfl);
+  *vF = *vT;
+  vF->J = c->B[0];
+  vF->Hx = c->B[1];
+  vF->Hy = c->B[2];
+  vF->Jo = c->A[0];
+  vF->Hxo = c->A[1];
+  vF->Hyo = c->A[2];
+}
+
+// re-upload, stream-ordered before the next launch, the views of contexts
+// whose c_tilde changed since the last upload (the kernels and the captured
+// graph read the views from device memory)
+int refresh_views(lym1_batch* b, cudaStream_t s) {
+  for (size_t i = 0; i < b->ctxs.size(); ++i) {
+    const lym1_ctx* c = b->ctxs[i];
+    if (c->view_gen == b->gens[i]) continue;
+    DeviceView v[2];
+    batch_views(c, &v[0], &v[1]);
+    LYM1_TRY(cudaMemcpyAsync(b->viewsT + i, &v[0], sizeof(DeviceView), cudaMemcpyHostToDevice, s));
+    LYM1_TRY(cudaMemcpyAsync(b->viewsF + i, &v[1], sizeof(DeviceView), cudaMemcpyHostToDevice, s));
+    LYM1_TRY(cudaStreamSynchronize(s));
+    b->gens[i] = c->view_gen;
+  }
+  return LYM1_OK;
+}
 
 int batch_launch(lym1_batch* b, cudaStream_t s) {
   const int n = static_cast<int>(b->ctxs.size());
@@ -500,6 +536,7 @@ int lym1_create(const lym1_grid* grid, const lym1_groups* groups, const lym1_opa
   if (rc == LYM1_OK) rc = dalloc_t(c, &c->acc, 16);
   if (rc == LYM1_OK) rc = dalloc_t(c, &c->fpart, 2 * kForceBlocks);
   if (rc == LYM1_OK) rc = dalloc_t(c, &c->status, 4);
+  if (rc == LYM1_OK) rc = dalloc_t(c, &c->ctw, 2);
   float** ftabs[] = {&c->f_H, &c->f_dnu, &c->f_G, &c->f_R, &c->f_nbc, &c->f_half};
   for (float** p : ftabs)
     if (rc == LYM1_OK) rc = dalloc_t(c, p, static_cast<size_t>(c->nb));
@@ -518,7 +555,7 @@ int lym1_create(const lym1_grid* grid, const lym1_groups* groups, const lym1_opa
       build_cell_tables(edges, hT.data(), nc, c->dx, c->gray, c->recoil, grid->geometry, &ct);
       if (rc == LYM1_OK) rc = dalloc(c, &c->Hc, nstate * c->selem);
       if (rc == LYM1_OK) rc = dalloc(c, &c->Gc, nstate * c->selem);
-      double** pc[] = {&c->gmaxc, &c->Kcc, &c->hkTc, &c->sig0c};
+      double** pc[] = {&c->gmaxc, &c->Kcc, &c->hkTc, &c->sig0c, &c->Tc};
       for (double** q : pc)
         if (rc == LYM1_OK) rc = dalloc_t(c, q, plane);
       if (rc == LYM1_OK) rc = dalloc_t(c, &c->t_2nu, static_cast<size_t>(c->nb));
@@ -598,6 +635,7 @@ int lym1_create(const lym1_grid* grid, const lym1_groups* groups, const lym1_opa
         cudaMemcpy(c->Kcc, ct.Kc.data(), pb, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(c->hkTc, hk.data(), pb, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(c->sig0c, ct.sigma0.data(), pb, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(c->Tc, op->temp_field, pb, cudaMemcpyDefault) != cudaSuccess ||
         cudaMemcpy(c->t_2nu, t2.data(), sizeof(double) * c->nb, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(c->f_2nu, f2.data(), sizeof(float) * c->nb, cudaMemcpyHostToDevice) != cudaSuccess)
       return fail(LYM1_ECUDA);
@@ -731,6 +769,10 @@ int lym1_substeps(lym1_ctx* c, int n, double dt) {
     }
     if (!c->profiling) return lym1_batch_substeps(c->self_batch, n);
     lym1_batch* b = c->self_batch;
+    {
+      const int rc = refresh_views(b, c->stream);
+      if (rc != LYM1_OK) return rc;
+    }
     int done = 0;
     if (!b->tuned) {  // the tuning substeps (untimed) count toward n
       done = std::min(n, static_cast<int>(b->candT.size()));
@@ -917,16 +959,11 @@ int lym1_batch_create(lym1_ctx* const* ctxs, int n_ctx, lym1_batch** out) {
   std::vector<FinalizeJob> jobs;
   for (int i = 0; i < n_ctx; ++i) {
     lym1_ctx* c = ctxs[i];
-    DeviceView v = make_view(c, c->dt_cfl);
+    DeviceView v, w;
+    batch_views(c, &v, &w);
     vT.push_back(v);
-    DeviceView w = v;  // frequency step reads B, writes A
-    w.J = c->B[0];
-    w.Hx = c->B[1];
-    w.Hy = c->B[2];
-    w.Jo = c->A[0];
-    w.Hxo = c->A[1];
-    w.Hyo = c->A[2];
     vF.push_back(w);
+    b->gens.push_back(c->view_gen);
     const int gx = (c->nx + kTileX - 1) / kTileX, gy = (c->ny + kTileY - 1) / kTileY;
     for (int by = 0; by < gy; ++by)
       for (int bx = 0; bx < gx; ++bx) iT.push_back({i, bx * kTileX, by * kTileY, by * gx + bx});
@@ -983,6 +1020,10 @@ int lym1_batch_substeps(lym1_batch* b, int n) {
   if (n == 0) return LYM1_OK;
   LYM1_TRY(cudaEventRecord(b->ev_in, b->ctx_stream));
   LYM1_TRY(cudaStreamWaitEvent(b->bs, b->ev_in, 0));
+  {
+    const int rc = refresh_views(b, b->bs);
+    if (rc != LYM1_OK) return rc;
+  }
   int done = 0;
   // tuning: the first substeps run once with each candidate persistent grid
   while (!b->tuned && done < n) {
@@ -1103,4 +1144,34 @@ int lym1_spectrum_read(lym1_ctx* c, double* out, int* n_faces) {
   LYM1_TRY(cudaMemcpyAsync(out, c->spec, bytes, cudaMemcpyDefault, c->stream));
   LYM1_TRY(cudaStreamSynchronize(c->stream));
   return LYM1_OK;
+}
+
+int lym1_set_ctilde(lym1_ctx* c, double c_tilde) {
+  if (!c || !(c_tilde > 0.0) || !(c_tilde <= kLight)) return LYM1_EINVAL;
+  c->c_tilde = c_tilde;
+  c->dt_cfl = (c->cfl / 2.0) * (c->dx / (c_tilde + c->umax));
+  c->view_gen += 1;
+  return LYM1_OK;
+}
+
+int lym1_dynamic_ctilde(lym1_ctx* c, const double* cs, double eps_rsl, double ct_min,
+                        double* c_tilde_out) {
+  if (!c || !(eps_rsl > 0.0) || !std::isfinite(eps_rsl) || !(ct_min >= 0.0) ||
+      !(ct_min <= kLight))
+    return LYM1_EINVAL;
+  const double* dcs = nullptr;
+  if (cs) {
+    LYM1_TRY(cudaMemcpyAsync(c->staging, cs, static_cast<size_t>(c->nc) * sizeof(double),
+                             cudaMemcpyDefault, c->stream));
+    dcs = c->staging;
+  }
+  LYM1_TRYK(launch_dynamic_ctilde(c->alpha, c->rho, c->pd, c->ux, c->uy, c->Tc, c->T, dcs, c->kabs,
+                                  c->dx, c->nc, eps_rsl, ct_min, c->c_tilde, c->ctw, c->stream));
+  double ct = 0.0;
+  LYM1_TRY(cudaMemcpyAsync(&ct, c->ctw + 1, sizeof ct, cudaMemcpyDeviceToHost, c->stream));
+  LYM1_TRY(cudaStreamSynchronize(c->stream));
+  if (!(ct > 0.0) || !(ct <= kLight)) return LYM1_ENONFINITE;
+  const int rc = lym1_set_ctilde(c, ct);
+  if (rc == LYM1_OK && c_tilde_out) *c_tilde_out = ct;
+  return rc;
 }

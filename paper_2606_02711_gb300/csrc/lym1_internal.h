@@ -199,6 +199,13 @@ int launch_convert_out(int precision, const void* src, double* dst, long long n,
 int launch_convert_in(int precision, const double* src, void* dst, long long n, void* stream);
 int launch_force_reduce(const double* fx, const double* fy, int nx, int ny, double dx,
                         int geometry, double* part, int nblocks, void* stream);
+// dynamic reduced speed of light: work holds 2 words (the running maximum,
+// then the new c_tilde as a double); Tc per-cell temperatures or nullptr (T),
+// cs per-cell sound speeds or nullptr (neutral gas at T)
+int launch_dynamic_ctilde(const double* alpha, const double* rho, const double* pd,
+                          const double* ux, const double* uy, const double* Tc, double T,
+                          const double* cs, double kabs, double dx, long long nc, double eps,
+                          double ct_min, double prev, unsigned long long* work, void* stream);
 
 // batched (multi-context) launches; kind 0 = transport, 1 = frequency step;
 // items point to device arrays of {ctx, x0, y0, blk}

@@ -274,6 +274,64 @@ int launch_force_reduce(const double* fx, const double* fy, int nx, int ny, doub
   return static_cast<int>(cudaGetLastError());
 }
 
+// Dynamic reduced speed of light (Sec. 2.1).  Per cell: tau_0 = alpha dx, the
+// continuum absorption depth tau_c = rho_d kappa_abs dx, X = (a_v tau_0)^(1/3)
+// with a_v at the cell's temperature, f_abs = 1 / (1 + X tau_c + 0.6 p_d tau_0)
+// and the term max[1, X f_abs] max[|u|, c_s]; c_s from cs, else that of neutral
+// atomic gas at T (gamma = 5/3, mu = 1.22).  The terms are >= 0, so the
+// maximum over cells is a 64-bit atomicMax on their IEEE bit patterns (one
+// per block); NaN terms are dropped by fmax.
+__global__ void __launch_bounds__(256) ctilde_reduce_kernel(
+    const double* alpha, const double* rho, const double* pd, const double* ux, const double* uy,
+    const double* Tc, double T, const double* cs, double kabs, double dx, long long nc,
+    unsigned long long* mx) {
+  __shared__ double red[8];
+  double m = 0.0;
+  for (long long id = static_cast<long long>(blockIdx.x) * 256 + threadIdx.x; id < nc;
+       id += static_cast<long long>(gridDim.x) * 256) {
+    const double Tk = Tc ? Tc[id] : T;
+    const double dnuD = (kNuLya * sqrt((2.0 * kBoltzmann * Tk) / kMassH)) / kLight;
+    const double a_v = kEinsteinA / ((4.0 * kPi) * dnuD);
+    const double tau0 = alpha[id] * dx;
+    const double tauc = (rho[id] * kabs) * dx;
+    const double X = cbrt(a_v * tau0);
+    const double fa = 1.0 / ((1.0 + X * tauc) + (0.6 * pd[id]) * tau0);
+    const double u = sqrt(ux[id] * ux[id] + uy[id] * uy[id]);
+    const double s = cs ? cs[id] : sqrt(((5.0 / 3.0) * (kBoltzmann * Tk)) / (1.22 * kMassH));
+    m = fmax(m, fmax(1.0, X * fa) * fmax(u, s));
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < 8; ++w) m = fmax(m, red[w]);
+    atomicMax(mx, static_cast<unsigned long long>(__double_as_longlong(m)));
+  }
+}
+
+// c_tilde = min[max(c_min, eps_RSL max), c], then at most -25 % / x4 from prev
+__global__ void ctilde_finalize_kernel(const unsigned long long* mx, double eps, double ct_min,
+                                       double prev, double* out) {
+  const double m = __longlong_as_double(static_cast<long long>(*mx));
+  double ct = fmin(fmax(ct_min, eps * m), kLight);
+  ct = fmin(fmax(ct, 0.75 * prev), 4.0 * prev);
+  *out = ct;
+}
+
+int launch_dynamic_ctilde(const double* alpha, const double* rho, const double* pd,
+                          const double* ux, const double* uy, const double* Tc, double T,
+                          const double* cs, double kabs, double dx, long long nc, double eps,
+                          double ct_min, double prev, unsigned long long* work, void* st) {
+  const cudaStream_t s = static_cast<cudaStream_t>(st);
+  cudaError_t e = cudaMemsetAsync(work, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return static_cast<int>(e);
+  ctilde_reduce_kernel<<<grid_for(nc), 256, 0, s>>>(alpha, rho, pd, ux, uy, Tc, T, cs, kabs, dx,
+                                                   nc, work);
+  ctilde_finalize_kernel<<<1, 1, 0, s>>>(work, eps, ct_min, prev,
+                                         reinterpret_cast<double*>(work + 1));
+  return static_cast<int>(cudaGetLastError());
+}
+
 // one block per context: the per-substep reduction of finalize_kernel for a batch
 __global__ void __launch_bounds__(256) finalize_batched_kernel(const FinalizeJob* jobs) {
   const FinalizeJob j = jobs[blockIdx.x];

@@ -78,6 +78,8 @@ SIGNATURES = {
     "lym1_strerror": (C.c_char_p, [C.c_int]),
     "lym1_spectrum_enable": (C.c_int, [C.c_void_p, C.c_int]),
     "lym1_spectrum_read": (C.c_int, [C.c_void_p, _PD, C.POINTER(C.c_int)]),
+    "lym1_set_ctilde": (C.c_int, [C.c_void_p, C.c_double]),
+    "lym1_dynamic_ctilde": (C.c_int, [C.c_void_p, _PD, C.c_double, C.c_double, _PD]),
     "lym1_create": (C.c_int, [C.POINTER(lym1_grid), C.POINTER(lym1_groups),
                               C.POINTER(lym1_opacities), C.POINTER(C.c_void_p)]),
     "lym1_destroy": (None, [C.c_void_p]),
@@ -282,6 +284,27 @@ class Context:
         _check(lib().lym1_spectrum_read(self.handle, out.ctypes.data_as(_PD), C.byref(nf)),
                "lym1_spectrum_read")
         return out
+
+    def set_ctilde(self, c_tilde: float):
+        """Reduced speed of light (cm/s); the RT time step follows it."""
+        _check(lib().lym1_set_ctilde(self.handle, float(c_tilde)), "lym1_set_ctilde")
+        self.dt_cfl = self.info()["dt_cfl"]
+
+    def dynamic_ctilde(self, cs=None, eps_rsl: float = 4.0, ct_min: float = 1.0e7) -> float:
+        """Dynamic reduced speed of light (Sec. 2.1) from the context's fields;
+        cs: per-cell sound speed (cm/s) or None for neutral gas at T.  Returns
+        the new c_tilde."""
+        keep = []
+        p = None
+        if cs is not None:
+            if not hasattr(cs, "data_ptr"):
+                cs = np.broadcast_to(np.asarray(cs, dtype=np.float64), (self.ny, self.nx))
+            p = _ptr(cs, keep)
+        out = C.c_double()
+        _check(lib().lym1_dynamic_ctilde(self.handle, p, float(eps_rsl), float(ct_min),
+                                         C.byref(out)), "lym1_dynamic_ctilde")
+        self.dt_cfl = self.info()["dt_cfl"]
+        return out.value
 
     def info(self) -> dict:
         i = lym1_info()
