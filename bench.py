@@ -398,6 +398,22 @@ def main():
                                     "field": "two-phase 80 K / 2e4 K (seeded k^-4 field)"}
         c3.destroy()
 
+        # the finer frequency grid of Sec. 4.1, Test 2 (q = 1.03: 542 bins by the grid's
+        # truncation rule), headline policy: a cell-update here carries 542 bins, not 194
+        c4 = L.from_cloud(cloud, precision=prec, q=1.03)
+        c4.substeps(4)
+        c4.synchronize()
+        n = 4 * args.fp64_steps
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        c4.substeps(n)
+        b.record()
+        torch.cuda.synchronize()
+        m = a.elapsed_time(b)
+        out["fine_grid"] = {"value": nc * n / (m * 1e-3), "unit": UNIT, "ms_per_step": m / n,
+                            "steps": n, "bins": c4.nb, "q": 1.03}
+        c4.destroy()
+
         if rank == 0 and world == 1 and not args.no_cpu:
             out["cpu_baseline"] = cpu_baseline(cloud, seconds=args.cpu_seconds)
 

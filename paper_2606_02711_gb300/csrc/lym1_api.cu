@@ -1002,10 +1002,12 @@ int lym1_batch_create(lym1_ctx* const* ctxs, int n_ctx, lym1_batch** out) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   if (nsm < 1) nsm = 1;
-  const int rT = b->precision == LYM1_FP64_DET ? resident_blocks_det(0, b->geometry, b->pt)
-                                               : resident_blocks_fast(b->precision, 0, b->geometry, b->pt);
-  const int rF = b->precision == LYM1_FP64_DET ? resident_blocks_det(1, b->geometry, b->pt)
-                                               : resident_blocks_fast(b->precision, 1, b->geometry, b->pt);
+  const int rT = b->precision == LYM1_FP64_DET
+                     ? resident_blocks_det(0, b->geometry, b->pt, b->nb)
+                     : resident_blocks_fast(b->precision, 0, b->geometry, b->pt, b->nb);
+  const int rF = b->precision == LYM1_FP64_DET
+                     ? resident_blocks_det(1, b->geometry, b->pt, b->nb)
+                     : resident_blocks_fast(b->precision, 1, b->geometry, b->pt, b->nb);
   for (int m = 1; m <= rT; ++m) b->candT.push_back(std::min(b->nT, m * nsm));
   const int gf = std::min(b->nF, rF * nsm);
   b->candF.push_back(gf);

@@ -221,8 +221,10 @@ int launch_batched_det(int kind, int geometry, int pt, const DeviceView* views, 
                        int n, int grid, int nb_max, void* stream);
 int launch_batched_fast(int precision, int kind, int geometry, int pt, const DeviceView* views,
                         const void* items, int n, int grid, int nb_max, void* stream);
-int resident_blocks_det(int kind, int geometry, int pt);
-int resident_blocks_fast(int precision, int kind, int geometry, int pt);
+// blocks of one persistent launch resident per SM at nb_max bins (also opts
+// the frequency kernels in to their shared-memory size; call outside capture)
+int resident_blocks_det(int kind, int geometry, int pt, int nb_max);
+int resident_blocks_fast(int precision, int kind, int geometry, int pt, int nb_max);
 int launch_finalize_batched(const FinalizeJob* jobs, int n, void* stream);
 
 inline int transport_blocks(int nx, int ny) {

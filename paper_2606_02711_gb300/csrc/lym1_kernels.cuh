@@ -23,6 +23,7 @@
 
 #include <cstdint>
 
+#include "lym1.h"
 #include "lym1_internal.h"
 
 namespace lym1 {
@@ -1826,12 +1827,22 @@ int launch_freq_batched_t(int geometry, int pt, const DeviceView* views, const B
   return LYM1_GPT(launch_freq_batched_g, views, items, n, grid, nb_max, st);
 }
 
+// The frequency step keeps its per-bin tables in dynamic shared memory, 7
+// words per bin; beside the static ring and reduction buffers that passes the
+// 48 KB a launch may take by default from about 500 bins on.  The kernels are
+// opted in to the size for LYM1_MAX_BINS bins once per device, outside any
+// stream capture (at batch creation and before a direct launch), so that every
+// bin count the ABI accepts launches.  The FP32 transport tables (4 floats per
+// bin) stay under the default at LYM1_MAX_BINS.
+constexpr size_t kFreqSmemMax = sizeof(double) * 7 * LYM1_MAX_BINS;
+
 template <class P, int G, bool PT>
-int max_resident_transport_g() {
+int max_resident_transport_g(int nb_max) {
   int nblk = 0;
   if constexpr (sizeof(typename P::S) == 4)
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nblk, transport_batched_f32<P, G, PT>,
-                                                  kTileX * kTileY, sizeof(float) * 4 * 194);
+                                                  kTileX * kTileY,
+                                                  sizeof(float) * 4 * static_cast<size_t>(nb_max));
   else
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nblk, transport_batched<P, G, PT>,
                                                   kTileX * kTileY, 0);
@@ -1839,21 +1850,23 @@ int max_resident_transport_g() {
 }
 
 template <class P, int G, bool PT>
-int max_resident_freq_g() {
+int max_resident_freq_g(int nb_max) {
+  cudaFuncSetAttribute(freq_batched<P, G, PT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       static_cast<int>(kFreqSmemMax));
   int nblk = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nblk, freq_batched<P, G, PT>, kFreqThreads,
-                                                sizeof(double) * 7 * 194);
+                                                sizeof(double) * 7 * static_cast<size_t>(nb_max));
   return nblk < 1 ? 1 : nblk;
 }
 
 template <class P>
-int max_resident_transport(int geometry, int pt) {
-  return LYM1_GPT(max_resident_transport_g);
+int max_resident_transport(int geometry, int pt, int nb_max) {
+  return LYM1_GPT(max_resident_transport_g, nb_max);
 }
 
 template <class P>
-int max_resident_freq(int geometry, int pt) {
-  return LYM1_GPT(max_resident_freq_g);
+int max_resident_freq(int geometry, int pt, int nb_max) {
+  return LYM1_GPT(max_resident_freq_g, nb_max);
 }
 
 template <class P, int G, bool PT>
@@ -1871,6 +1884,8 @@ int launch_transport_g(const DeviceView& v, cudaStream_t st) {
 template <class P, int G, bool PT>
 int launch_freq_g(const DeviceView& v, cudaStream_t st) {
   const size_t smem = sizeof(double) * 7 * static_cast<size_t>(v.nb);
+  cudaFuncSetAttribute(freq_kernel<P, G, PT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       static_cast<int>(kFreqSmemMax));
   freq_kernel<P, G, PT><<<freq_blocks(v.nc), kFreqThreads, smem, st>>>(v);
   return static_cast<int>(cudaGetLastError());
 }

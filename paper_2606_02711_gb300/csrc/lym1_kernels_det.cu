@@ -23,9 +23,9 @@ int launch_batched_det(int kind, int geometry, int pt, const DeviceView* views, 
   return launch_freq_batched_t<PolDet>(geometry, pt, views, it, n, grid, nb_max, s);
 }
 
-int resident_blocks_det(int kind, int geometry, int pt) {
-  return kind == 0 ? max_resident_transport<PolDet>(geometry, pt)
-                   : max_resident_freq<PolDet>(geometry, pt);
+int resident_blocks_det(int kind, int geometry, int pt, int nb_max) {
+  return kind == 0 ? max_resident_transport<PolDet>(geometry, pt, nb_max)
+                   : max_resident_freq<PolDet>(geometry, pt, nb_max);
 }
 
 

@@ -43,14 +43,14 @@ int launch_batched_fast(int precision, int kind, int geometry, int pt, const Dev
   }
 }
 
-int resident_blocks_fast(int precision, int kind, int geometry, int pt) {
+int resident_blocks_fast(int precision, int kind, int geometry, int pt, int nb_max) {
   switch (precision * 2 + kind) {
-    case 2: return max_resident_transport<PolF64>(geometry, pt);
-    case 3: return max_resident_freq<PolF64>(geometry, pt);
-    case 4: return max_resident_transport<PolMix>(geometry, pt);
-    case 5: return max_resident_freq<PolMix>(geometry, pt);
-    case 6: return max_resident_transport<PolMixFast>(geometry, pt);
-    case 7: return max_resident_freq<PolMixFast>(geometry, pt);
+    case 2: return max_resident_transport<PolF64>(geometry, pt, nb_max);
+    case 3: return max_resident_freq<PolF64>(geometry, pt, nb_max);
+    case 4: return max_resident_transport<PolMix>(geometry, pt, nb_max);
+    case 5: return max_resident_freq<PolMix>(geometry, pt, nb_max);
+    case 6: return max_resident_transport<PolMixFast>(geometry, pt, nb_max);
+    case 7: return max_resident_freq<PolMixFast>(geometry, pt, nb_max);
     default: return 1;
   }
 }

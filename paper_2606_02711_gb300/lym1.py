@@ -399,12 +399,13 @@ def substeps_batched(contexts, n):
     _check(lib().lym1_substeps_batched(arr, len(contexts), int(n)), "lym1_substeps_batched")
 
 
-def from_cloud(cloud, precision=FP64_DET, stream=None, edges=None) -> Context:
-    """A context for a ``workloads.Cloud`` with its sources set."""
+def from_cloud(cloud, precision=FP64_DET, stream=None, edges=None, q=0.0) -> Context:
+    """A context for a ``workloads.Cloud`` with its sources set; edges None
+    takes the paper grid with growth factor q (0: 1.1)."""
     return Context(nx=cloud.nx, ny=cloud.ny, dx=cloud.dx, n_hi=cloud.n_hi, rho_d=cloud.rho_d,
                    p_d=cloud.p_d, ux=cloud.ux, uy=cloud.uy, T=cloud.T, kappa_abs=cloud.kappa_abs,
                    kappa_F=cloud.kappa_F, c_tilde=cloud.c_tilde, cfl=cloud.cfl,
                    recoil=cloud.recoil, freq_step=cloud.freq_step, gray=cloud.gray, edges=edges,
-                   precision=precision, stream=stream, lum=cloud.lum,
+                   precision=precision, stream=stream, lum=cloud.lum, q=q,
                    geometry=getattr(cloud, "geometry", 0), bc=getattr(cloud, "bc", (0, 0, 0, 0)),
                    temp=getattr(cloud, "temp", None))
