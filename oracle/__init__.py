@@ -50,7 +50,8 @@ class Problem(C.Structure):
                 ("c_tilde", _D), ("cfl", _D), ("kappa_abs", _D), ("kappa_F", _D),
                 ("edges", _PD), ("n_hi", _PD), ("rho_d", _PD), ("p_d", _PD),
                 ("ux", _PD), ("uy", _PD), ("lum", _PD), ("geometry", C.c_int),
-                ("bc", C.c_int * 4), ("temp", _PD)]
+                ("bc", C.c_int * 4), ("temp", _PD), ("band_aF", _PD), ("band_kap", _PD),
+                ("band_j", _PD)]
 
 
 class Diag(C.Structure):
@@ -211,7 +212,12 @@ class Oracle:
     def __init__(self, *, nx, ny, dx, edges, T, n_hi, rho_d, p_d, ux, uy, lum,
                  kappa_abs=0.0, kappa_F=0.0, c_tilde=2.99792458e10, cfl=0.4,
                  gray=False, recoil=True, freq_step=True, geometry=0, bc=(0, 0, 0, 0),
-                 temp=None):
+                 temp=None, bands=None):
+        bd = None
+        if bands is not None:
+            # (alpha_F, kappa, emissivity), each [n_bands][ny][nx]
+            bd = [_f64(np.broadcast_to(a, np.shape(bands[0])[:1] + (ny, nx))) for a in bands]
+            edges = np.arange(bd[0].shape[0] + 1, dtype=np.float64)
         self._keep = [_f64(edges)] + [_f64(np.broadcast_to(a, (ny, nx)))
                                       for a in (n_hi, rho_d, p_d, ux, uy, lum)]
         e, n_hi, rho_d, p_d, ux, uy, lum = self._keep
@@ -219,12 +225,15 @@ class Oracle:
         if temp is not None:
             tp = _f64(np.broadcast_to(temp, (ny, nx)))
             self._keep.append(tp)
+        if bd is not None:
+            self._keep += bd
         self.nx, self.ny = int(nx), int(ny)
         self.prob = Problem(self.nx, self.ny, e.size - 1, int(gray), int(recoil), int(freq_step),
                             float(dx), float(T), float(c_tilde), float(cfl), float(kappa_abs),
                             float(kappa_F), _p(e), _p(n_hi), _p(rho_d), _p(p_d), _p(ux), _p(uy),
                             _p(lum), int(geometry), (C.c_int * 4)(*[int(b) for b in bc]),
-                            _p(tp) if tp is not None else None)
+                            _p(tp) if tp is not None else None,
+                            *([_p(a) for a in bd] if bd is not None else [None, None, None]))
         self.ctx = lib().lym1o_create(C.byref(self.prob))
         if not self.ctx:
             raise ValueError("invalid oracle problem")
@@ -246,6 +255,16 @@ class Oracle:
         dnu, nubar, Havg, gem = (np.zeros(nb) for _ in range(4))
         lib().lym1o_tables(self.ctx, _p(dnu), _p(nubar), _p(Havg), _p(gem))
         return {"dnu": dnu, "nubar": nubar, "Havg": Havg, "gem": gem}
+
+    @classmethod
+    def for_bands(cls, *, nx, ny, dx, alpha_F, kappa, emissivity, ux=0.0, uy=0.0,
+                  c_tilde=2.99792458e10, cfl=0.4, geometry=0, bc=(0, 0, 0, 0)):
+        """Broad-band problem (stellar / IR bands): per-[band][cell] flux
+        opacity, absorption opacity (cm^-1) and emissivity (erg/s/cm^3/sr)."""
+        z = np.zeros((ny, nx))
+        return cls(nx=nx, ny=ny, dx=dx, edges=None, T=1e4, n_hi=z, rho_d=z, p_d=z, ux=ux, uy=uy,
+                   lum=z, c_tilde=c_tilde, cfl=cfl, recoil=False, freq_step=False,
+                   geometry=geometry, bc=bc, bands=(alpha_F, kappa, emissivity))
 
     def zero_state(self):
         s = (self.nb, self.ny, self.nx)

@@ -347,6 +347,14 @@ typedef struct {
                             radiation; opacities and velocities are still copied); the
                             mirrored sides of geometry 1 ignore their entry */
     const double *temp;  /* [ny][nx] gas temperature (K) per cell, or NULL for the uniform T */
+    /* Broad bands (Sec. 3, stellar and IR bands: the M1 moment equations per
+     * band without frequency-derivative terms).  With band_aF set, nbins
+     * counts bands, each a frequency-integrated group (dnu = 1, edges
+     * ignored), step 3 is off, and the opacities and emission of each
+     * [band][cell] are given: flux opacity alpha_F (cm^-1), absorption
+     * opacity kappa (cm^-1) and emissivity j (erg s^-1 cm^-3 sr^-1).  The
+     * Lya inputs (n_hi, rho_d, p_d, lum, temp) are not used. */
+    const double *band_aF, *band_kap, *band_j;
 } lym1o_problem;
 
 typedef struct {
@@ -417,8 +425,10 @@ lym1o_ctx *lym1o_create(const lym1o_problem *p)
     if (p->nx < 1 || p->ny < 1 || p->nbins < 1 || p->dx <= 0.0) return NULL;
     for (int s = 0; s < 4; ++s)
         if (p->bc[s] != 0 && p->bc[s] != 1) return NULL;
+    if (p->band_aF && (!p->band_kap || !p->band_j || p->gray || p->temp)) return NULL;
     lym1o_ctx *c = (lym1o_ctx *)calloc(1, sizeof *c);
     c->p = *p;
+    if (p->band_aF) c->p.freq_step = 0;
     int nx = p->nx, ny = p->ny, N = p->nbins;
     double ln[3];
     lym1o_line(p->T, ln);
@@ -428,7 +438,7 @@ lym1o_ctx *lym1o_create(const lym1o_problem *p)
     c->hkT = O_HPL / (O_KB * p->T);
     double *dnu = malloc(N * sizeof(double)), *nub = malloc(N * sizeof(double));
     double *Hv = malloc(N * sizeof(double)), *w = malloc(N * sizeof(double));
-    c->eta = lym1o_bin_tables(N, p->edges, p->T, dnu, nub, Hv, w);
+    c->eta = p->band_aF ? 1.0 : lym1o_bin_tables(N, p->edges, p->T, dnu, nub, Hv, w);
     c->nb = p->gray ? 1 : N;
     int nb = c->nb;
     c->dnu = malloc(nb * sizeof(double));
@@ -447,6 +457,15 @@ lym1o_ctx *lym1o_create(const lym1o_problem *p)
         c->gem[0] = 1.0 / fourpiV;
         c->Rk[0] = 0.0;
         c->half[0] = 0.5;
+    } else if (p->band_aF) {
+        for (int k = 0; k < N; ++k) {
+            c->dnu[k] = 1.0;
+            c->nubar[k] = O_NU_LYA;
+            c->Havg[k] = 1.0;
+            c->gem[k] = 0.0;
+            c->Rk[k] = 0.0;
+            c->half[k] = 0.5;
+        }
     } else {
         for (int k = 0; k < N; ++k) {
             c->dnu[k] = dnu[k];
@@ -493,6 +512,8 @@ lym1o_ctx *lym1o_create(const lym1o_problem *p)
         }
         if (p->gray) {
             c->gemc[0] = 1.0 / (4.0 * O_PI);
+        } else if (p->band_aF) {
+            for (int k = 0; k < N; ++k) c->gemc[k] = 0.0;
         } else {
             /* j_k = (L_cell / (2 pi Vol)) w_k / (4 pi dnu_k) */
             double *t1 = malloc(N * sizeof(double)), *t2 = malloc(N * sizeof(double));
@@ -893,6 +914,8 @@ int lym1o_substep_cyl(const lym1o_ctx *c, double dt, const double *J, const doub
 #define HAV(k, id) (c->Hc ? c->Hc[(size_t)(k) * nc + (id)] : c->Havg[k])
 #define GEMK(k, id) (c->Gc ? c->Gc[(size_t)(k) * nc + (id)] : c->gem[k])
 #define GEMC(k, id) (c->Gc ? c->Gc[(size_t)(k) * nc + (id)] : c->gemc[k])
+/* a band's own [band][cell] input */
+#define BND(a, k, id) (p->a[(size_t)(k) * nc + (id)])
 
 /* step 3 of one cell: the per-bin tables or the cell's own (temperature field) */
 static void o_freq_of_cell(const lym1o_ctx *c, size_t id, size_t nc, const double *nbc,
@@ -946,7 +969,7 @@ int lym1o_substep(const lym1o_ctx *c, double dt, const double *J, const double *
 
     for (int k = 0; k < nb; ++k) {
         const double *Jk = J + (size_t)k * nc, *Hxk = Hx + (size_t)k * nc, *Hyk = Hy + (size_t)k * nc;
-#define AF(id) (c->alpha[id] * HAV(k, id) + p->rho_d[id] * p->kappa_F)
+#define AF(id) (p->band_aF ? BND(band_aF, k, id) : c->alpha[id] * HAV(k, id) + p->rho_d[id] * p->kappa_F)
         /* x faces: face i sits between cells i-1 and i, i = 0..nx */
 #pragma omp parallel for schedule(static)
         for (int j = 0; j < ny; ++j)
@@ -1008,6 +1031,11 @@ int lym1o_substep(const lym1o_ctx *c, double dt, const double *J, const double *
                 double kap = p->rho_d[id] * p->kappa_abs + p->p_d[id] * aH;
                 double aF = aH + p->rho_d[id] * p->kappa_F;
                 double js = p->lum[id] * GEMK(k, id);
+                if (p->band_aF) {
+                    kap = BND(band_kap, k, id);
+                    aF = BND(band_aF, k, id);
+                    js = BND(band_j, k, id);
+                }
                 double J2 = (J1 + cdt * js) / (1.0 + cdt * kap);
                 double Hx2 = Hx1 / (1.0 + cdt * aF);
                 double Hy2 = Hy1 / (1.0 + cdt * aF);
@@ -1023,6 +1051,10 @@ int lym1o_substep(const lym1o_ctx *c, double dt, const double *J, const double *
             double aH = c->alpha[id] * HAV(k, id);
             double kap = p->rho_d[id] * p->kappa_abs + p->p_d[id] * aH;
             double js = p->lum[id] * GEMK(k, id);
+            if (p->band_aF) {
+                kap = BND(band_kap, k, id);
+                js = BND(band_j, k, id);
+            }
             o_kadd(&s_em, c->dnu[k] * (cdt * js));
             o_kadd(&s_ab, c->dnu[k] * (cdt * (kap * Jo[kid])));
             o_kadd(&s_wk, c->dnu[k] * (cdt * (Wk[id] / O_C)));
@@ -1177,7 +1209,7 @@ int lym1o_substep_cyl(const lym1o_ctx *c, double dt, const double *J, const doub
 
     for (int k = 0; k < nb; ++k) {
         const double *Jk = J + (size_t)k * nc, *Hxk = Hx + (size_t)k * nc, *Hyk = Hy + (size_t)k * nc;
-#define AFC(id) (c->alpha[id] * HAV(k, id) + p->rho_d[id] * p->kappa_F)
+#define AFC(id) (p->band_aF ? BND(band_aF, k, id) : c->alpha[id] * HAV(k, id) + p->rho_d[id] * p->kappa_F)
         /* R faces: face i between cells i-1 and i */
 #pragma omp parallel for schedule(static)
         for (int j = 0; j < ny; ++j)
@@ -1255,6 +1287,11 @@ int lym1o_substep_cyl(const lym1o_ctx *c, double dt, const double *J, const doub
                 double kap = p->rho_d[id] * p->kappa_abs + p->p_d[id] * aH;
                 double aF = aH + p->rho_d[id] * p->kappa_F;
                 double js = (p->lum[id] / c->V2pi[i]) * GEMC(k, id);
+                if (p->band_aF) {
+                    kap = BND(band_kap, k, id);
+                    aF = BND(band_aF, k, id);
+                    js = BND(band_j, k, id);
+                }
                 double J2 = (J1 + cdt * js) / (1.0 + cdt * kap);
                 double Hx2 = Hx1 / (1.0 + cdt * aF);
                 double Hy2 = Hy1 / (1.0 + cdt * aF);
@@ -1270,6 +1307,10 @@ int lym1o_substep_cyl(const lym1o_ctx *c, double dt, const double *J, const doub
             double aH = c->alpha[id] * HAV(k, id);
             double kap = p->rho_d[id] * p->kappa_abs + p->p_d[id] * aH;
             double js = (p->lum[id] / c->V2pi[i]) * GEMC(k, id);
+            if (p->band_aF) {
+                kap = BND(band_kap, k, id);
+                js = BND(band_j, k, id);
+            }
             o_kadd(&s_em, c->V2pi[i] * (c->dnu[k] * (cdt * js)));
             o_kadd(&s_ab, c->V2pi[i] * (c->dnu[k] * (cdt * (kap * Jo[kid]))));
             o_kadd(&s_wk, c->V2pi[i] * (c->dnu[k] * (cdt * (Wk[id] / O_C))));
