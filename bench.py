@@ -414,6 +414,25 @@ def main():
                             "steps": n, "bins": c4.nb, "q": 1.03}
         c4.destroy()
 
+        # the seven stellar/IR bands of Sec. 3 on the same cloud: per band the
+        # transport and source step, no frequency step, headline policy
+        aF, ka, je = wl.stellar_bands(cloud)
+        c5 = L.Context.for_bands(nx=cloud.nx, ny=cloud.ny, dx=cloud.dx, ux=cloud.ux, uy=cloud.uy,
+                                 alpha_F=aF, kappa=ka, emissivity=je, precision=prec)
+        c5.substeps(4)
+        c5.synchronize()
+        n = 16 * args.fp64_steps
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        c5.substeps(n)
+        b.record()
+        torch.cuda.synchronize()
+        m = a.elapsed_time(b)
+        out["stellar_bands"] = {"value": nc * n / (m * 1e-3), "unit": UNIT, "ms_per_step": m / n,
+                                "steps": n, "bands": c5.nb,
+                                "note": "cell-updates over 7 bands (IR, opt, FUV, LW, EUV1-3)"}
+        c5.destroy()
+
         if rank == 0 and world == 1 and not args.no_cpu:
             out["cpu_baseline"] = cpu_baseline(cloud, seconds=args.cpu_seconds)
 

@@ -349,6 +349,47 @@ int lym1_set_ctilde(lym1_ctx *ctx, double c_tilde);
 int lym1_dynamic_ctilde(lym1_ctx *ctx, const double *cs, double eps_rsl, double ct_min,
                         double *c_tilde_out);
 
+/*
+ * Broad bands (Sec. 3: the stellar bands IR, optical, FUV, LW, EUV1-3 are
+ * solved, like Lya, with the M1 moment equations of Sec. 2.1 but without the
+ * frequency-derivative terms; the IR band's dust emission enters as its
+ * emissivity).  A band context advances n_bands frequency-integrated groups
+ * with the transport of Sec. 2.1 step 1 (closure, corrected GLF fluxes with
+ * each band's own face optical depth, advection and -grad u : K / c) and the
+ * implicit absorption/emission of step 2:
+ *   (J'' - J') / (c_tilde dt) = j - kappa J'',  (H'' - H') / (c_tilde dt) = -alpha_F H'',
+ * and the force of Sec. 2.3 summed over bands.  There is no frequency step.
+ * Per-[band][cell] inputs, [n_bands][ny][nx] FP64, host or device pointers,
+ * copied during the call, each finite and >= 0:
+ *   alpha_F     flux opacity, cm^-1 (absorption plus scattering weighted by 1 - g)
+ *   kappa       absorption opacity, cm^-1
+ *   emissivity  j, erg s^-1 cm^-3 sr^-1
+ * The state J, H of each band is frequency integrated (erg s^-1 cm^-2 sr^-1)
+ * and the bin width of every band is 1.  Every other call (substeps, step,
+ * state, moments, force, diagnostics with M_F over the total emitted power,
+ * spectrum, profiling, set_ctilde) works on a band context as on a Lya one;
+ * lym1_set_sources and lym1_dynamic_ctilde return LYM1_EINVAL, and band
+ * contexts cannot join a lym1_batch (no frequency step: each substep is one
+ * transport launch and one reduction).
+ * lym1_bands_update replaces the three inputs (opacities that follow the
+ * chemistry and dust between hydro steps); the state is kept.
+ * Errors: LYM1_EINVAL for null pointers, n_bands outside 1..LYM1_MAX_BINS, a
+ * bad grid or precision, or any input value negative or not finite (an update
+ * that fails changes nothing); LYM1_ENOMEM, LYM1_ECUDA, LYM1_ENODEVICE as for
+ * lym1_create.
+ */
+typedef struct {
+  int n_bands;
+  const double *alpha_F;
+  const double *kappa;
+  const double *emissivity;
+} lym1_bands;
+int lym1_create_bands(const lym1_grid *grid, const lym1_bands *bands, const double *ux,
+                      const double *uy, double c_tilde, double cfl, int precision,
+                      void *cuda_stream, lym1_ctx **out);
+int lym1_bands_update(lym1_ctx *ctx, const double *alpha_F, const double *kappa,
+                      const double *emissivity);
+
 #ifdef __cplusplus
 }
 #endif

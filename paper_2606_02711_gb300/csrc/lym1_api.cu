@@ -24,6 +24,9 @@ struct lym1_ctx {
   double *gmaxc = nullptr, *Kcc = nullptr, *hkTc = nullptr, *t_2nu = nullptr, *sig0c = nullptr,
          *Tc = nullptr;
   float* f_2nu = nullptr;
+  // broad bands (pt = 2): Hc = alpha_F, Gc = emissivity, Kb = kappa per [band][cell]
+  int bands = 0;
+  void* Kb = nullptr;
   // emergent spectrum accumulation (lym1_spectrum_enable)
   double* spec = nullptr;
   int spec_on = 0;
@@ -186,6 +189,7 @@ DeviceView make_view(const lym1_ctx* c, double dt) {
   v.pt = c->pt;
   v.Hc = c->Hc;
   v.Gc = c->Gc;
+  v.Kb = c->Kb;
   v.gmaxc = c->gmaxc;
   v.Kcc = c->Kcc;
   v.hkTc = c->hkTc;
@@ -313,6 +317,58 @@ int one_substep(lym1_ctx* c, double dt) {
                               transport_blocks(c->nx, c->ny), c->acc, 0, c->stream));
   }
   c->substeps_done += 1;
+  return LYM1_OK;
+}
+
+// Validates and uploads the per-[band][cell] inputs of a band context (host or
+// device pointers, FP64): flux opacity and absorption opacity into Hc and Kb,
+// emissivity into Gc (FP32 policies: over its per-cell maximum, kept in gmaxc,
+// so that the kernels' jsc = lum gmax with lum = 1 restores it).  Nothing is
+// changed unless every value is finite and >= 0.
+int bands_upload(lym1_ctx* c, const double* aF, const double* kap, const double* j) {
+  if (!aF || !kap || !j) return LYM1_EINVAL;
+  const size_t plane = static_cast<size_t>(c->nc), n = plane * c->nb;
+  std::vector<double> ha(n), hk(n), hj(n);
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return LYM1_ECUDA;
+  if (cudaMemcpy(ha.data(), aF, n * sizeof(double), cudaMemcpyDefault) != cudaSuccess ||
+      cudaMemcpy(hk.data(), kap, n * sizeof(double), cudaMemcpyDefault) != cudaSuccess ||
+      cudaMemcpy(hj.data(), j, n * sizeof(double), cudaMemcpyDefault) != cudaSuccess) {
+    cudaGetLastError();
+    return LYM1_EINVAL;
+  }
+  for (size_t q = 0; q < n; ++q)
+    if (!(ha[q] >= 0.0) || !(hk[q] >= 0.0) || !(hj[q] >= 0.0) || !std::isfinite(ha[q]) ||
+        !std::isfinite(hk[q]) || !std::isfinite(hj[q]))
+      return LYM1_EINVAL;
+  // total emitted power over the cells (ring volumes pi (2i + 1) dx^3 of the
+  // half-space Z > 0 on the axisymmetric grid), the M_F normaliser
+  const double V = (c->dx * c->dx) * c->dx;
+  double L = 0.0;
+  for (size_t q = 0; q < n; ++q) {
+    const double Vc = c->geometry == 1 ? kPi * (2.0 * static_cast<double>((q % plane) % c->nx) + 1.0) * V : V;
+    L += (4.0 * kPi) * hj[q] * Vc;
+  }
+  if (c->selem == 8) {
+    LYM1_TRY(cudaMemcpy(c->Hc, ha.data(), n * sizeof(double), cudaMemcpyHostToDevice));
+    LYM1_TRY(cudaMemcpy(c->Kb, hk.data(), n * sizeof(double), cudaMemcpyHostToDevice));
+    LYM1_TRY(cudaMemcpy(c->Gc, hj.data(), n * sizeof(double), cudaMemcpyHostToDevice));
+  } else {
+    std::vector<double> gmax(plane, 0.0);
+    for (size_t q = 0; q < n; ++q) gmax[q % plane] = std::max(gmax[q % plane], hj[q]);
+    for (double& g : gmax)
+      if (!(g > 0.0)) g = 1.0;
+    std::vector<float> fa(n), fk(n), fj(n);
+    for (size_t q = 0; q < n; ++q) {
+      fa[q] = static_cast<float>(ha[q]);
+      fk[q] = static_cast<float>(hk[q]);
+      fj[q] = static_cast<float>(hj[q] / gmax[q % plane]);
+    }
+    LYM1_TRY(cudaMemcpy(c->Hc, fa.data(), n * sizeof(float), cudaMemcpyHostToDevice));
+    LYM1_TRY(cudaMemcpy(c->Kb, fk.data(), n * sizeof(float), cudaMemcpyHostToDevice));
+    LYM1_TRY(cudaMemcpy(c->Gc, fj.data(), n * sizeof(float), cudaMemcpyHostToDevice));
+    LYM1_TRY(cudaMemcpy(c->gmaxc, gmax.data(), plane * sizeof(double), cudaMemcpyHostToDevice));
+  }
+  c->L_tot = L;
   return LYM1_OK;
 }
 
@@ -458,8 +514,8 @@ const char* lym1_strerror(int s) {
   }
 }
 
-int lym1_create(const lym1_grid* grid, const lym1_groups* groups, const lym1_opacities* op,
-                lym1_ctx** out) {
+static int create_impl(const lym1_grid* grid, const lym1_groups* groups, const lym1_opacities* op,
+                       const lym1_bands* bands, lym1_ctx** out) {
   if (!out) return LYM1_EINVAL;
   *out = nullptr;
   if (!grid || !groups || !op) return LYM1_EINVAL;
@@ -541,7 +597,18 @@ int lym1_create(const lym1_grid* grid, const lym1_groups* groups, const lym1_opa
   for (float** p : ftabs)
     if (rc == LYM1_OK) rc = dalloc_t(c, p, static_cast<size_t>(c->nb));
   CellTables ct;
-  if (op->temp_field) {
+  if (bands) {
+    // broad bands: per-[band][cell] tables in the state type; alpha = n_HI
+    // sigma0c = 1 and rho_d = 0, so that the kernels' alpha_F = alpha Hc +
+    // rho_d kappa_F is the band's own flux opacity
+    c->pt = 2;
+    c->bands = 1;
+    if (rc == LYM1_OK) rc = dalloc(c, &c->Hc, nstate * c->selem);
+    if (rc == LYM1_OK) rc = dalloc(c, &c->Gc, nstate * c->selem);
+    if (rc == LYM1_OK) rc = dalloc(c, &c->Kb, nstate * c->selem);
+    if (rc == LYM1_OK) rc = dalloc_t(c, &c->gmaxc, plane);
+    if (rc == LYM1_OK) rc = dalloc_t(c, &c->sig0c, plane);
+  } else if (op->temp_field) {
     // per-cell A0 on the host (the field may live on the device)
     std::vector<double> hT(plane);
     if (cudaMemcpy(hT.data(), op->temp_field, plane * sizeof(double), cudaMemcpyDefault) != cudaSuccess) {
@@ -604,7 +671,12 @@ int lym1_create(const lym1_grid* grid, const lym1_groups* groups, const lym1_opa
       cudaMemcpyAsync(c->rho, op->rho_dust, pb, cudaMemcpyDefault, s) != cudaSuccess ||
       cudaMemcpyAsync(c->pd, op->p_d, pb, cudaMemcpyDefault, s) != cudaSuccess)
     return fail(LYM1_ECUDA);
-  if (c->pt) {
+  if (c->pt == 2) {
+    std::vector<double> ones(plane, 1.0);
+    if (cudaMemcpy(c->sig0c, ones.data(), pb, cudaMemcpyHostToDevice) != cudaSuccess)
+      return fail(LYM1_ECUDA);
+  }
+  if (c->pt == 1) {
     // per-[bin][cell] tables in the state type (FP32 policies: G / gmax)
     const size_t nsv = ct.H.size();
     if (c->selem == 8) {
@@ -704,8 +776,60 @@ int lym1_create(const lym1_grid* grid, const lym1_groups* groups, const lym1_opa
   if (cudaMemcpyAsync(c->acc + 13, &eunit, sizeof(double), cudaMemcpyHostToDevice, s) != cudaSuccess)
     return fail(LYM1_ECUDA);
   if (reset_counters(c) != LYM1_OK || cudaStreamSynchronize(s) != cudaSuccess) return fail(LYM1_ECUDA);
+  if (bands) {
+    // lum = 1 per cell: the kernels' j = lum Gc is then the band emissivity
+    std::vector<double> ones(plane, 1.0);
+    if (cudaMemcpy(c->lum, ones.data(), pb, cudaMemcpyHostToDevice) != cudaSuccess)
+      return fail(LYM1_ECUDA);
+    const int rb = bands_upload(c, bands->alpha_F, bands->kappa, bands->emissivity);
+    if (rb != LYM1_OK) return fail(rb);
+  }
   *out = c;
   return LYM1_OK;
+}
+
+int lym1_create(const lym1_grid* grid, const lym1_groups* groups, const lym1_opacities* op,
+                lym1_ctx** out) {
+  return create_impl(grid, groups, op, nullptr, out);
+}
+
+int lym1_create_bands(const lym1_grid* grid, const lym1_bands* bands, const double* ux,
+                      const double* uy, double c_tilde, double cfl, int precision,
+                      void* cuda_stream, lym1_ctx** out) {
+  if (!out) return LYM1_EINVAL;
+  *out = nullptr;
+  if (!grid || !bands || !ux || !uy || !bands->alpha_F || !bands->kappa || !bands->emissivity)
+    return LYM1_EINVAL;
+  if (bands->n_bands < 1 || bands->n_bands > LYM1_MAX_BINS) return LYM1_EINVAL;
+  if (grid->nx < 1 || grid->ny < 1) return LYM1_EINVAL;
+  const long long nc = static_cast<long long>(grid->nx) * grid->ny;
+  if (nc > (1LL << 31)) return LYM1_EINVAL;
+  const size_t plane = static_cast<size_t>(nc);
+  std::vector<double> ones(plane, 1.0), zeros(plane, 0.0), edges(bands->n_bands + 1);
+  for (int k = 0; k <= bands->n_bands; ++k) edges[k] = static_cast<double>(k);
+  lym1_groups g;
+  std::memset(&g, 0, sizeof g);
+  g.n_bins = bands->n_bands;
+  g.edges_dnu_hz = edges.data();
+  lym1_opacities o;
+  std::memset(&o, 0, sizeof o);
+  o.n_hi = ones.data();
+  o.rho_dust = zeros.data();
+  o.p_d = zeros.data();
+  o.ux = ux;
+  o.uy = uy;
+  o.temp_K = 1.0e4;
+  o.c_tilde = c_tilde;
+  o.cfl = cfl;
+  o.precision = precision;
+  o.cuda_stream = cuda_stream;
+  return create_impl(grid, &g, &o, bands, out);
+}
+
+int lym1_bands_update(lym1_ctx* c, const double* alpha_F, const double* kappa,
+                      const double* emissivity) {
+  if (!c || !c->bands) return LYM1_EINVAL;
+  return bands_upload(c, alpha_F, kappa, emissivity);
 }
 
 void lym1_destroy(lym1_ctx* c) {
@@ -719,7 +843,7 @@ void lym1_destroy(lym1_ctx* c) {
 }
 
 int lym1_set_sources(lym1_ctx* c, const double* lum) {
-  if (!c || !lum) return LYM1_EINVAL;
+  if (!c || !lum || c->bands) return LYM1_EINVAL;
   const size_t n = static_cast<size_t>(c->nc);
   LYM1_TRY(cudaMemcpyAsync(c->lum, lum, n * sizeof(double), cudaMemcpyDefault, c->stream));
   // axisymmetric grid: the kernels take the luminosity per unit ring volume
@@ -1158,7 +1282,7 @@ int lym1_set_ctilde(lym1_ctx* c, double c_tilde) {
 
 int lym1_dynamic_ctilde(lym1_ctx* c, const double* cs, double eps_rsl, double ct_min,
                         double* c_tilde_out) {
-  if (!c || !(eps_rsl > 0.0) || !std::isfinite(eps_rsl) || !(ct_min >= 0.0) ||
+  if (!c || c->bands || !(eps_rsl > 0.0) || !std::isfinite(eps_rsl) || !(ct_min >= 0.0) ||
       !(ct_min <= kLight))
     return LYM1_EINVAL;
   const double* dcs = nullptr;

@@ -154,6 +154,9 @@ struct DeviceView {
   int pt = 0;
   const void* Hc = nullptr;
   const void* Gc = nullptr;
+  // broad bands (pt = 2): Hc holds alpha_F, Gc the emissivity (over gmaxc in
+  // FP32) and Kb the absorption opacity kappa of each [band][cell]
+  const void* Kb = nullptr;
   const double* gmaxc = nullptr;
   const double* Kcc = nullptr;
   const double* hkTc = nullptr;

@@ -371,7 +371,7 @@ __device__ __forceinline__ double block_max(double v, double* red) {
 }
 
 // ------------------------------------------------------------ transport kernel
-template <class P, int G, bool PT>
+template <class P, int G, int PT>
 __device__ __forceinline__ void transport_tile(const DeviceView& v, int x0, int y0, int blk) {
   using S = typename P::S;
   using F = typename P::F;
@@ -387,6 +387,7 @@ __device__ __forceinline__ void transport_tile(const DeviceView& v, int x0, int 
   __shared__ F qH[PT ? QY : 1][PT ? QX : 1];  // temperature field: <H>_k of the one-cell halo
   const S* __restrict__ Hcs = static_cast<const S*>(v.Hc);
   const S* __restrict__ Gcs = static_cast<const S*>(v.Gc);
+  const S* __restrict__ Kbs = static_cast<const S*>(v.Kb);  // bands: kappa per [band][cell]
   __shared__ double red[NT / 32];
 
   const S* __restrict__ Jin = static_cast<const S*>(v.J);
@@ -557,7 +558,7 @@ __device__ __forceinline__ void transport_tile(const DeviceView& v, int x0, int 
         }
       }
       const I aH = alpha_c * (PT ? I(Hcs[base + cell]) : I(Hk_d));
-      const I kap = rho_c * kabs + pd_c * aH;
+      const I kap = (PT == 2) ? I(Kbs[base + cell]) : rho_c * kabs + pd_c * aH;
       const I aF = aH + rho_c * kF;
       // j_k = L w_k / (4 pi V dnu_k): formed in FP64 (L ~ 1e39 erg/s and
       // w_k / (4 pi V dnu_k) ~ 1e-58 are both outside the FP32 range); on the
@@ -646,7 +647,7 @@ __device__ __forceinline__ void transport_tile(const DeviceView& v, int x0, int 
 }
 
 
-template <class P, int G, bool PT>
+template <class P, int G, int PT>
 __global__ void __launch_bounds__(kTileX* kTileY) transport_kernel(DeviceView v) {
   transport_tile<P, G, PT>(v, blockIdx.x * kTileX, blockIdx.y * kTileY, blockIdx.y * gridDim.x + blockIdx.x);
 }
@@ -753,7 +754,7 @@ __device__ __forceinline__ void face_flux_f32(float Jm, float nm, float tm, floa
 // distances) of a thread's faces do not depend on the bin and stay in
 // registers.  The implicit source step runs in type I (FP64 for LYM1_MIXED,
 // FP32 for LYM1_MIXED_FAST).
-template <class P, int G, bool PT>
+template <class P, int G, int PT>
 __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, int y0, int blk) {
   using I = typename P::I;
   constexpr int TX = kTileX, TY = kTileY, SX = TX + 4, SY = TY + 4;
@@ -778,6 +779,7 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
   // temperature field: <H>_k and gem_k / gmax per [k][cell]
   const float* __restrict__ Hcf = static_cast<const float*>(v.Hc);
   const float* __restrict__ Gcf = static_cast<const float*>(v.Gc);
+  const float* __restrict__ Kbf = static_cast<const float*>(v.Kb);  // bands: kappa per [band][cell]
 
   const int nx = v.nx, ny = v.ny, nb = v.nb;
   const long long nc = v.nc;
@@ -1015,7 +1017,7 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
         aH = alpha_c * (PT ? Hcf[base + cell] : Hk);
         dnu = tb.y;
       }
-      const I kap = rho_c * kabs + pd_c * aH;
+      const I kap = (PT == 2) ? I(Kbf[base + cell]) : rho_c * kabs + pd_c * aH;
       const I aF = aH + rho_c * kF;
       I js;
       if constexpr (sizeof(I) == 8)
@@ -1108,7 +1110,7 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
   }
 }
 
-template <class P, int G, bool PT>
+template <class P, int G, int PT>
 __global__ void __launch_bounds__(kTileX* kTileY, 3) transport_kernel_f32(DeviceView v) {
   transport_tile_f32<P, G, PT>(v, blockIdx.x * kTileX, blockIdx.y * kTileY,
                            blockIdx.y * gridDim.x + blockIdx.x);
@@ -1179,7 +1181,7 @@ __device__ __forceinline__ void freq_coef(typename P::F Jc, typename P::F Hxc, t
   }
 }
 
-template <class P, int G, bool PT>
+template <class P, int G, int PT>
 __device__ __forceinline__ void freq_block(const DeviceView& v, int blk) {
   using S = typename P::S;
   using F = typename P::F;
@@ -1470,7 +1472,7 @@ __device__ __forceinline__ void fence_mbar_init() {
 // streamed through the ring (cell count a multiple of 4, so that every row
 // segment starts on a 16-byte boundary and is a whole number of 16 bytes).
 // Same arithmetic, in the same order, as freq_block.
-template <class P, int G, bool PT>
+template <class P, int G, int PT>
 __device__ __forceinline__ void freq_block_bulk(const DeviceView& v, int blk) {
   using F = typename P::F;
   using I = typename P::I;
@@ -1728,7 +1730,7 @@ __device__ __forceinline__ void freq_block_bulk(const DeviceView& v, int blk) {
 
 // FP32 state with a cell count that is a multiple of 4 takes the bulk-copy
 // pipeline; everything else the register-prefetch sweep
-template <class P, int G, bool PT>
+template <class P, int G, int PT>
 __device__ __forceinline__ void freq_dispatch(const DeviceView& v, int blk) {
   if constexpr (sizeof(typename P::S) == 4) {
     if ((v.nc & 3) == 0) {
@@ -1741,7 +1743,7 @@ __device__ __forceinline__ void freq_dispatch(const DeviceView& v, int blk) {
 
 // FP32 state: at most 64 registers so that 8 blocks (32 warps) per SM keep
 // enough loads in flight for the latency-bound bin sweeps
-template <class P, int G, bool PT>
+template <class P, int G, int PT>
 __global__ void __launch_bounds__(kFreqThreads, sizeof(typename P::S) == 4 ? 8 : 1)
     freq_kernel(DeviceView v) {
   freq_dispatch<P, G, PT>(v, blockIdx.x);
@@ -1756,7 +1758,7 @@ struct BatchItem {
   int ctx, x0, y0, blk;
 };
 
-template <class P, int G, bool PT>
+template <class P, int G, int PT>
 __global__ void __launch_bounds__(kTileX* kTileY) transport_batched(const DeviceView* views,
                                                                     const BatchItem* items, int n) {
   for (int i = blockIdx.x; i < n; i += gridDim.x) {
@@ -1767,7 +1769,7 @@ __global__ void __launch_bounds__(kTileX* kTileY) transport_batched(const Device
   }
 }
 
-template <class P, int G, bool PT>
+template <class P, int G, int PT>
 __global__ void __launch_bounds__(kTileX* kTileY, 3) transport_batched_f32(const DeviceView* views,
                                                                            const BatchItem* items,
                                                                            int n) {
@@ -1779,7 +1781,7 @@ __global__ void __launch_bounds__(kTileX* kTileY, 3) transport_batched_f32(const
   }
 }
 
-template <class P, int G, bool PT>
+template <class P, int G, int PT>
 __global__ void __launch_bounds__(kFreqThreads, sizeof(typename P::S) == 4 ? 8 : 1)
     freq_batched(const DeviceView* views, const BatchItem* items, int n) {
   for (int i = blockIdx.x; i < n; i += gridDim.x) {
@@ -1790,7 +1792,7 @@ __global__ void __launch_bounds__(kFreqThreads, sizeof(typename P::S) == 4 ? 8 :
   }
 }
 
-template <class P, int G, bool PT>
+template <class P, int G, int PT>
 int launch_transport_batched_g(const DeviceView* views, const BatchItem* items, int n, int grid,
                                int nb_max, cudaStream_t st) {
   if constexpr (sizeof(typename P::S) == 4) {
@@ -1802,7 +1804,7 @@ int launch_transport_batched_g(const DeviceView* views, const BatchItem* items, 
   return static_cast<int>(cudaGetLastError());
 }
 
-template <class P, int G, bool PT>
+template <class P, int G, int PT>
 int launch_freq_batched_g(const DeviceView* views, const BatchItem* items, int n, int grid,
                           int nb_max, cudaStream_t st) {
   const size_t smem = sizeof(double) * 7 * static_cast<size_t>(nb_max);
@@ -1811,9 +1813,18 @@ int launch_freq_batched_g(const DeviceView* views, const BatchItem* items, int n
 }
 
 // (geometry, temperature mode) -> template instance
-#define LYM1_GPT(F_, ...)                                              \
-  (geometry == 1 ? (pt ? F_<P, 1, true>(__VA_ARGS__) : F_<P, 1, false>(__VA_ARGS__)) \
-                 : (pt ? F_<P, 0, true>(__VA_ARGS__) : F_<P, 0, false>(__VA_ARGS__)))
+// transport: pt 0 = uniform temperature, 1 = temperature field, 2 = broad bands
+#define LYM1_GPT(F_, ...)                                                               \
+  (geometry == 1 ? (pt == 2   ? F_<P, 1, 2>(__VA_ARGS__)                                \
+                    : pt == 1 ? F_<P, 1, 1>(__VA_ARGS__)                                \
+                              : F_<P, 1, 0>(__VA_ARGS__))                               \
+                 : (pt == 2   ? F_<P, 0, 2>(__VA_ARGS__)                                \
+                    : pt == 1 ? F_<P, 0, 1>(__VA_ARGS__)                                \
+                              : F_<P, 0, 0>(__VA_ARGS__)))
+// frequency step: bands have none (pt 2 is refused before any launch)
+#define LYM1_GPT_F(F_, ...)                                                        \
+  (geometry == 1 ? (pt ? F_<P, 1, 1>(__VA_ARGS__) : F_<P, 1, 0>(__VA_ARGS__)) \
+                 : (pt ? F_<P, 0, 1>(__VA_ARGS__) : F_<P, 0, 0>(__VA_ARGS__)))
 
 template <class P>
 int launch_transport_batched_t(int geometry, int pt, const DeviceView* views, const BatchItem* items,
@@ -1824,7 +1835,8 @@ int launch_transport_batched_t(int geometry, int pt, const DeviceView* views, co
 template <class P>
 int launch_freq_batched_t(int geometry, int pt, const DeviceView* views, const BatchItem* items,
                           int n, int grid, int nb_max, cudaStream_t st) {
-  return LYM1_GPT(launch_freq_batched_g, views, items, n, grid, nb_max, st);
+  if (pt == 2) return static_cast<int>(cudaErrorInvalidValue);
+  return LYM1_GPT_F(launch_freq_batched_g, views, items, n, grid, nb_max, st);
 }
 
 // The frequency step keeps its per-bin tables in dynamic shared memory, 7
@@ -1836,7 +1848,7 @@ int launch_freq_batched_t(int geometry, int pt, const DeviceView* views, const B
 // bin) stay under the default at LYM1_MAX_BINS.
 constexpr size_t kFreqSmemMax = sizeof(double) * 7 * LYM1_MAX_BINS;
 
-template <class P, int G, bool PT>
+template <class P, int G, int PT>
 int max_resident_transport_g(int nb_max) {
   int nblk = 0;
   if constexpr (sizeof(typename P::S) == 4)
@@ -1849,7 +1861,7 @@ int max_resident_transport_g(int nb_max) {
   return nblk < 1 ? 1 : nblk;
 }
 
-template <class P, int G, bool PT>
+template <class P, int G, int PT>
 int max_resident_freq_g(int nb_max) {
   cudaFuncSetAttribute(freq_batched<P, G, PT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        static_cast<int>(kFreqSmemMax));
@@ -1866,10 +1878,11 @@ int max_resident_transport(int geometry, int pt, int nb_max) {
 
 template <class P>
 int max_resident_freq(int geometry, int pt, int nb_max) {
-  return LYM1_GPT(max_resident_freq_g, nb_max);
+  if (pt == 2) return 1;
+  return LYM1_GPT_F(max_resident_freq_g, nb_max);
 }
 
-template <class P, int G, bool PT>
+template <class P, int G, int PT>
 int launch_transport_g(const DeviceView& v, cudaStream_t st) {
   dim3 grid((v.nx + kTileX - 1) / kTileX, (v.ny + kTileY - 1) / kTileY);
   if constexpr (sizeof(typename P::S) == 4) {
@@ -1881,7 +1894,7 @@ int launch_transport_g(const DeviceView& v, cudaStream_t st) {
   return static_cast<int>(cudaGetLastError());
 }
 
-template <class P, int G, bool PT>
+template <class P, int G, int PT>
 int launch_freq_g(const DeviceView& v, cudaStream_t st) {
   const size_t smem = sizeof(double) * 7 * static_cast<size_t>(v.nb);
   cudaFuncSetAttribute(freq_kernel<P, G, PT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1899,7 +1912,8 @@ int launch_transport_t(const DeviceView& v, cudaStream_t st) {
 template <class P>
 int launch_freq_t(const DeviceView& v, cudaStream_t st) {
   const int geometry = v.geometry, pt = v.pt;
-  return LYM1_GPT(launch_freq_g, v, st);
+  if (pt == 2) return static_cast<int>(cudaErrorInvalidValue);
+  return LYM1_GPT_F(launch_freq_g, v, st);
 }
 
 }  // namespace lym1

@@ -65,6 +65,10 @@ class lym1_diag(C.Structure):
                 ("substeps", C.c_longlong)]
 
 
+class lym1_bands(C.Structure):
+    _fields_ = [("n_bands", C.c_int), ("alpha_F", _PD), ("kappa", _PD), ("emissivity", _PD)]
+
+
 class lym1_profile(C.Structure):
     _fields_ = [("transport_ms", C.c_double), ("freq_ms", C.c_double),
                 ("finalize_ms", C.c_double), ("transport_launches", C.c_longlong),
@@ -79,6 +83,10 @@ SIGNATURES = {
     "lym1_spectrum_enable": (C.c_int, [C.c_void_p, C.c_int]),
     "lym1_spectrum_read": (C.c_int, [C.c_void_p, _PD, C.POINTER(C.c_int)]),
     "lym1_set_ctilde": (C.c_int, [C.c_void_p, C.c_double]),
+    "lym1_create_bands": (C.c_int, [C.POINTER(lym1_grid), C.POINTER(lym1_bands), _PD, _PD,
+                                    C.c_double, C.c_double, C.c_int, C.c_void_p,
+                                    C.POINTER(C.c_void_p)]),
+    "lym1_bands_update": (C.c_int, [C.c_void_p, _PD, _PD, _PD]),
     "lym1_dynamic_ctilde": (C.c_int, [C.c_void_p, _PD, C.c_double, C.c_double, _PD]),
     "lym1_create": (C.c_int, [C.POINTER(lym1_grid), C.POINTER(lym1_groups),
                               C.POINTER(lym1_opacities), C.POINTER(C.c_void_p)]),
@@ -206,6 +214,51 @@ class Context:
         self.precision = int(precision)
         if lum is not None:
             self.set_sources(lum)
+
+    @classmethod
+    def for_bands(cls, *, nx, ny, dx, alpha_F, kappa, emissivity, ux=0.0, uy=0.0, c_tilde=0.0,
+                  cfl=0.0, precision=FP64_DET, stream=None, geometry=0, bc=(0, 0, 0, 0)):
+        """``lym1_create_bands``: broad bands with per-[band][cell] flux opacity,
+        absorption opacity (cm^-1) and emissivity (erg/s/cm^3/sr)."""
+        keep = []
+        if isinstance(precision, str):
+            precision = PRECISIONS[precision]
+        nb = int(np.shape(alpha_F)[0])
+        g = lym1_grid(int(nx), int(ny), float(dx), int(geometry),
+                      (C.c_int * 4)(*[int(b) for b in bc]))
+
+        def arr(a, shape):
+            if hasattr(a, "data_ptr"):
+                return _ptr(a, keep)
+            return _ptr(np.broadcast_to(np.asarray(a, dtype=np.float64), shape), keep)
+
+        bs = (nb, int(ny), int(nx))
+        b = lym1_bands(nb, arr(alpha_F, bs), arr(kappa, bs), arr(emissivity, bs))
+        h = C.c_void_p()
+        _check(lib().lym1_create_bands(C.byref(g), C.byref(b), arr(ux, bs[1:]), arr(uy, bs[1:]),
+                                       float(c_tilde), float(cfl), int(precision),
+                                       _stream_handle(stream), C.byref(h)), "lym1_create_bands")
+        self = cls.__new__(cls)
+        self.handle = h
+        self.nx, self.ny = int(nx), int(ny)
+        inf = self.info()
+        self.nb = inf["nb"]
+        self.dt_cfl = inf["dt_cfl"]
+        self.precision = int(precision)
+        return self
+
+    def bands_update(self, alpha_F, kappa, emissivity):
+        """``lym1_bands_update``: new per-[band][cell] opacities and emissivity."""
+        keep = []
+        bs = (self.nb, self.ny, self.nx)
+
+        def arr(a):
+            if hasattr(a, "data_ptr"):
+                return _ptr(a, keep)
+            return _ptr(np.broadcast_to(np.asarray(a, dtype=np.float64), bs), keep)
+
+        _check(lib().lym1_bands_update(self.handle, arr(alpha_F), arr(kappa), arr(emissivity)),
+               "lym1_bands_update")
 
     # lifetime ------------------------------------------------------------
     def destroy(self):

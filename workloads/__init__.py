@@ -145,6 +145,51 @@ def lognormal_cloud(nx=512, ny=512, box_pc=2.0, mean_nh=1e3, sigma_ln=1.0, Z=0.0
                  meta={"seed": seed, "sigma_ln": sigma_ln, "mean_nh": mean_nh, "Z": Z})
 
 
+# Broad bands (Sec. 3): IR, optical, FUV, LW, EUV1, EUV2, EUV3.  Dust opacities of
+# the non-IR bands from the dust-opacity table of Sec. 3 (kappa_abs, kappa_F in cm^2
+# per g of dust in the bin, for silicate, graphite and PAH grains), weighted with
+# the bin mass fractions of its caption.
+BAND_NAMES = ("IR", "opt", "FUV", "LW", "EUV1", "EUV2", "EUV3")
+_BAND_DUST = {
+    "opt": ((5.98e3, 1.69e4), (2.09e4, 2.61e4), (2.27e5, 2.27e5)),
+    "FUV": ((1.71e4, 2.21e4), (2.29e4, 2.57e4), (2.86e5, 2.86e5)),
+    "LW": ((1.80e4, 2.18e4), (3.88e4, 4.48e4), (5.92e5, 5.92e5)),
+    "EUV1": ((1.53e4, 1.85e4), (5.60e4, 6.22e4), (1.08e6, 1.08e6)),
+    "EUV2": ((1.37e4, 1.46e4), (1.90e4, 2.12e4), (2.83e5, 2.84e5)),
+    "EUV3": ((1.30e4, 1.32e4), (1.04e4, 1.09e4), (8.81e4, 8.82e4)),
+}
+# stand-ins where the paper gives no number: the IR Planck-mean dust opacity
+# (shown only as a figure) and the H I photoionisation cross-section of the EUV
+# bands (hydrogenic 6.3e-18 cm^2 (E / 13.6 eV)^-3 at the band's mean energy)
+KAPPA_IR = 5.0               # cm^2 per g of dust
+_EUV_E = {"EUV1": 19.1, "EUV2": 39.5, "EUV3": 80.0}   # eV
+SIGMA_SB = 5.670374419e-5    # erg cm^-2 s^-1 K^-4
+
+
+def stellar_bands(cloud, T_dust=20.0, L_sun=None):
+    """Per-[band][cell] flux opacity, absorption opacity (cm^-1) and emissivity
+    (erg/s/cm^3/sr) of the seven bands for a cloud: dust in every band, neutral
+    H I absorption in the EUV bands, the cloud's source luminosity split evenly
+    over the six stellar bands, IR emission rho_d kappa_IR sigma T_d^4 / pi."""
+    ny, nx = cloud.n_hi.shape
+    rho, nh = cloud.rho_d, cloud.n_hi
+    aF = np.zeros((7, ny, nx))
+    ka = np.zeros((7, ny, nx))
+    je = np.zeros((7, ny, nx))
+    aF[0] = ka[0] = rho * KAPPA_IR
+    V = cloud.dx ** 3
+    lum = cloud.lum if L_sun is None else cloud.lum * (L_sun * L_SUN / cloud.lum.sum())
+    for b, name in enumerate(BAND_NAMES[1:], start=1):
+        kabs = sum(f * k[0] for f, k in zip(_F_BIN, _BAND_DUST[name]))
+        kF = sum(f * k[1] for f, k in zip(_F_BIN, _BAND_DUST[name]))
+        gas = 6.3e-18 * (13.6 / _EUV_E[name]) ** 3 * nh if name in _EUV_E else 0.0
+        ka[b] = rho * kabs + gas
+        aF[b] = rho * kF + gas
+        je[b] = lum / 6.0 / (4.0 * math.pi * V)
+    je[0] = rho * KAPPA_IR * SIGMA_SB * T_dust ** 4 / math.pi
+    return aF, ka, je
+
+
 def config_lognormal_512(seed=1):
     """512x512, 194 bins, sigma_ln = 1.0, mean n_H 1e3, Z = 0.01 Z_sun, 1e6 L_sun."""
     return lognormal_cloud(512, 512, mean_nh=1e3, sigma_ln=1.0, Z=0.01, L_sun=1e6, seed=seed,
