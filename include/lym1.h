@@ -384,6 +384,25 @@ typedef struct {
   const double *kappa;
   const double *emissivity;
 } lym1_bands;
+/*
+ * New gas temperatures for a context created with a temperature field
+ * (lym1_opacities.temp_field), e.g. after each hydro step of a
+ * radiation-hydrodynamics run.  Rebuilds on the GPU, one thread per cell, the
+ * per-cell tables of App. A and Sec. 2.1 that the field determines: <H>_k over
+ * every bin at the cell's Doppler width and a_v, the emission factors
+ * w_k / (4 pi V dnu_k) with w_k = <H>_k dx_k normalised to sum 1, sigma0 and
+ * alpha = n_HI sigma0, h / (k_B T) and dnu_D^2 / 2.  The steps and their order
+ * are those of the tables built at creation on the host; the device's exp,
+ * erf and erfc make the two agree to about 1e-15 relative, not bit for bit.
+ * temp_field: [ny][nx] K, host or device pointer, each value finite and > 0.
+ * The state J, H and the diagnostic counters are kept.  Synchronises the
+ * context's stream; takes a temporary device buffer of (nbins + 1) cell planes.
+ * Errors: LYM1_EINVAL for a null pointer, a context made without a temperature
+ * field, or any temperature <= 0 or not finite (nothing is changed);
+ * LYM1_ENOMEM, LYM1_ECUDA.
+ */
+int lym1_set_temperature(lym1_ctx *ctx, const double *temp_field);
+
 int lym1_create_bands(const lym1_grid *grid, const lym1_bands *bands, const double *ux,
                       const double *uy, double c_tilde, double cfl, int precision,
                       void *cuda_stream, lym1_ctx **out);

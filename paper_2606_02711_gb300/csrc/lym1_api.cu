@@ -23,6 +23,9 @@ struct lym1_ctx {
   void *Hc = nullptr, *Gc = nullptr;
   double *gmaxc = nullptr, *Kcc = nullptr, *hkTc = nullptr, *t_2nu = nullptr, *sig0c = nullptr,
          *Tc = nullptr;
+  // temperature field: n_HI and the grid edges, for lym1_set_temperature
+  double* nhi = nullptr;
+  std::vector<double> edges;
   float* f_2nu = nullptr;
   // broad bands (pt = 2): Hc = alpha_F, Gc = emissivity, Kb = kappa per [band][cell]
   int bands = 0;
@@ -622,7 +625,7 @@ static int create_impl(const lym1_grid* grid, const lym1_groups* groups, const l
       build_cell_tables(edges, hT.data(), nc, c->dx, c->gray, c->recoil, grid->geometry, &ct);
       if (rc == LYM1_OK) rc = dalloc(c, &c->Hc, nstate * c->selem);
       if (rc == LYM1_OK) rc = dalloc(c, &c->Gc, nstate * c->selem);
-      double** pc[] = {&c->gmaxc, &c->Kcc, &c->hkTc, &c->sig0c, &c->Tc};
+      double** pc[] = {&c->gmaxc, &c->Kcc, &c->hkTc, &c->sig0c, &c->Tc, &c->nhi};
       for (double** q : pc)
         if (rc == LYM1_OK) rc = dalloc_t(c, q, plane);
       if (rc == LYM1_OK) rc = dalloc_t(c, &c->t_2nu, static_cast<size_t>(c->nb));
@@ -710,6 +713,11 @@ static int create_impl(const lym1_grid* grid, const lym1_groups* groups, const l
         cudaMemcpy(c->Tc, op->temp_field, pb, cudaMemcpyDefault) != cudaSuccess ||
         cudaMemcpy(c->t_2nu, t2.data(), sizeof(double) * c->nb, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(c->f_2nu, f2.data(), sizeof(float) * c->nb, cudaMemcpyHostToDevice) != cudaSuccess)
+      return fail(LYM1_ECUDA);
+  }
+  if (c->pt == 1) {
+    c->edges = edges;
+    if (cudaMemcpyAsync(c->nhi, d_nhi, pb, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
       return fail(LYM1_ECUDA);
   }
   if (launch_setup_statics(d_nhi, c->ux, c->uy, c->tab.lc.sigma0, c->pt ? c->sig0c : nullptr, c->nx,
@@ -1299,5 +1307,42 @@ int lym1_dynamic_ctilde(lym1_ctx* c, const double* cs, double eps_rsl, double ct
   if (!(ct > 0.0) || !(ct <= kLight)) return LYM1_ENONFINITE;
   const int rc = lym1_set_ctilde(c, ct);
   if (rc == LYM1_OK && c_tilde_out) *c_tilde_out = ct;
+  return rc;
+}
+
+int lym1_set_temperature(lym1_ctx* c, const double* temp_field) {
+  if (!c || !temp_field || c->pt != 1) return LYM1_EINVAL;
+  const size_t plane = static_cast<size_t>(c->nc);
+  const size_t pb = plane * sizeof(double);
+  std::vector<double> hT(plane);
+  LYM1_TRY(cudaStreamSynchronize(c->stream));
+  if (cudaMemcpy(hT.data(), temp_field, pb, cudaMemcpyDefault) != cudaSuccess) {
+    cudaGetLastError();
+    return LYM1_EINVAL;
+  }
+  for (double t : hT)
+    if (!(t > 0.0) || !std::isfinite(t)) return LYM1_EINVAL;
+  const int n = static_cast<int>(c->edges.size()) - 1;
+  // scratch: the temperatures, the edges and n planes of <H>_k
+  double* scr = nullptr;
+  const size_t words = plane + static_cast<size_t>(n + 1) + static_cast<size_t>(n) * plane;
+  if (cudaMalloc(&scr, words * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return LYM1_ENOMEM;
+  }
+  double* dT = scr;
+  double* de = scr + plane;
+  double* dH = de + (n + 1);
+  int rc = LYM1_OK;
+  if (cudaMemcpy(dT, hT.data(), pb, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(de, c->edges.data(), sizeof(double) * (n + 1), cudaMemcpyHostToDevice) != cudaSuccess)
+    rc = LYM1_ECUDA;
+  if (rc == LYM1_OK &&
+      launch_cell_tables(static_cast<int>(c->selem), dT, c->nhi, de, n, c->gray, c->recoil,
+                         c->geometry, c->dx, c->nc, dH, c->Hc, c->Gc, c->gmaxc, c->Kcc, c->hkTc,
+                         c->sig0c, c->alpha, c->Tc, c->stream) != 0)
+    rc = LYM1_ECUDA;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) rc = LYM1_ECUDA;
+  cudaFree(scr);
   return rc;
 }

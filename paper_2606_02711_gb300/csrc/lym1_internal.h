@@ -202,6 +202,12 @@ int launch_convert_out(int precision, const void* src, double* dst, long long n,
 int launch_convert_in(int precision, const double* src, void* dst, long long n, void* stream);
 int launch_force_reduce(const double* fx, const double* fy, int nx, int ny, double dx,
                         int geometry, double* part, int nblocks, void* stream);
+// per-cell A0 tables of a temperature field on the device (n = bins of the
+// edges; scr holds n planes of doubles)
+int launch_cell_tables(int selem, const double* T, const double* nhi, const double* edges, int n,
+                       int gray, int recoil, int geometry, double dx, long long nc, double* scr,
+                       void* Hc, void* Gc, double* gmaxc, double* Kcc, double* hkTc,
+                       double* sig0c, double* alpha, double* Tc, void* stream);
 // dynamic reduced speed of light: work holds 2 words (the running maximum,
 // then the new c_tilde as a double); Tc per-cell temperatures or nullptr (T),
 // cs per-cell sound speeds or nullptr (neutral gas at T)

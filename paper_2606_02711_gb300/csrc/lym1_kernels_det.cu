@@ -332,6 +332,153 @@ int launch_dynamic_ctilde(const double* alpha, const double* rho, const double* 
   return static_cast<int>(cudaGetLastError());
 }
 
+// ---------------------------------------------------------------------------
+// Per-cell A0 on the device (App. A: <H>_k at each cell's temperature; Sec. 2.1
+// step 2: emission fractions w_k = <H>_k dx_k / sum; Sec. 2.1: Doppler width,
+// a_v, sigma0), for temperature fields that change between hydro steps.  The
+// same steps, in the same order, as the host tables of lym1_tables.cpp, with
+// CUDA's exp / erf / erfc in place of the host library's.
+
+// Dawson's integral: Maclaurin series below 0.2, Rybicki's sampling sum with
+// h = 0.2 below 10, the asymptotic series above
+__device__ double dawson_dev(double x) {
+  const double ax = fabs(x);
+  double f;
+  if (ax < 0.2) {
+    const double x2 = ax * ax;
+    double term = ax;
+    f = ax;
+    for (int n = 1; n <= 12; ++n) {
+      term = (term * (-2.0 * x2)) / (2.0 * n + 1.0);
+      f += term;
+    }
+  } else if (ax < 10.0) {
+    const double h = 0.2;
+    const int lo = static_cast<int>(ceil((ax - 8.0) / h));
+    const int hi = static_cast<int>(floor((ax + 8.0) / h));
+    double s = 0.0;
+    for (int n = lo; n <= hi; ++n) {
+      if ((n & 1) == 0) continue;
+      const double d = ax - n * h;
+      s += exp(-d * d) / n;
+    }
+    f = s / kSqrtPi;
+  } else {
+    const double y = 1.0 / (2.0 * ax * ax);
+    double term = 1.0, s = 1.0;
+    for (int n = 1; n <= 20; ++n) {
+      term = term * ((2.0 * n - 1.0) * y);
+      s += term;
+    }
+    f = s / (2.0 * ax);
+  }
+  return x < 0.0 ? -f : f;
+}
+
+// The a-dependent terms of I(x, a): -(2a/sqrt(pi)) F(x) + a^2 x exp(-x^2)
+__device__ double voigt_rest_dev(double x, double a) {
+  return -((2.0 * a) / kSqrtPi) * dawson_dev(x) + ((a * a) * x) * exp(-(x * x));
+}
+
+// One thread per cell.  scr: n planes of doubles (the cell's <H>_k between the
+// two passes).  Writes the per-[bin][cell] <H>_k and emission factors in the
+// state type S (FP32: over the cell's maximum factor, kept in gmaxc), sigma0,
+// h/(k_B T) (0 without recoil or for a gray group), dnu_D^2 / 2, alpha =
+// n_HI sigma0 and the temperature itself.
+template <class S>
+__global__ void __launch_bounds__(128) cell_tables_kernel(
+    const double* T, const double* nhi, const double* edges, int n, int gray, int recoil,
+    int geometry, double dx, long long nc, double* scr, S* Hc, S* Gc, double* gmaxc,
+    double* Kcc, double* hkTc, double* sig0c, double* alpha, double* Tc) {
+  const long long cell = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (cell >= nc) return;
+  const double t = T[cell];
+  const double dnuD = (kNuLya * sqrt((2.0 * kBoltzmann * t) / kMassH)) / kLight;
+  const double a_v = kEinsteinA / ((4.0 * kPi) * dnuD);
+  const double sigma0 = ((kSqrtPi * (kCharge * kCharge)) * kOscStrength) / ((kMassE * kLight) * dnuD);
+  // <H> over [xa, xb] (Doppler units): the erf difference through erfc on the
+  // side away from line centre, plus the a-dependent terms; each edge's erfc
+  // and I-terms are formed once and carried to the next bin
+  double S_ = 0.0;
+  double xa = edges[0] / dnuD;
+  double ea = erfc(fabs(xa)), ra = voigt_rest_dev(xa, a_v);
+  for (int k = 0; k < n; ++k) {
+    const double dnu = edges[k + 1] - edges[k];
+    const double xb = edges[k + 1] / dnuD;
+    const double dxk = dnu / dnuD;
+    const double eb = erfc(fabs(xb)), rb = voigt_rest_dev(xb, a_v);
+    double derf;
+    if (xa >= 0.0)
+      derf = (kSqrtPi / 2.0) * (ea - eb);
+    else if (xb <= 0.0)
+      derf = (kSqrtPi / 2.0) * (eb - ea);
+    else
+      derf = (kSqrtPi / 2.0) * (erf(xb) - erf(xa));
+    const double Hv = (derf + (rb - ra)) / dxk;
+    scr[static_cast<long long>(k) * nc + cell] = Hv;
+    S_ += Hv * dxk;
+    xa = xb;
+    ea = eb;
+    ra = rb;
+  }
+  const double V = geometry == 1 ? 1.0 : (dx * dx) * dx;
+  const double fourpiV = (4.0 * kPi) * V;
+  double gmax = 0.0;
+  if (gray) {
+    double eta = 0.0;
+    for (int k = 0; k < n; ++k) {
+      const double dxk = (edges[k + 1] - edges[k]) / dnuD;
+      const double Hv = scr[static_cast<long long>(k) * nc + cell];
+      eta += ((Hv * dxk) / S_) * Hv;
+    }
+    gmax = 1.0 / fourpiV;
+    Hc[cell] = S(eta);
+    Gc[cell] = sizeof(S) == 8 ? S(gmax) : S(1.0);
+  } else {
+    for (int k = 0; k < n; ++k) {
+      const double dnu = edges[k + 1] - edges[k];
+      const double Hv = scr[static_cast<long long>(k) * nc + cell];
+      const double g = ((Hv * (dnu / dnuD)) / S_) / (fourpiV * dnu);
+      gmax = fmax(gmax, g);
+      Hc[static_cast<long long>(k) * nc + cell] = S(Hv);
+      if (sizeof(S) == 8) Gc[static_cast<long long>(k) * nc + cell] = S(g);
+    }
+    if (!(gmax > 0.0)) gmax = 1.0;
+    if (sizeof(S) == 4)
+      for (int k = 0; k < n; ++k) {
+        const double dnu = edges[k + 1] - edges[k];
+        const double Hv = scr[static_cast<long long>(k) * nc + cell];
+        const double g = ((Hv * (dnu / dnuD)) / S_) / (fourpiV * dnu);
+        Gc[static_cast<long long>(k) * nc + cell] = S(g / gmax);
+      }
+  }
+  gmaxc[cell] = gmax;
+  sig0c[cell] = sigma0;
+  hkTc[cell] = (recoil && !gray) ? kPlanck / (kBoltzmann * t) : 0.0;
+  Kcc[cell] = 0.5 * (dnuD * dnuD);
+  alpha[cell] = nhi[cell] * sigma0;
+  Tc[cell] = t;
+}
+
+int launch_cell_tables(int selem, const double* T, const double* nhi, const double* edges, int n,
+                       int gray, int recoil, int geometry, double dx, long long nc, double* scr,
+                       void* Hc, void* Gc, double* gmaxc, double* Kcc, double* hkTc,
+                       double* sig0c, double* alpha, double* Tc, void* st) {
+  const cudaStream_t s = static_cast<cudaStream_t>(st);
+  const int blocks = static_cast<int>((nc + 127) / 128);
+  if (selem == 8)
+    cell_tables_kernel<double><<<blocks, 128, 0, s>>>(T, nhi, edges, n, gray, recoil, geometry, dx,
+                                                      nc, scr, static_cast<double*>(Hc),
+                                                      static_cast<double*>(Gc), gmaxc, Kcc, hkTc,
+                                                      sig0c, alpha, Tc);
+  else
+    cell_tables_kernel<float><<<blocks, 128, 0, s>>>(T, nhi, edges, n, gray, recoil, geometry, dx,
+                                                     nc, scr, static_cast<float*>(Hc),
+                                                     static_cast<float*>(Gc), gmaxc, Kcc, hkTc,
+                                                     sig0c, alpha, Tc);
+  return static_cast<int>(cudaGetLastError());
+}
+
 // one block per context: the per-substep reduction of finalize_kernel for a batch
 __global__ void __launch_bounds__(256) finalize_batched_kernel(const FinalizeJob* jobs) {
   const FinalizeJob j = jobs[blockIdx.x];

@@ -87,6 +87,7 @@ SIGNATURES = {
                                     C.c_double, C.c_double, C.c_int, C.c_void_p,
                                     C.POINTER(C.c_void_p)]),
     "lym1_bands_update": (C.c_int, [C.c_void_p, _PD, _PD, _PD]),
+    "lym1_set_temperature": (C.c_int, [C.c_void_p, _PD]),
     "lym1_dynamic_ctilde": (C.c_int, [C.c_void_p, _PD, C.c_double, C.c_double, _PD]),
     "lym1_create": (C.c_int, [C.POINTER(lym1_grid), C.POINTER(lym1_groups),
                               C.POINTER(lym1_opacities), C.POINTER(C.c_void_p)]),
@@ -246,6 +247,13 @@ class Context:
         self.dt_cfl = inf["dt_cfl"]
         self.precision = int(precision)
         return self
+
+    def set_temperature(self, temp):
+        """``lym1_set_temperature``: per-cell tables for new gas temperatures."""
+        keep = []
+        if not hasattr(temp, "data_ptr"):
+            temp = np.broadcast_to(np.asarray(temp, dtype=np.float64), (self.ny, self.nx))
+        _check(lib().lym1_set_temperature(self.handle, _ptr(temp, keep)), "lym1_set_temperature")
 
     def bands_update(self, alpha_F, kappa, emissivity):
         """``lym1_bands_update``: new per-[band][cell] opacities and emissivity."""
