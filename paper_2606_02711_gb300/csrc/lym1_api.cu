@@ -40,6 +40,9 @@ struct lym1_ctx {
   // batch holding this context re-uploads its views before the next launch
   unsigned view_gen = 0;
   unsigned long long* ctw = nullptr;  // dynamic c_tilde: running max, result
+  // luminosity sum on the device (lym1_set_sources), read back when needed
+  double* lsum = nullptr;
+  int L_pending = 0;
   long long substeps_done = 0;
   cudaStream_t stream = nullptr;
   BinTables tab;
@@ -596,6 +599,7 @@ static int create_impl(const lym1_grid* grid, const lym1_groups* groups, const l
   if (rc == LYM1_OK) rc = dalloc_t(c, &c->fpart, 2 * kForceBlocks);
   if (rc == LYM1_OK) rc = dalloc_t(c, &c->status, 4);
   if (rc == LYM1_OK) rc = dalloc_t(c, &c->ctw, 2);
+  if (rc == LYM1_OK) rc = dalloc_t(c, &c->lsum, kSumWork);
   float** ftabs[] = {&c->f_H, &c->f_dnu, &c->f_G, &c->f_R, &c->f_nbc, &c->f_half};
   for (float** p : ftabs)
     if (rc == LYM1_OK) rc = dalloc_t(c, p, static_cast<size_t>(c->nb));
@@ -764,7 +768,8 @@ static int create_impl(const lym1_grid* grid, const lym1_groups* groups, const l
     if (cudaMemsetAsync(c->A[i], 0, nstate * c->selem, s) != cudaSuccess) return fail(LYM1_ECUDA);
   if (cudaMemsetAsync(c->lum, 0, pb, s) != cudaSuccess || cudaMemsetAsync(c->fx, 0, pb, s) != cudaSuccess ||
       cudaMemsetAsync(c->fy, 0, pb, s) != cudaSuccess || cudaMemsetAsync(c->acc, 0, 16 * sizeof(double), s) != cudaSuccess ||
-      cudaMemsetAsync(c->status, 0, 4 * sizeof(int), s) != cudaSuccess)
+      cudaMemsetAsync(c->status, 0, 4 * sizeof(int), s) != cudaSuccess ||
+      cudaMemsetAsync(c->lsum, 0, kSumWork * sizeof(double), s) != cudaSuccess)
     return fail(LYM1_ECUDA);
   // max |u| for the RT time step (Sec. 2.1, CFL condition with D = 2)
   std::vector<double> hux(plane), huy(plane);
@@ -854,19 +859,13 @@ int lym1_set_sources(lym1_ctx* c, const double* lum) {
   if (!c || !lum || c->bands) return LYM1_EINVAL;
   const size_t n = static_cast<size_t>(c->nc);
   LYM1_TRY(cudaMemcpyAsync(c->lum, lum, n * sizeof(double), cudaMemcpyDefault, c->stream));
+  // the total luminosity (M_F normaliser), summed on the device and read back
+  // only by the diagnostics: the call does not wait for the GPU
+  LYM1_TRYK(launch_sum_cells(c->lum, c->nc, c->lsum, c->stream));
+  c->L_pending = 1;
   // axisymmetric grid: the kernels take the luminosity per unit ring volume
   if (c->geometry == 1)
     LYM1_TRYK(launch_scale_columns(c->lum, c->g_V2pi, c->nx, c->nc, c->stream));
-  double L = 0.0;
-  if (is_device_ptr(lum)) {
-    std::vector<double> h(n);
-    LYM1_TRY(cudaMemcpyAsync(h.data(), lum, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-    LYM1_TRY(cudaStreamSynchronize(c->stream));
-    for (double x : h) L += x;
-  } else {
-    for (size_t i = 0; i < n; ++i) L += lum[i];
-  }
-  c->L_tot = L;
   return LYM1_OK;
 }
 
@@ -962,9 +961,16 @@ int lym1_diagnostics(lym1_ctx* c, lym1_diag* d) {
   LYM1_TRYK(launch_force_reduce(c->fx, c->fy, c->nx, c->ny, c->dx, c->geometry, c->fpart,
                                 kForceBlocks, c->stream));
   LYM1_TRY(cudaMemcpyAsync(acc, c->acc, sizeof acc, cudaMemcpyDeviceToHost, c->stream));
+  double Ldev = 0.0;
+  if (c->L_pending)
+    LYM1_TRY(cudaMemcpyAsync(&Ldev, c->lsum + 152, sizeof Ldev, cudaMemcpyDeviceToHost, c->stream));
   LYM1_TRY(cudaMemcpyAsync(fp.data(), c->fpart, fp.size() * sizeof(double), cudaMemcpyDeviceToHost,
                            c->stream));
   LYM1_TRY(cudaStreamSynchronize(c->stream));
+  if (c->L_pending) {
+    c->L_tot = Ldev;
+    c->L_pending = 0;
+  }
   std::memset(d, 0, sizeof *d);
   d->emitted = acc[0] + acc[1];
   d->absorbed = acc[2] + acc[3];

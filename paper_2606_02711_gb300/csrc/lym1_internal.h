@@ -202,6 +202,10 @@ int launch_convert_out(int precision, const void* src, double* dst, long long n,
 int launch_convert_in(int precision, const double* src, void* dst, long long n, void* stream);
 int launch_force_reduce(const double* fx, const double* fy, int nx, int ny, double dx,
                         int geometry, double* part, int nblocks, void* stream);
+// sum over cells of a[n] into work[152] (work: 152 partials, the sum, a zeroed
+// counter word; kSumWork doubles)
+constexpr int kSumWork = 154;
+int launch_sum_cells(const double* a, long long n, double* work, void* stream);
 // per-cell A0 tables of a temperature field on the device (n = bins of the
 // edges; scr holds n planes of doubles)
 int launch_cell_tables(int selem, const double* T, const double* nhi, const double* edges, int n,

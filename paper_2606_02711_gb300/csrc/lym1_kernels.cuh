@@ -1481,7 +1481,6 @@ __device__ __forceinline__ void freq_block_bulk(const DeviceView& v, int blk) {
   __shared__ __align__(128) float ring[D][5][NT];
   __shared__ __align__(8) unsigned long long barF[D], barB[D];
   __shared__ double red[NT / 32];
-  __shared__ int failed;
   extern __shared__ double tabs_raw[];
   T* tabs = reinterpret_cast<T*>(tabs_raw);
   const int nb = v.nb;
@@ -1505,7 +1504,6 @@ __device__ __forceinline__ void freq_block_bulk(const DeviceView& v, int blk) {
     tact[i] = I(fmaxf(thr, 1e-30f) / v.f_dnu[i]);
   }
   if (tid == 0) {
-    failed = 0;
     for (int s = 0; s < D; ++s) {
       mbar_init(&barF[s], 1);
       mbar_init(&barB[s], 1);
@@ -1590,13 +1588,11 @@ __device__ __forceinline__ void freq_block_bulk(const DeviceView& v, int blk) {
   long long ofw = cell - nc;  // plane offset of row k - 1
   for (int k = 0; k < nb; ++k, ofw += nc) {
     const int s = k % D;
-    if (!mbar_wait_bounded(&barF[s], (k / D) & 1)) failed = 1;
-    __syncthreads();
-    if (failed) {
-      give_up(barF, nb < k + D ? nb : k + D, k);
-      return;
-    }
-    if (act) {
+    // every thread waits for the stage itself (the completed phase makes the
+    // copied rows visible to it); a wait that ran out is caught at the one
+    // block barrier below, after which nobody reads the ring
+    const bool okF = mbar_wait_bounded(&barF[s], (k / D) & 1);
+    if (act && okF) {
       const F Jc = F(ring[s][0][tid]), Xc = F(ring[s][1][tid]), Yc = F(ring[s][2][tid]);
       F Pk, ak, ek;
       const F Hk = PT ? F(ring[s][3][tid]) : F(tH[k]);
@@ -1639,7 +1635,10 @@ __device__ __forceinline__ void freq_block_bulk(const DeviceView& v, int blk) {
       ep = ek;
       Jp = I(Jc);
     }
-    __syncthreads();  // stage s consumed
+    if (__syncthreads_or(okF ? 0 : 1)) {  // stage s consumed (or a wait ran out)
+      give_up(barF, nb < k + D ? nb : k + D, k);
+      return;
+    }
     if (tid == 0 && k + D < nb) issue_fwd(k + D);
   }
   if (act) {  // last row: no interface above
@@ -1671,13 +1670,8 @@ __device__ __forceinline__ void freq_block_bulk(const DeviceView& v, int blk) {
   long long obw = static_cast<long long>(nb - 1) * nc + cell;  // plane offset of row k
   for (int j = 0; j < nb; ++j, obw -= nc) {
     const int s = j % D, k = nb - 1 - j;
-    if (!mbar_wait_bounded(&barB[s], (j / D) & 1)) failed = 1;
-    __syncthreads();
-    if (failed) {
-      give_up(barB, nb < j + D ? nb : j + D, j);
-      return;
-    }
-    if (valid) {
+    const bool okB = mbar_wait_bounded(&barB[s], (j / D) & 1);
+    if (valid && okB) {
       const long long o = obw;
       const float Jo = ring[s][2][tid], Xo = ring[s][3][tid], Yo = ring[s][4][tid];
       if (act) {
@@ -1715,7 +1709,10 @@ __device__ __forceinline__ void freq_block_bulk(const DeviceView& v, int blk) {
         }
       }
     }
-    __syncthreads();
+    if (__syncthreads_or(okB ? 0 : 1)) {  // stage s consumed (or a wait ran out)
+      give_up(barB, nb < j + D ? nb : j + D, j);
+      return;
+    }
     if (tid == 0 && j + D < nb) issue_bwd(j + D);
   }
   double* part = v.partF + static_cast<long long>(blk) * kDiagSlots;

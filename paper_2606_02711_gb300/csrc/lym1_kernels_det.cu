@@ -479,6 +479,42 @@ int launch_cell_tables(int selem, const double* T, const double* nhi, const doub
   return static_cast<int>(cudaGetLastError());
 }
 
+// Sum of a per-cell array (the luminosity), in a fixed order: a fixed grid of
+// grid-stride block partials, which the last block to finish adds in block order
+// (the count returns to 0 for the next call).  Nothing waits on another block.
+constexpr int kSumBlocks = 152;
+
+__global__ void __launch_bounds__(256) sum_cells_kernel(const double* a, long long n, double* part,
+                                                        unsigned* count, double* out) {
+  __shared__ double red[8];
+  __shared__ int last;
+  double s = 0.0;
+  for (long long id = static_cast<long long>(blockIdx.x) * 256 + threadIdx.x; id < n;
+       id += static_cast<long long>(gridDim.x) * 256)
+    s += a[id];
+  s = block_sum<256>(s, red);
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = s;
+    __threadfence();
+    last = atomicAdd(count, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    double t = 0.0;
+    for (int b = 0; b < static_cast<int>(gridDim.x); ++b) t += __ldcg(part + b);
+    *out = t;
+    *count = 0u;
+  }
+}
+
+int launch_sum_cells(const double* a, long long n, double* work, void* st) {
+  // work: kSumBlocks partials, the result, then the counter (in the next word)
+  sum_cells_kernel<<<kSumBlocks, 256, 0, static_cast<cudaStream_t>(st)>>>(
+      a, n, work, reinterpret_cast<unsigned*>(work + kSumBlocks + 1), work + kSumBlocks);
+  return static_cast<int>(cudaGetLastError());
+}
+
 // one block per context: the per-substep reduction of finalize_kernel for a batch
 __global__ void __launch_bounds__(256) finalize_batched_kernel(const FinalizeJob* jobs) {
   const FinalizeJob j = jobs[blockIdx.x];
