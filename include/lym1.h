@@ -396,7 +396,7 @@ typedef struct {
  * erf and erfc make the two agree to about 1e-15 relative, not bit for bit.
  * temp_field: [ny][nx] K, host or device pointer, each value finite and > 0.
  * The state J, H and the diagnostic counters are kept.  Synchronises the
- * context's stream; takes a temporary device buffer of (nbins + 1) cell planes.
+ * context's stream; takes a temporary device buffer of one cell plane.
  * Errors: LYM1_EINVAL for a null pointer, a context made without a temperature
  * field, or any temperature <= 0 or not finite (nothing is changed);
  * LYM1_ENOMEM, LYM1_ECUDA.

@@ -1329,23 +1329,22 @@ int lym1_set_temperature(lym1_ctx* c, const double* temp_field) {
   for (double t : hT)
     if (!(t > 0.0) || !std::isfinite(t)) return LYM1_EINVAL;
   const int n = static_cast<int>(c->edges.size()) - 1;
-  // scratch: the temperatures, the edges and n planes of <H>_k
+  // scratch: the temperatures and the edges
   double* scr = nullptr;
-  const size_t words = plane + static_cast<size_t>(n + 1) + static_cast<size_t>(n) * plane;
+  const size_t words = plane + static_cast<size_t>(n + 1);
   if (cudaMalloc(&scr, words * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
     return LYM1_ENOMEM;
   }
   double* dT = scr;
   double* de = scr + plane;
-  double* dH = de + (n + 1);
   int rc = LYM1_OK;
   if (cudaMemcpy(dT, hT.data(), pb, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(de, c->edges.data(), sizeof(double) * (n + 1), cudaMemcpyHostToDevice) != cudaSuccess)
     rc = LYM1_ECUDA;
   if (rc == LYM1_OK &&
       launch_cell_tables(static_cast<int>(c->selem), dT, c->nhi, de, n, c->gray, c->recoil,
-                         c->geometry, c->dx, c->nc, dH, c->Hc, c->Gc, c->gmaxc, c->Kcc, c->hkTc,
+                         c->geometry, c->dx, c->nc, c->Hc, c->Gc, c->gmaxc, c->Kcc, c->hkTc,
                          c->sig0c, c->alpha, c->Tc, c->stream) != 0)
     rc = LYM1_ECUDA;
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) rc = LYM1_ECUDA;

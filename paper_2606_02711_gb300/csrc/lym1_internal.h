@@ -206,12 +206,11 @@ int launch_force_reduce(const double* fx, const double* fy, int nx, int ny, doub
 // counter word; kSumWork doubles)
 constexpr int kSumWork = 154;
 int launch_sum_cells(const double* a, long long n, double* work, void* stream);
-// per-cell A0 tables of a temperature field on the device (n = bins of the
-// edges; scr holds n planes of doubles)
+// per-cell A0 tables of a temperature field on the device (n = bins of the edges)
 int launch_cell_tables(int selem, const double* T, const double* nhi, const double* edges, int n,
-                       int gray, int recoil, int geometry, double dx, long long nc, double* scr,
-                       void* Hc, void* Gc, double* gmaxc, double* Kcc, double* hkTc,
-                       double* sig0c, double* alpha, double* Tc, void* stream);
+                       int gray, int recoil, int geometry, double dx, long long nc, void* Hc,
+                       void* Gc, double* gmaxc, double* Kcc, double* hkTc, double* sig0c,
+                       double* alpha, double* Tc, void* stream);
 // dynamic reduced speed of light: work holds 2 words (the running maximum,
 // then the new c_tilde as a double); Tc per-cell temperatures or nullptr (T),
 // cs per-cell sound speeds or nullptr (neutral gas at T)

@@ -380,16 +380,18 @@ __device__ double voigt_rest_dev(double x, double a) {
   return -((2.0 * a) / kSqrtPi) * dawson_dev(x) + ((a * a) * x) * exp(-(x * x));
 }
 
-// One thread per cell.  scr: n planes of doubles (the cell's <H>_k between the
-// two passes).  Writes the per-[bin][cell] <H>_k and emission factors in the
-// state type S (FP32: over the cell's maximum factor, kept in gmaxc), sigma0,
-// h/(k_B T) (0 without recoil or for a gray group), dnu_D^2 / 2, alpha =
-// n_HI sigma0 and the temperature itself.
+// One thread per cell.  Writes the per-[bin][cell] <H>_k and emission factors
+// in the state type S (FP32: the factors over the cell's maximum, kept in
+// gmaxc), sigma0, h/(k_B T) (0 without recoil or for a gray group),
+// dnu_D^2 / 2, alpha = n_HI sigma0 and the temperature itself.  <H>_k goes
+// straight into Hc; the normalisation sum always takes the FP64 value, and the
+// emission factors are formed from Hc (exact for FP64 state, the stored FP32
+// value otherwise).  A gray group (one table entry per cell) forms <H>_k twice.
 template <class S>
 __global__ void __launch_bounds__(128) cell_tables_kernel(
     const double* T, const double* nhi, const double* edges, int n, int gray, int recoil,
-    int geometry, double dx, long long nc, double* scr, S* Hc, S* Gc, double* gmaxc,
-    double* Kcc, double* hkTc, double* sig0c, double* alpha, double* Tc) {
+    int geometry, double dx, long long nc, S* Hc, S* Gc, double* gmaxc, double* Kcc,
+    double* hkTc, double* sig0c, double* alpha, double* Tc) {
   const long long cell = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (cell >= nc) return;
   const double t = T[cell];
@@ -398,56 +400,56 @@ __global__ void __launch_bounds__(128) cell_tables_kernel(
   const double sigma0 = ((kSqrtPi * (kCharge * kCharge)) * kOscStrength) / ((kMassE * kLight) * dnuD);
   // <H> over [xa, xb] (Doppler units): the erf difference through erfc on the
   // side away from line centre, plus the a-dependent terms; each edge's erfc
-  // and I-terms are formed once and carried to the next bin
-  double S_ = 0.0;
-  double xa = edges[0] / dnuD;
-  double ea = erfc(fabs(xa)), ra = voigt_rest_dev(xa, a_v);
-  for (int k = 0; k < n; ++k) {
-    const double dnu = edges[k + 1] - edges[k];
-    const double xb = edges[k + 1] / dnuD;
-    const double dxk = dnu / dnuD;
-    const double eb = erfc(fabs(xb)), rb = voigt_rest_dev(xb, a_v);
-    double derf;
-    if (xa >= 0.0)
-      derf = (kSqrtPi / 2.0) * (ea - eb);
-    else if (xb <= 0.0)
-      derf = (kSqrtPi / 2.0) * (eb - ea);
-    else
-      derf = (kSqrtPi / 2.0) * (erf(xb) - erf(xa));
-    const double Hv = (derf + (rb - ra)) / dxk;
-    scr[static_cast<long long>(k) * nc + cell] = Hv;
-    S_ += Hv * dxk;
-    xa = xb;
-    ea = eb;
-    ra = rb;
+  // and I-terms are formed once and carried to the next bin.  pass 0 sums the
+  // emission weights (and stores <H>_k), pass 1 (gray group only) forms eta.
+  double S_ = 0.0, eta = 0.0;
+  for (int pass = 0; pass < (gray ? 2 : 1); ++pass) {
+    double xa = edges[0] / dnuD;
+    double ea = erfc(fabs(xa)), ra = voigt_rest_dev(xa, a_v);
+    for (int k = 0; k < n; ++k) {
+      const double dnu = edges[k + 1] - edges[k];
+      const double xb = edges[k + 1] / dnuD;
+      const double dxk = dnu / dnuD;
+      const double eb = erfc(fabs(xb)), rb = voigt_rest_dev(xb, a_v);
+      double derf;
+      if (xa >= 0.0)
+        derf = (kSqrtPi / 2.0) * (ea - eb);
+      else if (xb <= 0.0)
+        derf = (kSqrtPi / 2.0) * (eb - ea);
+      else
+        derf = (kSqrtPi / 2.0) * (erf(xb) - erf(xa));
+      const double Hv = (derf + (rb - ra)) / dxk;
+      if (pass == 0) {
+        if (!gray) Hc[static_cast<long long>(k) * nc + cell] = S(Hv);
+        S_ += Hv * dxk;
+      } else {
+        eta += ((Hv * dxk) / S_) * Hv;
+      }
+      xa = xb;
+      ea = eb;
+      ra = rb;
+    }
   }
   const double V = geometry == 1 ? 1.0 : (dx * dx) * dx;
   const double fourpiV = (4.0 * kPi) * V;
   double gmax = 0.0;
   if (gray) {
-    double eta = 0.0;
-    for (int k = 0; k < n; ++k) {
-      const double dxk = (edges[k + 1] - edges[k]) / dnuD;
-      const double Hv = scr[static_cast<long long>(k) * nc + cell];
-      eta += ((Hv * dxk) / S_) * Hv;
-    }
     gmax = 1.0 / fourpiV;
     Hc[cell] = S(eta);
     Gc[cell] = sizeof(S) == 8 ? S(gmax) : S(1.0);
   } else {
     for (int k = 0; k < n; ++k) {
       const double dnu = edges[k + 1] - edges[k];
-      const double Hv = scr[static_cast<long long>(k) * nc + cell];
+      const double Hv = double(Hc[static_cast<long long>(k) * nc + cell]);
       const double g = ((Hv * (dnu / dnuD)) / S_) / (fourpiV * dnu);
       gmax = fmax(gmax, g);
-      Hc[static_cast<long long>(k) * nc + cell] = S(Hv);
       if (sizeof(S) == 8) Gc[static_cast<long long>(k) * nc + cell] = S(g);
     }
     if (!(gmax > 0.0)) gmax = 1.0;
     if (sizeof(S) == 4)
       for (int k = 0; k < n; ++k) {
         const double dnu = edges[k + 1] - edges[k];
-        const double Hv = scr[static_cast<long long>(k) * nc + cell];
+        const double Hv = double(Hc[static_cast<long long>(k) * nc + cell]);
         const double g = ((Hv * (dnu / dnuD)) / S_) / (fourpiV * dnu);
         Gc[static_cast<long long>(k) * nc + cell] = S(g / gmax);
       }
@@ -461,19 +463,19 @@ __global__ void __launch_bounds__(128) cell_tables_kernel(
 }
 
 int launch_cell_tables(int selem, const double* T, const double* nhi, const double* edges, int n,
-                       int gray, int recoil, int geometry, double dx, long long nc, double* scr,
-                       void* Hc, void* Gc, double* gmaxc, double* Kcc, double* hkTc,
-                       double* sig0c, double* alpha, double* Tc, void* st) {
+                       int gray, int recoil, int geometry, double dx, long long nc, void* Hc,
+                       void* Gc, double* gmaxc, double* Kcc, double* hkTc, double* sig0c,
+                       double* alpha, double* Tc, void* st) {
   const cudaStream_t s = static_cast<cudaStream_t>(st);
   const int blocks = static_cast<int>((nc + 127) / 128);
   if (selem == 8)
     cell_tables_kernel<double><<<blocks, 128, 0, s>>>(T, nhi, edges, n, gray, recoil, geometry, dx,
-                                                      nc, scr, static_cast<double*>(Hc),
+                                                      nc, static_cast<double*>(Hc),
                                                       static_cast<double*>(Gc), gmaxc, Kcc, hkTc,
                                                       sig0c, alpha, Tc);
   else
     cell_tables_kernel<float><<<blocks, 128, 0, s>>>(T, nhi, edges, n, gray, recoil, geometry, dx,
-                                                     nc, scr, static_cast<float*>(Hc),
+                                                     nc, static_cast<float*>(Hc),
                                                      static_cast<float*>(Gc), gmaxc, Kcc, hkTc,
                                                      sig0c, alpha, Tc);
   return static_cast<int>(cudaGetLastError());

@@ -5,6 +5,8 @@ benchmark times (one context, the default stream, CFL substeps).
 * lognormal-512 (512x512x194): FP64_DET bit-exact after 2 substeps and
   MIXED_FAST (the benchmarked policy) within 1e-4 normwise after 5, against
   the oracle on the full grid;
+* the seven stellar/IR bands on lognormal-512: FP64_DET bit-exact and
+  MIXED_FAST within 1e-4 normwise after 10 substeps, on the full grid;
 * lognormal-2048 (2048x2048x194), MIXED_FAST: 5 substeps from the empty
   state; the oracle computes the central 64x64 crop, which the radiation
   cannot leave in 5 substeps (the stencil reaches 2 cells per substep), so
@@ -74,6 +76,25 @@ def test_lognormal_512_mixed_fast(L):
         _normwise(a, b, 1e-4, n)
     assert d["e_tot"] == pytest.approx(diags[-1]["e_after"], rel=1e-5)
     assert d["max_f"] < 2.0
+
+
+@pytest.mark.parametrize("precision", ["fp64_det", "mixed_fast"])
+def test_seven_bands_lognormal_512(L, precision):
+    # the bench's band line: the seven stellar/IR bands on lognormal-512,
+    # against the oracle's band mode on the full grid (FP64_DET bit-exact)
+    c = wl.config_lognormal_512()
+    aF, ka, je = wl.stellar_bands(c)
+    kw = dict(nx=c.nx, ny=c.ny, dx=c.dx, ux=c.ux, uy=c.uy)
+    ctx = L.Context.for_bands(alpha_F=aF, kappa=ka, emissivity=je, precision=precision, **kw)
+    ctx.substeps(10)
+    got = ctx.get_state() + ctx.force()
+    ctx.destroy()
+    ref, _ = oracle.Oracle.for_bands(alpha_F=aF, kappa=ka, emissivity=je, **kw).run(10)
+    for a, b, n in zip(got, ref, ("J", "Hx", "Hy", "fx", "fy")):
+        if precision == "fp64_det":
+            assert np.array_equal(a, b), n
+        else:
+            _normwise(a, b, 1e-4, n)
 
 
 def test_lognormal_2048_mixed_fast_central_crop(L):
