@@ -163,9 +163,15 @@ void lym1_destroy(lym1_ctx *ctx);
 /*
  * Sets the Lya sources: lum_erg_s[ny][nx] is the luminosity emitted in each
  * cell, spread over the bins with the emission fractions w_k (phi_nu = H/sqrt
- * pi, Sec. 2.1 step 2): j_k = lum w_k / (4 pi dx^3 dnu_k).  Host or device
- * pointer.  The diagnostic counters keep running (emission is booked per
- * substep with the sources in force).
+ * pi, Sec. 2.1 step 2): j_k = lum w_k / (4 pi dx^3 dnu_k) (axisymmetric grid:
+ * the cell's ring volume 2 pi Vol in place of dx^3).  Host or device pointer.
+ * The call only enqueues work on the context's stream (the copy, a device sum
+ * of the total luminosity that lym1_diagnostics reads back for M_F, and the
+ * ring-volume scaling) and returns without waiting: a pinned host buffer must
+ * stay unchanged until the stream has passed the copy (pageable memory is
+ * staged before the call returns).  The diagnostic counters keep running
+ * (emission is booked per substep with the sources in force).  LYM1_EINVAL for
+ * a band context (lym1_bands_update sets band emission).
  */
 int lym1_set_sources(lym1_ctx *ctx, const double *lum_erg_s);
 
