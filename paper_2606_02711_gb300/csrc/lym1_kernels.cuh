@@ -1181,6 +1181,12 @@ __device__ __forceinline__ void freq_coef(typename P::F Jc, typename P::F Hxc, t
   }
 }
 
+// shared memory of the frequency step's per-bin tables, per bin
+template <class P>
+constexpr size_t freq_smem_per_bin() {
+  return 2 * sizeof(typename P::I) + 5 * sizeof(typename P::F);
+}
+
 template <class P, int G, int PT>
 __device__ __forceinline__ void freq_block(const DeviceView& v, int blk) {
   using S = typename P::S;
@@ -1189,16 +1195,18 @@ __device__ __forceinline__ void freq_block(const DeviceView& v, int blk) {
   using T = F;  // table type in shared memory
   constexpr int NT = kFreqThreads;
   extern __shared__ double tabs_raw[];
-  T* tabs = reinterpret_cast<T*>(tabs_raw);
   __shared__ double red[NT / 32];
   const int nb = v.nb;
+  // per-bin tables, freq_smem_per_bin<P>() bytes a bin: two in the elimination
+  // type I, then five in the coefficient type T
+  I* tdi = reinterpret_cast<I*>(tabs_raw);  // dnu_k in the elimination type
+  I* tact = tdi + nb;                       // J above which |H|/J is checked
+  T* tabs = reinterpret_cast<T*>(tact + nb);
   T* tH = tabs;
   T* tR = tabs + nb;
   T* tn = tabs + 2 * nb;
   T* th = tabs + 3 * nb;
   T* td = tabs + 4 * nb;
-  I* tdi = reinterpret_cast<I*>(tabs_raw + 5 * nb);  // dnu_k in the elimination type
-  I* tact = reinterpret_cast<I*>(tabs_raw + 6 * nb);  // J above which |H|/J is checked
   if constexpr (sizeof(F) == 4) {
     const float thr = float(v.acc[14]);
     for (int i = threadIdx.x; i < nb; i += NT) {
@@ -1482,14 +1490,14 @@ __device__ __forceinline__ void freq_block_bulk(const DeviceView& v, int blk) {
   __shared__ __align__(8) unsigned long long barF[D], barB[D];
   __shared__ double red[NT / 32];
   extern __shared__ double tabs_raw[];
-  T* tabs = reinterpret_cast<T*>(tabs_raw);
   const int nb = v.nb;
+  I* tdi = reinterpret_cast<I*>(tabs_raw);  // same layout as freq_block
+  I* tact = tdi + nb;
+  T* tabs = reinterpret_cast<T*>(tact + nb);
   T* tH = tabs;
   T* tR = tabs + nb;
   T* tn = tabs + 2 * nb;
   T* th = tabs + 3 * nb;
-  I* tdi = reinterpret_cast<I*>(tabs_raw + 5 * nb);
-  I* tact = reinterpret_cast<I*>(tabs_raw + 6 * nb);
   const int tid = threadIdx.x;
   const float thr = float(v.acc[14]);
   for (int i = tid; i < nb; i += NT) {
@@ -1804,7 +1812,7 @@ int launch_transport_batched_g(const DeviceView* views, const BatchItem* items, 
 template <class P, int G, int PT>
 int launch_freq_batched_g(const DeviceView* views, const BatchItem* items, int n, int grid,
                           int nb_max, cudaStream_t st) {
-  const size_t smem = sizeof(double) * 7 * static_cast<size_t>(nb_max);
+  const size_t smem = freq_smem_per_bin<P>() * static_cast<size_t>(nb_max);
   freq_batched<P, G, PT><<<grid, kFreqThreads, smem, st>>>(views, items, n);
   return static_cast<int>(cudaGetLastError());
 }
@@ -1836,9 +1844,10 @@ int launch_freq_batched_t(int geometry, int pt, const DeviceView* views, const B
   return LYM1_GPT_F(launch_freq_batched_g, views, items, n, grid, nb_max, st);
 }
 
-// The frequency step keeps its per-bin tables in dynamic shared memory, 7
-// words per bin; beside the static ring and reduction buffers that passes the
-// 48 KB a launch may take by default from about 500 bins on.  The kernels are
+// The frequency step keeps its per-bin tables in dynamic shared memory, at most
+// 7 doubles per bin (28 bytes for FP32 state); beside the static ring and
+// reduction buffers that passes the 48 KB a launch may take by default for
+// large bin counts.  The kernels are
 // opted in to the size for LYM1_MAX_BINS bins once per device, outside any
 // stream capture (at batch creation and before a direct launch), so that every
 // bin count the ABI accepts launches.  The FP32 transport tables (4 floats per
@@ -1864,7 +1873,7 @@ int max_resident_freq_g(int nb_max) {
                        static_cast<int>(kFreqSmemMax));
   int nblk = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nblk, freq_batched<P, G, PT>, kFreqThreads,
-                                                sizeof(double) * 7 * static_cast<size_t>(nb_max));
+                                                freq_smem_per_bin<P>() * static_cast<size_t>(nb_max));
   return nblk < 1 ? 1 : nblk;
 }
 
@@ -1893,7 +1902,7 @@ int launch_transport_g(const DeviceView& v, cudaStream_t st) {
 
 template <class P, int G, int PT>
 int launch_freq_g(const DeviceView& v, cudaStream_t st) {
-  const size_t smem = sizeof(double) * 7 * static_cast<size_t>(v.nb);
+  const size_t smem = freq_smem_per_bin<P>() * static_cast<size_t>(v.nb);
   cudaFuncSetAttribute(freq_kernel<P, G, PT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        static_cast<int>(kFreqSmemMax));
   freq_kernel<P, G, PT><<<freq_blocks(v.nc), kFreqThreads, smem, st>>>(v);
