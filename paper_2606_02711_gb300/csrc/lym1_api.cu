@@ -174,6 +174,8 @@ DeviceView make_view(const lym1_ctx* c, double dt) {
   v.kF = c->kF;
   v.Kc = 0.5 * (c->tab.lc.dnu_D * c->tab.lc.dnu_D);
   v.cdt = c->c_tilde * dt;
+  v.cdt_dx = v.cdt / c->dx;
+  v.cdt_c = v.cdt / kLight;
   // Sec. 2.3: f = 4 pi / (c ct dt) sum_k dnu_k (H' - H'')
   v.fcoef = (4.0 * kPi) / ((kLight * c->c_tilde) * dt);
   v.freq_step = c->freq_step;

@@ -121,6 +121,9 @@ struct DeviceView {
   double* partF = nullptr;  // frequency-kernel block partials [blocks][kDiagSlots]
   // scalars
   double kabs = 0, kF = 0, Kc = 0, cdt = 0, fcoef = 0;
+  // c_tilde dt / dx and c_tilde dt / c, formed on the host (the FP32 tiles
+  // would otherwise divide in FP64 on every thread of every tile)
+  double cdt_dx = 0, cdt_c = 0;
   double gem_max = 1;  // max_k gem_k (FP32 emissivity scaling)
   const double* acc = nullptr;  // running totals: [8] energy of the last substep, [13] energy unit
   int* status = nullptr;        // device status word: nonzero after a bounded wait expired

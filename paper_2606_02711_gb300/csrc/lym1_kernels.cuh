@@ -357,6 +357,20 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
     for (int w = 0; w < NT / 32; ++w) s += red[w];
   return s;
 }
+// FP32 partials: the warp sums in FP32 (on the FP32 pipe), their total in FP64
+// in warp order
+template <int NT>
+__device__ __forceinline__ double block_sum_f32(float v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  __syncthreads();
+  if ((tid & 31) == 0) red[tid >> 5] = double(v);
+  __syncthreads();
+  double s = 0.0;
+  if (tid == 0)
+    for (int w = 0; w < NT / 32; ++w) s += red[w];
+  return s;
+}
 template <int NT>
 __device__ __forceinline__ double block_max(double v, double* red) {
   for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
@@ -767,7 +781,7 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
   // (J, K_yy, K_yx)
   __shared__ float4 xF[TY][TX + 1];
   __shared__ float4 yF[TY + 1][TX];
-  __shared__ double red[NT / 32];
+  __shared__ double red[2 * (NT / 32)];  // the last pair of reductions uses both halves
   extern __shared__ float4 tab4[];  // per bin (<H>_k, dnu_k, gem_k / gem_max, J_act,k) as FP32
 
   const float* __restrict__ Jin = static_cast<const float*>(v.J);
@@ -874,8 +888,8 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
   }
   const float cdt_f = float(v.cdt);
   const float inv_dx = 1.0f / float(v.dx);
-  const float cdt_dx = float(v.cdt / v.dx);
-  const I cdt = I(v.cdt), kabs = I(v.kabs), kF = I(v.kF), cdx = I(v.cdt / v.dx);
+  const float cdt_dx = float(v.cdt_dx);
+  const I cdt = I(v.cdt), kabs = I(v.kabs), kF = I(v.kF), cdx = I(v.cdt_dx);
   const I wR = I(v.g_wR), wcol = I(wvf);
   I ax = 0, ay = 0;
   // per-cell bookkeeping sums over the bins: FP64 (compensation-free, exact
@@ -1091,22 +1105,59 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
   }
   double* part = v.partT + static_cast<long long>(blk) * kDiagSlots;
   double s;
-  const double wd = G == 1 ? double(wvf) : 1.0;
-  s = block_sum<NT>(double(em) * (v.cdt * wd), red);
-  if (tid == 0) part[kSlotEmitted] = s;
-  s = block_sum<NT>(double(ab) * (v.cdt * wd), red);
-  if (tid == 0) part[kSlotAbsorbed] = s;
-  s = block_sum<NT>(double(out), red);
-  if (tid == 0) part[kSlotOutflow] = s;
-  s = block_sum<NT>(double(wk) * ((v.cdt / kLight) * wd), red);
-  if (tid == 0) part[kSlotWork] = s;
-  if (tdiag) {
-    s = block_sum<NT>(double(en) * wd, red);
-    if (tid == 0) part[kSlotEnergy] = s;
-    s = block_max<NT>(sqrt(double(mxf2)), red);
-    if (tid == 0) part[kSlotMaxF] = s;
-    s = block_sum<NT>(double(bad), red);
-    if (tid == 0) part[kSlotBad] = s;
+  if constexpr (sizeof(I) == 4) {
+    // FP32 accumulators: each tile's reductions stay off GB300's FP64 pipe
+    // (~1/60 of the FP32 rate) except for the last eight-term sum
+    const float wf = G == 1 ? wvf : 1.0f;
+    s = block_sum_f32<NT>(em * wf, red);
+    if (tid == 0) part[kSlotEmitted] = s * v.cdt;
+    s = block_sum_f32<NT>(ab * wf, red);
+    if (tid == 0) part[kSlotAbsorbed] = s * v.cdt;
+    s = block_sum_f32<NT>(out, red);
+    if (tid == 0) part[kSlotOutflow] = s;
+    s = block_sum_f32<NT>(wk * wf, red);
+    if (tid == 0) part[kSlotWork] = s * v.cdt_c;
+    if (tdiag) {
+      s = block_sum_f32<NT>(en * wf, red);
+      if (tid == 0) part[kSlotEnergy] = s;
+      int b = bad;
+      for (int o = 16; o > 0; o >>= 1) b += __shfl_down_sync(0xffffffffu, b, o);
+      float m = mxf2;
+      for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_down_sync(0xffffffffu, m, o));
+      __syncthreads();
+      if ((tid & 31) == 0) {
+        red[tid >> 5] = double(b);
+        red[NT / 32 + (tid >> 5)] = double(m);
+      }
+      __syncthreads();
+      if (tid == 0) {
+        double sb = 0.0, sm = 0.0;
+        for (int w = 0; w < NT / 32; ++w) {
+          sb += red[w];
+          sm = fmax(sm, red[NT / 32 + w]);
+        }
+        part[kSlotBad] = sb;
+        part[kSlotMaxF] = sqrt(sm);
+      }
+    }
+  } else {
+    const double wd = G == 1 ? double(wvf) : 1.0;
+    s = block_sum<NT>(double(em) * (v.cdt * wd), red);
+    if (tid == 0) part[kSlotEmitted] = s;
+    s = block_sum<NT>(double(ab) * (v.cdt * wd), red);
+    if (tid == 0) part[kSlotAbsorbed] = s;
+    s = block_sum<NT>(double(out), red);
+    if (tid == 0) part[kSlotOutflow] = s;
+    s = block_sum<NT>(double(wk) * (v.cdt_c * wd), red);
+    if (tid == 0) part[kSlotWork] = s;
+    if (tdiag) {
+      s = block_sum<NT>(double(en) * wd, red);
+      if (tid == 0) part[kSlotEnergy] = s;
+      s = block_max<NT>(sqrt(double(mxf2)), red);
+      if (tid == 0) part[kSlotMaxF] = s;
+      s = block_sum<NT>(double(bad), red);
+      if (tid == 0) part[kSlotBad] = s;
+    }
   }
 }
 
