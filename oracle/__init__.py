@@ -51,7 +51,7 @@ class Problem(C.Structure):
                 ("edges", _PD), ("n_hi", _PD), ("rho_d", _PD), ("p_d", _PD),
                 ("ux", _PD), ("uy", _PD), ("lum", _PD), ("geometry", C.c_int),
                 ("bc", C.c_int * 4), ("temp", _PD), ("band_aF", _PD), ("band_kap", _PD),
-                ("band_j", _PD)]
+                ("band_j", _PD), ("prune", C.c_double)]
 
 
 class Diag(C.Structure):
@@ -212,7 +212,7 @@ class Oracle:
     def __init__(self, *, nx, ny, dx, edges, T, n_hi, rho_d, p_d, ux, uy, lum,
                  kappa_abs=0.0, kappa_F=0.0, c_tilde=2.99792458e10, cfl=0.4,
                  gray=False, recoil=True, freq_step=True, geometry=0, bc=(0, 0, 0, 0),
-                 temp=None, bands=None):
+                 temp=None, bands=None, prune=0.0):
         bd = None
         if bands is not None:
             # (alpha_F, kappa, emissivity), each [n_bands][ny][nx]
@@ -233,7 +233,8 @@ class Oracle:
                             float(kappa_F), _p(e), _p(n_hi), _p(rho_d), _p(p_d), _p(ux), _p(uy),
                             _p(lum), int(geometry), (C.c_int * 4)(*[int(b) for b in bc]),
                             _p(tp) if tp is not None else None,
-                            *([_p(a) for a in bd] if bd is not None else [None, None, None]))
+                            *([_p(a) for a in bd] if bd is not None else [None, None, None]),
+                            float(prune))
         self.ctx = lib().lym1o_create(C.byref(self.prob))
         if not self.ctx:
             raise ValueError("invalid oracle problem")

@@ -355,6 +355,12 @@ typedef struct {
      * opacity kappa (cm^-1) and emissivity j (erg s^-1 cm^-3 sr^-1).  The
      * Lya inputs (n_hi, rho_d, p_d, lum, temp) are not used. */
     const double *band_aF, *band_kap, *band_j;
+    /* Active-bin pruning (Sec. 2.2): with prune > 0 a bin is advected only
+     * while it holds more than prune of the Lya energy in the domain (the
+     * paper's value is 1e-10), taken on the state at the start of the
+     * substep; the other bins skip step 1 (fluxes, advection, work and hoop
+     * terms) and still take steps 2 and 3.  0: every bin is advected. */
+    double prune;
 } lym1o_problem;
 
 typedef struct {
@@ -890,6 +896,38 @@ static void o_kadd(o_ksum *a, double v)
 }
 static double o_kval(const o_ksum *a) { return a->s + a->c; }
 
+/* Active bins of a substep (Sec. 2.2): E_k = dnu_k sum_cells w J_k (w: the
+ * cell volume up to a constant), active while E_k > prune sum_k E_k.  NULL
+ * when pruning is off. */
+static unsigned char *o_active_bins(const lym1o_ctx *c, const double *J)
+{
+    const lym1o_problem *p = &c->p;
+    if (!(p->prune > 0.0)) return NULL;
+    const int nb = c->nb, nx = p->nx;
+    const size_t nc = (size_t)nx * p->ny;
+    double *E = malloc(nb * sizeof(double));
+    o_ksum tot = {0.0, 0.0};
+    for (int k = 0; k < nb; ++k) {
+        o_ksum s = {0.0, 0.0};
+        for (size_t id = 0; id < nc; ++id) {
+            const double w = p->geometry == 1 ? c->V2pi[id % nx] : 1.0;
+            o_kadd(&s, w * J[(size_t)k * nc + id]);
+        }
+        E[k] = c->dnu[k] * o_kval(&s);
+        o_kadd(&tot, E[k]);
+    }
+    unsigned char *a = malloc(nb);
+    const double cut = p->prune * o_kval(&tot);
+    for (int k = 0; k < nb; ++k) a[k] = E[k] > cut;
+    free(E);
+    return a;
+}
+
+static void o_zero(double *a, size_t n)
+{
+    for (size_t i = 0; i < n; ++i) a[i] = 0.0;
+}
+
 static double o_energy(const lym1o_ctx *c, const double *J)
 {
     size_t nc = (size_t)c->p.nx * c->p.ny;
@@ -966,10 +1004,20 @@ int lym1o_substep(const lym1o_ctx *c, double dt, const double *J, const double *
         ax[id] = 0.0;
         ay[id] = 0.0;
     }
+    unsigned char *act = o_active_bins(c, J);
 
     for (int k = 0; k < nb; ++k) {
         const double *Jk = J + (size_t)k * nc, *Hxk = Hx + (size_t)k * nc, *Hyk = Hy + (size_t)k * nc;
 #define AF(id) (p->band_aF ? BND(band_aF, k, id) : c->alpha[id] * HAV(k, id) + p->rho_d[id] * p->kappa_F)
+        const int on = !act || act[k]; /* pruned bins: no step 1 */
+        if (!on) {
+            o_zero(FJx, (size_t)(nx + 1) * ny);
+            o_zero(FHxx, (size_t)(nx + 1) * ny);
+            o_zero(FHyx, (size_t)(nx + 1) * ny);
+            o_zero(FJy, (size_t)nx * (ny + 1));
+            o_zero(FHxy, (size_t)nx * (ny + 1));
+            o_zero(FHyy, (size_t)nx * (ny + 1));
+        } else {
         /* x faces: face i sits between cells i-1 and i, i = 0..nx */
 #pragma omp parallel for schedule(static)
         for (int j = 0; j < ny; ++j)
@@ -1002,6 +1050,7 @@ int lym1o_substep(const lym1o_ctx *c, double dt, const double *J, const double *
                 o_face(q[0], q[1], q[2], q[3], AF(i0), AF(i1), p->uy[i0], p->uy[i1], half_dx, half_dx,
                        &FJy[f], &FHyy[f], &FHxy[f]);
             }
+        }
         /* A3 explicit update, A4 implicit source, A5 force accumulation */
 #pragma omp parallel for schedule(static)
         for (int j = 0; j < ny; ++j)
@@ -1018,6 +1067,7 @@ int lym1o_substep(const lym1o_ctx *c, double dt, const double *J, const double *
                 o_closure(fxc, fyc, &Dxx, &Dxy, &Dyy);
                 double W = ((Dxx * Jk[id]) * c->gxx[id] + (Dyy * Jk[id]) * c->gyy[id]) +
                            (Dxy * Jk[id]) * c->gsh[id];
+                if (!on) W = 0.0;
                 Wk[id] = W;
                 size_t fxl = (size_t)j * (nx + 1) + i, fyl = (size_t)j * nx + i;
                 double divJ = (FJx[fxl + 1] - FJx[fxl]) + (FJy[fyl + nx] - FJy[fyl]);
@@ -1171,6 +1221,7 @@ int lym1o_substep(const lym1o_ctx *c, double dt, const double *J, const double *
     d.force_radial = o_kval(&fr);
     if (dg) *dg = d;
     free(FJx); free(FHxx); free(FHyx); free(FJy); free(FHxy); free(FHyy); free(Wk); free(ax); free(ay);
+    free(act);
     return 0;
 }
 
@@ -1206,10 +1257,20 @@ int lym1o_substep_cyl(const lym1o_ctx *c, double dt, const double *J, const doub
     double *FHyy = malloc((size_t)nx * (ny + 1) * sizeof(double));
     double *Wk = malloc(nc * sizeof(double));
     double *ax = calloc(nc, sizeof(double)), *ay = calloc(nc, sizeof(double));
+    unsigned char *act = o_active_bins(c, J);
 
     for (int k = 0; k < nb; ++k) {
         const double *Jk = J + (size_t)k * nc, *Hxk = Hx + (size_t)k * nc, *Hyk = Hy + (size_t)k * nc;
 #define AFC(id) (p->band_aF ? BND(band_aF, k, id) : c->alpha[id] * HAV(k, id) + p->rho_d[id] * p->kappa_F)
+        const int on = !act || act[k]; /* pruned bins: no step 1 */
+        if (!on) {
+            o_zero(FJx, (size_t)(nx + 1) * ny);
+            o_zero(FHxx, (size_t)(nx + 1) * ny);
+            o_zero(FHyx, (size_t)(nx + 1) * ny);
+            o_zero(FJy, (size_t)nx * (ny + 1));
+            o_zero(FHxy, (size_t)nx * (ny + 1));
+            o_zero(FHyy, (size_t)nx * (ny + 1));
+        } else {
         /* R faces: face i between cells i-1 and i */
 #pragma omp parallel for schedule(static)
         for (int j = 0; j < ny; ++j)
@@ -1252,6 +1313,7 @@ int lym1o_substep_cyl(const lym1o_ctx *c, double dt, const double *J, const doub
                 o_face(q[0], q[1], q[2], q[3], AFC(i0), AFC(i1), uz[0], uz[1], half_dx, half_dx,
                        &FJy[f], &FHyy[f], &FHxy[f]);
             }
+        }
 #pragma omp parallel for schedule(static)
         for (int j = 0; j < ny; ++j)
             for (int i = 0; i < nx; ++i) {
@@ -1271,6 +1333,7 @@ int lym1o_substep_cyl(const lym1o_ctx *c, double dt, const double *J, const doub
                 double W = (((Dxx * Jk[id]) * c->gxx[id] + (Dyy * Jk[id]) * c->gyy[id]) +
                             (Dxy * Jk[id]) * c->gsh[id]) +
                            (Dpp * Jk[id]) * c->gphi[id];
+                if (!on) W = 0.0;
                 Wk[id] = W;
                 size_t fxl = (size_t)j * (nx + 1) + i, fyl = (size_t)j * nx + i;
                 double divJ = ((c->AR[i + 1] * FJx[fxl + 1] - c->AR[i] * FJx[fxl]) +
@@ -1278,6 +1341,7 @@ int lym1o_substep_cyl(const lym1o_ctx *c, double dt, const double *J, const doub
                 double divHx = ((c->AR[i + 1] * FHxx[fxl + 1] - c->AR[i] * FHxx[fxl]) +
                                 c->AZ[i] * (FHxy[fyl + nx] - FHxy[fyl])) / c->Vol[i] -
                                (Dpp * Jk[id]) * c->invR[i];
+                if (!on) divHx = 0.0;
                 double divHy = ((c->AR[i + 1] * FHyx[fxl + 1] - c->AR[i] * FHyx[fxl]) +
                                 c->AZ[i] * (FHyy[fyl + nx] - FHyy[fyl])) / c->Vol[i];
                 double J1 = Jk[id] - cdt * (divJ + W / O_C);
@@ -1418,6 +1482,7 @@ int lym1o_substep_cyl(const lym1o_ctx *c, double dt, const double *J, const doub
     d.force_radial = o_kval(&fr);
     if (dg) *dg = d;
     free(FJx); free(FHxx); free(FHyx); free(FJy); free(FHxy); free(FHyy); free(Wk); free(ax); free(ay);
+    free(act);
     return 0;
 }
 
