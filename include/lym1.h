@@ -409,6 +409,20 @@ typedef struct {
  */
 int lym1_set_temperature(lym1_ctx *ctx, const double *temp_field);
 
+/*
+ * Active-bin pruning (Sec. 2.2): with cut > 0 (the paper uses 1e-10) each
+ * substep first takes, on the GPU, the energy of every bin, dnu_k sum_cells
+ * V_cell J_k, and advects only the bins holding more than cut of the total;
+ * the others skip step 1 (no fluxes, advection, work or hoop terms: J' = J,
+ * H' = H) and still take steps 2 and 3.  cut = 0 (the default) advects every
+ * bin.  Pruning changes results where it skips a bin; it pays off once many
+ * bins hold a negligible share of the energy.  A lym1_batch captures the
+ * setting of its contexts at creation: after a change of the cut, create the
+ * batch anew (lym1_batch_substeps returns LYM1_EINVAL until then).
+ * Errors: LYM1_EINVAL for a null ctx or cut outside [0, 1); LYM1_ENOMEM.
+ */
+int lym1_set_pruning(lym1_ctx *ctx, double cut);
+
 int lym1_create_bands(const lym1_grid *grid, const lym1_bands *bands, const double *ux,
                       const double *uy, double c_tilde, double cfl, int precision,
                       void *cuda_stream, lym1_ctx **out);

@@ -43,6 +43,12 @@ struct lym1_ctx {
   // luminosity sum on the device (lym1_set_sources), read back when needed
   double* lsum = nullptr;
   int L_pending = 0;
+  // active-bin pruning (lym1_set_pruning): cut, per-bin energies and flags;
+  // prune_gen changes whenever the cut changes
+  double prune = 0.0;
+  double* Ebin = nullptr;
+  unsigned char* active = nullptr;
+  unsigned prune_gen = 0;
   long long substeps_done = 0;
   cudaStream_t stream = nullptr;
   BinTables tab;
@@ -194,10 +200,12 @@ DeviceView make_view(const lym1_ctx* c, double dt) {
   v.spec = c->spec_on ? c->spec : nullptr;
   v.spec_unit = (4.0 * kPi) / kLight;
   v.nf = c->geometry == 1 ? (c->nx + c->ny) : 2 * (c->nx + c->ny);
-  v.pt = c->pt;
+  // table mode, with bit 4 for the transport's active-bin pruning variant
+  v.pt = c->pt | (c->prune > 0.0 ? 4 : 0);
   v.Hc = c->Hc;
   v.Gc = c->Gc;
   v.Kb = c->Kb;
+  v.active = c->prune > 0.0 ? c->active : nullptr;
   v.gmaxc = c->gmaxc;
   v.Kcc = c->Kcc;
   v.hkTc = c->hkTc;
@@ -290,7 +298,21 @@ struct KernelTimer {
   }
 };
 
+// active-bin pruning: the flags of this substep from the current state,
+// enqueued before its transport
+int prune_launch(lym1_ctx* c, cudaStream_t s) {
+  if (!(c->prune > 0.0)) return LYM1_OK;
+  LYM1_TRYK(launch_active_bins(static_cast<int>(c->selem), c->A[0], c->nb, c->nc, c->nx,
+                               c->geometry == 1 ? c->g_wv : nullptr, c->t_dnu, c->prune, c->Ebin,
+                               c->active, s));
+  return LYM1_OK;
+}
+
 int one_substep(lym1_ctx* c, double dt) {
+  {
+    const int rc = prune_launch(c, c->stream);
+    if (rc != LYM1_OK) return rc;
+  }
   const DeviceView v = make_view(c, dt);
   {
     KernelTimer t(c, 0);
@@ -393,12 +415,14 @@ void drop_events(lym1_ctx* c) {
 struct lym1_batch {
   std::vector<lym1_ctx*> ctxs;
   int precision = 0, nb = 0, nT = 0, nF = 0, geometry = 0, pt = 0;
+  int tpt = 0;  // the transport's mode: pt, with bit 4 if a context prunes
   cudaStream_t ctx_stream = nullptr, bs = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr, t0 = nullptr, t1 = nullptr;
   DeviceView *viewsT = nullptr, *viewsF = nullptr;
   void *itemsT = nullptr, *itemsF = nullptr;
   FinalizeJob* jobs = nullptr;
   std::vector<unsigned> gens;  // view_gen of each context at the last upload
+  std::vector<unsigned> prune_gens;  // prune_gen of each context at creation
   int gridT = 0, gridF = 0;
   // tuning state: candidate persistent grids (multiples of the SM count)
   std::vector<int> candT, candF;
@@ -442,11 +466,15 @@ int refresh_views(lym1_batch* b, cudaStream_t s) {
 
 int batch_launch(lym1_batch* b, cudaStream_t s) {
   const int n = static_cast<int>(b->ctxs.size());
+  for (lym1_ctx* c : b->ctxs) {
+    const int rc = prune_launch(c, s);
+    if (rc != LYM1_OK) return rc;
+  }
   if (b->precision == LYM1_FP64_DET) {
-    LYM1_TRYK(launch_batched_det(0, b->geometry, b->pt, b->viewsT, b->itemsT, b->nT, b->gridT, b->nb, s));
+    LYM1_TRYK(launch_batched_det(0, b->geometry, b->tpt, b->viewsT, b->itemsT, b->nT, b->gridT, b->nb, s));
     LYM1_TRYK(launch_batched_det(1, b->geometry, b->pt, b->viewsF, b->itemsF, b->nF, b->gridF, b->nb, s));
   } else {
-    LYM1_TRYK(launch_batched_fast(b->precision, 0, b->geometry, b->pt, b->viewsT, b->itemsT, b->nT,
+    LYM1_TRYK(launch_batched_fast(b->precision, 0, b->geometry, b->tpt, b->viewsT, b->itemsT, b->nT,
                                   b->gridT, b->nb, s));
     LYM1_TRYK(launch_batched_fast(b->precision, 1, b->geometry, b->pt, b->viewsF, b->itemsF, b->nF,
                                   b->gridF, b->nb, s));
@@ -459,13 +487,17 @@ int batch_launch(lym1_batch* b, cudaStream_t s) {
 // bracketed by profiling events (no graph)
 int batch_launch_timed(lym1_batch* b, lym1_ctx* c) {
   const int n = static_cast<int>(b->ctxs.size());
+  for (lym1_ctx* x : b->ctxs) {
+    const int rc = prune_launch(x, c->stream);
+    if (rc != LYM1_OK) return rc;
+  }
   {
     KernelTimer t(c, 0);
     if (b->precision == LYM1_FP64_DET)
-      LYM1_TRYK(launch_batched_det(0, b->geometry, b->pt, b->viewsT, b->itemsT, b->nT, b->gridT,
+      LYM1_TRYK(launch_batched_det(0, b->geometry, b->tpt, b->viewsT, b->itemsT, b->nT, b->gridT,
                                    b->nb, c->stream));
     else
-      LYM1_TRYK(launch_batched_fast(b->precision, 0, b->geometry, b->pt, b->viewsT, b->itemsT, b->nT,
+      LYM1_TRYK(launch_batched_fast(b->precision, 0, b->geometry, b->tpt, b->viewsT, b->itemsT, b->nT,
                                     b->gridT, b->nb, c->stream));
   }
   {
@@ -1092,6 +1124,9 @@ int lym1_batch_create(lym1_ctx* const* ctxs, int n_ctx, lym1_batch** out) {
   b->precision = ctxs[0]->precision;
   b->geometry = ctxs[0]->geometry;
   b->pt = ctxs[0]->pt;
+  b->tpt = b->pt;
+  for (int i = 0; i < n_ctx; ++i)
+    if (ctxs[i]->prune > 0.0) b->tpt = b->pt | 4;
   b->nb = ctxs[0]->nb;
   b->ctx_stream = ctxs[0]->stream;
   std::vector<DeviceView> vT, vF;
@@ -1104,6 +1139,7 @@ int lym1_batch_create(lym1_ctx* const* ctxs, int n_ctx, lym1_batch** out) {
     vT.push_back(v);
     vF.push_back(w);
     b->gens.push_back(c->view_gen);
+    b->prune_gens.push_back(c->prune_gen);
     const int gx = (c->nx + kTileX - 1) / kTileX, gy = (c->ny + kTileY - 1) / kTileY;
     for (int by = 0; by < gy; ++by)
       for (int bx = 0; bx < gx; ++bx) iT.push_back({i, bx * kTileX, by * kTileY, by * gx + bx});
@@ -1143,8 +1179,8 @@ int lym1_batch_create(lym1_ctx* const* ctxs, int n_ctx, lym1_batch** out) {
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   if (nsm < 1) nsm = 1;
   const int rT = b->precision == LYM1_FP64_DET
-                     ? resident_blocks_det(0, b->geometry, b->pt, b->nb)
-                     : resident_blocks_fast(b->precision, 0, b->geometry, b->pt, b->nb);
+                     ? resident_blocks_det(0, b->geometry, b->tpt, b->nb)
+                     : resident_blocks_fast(b->precision, 0, b->geometry, b->tpt, b->nb);
   const int rF = b->precision == LYM1_FP64_DET
                      ? resident_blocks_det(1, b->geometry, b->pt, b->nb)
                      : resident_blocks_fast(b->precision, 1, b->geometry, b->pt, b->nb);
@@ -1159,6 +1195,10 @@ int lym1_batch_create(lym1_ctx* const* ctxs, int n_ctx, lym1_batch** out) {
 
 int lym1_batch_substeps(lym1_batch* b, int n) {
   if (!b || n < 0) return LYM1_EINVAL;
+  // the captured launches include the pruning kernels of the contexts that
+  // pruned at creation: switching pruning since then needs a new batch
+  for (size_t i = 0; i < b->ctxs.size(); ++i)
+    if (b->ctxs[i]->prune_gen != b->prune_gens[i]) return LYM1_EINVAL;
   if (n == 0) return LYM1_OK;
   LYM1_TRY(cudaEventRecord(b->ev_in, b->ctx_stream));
   LYM1_TRY(cudaStreamWaitEvent(b->bs, b->ev_in, 0));
@@ -1352,4 +1392,27 @@ int lym1_set_temperature(lym1_ctx* c, const double* temp_field) {
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) rc = LYM1_ECUDA;
   cudaFree(scr);
   return rc;
+}
+
+int lym1_set_pruning(lym1_ctx* c, double cut) {
+  if (!c || !(cut >= 0.0) || !(cut < 1.0)) return LYM1_EINVAL;
+  if (cut > 0.0 && !c->active) {
+    int rc = dalloc_t(c, &c->Ebin, static_cast<size_t>(c->nb));
+    if (rc == LYM1_OK) rc = dalloc_t(c, &c->active, static_cast<size_t>(c->nb));
+    if (rc != LYM1_OK) return rc;
+  }
+  // the captured launches hold the cut by value: any change rebuilds them
+  const bool changed = cut != c->prune;
+  c->prune = cut;
+  if (changed) {
+    c->prune_gen += 1;
+    c->view_gen += 1;
+    // the graph-replayed path captured its launches with the old setting
+    if (c->self_batch) {
+      LYM1_TRY(cudaStreamSynchronize(c->stream));
+      lym1_batch_destroy(c->self_batch);
+      c->self_batch = nullptr;
+    }
+  }
+  return LYM1_OK;
 }

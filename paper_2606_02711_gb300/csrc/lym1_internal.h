@@ -160,6 +160,9 @@ struct DeviceView {
   // broad bands (pt = 2): Hc holds alpha_F, Gc the emissivity (over gmaxc in
   // FP32) and Kb the absorption opacity kappa of each [band][cell]
   const void* Kb = nullptr;
+  // active-bin pruning: 1 per bin that step 1 advects this substep, or
+  // nullptr (every bin)
+  const unsigned char* active = nullptr;
   const double* gmaxc = nullptr;
   const double* Kcc = nullptr;
   const double* hkTc = nullptr;
@@ -209,6 +212,11 @@ int launch_force_reduce(const double* fx, const double* fy, int nx, int ny, doub
 // counter word; kSumWork doubles)
 constexpr int kSumWork = 154;
 int launch_sum_cells(const double* a, long long n, double* work, void* stream);
+// active-bin pruning: E[k] = dnu_k sum_cells w J_k (w = wcol[column], or 1),
+// then active[k] = E[k] > cut sum_k E[k]
+int launch_active_bins(int selem, const void* J, int nb, long long nc, int nx, const double* wcol,
+                       const double* dnu, double cut, double* E, unsigned char* active,
+                       void* stream);
 // per-cell A0 tables of a temperature field on the device (n = bins of the edges)
 int launch_cell_tables(int selem, const double* T, const double* nhi, const double* edges, int n,
                        int gray, int recoil, int geometry, double dx, long long nc, void* Hc,

@@ -387,6 +387,10 @@ __device__ __forceinline__ double block_max(double v, double* red) {
 // ------------------------------------------------------------ transport kernel
 template <class P, int G, int PT>
 __device__ __forceinline__ void transport_tile(const DeviceView& v, int x0, int y0, int blk) {
+  // table mode (0 uniform T, 1 temperature field, 2 broad bands) and, in bit 4,
+  // active-bin pruning: without it the tile compiles with no pruning code
+  constexpr int TM = PT & 3;
+  constexpr bool PR = (PT & 4) != 0;
   using S = typename P::S;
   using F = typename P::F;
   using I = typename P::I;
@@ -398,7 +402,7 @@ __device__ __forceinline__ void transport_tile(const DeviceView& v, int x0, int 
   __shared__ F xJ[TY][TX + 1], xN[TY][TX + 1], xT[TY][TX + 1];
   __shared__ F yJ[TY + 1][TX], yN[TY + 1][TX], yT[TY + 1][TX];
   __shared__ F sdl[2][G == 1 ? TX + 1 : 1];  // axisymmetric: centroid distances per R face
-  __shared__ F qH[PT ? QY : 1][PT ? QX : 1];  // temperature field: <H>_k of the one-cell halo
+  __shared__ F qH[TM ? QY : 1][TM ? QX : 1];  // temperature field: <H>_k of the one-cell halo
   const S* __restrict__ Hcs = static_cast<const S*>(v.Hc);
   const S* __restrict__ Gcs = static_cast<const S*>(v.Gc);
   const S* __restrict__ Kbs = static_cast<const S*>(v.Kb);  // bands: kappa per [band][cell]
@@ -469,7 +473,10 @@ __device__ __forceinline__ void transport_tile(const DeviceView& v, int x0, int 
     const long long base = static_cast<long long>(k) * nc;
     const double Hk_d = v.t_H[k];
     const F Hk = F(Hk_d);
-    if constexpr (PT) {  // <H>_k of the one-cell halo at each cell's temperature
+    // active-bin pruning: a bin left out this substep takes no step 1 (zero
+    // face fluxes, J' = J, H' = H); the flag is the same for the whole block
+    const bool on = !PR || !v.active || v.active[k];
+    if constexpr (TM) {  // <H>_k of the one-cell halo at each cell's temperature
       for (int idx = tid; idx < QX * QY; idx += NT) {
         const int lx = idx % QX, ly = idx / QX;
         bool fxg, fyg;
@@ -510,11 +517,22 @@ __device__ __forceinline__ void transport_tile(const DeviceView& v, int x0, int 
     __syncthreads();
     // phase B: every x and y face of the tile once
     for (int f = tid; f < NXF + NYF; f += NT) {
+      if (!on) {
+        if (f < NXF) {
+          const int fi = f % (TX + 1), fj = f / (TX + 1);
+          xJ[fj][fi] = xN[fj][fi] = xT[fj][fi] = F(0);
+        } else {
+          const int g = f - NXF;
+          const int fi = g % TX, fj = g / TX;
+          yJ[fj][fi] = yN[fj][fi] = yT[fj][fi] = F(0);
+        }
+        continue;
+      }
       if (f < NXF) {
         const int fi = f % (TX + 1), fj = f / (TX + 1);
         const int r = fj + 2;
-        const F aF0 = qA[fj + 1][fi] * (PT ? qH[fj + 1][fi] : Hk) + qR[fj + 1][fi] * kF_f;
-        const F aF1 = qA[fj + 1][fi + 1] * (PT ? qH[fj + 1][fi + 1] : Hk) + qR[fj + 1][fi + 1] * kF_f;
+        const F aF0 = qA[fj + 1][fi] * (TM ? qH[fj + 1][fi] : Hk) + qR[fj + 1][fi] * kF_f;
+        const F aF1 = qA[fj + 1][fi + 1] * (TM ? qH[fj + 1][fi + 1] : Hk) + qR[fj + 1][fi + 1] * kF_f;
         F dl0 = half_dx, dl1 = half_dx;
         if constexpr (G == 1) {
           dl0 = sdl[0][fi];
@@ -528,8 +546,8 @@ __device__ __forceinline__ void transport_tile(const DeviceView& v, int x0, int 
         const int g = f - NXF;
         const int fi = g % TX, fj = g / TX;
         const int cc = fi + 2;
-        const F aF0 = qA[fj][fi + 1] * (PT ? qH[fj][fi + 1] : Hk) + qR[fj][fi + 1] * kF_f;
-        const F aF1 = qA[fj + 1][fi + 1] * (PT ? qH[fj + 1][fi + 1] : Hk) + qR[fj + 1][fi + 1] * kF_f;
+        const F aF0 = qA[fj][fi + 1] * (TM ? qH[fj][fi + 1] : Hk) + qR[fj][fi + 1] * kF_f;
+        const F aF1 = qA[fj + 1][fi + 1] * (TM ? qH[fj + 1][fi + 1] : Hk) + qR[fj + 1][fi + 1] * kF_f;
         face_flux<F, P::DET>(sJ[fj][cc], sfy[fj][cc], sfx[fj][cc], sJ[fj + 1][cc], sfy[fj + 1][cc],
                      sfx[fj + 1][cc], sJ[fj + 2][cc], sfy[fj + 2][cc], sfx[fj + 2][cc],
                      sJ[fj + 3][cc], sfy[fj + 3][cc], sfx[fj + 3][cc], aF0, aF1, qUy[fj][fi + 1],
@@ -571,13 +589,19 @@ __device__ __forceinline__ void transport_tile(const DeviceView& v, int x0, int 
           Hy1 = Hy - cdx * divHy;
         }
       }
-      const I aH = alpha_c * (PT ? I(Hcs[base + cell]) : I(Hk_d));
-      const I kap = (PT == 2) ? I(Kbs[base + cell]) : rho_c * kabs + pd_c * aH;
+      if (!on) {  // pruned bin: no step 1
+        J1 = J;
+        Hx1 = Hx;
+        Hy1 = Hy;
+        W = F(0);
+      }
+      const I aH = alpha_c * (TM ? I(Hcs[base + cell]) : I(Hk_d));
+      const I kap = (TM == 2) ? I(Kbs[base + cell]) : rho_c * kabs + pd_c * aH;
       const I aF = aH + rho_c * kF;
       // j_k = L w_k / (4 pi V dnu_k): formed in FP64 (L ~ 1e39 erg/s and
       // w_k / (4 pi V dnu_k) ~ 1e-58 are both outside the FP32 range); on the
       // axisymmetric grid lum already holds L / (2 pi Vol) and gem_k has V = 1
-      const I js = (lum_d != 0.0) ? I(lum_d * (PT ? double(Gcs[base + cell]) : v.t_gem[k])) : I(0);
+      const I js = (lum_d != 0.0) ? I(lum_d * (TM ? double(Gcs[base + cell]) : v.t_gem[k])) : I(0);
       I J2, Hx2, Hy2;
       if constexpr (P::DET) {
         J2 = (I(J1) + cdt * js) / (I(1) + cdt * kap);
@@ -770,6 +794,10 @@ __device__ __forceinline__ void face_flux_f32(float Jm, float nm, float tm, floa
 // FP32 for LYM1_MIXED_FAST).
 template <class P, int G, int PT>
 __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, int y0, int blk) {
+  // table mode (0 uniform T, 1 temperature field, 2 broad bands) and, in bit 4,
+  // active-bin pruning: without it the tile compiles with no pruning code
+  constexpr int TM = PT & 3;
+  constexpr bool PR = (PT & 4) != 0;
   using I = typename P::I;
   constexpr int TX = kTileX, TY = kTileY, SX = TX + 4, SY = TY + 4;
   constexpr int NT = TX * TY;
@@ -901,7 +929,7 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
   // emissivity j_k = (L_cell gem_max) (gem_k / gem_max): both factors lie in
   // the FP32 range, unlike L_cell (~1e39 erg/s) and gem_k (~1e-58) alone
   const bool src = lum_d != 0.0;
-  const double gmax_c = PT ? (valid ? v.gmaxc[cell] : 1.0) : v.gem_max;
+  const double gmax_c = TM ? (valid ? v.gmaxc[cell] : 1.0) : v.gem_max;
   const float jsc = float(lum_d * gmax_c);
   const bool bnd = valid && (G == 1 ? (gx == nx - 1 || gy == ny - 1)
                                      : (gx == 0 || gx == nx - 1 || gy == 0 || gy == ny - 1));
@@ -914,7 +942,7 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
     pX1 = Hxin[off1];
     pY1 = Hyin[off1];
   }
-  if constexpr (PT) {
+  if constexpr (TM) {
     pH0 = Hcf[off0];
     if (has1) pH1 = Hcf[off1];
   }
@@ -923,6 +951,9 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
     const int b = k & 1;
     const float4 tb = tab4[k];  // (<H>_k, dnu_k, gem_k / gem_max, J_act,k)
     const float Hk = tb.x;
+    // active-bin pruning: a bin left out this substep takes no step 1 (zero
+    // face fluxes, J' = J, H' = H); the flag is the same for the whole block
+    const bool on = !PR || !v.active || v.active[k];
     {  // halo entries of bin k: registers -> shared, with primitives and alpha_F
       float J0 = pJ0, X0 = pX0, Y0 = pY0, J1 = pJ1, X1 = pX1, Y1 = pY1;
       if (vz0) J0 = X0 = Y0 = 0.0f;
@@ -934,12 +965,12 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
         Y1 *= sy1;
       }
       const float r0 = J0 > kTinyJ ? frcp(J0) : 0.0f;
-      sq[b][ey0][ex0] = make_float4(J0, X0 * r0, Y0 * r0, al0 * (PT ? pH0 : Hk) + rk0);
+      sq[b][ey0][ex0] = make_float4(J0, X0 * r0, Y0 * r0, al0 * (TM ? pH0 : Hk) + rk0);
       sHx[b][ey0][ex0] = X0;
       sHy[b][ey0][ex0] = Y0;
       if (has1) {
         const float r1 = J1 > kTinyJ ? frcp(J1) : 0.0f;
-        sq[b][ey1][ex1] = make_float4(J1, X1 * r1, Y1 * r1, al1 * (PT ? pH1 : Hk) + rk1);
+        sq[b][ey1][ex1] = make_float4(J1, X1 * r1, Y1 * r1, al1 * (TM ? pH1 : Hk) + rk1);
         sHx[b][ey1][ex1] = X1;
         sHy[b][ey1][ex1] = Y1;
       }
@@ -957,7 +988,7 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
         pX1 = Xn[off1];
         pY1 = Yn[off1];
       }
-      if constexpr (PT) {
+      if constexpr (TM) {
         pH0 = Hcf[nbase + off0];
         if (has1) pH1 = Hcf[nbase + off1];
       }
@@ -983,19 +1014,26 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
                     (q0.w + q1.w) * half_dx, wf, oJ, oN, oT);
       yF[fj][fi] = make_float4(oJ, oN, oT, 0.0f);
     };
-    xface(tx, ty, wfx, dlA0, dlA1);
-    yface(tx, ty, wfy);
-    if (xtra) {  // one evaluation for both kinds of extra face
-      const float4* q = xisx ? &sq[b][xfj + 2][xfi] : &sq[b][xfj][xfi + 2];
-      const int st = xisx ? 1 : SX;
-      const float4 qm = q[0], q0 = q[st], q1 = q[2 * st], q2 = q[3 * st];
-      const float tau = q0.w * dlB0 + q1.w * dlB1;
-      float oJ, oN, oT;
-      face_flux_f32(qm.x, xisx ? qm.y : qm.z, xisx ? qm.z : qm.y, q0.x, xisx ? q0.y : q0.z,
-                    xisx ? q0.z : q0.y, q1.x, xisx ? q1.y : q1.z, xisx ? q1.z : q1.y, q2.x,
-                    xisx ? q2.y : q2.z, xisx ? q2.z : q2.y, tau, wf2, oJ, oN, oT);
-      float4* dst = xisx ? &xF[xfj][TX] : &yF[TY][xfi];
-      *dst = make_float4(oJ, oN, oT, 0.0f);
+    if (on) {
+      xface(tx, ty, wfx, dlA0, dlA1);
+      yface(tx, ty, wfy);
+      if (xtra) {  // one evaluation for both kinds of extra face
+        const float4* q = xisx ? &sq[b][xfj + 2][xfi] : &sq[b][xfj][xfi + 2];
+        const int st = xisx ? 1 : SX;
+        const float4 qm = q[0], q0 = q[st], q1 = q[2 * st], q2 = q[3 * st];
+        const float tau = q0.w * dlB0 + q1.w * dlB1;
+        float oJ, oN, oT;
+        face_flux_f32(qm.x, xisx ? qm.y : qm.z, xisx ? qm.z : qm.y, q0.x, xisx ? q0.y : q0.z,
+                      xisx ? q0.z : q0.y, q1.x, xisx ? q1.y : q1.z, xisx ? q1.z : q1.y, q2.x,
+                      xisx ? q2.y : q2.z, xisx ? q2.z : q2.y, tau, wf2, oJ, oN, oT);
+        float4* dst = xisx ? &xF[xfj][TX] : &yF[TY][xfi];
+        *dst = make_float4(oJ, oN, oT, 0.0f);
+      }
+    } else {  // pruned bin: zero fluxes on this thread's faces
+      const float4 z4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      xF[ty][tx] = z4;
+      yF[ty][tx] = z4;
+      if (xtra) *(xisx ? &xF[xfj][TX] : &yF[TY][xfi]) = z4;
     }
     __syncthreads();
     if (valid) {
@@ -1020,24 +1058,25 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
         divHx = (xr.y - xl.y) + (yt.z - yb.z);
         divHy = (xr.z - xl.z) + (yt.y - yb.y);
       }
-      const float J1 = J - cdt_f * (divJ * inv_dx + W * inv_c);
-      const float Hx1 = Hx - cdt_dx * divHx;
-      const float Hy1 = Hy - cdt_dx * divHy;
+      if (!on) W = 0.0f;  // pruned bin: no step 1
+      const float J1 = on ? J - cdt_f * (divJ * inv_dx + W * inv_c) : J;
+      const float Hx1 = on ? Hx - cdt_dx * divHx : Hx;
+      const float Hy1 = on ? Hy - cdt_dx * divHy : Hy;
       I aH, dnu;
       if constexpr (sizeof(I) == 8) {
-        aH = alpha_c * (PT ? double(Hcf[base + cell]) : v.t_H[k]);
+        aH = alpha_c * (TM ? double(Hcf[base + cell]) : v.t_H[k]);
         dnu = v.t_dnu[k];
       } else {
-        aH = alpha_c * (PT ? Hcf[base + cell] : Hk);
+        aH = alpha_c * (TM ? Hcf[base + cell] : Hk);
         dnu = tb.y;
       }
-      const I kap = (PT == 2) ? I(Kbf[base + cell]) : rho_c * kabs + pd_c * aH;
+      const I kap = (TM == 2) ? I(Kbf[base + cell]) : rho_c * kabs + pd_c * aH;
       const I aF = aH + rho_c * kF;
       I js;
       if constexpr (sizeof(I) == 8)
-        js = src ? lum_d * (PT ? gmax_c * double(Gcf[base + cell]) : v.t_gem[k]) : 0.0;
+        js = src ? lum_d * (TM ? gmax_c * double(Gcf[base + cell]) : v.t_gem[k]) : 0.0;
       else
-        js = src ? jsc * (PT ? Gcf[base + cell] : tb.z) : 0.0f;
+        js = src ? jsc * (TM ? Gcf[base + cell] : tb.z) : 0.0f;
       I J2, Hx2, Hy2;
       if constexpr (sizeof(I) == 8) {
         J2 = (I(J1) + cdt * js) / (I(1) + cdt * kap);
@@ -1873,14 +1912,17 @@ int launch_freq_batched_g(const DeviceView* views, const BatchItem* items, int n
 }
 
 // (geometry, temperature mode) -> template instance
-// transport: pt 0 = uniform temperature, 1 = temperature field, 2 = broad bands
-#define LYM1_GPT(F_, ...)                                                               \
-  (geometry == 1 ? (pt == 2   ? F_<P, 1, 2>(__VA_ARGS__)                                \
-                    : pt == 1 ? F_<P, 1, 1>(__VA_ARGS__)                                \
-                              : F_<P, 1, 0>(__VA_ARGS__))                               \
-                 : (pt == 2   ? F_<P, 0, 2>(__VA_ARGS__)                                \
-                    : pt == 1 ? F_<P, 0, 1>(__VA_ARGS__)                                \
-                              : F_<P, 0, 0>(__VA_ARGS__)))
+// transport: pt & 3 = 0 uniform temperature, 1 temperature field, 2 broad
+// bands; pt & 4 = active-bin pruning
+#define LYM1_PT_(F_, G_, ...)                                                   \
+  (pt == 6   ? F_<P, G_, 6>(__VA_ARGS__)                                        \
+   : pt == 5 ? F_<P, G_, 5>(__VA_ARGS__)                                        \
+   : pt == 4 ? F_<P, G_, 4>(__VA_ARGS__)                                        \
+   : pt == 2 ? F_<P, G_, 2>(__VA_ARGS__)                                        \
+   : pt == 1 ? F_<P, G_, 1>(__VA_ARGS__)                                        \
+             : F_<P, G_, 0>(__VA_ARGS__))
+#define LYM1_GPT(F_, ...) \
+  (geometry == 1 ? LYM1_PT_(F_, 1, __VA_ARGS__) : LYM1_PT_(F_, 0, __VA_ARGS__))
 // frequency step: bands have none (pt 2 is refused before any launch)
 #define LYM1_GPT_F(F_, ...)                                                        \
   (geometry == 1 ? (pt ? F_<P, 1, 1>(__VA_ARGS__) : F_<P, 1, 0>(__VA_ARGS__)) \
@@ -1895,6 +1937,7 @@ int launch_transport_batched_t(int geometry, int pt, const DeviceView* views, co
 template <class P>
 int launch_freq_batched_t(int geometry, int pt, const DeviceView* views, const BatchItem* items,
                           int n, int grid, int nb_max, cudaStream_t st) {
+  pt &= 3;
   if (pt == 2) return static_cast<int>(cudaErrorInvalidValue);
   return LYM1_GPT_F(launch_freq_batched_g, views, items, n, grid, nb_max, st);
 }
@@ -1939,6 +1982,7 @@ int max_resident_transport(int geometry, int pt, int nb_max) {
 
 template <class P>
 int max_resident_freq(int geometry, int pt, int nb_max) {
+  pt &= 3;
   if (pt == 2) return 1;
   return LYM1_GPT_F(max_resident_freq_g, nb_max);
 }
@@ -1972,7 +2016,7 @@ int launch_transport_t(const DeviceView& v, cudaStream_t st) {
 
 template <class P>
 int launch_freq_t(const DeviceView& v, cudaStream_t st) {
-  const int geometry = v.geometry, pt = v.pt;
+  const int geometry = v.geometry, pt = v.pt & 3;
   if (pt == 2) return static_cast<int>(cudaErrorInvalidValue);
   return LYM1_GPT_F(launch_freq_g, v, st);
 }

@@ -481,6 +481,41 @@ int launch_cell_tables(int selem, const double* T, const double* nhi, const doub
   return static_cast<int>(cudaGetLastError());
 }
 
+// Active-bin pruning (Sec. 2.2): the energy of each bin, dnu_k sum_cells w J_k
+// with w the column weight of the axisymmetric grid (1 on the Cartesian one),
+// in a fixed order (one block per bin); then, in one thread, the total in bin
+// order and the strict cut of the bins that step 1 advects.
+template <class S>
+__global__ void __launch_bounds__(256) bin_energy_kernel(const S* J, long long nc, int nx,
+                                                         const double* wcol, const double* dnu,
+                                                         double* E) {
+  __shared__ double red[8];
+  const S* Jk = J + static_cast<long long>(blockIdx.x) * nc;
+  double s = 0.0;
+  for (long long id = threadIdx.x; id < nc; id += 256)
+    s += wcol ? double(Jk[id]) * wcol[id % nx] : double(Jk[id]);
+  s = block_sum<256>(s, red);
+  if (threadIdx.x == 0) E[blockIdx.x] = dnu[blockIdx.x] * s;
+}
+
+__global__ void active_bins_kernel(const double* E, int nb, double cut, unsigned char* active) {
+  double tot = 0.0;
+  for (int k = 0; k < nb; ++k) tot += E[k];
+  const double c = cut * tot;
+  for (int k = 0; k < nb; ++k) active[k] = E[k] > c ? 1 : 0;
+}
+
+int launch_active_bins(int selem, const void* J, int nb, long long nc, int nx, const double* wcol,
+                       const double* dnu, double cut, double* E, unsigned char* active, void* st) {
+  const cudaStream_t s = static_cast<cudaStream_t>(st);
+  if (selem == 8)
+    bin_energy_kernel<double><<<nb, 256, 0, s>>>(static_cast<const double*>(J), nc, nx, wcol, dnu, E);
+  else
+    bin_energy_kernel<float><<<nb, 256, 0, s>>>(static_cast<const float*>(J), nc, nx, wcol, dnu, E);
+  active_bins_kernel<<<1, 1, 0, s>>>(E, nb, cut, active);
+  return static_cast<int>(cudaGetLastError());
+}
+
 // Sum of a per-cell array (the luminosity), in a fixed order: a fixed grid of
 // grid-stride block partials, which the last block to finish adds in block order
 // (the count returns to 0 for the next call).  Nothing waits on another block.

@@ -88,6 +88,7 @@ SIGNATURES = {
                                     C.POINTER(C.c_void_p)]),
     "lym1_bands_update": (C.c_int, [C.c_void_p, _PD, _PD, _PD]),
     "lym1_set_temperature": (C.c_int, [C.c_void_p, _PD]),
+    "lym1_set_pruning": (C.c_int, [C.c_void_p, C.c_double]),
     "lym1_dynamic_ctilde": (C.c_int, [C.c_void_p, _PD, C.c_double, C.c_double, _PD]),
     "lym1_create": (C.c_int, [C.POINTER(lym1_grid), C.POINTER(lym1_groups),
                               C.POINTER(lym1_opacities), C.POINTER(C.c_void_p)]),
@@ -247,6 +248,10 @@ class Context:
         self.dt_cfl = inf["dt_cfl"]
         self.precision = int(precision)
         return self
+
+    def set_pruning(self, cut: float = 1e-10):
+        """``lym1_set_pruning``: advect only bins above cut of the energy (0: all)."""
+        _check(lib().lym1_set_pruning(self.handle, float(cut)), "lym1_set_pruning")
 
     def set_temperature(self, temp):
         """``lym1_set_temperature``: per-cell tables for new gas temperatures."""
