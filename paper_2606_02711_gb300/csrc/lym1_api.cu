@@ -1397,7 +1397,7 @@ int lym1_set_temperature(lym1_ctx* c, const double* temp_field) {
 int lym1_set_pruning(lym1_ctx* c, double cut) {
   if (!c || !(cut >= 0.0) || !(cut < 1.0)) return LYM1_EINVAL;
   if (cut > 0.0 && !c->active) {
-    int rc = dalloc_t(c, &c->Ebin, static_cast<size_t>(c->nb));
+    int rc = dalloc_t(c, &c->Ebin, static_cast<size_t>(c->nb) * 17);
     if (rc == LYM1_OK) rc = dalloc_t(c, &c->active, static_cast<size_t>(c->nb));
     if (rc != LYM1_OK) return rc;
   }

@@ -213,7 +213,8 @@ int launch_force_reduce(const double* fx, const double* fy, int nx, int ny, doub
 constexpr int kSumWork = 154;
 int launch_sum_cells(const double* a, long long n, double* work, void* stream);
 // active-bin pruning: E[k] = dnu_k sum_cells w J_k (w = wcol[column], or 1),
-// then active[k] = E[k] > cut sum_k E[k]
+// then active[k] = E[k] > cut sum_k E[k]; E holds nb x (1 + 16) doubles
+// (the energies, then per-chunk partial sums)
 int launch_active_bins(int selem, const void* J, int nb, long long nc, int nx, const double* wcol,
                        const double* dnu, double cut, double* E, unsigned char* active,
                        void* stream);

@@ -482,25 +482,54 @@ int launch_cell_tables(int selem, const double* T, const double* nhi, const doub
 }
 
 // Active-bin pruning (Sec. 2.2): the energy of each bin, dnu_k sum_cells w J_k
-// with w the column weight of the axisymmetric grid (1 on the Cartesian one),
-// in a fixed order (one block per bin); then, in one thread, the total in bin
-// order and the strict cut of the bins that step 1 advects.
+// with w the column weight of the axisymmetric grid (1 on the Cartesian one).
+// Each bin plane is split into kBinChunks chunks, one block each; a block sums
+// its chunk in a fixed order (FP32 state: per-thread compensated FP32 sums,
+// accurate to ~1e-12, since GB300's FP64 pipe runs at ~1/60 of FP32; FP64
+// state: FP64), then one thread adds the chunks in order, forms the total in
+// bin order and makes the strict cut of the bins that step 1 advects.
+constexpr int kBinChunks = 16;
+
 template <class S>
 __global__ void __launch_bounds__(256) bin_energy_kernel(const S* J, long long nc, int nx,
-                                                         const double* wcol, const double* dnu,
-                                                         double* E) {
+                                                         const double* wcol, double* part) {
   __shared__ double red[8];
-  const S* Jk = J + static_cast<long long>(blockIdx.x) * nc;
-  double s = 0.0;
-  for (long long id = threadIdx.x; id < nc; id += 256)
-    s += wcol ? double(Jk[id]) * wcol[id % nx] : double(Jk[id]);
-  s = block_sum<256>(s, red);
-  if (threadIdx.x == 0) E[blockIdx.x] = dnu[blockIdx.x] * s;
+  const int k = blockIdx.y, ch = blockIdx.x;
+  const S* Jk = J + static_cast<long long>(k) * nc;
+  const long long per = (nc + kBinChunks - 1) / kBinChunks;
+  const long long lo = static_cast<long long>(ch) * per;
+  const long long hi = lo + per < nc ? lo + per : nc;
+  double v;
+  if constexpr (sizeof(S) == 4) {
+    float s = 0.0f, c = 0.0f;
+    for (long long id = lo + threadIdx.x; id < hi; id += 256) {
+      const float x = wcol ? Jk[id] * float(wcol[id % nx]) : Jk[id];
+      const float t = s + x;
+      if (fabsf(s) >= fabsf(x))
+        c += (s - t) + x;
+      else
+        c += (x - t) + s;
+      s = t;
+    }
+    v = double(s) + double(c);
+  } else {
+    v = 0.0;
+    for (long long id = lo + threadIdx.x; id < hi; id += 256)
+      v += wcol ? double(Jk[id]) * wcol[id % nx] : double(Jk[id]);
+  }
+  v = block_sum<256>(v, red);
+  if (threadIdx.x == 0) part[static_cast<long long>(k) * kBinChunks + ch] = v;
 }
 
-__global__ void active_bins_kernel(const double* E, int nb, double cut, unsigned char* active) {
+__global__ void active_bins_kernel(const double* part, const double* dnu, int nb, double cut,
+                                   double* E, unsigned char* active) {
   double tot = 0.0;
-  for (int k = 0; k < nb; ++k) tot += E[k];
+  for (int k = 0; k < nb; ++k) {
+    double s = 0.0;
+    for (int ch = 0; ch < kBinChunks; ++ch) s += part[k * kBinChunks + ch];
+    E[k] = dnu[k] * s;
+    tot += E[k];
+  }
   const double c = cut * tot;
   for (int k = 0; k < nb; ++k) active[k] = E[k] > c ? 1 : 0;
 }
@@ -508,11 +537,13 @@ __global__ void active_bins_kernel(const double* E, int nb, double cut, unsigned
 int launch_active_bins(int selem, const void* J, int nb, long long nc, int nx, const double* wcol,
                        const double* dnu, double cut, double* E, unsigned char* active, void* st) {
   const cudaStream_t s = static_cast<cudaStream_t>(st);
+  double* part = E + nb;  // E holds nb energies, then nb x kBinChunks partials
+  const dim3 grid(kBinChunks, nb);
   if (selem == 8)
-    bin_energy_kernel<double><<<nb, 256, 0, s>>>(static_cast<const double*>(J), nc, nx, wcol, dnu, E);
+    bin_energy_kernel<double><<<grid, 256, 0, s>>>(static_cast<const double*>(J), nc, nx, wcol, part);
   else
-    bin_energy_kernel<float><<<nb, 256, 0, s>>>(static_cast<const float*>(J), nc, nx, wcol, dnu, E);
-  active_bins_kernel<<<1, 1, 0, s>>>(E, nb, cut, active);
+    bin_energy_kernel<float><<<grid, 256, 0, s>>>(static_cast<const float*>(J), nc, nx, wcol, part);
+  active_bins_kernel<<<1, 1, 0, s>>>(part, dnu, nb, cut, E, active);
   return static_cast<int>(cudaGetLastError());
 }
 
