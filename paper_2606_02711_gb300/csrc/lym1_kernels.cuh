@@ -1517,7 +1517,13 @@ __device__ __forceinline__ void freq_block(const DeviceView& v, int blk) {
 // Shared-memory ring fed by cp.async.bulk (one thread issues, an mbarrier per
 // stage counts the bytes).  Every wait is bounded: past kMaxSpins polls the
 // block records LYM1_ETIMEOUT in the context's status word and gives up.
-constexpr int kBulkDepth = 8;
+// ring depth of the bulk-copy pipeline: 6 bins for an FP32 elimination (the
+// smaller ring lets 9 blocks share an SM), 8 for an FP64 one (FP64-pipe-bound,
+// where the resident blocks are fewer and each needs more bytes in flight)
+template <class I>
+__host__ __device__ constexpr int bulk_depth() {
+  return sizeof(I) == 4 ? 6 : 8;
+}
 constexpr long long kMaxSpins = 100000000;          // backstop on the number of polls
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s per wait
 
@@ -1579,7 +1585,7 @@ __device__ __forceinline__ void freq_block_bulk(const DeviceView& v, int blk) {
   using F = typename P::F;
   using I = typename P::I;
   using T = F;
-  constexpr int NT = kFreqThreads, D = kBulkDepth;
+  constexpr int NT = kFreqThreads, D = bulk_depth<I>();
   __shared__ __align__(128) float ring[D][5][NT];
   __shared__ __align__(8) unsigned long long barF[D], barB[D];
   __shared__ double red[NT / 32];
@@ -1843,7 +1849,7 @@ __device__ __forceinline__ void freq_dispatch(const DeviceView& v, int blk) {
 // FP32 state: at most 64 registers so that 8 blocks (32 warps) per SM keep
 // enough loads in flight for the latency-bound bin sweeps
 template <class P, int G, int PT>
-__global__ void __launch_bounds__(kFreqThreads, sizeof(typename P::S) == 4 ? 8 : 1)
+__global__ void __launch_bounds__(kFreqThreads, sizeof(typename P::S) == 4 ? (sizeof(typename P::I) == 4 ? 9 : 8) : 1)
     freq_kernel(DeviceView v) {
   freq_dispatch<P, G, PT>(v, blockIdx.x);
 }
@@ -1881,7 +1887,7 @@ __global__ void __launch_bounds__(kTileX* kTileY, 3) transport_batched_f32(const
 }
 
 template <class P, int G, int PT>
-__global__ void __launch_bounds__(kFreqThreads, sizeof(typename P::S) == 4 ? 8 : 1)
+__global__ void __launch_bounds__(kFreqThreads, sizeof(typename P::S) == 4 ? (sizeof(typename P::I) == 4 ? 9 : 8) : 1)
     freq_batched(const DeviceView* views, const BatchItem* items, int n) {
   for (int i = blockIdx.x; i < n; i += gridDim.x) {
     const BatchItem it = items[i];
