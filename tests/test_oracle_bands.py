@@ -122,3 +122,21 @@ def test_invalid_band_problems():
     with pytest.raises(ValueError):
         oracle.Oracle(nx=4, ny=4, dx=1e16, edges=None, T=1e4, n_hi=0, rho_d=0, p_d=0, ux=0,
                       uy=0, lum=0, gray=True, bands=(z, z, z))
+
+
+def test_stellar_band_inputs():
+    # the seven-band recipe: absorption never exceeds the flux opacity (kappa_abs
+    # <= kappa_F in the dust table, gas absorption counted in both), the six
+    # stellar bands together carry the cloud's luminosity, and the IR band's
+    # emissivity is the dust's rho_d kappa_IR sigma T_d^4 / pi
+    c = wl.lognormal_cloud(24, 20, seed=181, Z=0.3)
+    aF, ka, je = wl.stellar_bands(c, T_dust=25.0)
+    assert aF.shape == ka.shape == je.shape == (7, 20, 24)
+    assert np.all(ka <= aF * (1 + 1e-15)) and np.all(ka >= 0) and np.all(je >= 0)
+    V = c.dx ** 3
+    L6 = (4.0 * math.pi * je[1:] * V).sum()
+    assert L6 == pytest.approx(c.lum.sum(), rel=1e-12)
+    np.testing.assert_allclose(je[0], c.rho_d * wl.KAPPA_IR * wl.SIGMA_SB * 25.0 ** 4 / math.pi,
+                               rtol=1e-15)
+    # EUV1 is absorbed by neutral gas far more strongly than the optical band
+    assert np.all(ka[4] > 100 * ka[1])
