@@ -1,0 +1,88 @@
+"""Y-slab decomposition of one grid over the ranks of a process group: the
+exchange step of a single large solve spread over several GPUs.
+
+The substep's stencil reaches two cells each way (MinMod reconstruction of
+the face states, Sec. 2.1 step 1; the velocity gradients reach one), and the
+source and frequency steps are cell-local.  So rank r owns rows [y0, y1) and
+keeps HALO = 2 rows of each neighbour around them; before every substep the
+ranks swap their edge rows, every rank advances its extended slab with the
+same (global) time step, and its own rows then come out exactly as in a
+single-domain run: they depend only on rows the rank holds correctly.  The
+halo rows come out wrong (their own stencil reaches beyond the slab) and are
+overwritten by the next swap.
+
+The module is solver-agnostic: state arrays are [nb][rows][nx] numpy arrays
+or torch tensors (CPU with gloo, CUDA with NCCL); the caller advances its
+slab with whatever it uses (a lym1 context through set_state / substeps /
+get_state, for instance).
+"""
+import numpy as np
+import torch
+import torch.distributed as dist
+
+HALO = 2
+
+
+def slab_rows(ny: int, world: int, rank: int):
+    """Rows [y0, y1) owned by rank: a balanced split, sizes differing by at most one."""
+    base, extra = divmod(ny, world)
+    y0 = rank * base + min(rank, extra)
+    return y0, y0 + base + (1 if rank < extra else 0)
+
+
+def extended_rows(ny: int, world: int, rank: int):
+    """Rows [e0, e1) the rank holds: its own plus up to HALO of each neighbour."""
+    y0, y1 = slab_rows(ny, world, rank)
+    return max(0, y0 - HALO), min(ny, y1 + HALO)
+
+
+def check_split(ny: int, world: int):
+    """Every slab must hold at least HALO rows, so that a neighbour's halo
+    comes from a single rank."""
+    for r in range(world):
+        y0, y1 = slab_rows(ny, world, r)
+        if y1 - y0 < HALO:
+            raise ValueError(f"{ny} rows over {world} ranks leaves rank {r} fewer than {HALO} rows")
+
+
+def _as_tensor(a):
+    return a if isinstance(a, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(a))
+
+
+def exchange(arrays, ny: int, world: int, rank: int, group=None):
+    """Swap the halo rows of the extended-slab arrays ([nb][e1 - e0][nx]) in
+    place: this rank's lowest and highest HALO own rows go to the ranks below
+    and above, whose edge rows fill this rank's halo."""
+    if world == 1:
+        return
+    y0, y1 = slab_rows(ny, world, rank)
+    e0, e1 = extended_rows(ny, world, rank)
+    lo, hi = y0 - e0, y1 - e0  # own rows, relative to the extended slab
+    for a in arrays:
+        t = _as_tensor(a)
+        reqs, recvs = [], []
+        if rank > 0:
+            reqs.append(dist.isend(t[:, lo:lo + HALO].contiguous(), rank - 1, group=group))
+            buf = torch.empty_like(t[:, 0:lo].contiguous())
+            reqs.append(dist.irecv(buf, rank - 1, group=group))
+            recvs.append((slice(0, lo), buf))
+        if rank < world - 1:
+            reqs.append(dist.isend(t[:, hi - HALO:hi].contiguous(), rank + 1, group=group))
+            buf = torch.empty_like(t[:, hi:].contiguous())
+            reqs.append(dist.irecv(buf, rank + 1, group=group))
+            recvs.append((slice(hi, t.shape[1]), buf))
+        for r in reqs:
+            r.wait()
+        for rows, buf in recvs:
+            if isinstance(a, torch.Tensor):
+                a[:, rows].copy_(buf)
+            else:
+                a[:, rows] = buf.numpy()
+
+
+def global_dt(local_dt: float, group=None) -> float:
+    """The single-domain CFL step: the smallest of the slabs' own steps (each
+    slab sees a subset of the velocities, and every cell is in some slab)."""
+    t = torch.tensor([float(local_dt)], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MIN, group=group)
+    return float(t.item())

@@ -1,0 +1,118 @@
+"""Y-slab decomposition of one grid (paper_2606_02711_gb300/slabs.py) on CPU
+ranks with gloo, the oracle advancing each rank's slab: with the halo rows
+swapped before every substep and the global time step, the rows each rank
+owns equal the single-domain oracle run bit for bit (Cartesian with outflow
+edges, axisymmetric with the midplane mirror and vacuum outer edge)."""
+import os
+import socket
+
+import numpy as np
+import pytest
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+from paper_2606_02711_gb300 import slabs
+
+NSTEPS = 3
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _cloud(geometry):
+    import workloads as wl
+    c = wl.lognormal_cloud(20, 17, seed=191, v_edge_kms=150.0, Z=0.3, p_d=1e-7)
+    c.geometry = geometry
+    c.bc = (0, 1, 0, 1) if geometry == 1 else (1, 1, 1, 1)
+    return c
+
+
+def _state(c):
+    g = np.random.default_rng(192)
+    J = 1e-3 * np.exp(g.normal(0, 0.5, (194, c.ny, c.nx)))
+    return J, 0.4 * J * g.uniform(-1, 1, J.shape), 0.4 * J * g.uniform(-1, 1, J.shape)
+
+
+def _slab_oracle(c, e0, e1, ny):
+    import oracle
+    kw = c.kwargs()
+    for f in ("n_hi", "rho_d", "p_d", "ux", "uy", "lum"):
+        kw[f] = np.ascontiguousarray(np.broadcast_to(kw[f], (ny, c.nx))[e0:e1])
+    kw["ny"] = e1 - e0
+    bc = list(kw["bc"])
+    if e0 > 0:
+        bc[2] = 0  # interior edges: whatever ghosts, only the halo rows see them
+    if e1 < ny:
+        bc[3] = 0
+    kw["bc"] = tuple(bc)
+    return oracle.Oracle(edges=oracle.freq_grid(), **kw)
+
+
+def _worker(rank, world, port, geometry, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    c = _cloud(geometry)
+    ny = c.ny
+    slabs.check_split(ny, world)
+    y0, y1 = slabs.slab_rows(ny, world, rank)
+    e0, e1 = slabs.extended_rows(ny, world, rank)
+    O = _slab_oracle(c, e0, e1, ny)
+    dt = slabs.global_dt(O.dt_cfl)
+    J, Hx, Hy = (np.ascontiguousarray(a[:, e0:e1]) for a in _state(c))
+    fx = fy = None
+    for _ in range(NSTEPS):
+        slabs.exchange((J, Hx, Hy), ny, world, rank)
+        J, Hx, Hy, fx, fy, _ = O.substep(J, Hx, Hy, dt)
+    own = slice(y0 - e0, y1 - e0)
+    mine = (y0, y1, J[:, own], Hx[:, own], Hy[:, own], fx[own], fy[own], dt)
+    gathered = [None] * world
+    dist.all_gather_object(gathered, mine)
+    if rank == 0:
+        out.put(gathered)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_split_is_a_balanced_partition():
+    for ny in (4, 17, 512, 2048):
+        for world in (1, 2, 3, 8):
+            if ny < 2 * world:
+                continue
+            rows = [slabs.slab_rows(ny, world, r) for r in range(world)]
+            assert rows[0][0] == 0 and rows[-1][1] == ny
+            assert all(a[1] == b[0] for a, b in zip(rows, rows[1:]))
+            sizes = [y1 - y0 for y0, y1 in rows]
+            assert max(sizes) - min(sizes) <= 1
+            slabs.check_split(ny, world)
+    with pytest.raises(ValueError):
+        slabs.check_split(5, 3)
+
+
+@pytest.mark.parametrize("geometry,world", [(0, 2), (0, 3), (1, 3)])
+def test_decomposed_run_equals_single_domain(geometry, world):
+    import oracle
+    c = _cloud(geometry)
+    ref_O = oracle.Oracle(edges=oracle.freq_grid(), **c.kwargs())
+    (J, Hx, Hy, fx, fy), _ = ref_O.run(NSTEPS, _state(c))
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, world, port, geometry, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    gathered = q.get(timeout=300)
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    for y0, y1, Js, Hxs, Hys, fxs, fys, dt in gathered:
+        assert dt == ref_O.dt_cfl
+        np.testing.assert_array_equal(Js, J[:, y0:y1])
+        np.testing.assert_array_equal(Hxs, Hx[:, y0:y1])
+        np.testing.assert_array_equal(Hys, Hy[:, y0:y1])
+        np.testing.assert_array_equal(fxs, fx[y0:y1])
+        np.testing.assert_array_equal(fys, fy[y0:y1])
