@@ -290,3 +290,224 @@ def test_brute_force_substep_matches_oracle(bc):
         assert err < 1e-12, (n, err)
     # the problem reaches the upwind regime of the frequency step
     assert pmax > 5.0
+
+
+def brute_substep_cyl(p, J, Hx, Hy):
+    """The same substep on the axisymmetric grid (x = R from the axis, y = Z
+    from the midplane, per-radian finite volumes): R faces of area R dZ, Z faces
+    (R+^2 - R-^2)/2, volume (R+^2 - R-^2) dZ / 2, centroid distances in tau, the
+    hoop source -K_phiphi <1/R> in the H_R balance and D_phiphi <u_R/R> in the
+    work and Doppler terms; the axis and the midplane are mirrors."""
+    nx, ny, dx = p["nx"], p["ny"], p["dx"]
+    e = p["edges"]
+    nb = e.size - 1
+    T = p["T"]
+    dnuD, av, s0 = line(T)
+    dnu = np.diff(e)
+    nubar = NU0 + 0.5 * (e[1:] + e[:-1])
+    x = e / dnuD
+    Hk = (I_voigt(x[1:], av) - I_voigt(x[:-1], av)) / (dnu / dnuD)
+    w = Hk * (dnu / dnuD)
+    w = w / w.sum()
+    alpha = p["n_hi"] * s0
+    rho, pd, ux, uy, lum = p["rho_d"], p["p_d"], p["ux"], p["uy"], p["lum"]
+    kabs, kF = p["kappa_abs"], p["kappa_F"]
+    ct = p["c_tilde"]
+    umax = np.hypot(ux, uy).max()
+    dt = (p["cfl"] / 2.0) * dx / (ct + umax)
+    cdt = ct * dt
+    bc = p["bc"]
+    Rf = np.arange(nx + 1) * dx                      # R faces
+    AZ = 0.5 * (Rf[1:] ** 2 - Rf[:-1] ** 2)          # Z-face areas
+    Vol = AZ * dx
+    Rbar = (2.0 / 3.0) * (Rf[1:] ** 3 - Rf[:-1] ** 3) / (Rf[1:] ** 2 - Rf[:-1] ** 2)
+
+    def uR(i, j):  # with the axis mirror (u_R flips) and copied outer ghosts
+        if i < 0:
+            return -ux[min(max(j, -1 - j) if j < 0 else j, ny - 1), -1 - i]
+        return ux[min(j if j >= 0 else -1 - j, ny - 1), min(i, nx - 1)]
+
+    def uZ(i, j):  # with the midplane mirror (u_Z flips) and copied outer ghosts
+        ii = min(i if i >= 0 else -1 - i, nx - 1)
+        if j < 0:
+            return -uy[-1 - j, ii]
+        return uy[min(j, ny - 1), ii]
+
+    gxx = np.zeros((ny, nx))
+    gyy = np.zeros((ny, nx))
+    gsh = np.zeros((ny, nx))
+    gphi = np.zeros((ny, nx))
+    for j in range(ny):
+        for i in range(nx):
+            gxx[j, i] = (uR(i + 1, j) - uR(i - 1, j)) / (2 * dx)
+            gyy[j, i] = (uZ(i, j + 1) - uZ(i, j - 1)) / (2 * dx)
+            gsh[j, i] = (uR(i, j + 1) - uR(i, j - 1)) / (2 * dx) + (uZ(i + 1, j) - uZ(i - 1, j)) / (2 * dx)
+            fl = 0.5 * (uR(i - 1, j) + uR(i, j))
+            fr = 0.5 * (uR(i, j) + uR(i + 1, j))
+            gphi[j, i] = (fl + fr) / (Rf[i] + Rf[i + 1])
+
+    J1 = np.empty_like(J)
+    Hx1 = np.empty_like(J)
+    Hy1 = np.empty_like(J)
+    for k in range(nb):
+        aF = alpha * Hk[k] + rho * kF
+
+        def cell(i, j, axis):
+            # (J, f_n, f_t), u_n, alpha_F of a (ghost) cell; axis 0: n = R, axis 1: n = Z
+            flipR = i < 0
+            flipZ = j < 0
+            ii = -1 - i if i < 0 else min(i, nx - 1)
+            jj = -1 - j if j < 0 else min(j, ny - 1)
+            vac = (i >= nx and bc[1] == 1) or (j >= ny and bc[3] == 1)
+            u = (-1.0 if flipR else 1.0) * ux[jj, ii] if axis == 0 else (-1.0 if flipZ else 1.0) * uy[jj, ii]
+            if vac:
+                return (0.0, 0.0, 0.0), u, aF[jj, ii]
+            jv = J[k, jj, ii]
+            hR = (-1.0 if flipR else 1.0) * Hx[k, jj, ii]
+            hZ = (-1.0 if flipZ else 1.0) * Hy[k, jj, ii]
+            fR, fZ = prim(jv, hR, hZ)
+            return ((jv, fR, fZ) if axis == 0 else (jv, fZ, fR)), u, aF[jj, ii]
+
+        def face(q, u0, u1, a0, a1, d0, d1):
+            (Jm, nm, tm), (J0, n0, t0), (Jp, n1, t1), (J2, n2, t2) = q
+            JL = J0 + 0.5 * minmod(J0 - Jm, Jp - J0)
+            JR = Jp - 0.5 * minmod(Jp - J0, J2 - Jp)
+            nL = n0 + 0.5 * minmod(n0 - nm, n1 - n0)
+            tL = t0 + 0.5 * minmod(t0 - tm, t1 - t0)
+            nR = n1 - 0.5 * minmod(n1 - n0, n2 - n1)
+            tR = t1 - 0.5 * minmod(t1 - t0, t2 - t1)
+            nL, tL = cap(nL, tL)
+            nR, tR = cap(nR, tR)
+            HnL, HtL, HnR, HtR = JL * nL, JL * tL, JR * nR, JR * tR
+            DnnL, DntL, _, _ = closure(nL, tL)
+            DnnR, DntR, _, _ = closure(nR, tR)
+            tau = a0 * d0 + a1 * d1
+            eps = (0.2 + tau) / (0.2 + tau + tau * tau)
+            diff = (1.0 - eps) * (Jp - J0) / (3.0 * tau) if tau > 0.0 else 0.0
+            wf = 0.5 * (u0 + u1) / C
+            up = wf > 0.0
+            FJ = eps * 0.5 * (HnL + HnR) - eps * 0.5 * (JR - JL) - diff + wf * (JL if up else JR)
+            FN = 0.5 * (DnnL * JL + DnnR * JR) - eps * 0.5 * (HnR - HnL) + wf * (HnL if up else HnR)
+            FT = 0.5 * (DntL * JL + DntR * JR) - eps * 0.5 * (HtR - HtL) + wf * (HtL if up else HtR)
+            return FJ, FN, FT
+
+        FR = np.zeros((3, ny, nx + 1))
+        for j in range(ny):
+            for i in range(nx + 1):  # R face i between cells i-1 and i
+                cs = [cell(i - 2 + m, j, 0) for m in range(4)]
+                left = -Rbar[0] if i == 0 else Rbar[i - 1]
+                right = Rbar[nx - 1] + dx if i == nx else Rbar[i]
+                FR[:, j, i] = face([c[0] for c in cs], cs[1][1], cs[2][1], cs[1][2], cs[2][2],
+                                   Rf[i] - left, right - Rf[i])
+        FZ = np.zeros((3, ny + 1, nx))
+        for j in range(ny + 1):
+            for i in range(nx):
+                cs = [cell(i, j - 2 + m, 1) for m in range(4)]
+                FZ[:, j, i] = face([c[0] for c in cs], cs[1][1], cs[2][1], cs[1][2], cs[2][2],
+                                   dx / 2.0, dx / 2.0)
+        for j in range(ny):
+            for i in range(nx):
+                jv = J[k, j, i]
+                fx, fy = cap(*prim(jv, Hx[k, j, i], Hy[k, j, i]))
+                Dxx, Dxy, Dyy, Dpp = closure(fx, fy)
+                Wc = (Dxx * gxx[j, i] + Dyy * gyy[j, i] + Dxy * gsh[j, i] + Dpp * gphi[j, i]) * jv
+
+                def div(fr, fz):
+                    return ((Rf[i + 1] * dx * fr[j, i + 1] - Rf[i] * dx * fr[j, i])
+                            + AZ[i] * (fz[j + 1, i] - fz[j, i])) / Vol[i]
+                invR = dx * dx / Vol[i]
+                J1[k, j, i] = jv - cdt * (div(FR[0], FZ[0]) + Wc / C)
+                Hx1[k, j, i] = Hx[k, j, i] - cdt * (div(FR[1], FZ[2]) - Dpp * jv * invR)
+                Hy1[k, j, i] = Hy[k, j, i] - cdt * div(FR[2], FZ[1])
+
+    aH = alpha[None] * Hk[:, None, None]
+    kap = rho[None] * kabs + pd[None] * aH
+    aFk = aH + rho[None] * kF
+    js = (lum / (2.0 * math.pi * Vol[None, :]))[None] * (w / (4.0 * math.pi * dnu))[:, None, None]
+    J2 = (J1 + cdt * js) / (1.0 + cdt * kap)
+    Hx2 = Hx1 / (1.0 + cdt * aFk)
+    Hy2 = Hy1 / (1.0 + cdt * aFk)
+    fcoef = 4.0 * math.pi / (C * ct * dt)
+    fx_out = fcoef * (dnu[:, None, None] * (Hx1 - Hx2)).sum(axis=0)
+    fy_out = fcoef * (dnu[:, None, None] * (Hy1 - Hy2)).sum(axis=0)
+    # step 3 with D_phiphi <u_R/R> in the Doppler term: the Cartesian routine's
+    # solve, on gradients that include the hoop part
+    q = dict(p, _grads=(gxx, gyy, gsh, gphi))
+    return _freq_and_cap(q, J2, Hx2, Hy2, Hk, dnu, nubar, dnuD, alpha, cdt, T), fx_out, fy_out
+
+
+def _freq_and_cap(p, J2, Hx2, Hy2, Hk, dnu, nubar, dnuD, alpha, cdt, T):
+    nb = dnu.size
+    ny, nx = alpha.shape
+    gxx, gyy, gsh, gphi = p["_grads"]
+    hkT = HPL / (KB * T)
+    Rk = hkT - 2.0 / nubar if p["recoil"] else np.zeros(nb)
+    half = 0.5 * dnu
+    J3, Hx3, Hy3 = J2.copy(), Hx2.copy(), Hy2.copy()
+
+    def phiL(P):
+        return -math.expm1(-P)
+
+    def phiR(P):
+        return -math.expm1(P)
+
+    def chiL(P):
+        return 1.0 if P == 0.0 else phiL(P) / P
+
+    def chiR(P):
+        return -1.0 if P == 0.0 else phiR(P) / P
+
+    for j in range(ny):
+        for i in range(nx):
+            if alpha[j, i] > 0.0:
+                K = 0.5 * dnuD * dnuD * alpha[j, i] * Hk
+                Cc = np.empty(nb)
+                for k in range(nb):
+                    fx, fy = cap(*prim(J2[k, j, i], Hx2[k, j, i], Hy2[k, j, i]))
+                    Dxx, Dxy, Dyy, Dpp = closure(fx, fy)
+                    DdU = Dxx * gxx[j, i] + Dyy * gyy[j, i] + Dxy * gsh[j, i] + Dpp * gphi[j, i]
+                    Cc[k] = K[k] * Rk[k] + nubar[k] / C * DdU
+                P = Cc * half / K
+                M = np.zeros((nb, nb))
+                for k in range(nb):
+                    M[k, k] = 1.0 / cdt
+                    if k + 1 < nb:
+                        den = chiL(P[k]) * half[k] / K[k] - chiR(P[k + 1]) * half[k + 1] / K[k + 1]
+                        M[k, k + 1] -= (1.0 - phiR(P[k + 1])) / den / dnu[k]
+                        M[k, k] += (1.0 - phiL(P[k])) / den / dnu[k]
+                    if k > 0:
+                        den = chiL(P[k - 1]) * half[k - 1] / K[k - 1] - chiR(P[k]) * half[k] / K[k]
+                        M[k, k - 1] -= (1.0 - phiL(P[k - 1])) / den / dnu[k]
+                        M[k, k] += (1.0 - phiR(P[k])) / den / dnu[k]
+                Jn = np.linalg.solve(M, J2[:, j, i] / cdt)
+                Jo = J2[:, j, i]
+                ratio = np.where(Jo > 0.0, Jn / np.where(Jo > 0, Jo, 1.0), 0.0)
+                J3[:, j, i] = Jn
+                Hx3[:, j, i] = ratio * Hx2[:, j, i]
+                Hy3[:, j, i] = ratio * Hy2[:, j, i]
+            for k in range(nb):
+                jv, h1, h2 = J3[k, j, i], Hx3[k, j, i], Hy3[k, j, i]
+                hn = math.hypot(h1, h2)
+                if jv <= 0.0:
+                    Hx3[k, j, i] = Hy3[k, j, i] = 0.0
+                elif hn > jv:
+                    Hx3[k, j, i] = h1 * jv / hn
+                    Hy3[k, j, i] = h2 * jv / hn
+    return J3, Hx3, Hy3
+
+
+@pytest.mark.parametrize("bc", [(0, 0, 0, 0), (0, 1, 0, 1)])
+def test_brute_force_axisymmetric_substep_matches_oracle(bc):
+    p, st = _problem(bc, 211 + sum(bc))
+    p["geometry"] = 1
+    O = oracle.Oracle(nx=p["nx"], ny=p["ny"], dx=p["dx"], edges=p["edges"], T=p["T"],
+                      n_hi=p["n_hi"], rho_d=p["rho_d"], p_d=p["p_d"], ux=p["ux"], uy=p["uy"],
+                      lum=p["lum"], kappa_abs=p["kappa_abs"], kappa_F=p["kappa_F"],
+                      c_tilde=p["c_tilde"], cfl=p["cfl"], recoil=True, bc=bc, geometry=1)
+    ref = O.substep(*st)[:5]
+    (J3, Hx3, Hy3), fx, fy = brute_substep_cyl(p, *st)
+    for a, b, n in zip((J3, Hx3, Hy3, fx, fy), ref, ("J", "Hx", "Hy", "fx", "fy")):
+        scale = np.abs(b).max()
+        assert scale > 0
+        err = np.abs(a - b).max() / scale
+        assert err < 1e-12, (n, err)
