@@ -74,15 +74,26 @@ def brute_substep(p, J, Hx, Hy):
     nx, ny, dx = p["nx"], p["ny"], p["dx"]
     e = p["edges"]
     nb = e.size - 1
-    T = p["T"]
-    dnuD, av, s0 = line(T)
     dnu = np.diff(e)
     nubar = NU0 + 0.5 * (e[1:] + e[:-1])
-    x = e / dnuD
-    Hk = (I_voigt(x[1:], av) - I_voigt(x[:-1], av)) / (dnu / dnuD)
-    w = Hk * (dnu / dnuD)
-    w = w / w.sum()
-    alpha = p["n_hi"] * s0
+    # per-cell line constants and tables (App. A at each cell's own temperature)
+    Tc = p.get("temp")
+    Tc = np.full((ny, nx), p["T"]) if Tc is None else Tc
+    Hkc = np.empty((nb, ny, nx))
+    wc = np.empty((nb, ny, nx))
+    dnuDc = np.empty((ny, nx))
+    s0c = np.empty((ny, nx))
+    for j in range(ny):
+        for i in range(nx):
+            dD, av, s0 = line(Tc[j, i])
+            xx = e / dD
+            h = (I_voigt(xx[1:], av) - I_voigt(xx[:-1], av)) / (dnu / dD)
+            ww = h * (dnu / dD)
+            Hkc[:, j, i] = h
+            wc[:, j, i] = ww / ww.sum()
+            dnuDc[j, i] = dD
+            s0c[j, i] = s0
+    alpha = p["n_hi"] * s0c
     rho, pd, ux, uy, lum = p["rho_d"], p["p_d"], p["ux"], p["uy"], p["lum"]
     kabs, kF = p["kappa_abs"], p["kappa_F"]
     ct = p["c_tilde"]
@@ -112,7 +123,7 @@ def brute_substep(p, J, Hx, Hy):
     Hy1 = np.empty_like(J)
     W = np.zeros((nb, ny, nx))
     for k in range(nb):
-        aF = alpha * Hk[k] + rho * kF
+        aF = alpha * Hkc[k] + rho * kF
 
         def cell(i, j, axis):
             # the state of a (possibly ghost) cell: (J, f_n, f_t), u_n, alpha_F
@@ -183,10 +194,10 @@ def brute_substep(p, J, Hx, Hy):
                 Hy1[k, j, i] = Hy[k, j, i] - cdt * divHy / dx
 
     # step 2 and the force
-    aH = alpha[None] * Hk[:, None, None]
+    aH = alpha[None] * Hkc
     kap = rho[None] * kabs + pd[None] * aH
     aFk = aH + rho[None] * kF
-    js = lum[None] * (w / (4.0 * math.pi * V * dnu))[:, None, None]
+    js = lum[None] * wc / (4.0 * math.pi * V * dnu[:, None, None])
     J2 = (J1 + cdt * js) / (1.0 + cdt * kap)
     Hx2 = Hx1 / (1.0 + cdt * aFk)
     Hy2 = Hy1 / (1.0 + cdt * aFk)
@@ -195,8 +206,6 @@ def brute_substep(p, J, Hx, Hy):
     fy_out = fcoef * (dnu[:, None, None] * (Hy1 - Hy2)).sum(axis=0)
 
     # step 3, a dense BDF1 solve per cell in the printed leakage form
-    hkT = HPL / (KB * T)
-    Rk = hkT - 2.0 / nubar if p["recoil"] else np.zeros(nb)
     half = 0.5 * dnu  # delta nu_k on either side of a midpoint centre
     pmax = 0.0
     J3 = J2.copy()
@@ -218,7 +227,9 @@ def brute_substep(p, J, Hx, Hy):
     for j in range(ny):
         for i in range(nx):
             if alpha[j, i] > 0.0:
-                K = 0.5 * dnuD * dnuD * alpha[j, i] * Hk
+                dD = dnuDc[j, i]
+                K = 0.5 * dD * dD * alpha[j, i] * Hkc[:, j, i]
+                Rk = HPL / (KB * Tc[j, i]) - 2.0 / nubar if p["recoil"] else np.zeros(nb)
                 Cc = np.empty(nb)
                 for k in range(nb):
                     fx, fy = cap(*prim(J2[k, j, i], Hx2[k, j, i], Hy2[k, j, i]))
@@ -509,5 +520,23 @@ def test_brute_force_axisymmetric_substep_matches_oracle(bc):
     for a, b, n in zip((J3, Hx3, Hy3, fx, fy), ref, ("J", "Hx", "Hy", "fx", "fy")):
         scale = np.abs(b).max()
         assert scale > 0
+        err = np.abs(a - b).max() / scale
+        assert err < 1e-12, (n, err)
+
+
+def test_brute_force_temperature_field_matches_oracle():
+    # per-cell temperatures from 5e3 K to 3e4 K (colder cells push the Peclet
+    # numbers of this grid past the printed form's range): every A0 table per cell
+    p, st = _problem((1, 0, 0, 1), 221)
+    g = np.random.default_rng(222)
+    p["temp"] = 10.0 ** g.uniform(np.log10(5e3), np.log10(3e4), (p["ny"], p["nx"]))
+    O = oracle.Oracle(nx=p["nx"], ny=p["ny"], dx=p["dx"], edges=p["edges"], T=p["T"],
+                      n_hi=p["n_hi"], rho_d=p["rho_d"], p_d=p["p_d"], ux=p["ux"], uy=p["uy"],
+                      lum=p["lum"], kappa_abs=p["kappa_abs"], kappa_F=p["kappa_F"],
+                      c_tilde=p["c_tilde"], cfl=p["cfl"], recoil=True, bc=p["bc"], temp=p["temp"])
+    ref = O.substep(*st)[:5]
+    got, pmax = brute_substep(p, *st)
+    for a, b, n in zip(got, ref, ("J", "Hx", "Hy", "fx", "fy")):
+        scale = np.abs(b).max()
         err = np.abs(a - b).max() / scale
         assert err < 1e-12, (n, err)
