@@ -70,20 +70,29 @@ def prim(J, H1, H2):
     return (H1 / J, H2 / J) if J > 0.0 else (0.0, 0.0)
 
 
-def brute_substep(p, J, Hx, Hy):
+def brute_substep(p, J, Hx, Hy, bands=None, prune=0.0):
+    """bands: (alpha_F, kappa, j) per [band][cell] for broad bands (Sec. 3):
+    each band is one frequency-integrated group (dnu = 1) with the given flux
+    and absorption opacities and emissivity, and no step 3.  prune: bins
+    holding no more than this share of sum_k dnu_k sum_cells J_k skip step 1
+    (Sec. 2.2)."""
     nx, ny, dx = p["nx"], p["ny"], p["dx"]
-    e = p["edges"]
-    nb = e.size - 1
-    dnu = np.diff(e)
-    nubar = NU0 + 0.5 * (e[1:] + e[:-1])
+    if bands is None:
+        e = p["edges"]
+        nb = e.size - 1
+        dnu = np.diff(e)
+        nubar = NU0 + 0.5 * (e[1:] + e[:-1])
+    else:
+        nb = bands[0].shape[0]
+        dnu = np.ones(nb)
     # per-cell line constants and tables (App. A at each cell's own temperature)
     Tc = p.get("temp")
     Tc = np.full((ny, nx), p["T"]) if Tc is None else Tc
-    Hkc = np.empty((nb, ny, nx))
-    wc = np.empty((nb, ny, nx))
+    Hkc = np.zeros((nb, ny, nx))
+    wc = np.zeros((nb, ny, nx))
     dnuDc = np.empty((ny, nx))
-    s0c = np.empty((ny, nx))
-    for j in range(ny):
+    s0c = np.zeros((ny, nx))
+    for j in range(ny if bands is None else 0):
         for i in range(nx):
             dD, av, s0 = line(Tc[j, i])
             xx = e / dD
@@ -122,8 +131,13 @@ def brute_substep(p, J, Hx, Hy):
     Hx1 = np.empty_like(J)
     Hy1 = np.empty_like(J)
     W = np.zeros((nb, ny, nx))
+    Ek = dnu * J.sum(axis=(1, 2))
+    on = Ek > prune * Ek.sum() if prune > 0.0 else np.ones(nb, bool)
     for k in range(nb):
-        aF = alpha * Hkc[k] + rho * kF
+        if not on[k]:  # a pruned bin keeps its state through step 1
+            J1[k], Hx1[k], Hy1[k] = J[k], Hx[k], Hy[k]
+            continue
+        aF = alpha * Hkc[k] + rho * kF if bands is None else bands[0][k]
 
         def cell(i, j, axis):
             # the state of a (possibly ghost) cell: (J, f_n, f_t), u_n, alpha_F
@@ -198,12 +212,17 @@ def brute_substep(p, J, Hx, Hy):
     kap = rho[None] * kabs + pd[None] * aH
     aFk = aH + rho[None] * kF
     js = lum[None] * wc / (4.0 * math.pi * V * dnu[:, None, None])
+    if bands is not None:
+        aFk, kap, js = bands
     J2 = (J1 + cdt * js) / (1.0 + cdt * kap)
     Hx2 = Hx1 / (1.0 + cdt * aFk)
     Hy2 = Hy1 / (1.0 + cdt * aFk)
     fcoef = 4.0 * math.pi / (C * ct * dt)
     fx_out = fcoef * (dnu[:, None, None] * (Hx1 - Hx2)).sum(axis=0)
     fy_out = fcoef * (dnu[:, None, None] * (Hy1 - Hy2)).sum(axis=0)
+
+    if bands is not None or not p.get("freq_step", True):  # no step 3 (nor its cap)
+        return (J2, Hx2, Hy2, fx_out, fy_out), 0.0
 
     # step 3, a dense BDF1 solve per cell in the printed leakage form
     half = 0.5 * dnu  # delta nu_k on either side of a midpoint centre
@@ -303,12 +322,13 @@ def test_brute_force_substep_matches_oracle(bc):
     assert pmax > 5.0
 
 
-def brute_substep_cyl(p, J, Hx, Hy):
+def brute_substep_cyl(p, J, Hx, Hy, prune=0.0):
     """The same substep on the axisymmetric grid (x = R from the axis, y = Z
     from the midplane, per-radian finite volumes): R faces of area R dZ, Z faces
     (R+^2 - R-^2)/2, volume (R+^2 - R-^2) dZ / 2, centroid distances in tau, the
     hoop source -K_phiphi <1/R> in the H_R balance and D_phiphi <u_R/R> in the
-    work and Doppler terms; the axis and the midplane are mirrors."""
+    work and Doppler terms; the axis and the midplane are mirrors.  prune: as
+    for the Cartesian grid, the bin energies weighted by the ring volumes."""
     nx, ny, dx = p["nx"], p["ny"], p["dx"]
     e = p["edges"]
     nb = e.size - 1
@@ -360,7 +380,12 @@ def brute_substep_cyl(p, J, Hx, Hy):
     J1 = np.empty_like(J)
     Hx1 = np.empty_like(J)
     Hy1 = np.empty_like(J)
+    Ek = dnu * (J * Vol[None, None, :]).sum(axis=(1, 2))
+    on = Ek > prune * Ek.sum() if prune > 0.0 else np.ones(nb, bool)
     for k in range(nb):
+        if not on[k]:  # a pruned bin keeps its state through step 1
+            J1[k], Hx1[k], Hy1[k] = J[k], Hx[k], Hy[k]
+            continue
         aF = alpha * Hk[k] + rho * kF
 
         def cell(i, j, axis):
@@ -441,6 +466,8 @@ def brute_substep_cyl(p, J, Hx, Hy):
     fcoef = 4.0 * math.pi / (C * ct * dt)
     fx_out = fcoef * (dnu[:, None, None] * (Hx1 - Hx2)).sum(axis=0)
     fy_out = fcoef * (dnu[:, None, None] * (Hy1 - Hy2)).sum(axis=0)
+    if not p.get("freq_step", True):
+        return (J2, Hx2, Hy2), fx_out, fy_out
     # step 3 with D_phiphi <u_R/R> in the Doppler term: the Cartesian routine's
     # solve, on gradients that include the hoop part
     q = dict(p, _grads=(gxx, gyy, gsh, gphi))
@@ -539,4 +566,121 @@ def test_brute_force_temperature_field_matches_oracle():
     for a, b, n in zip(got, ref, ("J", "Hx", "Hy", "fx", "fy")):
         scale = np.abs(b).max()
         err = np.abs(a - b).max() / scale
+        assert err < 1e-12, (n, err)
+
+
+def _per_bin_err(a, b):
+    # worst error over the bin planes, each relative to its own largest value
+    return max(np.abs(a[k] - b[k]).max() / np.abs(b[k]).max() for k in range(b.shape[0]))
+
+
+CUT = 1e-10
+
+
+@pytest.mark.parametrize("geometry", [0, 1])
+def test_brute_force_pruning_matches_oracle(geometry):
+    # Bins of unequal width (quadratic in nu), no sources, no step 3 (so that
+    # each bin plane shows its own step 1).  Bins 0, 4, 11 hold ~1e-15 of the
+    # energy; bin 6 (the narrowest) holds 0.4 cut and bin 8 holds 2.5 cut of
+    # sum_k dnu_k sum_cells w J_k, w the ring volume on the axisymmetric grid,
+    # where bin 6 lives on the axis column only.  Bin 6 is pruned and bin 8 is
+    # not; leaving out dnu or w, or comparing with the mean bin, flips one of
+    # the two decisions, and so does a reversed comparison.
+    bc = (1, 0, 0, 1) if geometry == 0 else (0, 1, 0, 1)
+    p, (J, Hx, Hy) = _problem(bc, 231 + geometry)
+    dnuD = line(p["T"])[0]
+    x = np.linspace(-1.0, 1.0, 13)
+    p["edges"] = 3.0 * dnuD * np.sign(x) * x * x
+    p["lum"] = np.zeros_like(p["lum"])
+    p["freq_step"] = False
+    nx, ny = p["nx"], p["ny"]
+    dnu = np.diff(p["edges"])
+    Vol = 0.5 * (2 * np.arange(nx) + 1) * p["dx"] ** 3 if geometry == 1 else np.ones(nx)
+    for k in (0, 4, 11):
+        J[k] *= 1e-14
+        Hx[k] *= 1e-14
+        Hy[k] *= 1e-14
+
+    def energies(J, w_col, with_dnu=True):
+        return (dnu if with_dnu else 1.0) * (J * w_col[None, None, :]).sum(axis=(1, 2))
+
+    g = np.random.default_rng(233)
+    J[6] = J[8] = 0.0
+    Erest = energies(J, Vol).sum()
+    for k, share in ((6, 0.4 * CUT), (8, 2.5 * CUT)):
+        plane = np.zeros((ny, nx))
+        if geometry == 1 and k == 6:
+            plane[:, 0] = 1.0
+        else:
+            plane[:] = np.exp(g.normal(0, 0.3, (ny, nx)))
+        S = (plane * Vol[None, :]).sum()
+        J[k] = plane * (share * Erest / (1.0 - 2.9 * CUT)) / (dnu[k] * S)
+        th = g.uniform(0, 2 * np.pi, (ny, nx))
+        Hx[k] = 0.5 * J[k] * np.cos(th)
+        Hy[k] = 0.5 * J[k] * np.sin(th)
+    E = energies(J, Vol)
+    assert E[6] / E.sum() == pytest.approx(0.4 * CUT, rel=1e-9)
+    assert E[8] / E.sum() == pytest.approx(2.5 * CUT, rel=1e-9)
+    # the readings that a plausible mistake takes all flip a decision
+    Eu = energies(J, Vol, with_dnu=False)
+    assert Eu[6] > 2.0 * CUT * Eu.sum()
+    if geometry == 1:
+        Ev = energies(J, np.ones(nx))
+        assert Ev[6] > 2.0 * CUT * Ev.sum()
+    assert E[6] > CUT * E.mean()
+    st = (J, Hx, Hy)
+
+    O = oracle.Oracle(nx=nx, ny=ny, dx=p["dx"], edges=p["edges"], T=p["T"], n_hi=p["n_hi"],
+                      rho_d=p["rho_d"], p_d=p["p_d"], ux=p["ux"], uy=p["uy"], lum=p["lum"],
+                      kappa_abs=p["kappa_abs"], kappa_F=p["kappa_F"], c_tilde=p["c_tilde"],
+                      cfl=p["cfl"], recoil=True, freq_step=False, bc=bc, geometry=geometry,
+                      prune=CUT)
+    ref = O.substep(*st)[:5]
+    if geometry == 0:
+        got = brute_substep(p, *st, prune=CUT)[0]
+        plain = brute_substep(p, *st)[0]
+    else:
+        (J3, Hx3, Hy3), fx, fy = brute_substep_cyl(p, *st, prune=CUT)
+        got = (J3, Hx3, Hy3, fx, fy)
+        (J3, Hx3, Hy3), fx, fy = brute_substep_cyl(p, *st)
+        plain = (J3, Hx3, Hy3, fx, fy)
+    for a, b, n in zip(got[:3], ref[:3], ("J", "Hx", "Hy")):
+        err = _per_bin_err(a, b)
+        assert err < 1e-12, (n, err)
+    for a, b, n in zip(got[3:], ref[3:], ("fx", "fy")):
+        err = np.abs(a - b).max() / np.abs(b).max()
+        assert err < 1e-12, (n, err)
+    # without pruning the skipped bins come out far from the oracle's
+    for k in (0, 4, 6, 11):
+        assert np.abs(plain[0][k] - ref[0][k]).max() > 1e-6 * np.abs(ref[0][k]).max(), k
+    assert np.abs(plain[0][8] - ref[0][8]).max() < 1e-12 * np.abs(ref[0][8]).max()
+
+
+@pytest.mark.parametrize("bc", [(0, 0, 0, 0), (1, 1, 1, 1)])
+def test_brute_force_bands_match_oracle(bc):
+    # three broad bands (Sec. 3): per-[band][cell] flux opacity with optical
+    # depths 1e-2 to 1e2 per half cell, absorption 10-100 % of it, and an
+    # emissivity that supplies a J of the state's order in one step
+    nx = ny = 8
+    dx = 1e16
+    g = np.random.default_rng(241 + sum(bc))
+    nb = 3
+    aF = 10.0 ** g.uniform(-2, 2, (nb, ny, nx)) * 2.0 / dx
+    kap = aF * g.uniform(0.1, 1.0, aF.shape)
+    js = 5e-19 * g.uniform(0, 1, aF.shape)
+    ux = g.uniform(-300, 300, (ny, nx)) * 1e5
+    uy = g.uniform(-300, 300, (ny, nx)) * 1e5
+    J = 1e-3 * np.exp(g.normal(0, 1.0, (nb, ny, nx)))
+    th = g.uniform(0, 2 * np.pi, J.shape)
+    f = g.uniform(0, 0.9, J.shape)
+    st = (J, J * f * np.cos(th), J * f * np.sin(th))
+    O = oracle.Oracle.for_bands(nx=nx, ny=ny, dx=dx, alpha_F=aF, kappa=kap, emissivity=js,
+                                ux=ux, uy=uy, cfl=0.4, bc=bc)
+    ref = O.substep(*st)[:5]
+    z = np.zeros((ny, nx))
+    p = dict(nx=nx, ny=ny, dx=dx, T=1e4, n_hi=z, rho_d=z, p_d=z, ux=ux, uy=uy, lum=z,
+             kappa_abs=0.0, kappa_F=0.0, c_tilde=C, cfl=0.4, bc=bc)
+    got = brute_substep(p, *st, bands=(aF, kap, js))[0]
+    for a, b, n in zip(got, ref, ("J", "Hx", "Hy", "fx", "fy")):
+        err = _per_bin_err(a, b) if a.ndim == 3 else np.abs(a - b).max() / np.abs(b).max()
         assert err < 1e-12, (n, err)
