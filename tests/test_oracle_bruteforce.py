@@ -684,3 +684,33 @@ def test_brute_force_bands_match_oracle(bc):
     for a, b, n in zip(got, ref, ("J", "Hx", "Hy", "fx", "fy")):
         err = _per_bin_err(a, b) if a.ndim == 3 else np.abs(a - b).max() / np.abs(b).max()
         assert err < 1e-12, (n, err)
+
+
+@pytest.mark.parametrize("bc", [(0, 0, 0, 0), (1, 0, 0, 1)])
+def test_brute_force_gray_group_matches_oracle(bc):
+    # one gray group: the band equations with alpha_F = alpha eta + rho kappa_F,
+    # kappa = rho kappa_abs + p_d alpha eta and j = L / (4 pi V), where
+    # eta = sum_k w_k <H>_k over the bins of the grid (App. A tables)
+    p, st = _problem(bc, 251 + sum(bc))
+    e = p["edges"]
+    dD, av, s0 = line(p["T"])
+    xx = e / dD
+    h = (I_voigt(xx[1:], av) - I_voigt(xx[:-1], av)) / (np.diff(e) / dD)
+    w = h * np.diff(e) / dD
+    w = w / w.sum()
+    eta = float((w * h).sum())
+    alpha = p["n_hi"] * s0
+    aF = (alpha * eta + p["rho_d"] * p["kappa_F"])[None]
+    kap = (p["rho_d"] * p["kappa_abs"] + p["p_d"] * alpha * eta)[None]
+    js = (p["lum"] / (4.0 * math.pi * p["dx"] ** 3))[None]
+    st1 = tuple(np.ascontiguousarray(a[5:6]) for a in st)
+    O = oracle.Oracle(nx=p["nx"], ny=p["ny"], dx=p["dx"], edges=e, T=p["T"], n_hi=p["n_hi"],
+                      rho_d=p["rho_d"], p_d=p["p_d"], ux=p["ux"], uy=p["uy"], lum=p["lum"],
+                      kappa_abs=p["kappa_abs"], kappa_F=p["kappa_F"], c_tilde=p["c_tilde"],
+                      cfl=p["cfl"], recoil=True, bc=bc, gray=True)
+    assert O.nb == 1
+    ref = O.substep(*st1)[:5]
+    got = brute_substep(p, *st1, bands=(aF, kap, js))[0]
+    for a, b, n in zip(got, ref, ("J", "Hx", "Hy", "fx", "fy")):
+        err = np.abs(a - b).max() / np.abs(b).max()
+        assert err < 1e-12, (n, err)
