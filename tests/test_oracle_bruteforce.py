@@ -70,12 +70,13 @@ def prim(J, H1, H2):
     return (H1 / J, H2 / J) if J > 0.0 else (0.0, 0.0)
 
 
-def brute_substep(p, J, Hx, Hy, bands=None, prune=0.0):
+def brute_substep(p, J, Hx, Hy, bands=None, prune=0.0, diag=None):
     """bands: (alpha_F, kappa, j) per [band][cell] for broad bands (Sec. 3):
     each band is one frequency-integrated group (dnu = 1) with the given flux
     and absorption opacities and emissivity, and no step 3.  prune: bins
     holding no more than this share of sum_k dnu_k sum_cells J_k skip step 1
-    (Sec. 2.2)."""
+    (Sec. 2.2).  diag: a dict that receives the J face fluxes, the work term,
+    kappa, j and J'' of every bin, with c_tilde dt and the bin widths."""
     nx, ny, dx = p["nx"], p["ny"], p["dx"]
     if bands is None:
         e = p["edges"]
@@ -131,6 +132,8 @@ def brute_substep(p, J, Hx, Hy, bands=None, prune=0.0):
     Hx1 = np.empty_like(J)
     Hy1 = np.empty_like(J)
     W = np.zeros((nb, ny, nx))
+    FXJk = np.zeros((nb, ny, nx + 1))
+    FYJk = np.zeros((nb, ny + 1, nx))
     Ek = dnu * J.sum(axis=(1, 2))
     on = Ek > prune * Ek.sum() if prune > 0.0 else np.ones(nb, bool)
     for k in range(nb):
@@ -194,6 +197,7 @@ def brute_substep(p, J, Hx, Hy, bands=None, prune=0.0):
                 cs = [cell(i, j - 2 + m, 1) for m in range(4)]
                 FYJ[j, i], FYN[j, i], FYT[j, i] = face([c[0] for c in cs], cs[1][1], cs[2][1],
                                                        cs[1][2], cs[2][2])
+        FXJk[k], FYJk[k] = FXJ, FYJ
         for j in range(ny):
             for i in range(nx):
                 jv = J[k, j, i]
@@ -220,6 +224,10 @@ def brute_substep(p, J, Hx, Hy, bands=None, prune=0.0):
     fcoef = 4.0 * math.pi / (C * ct * dt)
     fx_out = fcoef * (dnu[:, None, None] * (Hx1 - Hx2)).sum(axis=0)
     fy_out = fcoef * (dnu[:, None, None] * (Hy1 - Hy2)).sum(axis=0)
+    if diag is not None:
+        shape = (nb, ny, nx)
+        diag.update(FXJ=FXJk, FYJ=FYJk, W=W, kap=np.broadcast_to(kap, shape),
+                    js=np.broadcast_to(js, shape), J2=J2, cdt=cdt, dnu=dnu)
 
     if bands is not None or not p.get("freq_step", True):  # no step 3 (nor its cap)
         return (J2, Hx2, Hy2, fx_out, fy_out), 0.0
@@ -322,13 +330,14 @@ def test_brute_force_substep_matches_oracle(bc):
     assert pmax > 5.0
 
 
-def brute_substep_cyl(p, J, Hx, Hy, prune=0.0):
+def brute_substep_cyl(p, J, Hx, Hy, prune=0.0, diag=None):
     """The same substep on the axisymmetric grid (x = R from the axis, y = Z
     from the midplane, per-radian finite volumes): R faces of area R dZ, Z faces
     (R+^2 - R-^2)/2, volume (R+^2 - R-^2) dZ / 2, centroid distances in tau, the
     hoop source -K_phiphi <1/R> in the H_R balance and D_phiphi <u_R/R> in the
     work and Doppler terms; the axis and the midplane are mirrors.  prune: as
-    for the Cartesian grid, the bin energies weighted by the ring volumes."""
+    for the Cartesian grid, the bin energies weighted by the ring volumes.
+    diag: as for the Cartesian grid, with the geometry (R faces, volumes)."""
     nx, ny, dx = p["nx"], p["ny"], p["dx"]
     e = p["edges"]
     nb = e.size - 1
@@ -380,6 +389,9 @@ def brute_substep_cyl(p, J, Hx, Hy, prune=0.0):
     J1 = np.empty_like(J)
     Hx1 = np.empty_like(J)
     Hy1 = np.empty_like(J)
+    W = np.zeros((nb, ny, nx))
+    FRJ = np.zeros((nb, ny, nx + 1))
+    FZJ = np.zeros((nb, ny + 1, nx))
     Ek = dnu * (J * Vol[None, None, :]).sum(axis=(1, 2))
     on = Ek > prune * Ek.sum() if prune > 0.0 else np.ones(nb, bool)
     for k in range(nb):
@@ -441,12 +453,14 @@ def brute_substep_cyl(p, J, Hx, Hy, prune=0.0):
                 cs = [cell(i, j - 2 + m, 1) for m in range(4)]
                 FZ[:, j, i] = face([c[0] for c in cs], cs[1][1], cs[2][1], cs[1][2], cs[2][2],
                                    dx / 2.0, dx / 2.0)
+        FRJ[k], FZJ[k] = FR[0], FZ[0]
         for j in range(ny):
             for i in range(nx):
                 jv = J[k, j, i]
                 fx, fy = cap(*prim(jv, Hx[k, j, i], Hy[k, j, i]))
                 Dxx, Dxy, Dyy, Dpp = closure(fx, fy)
                 Wc = (Dxx * gxx[j, i] + Dyy * gyy[j, i] + Dxy * gsh[j, i] + Dpp * gphi[j, i]) * jv
+                W[k, j, i] = Wc
 
                 def div(fr, fz):
                     return ((Rf[i + 1] * dx * fr[j, i + 1] - Rf[i] * dx * fr[j, i])
@@ -466,6 +480,11 @@ def brute_substep_cyl(p, J, Hx, Hy, prune=0.0):
     fcoef = 4.0 * math.pi / (C * ct * dt)
     fx_out = fcoef * (dnu[:, None, None] * (Hx1 - Hx2)).sum(axis=0)
     fy_out = fcoef * (dnu[:, None, None] * (Hy1 - Hy2)).sum(axis=0)
+    if diag is not None:
+        shape = (nb, ny, nx)
+        diag.update(FXJ=FRJ, FYJ=FZJ, W=W, kap=np.broadcast_to(kap, shape),
+                    js=np.broadcast_to(js, shape), J2=J2, cdt=cdt, dnu=dnu, Rf=Rf, AZ=AZ,
+                    Vol=Vol)
     if not p.get("freq_step", True):
         return (J2, Hx2, Hy2), fx_out, fy_out
     # step 3 with D_phiphi <u_R/R> in the Doppler term: the Cartesian routine's
@@ -714,3 +733,80 @@ def test_brute_force_gray_group_matches_oracle(bc):
     for a, b, n in zip(got, ref, ("J", "Hx", "Hy", "fx", "fy")):
         err = np.abs(a - b).max() / np.abs(b).max()
         assert err < 1e-12, (n, err)
+
+
+@pytest.mark.parametrize("bc", [(1, 0, 0, 1), (0, 1, 1, 0)])
+def test_brute_force_bookkeeping_and_spectrum_match_oracle(bc):
+    # The photon bookkeeping of one substep, in erg (4 pi V / c per unit of
+    # sum_k dnu_k J_k): emission c_tilde dt j, absorption c_tilde dt kappa J'',
+    # work c_tilde dt W / c, and the emergent spectrum, the J flux through each
+    # outer face (x- rows, x+ rows, y- columns, y+ columns) per bin, whose sum
+    # is the outflow; e_after from the state after step 3.
+    p, st = _problem(bc, 261 + bc[0])
+    O = oracle.Oracle(nx=p["nx"], ny=p["ny"], dx=p["dx"], edges=p["edges"], T=p["T"],
+                      n_hi=p["n_hi"], rho_d=p["rho_d"], p_d=p["p_d"], ux=p["ux"], uy=p["uy"],
+                      lum=p["lum"], kappa_abs=p["kappa_abs"], kappa_F=p["kappa_F"],
+                      c_tilde=p["c_tilde"], cfl=p["cfl"], recoil=True, bc=bc)
+    O.spectrum_on()
+    out = O.substep(*st)
+    d, spec = out[5], O.spectrum.copy()
+    dg = {}
+    (J3, _, _, _, _), _ = brute_substep(p, *st, diag=dg)
+    nx, ny, dx = p["nx"], p["ny"], p["dx"]
+    eunit = 4.0 * math.pi * dx ** 3 / C
+    cdt, dnu = dg["cdt"], dg["dnu"]
+    per_bin = eunit * cdt * dnu / dx
+    faces = np.concatenate([-dg["FXJ"][:, :, 0], dg["FXJ"][:, :, nx],
+                            -dg["FYJ"][:, 0, :], dg["FYJ"][:, ny, :]], axis=1) * per_bin[:, None]
+    assert spec.shape == faces.shape == (dnu.size, 2 * (nx + ny))
+    assert np.abs(spec - faces).max() <= 1e-12 * np.abs(faces).max()
+    want = {
+        "e_before": eunit * (dnu[:, None, None] * st[0]).sum(),
+        "e_after": eunit * (dnu[:, None, None] * J3).sum(),
+        "emitted": eunit * cdt * (dnu[:, None, None] * dg["js"]).sum(),
+        "absorbed": eunit * cdt * (dnu[:, None, None] * dg["kap"] * dg["J2"]).sum(),
+        "work": eunit * cdt * (dnu[:, None, None] * dg["W"]).sum() / C,
+        "outflow": faces.sum(),
+    }
+    for name, v in want.items():
+        assert d[name] == pytest.approx(v, rel=1e-12), name
+    # every source emits L dt c_tilde / c in total, whatever the geometry
+    assert d["emitted"] == pytest.approx(p["lum"].sum() * cdt / C, rel=1e-12)
+
+
+@pytest.mark.parametrize("bc", [(0, 0, 0, 0), (0, 1, 0, 1)])
+def test_brute_force_axisymmetric_bookkeeping_matches_oracle(bc):
+    # the same on the axisymmetric grid: cell energies weighted by the ring
+    # volume 2 pi Vol, and the emergent spectrum through the outer R faces
+    # (area 2 pi R_out dZ) and the outer Z faces (area 2 pi (R+^2 - R-^2)/2)
+    p, st = _problem(bc, 271 + bc[1])
+    O = oracle.Oracle(nx=p["nx"], ny=p["ny"], dx=p["dx"], edges=p["edges"], T=p["T"],
+                      n_hi=p["n_hi"], rho_d=p["rho_d"], p_d=p["p_d"], ux=p["ux"], uy=p["uy"],
+                      lum=p["lum"], kappa_abs=p["kappa_abs"], kappa_F=p["kappa_F"],
+                      c_tilde=p["c_tilde"], cfl=p["cfl"], recoil=True, bc=bc, geometry=1)
+    O.spectrum_on()
+    d = O.substep(*st)[5]
+    spec = O.spectrum.copy()
+    dg = {}
+    (J3, _, _), _, _ = brute_substep_cyl(p, *st, diag=dg)
+    nx, ny, dx = p["nx"], p["ny"], p["dx"]
+    eu = 4.0 * math.pi / C
+    cdt, dnu = dg["cdt"], dg["dnu"]
+    ring = 2.0 * math.pi * dg["Vol"][None, None, :]
+    per_bin = eu * 2.0 * math.pi * cdt * dnu
+    faces = np.concatenate([dg["FXJ"][:, :, nx] * (dg["Rf"][nx] * dx),
+                            dg["FYJ"][:, ny, :] * dg["AZ"][None, :]], axis=1) * per_bin[:, None]
+    assert spec.shape == faces.shape == (dnu.size, nx + ny)
+    assert np.abs(spec - faces).max() <= 1e-12 * np.abs(faces).max()
+    want = {
+        "e_before": eu * (dnu[:, None, None] * st[0] * ring).sum(),
+        "e_after": eu * (dnu[:, None, None] * J3 * ring).sum(),
+        "emitted": eu * cdt * (dnu[:, None, None] * dg["js"] * ring).sum(),
+        "absorbed": eu * cdt * (dnu[:, None, None] * dg["kap"] * dg["J2"] * ring).sum(),
+        "work": eu * cdt * (dnu[:, None, None] * dg["W"] * ring).sum() / C,
+        "outflow": faces.sum(),
+    }
+    for name, v in want.items():
+        assert d[name] == pytest.approx(v, rel=1e-12), name
+    # every source emits L dt c_tilde / c in total, whatever the geometry
+    assert d["emitted"] == pytest.approx(p["lum"].sum() * cdt / C, rel=1e-12)
