@@ -997,7 +997,7 @@ int lym1_diagnostics(lym1_ctx* c, lym1_diag* d) {
   LYM1_TRY(cudaMemcpyAsync(acc, c->acc, sizeof acc, cudaMemcpyDeviceToHost, c->stream));
   double Ldev = 0.0;
   if (c->L_pending)
-    LYM1_TRY(cudaMemcpyAsync(&Ldev, c->lsum + 152, sizeof Ldev, cudaMemcpyDeviceToHost, c->stream));
+    LYM1_TRY(cudaMemcpyAsync(&Ldev, c->lsum + kSumResult, sizeof Ldev, cudaMemcpyDeviceToHost, c->stream));
   LYM1_TRY(cudaMemcpyAsync(fp.data(), c->fpart, fp.size() * sizeof(double), cudaMemcpyDeviceToHost,
                            c->stream));
   LYM1_TRY(cudaStreamSynchronize(c->stream));
@@ -1396,9 +1396,9 @@ int lym1_set_temperature(lym1_ctx* c, const double* temp_field) {
 
 int lym1_set_pruning(lym1_ctx* c, double cut) {
   if (!c || !(cut >= 0.0) || !(cut < 1.0)) return LYM1_EINVAL;
-  if (cut > 0.0 && !c->active) {
-    int rc = dalloc_t(c, &c->Ebin, static_cast<size_t>(c->nb) * 17);
-    if (rc == LYM1_OK) rc = dalloc_t(c, &c->active, static_cast<size_t>(c->nb));
+  if (cut > 0.0) {  // each buffer once (a failed call leaves the other for the next)
+    int rc = c->Ebin ? LYM1_OK : dalloc_t(c, &c->Ebin, static_cast<size_t>(c->nb) * 17);
+    if (rc == LYM1_OK && !c->active) rc = dalloc_t(c, &c->active, static_cast<size_t>(c->nb));
     if (rc != LYM1_OK) return rc;
   }
   // the captured launches hold the cut by value: any change rebuilds them

@@ -211,6 +211,7 @@ int launch_force_reduce(const double* fx, const double* fy, int nx, int ny, doub
 // sum over cells of a[n] into work[152] (work: 152 partials, the sum, a zeroed
 // counter word; kSumWork doubles)
 constexpr int kSumWork = 154;
+constexpr int kSumResult = 152;  // index of the sum in work
 int launch_sum_cells(const double* a, long long n, double* work, void* stream);
 // active-bin pruning: E[k] = dnu_k sum_cells w J_k (w = wcol[column], or 1),
 // then active[k] = E[k] > cut sum_k E[k]; E holds nb x (1 + 16) doubles
