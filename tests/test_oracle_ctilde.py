@@ -137,3 +137,48 @@ def test_time_step_follows_ctilde():
     assert O.dt_cfl * (ct + u) == pytest.approx(dt0 * (C + u), rel=1e-14)
     O.set_ctilde(3e8)
     assert O.dt_cfl * (3e8 + u) == pytest.approx(dt0 * (C + u), rel=1e-14)
+
+
+def test_random_field_matches_the_printed_rule():
+    # every term on, per-cell temperatures, sound speeds given or defaulted:
+    # the printed rule evaluated cell by cell in numpy, with the line constants
+    # from their definitions (tau_cell,0 = alpha dx, tau_cell,c = rho_d kappa_abs dx),
+    # then the floor, the cap and the rate limits against the previous value.
+    # A fast flow lets |u| decide the deciding cell, a slow one c_s.
+    KB, MH, ME, QE = 1.380649e-16, 1.67353284e-24, 9.1093837015e-28, 4.803204712570263e-10
+    NU0 = C / 1215.67e-8
+    nx, ny, dx = 9, 7, 3e16
+    g = np.random.default_rng(31)
+    T = 10.0 ** g.uniform(3.5, 4.5, (ny, nx))
+    n_hi = 10.0 ** g.uniform(-3, 3, (ny, nx))
+    rho = 10.0 ** g.uniform(-27, -23, (ny, nx))
+    pd = 10.0 ** g.uniform(-8, -3, (ny, nx))
+    ux0 = g.uniform(-30, 30, (ny, nx)) * KM
+    uy0 = g.uniform(-30, 30, (ny, nx)) * KM
+    cs = g.uniform(1, 20, (ny, nx)) * KM
+    kabs = 2.682e4
+    dnuD = NU0 * np.sqrt(2.0 * KB * T / MH) / C
+    a_v = 6.265e8 / (4.0 * np.pi * dnuD)
+    sigma0 = np.sqrt(np.pi) * QE * QE * 0.4162 / (ME * C * dnuD)
+    tau0 = n_hi * sigma0 * dx
+    tauc = rho * kabs * dx
+    trap = np.cbrt(a_v * tau0)
+    fac = np.maximum(1.0, trap / (1.0 + trap * tauc + 0.6 * pd * tau0))
+    cs_neutral = np.sqrt((5.0 / 3.0) * KB * T / (1.22 * MH))
+    assert (fac > 1.0).any() and (fac == 1.0).any()
+    for scale in (1.0, 0.05):
+        ux, uy = scale * ux0, scale * uy0
+        speed = np.hypot(ux, uy)
+        for c_s, given in ((cs, cs), (cs_neutral, None)):
+            term = fac * np.maximum(speed, c_s)
+            top = np.unravel_index(np.argmax(term), term.shape)
+            assert (speed[top] > c_s[top]) == (scale == 1.0)
+            for eps in (4.0, 2.5):
+                want = min(max(1e7, eps * term.max()), C)
+                assert 1e7 < want < C
+                for prev, expect in ((1.2 * want, want), (3.0 * want, 2.25 * want),
+                                     (want / 8.0, want / 2.0)):
+                    O = _oracle(n_hi, ux, uy, kappa_abs=kabs, rho_d=rho, p_d=pd, c_tilde=prev,
+                                temp=T, nx=nx, ny=ny, dx=dx)
+                    got = O.dynamic_ctilde(given, eps_rsl=eps, ct_min=1e7)
+                    assert got == pytest.approx(expect, rel=1e-12), (scale, eps, prev / want)
