@@ -337,18 +337,29 @@ def brute_substep_cyl(p, J, Hx, Hy, prune=0.0, diag=None):
     hoop source -K_phiphi <1/R> in the H_R balance and D_phiphi <u_R/R> in the
     work and Doppler terms; the axis and the midplane are mirrors.  prune: as
     for the Cartesian grid, the bin energies weighted by the ring volumes.
-    diag: as for the Cartesian grid, with the geometry (R faces, volumes)."""
+    diag: as for the Cartesian grid, with the geometry (R faces, volumes).
+    p["temp"]: per-cell temperatures, every A0 table per cell."""
     nx, ny, dx = p["nx"], p["ny"], p["dx"]
     e = p["edges"]
     nb = e.size - 1
-    T = p["T"]
-    dnuD, av, s0 = line(T)
     dnu = np.diff(e)
     nubar = NU0 + 0.5 * (e[1:] + e[:-1])
-    x = e / dnuD
-    Hk = (I_voigt(x[1:], av) - I_voigt(x[:-1], av)) / (dnu / dnuD)
-    w = Hk * (dnu / dnuD)
-    w = w / w.sum()
+    Tc = p.get("temp")
+    Tc = np.full((ny, nx), p["T"]) if Tc is None else Tc
+    Hk = np.empty((nb, ny, nx))
+    w = np.empty((nb, ny, nx))
+    dnuD = np.empty((ny, nx))
+    s0 = np.empty((ny, nx))
+    for j in range(ny):
+        for i in range(nx):
+            dD, av, sg = line(Tc[j, i])
+            x = e / dD
+            h = (I_voigt(x[1:], av) - I_voigt(x[:-1], av)) / (dnu / dD)
+            ww = h * (dnu / dD)
+            Hk[:, j, i] = h
+            w[:, j, i] = ww / ww.sum()
+            dnuD[j, i] = dD
+            s0[j, i] = sg
     alpha = p["n_hi"] * s0
     rho, pd, ux, uy, lum = p["rho_d"], p["p_d"], p["ux"], p["uy"], p["lum"]
     kabs, kF = p["kappa_abs"], p["kappa_F"]
@@ -470,10 +481,10 @@ def brute_substep_cyl(p, J, Hx, Hy, prune=0.0, diag=None):
                 Hx1[k, j, i] = Hx[k, j, i] - cdt * (div(FR[1], FZ[2]) - Dpp * jv * invR)
                 Hy1[k, j, i] = Hy[k, j, i] - cdt * div(FR[2], FZ[1])
 
-    aH = alpha[None] * Hk[:, None, None]
+    aH = alpha[None] * Hk
     kap = rho[None] * kabs + pd[None] * aH
     aFk = aH + rho[None] * kF
-    js = (lum / (2.0 * math.pi * Vol[None, :]))[None] * (w / (4.0 * math.pi * dnu))[:, None, None]
+    js = (lum / (2.0 * math.pi * Vol[None, :]))[None] * w / (4.0 * math.pi * dnu[:, None, None])
     J2 = (J1 + cdt * js) / (1.0 + cdt * kap)
     Hx2 = Hx1 / (1.0 + cdt * aFk)
     Hy2 = Hy1 / (1.0 + cdt * aFk)
@@ -490,15 +501,14 @@ def brute_substep_cyl(p, J, Hx, Hy, prune=0.0, diag=None):
     # step 3 with D_phiphi <u_R/R> in the Doppler term: the Cartesian routine's
     # solve, on gradients that include the hoop part
     q = dict(p, _grads=(gxx, gyy, gsh, gphi))
-    return _freq_and_cap(q, J2, Hx2, Hy2, Hk, dnu, nubar, dnuD, alpha, cdt, T), fx_out, fy_out
+    return _freq_and_cap(q, J2, Hx2, Hy2, Hk, dnu, nubar, dnuD, alpha, cdt, Tc), fx_out, fy_out
 
 
 def _freq_and_cap(p, J2, Hx2, Hy2, Hk, dnu, nubar, dnuD, alpha, cdt, T):
+    # Hk [bin][cell], dnuD and T per cell
     nb = dnu.size
     ny, nx = alpha.shape
     gxx, gyy, gsh, gphi = p["_grads"]
-    hkT = HPL / (KB * T)
-    Rk = hkT - 2.0 / nubar if p["recoil"] else np.zeros(nb)
     half = 0.5 * dnu
     J3, Hx3, Hy3 = J2.copy(), Hx2.copy(), Hy2.copy()
 
@@ -517,7 +527,9 @@ def _freq_and_cap(p, J2, Hx2, Hy2, Hk, dnu, nubar, dnuD, alpha, cdt, T):
     for j in range(ny):
         for i in range(nx):
             if alpha[j, i] > 0.0:
-                K = 0.5 * dnuD * dnuD * alpha[j, i] * Hk
+                K = 0.5 * dnuD[j, i] ** 2 * alpha[j, i] * Hk[:, j, i]
+                hkT = HPL / (KB * T[j, i])
+                Rk = hkT - 2.0 / nubar if p["recoil"] else np.zeros(nb)
                 Cc = np.empty(nb)
                 for k in range(nb):
                     fx, fy = cap(*prim(J2[k, j, i], Hx2[k, j, i], Hy2[k, j, i]))
@@ -810,3 +822,21 @@ def test_brute_force_axisymmetric_bookkeeping_matches_oracle(bc):
         assert d[name] == pytest.approx(v, rel=1e-12), name
     # every source emits L dt c_tilde / c in total, whatever the geometry
     assert d["emitted"] == pytest.approx(p["lum"].sum() * cdt / C, rel=1e-12)
+
+
+def test_brute_force_axisymmetric_temperature_field_matches_oracle():
+    # the axisymmetric substep under per-cell temperatures (5e3 K to 3e4 K):
+    # every A0 table per cell, the emission per ring volume
+    p, st = _problem((0, 1, 0, 1), 281)
+    g = np.random.default_rng(282)
+    p["temp"] = 10.0 ** g.uniform(np.log10(5e3), np.log10(3e4), (p["ny"], p["nx"]))
+    O = oracle.Oracle(nx=p["nx"], ny=p["ny"], dx=p["dx"], edges=p["edges"], T=p["T"],
+                      n_hi=p["n_hi"], rho_d=p["rho_d"], p_d=p["p_d"], ux=p["ux"], uy=p["uy"],
+                      lum=p["lum"], kappa_abs=p["kappa_abs"], kappa_F=p["kappa_F"],
+                      c_tilde=p["c_tilde"], cfl=p["cfl"], recoil=True, bc=p["bc"], geometry=1,
+                      temp=p["temp"])
+    ref = O.substep(*st)[:5]
+    (J3, Hx3, Hy3), fx, fy = brute_substep_cyl(p, *st)
+    for a, b, n in zip((J3, Hx3, Hy3, fx, fy), ref, ("J", "Hx", "Hy", "fx", "fy")):
+        err = np.abs(a - b).max() / np.abs(b).max()
+        assert err < 1e-12, (n, err)
