@@ -11,6 +11,11 @@ single-domain run: they depend only on rows the rank holds correctly.  The
 halo rows come out wrong (their own stencil reaches beyond the slab) and are
 overwritten by the next swap.
 
+Domain-wide quantities reduce across the slabs: the time step (global_dt)
+and the dynamic reduced speed of light (global_ctilde).  Active-bin pruning
+decides on the domain's energy per bin, which no slab holds, so slab runs
+keep it off.
+
 The module is solver-agnostic: state arrays are [nb][rows][nx] numpy arrays
 or torch tensors (CPU with gloo, CUDA with NCCL); the caller advances its
 slab with whatever it uses (a lym1 context through set_state / substeps /
@@ -78,6 +83,18 @@ def exchange(arrays, ny: int, world: int, rank: int, group=None):
                 a[:, rows].copy_(buf)
             else:
                 a[:, rows] = buf.numpy()
+
+
+def global_ctilde(local_ctilde: float, group=None) -> float:
+    """The single-domain dynamic reduced speed of light (Sec. 2.1, the
+    dynamic-RSL rule): each slab applies the rule to its own cells from the
+    same previous value.  The rule is a maximum over cells followed by the
+    floor, the cap and the rate limits, all non-decreasing, so the domain's
+    value is the largest of the slabs' values.  Every slab then takes it
+    (set_ctilde), which keeps the previous values equal for the next update."""
+    t = torch.tensor([float(local_ctilde)], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX, group=group)
+    return float(t.item())
 
 
 def global_dt(local_dt: float, group=None) -> float:

@@ -56,6 +56,8 @@ def _slab_oracle(c, e0, e1, ny):
 def _worker(rank, world, port, geometry, out):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     dist.init_process_group("gloo", rank=rank, world_size=world)
+    import oracle
+    oracle.set_threads(1)  # one thread per rank: the ranks share the host's cores
     c = _cloud(geometry)
     ny = c.ny
     slabs.check_split(ny, world)
@@ -76,6 +78,52 @@ def _worker(rank, world, port, geometry, out):
         out.put(gathered)
     dist.barrier()
     dist.destroy_process_group()
+
+
+def _worker_ctilde(rank, world, port, geometry, out):
+    # two dynamic c_tilde updates from 1e8 cm/s (the first bound by the x4
+    # rate limit), each followed by two substeps
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import oracle
+    oracle.set_threads(1)  # one thread per rank: the ranks share the host's cores
+    c = _cloud(geometry)
+    ny = c.ny
+    y0, y1 = slabs.slab_rows(ny, world, rank)
+    e0, e1 = slabs.extended_rows(ny, world, rank)
+    O = _slab_oracle(c, e0, e1, ny)
+    O.set_ctilde(1e8)
+    J, Hx, Hy = (np.ascontiguousarray(a[:, e0:e1]) for a in _state(c))
+    cts = []
+    for _ in range(2):
+        ct = slabs.global_ctilde(O.dynamic_ctilde())
+        O.set_ctilde(ct)
+        cts.append(ct)
+        dt = slabs.global_dt(O.dt_cfl)
+        for _ in range(2):
+            slabs.exchange((J, Hx, Hy), ny, world, rank)
+            J, Hx, Hy, _, _, _ = O.substep(J, Hx, Hy, dt)
+    own = slice(y0 - e0, y1 - e0)
+    gathered = [None] * world
+    dist.all_gather_object(gathered, (y0, y1, J[:, own], cts))
+    if rank == 0:
+        out.put(gathered)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def _run_workers(target, world, geometry):
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=target, args=(r, world, port, geometry, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    gathered = q.get(timeout=300)
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    return gathered
 
 
 def test_split_is_a_balanced_partition():
@@ -116,3 +164,29 @@ def test_decomposed_run_equals_single_domain(geometry, world):
         np.testing.assert_array_equal(Hys, Hy[:, y0:y1])
         np.testing.assert_array_equal(fxs, fx[y0:y1])
         np.testing.assert_array_equal(fys, fy[y0:y1])
+
+
+@pytest.mark.parametrize("geometry,world", [(0, 3), (1, 2)])
+def test_decomposed_dynamic_ctilde_equals_single_domain(geometry, world):
+    import oracle
+    c = _cloud(geometry)
+    ref_O = oracle.Oracle(edges=oracle.freq_grid(), **c.kwargs())
+    ref_O.set_ctilde(1e8)
+    st = _state(c)
+    cts = []
+    for _ in range(2):
+        cts.append(ref_O.dynamic_ctilde())
+        st, _ = ref_O.run(2, st)
+        st = st[:3]
+    assert cts[0] == 4e8 and cts[1] > cts[0]  # rate-limited, then the rule's own value
+    # the deciding cell sits in one slab: the others reach lower values
+    local = []
+    for r in range(world):
+        e0, e1 = slabs.extended_rows(c.ny, world, r)
+        O = _slab_oracle(c, e0, e1, c.ny)
+        O.set_ctilde(4e8)
+        local.append(O.dynamic_ctilde())
+    assert max(local) == cts[1] and min(local) < cts[1]
+    for y0, y1, Js, got in _run_workers(_worker_ctilde, world, geometry):
+        assert got == cts
+        np.testing.assert_array_equal(Js, st[0][:, y0:y1])
