@@ -126,6 +126,41 @@ def _run_workers(target, world, geometry):
     return gathered
 
 
+def _worker_rows(rank, world, port, ny, out):
+    # each rank fills its own rows with their global row index (halo rows -1),
+    # as a numpy array and as a torch tensor, and swaps the halos
+    import torch
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    y0, y1 = slabs.slab_rows(ny, world, rank)
+    e0, e1 = slabs.extended_rows(ny, world, rank)
+    rows = np.arange(e0, e1, dtype=np.float64)
+    a = np.where((rows >= y0) & (rows < y1), rows, -1.0)[None, :, None] * np.ones((3, 1, 5))
+    t = torch.from_numpy(a.copy())
+    slabs.exchange((a, t), ny, world, rank)
+    out.put((rank, a, t.numpy(), rows))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("ny,world", [(9, 4), (17, 3), (4, 2)])
+def test_exchange_fills_every_halo_row_from_its_owner(ny, world):
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker_rows, args=(r, world, port, ny, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = [q.get(timeout=120) for _ in range(world)]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, a, t, rows in res:
+        want = np.broadcast_to(rows[None, :, None], a.shape)
+        np.testing.assert_array_equal(a, want)
+        np.testing.assert_array_equal(t, want)
+
+
 def test_split_is_a_balanced_partition():
     for ny in (4, 17, 512, 2048):
         for world in (1, 2, 3, 8):
