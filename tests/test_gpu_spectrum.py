@@ -3,7 +3,6 @@ parity with the oracle's per-substep spectra summed over substeps (bit-exact in
 FP64_DET, 1e-4 normwise per bin in mixed_fast) and the frequency scaling of
 escaping photons, |nu - nu_Lya| ~ (a_v tau_0)^(1/3) dnu_D (Sec. 2.1), seen
 in the peaks of the emergent spectra of two thick spheres."""
-import math
 
 import numpy as np
 import pytest

@@ -4,7 +4,6 @@ passes between ranks except the final statistics."""
 import os
 import socket
 
-import pytest
 import torch.distributed as dist
 import torch.multiprocessing as mp
 

@@ -3,7 +3,6 @@ continuous batching rounds, steady-state rule, substep cap), with a fake
 backend whose energy relaxes as E_n = 1 - exp(-n / tau) -- no GPU."""
 import math
 
-import pytest
 
 from paper_2606_02711_gb300.serve import Request, Server, shard, state_bytes, summarize
 
