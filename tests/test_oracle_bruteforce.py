@@ -763,7 +763,7 @@ def test_brute_force_bookkeeping_and_spectrum_match_oracle(bc):
     out = O.substep(*st)
     d, spec = out[5], O.spectrum.copy()
     dg = {}
-    (J3, _, _, _, _), _ = brute_substep(p, *st, diag=dg)
+    (J3, Hx3, Hy3, fxb, fyb), _ = brute_substep(p, *st, diag=dg)
     nx, ny, dx = p["nx"], p["ny"], p["dx"]
     eunit = 4.0 * math.pi * dx ** 3 / C
     cdt, dnu = dg["cdt"], dg["dnu"]
@@ -780,10 +780,20 @@ def test_brute_force_bookkeeping_and_spectrum_match_oracle(bc):
         "work": eunit * cdt * (dnu[:, None, None] * dg["W"]).sum() / C,
         "outflow": faces.sum(),
     }
+    # the force integrals, |f| dV and f . r_hat dV with r from the box centre
+    x = (np.arange(nx) + 0.5) * dx - 0.5 * nx * dx
+    y = (np.arange(ny) + 0.5) * dx - 0.5 * ny * dx
+    X, Y = np.meshgrid(x, y)
+    want["force_abs"] = (np.hypot(fxb, fyb) * dx ** 3).sum()
+    want["force_radial"] = ((fxb * X + fyb * Y) / np.hypot(X, Y) * dx ** 3).sum()
     for name, v in want.items():
         assert d[name] == pytest.approx(v, rel=1e-12), name
     # every source emits L dt c_tilde / c in total, whatever the geometry
     assert d["emitted"] == pytest.approx(p["lum"].sum() * cdt / C, rel=1e-12)
+    # realisability after the causality cap of step 3
+    hn = np.hypot(Hx3, Hy3)
+    assert d["max_f"] == pytest.approx((hn[J3 > 0] / J3[J3 > 0]).max(), rel=1e-12)
+    assert d["max_f"] <= 1.0 + 1e-15 and d["n_unrealisable"] == 0
 
 
 @pytest.mark.parametrize("bc", [(0, 0, 0, 0), (0, 1, 0, 1)])
@@ -800,7 +810,7 @@ def test_brute_force_axisymmetric_bookkeeping_matches_oracle(bc):
     d = O.substep(*st)[5]
     spec = O.spectrum.copy()
     dg = {}
-    (J3, _, _), _, _ = brute_substep_cyl(p, *st, diag=dg)
+    (J3, Hx3, Hy3), fxb, fyb = brute_substep_cyl(p, *st, diag=dg)
     nx, ny, dx = p["nx"], p["ny"], p["dx"]
     eu = 4.0 * math.pi / C
     cdt, dnu = dg["cdt"], dg["dnu"]
@@ -818,10 +828,19 @@ def test_brute_force_axisymmetric_bookkeeping_matches_oracle(bc):
         "work": eu * cdt * (dnu[:, None, None] * dg["W"] * ring).sum() / C,
         "outflow": faces.sum(),
     }
+    # the force integrals over the rings, r_hat from the origin (R, Z) = (0, 0)
+    R = (np.arange(nx) + 0.5) * dx
+    Z = (np.arange(ny) + 0.5) * dx
+    RR, ZZ = np.meshgrid(R, Z)
+    want["force_abs"] = (np.hypot(fxb, fyb) * ring[0]).sum()
+    want["force_radial"] = ((fxb * RR + fyb * ZZ) / np.hypot(RR, ZZ) * ring[0]).sum()
     for name, v in want.items():
         assert d[name] == pytest.approx(v, rel=1e-12), name
     # every source emits L dt c_tilde / c in total, whatever the geometry
     assert d["emitted"] == pytest.approx(p["lum"].sum() * cdt / C, rel=1e-12)
+    hn = np.hypot(Hx3, Hy3)
+    assert d["max_f"] == pytest.approx((hn[J3 > 0] / J3[J3 > 0]).max(), rel=1e-12)
+    assert d["max_f"] <= 1.0 + 1e-15 and d["n_unrealisable"] == 0
 
 
 def test_brute_force_axisymmetric_temperature_field_matches_oracle():
