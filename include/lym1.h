@@ -276,20 +276,36 @@ int lym1_profile_enable(lym1_ctx *ctx, int on);
  * otherwise).
  */
 int lym1_debug_expire_wait(lym1_ctx *ctx);
+
+/*
+ * Test hook for the FP64 helpers of the LYM1_MIXED kernels (no counterpart in
+ * the paper: GB300 runs FP64 arithmetic and FP32 <-> FP64 conversions on a
+ * pipe of ~1/70 of the FP32 rate, so those kernels convert on the integer
+ * pipe and refine a hardware reciprocal approximation by Newton-Raphson).
+ * For i < n (device pointers, caller-owned): wide[i] = xf[i] widened to FP64,
+ * narrow[i] = xd[i] narrowed to FP32 (round to nearest even), rcp[i] = 1 /
+ * xd[i]; both conversions flush subnormals to zero.  Runs on the legacy default
+ * stream and synchronises it.  LYM1_EINVAL for null pointers or n < 0;
+ * LYM1_ECUDA if the launch fails.
+ */
+int lym1_debug_fp64_helpers(const float *xf, const double *xd, long long n, double *wide,
+                            float *narrow, double *rcp);
 int lym1_profile_read(lym1_ctx *ctx, lym1_profile *out, int reset);
 
 /*
  * Allocation-free energy of a caller-owned state.  The paper has no
  * counterpart: this is a service for callers that cannot allocate device
  * memory when they need the number -- for instance a host code whose device
- * memory is owned by another runtime's allocator, a real-time loop that
- * forbids allocation, or work recorded into a CUDA graph.
+ * memory is owned by another runtime's allocator (a framework that has already
+ * reserved most of HBM), or a real-time loop that forbids allocation.
  *
  * Returns in *e_out (host or device pointer) the Lya energy in erg,
  * (4 pi / c) dx^3 sum_cells sum_k dnu_k J_k, of J[nb][nc] (FP64, device
- * pointer) with bin widths dnu[nb] (host pointer, Hz), using the same
- * reduction order as the energy in lym1_diagnostics.  Runs on cuda_stream
- * (NULL = legacy default stream) and synchronises it before returning.
+ * memory of the current device) with bin widths dnu[nb] (host pointer, Hz),
+ * with the same partition, reduction order and rounding as the energy that
+ * lym1_diagnostics reports for a Cartesian FP64 context holding that state.
+ * Runs on cuda_stream (NULL = legacy default stream) and synchronises it
+ * before returning.
  *
  * Memory: calls no cudaMalloc/cudaFree and no allocating library routine.
  * Its partial sums live in one file-scope device array of
@@ -300,9 +316,13 @@ int lym1_profile_read(lym1_ctx *ctx, lym1_profile *out, int reset);
  * capture.  All calls share the array and it keeps the last call's contents:
  * calls that overlap on the GPU (other streams, other host threads) race and
  * must be serialised by the caller.
- * Errors: LYM1_EINVAL for null pointers, nb or nc < 1, dx_cm <= 0;
+ * Errors: LYM1_EINVAL for null pointers, nb or nc < 1, dx_cm <= 0, or a J
+ * that is not device (or managed) memory of the current device (host arrays
+ * included), checked with cudaPointerGetAttributes before any launch;
  * LYM1_ERANGE for nb > LYM1_NOALLOC_MAX_BINS or nc > LYM1_NOALLOC_MAX_CELLS;
- * LYM1_ECUDA if a launch or copy fails.
+ * LYM1_ECUDA if a launch or copy fails.  A CUDA error already pending when
+ * the call starts is reported as LYM1_ECUDA and left pending for the caller;
+ * an error raised by the call itself is cleared before it returns.
  */
 #define LYM1_NOALLOC_MAX_CELLS (1 << 24) /* 16,777,216 cells, e.g. 4096 x 4096 */
 #define LYM1_NOALLOC_MAX_BINS 1024

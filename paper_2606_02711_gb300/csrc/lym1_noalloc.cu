@@ -3,11 +3,10 @@
 //
 // Some callers cannot call cudaMalloc at the moment they need this number: a
 // host code whose device memory is owned by another runtime's allocator (a
-// framework that preallocates most of HBM), a real-time loop that forbids
-// allocation, or work being recorded into a CUDA graph.  This entry point
-// runs the same two-stage reduction as the library's own energy bookkeeping,
-// with its per-block partial sums in a file-scope device array of fixed size
-// instead of a context's allocation.
+// framework that preallocates most of HBM), or a real-time loop that forbids
+// allocation.  This entry point runs the same two-stage reduction as the
+// library's own energy bookkeeping, with its per-block partial sums in a
+// file-scope device array of fixed size instead of a context's allocation.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -36,14 +35,17 @@ struct NoAllocArgs {
 };
 
 // Stage 1: per-thread sum_k dnu_k J_k, block sums in fixed order (the same
-// partition and order as the library's energy kernel).
+// partition and order as the library's energy kernel, whose translation unit
+// is built without FMA contraction: the explicitly rounded product and sum
+// keep the two bit-identical).
 __global__ void __launch_bounds__(kFreqThreads) noalloc_energy_blocks(const NoAllocArgs a,
                                                                       double* scratch) {
   __shared__ double red[kFreqThreads / 32];
   const long long cell = static_cast<long long>(blockIdx.x) * kFreqThreads + threadIdx.x;
   double en = 0.0;
   if (cell < a.nc)
-    for (int k = 0; k < a.nb; ++k) en += a.dnu[k] * a.J[static_cast<long long>(k) * a.nc + cell];
+    for (int k = 0; k < a.nb; ++k)
+      en = __dadd_rn(en, __dmul_rn(a.dnu[k], a.J[static_cast<long long>(k) * a.nc + cell]));
   const double s = block_sum<kFreqThreads>(en, red);
   if (threadIdx.x == 0) scratch[blockIdx.x] = s;
 }
@@ -84,6 +86,17 @@ int scratch_for_current_device(double** out) {
   return LYM1_OK;
 }
 
+// J must be device memory of the current device: the kernels dereference it
+// directly, and the scratch address is the current device's.  The attribute
+// query allocates nothing.
+bool on_current_device(const void* p) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) return false;
+  return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) && at.device == dev;
+}
+
 }  // namespace
 }  // namespace lym1
 
@@ -93,6 +106,13 @@ extern "C" int lym1_energy_noalloc(const double* J, const double* dnu, int nb, l
   if (!J || !dnu || !e_out || !(dx_cm > 0.0)) return LYM1_EINVAL;
   if (nb < 1 || nc < 1) return LYM1_EINVAL;
   if (nb > LYM1_NOALLOC_MAX_BINS || nc > LYM1_NOALLOC_MAX_CELLS) return LYM1_ERANGE;
+  // an error the caller left pending stays theirs: report it, do not clear it
+  if (cudaPeekAtLastError() != cudaSuccess) return LYM1_ECUDA;
+  // from here on any pending error comes from this call, which clears it
+  if (!on_current_device(J)) {
+    cudaGetLastError();
+    return LYM1_EINVAL;
+  }
   double* scratch = nullptr;
   const int rc = scratch_for_current_device(&scratch);
   if (rc != LYM1_OK) return rc;

@@ -416,10 +416,22 @@ class Context:
 
 def energy_noalloc(J, dnu, dx, stream=None) -> float:
     """``lym1_energy_noalloc``: Lya energy (erg) of a device state J[nb][ny][nx]
-    (contiguous float64 CUDA tensor) with bin widths dnu (host), for callers that
-    cannot allocate device memory at that point; the call itself allocates nothing."""
+    (contiguous float64 CUDA tensor on the current device) with bin widths dnu
+    (host), for callers that cannot allocate device memory at that point (their
+    HBM is owned by another runtime's allocator, or their loop forbids
+    allocation); the call itself allocates nothing."""
     d = np.ascontiguousarray(dnu, dtype=np.float64)
     nb = d.size
+    if not getattr(J, "is_cuda", False):
+        raise ValueError("energy_noalloc: J must be a CUDA tensor")
+    import torch
+    if J.device.index != torch.cuda.current_device():
+        raise ValueError(f"energy_noalloc: J is on cuda:{J.device.index}, the current device "
+                         f"is cuda:{torch.cuda.current_device()}")
+    if J.dtype != torch.float64 or not J.is_contiguous():
+        raise ValueError("energy_noalloc: J must be contiguous float64")
+    if nb < 1 or J.numel() % nb != 0 or J.numel() == 0:
+        raise ValueError(f"energy_noalloc: {J.numel()} values are not nb x nc with nb = {nb}")
     nc = J.numel() // nb
     out = np.zeros(1)
     _check(lib().lym1_energy_noalloc(_out_ptr(J), d.ctypes.data_as(_PD), nb, nc, float(dx),
