@@ -290,6 +290,20 @@ int lym1_debug_expire_wait(lym1_ctx *ctx);
  */
 int lym1_debug_fp64_helpers(const float *xf, const double *xd, long long n, double *wide,
                             float *narrow, double *rcp);
+
+/*
+ * Test hook for the FP64 helpers of the LYM1_MIXED kernels (no counterpart in
+ * the paper: GB300 runs FP64 arithmetic and FP32 <-> FP64 conversions on a
+ * pipe of ~1/70 of the FP32 rate, so those kernels convert on the integer
+ * pipe and refine a hardware reciprocal approximation by Newton-Raphson).
+ * For i < n (device pointers, caller-owned): wide[i] = xf[i] widened to FP64,
+ * narrow[i] = xd[i] narrowed to FP32 (round to nearest even), rcp[i] = 1 /
+ * xd[i]; both conversions flush subnormals to zero.  Runs on the legacy default
+ * stream and synchronises it.  LYM1_EINVAL for null pointers or n < 0;
+ * LYM1_ECUDA if the launch fails.
+ */
+int lym1_debug_fp64_helpers(const float *xf, const double *xd, long long n, double *wide,
+                            float *narrow, double *rcp);
 int lym1_profile_read(lym1_ctx *ctx, lym1_profile *out, int reset);
 
 /*

@@ -187,6 +187,8 @@ DeviceView make_view(const lym1_ctx* c, double dt) {
   v.freq_step = c->freq_step;
   v.tdiag = (!c->gray && c->freq_step) ? 0 : 1;
   v.gem_max = c->gem_max;
+  v.rcdt = 1.0 / v.cdt;
+  for (int k = 0; k < c->nb && !c->tab.gem.empty(); ++k) v.sg += c->tab.dnu[k] * c->tab.gem[k];
   v.acc = c->acc;
   v.status = c->status;
   v.f_H = c->f_H;

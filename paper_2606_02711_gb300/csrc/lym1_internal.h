@@ -125,6 +125,8 @@ struct DeviceView {
   // would otherwise divide in FP64 on every thread of every tile)
   double cdt_dx = 0, cdt_c = 0;
   double gem_max = 1;  // max_k gem_k (FP32 emissivity scaling)
+  double sg = 0;       // sum_k dnu_k gem_k (emission of a uniform-temperature cell per unit L c dt)
+  double rcdt = 0;     // 1 / (c_tilde dt)
   const double* acc = nullptr;  // running totals: [8] energy of the last substep, [13] energy unit
   int* status = nullptr;        // device status word: nonzero after a bounded wait expired
   // FP32 copies of the per-bin tables for the FP32 policies: <H>_k, dnu_k,

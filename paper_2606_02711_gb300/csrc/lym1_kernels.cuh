@@ -705,6 +705,61 @@ constexpr float kTinyJ = 1e-30f;
 // kActiveShare E / unit for the next one)
 constexpr double kActiveShare = 1e-8;
 
+// ------------------------------------------- FP64 on GB300's narrow FP64 pipe
+// GB300 issues FP64 arithmetic, and the FP32 <-> FP64 conversions, on a pipe
+// of about 1/70 of the FP32 rate (measured: 0.53 T DFMA/s against 37 T FFMA/s
+// per GPU; one conversion costs about one DFMA, an IEEE FP64 division about
+// nine).  The LYM1_MIXED policy keeps its implicit steps and its sums in FP64
+// and spends that pipe on them only:
+//  - conversions run on the integer pipe.  binary32 -> binary64 widening is
+//    exact: the exponent is rebiased by 1023 - 127 = 896 and the 23-bit
+//    significand moves up by 29 bits.  binary64 -> binary32 narrowing drops 29
+//    significand bits and rounds them to nearest, ties to even (a carry into
+//    the exponent is the correct rounding, up to infinity).  Both flush
+//    subnormal inputs and results to signed zero, like the -ftz FP32
+//    arithmetic of these kernels; infinities and NaN map to infinities and
+//    quiet NaN.
+//  - reciprocals: the hardware approximation rcp.approx.ftz.f64 refined by
+//    two Newton-Raphson steps y <- y + y (1 - x y), each of which squares the
+//    relative error (within one ulp of 1/x for normal x).
+__device__ __forceinline__ double f2d_alu(float x) {
+  const unsigned u = __float_as_uint(x);
+  const unsigned s = u & 0x80000000u, a = u & 0x7fffffffu;
+  unsigned hi = s | ((a >> 3) + 0x38000000u);
+  unsigned lo = u << 29;
+  if (a < 0x00800000u) {  // zero or subnormal: signed zero
+    hi = s;
+    lo = 0u;
+  } else if (a >= 0x7f800000u) {  // infinity, NaN
+    hi = s | (a > 0x7f800000u ? 0x7ff80000u : 0x7ff00000u);
+    lo = 0u;
+  }
+  return __hiloint2double(static_cast<int>(hi), static_cast<int>(lo));
+}
+
+__device__ __forceinline__ float d2f_alu(double x) {
+  const unsigned hi = static_cast<unsigned>(__double2hiint(x));
+  const unsigned lo = static_cast<unsigned>(__double2loint(x));
+  const unsigned s = hi & 0x80000000u, a = hi & 0x7fffffffu;
+  // biased binary64 exponent e = a >> 20; binary32 normals need 897 <= e <= 1150
+  unsigned f = ((a - 0x38000000u) << 3) | (lo >> 29);
+  const unsigned r = lo & 0x1fffffffu;  // the 29 dropped bits, half = 2^28
+  f += (r > 0x10000000u || (r == 0x10000000u && (f & 1u))) ? 1u : 0u;
+  if (a < 0x38100000u) f = 0u;  // below the binary32 normal range
+  if (a >= 0x47f00000u)         // beyond the binary32 range, infinity, NaN
+    f = (a > 0x7ff00000u || (a == 0x7ff00000u && lo != 0u)) ? 0x7fc00000u : 0x7f800000u;
+  return __uint_as_float(s | f);
+}
+
+__device__ __forceinline__ double drcp_nr(double x) {
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  double e = fma(-x, y, 1.0);
+  y = fma(y, e, y);
+  e = fma(-x, y, 1.0);
+  return fma(y, e, y);
+}
+
 // Levermore closure for FP32 from f = (fn, ft) and f2 = |f|^2.  With
 // s = sqrt(4 - 3 f2) (so f2 = (4 - s^2)/3) the printed chi reduces exactly to
 // chi = (5 - 2s)/3, hence
@@ -919,6 +974,19 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
   const float cdt_dx = float(v.cdt_dx);
   const I cdt = I(v.cdt), kabs = I(v.kabs), kF = I(v.kF), cdx = I(v.cdt_dx);
   const I wR = I(v.g_wR), wcol = I(wvf);
+  // LYM1_MIXED (FP64 implicit step): the per-cell factors with c_tilde dt
+  // folded in, c dt kappa_k = cA + cB <H>_k and c dt alpha_F,k = cD + cC <H>_k
+  // (bands: c dt kappa_k from their kappa table, alpha = 1, rho_d = 0)
+  constexpr bool MIX = sizeof(I) == 8;
+  double cA = 0.0, cB = 0.0, cC = 0.0, cD = 0.0, cjs = 0.0;
+  if constexpr (MIX) {
+    const double cd = v.cdt;
+    cA = cd * (double(rho_c) * v.kabs);
+    cB = cd * (double(pd_c) * double(alpha_c));
+    cC = cd * double(alpha_c);
+    cD = cd * (double(rho_c) * v.kF);
+    cjs = cd * lum_d;
+  }
   I ax = 0, ay = 0;
   // per-cell bookkeeping sums over the bins: FP64 (compensation-free, exact
   // enough at 194 terms) for LYM1_MIXED, plain FP32 for LYM1_MIXED_FAST; the
@@ -1062,52 +1130,80 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
       const float J1 = on ? J - cdt_f * (divJ * inv_dx + W * inv_c) : J;
       const float Hx1 = on ? Hx - cdt_dx * divHx : Hx;
       const float Hy1 = on ? Hy - cdt_dx * divHy : Hy;
-      I aH, dnu;
-      if constexpr (sizeof(I) == 8) {
-        aH = alpha_c * (TM ? double(Hcf[base + cell]) : v.t_H[k]);
-        dnu = v.t_dnu[k];
+      if constexpr (MIX) {
+        // FP64 implicit step (Sec. 2.1 step 2) with one shared reciprocal:
+        // r = 1 / (d1 d2) gives 1/d1 = d2 r and 1/d2 = d1 r, with
+        // d1 = 1 + c dt kappa_k and d2 = 1 + c dt alpha_F,k
+        const double Hd = TM ? f2d_alu(Hcf[base + cell]) : v.t_H[k];
+        const double dnud = v.t_dnu[k];
+        double ck;
+        if constexpr (TM == 2)
+          ck = v.cdt * f2d_alu(Kbf[base + cell]);
+        else
+          ck = fma(cB, Hd, cA);
+        const double caF = fma(cC, Hd, cD);
+        const double d1 = 1.0 + ck, d2 = 1.0 + caF;
+        const double rp = drcp_nr(d1 * d2);
+        const double ra = d1 * rp;
+        double num = f2d_alu(J1);
+        if (src) {
+          const double gk = TM ? gmax_c * f2d_alu(Gcf[base + cell]) : v.t_gem[k];
+          num = fma(cjs, gk, num);
+          if constexpr (TM != 0) em = fma(dnud, gk, em);
+        }
+        const double J2d = num * (d2 * rp);
+        const float J2 = d2f_alu(J2d);
+        // H'' = H' / d2 with the FP64 factor (H is FP32 state); the force term
+        // dnu_k (H' - H'') = dnu_k (c dt alpha_F / d2) H' has no cancellation
+        const float raf = d2f_alu(ra);
+        const float Hx2 = Hx1 * raf, Hy2 = Hy1 * raf;
+        (Jout + base)[cell32] = J2;
+        (Hxout + base)[cell32] = Hx2;
+        (Hyout + base)[cell32] = Hy2;
+        const float wq = d2f_alu(dnud * (caF * ra));
+        ax += f2d_alu(wq * Hx1);
+        ay += f2d_alu(wq * Hy1);
+        // A7 bookkeeping in FP64 (c_tilde dt is in ck; 1/c and the energy
+        // units once per substep)
+        ab = fma(dnud * ck, J2d, ab);
+        wk += f2d_alu(tb.y * W);
+        if (tdiag) {  // the frequency step recomputes these when it follows
+          en = fma(dnud, J2d, en);
+          const float h2 = Hx2 * Hx2 + Hy2 * Hy2, jj = J2 * J2;
+          if ((G == 1 ? J2 * wvf : J2) > tb.w) {
+            mxf2 = fmaxf(mxf2, fdiv(h2, jj));
+            bad += (h2 > jj * 1.000002f) ? 1 : 0;
+          }
+        }
       } else {
-        aH = alpha_c * (TM ? Hcf[base + cell] : Hk);
-        dnu = tb.y;
-      }
-      const I kap = (TM == 2) ? I(Kbf[base + cell]) : rho_c * kabs + pd_c * aH;
-      const I aF = aH + rho_c * kF;
-      I js;
-      if constexpr (sizeof(I) == 8)
-        js = src ? lum_d * (TM ? gmax_c * double(Gcf[base + cell]) : v.t_gem[k]) : 0.0;
-      else
-        js = src ? jsc * (TM ? Gcf[base + cell] : tb.z) : 0.0f;
-      I J2, Hx2, Hy2;
-      if constexpr (sizeof(I) == 8) {
-        J2 = (I(J1) + cdt * js) / (I(1) + cdt * kap);
-        const I ra = I(1) / (I(1) + cdt * aF);
-        Hx2 = I(Hx1) * ra;
-        Hy2 = I(Hy1) * ra;
-      } else {
-        J2 = (J1 + cdt * js) * frcp(1.0f + cdt * kap);
+        const float aH = alpha_c * (TM ? Hcf[base + cell] : Hk);
+        const float dnu = tb.y;
+        const float kap = (TM == 2) ? Kbf[base + cell] : rho_c * kabs + pd_c * aH;
+        const float aF = aH + rho_c * kF;
+        const float js = src ? jsc * (TM ? Gcf[base + cell] : tb.z) : 0.0f;
+        const float J2 = (J1 + cdt * js) * frcp(1.0f + cdt * kap);
         const float ra = frcp(1.0f + cdt * aF);
-        Hx2 = Hx1 * ra;
-        Hy2 = Hy1 * ra;
-      }
-      (Jout + base)[cell32] = float(J2);
-      (Hxout + base)[cell32] = float(Hx2);
-      (Hyout + base)[cell32] = float(Hy2);
-      ax += dnu * (I(Hx1) - Hx2);
-      ay += dnu * (I(Hy1) - Hy2);
-      // A7 bookkeeping (energy units applied once per substep; the factors
-      // c_tilde dt and 1/c once per cell after the bin loop)
-      if (src) em += dnu * js;
-      ab += dnu * (kap * J2);
-      wk += dnu * I(W);
-      if (tdiag) {  // the frequency step recomputes these when it follows
-        en += dnu * J2;
-        const float j2f = float(J2), h2 = float(Hx2) * float(Hx2) + float(Hy2) * float(Hy2);
-        const float jj = j2f * j2f;
-        if ((G == 1 ? j2f * wvf : j2f) > tb.w) {
-          mxf2 = fmaxf(mxf2, fdiv(h2, jj));
-          bad += (h2 > jj * 1.000002f) ? 1 : 0;
+        const float Hx2 = Hx1 * ra, Hy2 = Hy1 * ra;
+        (Jout + base)[cell32] = J2;
+        (Hxout + base)[cell32] = Hx2;
+        (Hyout + base)[cell32] = Hy2;
+        ax += dnu * (Hx1 - Hx2);
+        ay += dnu * (Hy1 - Hy2);
+        // A7 bookkeeping (energy units applied once per substep; the factors
+        // c_tilde dt and 1/c once per cell after the bin loop)
+        if (src) em += dnu * js;
+        ab += dnu * (kap * J2);
+        wk += dnu * W;
+        if (tdiag) {  // the frequency step recomputes these when it follows
+          en += dnu * J2;
+          const float h2 = Hx2 * Hx2 + Hy2 * Hy2, jj = J2 * J2;
+          if ((G == 1 ? J2 * wvf : J2) > tb.w) {
+            mxf2 = fmaxf(mxf2, fdiv(h2, jj));
+            bad += (h2 > jj * 1.000002f) ? 1 : 0;
+          }
         }
       }
+      const I dnu = MIX ? I(v.t_dnu[k]) : I(tb.y);
       if (bnd) {
         I o2 = 0;
         if constexpr (G == 1) {
@@ -1180,10 +1276,12 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
       }
     }
   } else {
+    // FP64 sums (LYM1_MIXED): c_tilde dt is already in ab; the emission of a
+    // uniform-temperature cell is c dt L_cell sum_k dnu_k gem_k
     const double wd = G == 1 ? double(wvf) : 1.0;
-    s = block_sum<NT>(double(em) * (v.cdt * wd), red);
+    s = block_sum<NT>((cjs * (TM ? double(em) : v.sg)) * wd, red);
     if (tid == 0) part[kSlotEmitted] = s;
-    s = block_sum<NT>(double(ab) * (v.cdt * wd), red);
+    s = block_sum<NT>(double(ab) * wd, red);
     if (tid == 0) part[kSlotAbsorbed] = s;
     s = block_sum<NT>(double(out), red);
     if (tid == 0) part[kSlotOutflow] = s;
@@ -1200,13 +1298,58 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
   }
 }
 
+// blocks per SM the FP32 tile is register-budgeted for: 3 (80 registers);
+// LYM1_MIXED's FP64 step holds more live values and is bound by the FP64
+// pipe, not by latency, so it takes 2 blocks of up to 128 registers
+template <class P>
+__host__ __device__ constexpr int tile_f32_min_blocks() {
+  return sizeof(typename P::I) == 8 ? 2 : 3;
+}
+
 template <class P, int G, int PT>
-__global__ void __launch_bounds__(kTileX* kTileY, 3) transport_kernel_f32(DeviceView v) {
+__global__ void __launch_bounds__(kTileX* kTileY, tile_f32_min_blocks<P>()) transport_kernel_f32(DeviceView v) {
   transport_tile_f32<P, G, PT>(v, blockIdx.x * kTileX, blockIdx.y * kTileY,
                            blockIdx.y * gridDim.x + blockIdx.x);
 }
 
 // ------------------------------------------------------------ frequency kernel
+// LYM1_MIXED (FP32 state and coefficients, FP64 elimination): the
+// elimination's conversions run on the integer pipe and its reciprocals are
+// Newton-refined hardware approximations; the H rescale, the causality cap and
+// the realisability check stay in the FP32 of the state.
+template <class P>
+__host__ __device__ constexpr bool freq_mix() {
+  return sizeof(typename P::S) == 4 && sizeof(typename P::I) == 8;
+}
+template <class P>
+__device__ __forceinline__ typename P::I to_elim(typename P::F x) {
+  if constexpr (freq_mix<P>()) return f2d_alu(x);
+  else return typename P::I(x);
+}
+template <class P>
+__device__ __forceinline__ typename P::S to_state(typename P::I x) {
+  if constexpr (freq_mix<P>()) return d2f_alu(x);
+  else return typename P::S(x);
+}
+template <class P>
+__device__ __forceinline__ typename P::I rcp_elim(typename P::I x) {
+  using I = typename P::I;
+  if constexpr (sizeof(I) == 4) return frcp(x);
+  else if constexpr (freq_mix<P>()) return drcp_nr(x);
+  else return I(1) / x;
+}
+// The causality cap and the FP32 realisability statistics (max |H|^2 / J^2
+// and the count of |H| > J) of the (cell, bin) pairs whose weighted J is above thr
+__device__ __forceinline__ void causal_stats_f32(float J, float& Hx, float& Hy, float wf, float thr,
+                                                 float& mxf2, int& bad) {
+  causal(J, Hx, Hy);
+  if (J * wf > thr) {
+    const float h2 = Hx * Hx + Hy * Hy, jj = J * J;
+    mxf2 = fmaxf(mxf2, fdiv(h2, jj));
+    bad += (h2 > jj * 1.000002f) ? 1 : 0;
+  }
+}
+
 // Coefficients of bin k for one cell (App. A): Peclet number P_k, dlt_k/K_k and
 // E(-|P_k|) = expm1(-|P_k|) / (-|P_k|), with D_k from the post-source state.
 template <class P, int G, class T>
@@ -1293,9 +1436,13 @@ __device__ __forceinline__ void freq_block(const DeviceView& v, int blk) {
   const int nb = v.nb;
   // per-bin tables, freq_smem_per_bin<P>() bytes a bin: two in the elimination
   // type I, then five in the coefficient type T
+  constexpr bool MIX = freq_mix<P>();
   I* tdi = reinterpret_cast<I*>(tabs_raw);  // dnu_k in the elimination type
   I* tact = tdi + nb;                       // J above which |H|/J is checked
-  T* tabs = reinterpret_cast<T*>(tact + nb);
+  // LYM1_MIXED: the threshold in FP32, and dnu_k / (c dt) in FP64
+  float* tactf = reinterpret_cast<float*>(tact);
+  I* tsk = MIX ? tact + nb : nullptr;
+  T* tabs = reinterpret_cast<T*>(MIX ? tsk + nb : tact + nb);
   T* tH = tabs;
   T* tR = tabs + nb;
   T* tn = tabs + 2 * nb;
@@ -1304,7 +1451,12 @@ __device__ __forceinline__ void freq_block(const DeviceView& v, int blk) {
   if constexpr (sizeof(F) == 4) {
     const float thr = float(v.acc[14]);
     for (int i = threadIdx.x; i < nb; i += NT) {
-      tact[i] = I(fmaxf(thr, 1e-30f) / v.f_dnu[i]);
+      if constexpr (MIX) {
+        tactf[i] = fmaxf(thr, 1e-30f) / v.f_dnu[i];
+        tsk[i] = v.t_dnu[i] * v.rcdt;
+      } else {
+        tact[i] = I(fmaxf(thr, 1e-30f) / v.f_dnu[i]);
+      }
       tH[i] = v.f_H[i];
       tR[i] = v.f_R[i];
       tn[i] = v.f_nbc[i];
@@ -1338,12 +1490,14 @@ __device__ __forceinline__ void freq_block(const DeviceView& v, int blk) {
   const long long cell = static_cast<long long>(blk) * NT + threadIdx.x;
   RSum<I> en;
   I mxf = 0;
+  float mxf2 = 0.0f;  // LYM1_MIXED: max |H|^2 / J^2
   int bad = 0;
   // axisymmetric grid: energy weight 2 pi Vol / dx^3 of the cell's column
   double wcell = 1.0;
   if constexpr (G == 1)
     if (cell < nc) wcell = v.g_wv[cell % v.nx];
   const I wI = I(wcell);
+  const float wf = float(wcell);
   if (cell < nc) {
     const double alpha = v.alpha[cell];
     if (v.freq_step && alpha > 0.0) {
@@ -1372,7 +1526,7 @@ __device__ __forceinline__ void freq_block(const DeviceView& v, int blk) {
       const float rcdt = float(1.0 / v.cdt);
       (void)rcdt;
       F P0, a0, e0, P1 = F(0), a1 = F(0), e1 = F(0);
-      I Jin0 = I(Jin[cell]);
+      I Jin0 = to_elim<P>(F(Jin[cell]));
       I Jin1 = 0;
       freq_coef<P, G>(F(Jin[cell]), F(Hxin[cell]), F(Hyin[cell]), Kc, gxx, gyy, gsh, gphi, H0, R0,
                       tn, th, 0, P0, a0, e0);
@@ -1395,7 +1549,7 @@ __device__ __forceinline__ void freq_block(const DeviceView& v, int blk) {
             nX = Hxin[o2];
             nY = Hyin[o2];
           }
-          Jin1 = I(Jr);
+          Jin1 = to_elim<P>(F(Jr));
           F H1, R1;
           HR(k + 1, H1, R1);
           freq_coef<P, G>(F(Jr), F(Xr), F(Yr), Kc, gxx, gyy, gsh, gphi, H1, R1, tn, th, k + 1, P1,
@@ -1406,8 +1560,8 @@ __device__ __forceinline__ void freq_block(const DeviceView& v, int blk) {
           const F den = m_exp<P::DET>(d1 - m) * (e0 * a0) + m_exp<P::DET>(d2 - m) * (e1 * a1);
           if constexpr (sizeof(F) == 4) {
             const float rden = frcp(den);
-            A = I(m_exp<P::DET>(-P0 - m) * rden);
-            B = I(m_exp<P::DET>(P1 - m) * rden);
+            A = to_elim<P>(m_exp<P::DET>(-P0 - m) * rden);
+            B = to_elim<P>(m_exp<P::DET>(P1 - m) * rden);
           } else if constexpr (P::DET) {
             A = I(m_exp<P::DET>(-P0 - m) / den);
             B = I(m_exp<P::DET>(P1 - m) / den);
@@ -1417,10 +1571,11 @@ __device__ __forceinline__ void freq_block(const DeviceView& v, int blk) {
             B = I(m_exp<P::DET>(P1 - m) * rden);
           }
         }
-        I s, inv_dummy = 0;
-        (void)inv_dummy;
+        I s;
         if constexpr (sizeof(I) == 4)
           s = tdi[k] * rcdt;
+        else if constexpr (MIX)
+          s = tsk[k];
         else if constexpr (P::DET)
           s = tdi[k] / cdt;
         else
@@ -1428,11 +1583,7 @@ __device__ __forceinline__ void freq_block(const DeviceView& v, int blk) {
         const I E = (k == 0) ? s : s + Bprev * qprev;
         const I r = (k == 0) ? s * Jin0 : s * Jin0 + Aprev * gprev;
         const I Dp = E + A;
-        I inv;
-        if constexpr (sizeof(I) == 4)
-          inv = frcp(Dp);
-        else
-          inv = I(1) / Dp;
+        const I inv = rcp_elim<P>(Dp);
         const I g = r * inv;
         const I h = B * inv;
         qprev = E * inv;
@@ -1440,8 +1591,8 @@ __device__ __forceinline__ void freq_block(const DeviceView& v, int blk) {
         Bprev = B;
         Aprev = A;
         const long long o = static_cast<long long>(k) * nc + cell;
-        Jout[o] = S(g);
-        Hxout[o] = S(h);
+        Jout[o] = to_state<P>(g);
+        Hxout[o] = to_state<P>(h);
         P0 = P1;
         a0 = a1;
         e0 = e1;
@@ -1460,6 +1611,20 @@ __device__ __forceinline__ void freq_block(const DeviceView& v, int blk) {
           cJ = Jin[o];
           cX = Hxin[o];
           cY = Hyin[o];
+        }
+        if constexpr (MIX) {
+          const double g = f2d_alu(gS), h = f2d_alu(hS);
+          const double Jn = (k == nb - 1) ? g : fma(h, Jnext, g);
+          Jnext = Jn;
+          const float Jnf = d2f_alu(Jn);
+          const float ratio = JS > kTinyJ ? fdiv(Jnf, JS) : 0.0f;
+          float Hx2 = ratio * XS, Hy2 = ratio * YS;
+          causal_stats_f32(Jnf, Hx2, Hy2, G == 1 ? wf : 1.0f, tactf[k], mxf2, bad);
+          Jout[oc] = Jnf;
+          Hxout[oc] = Hx2;
+          Hyout[oc] = Hy2;
+          en.add(tdi[k] * Jn);
+          continue;
         }
         const I g = I(gS), h = I(hS);
         const I Jn = (k == nb - 1) ? g : g + h * Jnext;
@@ -1487,6 +1652,15 @@ __device__ __forceinline__ void freq_block(const DeviceView& v, int blk) {
       for (int k = 0; k < nb; ++k) {
         const long long o = static_cast<long long>(k) * nc + cell;
         const S J = Jin[o];
+        if constexpr (MIX) {
+          float Hxi = Hxin[o], Hyi = Hyin[o];
+          causal_stats_f32(J, Hxi, Hyi, G == 1 ? wf : 1.0f, tactf[k], mxf2, bad);
+          Jout[o] = J;
+          Hxout[o] = Hxi;
+          Hyout[o] = Hyi;
+          en.add(tdi[k] * f2d_alu(J));
+          continue;
+        }
         const I Ji = I(J);
         I Hxi = I(Hxin[o]), Hyi = I(Hyin[o]);
         causal(Ji, Hxi, Hyi);
@@ -1506,7 +1680,7 @@ __device__ __forceinline__ void freq_block(const DeviceView& v, int blk) {
   double s;
   s = block_sum<NT>(en.value() * wcell, red);
   if (threadIdx.x == 0) part[kSlotEnergy] = s;
-  s = block_max<NT>(double(mxf), red);
+  s = block_max<NT>(MIX ? double(sqrtf(mxf2)) : double(mxf), red);
   if (threadIdx.x == 0) part[kSlotMaxF] = s;
   s = block_sum<NT>(double(bad), red);
   if (threadIdx.x == 0) part[kSlotBad] = s;
@@ -1591,9 +1765,12 @@ __device__ __forceinline__ void freq_block_bulk(const DeviceView& v, int blk) {
   __shared__ double red[NT / 32];
   extern __shared__ double tabs_raw[];
   const int nb = v.nb;
+  constexpr bool MIX = freq_mix<P>();
   I* tdi = reinterpret_cast<I*>(tabs_raw);  // same layout as freq_block
   I* tact = tdi + nb;
-  T* tabs = reinterpret_cast<T*>(tact + nb);
+  float* tactf = reinterpret_cast<float*>(tact);
+  I* tsk = MIX ? tact + nb : nullptr;
+  T* tabs = reinterpret_cast<T*>(MIX ? tsk + nb : tact + nb);
   T* tH = tabs;
   T* tR = tabs + nb;
   T* tn = tabs + 2 * nb;
@@ -1609,7 +1786,12 @@ __device__ __forceinline__ void freq_block_bulk(const DeviceView& v, int blk) {
       tdi[i] = v.f_dnu[i];
     else
       tdi[i] = v.t_dnu[i];
-    tact[i] = I(fmaxf(thr, 1e-30f) / v.f_dnu[i]);
+    if constexpr (MIX) {
+      tactf[i] = fmaxf(thr, 1e-30f) / v.f_dnu[i];
+      tsk[i] = v.t_dnu[i] * v.rcdt;
+    } else {
+      tact[i] = I(fmaxf(thr, 1e-30f) / v.f_dnu[i]);
+    }
   }
   if (tid == 0) {
     for (int s = 0; s < D; ++s) {
@@ -1712,22 +1894,20 @@ __device__ __forceinline__ void freq_block_bulk(const DeviceView& v, int blk) {
         const F m = (d1 > d2) ? d1 : d2;
         const F den = m_exp<P::DET>(d1 - m) * (ep * ap) + m_exp<P::DET>(d2 - m) * (ek * ak);
         const float rden = frcp(den);
-        const I A = I(m_exp<P::DET>(-Pp - m) * rden);
-        const I B = I(m_exp<P::DET>(Pk - m) * rden);
+        const I A = to_elim<P>(m_exp<P::DET>(-Pp - m) * rden);
+        const I B = to_elim<P>(m_exp<P::DET>(Pk - m) * rden);
         // row k-1
         I sk;
         if constexpr (sizeof(I) == 4)
           sk = tdi[k - 1] * rcdt;
+        else if constexpr (MIX)
+          sk = tsk[k - 1];
         else
           sk = tdi[k - 1] / cdt;
         const I E = (k == 1) ? sk : sk + Bprev * qprev;
         const I r = (k == 1) ? sk * Jp : sk * Jp + Aprev * gprev;
         const I Dp = E + A;
-        I inv;
-        if constexpr (sizeof(I) == 4)
-          inv = frcp(Dp);
-        else
-          inv = I(1) / Dp;
+        const I inv = rcp_elim<P>(Dp);
         const I g = r * inv;
         const I h = B * inv;
         qprev = E * inv;
@@ -1735,13 +1915,13 @@ __device__ __forceinline__ void freq_block_bulk(const DeviceView& v, int blk) {
         Bprev = B;
         Aprev = A;
         const long long o = ofw;
-        Jout[o] = float(g);
-        Hxout[o] = float(h);
+        Jout[o] = to_state<P>(g);
+        Hxout[o] = to_state<P>(h);
       }
       Pp = Pk;
       ap = ak;
       ep = ek;
-      Jp = I(Jc);
+      Jp = to_elim<P>(Jc);
     }
     if (__syncthreads_or(okF ? 0 : 1)) {  // stage s consumed (or a wait ran out)
       give_up(barF, nb < k + D ? nb : k + D, k);
@@ -1753,17 +1933,15 @@ __device__ __forceinline__ void freq_block_bulk(const DeviceView& v, int blk) {
     I sk;
     if constexpr (sizeof(I) == 4)
       sk = tdi[nb - 1] * rcdt;
+    else if constexpr (MIX)
+      sk = tsk[nb - 1];
     else
       sk = tdi[nb - 1] / cdt;
     const I E = (nb == 1) ? sk : sk + Bprev * qprev;
     const I r = (nb == 1) ? sk * Jp : sk * Jp + Aprev * gprev;
-    I inv;
-    if constexpr (sizeof(I) == 4)
-      inv = frcp(E);
-    else
-      inv = I(1) / E;
+    const I inv = rcp_elim<P>(E);
     const long long o = static_cast<long long>(nb - 1) * nc + cell;
-    Jout[o] = float(r * inv);
+    Jout[o] = to_state<P>(r * inv);
     Hxout[o] = 0.0f;
   }
   // the elimination factors go back through the async proxy
@@ -1773,8 +1951,10 @@ __device__ __forceinline__ void freq_block_bulk(const DeviceView& v, int blk) {
     for (int j = 0; j < nb && j < D; ++j) issue_bwd(j);
   RSum<I> en;
   I mxf = 0;
+  float mxf2 = 0.0f;  // LYM1_MIXED: max |H|^2 / J^2
   int bad = 0;
   I Jnext = 0;
+  const float wf = G == 1 ? float(wcell) : 1.0f;
   long long obw = static_cast<long long>(nb - 1) * nc + cell;  // plane offset of row k
   for (int j = 0; j < nb; ++j, obw -= nc) {
     const int s = j % D, k = nb - 1 - j;
@@ -1782,7 +1962,26 @@ __device__ __forceinline__ void freq_block_bulk(const DeviceView& v, int blk) {
     if (valid && okB) {
       const long long o = obw;
       const float Jo = ring[s][2][tid], Xo = ring[s][3][tid], Yo = ring[s][4][tid];
-      if (act) {
+      if (MIX && act) {
+        const double g = f2d_alu(ring[s][0][tid]), h = f2d_alu(ring[s][1][tid]);
+        const double Jn = (j == 0) ? g : fma(h, double(Jnext), g);
+        Jnext = I(Jn);
+        const float Jnf = d2f_alu(Jn);
+        const float ratio = Jo > kTinyJ ? fdiv(Jnf, Jo) : 0.0f;
+        float Hx2 = ratio * Xo, Hy2 = ratio * Yo;
+        causal_stats_f32(Jnf, Hx2, Hy2, wf, tactf[k], mxf2, bad);
+        Jout[o] = Jnf;
+        Hxout[o] = Hx2;
+        Hyout[o] = Hy2;
+        en.add(I(tdi[k] * Jn));
+      } else if (MIX) {
+        float Hxi = Xo, Hyi = Yo;
+        causal_stats_f32(Jo, Hxi, Hyi, wf, tactf[k], mxf2, bad);
+        Jout[o] = Jo;
+        Hxout[o] = Hxi;
+        Hyout[o] = Hyi;
+        en.add(I(tdi[k] * f2d_alu(Jo)));
+      } else if (act) {
         const I g = I(ring[s][0][tid]), h = I(ring[s][1][tid]);
         const I Jn = (j == 0) ? g : g + h * Jnext;
         Jnext = Jn;
@@ -1827,7 +2026,7 @@ __device__ __forceinline__ void freq_block_bulk(const DeviceView& v, int blk) {
   double sres;
   sres = block_sum<NT>(en.value() * wcell, red);
   if (tid == 0) part[kSlotEnergy] = sres;
-  sres = block_max<NT>(double(mxf), red);
+  sres = block_max<NT>(MIX ? double(sqrtf(mxf2)) : double(mxf), red);
   if (tid == 0) part[kSlotMaxF] = sres;
   sres = block_sum<NT>(double(bad), red);
   if (tid == 0) part[kSlotBad] = sres;
@@ -1875,7 +2074,7 @@ __global__ void __launch_bounds__(kTileX* kTileY) transport_batched(const Device
 }
 
 template <class P, int G, int PT>
-__global__ void __launch_bounds__(kTileX* kTileY, 3) transport_batched_f32(const DeviceView* views,
+__global__ void __launch_bounds__(kTileX* kTileY, tile_f32_min_blocks<P>()) transport_batched_f32(const DeviceView* views,
                                                                            const BatchItem* items,
                                                                            int n) {
   for (int i = blockIdx.x; i < n; i += gridDim.x) {
