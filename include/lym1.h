@@ -209,6 +209,19 @@ int lym1_diagnostics(lym1_ctx *ctx, lym1_diag *out);
 /* Static facts about the context. */
 int lym1_get_info(lym1_ctx *ctx, lym1_info *out);
 
+/*
+ * Device bytes that lym1_create will allocate for a Lya context on this grid
+ * with these groups and precision (temp_field != 0: with a per-cell
+ * temperature field), computed on the host from the same allocation list:
+ * equal to lym1_info.device_bytes of that context right after creation.  Not
+ * included: buffers made on demand later (lym1_spectrum_enable,
+ * lym1_set_pruning) and the persistent graph-replayed batch of lym1_substeps
+ * (a few kB).  For admission control by a device-memory budget (serving).
+ * LYM1_EINVAL for invalid sizes, groups or precision.  No CUDA call.
+ */
+int lym1_plan_bytes(const lym1_grid *grid, const lym1_groups *groups, int precision, int temp_field,
+                    double *bytes);
+
 /* Per-bin tables (host buffers of nb doubles, any may be NULL): bin width
  * dnu_k, absolute centre frequency nubar_k, bin-averaged Voigt <H>_k and the
  * emissivity factor w_k / (4 pi dx^3 dnu_k). */
@@ -231,11 +244,14 @@ int lym1_run_to_steady(lym1_ctx *ctx, double tol, int check_every, int max_subst
  * Batches: several contexts (clouds of different sizes, luminosities and
  * densities) advanced together.  Each substep of a batch is three launches in
  * total -- one persistent transport kernel over a work list of every
- * context's 32x8 tiles, one persistent frequency-step kernel over every
+ * context's 16x16 tiles, one persistent frequency-step kernel over every
  * context's cell blocks and one reduction kernel with a block per context --
  * captured once in a CUDA graph and replayed.  The persistent grid size is
  * tuned on the batch's first substeps (each candidate times one substep; the
- * choice does not change any result).  Every context advances with its own
+ * choice does not change any result) and kept in a process-wide cache keyed
+ * by device, precision, geometry, table mode, bin count and the power of two
+ * of the batch's tile count: a later batch of the same class starts tuned
+ * and skips those substeps.  Every context advances with its own
  * dt_RT and its own bookkeeping, exactly as with lym1_substeps.
  * The contexts must share precision, bin count and stream, and not be gray;
  * otherwise LYM1_EINVAL.  A batch holds device pointers of its contexts:
@@ -244,7 +260,8 @@ int lym1_run_to_steady(lym1_ctx *ctx, double tol, int check_every, int max_subst
 typedef struct lym1_batch lym1_batch;
 int lym1_batch_create(lym1_ctx *const *ctxs, int n_ctx, lym1_batch **out);
 int lym1_batch_substeps(lym1_batch *batch, int n);
-/* persistent grid sizes in use (0 until tuned) */
+/* persistent grid sizes in use (0 until tuned; set at creation when the
+ * tuned-grid cache holds the batch's class) */
 int lym1_batch_grid(lym1_batch *batch, int *transport_blocks, int *freq_blocks);
 void lym1_batch_destroy(lym1_batch *batch);
 
@@ -276,20 +293,6 @@ int lym1_profile_enable(lym1_ctx *ctx, int on);
  * otherwise).
  */
 int lym1_debug_expire_wait(lym1_ctx *ctx);
-
-/*
- * Test hook for the FP64 helpers of the LYM1_MIXED kernels (no counterpart in
- * the paper: GB300 runs FP64 arithmetic and FP32 <-> FP64 conversions on a
- * pipe of ~1/70 of the FP32 rate, so those kernels convert on the integer
- * pipe and refine a hardware reciprocal approximation by Newton-Raphson).
- * For i < n (device pointers, caller-owned): wide[i] = xf[i] widened to FP64,
- * narrow[i] = xd[i] narrowed to FP32 (round to nearest even), rcp[i] = 1 /
- * xd[i]; both conversions flush subnormals to zero.  Runs on the legacy default
- * stream and synchronises it.  LYM1_EINVAL for null pointers or n < 0;
- * LYM1_ECUDA if the launch fails.
- */
-int lym1_debug_fp64_helpers(const float *xf, const double *xd, long long n, double *wide,
-                            float *narrow, double *rcp);
 
 /*
  * Test hook for the FP64 helpers of the LYM1_MIXED kernels (no counterpart in

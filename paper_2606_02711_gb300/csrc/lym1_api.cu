@@ -6,6 +6,8 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <utility>
 #include <vector>
@@ -404,6 +406,28 @@ int bands_upload(lym1_ctx* c, const double* aF, const double* kap, const double*
   return LYM1_OK;
 }
 
+// Device bytes of a context's creation-time allocations, by the same list and
+// the same rounding (an empty allocation takes 16 bytes) as create_impl:
+// mode 0 uniform temperature, 1 temperature field, 2 broad bands.  Buffers
+// made on demand later (spectrum, pruning, the persistent batch) are not in it.
+double plan_context_bytes(long long nx, long long ny, long long nb, size_t selem, int mode,
+                          int geometry) {
+  auto a = [](double b) { return b > 0.0 ? b : 16.0; };
+  const double plane = static_cast<double>(nx) * static_cast<double>(ny);
+  const double nstate = plane * static_cast<double>(nb), ncol = static_cast<double>(nx);
+  const double tb = static_cast<double>(transport_blocks(static_cast<int>(nx), static_cast<int>(ny)));
+  const double fb = static_cast<double>(freq_blocks(static_cast<long long>(plane)));
+  double t = 6.0 * a(nstate * selem) + 12.0 * a(plane * 8) + 6.0 * a(nb * 8.0);
+  t += a(tb * kDiagSlots * 8) + a(fb * kDiagSlots * 8) + a(16 * 8) + a(2.0 * kForceBlocks * 8);
+  t += a(4 * sizeof(int)) + a(2 * sizeof(unsigned long long)) + a(kSumWork * 8) + 6.0 * a(nb * 4.0);
+  if (mode == 2) t += 3.0 * a(nstate * selem) + 2.0 * a(plane * 8);
+  if (mode == 1) t += 2.0 * a(nstate * selem) + 6.0 * a(plane * 8) + a(nb * 8.0) + a(nb * 4.0);
+  if (geometry == 1)
+    t += a(plane * 8) + 3.0 * a((ncol + 1) * 8) + 5.0 * a(ncol * 8) + 2.0 * a((ncol + 1) * 4) +
+         4.0 * a(ncol * 4);
+  return t;
+}
+
 void drop_events(lym1_ctx* c) {
   for (cudaEvent_t e : c->ev_start) cudaEventDestroy(e);
   for (cudaEvent_t e : c->ev_stop) cudaEventDestroy(e);
@@ -430,11 +454,31 @@ struct lym1_batch {
   std::vector<int> candT, candF;
   std::vector<float> timeT;
   int tuned = 0;
+  // class of this batch in the process-wide cache of tuned grids: device,
+  // precision, geometry, transport mode, bins, log2 of the tile count
+  std::vector<long long> tune_key;
   cudaGraphExec_t exec = nullptr;
   cudaGraph_t graph = nullptr;
 };
 
 namespace {
+
+// Tuned persistent grids shared by every batch of the same class, so that a
+// new batch (a new mix of clouds in the serving loop) skips the timed tuning
+// substeps when a batch of its class was tuned before on this device.
+std::mutex g_tune_mutex;
+std::map<std::vector<long long>, int> g_tune_cache;
+
+int tuned_grid_lookup(const std::vector<long long>& key) {
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  const auto it = g_tune_cache.find(key);
+  return it == g_tune_cache.end() ? 0 : it->second;
+}
+
+void tuned_grid_store(const std::vector<long long>& key, int grid) {
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  g_tune_cache[key] = grid;
+}
 
 // the two views of a context in a batch: the transport step reads A and
 // writes B, the frequency step reads B and writes A
@@ -1055,6 +1099,30 @@ int lym1_get_info(lym1_ctx* c, lym1_info* o) {
   return LYM1_OK;
 }
 
+int lym1_plan_bytes(const lym1_grid* grid, const lym1_groups* groups, int precision,
+                    int temp_field, double* bytes) {
+  if (!grid || !groups || !bytes) return LYM1_EINVAL;
+  if (grid->nx < 1 || grid->ny < 1 || (grid->geometry != 0 && grid->geometry != 1)) return LYM1_EINVAL;
+  if (precision < 0 || precision > 3) return LYM1_EINVAL;
+  if (static_cast<long long>(grid->nx) * grid->ny > (1LL << 31)) return LYM1_EINVAL;
+  int nb = 0;
+  if (groups->edges_dnu_hz) {
+    if (groups->n_bins < 1 || groups->n_bins > LYM1_MAX_BINS) return LYM1_EINVAL;
+    nb = groups->n_bins;
+  } else {
+    const double q = groups->q > 0.0 ? groups->q : 1.1;
+    const double Tm = groups->T_min > 0.0 ? groups->T_min : 30.0;
+    if (!(q > 1.0)) return LYM1_EINVAL;
+    std::vector<double> edges;
+    nb = paper_frequency_grid(Tm, q, &edges);
+    if (nb < 1 || nb > LYM1_MAX_BINS) return LYM1_EINVAL;
+  }
+  if (groups->gray) nb = 1;
+  *bytes = plan_context_bytes(grid->nx, grid->ny, nb, precision >= LYM1_MIXED ? 4 : 8,
+                              temp_field ? 1 : 0, grid->geometry);
+  return LYM1_OK;
+}
+
 int lym1_tables(lym1_ctx* c, double* dnu, double* nubar, double* Havg, double* gem) {
   if (!c) return LYM1_EINVAL;
   for (int k = 0; k < c->nb; ++k) {
@@ -1191,6 +1259,13 @@ int lym1_batch_create(lym1_ctx* const* ctxs, int n_ctx, lym1_batch** out) {
   b->candF.push_back(gf);
   b->gridT = b->candT.back();
   b->gridF = gf;
+  int lg = 0;
+  while ((2LL << lg) <= b->nT) ++lg;
+  b->tune_key = {dev, b->precision, b->geometry, b->tpt, b->nb, lg};
+  if (const int g = tuned_grid_lookup(b->tune_key)) {
+    b->gridT = std::min(g, b->nT);
+    b->tuned = 1;
+  }
   *out = b;
   return LYM1_OK;
 }
@@ -1228,6 +1303,7 @@ int lym1_batch_substeps(lym1_batch* b, int n) {
         if (b->timeT[k] < b->timeT[best]) best = k;
       b->gridT = b->candT[best];
       b->tuned = 1;
+      tuned_grid_store(b->tune_key, b->gridT);
     }
   }
   if (done < n) {

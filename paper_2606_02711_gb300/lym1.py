@@ -102,6 +102,8 @@ SIGNATURES = {
     "lym1_force": (C.c_int, [C.c_void_p, _PD, _PD]),
     "lym1_diagnostics": (C.c_int, [C.c_void_p, C.POINTER(lym1_diag)]),
     "lym1_get_info": (C.c_int, [C.c_void_p, C.POINTER(lym1_info)]),
+    "lym1_plan_bytes": (C.c_int, [C.POINTER(lym1_grid), C.POINTER(lym1_groups), C.c_int, C.c_int,
+                                  _PD]),
     "lym1_tables": (C.c_int, [C.c_void_p, _PD, _PD, _PD, _PD]),
     "lym1_synchronize": (C.c_int, [C.c_void_p]),
     "lym1_run_to_steady": (C.c_int, [C.c_void_p, C.c_double, C.c_int, C.c_int,
@@ -414,6 +416,26 @@ class Context:
             return False, n.value
         _check(st, "lym1_run_to_steady")
         return True, n.value
+
+
+def plan_bytes(nx, ny, precision, *, geometry=0, edges=None, q=0.0, T_min=0.0, gray=False,
+               temp_field=False) -> float:
+    """``lym1_plan_bytes``: device bytes a Lya context of this shape will
+    allocate at creation (no CUDA call)."""
+    if isinstance(precision, str):
+        precision = PRECISIONS[precision]
+    g = lym1_grid(int(nx), int(ny), 1.0, int(geometry), (C.c_int * 4)(0, 0, 0, 0))
+    keep = None
+    if edges is not None:
+        keep = np.ascontiguousarray(edges, dtype=np.float64)
+        gr = lym1_groups(keep.size - 1, keep.ctypes.data_as(_PD), float(q), float(T_min), int(gray))
+    else:
+        gr = lym1_groups(0, None, float(q), float(T_min), int(gray))
+    out = C.c_double()
+    _check(lib().lym1_plan_bytes(C.byref(g), C.byref(gr), int(precision), int(bool(temp_field)),
+                                 C.byref(out)), "lym1_plan_bytes")
+    del keep
+    return out.value
 
 
 def energy_noalloc(J, dnu, dx, stream=None) -> float:

@@ -4,7 +4,7 @@ backend whose energy relaxes as E_n = 1 - exp(-n / tau) -- no GPU."""
 import math
 
 
-from paper_2606_02711_gb300.serve import Request, Server, shard, state_bytes, summarize
+from paper_2606_02711_gb300.serve import Request, Server, shard, summarize
 
 
 class FakeCloud:
@@ -19,8 +19,8 @@ class FakeBackend:
         self.open_count = 0
         self.batches = []
 
-    def bins(self):
-        return 194
+    def bytes_for(self, cloud):
+        return 6 * 194 * cloud.nx * cloud.ny * 4 + 12 * cloud.nx * cloud.ny * 8
 
     def open(self, cloud):
         self.open_count += 1
@@ -71,7 +71,7 @@ def test_steady_state_rule_and_cap():
 def test_admission_respects_budget_and_slots():
     be, clk = FakeBackend(), FakeClock()
     cloud = FakeCloud(256, 256, 200.0)
-    per = state_bytes(cloud, 194, 3)
+    per = be.bytes_for(cloud)
     reqs = [Request(i, 0.0, cloud) for i in range(6)]
     srv = Server(be, hbm_budget=2.5 * per, max_active=8, check_every=50, tol=1e-5)
     res = srv.run(reqs, clock=clk, sleep=clk.sleep)

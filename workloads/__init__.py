@@ -202,16 +202,17 @@ def config_lognormal_2048(seed=1):
                            name="lognormal-2048", substeps=5000)
 
 
-def batch_clouds(n=256, base_seed=1000, side_lo=64, side_hi=512):
+def batch_clouds(n=256, base_seed=1000, side_lo=64, side_hi=512, nh_lo=1e2, nh_hi=1e5):
     """Independent clouds for a batched sweep: side log-uniform in
     [side_lo, side_hi] rounded to a multiple of 16, mean n_H log-uniform
-    [1e2, 1e5], L log-uniform [1e4, 1e7] L_sun, Z in {0, 1e-3, 1e-2} Z_sun."""
+    [nh_lo, nh_hi] (default [1e2, 1e5]), L log-uniform [1e4, 1e7] L_sun,
+    Z in {0, 1e-3, 1e-2} Z_sun."""
     g = rng(base_seed)
     out = []
     for i in range(n):
         side = int(round(math.exp(g.uniform(math.log(side_lo), math.log(side_hi))) / 16.0)) * 16
         side = max(16, side)
-        mean = 10 ** g.uniform(2, 5)
+        mean = 10 ** g.uniform(math.log10(nh_lo), math.log10(nh_hi))
         L = 10 ** g.uniform(4, 7)
         Z = (0.0, 1e-3, 1e-2)[int(g.integers(0, 3))]
         out.append(lognormal_cloud(side, side, mean_nh=mean, sigma_ln=1.0, Z=Z, L_sun=L,
@@ -302,3 +303,38 @@ def two_phase_temperature(nx, ny, seed, T_cold=100.0, T_hot=1.0e4, frac_hot=0.5,
     else:
         s = (g > t).astype(float)
     return np.exp(np.log(T_cold) + s * (np.log(T_hot) - np.log(T_cold)))
+
+
+def populated_state(cloud, nb, seed=11, ell_cells=24.0, f_out=0.4, x_peak=12.0, x_width=8.0,
+                    J0=1e-12):
+    """A smooth, realisable radiation state [nb][ny][nx] (J, Hx, Hy) shaped like the
+    field around a central source, for tests that must not start from zero.
+
+    Spectrum: a double peak in the bin index offset from line centre (the bins are
+    ordered from the blue wing to the red wing, symmetric about nb/2), peaks at
+    x_peak bins from the centre with width x_width, plus a 1e-6 floor.  Space: J
+    falls as (1 + r/ell)^-2 from the box centre, modulated by 1 + 0.3 g with g a
+    seeded smooth field in [-1, 1].  Flux: f = f_out tanh(r/ell) r_hat plus a
+    seeded smooth perturbation of 0.2, capped at |f| = 0.95.  Only shapes are
+    drawn here; no step of the method is computed."""
+    nx, ny = cloud.nx, cloud.ny
+    x = np.arange(nx) + 0.5 - 0.5 * nx
+    y = np.arange(ny) + 0.5 - 0.5 * ny
+    X, Y = np.meshgrid(x, y)
+    r = np.sqrt(X * X + Y * Y)
+    g = gaussian_field(nx, ny, seed)
+    g = np.tanh(g)
+    space = (1.0 + r / ell_cells) ** -2 * (1.0 + 0.3 * g)
+    kk = np.arange(nb) + 0.5 - 0.5 * nb
+    spec = np.exp(-((np.abs(kk) - x_peak) / x_width) ** 2) + 1e-6
+    J = J0 * spec[:, None, None] * space[None, :, :]
+    rs = np.maximum(r, 1e-12)
+    fr = f_out * np.tanh(r / ell_cells)
+    p1 = 0.2 * np.tanh(gaussian_field(nx, ny, seed + 1))
+    p2 = 0.2 * np.tanh(gaussian_field(nx, ny, seed + 2))
+    fx = fr * X / rs + p1
+    fy = fr * Y / rs + p2
+    fm = np.sqrt(fx * fx + fy * fy)
+    sc = np.where(fm > 0.95, 0.95 / np.maximum(fm, 1e-300), 1.0)
+    fx, fy = fx * sc, fy * sc
+    return J, J * fx[None], J * fy[None]
