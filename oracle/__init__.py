@@ -51,7 +51,7 @@ class Problem(C.Structure):
                 ("edges", _PD), ("n_hi", _PD), ("rho_d", _PD), ("p_d", _PD),
                 ("ux", _PD), ("uy", _PD), ("lum", _PD), ("geometry", C.c_int),
                 ("bc", C.c_int * 4), ("temp", _PD), ("band_aF", _PD), ("band_kap", _PD),
-                ("band_j", _PD), ("prune", C.c_double)]
+                ("band_j", _PD), ("prune", C.c_double), ("accept", C.c_int)]
 
 
 class Diag(C.Structure):
@@ -106,6 +106,7 @@ def lib():
                                     C.POINTER(Diag)]
         L.lym1o_set_threads.argtypes = [C.c_int]
         L.lym1o_set_spectrum.argtypes = [C.c_void_p, _PD]
+        L.lym1o_set_subcycle_out.argtypes = [C.c_void_p, C.POINTER(C.c_int)]
         L.lym1o_set_ctilde.argtypes = [C.c_void_p, _D]
         L.lym1o_dynamic_ctilde.restype = _D
         L.lym1o_dynamic_ctilde.argtypes = [C.c_void_p, _PD, _D, _D]
@@ -212,7 +213,7 @@ class Oracle:
     def __init__(self, *, nx, ny, dx, edges, T, n_hi, rho_d, p_d, ux, uy, lum,
                  kappa_abs=0.0, kappa_F=0.0, c_tilde=2.99792458e10, cfl=0.4,
                  gray=False, recoil=True, freq_step=True, geometry=0, bc=(0, 0, 0, 0),
-                 temp=None, bands=None, prune=0.0):
+                 temp=None, bands=None, prune=0.0, accept=False):
         bd = None
         if bands is not None:
             # (alpha_F, kappa, emissivity), each [n_bands][ny][nx]
@@ -234,7 +235,7 @@ class Oracle:
                             _p(lum), int(geometry), (C.c_int * 4)(*[int(b) for b in bc]),
                             _p(tp) if tp is not None else None,
                             *([_p(a) for a in bd] if bd is not None else [None, None, None]),
-                            float(prune))
+                            float(prune), int(bool(accept)))
         self.ctx = lib().lym1o_create(C.byref(self.prob))
         if not self.ctx:
             raise ValueError("invalid oracle problem")
@@ -304,6 +305,16 @@ class Oracle:
         else:
             lib().lym1o_set_spectrum(self.ctx, None)
             self.spectrum = None
+
+    def subcycle_on(self, on: bool = True):
+        """Record, per cell, the accepted step-2 substeps of each substep in
+        self.nsub (only with accept=True)."""
+        if on:
+            self.nsub = np.zeros((self.ny, self.nx), dtype=np.int32)
+            lib().lym1o_set_subcycle_out(self.ctx, self.nsub.ctypes.data_as(C.POINTER(C.c_int)))
+        else:
+            lib().lym1o_set_subcycle_out(self.ctx, None)
+            self.nsub = None
 
     def substep(self, J, Hx, Hy, dt=None):
         """Advance one substep; returns (J, Hx, Hy, fx, fy, diag dict)."""

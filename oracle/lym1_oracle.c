@@ -361,6 +361,17 @@ typedef struct {
      * substep; the other bins skip step 1 (fluxes, advection, work and hoop
      * terms) and still take steps 2 and 3.  0: every bin is advected. */
     double prune;
+    /* Substep acceptance of step 2 (Sec. 2.1 step 2 and its footnote): 0 takes
+     * one implicit emission/absorption update over dt (the default); 1
+     * subcycles it per cell.  A trial substep of a cell is accepted when its
+     * Lya energy density changes by |e'' - e'| / (e' + e_floor) < 0.1, with
+     * e_floor = 4 pi J_floor / c and J_floor = 1e-15 erg cm^-2 s^-1 sr^-1;
+     * otherwise the substep is halved and redone, until the accepted
+     * substeps fill dt.  Readings (the paper gives the halving only): every
+     * cell starts with the whole dt; after an accepted substep the next trial
+     * doubles it (capped by what is left of dt); substeps are whole multiples
+     * of dt / 2^40, and one of that size is accepted whatever the change. */
+    int accept;
 } lym1o_problem;
 
 typedef struct {
@@ -393,6 +404,9 @@ typedef struct {
      * per [bin][outer face], faces ordered x- (j), x+ (j), y- (i), y+ (i) for
      * geometry 0 and R outer (j), Z outer (i) for geometry 1 */
     double *spec;
+    /* accepted step-2 substeps of each cell in the last substep (NULL: not
+     * recorded); only with p.accept */
+    int *nsub;
 } lym1o_ctx;
 
 static int o_cl(int i, int n) { return i < 0 ? 0 : (i >= n ? n - 1 : i); }
@@ -432,6 +446,8 @@ lym1o_ctx *lym1o_create(const lym1o_problem *p)
     for (int s = 0; s < 4; ++s)
         if (p->bc[s] != 0 && p->bc[s] != 1) return NULL;
     if (p->band_aF && (!p->band_kap || !p->band_j || p->gray || p->temp)) return NULL;
+    /* the acceptance rule watches the Lya energy density: not for broad bands */
+    if (p->accept != 0 && (p->accept != 1 || p->band_aF)) return NULL;
     lym1o_ctx *c = (lym1o_ctx *)calloc(1, sizeof *c);
     c->p = *p;
     if (p->band_aF) c->p.freq_step = 0;
@@ -975,6 +991,71 @@ static void o_freq_of_cell(const lym1o_ctx *c, size_t id, size_t nc, const doubl
                 scr);
 }
 
+/* Step 2 of one cell with the substep acceptance rule (Sec. 2.1 step 2, see
+ * lym1o_problem.accept), in place on the cell's post-transport state
+ * (Jo, Hxo, Hyo).  Each accepted substep of length h is the printed implicit
+ * update J'' = (J' + c h j)/(1 + c h kappa), H'' = H'/(1 + c h alpha_F); the
+ * force sum dnu (H' - H''), the emission dnu c h j and the absorption
+ * dnu c h kappa J'' add up over the accepted substeps.  vol weights the
+ * emission and absorption (1 for geometry 0, the ring volume 2 pi Vol for
+ * geometry 1); jfac turns the cell's emission factor into j (lum for geometry
+ * 0, lum / (2 pi Vol) for geometry 1). */
+#define O_SUB_LEVELS 40
+#define O_J_FLOOR 1e-15
+static int o_step2_subcycle(const lym1o_ctx *c, size_t id, size_t nc, double dt, double jfac,
+                            int cyl, double *Jo, double *Hxo, double *Hyo, double *ax, double *ay,
+                            double *em, double *ab)
+{
+    const lym1o_problem *p = &c->p;
+    const int nb = c->nb;
+    const long long full = 1LL << O_SUB_LEVELS;
+    long long done = 0, size = full;
+    int n = 0;
+    double e_cur = 0.0;
+    for (int k = 0; k < nb; ++k) e_cur = e_cur + c->dnu[k] * Jo[(size_t)k * nc + id];
+    while (done < full) {
+        if (size > full - done) size = full - done;
+        const double h = dt * ((double)size / (double)full);
+        const double ch = p->c_tilde * h;
+        /* trial: the energy density after this substep (in units of 4 pi / c) */
+        double e_new = 0.0;
+        for (int k = 0; k < nb; ++k) {
+            const double aH = c->alpha[id] * HAV(k, id);
+            const double kap = p->rho_d[id] * p->kappa_abs + p->p_d[id] * aH;
+            const double js = jfac * (cyl ? GEMC(k, id) : GEMK(k, id));
+            const double Jt = (Jo[(size_t)k * nc + id] + ch * js) / (1.0 + ch * kap);
+            e_new = e_new + c->dnu[k] * Jt;
+        }
+        const double change = fabs(e_new - e_cur) / (e_cur + O_J_FLOOR);
+        if (!(change < 0.1) && size > 1) {
+            size = size / 2;
+            continue;
+        }
+        for (int k = 0; k < nb; ++k) {
+            const size_t kid = (size_t)k * nc + id;
+            const double aH = c->alpha[id] * HAV(k, id);
+            const double kap = p->rho_d[id] * p->kappa_abs + p->p_d[id] * aH;
+            const double aF = aH + p->rho_d[id] * p->kappa_F;
+            const double js = jfac * (cyl ? GEMC(k, id) : GEMK(k, id));
+            const double J2 = (Jo[kid] + ch * js) / (1.0 + ch * kap);
+            const double Hx2 = Hxo[kid] / (1.0 + ch * aF);
+            const double Hy2 = Hyo[kid] / (1.0 + ch * aF);
+            ax[id] = ax[id] + c->dnu[k] * (Hxo[kid] - Hx2);
+            ay[id] = ay[id] + c->dnu[k] * (Hyo[kid] - Hy2);
+            em[id] = em[id] + c->dnu[k] * (ch * js);
+            ab[id] = ab[id] + c->dnu[k] * (ch * (kap * J2));
+            Jo[kid] = J2;
+            Hxo[kid] = Hx2;
+            Hyo[kid] = Hy2;
+        }
+        e_cur = e_new;
+        done += size;
+        ++n;
+        size = size * 2;
+    }
+    return n;
+}
+
 int lym1o_substep(const lym1o_ctx *c, double dt, const double *J, const double *Hx,
                   const double *Hy, double *Jo, double *Hxo, double *Hyo, double *fx,
                   double *fy, lym1o_diag *dg)
@@ -1086,6 +1167,12 @@ int lym1o_substep(const lym1o_ctx *c, double dt, const double *J, const double *
                     aF = BND(band_aF, k, id);
                     js = BND(band_j, k, id);
                 }
+                if (p->accept) { /* step 2 is subcycled per cell after the bin loop */
+                    Jo[kid] = J1;
+                    Hxo[kid] = Hx1;
+                    Hyo[kid] = Hy1;
+                    continue;
+                }
                 double J2 = (J1 + cdt * js) / (1.0 + cdt * kap);
                 double Hx2 = Hx1 / (1.0 + cdt * aF);
                 double Hy2 = Hy1 / (1.0 + cdt * aF);
@@ -1105,8 +1192,10 @@ int lym1o_substep(const lym1o_ctx *c, double dt, const double *J, const double *
                 kap = BND(band_kap, k, id);
                 js = BND(band_j, k, id);
             }
-            o_kadd(&s_em, c->dnu[k] * (cdt * js));
-            o_kadd(&s_ab, c->dnu[k] * (cdt * (kap * Jo[kid])));
+            if (!p->accept) {
+                o_kadd(&s_em, c->dnu[k] * (cdt * js));
+                o_kadd(&s_ab, c->dnu[k] * (cdt * (kap * Jo[kid])));
+            }
             o_kadd(&s_wk, c->dnu[k] * (cdt * (Wk[id] / O_C)));
         }
         const int nf = 2 * (nx + ny);
@@ -1131,6 +1220,21 @@ int lym1o_substep(const lym1o_ctx *c, double dt, const double *J, const double *
             }
         }
 #undef AF
+    }
+    if (p->accept) { /* A4 subcycled per cell (Sec. 2.1 step 2, acceptance rule) */
+        double *em = calloc(nc, sizeof(double)), *ab = calloc(nc, sizeof(double));
+#pragma omp parallel for schedule(static)
+        for (long long idl = 0; idl < (long long)nc; ++idl) {
+            const size_t id = (size_t)idl;
+            const int n = o_step2_subcycle(c, id, nc, dt, p->lum[id], 0, Jo, Hxo, Hyo, ax, ay, em, ab);
+            if (c->nsub) c->nsub[id] = n;
+        }
+        for (size_t id = 0; id < nc; ++id) {
+            o_kadd(&s_em, em[id]);
+            o_kadd(&s_ab, ab[id]);
+        }
+        free(em);
+        free(ab);
     }
     /* A5: f = 4 pi / (c ct dt) sum_k dnu_k (H' - H'') */
     const double fcoef = (4.0 * O_PI) / ((O_C * p->c_tilde) * dt);
@@ -1356,6 +1460,12 @@ int lym1o_substep_cyl(const lym1o_ctx *c, double dt, const double *J, const doub
                     aF = BND(band_aF, k, id);
                     js = BND(band_j, k, id);
                 }
+                if (p->accept) { /* step 2 is subcycled per cell after the bin loop */
+                    Jo[kid] = J1;
+                    Hxo[kid] = Hx1;
+                    Hyo[kid] = Hy1;
+                    continue;
+                }
                 double J2 = (J1 + cdt * js) / (1.0 + cdt * kap);
                 double Hx2 = Hx1 / (1.0 + cdt * aF);
                 double Hy2 = Hy1 / (1.0 + cdt * aF);
@@ -1375,8 +1485,10 @@ int lym1o_substep_cyl(const lym1o_ctx *c, double dt, const double *J, const doub
                 kap = BND(band_kap, k, id);
                 js = BND(band_j, k, id);
             }
-            o_kadd(&s_em, c->V2pi[i] * (c->dnu[k] * (cdt * js)));
-            o_kadd(&s_ab, c->V2pi[i] * (c->dnu[k] * (cdt * (kap * Jo[kid]))));
+            if (!p->accept) {
+                o_kadd(&s_em, c->V2pi[i] * (c->dnu[k] * (cdt * js)));
+                o_kadd(&s_ab, c->V2pi[i] * (c->dnu[k] * (cdt * (kap * Jo[kid]))));
+            }
             o_kadd(&s_wk, c->V2pi[i] * (c->dnu[k] * (cdt * (Wk[id] / O_C))));
         }
         /* outflow through the outer R and Z faces (the axis and midplane are mirrors) */
@@ -1392,6 +1504,23 @@ int lym1o_substep_cyl(const lym1o_ctx *c, double dt, const double *J, const doub
             if (c->spec) c->spec[(size_t)k * nf + ny + i] = ((4.0 * O_PI) / O_C) * o;
         }
 #undef AFC
+    }
+    if (p->accept) { /* A4 subcycled per cell (Sec. 2.1 step 2, acceptance rule) */
+        double *em = calloc(nc, sizeof(double)), *ab = calloc(nc, sizeof(double));
+#pragma omp parallel for schedule(static)
+        for (long long idl = 0; idl < (long long)nc; ++idl) {
+            const size_t id = (size_t)idl;
+            const int i = (int)(id % nx);
+            const int n = o_step2_subcycle(c, id, nc, dt, p->lum[id] / c->V2pi[i], 1, Jo, Hxo, Hyo,
+                                           ax, ay, em, ab);
+            if (c->nsub) c->nsub[id] = n;
+        }
+        for (size_t id = 0; id < nc; ++id) {
+            o_kadd(&s_em, c->V2pi[id % nx] * em[id]);
+            o_kadd(&s_ab, c->V2pi[id % nx] * ab[id]);
+        }
+        free(em);
+        free(ab);
     }
     const double fcoef = (4.0 * O_PI) / ((O_C * p->c_tilde) * dt);
     for (size_t id = 0; id < nc; ++id) {
@@ -1533,6 +1662,7 @@ double lym1o_dynamic_ctilde(lym1o_ctx *c, const double *cs, double eps_rsl, doub
 /* emergent spectrum output of the following substeps (NULL: off); buf holds
  * nb x (2 (nx + ny)) doubles for geometry 0, nb x (nx + ny) for geometry 1 */
 void lym1o_set_spectrum(lym1o_ctx *c, double *buf) { c->spec = buf; }
+void lym1o_set_subcycle_out(lym1o_ctx *c, int *buf) { c->nsub = buf; }
 
 void lym1o_set_threads(int n)
 {
