@@ -263,6 +263,28 @@ int lym1_batch_substeps(lym1_batch *batch, int n);
 /* persistent grid sizes in use (0 until tuned; set at creation when the
  * tuned-grid cache holds the batch's class) */
 int lym1_batch_grid(lym1_batch *batch, int *transport_blocks, int *freq_blocks);
+/*
+ * Tile-shape autotuning of the batched transport.  Besides the persistent grid
+ * size, the tuner times the transport's work layouts (no counterpart in the
+ * paper, which loops over bins on CPU threads): 16 x 16 tiles (the only one
+ * of LYM1_FP64_DET batches, so that they equal solo runs bit for bit), 32 x 8
+ * tiles (plain table modes, no pruning or acceptance rule), and the bins of
+ * each 16 x 16 tile split over 2, 4 or 8 blocks when the tiles alone do not
+ * fill the GPU (small clouds; at least 16 bins a block; the groups' force
+ * sums are added in group order by the frequency step).  A layout changes
+ * only the summation order of the force and of the transport's bookkeeping,
+ * not J or H.  The winner is cached with the grid (see above).
+ * lym1_batch_config reports the layout and grids in use (all 0 until tuned):
+ * tile width and height, bin groups, transport and frequency-step grids.
+ * lym1_batch_configure fixes a layout instead of tuning it: tile_shape 0 =
+ * 16 x 16, 1 = 32 x 8 (LYM1_EINVAL with pruning, broad bands or the
+ * acceptance rule); bin_groups 1, 2, 4 or 8 (at most the bin count); grid_t
+ * persistent transport blocks (0 = all resident).  Call it outside stream
+ * capture; it synchronises the batch's stream and drops the captured graph.
+ */
+int lym1_batch_config(lym1_batch *batch, int *tile_x, int *tile_y, int *bin_groups,
+                      int *transport_blocks, int *freq_blocks);
+int lym1_batch_configure(lym1_batch *batch, int tile_shape, int bin_groups, int transport_blocks);
 void lym1_batch_destroy(lym1_batch *batch);
 
 /* One-shot batch: create, run n substeps, destroy. */
@@ -345,6 +367,27 @@ int lym1_profile_read(lym1_ctx *ctx, lym1_profile *out, int reset);
 #define LYM1_NOALLOC_MAX_BINS 1024
 int lym1_energy_noalloc(const double *J, const double *dnu, int nb, long long nc, double dx_cm,
                         double *e_out, void *cuda_stream);
+
+/*
+ * Substep acceptance rule of step 2 (Sec. 2.1 step 2 and its footnote), off
+ * by default.  With on = 1 every cell subcycles its implicit emission/
+ * absorption update: a trial substep is accepted when the cell's Lya energy
+ * density changes by |e'' - e'| / (e' + e_floor) < 0.1 (e_floor =
+ * 4 pi J_floor / c, J_floor = 1e-15 erg cm^-2 s^-1 sr^-1); otherwise it is
+ * halved and redone until the accepted substeps fill dt_RT.  Where the paper
+ * gives only the halving: each cell starts with the whole dt_RT, an accepted
+ * substep doubles the next trial (capped by what is left), substeps are whole
+ * multiples of dt_RT / 2^40 and one of that size is accepted whatever the
+ * change, and after 2^16 trials in a substep every further trial is accepted
+ * (a bound on the loop).  The force, emission and absorption add up over the
+ * accepted substeps; the frequency step follows with dt_RT.  The transport
+ * then leaves step 2 to one extra kernel (one thread per cell, a pass over
+ * the bins per trial), so a substep costs more where cells subcycle.
+ * Lya contexts only (LYM1_EINVAL for broad bands and on other than 0 or 1).
+ * A change rebuilds the graph-replayed path; batches made before it refuse to
+ * run (LYM1_EINVAL); all contexts of a batch share the setting.
+ */
+int lym1_set_accept(lym1_ctx *ctx, int on);
 
 /*
  * Emergent spectrum (Sec. 4: the spectra of photons leaving the domain, Test 6

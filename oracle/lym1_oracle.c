@@ -370,7 +370,9 @@ typedef struct {
      * substeps fill dt.  Readings (the paper gives the halving only): every
      * cell starts with the whole dt; after an accepted substep the next trial
      * doubles it (capped by what is left of dt); substeps are whole multiples
-     * of dt / 2^40, and one of that size is accepted whatever the change. */
+     * of dt / 2^40, one of that size is accepted whatever the change, and
+     * after 2^16 trials in one substep every further trial is accepted (a
+     * bound on the loop that finite inputs do not reach). */
     int accept;
 } lym1o_problem;
 
@@ -1001,6 +1003,7 @@ static void o_freq_of_cell(const lym1o_ctx *c, size_t id, size_t nc, const doubl
  * geometry 1); jfac turns the cell's emission factor into j (lum for geometry
  * 0, lum / (2 pi Vol) for geometry 1). */
 #define O_SUB_LEVELS 40
+#define O_SUB_MAX_TRIALS 65536
 #define O_J_FLOOR 1e-15
 static int o_step2_subcycle(const lym1o_ctx *c, size_t id, size_t nc, double dt, double jfac,
                             int cyl, double *Jo, double *Hxo, double *Hyo, double *ax, double *ay,
@@ -1010,13 +1013,14 @@ static int o_step2_subcycle(const lym1o_ctx *c, size_t id, size_t nc, double dt,
     const int nb = c->nb;
     const long long full = 1LL << O_SUB_LEVELS;
     long long done = 0, size = full;
-    int n = 0;
+    int n = 0, trials = 0;
     double e_cur = 0.0;
     for (int k = 0; k < nb; ++k) e_cur = e_cur + c->dnu[k] * Jo[(size_t)k * nc + id];
     while (done < full) {
         if (size > full - done) size = full - done;
         const double h = dt * ((double)size / (double)full);
         const double ch = p->c_tilde * h;
+        ++trials;
         /* trial: the energy density after this substep (in units of 4 pi / c) */
         double e_new = 0.0;
         for (int k = 0; k < nb; ++k) {
@@ -1027,7 +1031,7 @@ static int o_step2_subcycle(const lym1o_ctx *c, size_t id, size_t nc, double dt,
             e_new = e_new + c->dnu[k] * Jt;
         }
         const double change = fabs(e_new - e_cur) / (e_cur + O_J_FLOOR);
-        if (!(change < 0.1) && size > 1) {
+        if (!(change < 0.1) && size > 1 && trials <= O_SUB_MAX_TRIALS) {
             size = size / 2;
             continue;
         }

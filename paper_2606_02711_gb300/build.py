@@ -1,10 +1,11 @@
 """Builds liblym1.so (the CUDA library behind include/lym1.h) in-tree for sm_103a.
 
-Four translation units compiled in parallel, then linked:
+Translation units compiled in parallel, then linked:
   csrc/lym1_tables.cpp        host per-bin tables (g++, no FMA contraction)
   csrc/lym1_api.cu            C ABI host code
   csrc/lym1_kernels_det.cu    FP64 fixed-order kernels (-fmad=false)
-  csrc/lym1_kernels_fast.cu   FP64 / mixed kernels
+  csrc/lym1_kernels_fast.cu   dispatch to the FP64 / mixed policies
+  csrc/lym1_pol_*.cu          every kernel of one of those policies (one unit each)
   csrc/lym1_noalloc.cu        allocation-free energy reduction
 """
 from __future__ import annotations
@@ -23,8 +24,10 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 
 SOURCES = ["lym1_tables.cpp", "lym1_api.cu", "lym1_kernels_det.cu", "lym1_kernels_fast.cu",
-           "lym1_noalloc.cu"]
-HEADERS = ["lym1_internal.h", "lym1_kernels.cuh"]
+           "lym1_pol_f64.cu", "lym1_pol_mix.cu", "lym1_pol_mixf.cu", "lym1_noalloc.cu"]
+HEADERS = ["lym1_internal.h", "lym1_kernels.cuh", "lym1_policies.h", "lym1_pol_unit.cuh"]
+# FMA contraction, FP32 flush-to-zero and approximate FP32 divide/sqrt
+FAST_UNITS = ("lym1_kernels_fast.cu", "lym1_pol_f64.cu", "lym1_pol_mix.cu", "lym1_pol_mixf.cu")
 
 
 def _cmd(src: str) -> list[str]:
@@ -38,7 +41,7 @@ def _cmd(src: str) -> list[str]:
            "-Xcompiler", "-ffp-contract=off", *inc, "-c", path, "-o", obj]
     if src == "lym1_kernels_det.cu":
         cmd.insert(1, "-fmad=false")
-    if src == "lym1_kernels_fast.cu":
+    if src in FAST_UNITS:
         # FP32 policies: flush subnormals, approximate FP32 divide/sqrt (FP64
         # arithmetic is not affected by these flags)
         cmd[1:1] = ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"]

@@ -51,6 +51,10 @@ struct lym1_ctx {
   double* Ebin = nullptr;
   unsigned char* active = nullptr;
   unsigned prune_gen = 0;
+  // substep acceptance rule of step 2 (lym1_set_accept); accept_gen changes
+  // with it
+  int accept = 0;
+  unsigned accept_gen = 0;
   long long substeps_done = 0;
   cudaStream_t stream = nullptr;
   BinTables tab;
@@ -87,9 +91,10 @@ namespace {
 
 constexpr int kForceBlocks = 152 * 4;
 
-// host mirror of the kernels' BatchItem {ctx, x0, y0, blk}
+// host mirror of the kernels' BatchItem {ctx, x0, y0, blk, k0, k1, grp}
 struct BatchItemHost {
   int ctx, x0, y0, blk;
+  int k0, k1, grp;
 };
 
 int map_cuda(cudaError_t e) {
@@ -190,7 +195,6 @@ DeviceView make_view(const lym1_ctx* c, double dt) {
   v.tdiag = (!c->gray && c->freq_step) ? 0 : 1;
   v.gem_max = c->gem_max;
   v.rcdt = 1.0 / v.cdt;
-  for (int k = 0; k < c->nb && !c->tab.gem.empty(); ++k) v.sg += c->tab.dnu[k] * c->tab.gem[k];
   v.acc = c->acc;
   v.status = c->status;
   v.f_H = c->f_H;
@@ -204,8 +208,11 @@ DeviceView make_view(const lym1_ctx* c, double dt) {
   v.spec = c->spec_on ? c->spec : nullptr;
   v.spec_unit = (4.0 * kPi) / kLight;
   v.nf = c->geometry == 1 ? (c->nx + c->ny) : 2 * (c->nx + c->ny);
-  // table mode, with bit 4 for the transport's active-bin pruning variant
-  v.pt = c->pt | (c->prune > 0.0 ? 4 : 0);
+  // table mode, with bit 4 for the transport's active-bin pruning variant and
+  // bit 8 for its variant that leaves step 2 to the acceptance rule's kernel
+  v.pt = c->pt | (c->prune > 0.0 ? 4 : 0) | (c->accept ? 8 : 0);
+  v.ct = c->c_tilde;
+  v.dt = dt;
   v.Hc = c->Hc;
   v.Gc = c->Gc;
   v.Kb = c->Kb;
@@ -326,14 +333,22 @@ int one_substep(lym1_ctx* c, double dt) {
       LYM1_TRYK(launch_transport_fast(c->precision, v, c->stream));
   }
   const bool freq = !c->gray && c->freq_step;
+  DeviceView w = v;  // the frequency step and the acceptance rule read B
+  w.J = c->B[0];
+  w.Hx = c->B[1];
+  w.Hy = c->B[2];
+  w.Jo = c->A[0];
+  w.Hxo = c->A[1];
+  w.Hyo = c->A[2];
+  if (c->accept) {  // step 2 subcycled per cell, in place on B
+    KernelTimer t(c, 1);
+    if (c->precision == LYM1_FP64_DET)
+      LYM1_TRYK(launch_subcycle_det(w, c->stream));
+    else
+      LYM1_TRYK(launch_subcycle_fast(c->precision, w, c->stream));
+  }
+  const int fmode = c->accept ? 2 : 0;
   if (freq) {
-    DeviceView w = v;  // B -> A
-    w.J = c->B[0];
-    w.Hx = c->B[1];
-    w.Hy = c->B[2];
-    w.Jo = c->A[0];
-    w.Hxo = c->A[1];
-    w.Hyo = c->A[2];
     {
       KernelTimer t(c, 1);
       if (c->precision == LYM1_FP64_DET)
@@ -343,12 +358,18 @@ int one_substep(lym1_ctx* c, double dt) {
     }
     KernelTimer t(c, 2);
     LYM1_TRYK(launch_finalize(c->partT, transport_blocks(c->nx, c->ny), c->partF,
-                              freq_blocks(c->nc), c->acc, 0, c->stream));
+                              freq_blocks(c->nc), c->acc, fmode, c->stream));
   } else {
     for (int i = 0; i < 3; ++i) std::swap(c->A[i], c->B[i]);
     KernelTimer t(c, 2);
-    LYM1_TRYK(launch_finalize(c->partT, transport_blocks(c->nx, c->ny), c->partT,
-                              transport_blocks(c->nx, c->ny), c->acc, 0, c->stream));
+    // without a frequency step the energy comes from the transport, or from
+    // the acceptance rule's kernel when it ran
+    if (c->accept)
+      LYM1_TRYK(launch_finalize(c->partT, transport_blocks(c->nx, c->ny), c->partF,
+                                freq_blocks(c->nc), c->acc, fmode, c->stream));
+    else
+      LYM1_TRYK(launch_finalize(c->partT, transport_blocks(c->nx, c->ny), c->partT,
+                                transport_blocks(c->nx, c->ny), c->acc, 0, c->stream));
   }
   c->substeps_done += 1;
   return LYM1_OK;
@@ -438,23 +459,43 @@ void drop_events(lym1_ctx* c) {
 
 }  // namespace
 
+// One work layout of a batch's transport launch: the tile shape (TileShape)
+// and the number of blocks the bins of each tile are split over, with its
+// work items, the views that carry it and the finalize jobs.
+struct BatchLayout {
+  int shape = 0, groups = 1, nT = 0;
+  void* itemsT = nullptr;
+  DeviceView *viewsT = nullptr, *viewsF = nullptr;
+  FinalizeJob* jobs = nullptr;
+  int rT = 1;  // transport blocks resident per SM
+};
+
 struct lym1_batch {
   std::vector<lym1_ctx*> ctxs;
-  int precision = 0, nb = 0, nT = 0, nF = 0, geometry = 0, pt = 0;
-  int tpt = 0;  // the transport's mode: pt, with bit 4 if a context prunes
+  int precision = 0, nb = 0, nF = 0, geometry = 0, pt = 0;
+  int tpt = 0;  // the transport's mode: pt, with bit 4 if a context prunes, 8 under the acceptance rule
+  int accept = 0;  // the contexts subcycle step 2 (acceptance rule)
+  int gridS = 0;   // persistent grid of the acceptance rule's kernel
+  int nsm = 1, dev = 0;
   cudaStream_t ctx_stream = nullptr, bs = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr, t0 = nullptr, t1 = nullptr;
-  DeviceView *viewsT = nullptr, *viewsF = nullptr;
-  void *itemsT = nullptr, *itemsF = nullptr;
-  FinalizeJob* jobs = nullptr;
+  void* itemsF = nullptr;
+  std::vector<BatchLayout> layouts;
+  // batch-owned scratch of each context for split tiles: per-block partials
+  // and per-group force sums (DeviceView::fpg), sized for scratch_groups
+  std::vector<double*> partS, fpg;
+  int scratch_groups = 0;
   std::vector<unsigned> gens;  // view_gen of each context at the last upload
   std::vector<unsigned> prune_gens;  // prune_gen of each context at creation
-  int gridT = 0, gridF = 0;
-  // tuning state: candidate persistent grids (multiples of the SM count)
-  std::vector<int> candT, candF;
-  std::vector<float> timeT;
+  std::vector<unsigned> accept_gens;  // accept_gen of each context at creation
+  int gridF = 0;
+  // tuning: candidate (layout, persistent transport grid) pairs, each timed
+  // on one substep; cur is the one in use
+  std::vector<std::pair<int, int>> cands;
+  std::vector<float> ctime;
+  int cur = 0;
   int tuned = 0;
-  // class of this batch in the process-wide cache of tuned grids: device,
+  // class of this batch in the process-wide cache of tuned choices: device,
   // precision, geometry, transport mode, bins, log2 of the tile count
   std::vector<long long> tune_key;
   cudaGraphExec_t exec = nullptr;
@@ -467,23 +508,32 @@ namespace {
 // new batch (a new mix of clouds in the serving loop) skips the timed tuning
 // substeps when a batch of its class was tuned before on this device.
 std::mutex g_tune_mutex;
-std::map<std::vector<long long>, int> g_tune_cache;
+std::map<std::vector<long long>, std::vector<int>> g_tune_cache;  // {shape, groups, grid}
 
-int tuned_grid_lookup(const std::vector<long long>& key) {
+std::vector<int> tuned_lookup(const std::vector<long long>& key) {
   std::lock_guard<std::mutex> lock(g_tune_mutex);
   const auto it = g_tune_cache.find(key);
-  return it == g_tune_cache.end() ? 0 : it->second;
+  return it == g_tune_cache.end() ? std::vector<int>() : it->second;
 }
 
-void tuned_grid_store(const std::vector<long long>& key, int grid) {
+void tuned_store(const std::vector<long long>& key, const std::vector<int>& choice) {
   std::lock_guard<std::mutex> lock(g_tune_mutex);
-  g_tune_cache[key] = grid;
+  g_tune_cache[key] = choice;
 }
 
-// the two views of a context in a batch: the transport step reads A and
-// writes B, the frequency step reads B and writes A
-void batch_views(const lym1_ctx* c, DeviceView* vT, DeviceView* vF) {
+// the two views of context i in a batch under a layout: the transport step
+// reads A and writes B, the frequency step reads B and writes A; a layout
+// other than one 16 x 16 block per tile keeps its partials in the batch's
+// scratch and, with split tiles, its per-group force sums
+void batch_views(const lym1_batch* b, size_t i, const BatchLayout& L, DeviceView* vT,
+                 DeviceView* vF) {
+  const lym1_ctx* c = b->ctxs[i];
   *vT = make_view(c, c->dt_cfl);
+  if (L.shape != 0 || L.groups > 1) vT->partT = b->partS[i];
+  if (L.groups > 1) {
+    vT->ngrp = L.groups;
+    vT->fpg = b->fpg[i];
+  }
   *vF = *vT;
   vF->J = c->B[0];
   vF->Hx = c->B[1];
@@ -493,6 +543,25 @@ void batch_views(const lym1_ctx* c, DeviceView* vT, DeviceView* vF) {
   vF->Hyo = c->A[2];
 }
 
+// uploads the views and finalize jobs of every context under one layout
+int upload_layout(const lym1_batch* b, const BatchLayout& L, cudaStream_t s) {
+  const size_t n = b->ctxs.size();
+  std::vector<DeviceView> vT(n), vF(n);
+  std::vector<FinalizeJob> jobs(n);
+  for (size_t i = 0; i < n; ++i) {
+    const lym1_ctx* c = b->ctxs[i];
+    batch_views(b, i, L, &vT[i], &vF[i]);
+    jobs[i] = {vT[i].partT, c->partF, c->acc,
+               transport_blocks(c->nx, c->ny, L.shape) * L.groups, freq_blocks(c->nc),
+               c->accept ? 2 : 0};
+  }
+  LYM1_TRY(cudaMemcpyAsync(L.viewsT, vT.data(), sizeof(DeviceView) * n, cudaMemcpyHostToDevice, s));
+  LYM1_TRY(cudaMemcpyAsync(L.viewsF, vF.data(), sizeof(DeviceView) * n, cudaMemcpyHostToDevice, s));
+  LYM1_TRY(cudaMemcpyAsync(L.jobs, jobs.data(), sizeof(FinalizeJob) * n, cudaMemcpyHostToDevice, s));
+  LYM1_TRY(cudaStreamSynchronize(s));
+  return LYM1_OK;
+}
+
 // re-upload, stream-ordered before the next launch, the views of contexts
 // whose c_tilde changed since the last upload (the kernels and the captured
 // graph read the views from device memory)
@@ -500,14 +569,33 @@ int refresh_views(lym1_batch* b, cudaStream_t s) {
   for (size_t i = 0; i < b->ctxs.size(); ++i) {
     const lym1_ctx* c = b->ctxs[i];
     if (c->view_gen == b->gens[i]) continue;
-    DeviceView v[2];
-    batch_views(c, &v[0], &v[1]);
-    LYM1_TRY(cudaMemcpyAsync(b->viewsT + i, &v[0], sizeof(DeviceView), cudaMemcpyHostToDevice, s));
-    LYM1_TRY(cudaMemcpyAsync(b->viewsF + i, &v[1], sizeof(DeviceView), cudaMemcpyHostToDevice, s));
+    for (const BatchLayout& L : b->layouts) {
+      DeviceView v[2];
+      batch_views(b, i, L, &v[0], &v[1]);
+      LYM1_TRY(cudaMemcpyAsync(L.viewsT + i, &v[0], sizeof(DeviceView), cudaMemcpyHostToDevice, s));
+      LYM1_TRY(cudaMemcpyAsync(L.viewsF + i, &v[1], sizeof(DeviceView), cudaMemcpyHostToDevice, s));
+    }
     LYM1_TRY(cudaStreamSynchronize(s));
     b->gens[i] = c->view_gen;
   }
   return LYM1_OK;
+}
+
+// one launch of a batch kernel (kind 0 transport, 1 frequency step, 2 the
+// acceptance rule's step 2) under the layout and grid in use
+int batch_kernel(lym1_batch* b, int kind, cudaStream_t s) {
+  const BatchLayout& L = b->layouts[b->cands[b->cur].first];
+  const int gridT = b->cands[b->cur].second;
+  const bool tr = kind == 0;
+  const int pt = tr ? b->tpt : b->pt;
+  const DeviceView* views = tr ? L.viewsT : L.viewsF;
+  const void* items = tr ? L.itemsT : b->itemsF;
+  const int n = tr ? L.nT : b->nF;
+  const int grid = tr ? gridT : (kind == 2 ? b->gridS : b->gridF);
+  if (b->precision == LYM1_FP64_DET)
+    return launch_batched_det(kind, b->geometry, pt, views, items, n, grid, b->nb, s, L.shape);
+  return launch_batched_fast(b->precision, kind, b->geometry, pt, views, items, n, grid, b->nb, s,
+                             L.shape);
 }
 
 int batch_launch(lym1_batch* b, cudaStream_t s) {
@@ -516,16 +604,10 @@ int batch_launch(lym1_batch* b, cudaStream_t s) {
     const int rc = prune_launch(c, s);
     if (rc != LYM1_OK) return rc;
   }
-  if (b->precision == LYM1_FP64_DET) {
-    LYM1_TRYK(launch_batched_det(0, b->geometry, b->tpt, b->viewsT, b->itemsT, b->nT, b->gridT, b->nb, s));
-    LYM1_TRYK(launch_batched_det(1, b->geometry, b->pt, b->viewsF, b->itemsF, b->nF, b->gridF, b->nb, s));
-  } else {
-    LYM1_TRYK(launch_batched_fast(b->precision, 0, b->geometry, b->tpt, b->viewsT, b->itemsT, b->nT,
-                                  b->gridT, b->nb, s));
-    LYM1_TRYK(launch_batched_fast(b->precision, 1, b->geometry, b->pt, b->viewsF, b->itemsF, b->nF,
-                                  b->gridF, b->nb, s));
-  }
-  LYM1_TRYK(launch_finalize_batched(b->jobs, n, s));
+  LYM1_TRYK(batch_kernel(b, 0, s));
+  if (b->accept) LYM1_TRYK(batch_kernel(b, 2, s));
+  LYM1_TRYK(batch_kernel(b, 1, s));
+  LYM1_TRYK(launch_finalize_batched(b->layouts[b->cands[b->cur].first].jobs, n, s));
   return LYM1_OK;
 }
 
@@ -539,24 +621,15 @@ int batch_launch_timed(lym1_batch* b, lym1_ctx* c) {
   }
   {
     KernelTimer t(c, 0);
-    if (b->precision == LYM1_FP64_DET)
-      LYM1_TRYK(launch_batched_det(0, b->geometry, b->tpt, b->viewsT, b->itemsT, b->nT, b->gridT,
-                                   b->nb, c->stream));
-    else
-      LYM1_TRYK(launch_batched_fast(b->precision, 0, b->geometry, b->tpt, b->viewsT, b->itemsT, b->nT,
-                                    b->gridT, b->nb, c->stream));
+    LYM1_TRYK(batch_kernel(b, 0, c->stream));
   }
   {
-    KernelTimer t(c, 1);
-    if (b->precision == LYM1_FP64_DET)
-      LYM1_TRYK(launch_batched_det(1, b->geometry, b->pt, b->viewsF, b->itemsF, b->nF, b->gridF,
-                                   b->nb, c->stream));
-    else
-      LYM1_TRYK(launch_batched_fast(b->precision, 1, b->geometry, b->pt, b->viewsF, b->itemsF, b->nF,
-                                    b->gridF, b->nb, c->stream));
+    KernelTimer t(c, 1);  // with the acceptance rule, its kernel counts here
+    if (b->accept) LYM1_TRYK(batch_kernel(b, 2, c->stream));
+    LYM1_TRYK(batch_kernel(b, 1, c->stream));
   }
   KernelTimer t(c, 2);
-  LYM1_TRYK(launch_finalize_batched(b->jobs, n, c->stream));
+  LYM1_TRYK(launch_finalize_batched(b->layouts[b->cands[b->cur].first].jobs, n, c->stream));
   return LYM1_OK;
 }
 
@@ -572,13 +645,102 @@ int device_status(lym1_ctx* c) {
 void batch_free(lym1_batch* b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
-  void* ptrs[] = {b->viewsT, b->viewsF, b->itemsT, b->itemsF, b->jobs};
-  for (void* p : ptrs)
+  for (BatchLayout& L : b->layouts) {
+    void* ptrs[] = {L.itemsT, L.viewsT, L.viewsF, L.jobs};
+    for (void* p : ptrs)
+      if (p) cudaFree(p);
+  }
+  for (double* p : b->partS)
     if (p) cudaFree(p);
+  for (double* p : b->fpg)
+    if (p) cudaFree(p);
+  if (b->itemsF) cudaFree(b->itemsF);
   cudaEvent_t evs[] = {b->ev_in, b->ev_out, b->t0, b->t1};
   for (cudaEvent_t e : evs)
     if (e) cudaEventDestroy(e);
   if (b->bs) cudaStreamDestroy(b->bs);
+}
+
+// The batch's scratch for split tiles and other shapes, sized for up to
+// `groups` bin groups (grown, never shrunk; outside any capture).
+int ensure_scratch(lym1_batch* b, int groups) {
+  if (groups <= b->scratch_groups) return LYM1_OK;
+  for (size_t i = 0; i < b->ctxs.size(); ++i) {
+    const lym1_ctx* c = b->ctxs[i];
+    const int tiles = std::max(transport_blocks(c->nx, c->ny, 0), transport_blocks(c->nx, c->ny, 1));
+    double* ps = nullptr;
+    double* fg = nullptr;
+    if (cudaMalloc(reinterpret_cast<void**>(&ps), sizeof(double) * kDiagSlots * tiles * groups) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      return LYM1_ENOMEM;
+    }
+    if (groups > 1 &&
+        cudaMalloc(reinterpret_cast<void**>(&fg), sizeof(double) * 2 * groups * c->nc) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(ps);
+      return LYM1_ENOMEM;
+    }
+    if (b->partS[i]) cudaFree(b->partS[i]);
+    if (b->fpg[i]) cudaFree(b->fpg[i]);
+    b->partS[i] = ps;
+    b->fpg[i] = fg;
+  }
+  b->scratch_groups = groups;
+  return LYM1_OK;
+}
+
+// Index of the layout (shape, groups), made (items, views, jobs) if new.
+// Every layout's views are re-uploaded, since the scratch may have moved.
+int ensure_layout(lym1_batch* b, int shape, int groups, int* index) {
+  for (size_t j = 0; j < b->layouts.size(); ++j)
+    if (b->layouts[j].shape == shape && b->layouts[j].groups == groups) {
+      *index = static_cast<int>(j);
+      return LYM1_OK;
+    }
+  {
+    const int rc = ensure_scratch(b, groups);
+    if (rc != LYM1_OK) return rc;
+  }
+  BatchLayout L;
+  L.shape = shape;
+  L.groups = groups;
+  std::vector<BatchItemHost> it;
+  const int tx = tile_x(shape), ty = tile_y(shape);
+  for (size_t i = 0; i < b->ctxs.size(); ++i) {
+    const lym1_ctx* c = b->ctxs[i];
+    const int gx = (c->nx + tx - 1) / tx, gy = (c->ny + ty - 1) / ty, tiles = gx * gy;
+    for (int g = 0; g < groups; ++g) {
+      const int k0 = static_cast<int>(static_cast<long long>(c->nb) * g / groups);
+      const int k1 = static_cast<int>(static_cast<long long>(c->nb) * (g + 1) / groups);
+      for (int by = 0; by < gy; ++by)
+        for (int bx = 0; bx < gx; ++bx)
+          it.push_back({static_cast<int>(i), bx * tx, by * ty, g * tiles + by * gx + bx, k0, k1, g});
+    }
+  }
+  L.nT = static_cast<int>(it.size());
+  const size_t n = b->ctxs.size();
+  if (cudaMalloc(&L.itemsT, sizeof(BatchItemHost) * it.size()) != cudaSuccess ||
+      cudaMalloc(reinterpret_cast<void**>(&L.viewsT), sizeof(DeviceView) * n) != cudaSuccess ||
+      cudaMalloc(reinterpret_cast<void**>(&L.viewsF), sizeof(DeviceView) * n) != cudaSuccess ||
+      cudaMalloc(reinterpret_cast<void**>(&L.jobs), sizeof(FinalizeJob) * n) != cudaSuccess) {
+    cudaGetLastError();
+    void* ptrs[] = {L.itemsT, L.viewsT, L.viewsF, L.jobs};
+    for (void* p : ptrs)
+      if (p) cudaFree(p);
+    return LYM1_ENOMEM;
+  }
+  LYM1_TRY(cudaMemcpy(L.itemsT, it.data(), sizeof(BatchItemHost) * it.size(), cudaMemcpyHostToDevice));
+  L.rT = b->precision == LYM1_FP64_DET
+             ? resident_blocks_det(0, b->geometry, b->tpt, b->nb, shape)
+             : resident_blocks_fast(b->precision, 0, b->geometry, b->tpt, b->nb, shape);
+  b->layouts.push_back(L);
+  for (const BatchLayout& M : b->layouts) {
+    const int rc = upload_layout(b, M, b->bs);
+    if (rc != LYM1_OK) return rc;
+  }
+  *index = static_cast<int>(b->layouts.size()) - 1;
+  return LYM1_OK;
 }
 
 }  // namespace
@@ -986,7 +1148,7 @@ int lym1_substeps(lym1_ctx* c, int n, double dt) {
     }
     int done = 0;
     if (!b->tuned) {  // the tuning substeps (untimed) count toward n
-      done = std::min(n, static_cast<int>(b->candT.size()));
+      done = std::min(n, static_cast<int>(b->cands.size() - b->ctime.size()));
       const int rc = lym1_batch_substeps(b, done);
       if (rc != LYM1_OK) return rc;
     }
@@ -1185,7 +1347,7 @@ int lym1_batch_create(lym1_ctx* const* ctxs, int n_ctx, lym1_batch** out) {
     if (!ctxs[i] || ctxs[i]->gray || !ctxs[i]->freq_step) return LYM1_EINVAL;
     if (ctxs[i]->precision != ctxs[0]->precision || ctxs[i]->nb != ctxs[0]->nb ||
         ctxs[i]->stream != ctxs[0]->stream || ctxs[i]->geometry != ctxs[0]->geometry ||
-        ctxs[i]->pt != ctxs[0]->pt)
+        ctxs[i]->pt != ctxs[0]->pt || ctxs[i]->accept != ctxs[0]->accept)
       return LYM1_EINVAL;
   }
   lym1_batch* b = new (std::nothrow) lym1_batch();
@@ -1197,46 +1359,34 @@ int lym1_batch_create(lym1_ctx* const* ctxs, int n_ctx, lym1_batch** out) {
   b->tpt = b->pt;
   for (int i = 0; i < n_ctx; ++i)
     if (ctxs[i]->prune > 0.0) b->tpt = b->pt | 4;
+  b->accept = ctxs[0]->accept;
+  if (b->accept) b->tpt |= 8;
   b->nb = ctxs[0]->nb;
   b->ctx_stream = ctxs[0]->stream;
-  std::vector<DeviceView> vT, vF;
-  std::vector<BatchItemHost> iT, iF;
-  std::vector<FinalizeJob> jobs;
+  b->partS.assign(n_ctx, nullptr);
+  b->fpg.assign(n_ctx, nullptr);
+  std::vector<BatchItemHost> iF;
+  long long tiles0 = 0;
   for (int i = 0; i < n_ctx; ++i) {
     lym1_ctx* c = ctxs[i];
-    DeviceView v, w;
-    batch_views(c, &v, &w);
-    vT.push_back(v);
-    vF.push_back(w);
     b->gens.push_back(c->view_gen);
     b->prune_gens.push_back(c->prune_gen);
-    const int gx = (c->nx + kTileX - 1) / kTileX, gy = (c->ny + kTileY - 1) / kTileY;
-    for (int by = 0; by < gy; ++by)
-      for (int bx = 0; bx < gx; ++bx) iT.push_back({i, bx * kTileX, by * kTileY, by * gx + bx});
+    b->accept_gens.push_back(c->accept_gen);
     const int fb = freq_blocks(c->nc);
-    for (int k = 0; k < fb; ++k) iF.push_back({i, 0, 0, k});
-    jobs.push_back({c->partT, c->partF, c->acc, transport_blocks(c->nx, c->ny), fb});
+    for (int k = 0; k < fb; ++k) iF.push_back({i, 0, 0, k, 0, 0, 0});
+    tiles0 += transport_blocks(c->nx, c->ny, 0);
   }
-  b->nT = static_cast<int>(iT.size());
   b->nF = static_cast<int>(iF.size());
   auto fail = [&](int rc) {
     batch_free(b);
     delete b;
     return rc;
   };
-  if (cudaMalloc(reinterpret_cast<void**>(&b->viewsT), sizeof(DeviceView) * n_ctx) != cudaSuccess ||
-      cudaMalloc(reinterpret_cast<void**>(&b->viewsF), sizeof(DeviceView) * n_ctx) != cudaSuccess ||
-      cudaMalloc(&b->itemsT, sizeof(BatchItemHost) * iT.size()) != cudaSuccess ||
-      cudaMalloc(&b->itemsF, sizeof(BatchItemHost) * iF.size()) != cudaSuccess ||
-      cudaMalloc(reinterpret_cast<void**>(&b->jobs), sizeof(FinalizeJob) * n_ctx) != cudaSuccess) {
+  if (cudaMalloc(&b->itemsF, sizeof(BatchItemHost) * iF.size()) != cudaSuccess) {
     cudaGetLastError();
     return fail(LYM1_ENOMEM);
   }
-  if (cudaMemcpy(b->viewsT, vT.data(), sizeof(DeviceView) * n_ctx, cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy(b->viewsF, vF.data(), sizeof(DeviceView) * n_ctx, cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy(b->itemsT, iT.data(), sizeof(BatchItemHost) * iT.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy(b->itemsF, iF.data(), sizeof(BatchItemHost) * iF.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy(b->jobs, jobs.data(), sizeof(FinalizeJob) * n_ctx, cudaMemcpyHostToDevice) != cudaSuccess ||
+  if (cudaMemcpy(b->itemsF, iF.data(), sizeof(BatchItemHost) * iF.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaStreamCreateWithFlags(&b->bs, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming) != cudaSuccess ||
@@ -1244,28 +1394,68 @@ int lym1_batch_create(lym1_ctx* const* ctxs, int n_ctx, lym1_batch** out) {
     cudaGetLastError();
     return fail(LYM1_ECUDA);
   }
-  int dev = 0, nsm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  if (nsm < 1) nsm = 1;
-  const int rT = b->precision == LYM1_FP64_DET
-                     ? resident_blocks_det(0, b->geometry, b->tpt, b->nb)
-                     : resident_blocks_fast(b->precision, 0, b->geometry, b->tpt, b->nb);
+  cudaGetDevice(&b->dev);
+  cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, b->dev);
+  if (b->nsm < 1) b->nsm = 1;
+  const int nsm = b->nsm;
   const int rF = b->precision == LYM1_FP64_DET
                      ? resident_blocks_det(1, b->geometry, b->pt, b->nb)
                      : resident_blocks_fast(b->precision, 1, b->geometry, b->pt, b->nb);
-  for (int m = 1; m <= rT; ++m) b->candT.push_back(std::min(b->nT, m * nsm));
-  const int gf = std::min(b->nF, rF * nsm);
-  b->candF.push_back(gf);
-  b->gridT = b->candT.back();
-  b->gridF = gf;
+  b->gridF = std::min(b->nF, rF * nsm);
+  if (b->accept) {
+    const int rS = b->precision == LYM1_FP64_DET
+                       ? resident_blocks_det(2, b->geometry, b->pt, b->nb)
+                       : resident_blocks_fast(b->precision, 2, b->geometry, b->pt, b->nb);
+    b->gridS = std::min(b->nF, rS * nsm);
+  }
+  // candidate layouts: one 16 x 16 block per tile always; for the policies
+  // other than LYM1_FP64_DET (whose batches keep it, and so equal solo runs
+  // bit for bit) also 32 x 8 tiles in the plain table modes, and the bins of
+  // each tile split over 2, 4 or 8 blocks where the tiles alone do not fill
+  // the GPU (at least 16 bins a group)
+  int base = 0;
+  {
+    const int rc = ensure_layout(b, 0, 1, &base);
+    if (rc != LYM1_OK) return fail(rc);
+  }
+  std::vector<int> lay = {base};
+  if (b->precision != LYM1_FP64_DET) {
+    const long long room = 2LL * nsm * b->layouts[base].rT;
+    if (b->tpt == 0 || b->tpt == 1) {
+      int j = 0;
+      const int rc = ensure_layout(b, 1, 1, &j);
+      if (rc != LYM1_OK) return fail(rc);
+      lay.push_back(j);
+    }
+    for (int g = 2; g <= 8; g *= 2) {
+      if (b->nb < 16 * g || tiles0 * g > room) break;
+      int j = 0;
+      const int rc = ensure_layout(b, 0, g, &j);
+      if (rc != LYM1_OK) return fail(rc);
+      lay.push_back(j);
+    }
+  }
+  for (int j : lay) {
+    const BatchLayout& L = b->layouts[j];
+    int last = 0;
+    for (int m = 1; m <= L.rT; ++m) {
+      const int g = std::min(L.nT, m * nsm);
+      if (g != last) b->cands.push_back({j, g});
+      last = g;
+    }
+  }
   int lg = 0;
-  while ((2LL << lg) <= b->nT) ++lg;
-  b->tune_key = {dev, b->precision, b->geometry, b->tpt, b->nb, lg};
-  if (const int g = tuned_grid_lookup(b->tune_key)) {
-    b->gridT = std::min(g, b->nT);
+  while ((2LL << lg) <= tiles0) ++lg;
+  b->tune_key = {b->dev, b->precision, b->geometry, b->tpt, b->nb, lg};
+  const std::vector<int> known = tuned_lookup(b->tune_key);
+  if (known.size() == 3) {  // {shape, groups, grid} of an earlier batch of this class
+    int j = 0;
+    const int rc = ensure_layout(b, known[0], known[1], &j);
+    if (rc != LYM1_OK) return fail(rc);
+    b->cands = {{j, std::min(known[2], b->layouts[j].nT)}};
     b->tuned = 1;
   }
+  b->cur = static_cast<int>(b->cands.size()) - 1;
   *out = b;
   return LYM1_OK;
 }
@@ -1275,7 +1465,8 @@ int lym1_batch_substeps(lym1_batch* b, int n) {
   // the captured launches include the pruning kernels of the contexts that
   // pruned at creation: switching pruning since then needs a new batch
   for (size_t i = 0; i < b->ctxs.size(); ++i)
-    if (b->ctxs[i]->prune_gen != b->prune_gens[i]) return LYM1_EINVAL;
+    if (b->ctxs[i]->prune_gen != b->prune_gens[i] || b->ctxs[i]->accept_gen != b->accept_gens[i])
+      return LYM1_EINVAL;
   if (n == 0) return LYM1_OK;
   LYM1_TRY(cudaEventRecord(b->ev_in, b->ctx_stream));
   LYM1_TRY(cudaStreamWaitEvent(b->bs, b->ev_in, 0));
@@ -1284,10 +1475,9 @@ int lym1_batch_substeps(lym1_batch* b, int n) {
     if (rc != LYM1_OK) return rc;
   }
   int done = 0;
-  // tuning: the first substeps run once with each candidate persistent grid
+  // tuning: the first substeps run once with each candidate (layout, grid)
   while (!b->tuned && done < n) {
-    const size_t i = b->timeT.size();
-    b->gridT = b->candT[i];
+    b->cur = static_cast<int>(b->ctime.size());
     LYM1_TRY(cudaEventRecord(b->t0, b->bs));
     const int rc = batch_launch(b, b->bs);
     if (rc != LYM1_OK) return rc;
@@ -1295,15 +1485,16 @@ int lym1_batch_substeps(lym1_batch* b, int n) {
     LYM1_TRY(cudaEventSynchronize(b->t1));
     float ms = 0.0f;
     LYM1_TRY(cudaEventElapsedTime(&ms, b->t0, b->t1));
-    b->timeT.push_back(ms);
+    b->ctime.push_back(ms);
     ++done;
-    if (b->timeT.size() == b->candT.size()) {
+    if (b->ctime.size() == b->cands.size()) {
       size_t best = 0;
-      for (size_t k = 1; k < b->timeT.size(); ++k)
-        if (b->timeT[k] < b->timeT[best]) best = k;
-      b->gridT = b->candT[best];
+      for (size_t k = 1; k < b->ctime.size(); ++k)
+        if (b->ctime[k] < b->ctime[best]) best = k;
+      b->cur = static_cast<int>(best);
       b->tuned = 1;
-      tuned_grid_store(b->tune_key, b->gridT);
+      const BatchLayout& L = b->layouts[b->cands[best].first];
+      tuned_store(b->tune_key, {L.shape, L.groups, b->cands[best].second});
     }
   }
   if (done < n) {
@@ -1327,8 +1518,46 @@ int lym1_batch_substeps(lym1_batch* b, int n) {
 
 int lym1_batch_grid(lym1_batch* b, int* gt, int* gf) {
   if (!b) return LYM1_EINVAL;
-  if (gt) *gt = b->tuned ? b->gridT : 0;
+  if (gt) *gt = b->tuned ? b->cands[b->cur].second : 0;
   if (gf) *gf = b->tuned ? b->gridF : 0;
+  return LYM1_OK;
+}
+
+int lym1_batch_config(lym1_batch* b, int* tile_x_out, int* tile_y_out, int* groups, int* grid_t,
+                      int* grid_f) {
+  if (!b) return LYM1_EINVAL;
+  const BatchLayout& L = b->layouts[b->cands[b->cur].first];
+  if (tile_x_out) *tile_x_out = b->tuned ? tile_x(L.shape) : 0;
+  if (tile_y_out) *tile_y_out = b->tuned ? tile_y(L.shape) : 0;
+  if (groups) *groups = b->tuned ? L.groups : 0;
+  if (grid_t) *grid_t = b->tuned ? b->cands[b->cur].second : 0;
+  if (grid_f) *grid_f = b->tuned ? b->gridF : 0;
+  return LYM1_OK;
+}
+
+int lym1_batch_configure(lym1_batch* b, int tile_shape, int bin_groups, int grid_t) {
+  if (!b) return LYM1_EINVAL;
+  if (tile_shape != 0 && tile_shape != 1) return LYM1_EINVAL;
+  if (tile_shape == 1 && b->tpt != 0 && b->tpt != 1) return LYM1_EINVAL;
+  if (bin_groups != 1 && bin_groups != 2 && bin_groups != 4 && bin_groups != 8) return LYM1_EINVAL;
+  if (bin_groups > b->nb || grid_t < 0) return LYM1_EINVAL;
+  LYM1_TRY(cudaStreamSynchronize(b->bs));
+  int j = 0;
+  {
+    const int rc = ensure_layout(b, tile_shape, bin_groups, &j);
+    if (rc != LYM1_OK) return rc;
+  }
+  const BatchLayout& L = b->layouts[j];
+  const int g = grid_t > 0 ? grid_t : L.rT * b->nsm;
+  b->cands = {{j, std::min(g, L.nT)}};
+  b->ctime.clear();
+  b->cur = 0;
+  b->tuned = 1;
+  // the captured launches hold the old layout
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
   return LYM1_OK;
 }
 
@@ -1470,6 +1699,22 @@ int lym1_set_temperature(lym1_ctx* c, const double* temp_field) {
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) rc = LYM1_ECUDA;
   cudaFree(scr);
   return rc;
+}
+
+int lym1_set_accept(lym1_ctx* c, int on) {
+  if (!c || (on != 0 && on != 1)) return LYM1_EINVAL;
+  if (on && c->bands) return LYM1_EINVAL;  // the rule watches the Lya energy density
+  if (on == c->accept) return LYM1_OK;
+  c->accept = on;
+  c->accept_gen += 1;
+  c->view_gen += 1;
+  // the graph-replayed path captured its launches with the old setting
+  if (c->self_batch) {
+    LYM1_TRY(cudaStreamSynchronize(c->stream));
+    lym1_batch_destroy(c->self_batch);
+    c->self_batch = nullptr;
+  }
+  return LYM1_OK;
 }
 
 int lym1_set_pruning(lym1_ctx* c, double cut) {

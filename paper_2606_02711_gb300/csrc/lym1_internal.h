@@ -67,9 +67,18 @@ void build_cell_tables(const std::vector<double>& edges, const double* T, long l
 
 // ---------------------------------------------------------------- kernel side
 // transport tile: one thread per cell; 16 x 16 makes the 32 faces beyond
-// the per-thread left and bottom faces (top row, right column) one warp's work
+// the per-thread left and bottom faces (top row, right column) one warp's work.
+// Persistent batched launches may take the other shape the tuner times,
+// 32 x 8 (shape 1: rows of 128 bytes, 40 extra faces).
 constexpr int kTileX = 16;
 constexpr int kTileY = 16;
+template <int TS>
+struct TileShape {
+  static constexpr int X = TS == 1 ? 32 : 16;
+  static constexpr int Y = TS == 1 ? 8 : 16;
+};
+inline int tile_x(int shape) { return shape == 1 ? 32 : 16; }
+inline int tile_y(int shape) { return shape == 1 ? 8 : 16; }
 constexpr int kFreqThreads = 128;
 constexpr int kDiagSlots = 8;  // per-block partial sums written by the kernels
 
@@ -125,8 +134,14 @@ struct DeviceView {
   // would otherwise divide in FP64 on every thread of every tile)
   double cdt_dx = 0, cdt_c = 0;
   double gem_max = 1;  // max_k gem_k (FP32 emissivity scaling)
-  double sg = 0;       // sum_k dnu_k gem_k (emission of a uniform-temperature cell per unit L c dt)
   double rcdt = 0;     // 1 / (c_tilde dt)
+  double ct = 0, dt = 0;  // c_tilde and dt apart (substep lengths of the acceptance rule)
+  // bins of a small grid's tiles split over ngrp blocks (the batch's tuned
+  // choice): each group writes its raw force sums to fpg[(2 grp + c) nc +
+  // cell], which the frequency step adds up in group order; 1 = one block
+  // per tile writes the force itself
+  double* fpg = nullptr;
+  int ngrp = 1;
   const double* acc = nullptr;  // running totals: [8] energy of the last substep, [13] energy unit
   int* status = nullptr;        // device status word: nonzero after a bounded wait expired
   // FP32 copies of the per-bin tables for the FP32 policies: <H>_k, dnu_k,
@@ -193,6 +208,9 @@ int launch_transport_det(const DeviceView& v, void* stream);
 int launch_freq_det(const DeviceView& v, void* stream);
 int launch_transport_fast(int precision, const DeviceView& v, void* stream);
 int launch_freq_fast(int precision, const DeviceView& v, void* stream);
+// step 2 under the substep acceptance rule, in place on the view's input state
+int launch_subcycle_det(const DeviceView& v, void* stream);
+int launch_subcycle_fast(int precision, const DeviceView& v, void* stream);
 // wcol: per-column energy weights (nullptr = 1), nx columns
 int launch_energy(int precision, const void* J, const double* dnu, int nb, long long nc,
                   double* part, const double* wcol, int nx, void* stream);
@@ -234,28 +252,32 @@ int launch_dynamic_ctilde(const double* alpha, const double* rho, const double* 
                           const double* cs, double kabs, double dx, long long nc, double eps,
                           double ct_min, double prev, unsigned long long* work, void* stream);
 
-// batched (multi-context) launches; kind 0 = transport, 1 = frequency step;
+// batched (multi-context) launches; kind 0 = transport, 1 = frequency step,
+// 2 = step 2 under the acceptance rule (over the frequency step's items);
 // items point to device arrays of {ctx, x0, y0, blk}
 struct FinalizeJob {
   const double* partT;
   const double* partE;
   double* acc;
   int nT, nE;
+  int mode;  // 0, or 2 when step 2 ran in the subcycling kernel
 };
 // every context of one batched launch has the same geometry
 // every context of one batched launch has the same geometry and temperature mode
+// shape: the transport tile shape (TileShape; 1 only with table modes 0 and 1)
 int launch_batched_det(int kind, int geometry, int pt, const DeviceView* views, const void* items,
-                       int n, int grid, int nb_max, void* stream);
+                       int n, int grid, int nb_max, void* stream, int shape = 0);
 int launch_batched_fast(int precision, int kind, int geometry, int pt, const DeviceView* views,
-                        const void* items, int n, int grid, int nb_max, void* stream);
+                        const void* items, int n, int grid, int nb_max, void* stream, int shape = 0);
 // blocks of one persistent launch resident per SM at nb_max bins (also opts
 // the frequency kernels in to their shared-memory size; call outside capture)
-int resident_blocks_det(int kind, int geometry, int pt, int nb_max);
-int resident_blocks_fast(int precision, int kind, int geometry, int pt, int nb_max);
+int resident_blocks_det(int kind, int geometry, int pt, int nb_max, int shape = 0);
+int resident_blocks_fast(int precision, int kind, int geometry, int pt, int nb_max, int shape = 0);
 int launch_finalize_batched(const FinalizeJob* jobs, int n, void* stream);
 
-inline int transport_blocks(int nx, int ny) {
-  return ((nx + kTileX - 1) / kTileX) * ((ny + kTileY - 1) / kTileY);
+inline int transport_blocks(int nx, int ny, int shape = 0) {
+  const int tx = tile_x(shape), ty = tile_y(shape);
+  return ((nx + tx - 1) / tx) * ((ny + ty - 1) / ty);
 }
 inline int freq_blocks(long long nc) {
   return static_cast<int>((nc + kFreqThreads - 1) / kFreqThreads);

@@ -384,17 +384,51 @@ __device__ __forceinline__ double block_max(double v, double* red) {
   return s;
 }
 
+// The force of a cell from the sums over its bins sum_k dnu_k (H' - H'')
+// (Sec. 2.3): written directly when one block holds all bins; a bin group
+// of a split tile writes its raw sums to v.fpg, and the frequency step forms
+// the force from the groups in group order (combine_force_groups).
+__device__ __forceinline__ void store_force(const DeviceView& v, long long cell, int grp, double ax,
+                                            double ay) {
+  if (v.ngrp > 1) {
+    v.fpg[(2LL * grp) * v.nc + cell] = ax;
+    v.fpg[(2LL * grp + 1) * v.nc + cell] = ay;
+  } else {
+    v.fx[cell] = v.fcoef * ax;
+    v.fy[cell] = v.fcoef * ay;
+  }
+}
+
+__device__ __forceinline__ void combine_force_groups(const DeviceView& v, long long cell) {
+  if (v.ngrp <= 1 || (v.pt & 8)) return;  // under the acceptance rule its kernel writes the force
+  double ax = 0.0, ay = 0.0;
+  for (int g = 0; g < v.ngrp; ++g) {
+    ax += v.fpg[(2LL * g) * v.nc + cell];
+    ay += v.fpg[(2LL * g + 1) * v.nc + cell];
+  }
+  v.fx[cell] = v.fcoef * ax;
+  v.fy[cell] = v.fcoef * ay;
+}
+
 // ------------------------------------------------------------ transport kernel
-template <class P, int G, int PT>
-__device__ __forceinline__ void transport_tile(const DeviceView& v, int x0, int y0, int blk) {
+// One tile, bins [k0, k1) (the whole range unless the bins of a small grid's
+// tiles are split over several blocks: group grp of v.ngrp, see
+// DeviceView::fpg).
+template <class P, int G, int PT, int TS = 0>
+__device__ __forceinline__ void transport_tile(const DeviceView& v, int x0, int y0, int blk, int k0,
+                                               int k1, int grp) {
   // table mode (0 uniform T, 1 temperature field, 2 broad bands) and, in bit 4,
   // active-bin pruning: without it the tile compiles with no pruning code
   constexpr int TM = PT & 3;
   constexpr bool PR = (PT & 4) != 0;
+  // bit 8: step 2 is left to the subcycling kernel of the acceptance rule;
+  // the tile writes the post-transport state J', H'
+  constexpr bool DF = (PT & 8) != 0;
   using S = typename P::S;
   using F = typename P::F;
   using I = typename P::I;
-  constexpr int TX = kTileX, TY = kTileY, SX = TX + 4, SY = TY + 4, QX = TX + 2, QY = TY + 2;
+  constexpr int TX = TileShape<TS>::X, TY = TileShape<TS>::Y, SX = TX + 4, SY = TY + 4;
+  constexpr int QX = TX + 2, QY = TY + 2;
   constexpr int NT = TX * TY;
   constexpr int NXF = (TX + 1) * TY, NYF = TX * (TY + 1);
   __shared__ F sJ[SY][SX], sHx[SY][SX], sHy[SY][SX], sfx[SY][SX], sfy[SY][SX];
@@ -469,7 +503,7 @@ __device__ __forceinline__ void transport_tile(const DeviceView& v, int x0, int 
   double bad = 0;
   const double lum_d = valid ? v.lum[cell] : 0.0;
 
-  for (int k = 0; k < v.nb; ++k) {
+  for (int k = k0; k < k1; ++k) {
     const long long base = static_cast<long long>(k) * nc;
     const double Hk_d = v.t_H[k];
     const F Hk = F(Hk_d);
@@ -595,41 +629,49 @@ __device__ __forceinline__ void transport_tile(const DeviceView& v, int x0, int 
         Hy1 = Hy;
         W = F(0);
       }
-      const I aH = alpha_c * (TM ? I(Hcs[base + cell]) : I(Hk_d));
-      const I kap = (TM == 2) ? I(Kbs[base + cell]) : rho_c * kabs + pd_c * aH;
-      const I aF = aH + rho_c * kF;
-      // j_k = L w_k / (4 pi V dnu_k): formed in FP64 (L ~ 1e39 erg/s and
-      // w_k / (4 pi V dnu_k) ~ 1e-58 are both outside the FP32 range); on the
-      // axisymmetric grid lum already holds L / (2 pi Vol) and gem_k has V = 1
-      const I js = (lum_d != 0.0) ? I(lum_d * (TM ? double(Gcs[base + cell]) : v.t_gem[k])) : I(0);
-      I J2, Hx2, Hy2;
-      if constexpr (P::DET) {
-        J2 = (I(J1) + cdt * js) / (I(1) + cdt * kap);
-        Hx2 = I(Hx1) / (I(1) + cdt * aF);
-        Hy2 = I(Hy1) / (I(1) + cdt * aF);
+      if constexpr (DF) {  // step 2 follows in the subcycling kernel
+        const long long o = base + cell;
+        Jout[o] = S(J1);
+        Hxout[o] = S(Hx1);
+        Hyout[o] = S(Hy1);
       } else {
-        J2 = (I(J1) + cdt * js) / (I(1) + cdt * kap);
-        const I ra = I(1) / (I(1) + cdt * aF);
-        Hx2 = I(Hx1) * ra;
-        Hy2 = I(Hy1) * ra;
+        const I aH = alpha_c * (TM ? I(Hcs[base + cell]) : I(Hk_d));
+        const I kap = (TM == 2) ? I(Kbs[base + cell]) : rho_c * kabs + pd_c * aH;
+        const I aF = aH + rho_c * kF;
+        // j_k = L w_k / (4 pi V dnu_k): formed in FP64 (L ~ 1e39 erg/s and
+        // w_k / (4 pi V dnu_k) ~ 1e-58 are both outside the FP32 range); on the
+        // axisymmetric grid lum already holds L / (2 pi Vol) and gem_k has V = 1
+        const I js = (lum_d != 0.0) ? I(lum_d * (TM ? double(Gcs[base + cell]) : v.t_gem[k])) : I(0);
+        I J2, Hx2, Hy2;
+        if constexpr (P::DET) {
+          J2 = (I(J1) + cdt * js) / (I(1) + cdt * kap);
+          Hx2 = I(Hx1) / (I(1) + cdt * aF);
+          Hy2 = I(Hy1) / (I(1) + cdt * aF);
+        } else {
+          J2 = (I(J1) + cdt * js) / (I(1) + cdt * kap);
+          const I ra = I(1) / (I(1) + cdt * aF);
+          Hx2 = I(Hx1) * ra;
+          Hy2 = I(Hy1) * ra;
+        }
+        const long long o = base + cell;
+        Jout[o] = S(J2);
+        Hxout[o] = S(Hx2);
+        Hyout[o] = S(Hy2);
+        const I dnu = I(v.t_dnu[k]);
+        ax = ax + dnu * (I(Hx1) - Hx2);
+        ay = ay + dnu * (I(Hy1) - Hy2);
+        // A7 bookkeeping (energy units applied once per substep on the host side)
+        if (lum_d != 0.0) em.add(dnu * (cdt * js));
+        ab.add(dnu * (cdt * (kap * J2)));
+        if (v.tdiag) {  // the frequency step recomputes these when it follows
+          en.add(dnu * J2);
+          const I hn = sqrt(Hx2 * Hx2 + Hy2 * Hy2);
+          if (J2 > I(0)) mxf = fmax(mxf, hn / J2);
+          if (hn > J2 * I(1.000001) && hn > I(0)) bad += 1.0;
+        }
       }
-      const long long o = base + cell;
-      Jout[o] = S(J2);
-      Hxout[o] = S(Hx2);
-      Hyout[o] = S(Hy2);
       const I dnu = I(v.t_dnu[k]);
-      ax = ax + dnu * (I(Hx1) - Hx2);
-      ay = ay + dnu * (I(Hy1) - Hy2);
-      // A7 bookkeeping (energy units applied once per substep on the host side)
-      if (lum_d != 0.0) em.add(dnu * (cdt * js));
-      ab.add(dnu * (cdt * (kap * J2)));
       wk.add(dnu * (cdt * (I(W) / I(kLight))));
-      if (v.tdiag) {  // the frequency step recomputes these when it follows
-        en.add(dnu * J2);
-        const I hn = sqrt(Hx2 * Hx2 + Hy2 * Hy2);
-        if (J2 > I(0)) mxf = fmax(mxf, hn / J2);
-        if (hn > J2 * I(1.000001) && hn > I(0)) bad += 1.0;
-      }
       const I cdx = cdt / I(v.dx);
       if constexpr (G == 1) {  // outflow through the outer R and Z faces only
         if (gx == nx - 1) out.add(dnu * (cdx * (I(v.g_wR) * I(xJ[ty][tx + 1]))));
@@ -660,10 +702,7 @@ __device__ __forceinline__ void transport_tile(const DeviceView& v, int x0, int 
     }
     __syncthreads();
   }
-  if (valid) {
-    v.fx[cell] = v.fcoef * double(ax);
-    v.fy[cell] = v.fcoef * double(ay);
-  }
+  if (valid && !DF) store_force(v, cell, grp, double(ax), double(ay));
   double* part = v.partT + static_cast<long long>(blk) * kDiagSlots;
   double s;
   s = block_sum<NT>(em.value() * wcell, red);
@@ -674,7 +713,7 @@ __device__ __forceinline__ void transport_tile(const DeviceView& v, int x0, int 
   if (tid == 0) part[kSlotOutflow] = s;
   s = block_sum<NT>(wk.value() * wcell, red);
   if (tid == 0) part[kSlotWork] = s;
-  if (v.tdiag) {
+  if (v.tdiag && !DF) {
     s = block_sum<NT>(en.value() * wcell, red);
     if (tid == 0) part[kSlotEnergy] = s;
     s = block_max<NT>(double(mxf), red);
@@ -687,7 +726,8 @@ __device__ __forceinline__ void transport_tile(const DeviceView& v, int x0, int 
 
 template <class P, int G, int PT>
 __global__ void __launch_bounds__(kTileX* kTileY) transport_kernel(DeviceView v) {
-  transport_tile<P, G, PT>(v, blockIdx.x * kTileX, blockIdx.y * kTileY, blockIdx.y * gridDim.x + blockIdx.x);
+  transport_tile<P, G, PT>(v, blockIdx.x * kTileX, blockIdx.y * kTileY, blockIdx.y * gridDim.x + blockIdx.x,
+                           0, v.nb, 0);
 }
 
 // ------------------------------------------------------- FP32 fast-path math
@@ -766,21 +806,28 @@ __device__ __forceinline__ double drcp_nr(double x) {
 //   (1 - chi)/2 = (s - 1)/3   and   (3 chi - 1)/(2 f2) = (2 - s)/f2 = 3/(2 + s),
 // both free of cancellation at small f (where the printed 3 chi - 1 ~ 1.5 f2
 // loses every digit in FP32).  Dpp = (1 - chi)/2.
+//
+// The face flux and the closure are evaluated by several inlined copies (the
+// regular faces of each direction and the extra faces of a tile's edge), and a
+// face shared by two tiles must have one value whichever copy computes it.  So
+// every product and sum here is written with explicit rounding (fmaf for the
+// fused steps, __fmul_rn / __fadd_rn / __fsub_rn for the rest): the compiler
+// may not contract them, and each copy does the same operations.
 __device__ __forceinline__ void closure_f32q(float fn, float ft, float f2, float& Dnn, float& Dnt,
                                              float& Dtt, float& Dpp) {
-  const float y = 4.0f - 3.0f * f2;
-  const float s = y * rsqrtf(y);
-  const float dA = (s - 1.0f) * (1.0f / 3.0f);
-  const float g = 3.0f * frcp(2.0f + s);
-  Dnn = dA + g * (fn * fn);
-  Dnt = g * (fn * ft);
-  Dtt = dA + g * (ft * ft);
+  const float y = fmaf(-3.0f, f2, 4.0f);
+  const float s = __fmul_rn(y, rsqrtf(y));
+  const float dA = __fmul_rn(__fsub_rn(s, 1.0f), 1.0f / 3.0f);
+  const float g = __fmul_rn(3.0f, frcp(__fadd_rn(2.0f, s)));
+  Dnn = fmaf(g, __fmul_rn(fn, fn), dA);
+  Dnt = __fmul_rn(g, __fmul_rn(fn, ft));
+  Dtt = fmaf(g, __fmul_rn(ft, ft), dA);
   Dpp = dA;
 }
 
 __device__ __forceinline__ void closure_f32(float fn, float ft, float& Dnn, float& Dnt, float& Dtt,
                                             float& Dpp) {
-  closure_f32q(fn, ft, fn * fn + ft * ft, Dnn, Dnt, Dtt, Dpp);
+  closure_f32q(fn, ft, fmaf(fn, fn, __fmul_rn(ft, ft)), Dnn, Dnt, Dtt, Dpp);
 }
 
 __device__ __forceinline__ void closure_f32(float fn, float ft, float& Dnn, float& Dnt, float& Dtt) {
@@ -791,10 +838,10 @@ __device__ __forceinline__ void closure_f32(float fn, float ft, float& Dnn, floa
 // |f| > 1: scale to the unit circle (without a branch: the factor is
 // rsqrt(max(|f|^2, 1)), 1 for |f| <= 1); returns |f|^2 after the scaling
 __device__ __forceinline__ float cap_unit_f32(float& fn, float& ft) {
-  const float f2 = fn * fn + ft * ft;
+  const float f2 = fmaf(fn, fn, __fmul_rn(ft, ft));
   const float r = rsqrtf(fmaxf(f2, 1.0f));
-  fn *= r;
-  ft *= r;
+  fn = __fmul_rn(fn, r);
+  ft = __fmul_rn(ft, r);
   return fminf(f2, 1.0f);
 }
 
@@ -813,26 +860,32 @@ __device__ __forceinline__ void face_flux_f32(float Jm, float nm, float tm, floa
                                               float t0, float J1, float n1, float t1, float J2,
                                               float n2, float t2, float tau, float wf, float& oJ,
                                               float& oN, float& oT) {
-  const float d0 = J0 - Jm, d1 = J1 - J0, d2 = J2 - J1;
-  const float JL = J0 + 0.5f * minmod_f32(d0, d1), JR = J1 - 0.5f * minmod_f32(d1, d2);
-  const float e1 = n1 - n0, g1 = t1 - t0;
-  float nL = n0 + 0.5f * minmod_f32(n0 - nm, e1), tL = t0 + 0.5f * minmod_f32(t0 - tm, g1);
-  float nR = n1 - 0.5f * minmod_f32(e1, n2 - n1), tR = t1 - 0.5f * minmod_f32(g1, t2 - t1);
+  const float d0 = __fsub_rn(J0, Jm), d1 = __fsub_rn(J1, J0), d2 = __fsub_rn(J2, J1);
+  const float JL = fmaf(0.5f, minmod_f32(d0, d1), J0), JR = fmaf(-0.5f, minmod_f32(d1, d2), J1);
+  const float e1 = __fsub_rn(n1, n0), g1 = __fsub_rn(t1, t0);
+  float nL = fmaf(0.5f, minmod_f32(__fsub_rn(n0, nm), e1), n0);
+  float tL = fmaf(0.5f, minmod_f32(__fsub_rn(t0, tm), g1), t0);
+  float nR = fmaf(-0.5f, minmod_f32(e1, __fsub_rn(n2, n1)), n1);
+  float tR = fmaf(-0.5f, minmod_f32(g1, __fsub_rn(t2, t1)), t1);
   const float f2L = cap_unit_f32(nL, tL);
   const float f2R = cap_unit_f32(nR, tR);
-  const float HnL = JL * nL, HtL = JL * tL, HnR = JR * nR, HtR = JR * tR;
+  const float HnL = __fmul_rn(JL, nL), HtL = __fmul_rn(JL, tL);
+  const float HnR = __fmul_rn(JR, nR), HtR = __fmul_rn(JR, tR);
   float DnnL, DntL, DttL, DppL, DnnR, DntR, DttR, DppR;
   closure_f32q(nL, tL, f2L, DnnL, DntL, DttL, DppL);
   closure_f32q(nR, tR, f2R, DnnR, DntR, DttR, DppR);
-  const float a = 0.2f + tau;
-  const float rden = frcp(a + tau * tau);
-  const float eps = a * rden;
-  const float dcoef = tau * rden * (1.0f / 3.0f);
+  const float a = __fadd_rn(0.2f, tau);
+  const float rden = frcp(fmaf(tau, tau, a));
+  const float eps = __fmul_rn(a, rden);
+  const float dcoef = __fmul_rn(__fmul_rn(tau, rden), 1.0f / 3.0f);
   const bool up = wf > 0.0f;  // upwind donor: reconstructed state on the upwind side
   const float Jd = up ? JL : JR, Hnd = up ? HnL : HnR, Htd = up ? HtL : HtR;
-  oJ = 0.5f * eps * ((HnL + HnR) - (JR - JL)) - dcoef * d1 + wf * Jd;
-  oN = 0.5f * ((DnnL * JL + DnnR * JR) - eps * (HnR - HnL)) + wf * Hnd;
-  oT = 0.5f * ((DntL * JL + DntR * JR) - eps * (HtR - HtL)) + wf * Htd;
+  const float he = __fmul_rn(0.5f, eps);
+  oJ = fmaf(wf, Jd, fmaf(-dcoef, d1, __fmul_rn(he, __fsub_rn(__fadd_rn(HnL, HnR), __fsub_rn(JR, JL)))));
+  oN = fmaf(wf, Hnd,
+            __fmul_rn(0.5f, fmaf(-eps, __fsub_rn(HnR, HnL), fmaf(DnnL, JL, __fmul_rn(DnnR, JR)))));
+  oT = fmaf(wf, Htd,
+            __fmul_rn(0.5f, fmaf(-eps, __fsub_rn(HtR, HtL), fmaf(DntL, JL, __fmul_rn(DntR, JR)))));
 }
 
 // ------------------------------------------------ FP32 transport kernel
@@ -847,17 +900,20 @@ __device__ __forceinline__ void face_flux_f32(float Jm, float nm, float tm, floa
 // distances) of a thread's faces do not depend on the bin and stay in
 // registers.  The implicit source step runs in type I (FP64 for LYM1_MIXED,
 // FP32 for LYM1_MIXED_FAST).
-template <class P, int G, int PT>
-__device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, int y0, int blk) {
+template <class P, int G, int PT, int TS = 0>
+__device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, int y0, int blk,
+                                                   int k0, int k1, int grp) {
   // table mode (0 uniform T, 1 temperature field, 2 broad bands) and, in bit 4,
   // active-bin pruning: without it the tile compiles with no pruning code
   constexpr int TM = PT & 3;
   constexpr bool PR = (PT & 4) != 0;
+  // bit 8: step 2 is left to the subcycling kernel of the acceptance rule
+  constexpr bool DF = (PT & 8) != 0;
   using I = typename P::I;
-  constexpr int TX = kTileX, TY = kTileY, SX = TX + 4, SY = TY + 4;
+  constexpr int TX = TileShape<TS>::X, TY = TileShape<TS>::Y, SX = TX + 4, SY = TY + 4;
   constexpr int NT = TX * TY;
   static_assert(SX * SY <= 2 * NT, "two halo entries per thread at most");
-  static_assert(TX + TY == 32, "the extra faces are one warp's work");
+  static_assert(TX + TY <= 64, "the extra faces are the first two warps' work at most");
   __shared__ float4 sq[2][SY][SX];  // (J, f_x, f_y, alpha_F of the bin)
   __shared__ float sHx[2][SY][SX], sHy[2][SY][SX];
   // face fluxes (J, normal K, tangential K, -): x faces (J, K_xx, K_xy), y faces
@@ -919,15 +975,16 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
     bool fxg, fyg;
     const int ix = ghost<G>(x, nx, fxg), iy = ghost<G>(y, ny, fyg);
     const long long c = static_cast<long long>(iy) * nx + ix;
-    const float w = float(xdir ? v.ux[c] : v.uy[c]) * inv_c;
+    const float w = __fmul_rn(float(xdir ? v.ux[c] : v.uy[c]), inv_c);
     return (xdir ? fxg : fyg) ? -w : w;
   };
   const float wfx = 0.5f * (wcell(gx - 1, gy, true) + wcell(gx, gy, true));
   const float wfy = 0.5f * (wcell(gx, gy - 1, false) + wcell(gx, gy, false));
-  // the 32 extra faces are one evaluation by warp 0: lanes 0..TX-1 take the
-  // top row of y faces (fi = lane, fj = TY), lanes TX..31 the right column of
-  // x faces (fi = TX, fj = lane - TX)
-  const bool xtra = tid < 32;
+  // the TX + TY extra faces are one evaluation by the first threads (warp 0
+  // for 16 x 16): threads 0..TX-1 take the top row of y faces (fi = tid,
+  // fj = TY), threads TX..TX+TY-1 the right column of x faces (fi = TX,
+  // fj = tid - TX)
+  const bool xtra = tid < TX + TY;
   const bool xisx = tid >= TX;
   const int xfi = xisx ? TX : tid, xfj = xisx ? tid - TX : TY;
   float wf2 = 0.0f;
@@ -958,27 +1015,31 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
     rho_c = I(v.rho[cell]);
     pd_c = I(v.pd[cell]);
     lum_d = v.lum[cell];
-    gxx = float(v.gxx[cell]);
-    gyy = float(v.gyy[cell]);
-    gsh = float(v.gsh[cell]);
+    // velocity gradients times c_tilde dt / c: W below is then the step-1
+    // change of J itself, (c_tilde dt / c) D : grad u J, which stays in the
+    // FP32 range where J does (W / c alone is ~1e-20 J)
+    gxx = float(v.gxx[cell] * v.cdt_c);
+    gyy = float(v.gyy[cell] * v.cdt_c);
+    gsh = float(v.gsh[cell] * v.cdt_c);
     if constexpr (G == 1) {
-      gphi = float(v.gphi[cell]);
+      gphi = float(v.gphi[cell] * v.cdt_c);
       r0c = v.gf_r0[gx];
       r1c = v.gf_r1[gx];
       hoopc = v.gf_hoop[gx];
       wvf = v.gf_wv[gx];
     }
   }
-  const float cdt_f = float(v.cdt);
-  const float inv_dx = 1.0f / float(v.dx);
   const float cdt_dx = float(v.cdt_dx);
   const I cdt = I(v.cdt), kabs = I(v.kabs), kF = I(v.kF), cdx = I(v.cdt_dx);
   const I wR = I(v.g_wR), wcol = I(wvf);
   // LYM1_MIXED (FP64 implicit step): the per-cell factors with c_tilde dt
   // folded in, c dt kappa_k = cA + cB <H>_k and c dt alpha_F,k = cD + cC <H>_k
   // (bands: c dt kappa_k from their kappa table, alpha = 1, rho_d = 0)
-  constexpr bool MIX = sizeof(I) == 8;
+  constexpr bool MIX = sizeof(I) == 8 && !DF;
   double cA = 0.0, cB = 0.0, cC = 0.0, cD = 0.0, cjs = 0.0;
+  // emission of a uniform-temperature cell over this block's bins k0..k1-1:
+  // c dt L_cell sum_k dnu_k gem_k
+  double sgk = 0.0;
   if constexpr (MIX) {
     const double cd = v.cdt;
     cA = cd * (double(rho_c) * v.kabs);
@@ -986,6 +1047,9 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
     cC = cd * double(alpha_c);
     cD = cd * (double(rho_c) * v.kF);
     cjs = cd * lum_d;
+    if constexpr (TM == 0)
+      if (lum_d != 0.0)
+        for (int k = k0; k < k1; ++k) sgk = fma(v.t_dnu[k], v.t_gem[k], sgk);
   }
   I ax = 0, ay = 0;
   // per-cell bookkeeping sums over the bins: FP64 (compensation-free, exact
@@ -994,28 +1058,87 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
   I em = 0, ab = 0, out = 0, wk = 0, en = 0;
   float mxf2 = 0.0f;
   int bad = 0;
-  // emissivity j_k = (L_cell gem_max) (gem_k / gem_max): both factors lie in
-  // the FP32 range, unlike L_cell (~1e39 erg/s) and gem_k (~1e-58) alone
+  // source term c_tilde dt j_k = (c_tilde dt L_cell gem_max) (gem_k / gem_max):
+  // both factors lie in the FP32 range, unlike L_cell (~1e39 erg/s) and gem_k
+  // (~1e-75) alone, or j_k itself in the far wings (~1e-38)
   const bool src = lum_d != 0.0;
   const double gmax_c = TM ? (valid ? v.gmaxc[cell] : 1.0) : v.gem_max;
-  const float jsc = float(lum_d * gmax_c);
+  const float cjsc = float(v.cdt * (lum_d * gmax_c));
   const bool bnd = valid && (G == 1 ? (gx == nx - 1 || gy == ny - 1)
                                      : (gx == 0 || gx == nx - 1 || gy == 0 || gy == ny - 1));
 
-  float pJ0 = Jin[off0], pX0 = Hxin[off0], pY0 = Hyin[off0];
+  long long base = static_cast<long long>(k0) * nc;  // k * nc
+  float pJ0 = Jin[base + off0], pX0 = Hxin[base + off0], pY0 = Hyin[base + off0];
   float pJ1 = 0.f, pX1 = 0.f, pY1 = 0.f;
   float pH0 = 0.f, pH1 = 0.f;  // <H>_k of the halo entries (temperature field)
   if (has1) {
-    pJ1 = Jin[off1];
-    pX1 = Hxin[off1];
-    pY1 = Hyin[off1];
+    pJ1 = Jin[base + off1];
+    pX1 = Hxin[base + off1];
+    pY1 = Hyin[base + off1];
   }
   if constexpr (TM) {
-    pH0 = Hcf[off0];
-    if (has1) pH1 = Hcf[off1];
+    pH0 = Hcf[base + off0];
+    if (has1) pH1 = Hcf[base + off1];
   }
-  long long base = 0;  // k * nc
-  for (int k = 0; k < nb; ++k) {
+  // LYM1_MIXED: the FP64 implicit step of bin k - 1 (Sec. 2.1 step 2) is
+  // issued in the face phase of bin k, so that GB300's narrow FP64 pipe works
+  // while the FP32 face fluxes are formed; pending values of the last bin are
+  // finished after the loop.  live = false on the first pass (nothing pending):
+  // the arithmetic runs on zeros and nothing is stored or summed.
+  float dJ1 = 0.0f, dHx1 = 0.0f, dHy1 = 0.0f, dW = 0.0f;
+  auto step2_mix = [&](bool live, int kk, long long kbase) {
+    if constexpr (MIX) {
+      // one shared reciprocal: r = 1 / (d1 d2) gives 1/d1 = d2 r and
+      // 1/d2 = d1 r, with d1 = 1 + c dt kappa_k and d2 = 1 + c dt alpha_F,k
+      const double Hd = TM ? f2d_alu(Hcf[kbase + cell]) : v.t_H[kk];
+      const double dnud = v.t_dnu[kk];
+      double ck;
+      if constexpr (TM == 2)
+        ck = v.cdt * f2d_alu(Kbf[kbase + cell]);
+      else
+        ck = fma(cB, Hd, cA);
+      const double caF = fma(cC, Hd, cD);
+      const double d1 = 1.0 + ck, d2 = 1.0 + caF;
+      const double rp = drcp_nr(d1 * d2);
+      const double ra = d1 * rp;
+      double num = f2d_alu(dJ1);
+      double gk = 0.0;
+      if (src) {
+        gk = TM ? gmax_c * f2d_alu(Gcf[kbase + cell]) : v.t_gem[kk];
+        num = fma(cjs, gk, num);
+      }
+      const double J2d = num * (d2 * rp);
+      const float J2 = d2f_alu(J2d);
+      // H'' = H' / d2 with the FP64 factor (H is FP32 state); the force term
+      // dnu_k (H' - H'') = dnu_k (c dt alpha_F / d2) H' has no cancellation
+      const float raf = d2f_alu(ra);
+      const float Hx2 = dHx1 * raf, Hy2 = dHy1 * raf;
+      if (live && valid) {
+        (Jout + kbase)[cell32] = J2;
+        (Hxout + kbase)[cell32] = Hx2;
+        (Hyout + kbase)[cell32] = Hy2;
+      }
+      const float wq = tab4[kk].y * d2f_alu(caF * ra);  // dnu_k c dt alpha_F / d2
+      const double tx = f2d_alu(wq * dHx1), ty2 = f2d_alu(wq * dHy1);
+      // A7 bookkeeping in FP64 (c_tilde dt is in ck; 1/c and the energy units
+      // once per substep)
+      const double twk = f2d_alu(tab4[kk].y * dW);
+      ax = live ? ax + tx : ax;
+      ay = live ? ay + ty2 : ay;
+      ab = fma(live ? dnud * ck : 0.0, J2d, ab);
+      wk = live ? wk + twk : wk;
+      if constexpr (TM != 0) em = live ? fma(dnud, gk, em) : em;
+      if (tdiag && live) {  // the frequency step recomputes these when it follows
+        en = fma(dnud, J2d, en);
+        const float h2 = Hx2 * Hx2 + Hy2 * Hy2, jj = J2 * J2;
+        if ((G == 1 ? J2 * wvf : J2) > tab4[kk].w) {
+          mxf2 = fmaxf(mxf2, fdiv(h2, jj));
+          bad += (h2 > jj * 1.000002f) ? 1 : 0;
+        }
+      }
+    }
+  };
+  for (int k = k0; k < k1; ++k) {
     const int b = k & 1;
     const float4 tb = tab4[k];  // (<H>_k, dnu_k, gem_k / gem_max, J_act,k)
     const float Hk = tb.x;
@@ -1044,7 +1167,7 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
       }
     }
     const long long nbase = base + nc;
-    if (k + 1 < nb) {  // prefetch bin k+1
+    if (k + 1 < k1) {  // prefetch bin k+1
       const float* Jn = Jin + nbase;
       const float* Xn = Hxin + nbase;
       const float* Yn = Hyin + nbase;
@@ -1062,12 +1185,14 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
       }
     }
     __syncthreads();
+    if constexpr (MIX) step2_mix(k > k0, k > k0 ? k - 1 : k0, k > k0 ? base - nc : base);
     auto xface = [&](int fi, int fj, float wf, float dl0, float dl1) {
       // between tile cells (fi-1, fj) and (fi, fj)
       const int r = fj + 2;
       const float4 qm = sq[b][r][fi], q0 = sq[b][r][fi + 1], q1 = sq[b][r][fi + 2],
                    q2 = sq[b][r][fi + 3];
-      const float tau = (G == 1) ? q0.w * dl0 + q1.w * dl1 : (q0.w + q1.w) * dl0;
+      const float tau = (G == 1) ? fmaf(q0.w, dl0, __fmul_rn(q1.w, dl1))
+                                 : __fmul_rn(__fadd_rn(q0.w, q1.w), dl0);
       float oJ, oN, oT;
       face_flux_f32(qm.x, qm.y, qm.z, q0.x, q0.y, q0.z, q1.x, q1.y, q1.z, q2.x, q2.y, q2.z, tau,
                     wf, oJ, oN, oT);
@@ -1079,7 +1204,7 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
                    q2 = sq[b][fj + 3][cc];
       float oJ, oN, oT;
       face_flux_f32(qm.x, qm.z, qm.y, q0.x, q0.z, q0.y, q1.x, q1.z, q1.y, q2.x, q2.z, q2.y,
-                    (q0.w + q1.w) * half_dx, wf, oJ, oN, oT);
+                    __fmul_rn(__fadd_rn(q0.w, q1.w), half_dx), wf, oJ, oN, oT);
       yF[fj][fi] = make_float4(oJ, oN, oT, 0.0f);
     };
     if (on) {
@@ -1089,7 +1214,10 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
         const float4* q = xisx ? &sq[b][xfj + 2][xfi] : &sq[b][xfj][xfi + 2];
         const int st = xisx ? 1 : SX;
         const float4 qm = q[0], q0 = q[st], q1 = q[2 * st], q2 = q[3 * st];
-        const float tau = q0.w * dlB0 + q1.w * dlB1;
+        // the same expression as the regular faces, so that a face shared by
+        // two tiles has one value whichever tile evaluates it
+        const float tau = (G == 1 && xisx) ? fmaf(q0.w, dlB0, __fmul_rn(q1.w, dlB1))
+                                           : __fmul_rn(__fadd_rn(q0.w, q1.w), half_dx);
         float oJ, oN, oT;
         face_flux_f32(qm.x, xisx ? qm.y : qm.z, xisx ? qm.z : qm.y, q0.x, xisx ? q0.y : q0.z,
                       xisx ? q0.z : q0.y, q1.x, xisx ? q1.y : q1.z, xisx ? q1.z : q1.y, q2.x,
@@ -1127,61 +1255,30 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
         divHy = (xr.z - xl.z) + (yt.y - yb.y);
       }
       if (!on) W = 0.0f;  // pruned bin: no step 1
-      const float J1 = on ? J - cdt_f * (divJ * inv_dx + W * inv_c) : J;
+      // c_tilde dt / dx folded into one factor: divJ / dx alone leaves the
+      // FP32 range for J below ~1e-22
+      const float J1 = on ? J - fmaf(cdt_dx, divJ, W) : J;
       const float Hx1 = on ? Hx - cdt_dx * divHx : Hx;
       const float Hy1 = on ? Hy - cdt_dx * divHy : Hy;
-      if constexpr (MIX) {
-        // FP64 implicit step (Sec. 2.1 step 2) with one shared reciprocal:
-        // r = 1 / (d1 d2) gives 1/d1 = d2 r and 1/d2 = d1 r, with
-        // d1 = 1 + c dt kappa_k and d2 = 1 + c dt alpha_F,k
-        const double Hd = TM ? f2d_alu(Hcf[base + cell]) : v.t_H[k];
-        const double dnud = v.t_dnu[k];
-        double ck;
-        if constexpr (TM == 2)
-          ck = v.cdt * f2d_alu(Kbf[base + cell]);
-        else
-          ck = fma(cB, Hd, cA);
-        const double caF = fma(cC, Hd, cD);
-        const double d1 = 1.0 + ck, d2 = 1.0 + caF;
-        const double rp = drcp_nr(d1 * d2);
-        const double ra = d1 * rp;
-        double num = f2d_alu(J1);
-        if (src) {
-          const double gk = TM ? gmax_c * f2d_alu(Gcf[base + cell]) : v.t_gem[k];
-          num = fma(cjs, gk, num);
-          if constexpr (TM != 0) em = fma(dnud, gk, em);
-        }
-        const double J2d = num * (d2 * rp);
-        const float J2 = d2f_alu(J2d);
-        // H'' = H' / d2 with the FP64 factor (H is FP32 state); the force term
-        // dnu_k (H' - H'') = dnu_k (c dt alpha_F / d2) H' has no cancellation
-        const float raf = d2f_alu(ra);
-        const float Hx2 = Hx1 * raf, Hy2 = Hy1 * raf;
-        (Jout + base)[cell32] = J2;
-        (Hxout + base)[cell32] = Hx2;
-        (Hyout + base)[cell32] = Hy2;
-        const float wq = d2f_alu(dnud * (caF * ra));
-        ax += f2d_alu(wq * Hx1);
-        ay += f2d_alu(wq * Hy1);
-        // A7 bookkeeping in FP64 (c_tilde dt is in ck; 1/c and the energy
-        // units once per substep)
-        ab = fma(dnud * ck, J2d, ab);
-        wk += f2d_alu(tb.y * W);
-        if (tdiag) {  // the frequency step recomputes these when it follows
-          en = fma(dnud, J2d, en);
-          const float h2 = Hx2 * Hx2 + Hy2 * Hy2, jj = J2 * J2;
-          if ((G == 1 ? J2 * wvf : J2) > tb.w) {
-            mxf2 = fmaxf(mxf2, fdiv(h2, jj));
-            bad += (h2 > jj * 1.000002f) ? 1 : 0;
-          }
-        }
+      if constexpr (DF) {  // step 2 follows in the subcycling kernel
+        (Jout + base)[cell32] = J1;
+        (Hxout + base)[cell32] = Hx1;
+        (Hyout + base)[cell32] = Hy1;
+        wk += I(tb.y * W);
+      } else if constexpr (MIX) {
+        // the FP64 step of this bin runs in the face phase of the next bin
+        dJ1 = J1;
+        dHx1 = Hx1;
+        dHy1 = Hy1;
+        dW = W;
       } else {
         const float aH = alpha_c * (TM ? Hcf[base + cell] : Hk);
         const float dnu = tb.y;
         const float kap = (TM == 2) ? Kbf[base + cell] : rho_c * kabs + pd_c * aH;
         const float aF = aH + rho_c * kF;
-        const float js = src ? jsc * (TM ? Gcf[base + cell] : tb.z) : 0.0f;
-        const float J2 = (J1 + cdt * js) * frcp(1.0f + cdt * kap);
+        const float cjk = src ? cjsc * (TM ? Gcf[base + cell] : tb.z) : 0.0f;
+        const float ckap = cdt * kap;  // c_tilde dt kappa_k
+        const float J2 = (J1 + cjk) * frcp(1.0f + ckap);
         const float ra = frcp(1.0f + cdt * aF);
         const float Hx2 = Hx1 * ra, Hy2 = Hy1 * ra;
         (Jout + base)[cell32] = J2;
@@ -1191,8 +1288,8 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
         ay += dnu * (Hy1 - Hy2);
         // A7 bookkeeping (energy units applied once per substep; the factors
         // c_tilde dt and 1/c once per cell after the bin loop)
-        if (src) em += dnu * js;
-        ab += dnu * (kap * J2);
+        if (src) em += dnu * cjk;
+        ab += dnu * (ckap * J2);
         wk += dnu * W;
         if (tdiag) {  // the frequency step recomputes these when it follows
           en += dnu * J2;
@@ -1203,7 +1300,7 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
           }
         }
       }
-      const I dnu = MIX ? I(v.t_dnu[k]) : I(tb.y);
+      const I dnu = sizeof(I) == 8 ? I(v.t_dnu[k]) : I(tb.y);
       if (bnd) {
         I o2 = 0;
         if constexpr (G == 1) {
@@ -1234,10 +1331,8 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
     }
     base = nbase;
   }
-  if (valid) {
-    v.fx[cell] = v.fcoef * double(ax);
-    v.fy[cell] = v.fcoef * double(ay);
-  }
+  if constexpr (MIX) step2_mix(k1 > k0, k1 - 1, base - nc);
+  if (valid && !DF) store_force(v, cell, grp, double(ax), double(ay));
   double* part = v.partT + static_cast<long long>(blk) * kDiagSlots;
   double s;
   if constexpr (sizeof(I) == 4) {
@@ -1245,14 +1340,14 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
     // (~1/60 of the FP32 rate) except for the last eight-term sum
     const float wf = G == 1 ? wvf : 1.0f;
     s = block_sum_f32<NT>(em * wf, red);
-    if (tid == 0) part[kSlotEmitted] = s * v.cdt;
+    if (tid == 0) part[kSlotEmitted] = s;
     s = block_sum_f32<NT>(ab * wf, red);
-    if (tid == 0) part[kSlotAbsorbed] = s * v.cdt;
+    if (tid == 0) part[kSlotAbsorbed] = s;
     s = block_sum_f32<NT>(out, red);
     if (tid == 0) part[kSlotOutflow] = s;
     s = block_sum_f32<NT>(wk * wf, red);
-    if (tid == 0) part[kSlotWork] = s * v.cdt_c;
-    if (tdiag) {
+    if (tid == 0) part[kSlotWork] = s;
+    if (tdiag && !DF) {
       s = block_sum_f32<NT>(en * wf, red);
       if (tid == 0) part[kSlotEnergy] = s;
       int b = bad;
@@ -1279,15 +1374,15 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
     // FP64 sums (LYM1_MIXED): c_tilde dt is already in ab; the emission of a
     // uniform-temperature cell is c dt L_cell sum_k dnu_k gem_k
     const double wd = G == 1 ? double(wvf) : 1.0;
-    s = block_sum<NT>((cjs * (TM ? double(em) : v.sg)) * wd, red);
+    s = block_sum<NT>((cjs * (TM ? double(em) : sgk)) * wd, red);
     if (tid == 0) part[kSlotEmitted] = s;
     s = block_sum<NT>(double(ab) * wd, red);
     if (tid == 0) part[kSlotAbsorbed] = s;
     s = block_sum<NT>(double(out), red);
     if (tid == 0) part[kSlotOutflow] = s;
-    s = block_sum<NT>(double(wk) * (v.cdt_c * wd), red);
+    s = block_sum<NT>(double(wk) * wd, red);
     if (tid == 0) part[kSlotWork] = s;
-    if (tdiag) {
+    if (tdiag && !DF) {
       s = block_sum<NT>(double(en) * wd, red);
       if (tid == 0) part[kSlotEnergy] = s;
       s = block_max<NT>(sqrt(double(mxf2)), red);
@@ -1309,7 +1404,7 @@ __host__ __device__ constexpr int tile_f32_min_blocks() {
 template <class P, int G, int PT>
 __global__ void __launch_bounds__(kTileX* kTileY, tile_f32_min_blocks<P>()) transport_kernel_f32(DeviceView v) {
   transport_tile_f32<P, G, PT>(v, blockIdx.x * kTileX, blockIdx.y * kTileY,
-                           blockIdx.y * gridDim.x + blockIdx.x);
+                               blockIdx.y * gridDim.x + blockIdx.x, 0, v.nb, 0);
 }
 
 // ------------------------------------------------------------ frequency kernel
@@ -1338,6 +1433,19 @@ __device__ __forceinline__ typename P::I rcp_elim(typename P::I x) {
   else if constexpr (freq_mix<P>()) return drcp_nr(x);
   else return I(1) / x;
 }
+// Exponential of the frequency-step coefficients: the FP64 policies' own
+// (LYM1_FP64_DET) or library exp; FP32 coefficients take the accurate expf
+// under LYM1_MIXED, whose frequency kernel is bound by its FP64 elimination
+// (the FP32 pipe has room), and the fast __expf under LYM1_MIXED_FAST.  The
+// approximate exponential's error grows with |x|, and the Peclet numbers of
+// the line wings reach |P| ~ 1e3-1e5.
+template <class P>
+__device__ __forceinline__ typename P::F fexp(typename P::F x) {
+  if constexpr (sizeof(typename P::F) == 8) return m_exp<P::DET>(x);
+  else if constexpr (sizeof(typename P::I) == 8) return expf(x);
+  else return __expf(x);
+}
+
 // The causality cap and the FP32 realisability statistics (max |H|^2 / J^2
 // and the count of |H| > J) of the (cell, bin) pairs whose weighted J is above thr
 __device__ __forceinline__ void causal_stats_f32(float J, float& Hx, float& Hy, float wf, float thr,
@@ -1381,7 +1489,7 @@ __device__ __forceinline__ void freq_coef(typename P::F Jc, typename P::F Hxc, t
     // most a factor 2.5 of e^z's relative error
     const float poly =
         1.0f + z * (0.5f + z * (1.0f / 6 + z * (1.0f / 24 + z * (1.0f / 120 + z * (1.0f / 720 + z * (1.0f / 5040))))));
-    ek = (z > -0.5f) ? poly : (__expf(z) - 1.0f) * frcp(z);
+    ek = (z > -0.5f) ? poly : (fexp<P>(z) - 1.0f) * frcp(z);
   } else {
     F fx = F(0), fy = F(0);
     if (Jc > F(0)) {
@@ -1499,6 +1607,7 @@ __device__ __forceinline__ void freq_block(const DeviceView& v, int blk) {
   const I wI = I(wcell);
   const float wf = float(wcell);
   if (cell < nc) {
+    combine_force_groups(v, cell);
     const double alpha = v.alpha[cell];
     if (v.freq_step && alpha > 0.0) {
       const F Kc = PT ? F(v.Kcc[cell] * alpha) : F(v.Kc * alpha);
@@ -1557,18 +1666,18 @@ __device__ __forceinline__ void freq_block(const DeviceView& v, int blk) {
           const F d1 = (-P0 > F(0)) ? -P0 : F(0);
           const F d2 = (P1 > F(0)) ? P1 : F(0);
           const F m = (d1 > d2) ? d1 : d2;
-          const F den = m_exp<P::DET>(d1 - m) * (e0 * a0) + m_exp<P::DET>(d2 - m) * (e1 * a1);
+          const F den = fexp<P>(d1 - m) * (e0 * a0) + fexp<P>(d2 - m) * (e1 * a1);
           if constexpr (sizeof(F) == 4) {
             const float rden = frcp(den);
-            A = to_elim<P>(m_exp<P::DET>(-P0 - m) * rden);
-            B = to_elim<P>(m_exp<P::DET>(P1 - m) * rden);
+            A = to_elim<P>(fexp<P>(-P0 - m) * rden);
+            B = to_elim<P>(fexp<P>(P1 - m) * rden);
           } else if constexpr (P::DET) {
-            A = I(m_exp<P::DET>(-P0 - m) / den);
-            B = I(m_exp<P::DET>(P1 - m) / den);
+            A = I(fexp<P>(-P0 - m) / den);
+            B = I(fexp<P>(P1 - m) / den);
           } else {
             const F rden = F(1) / den;
-            A = I(m_exp<P::DET>(-P0 - m) * rden);
-            B = I(m_exp<P::DET>(P1 - m) * rden);
+            A = I(fexp<P>(-P0 - m) * rden);
+            B = I(fexp<P>(P1 - m) * rden);
           }
         }
         I s;
@@ -1833,6 +1942,7 @@ __device__ __forceinline__ void freq_block_bulk(const DeviceView& v, int blk) {
   const I cdt = I(v.cdt);
   const float rcdt = float(1.0 / v.cdt);
   (void)rcdt;
+  if (valid) combine_force_groups(v, cell);
 
   auto issue_fwd = [&](int k) {
     const int s = k % D;
@@ -1892,10 +2002,10 @@ __device__ __forceinline__ void freq_block_bulk(const DeviceView& v, int blk) {
         const F d1 = (-Pp > F(0)) ? -Pp : F(0);
         const F d2 = (Pk > F(0)) ? Pk : F(0);
         const F m = (d1 > d2) ? d1 : d2;
-        const F den = m_exp<P::DET>(d1 - m) * (ep * ap) + m_exp<P::DET>(d2 - m) * (ek * ak);
+        const F den = fexp<P>(d1 - m) * (ep * ap) + fexp<P>(d2 - m) * (ek * ak);
         const float rden = frcp(den);
-        const I A = to_elim<P>(m_exp<P::DET>(-Pp - m) * rden);
-        const I B = to_elim<P>(m_exp<P::DET>(Pk - m) * rden);
+        const I A = to_elim<P>(fexp<P>(-Pp - m) * rden);
+        const I B = to_elim<P>(fexp<P>(Pk - m) * rden);
         // row k-1
         I sk;
         if constexpr (sizeof(I) == 4)
@@ -2053,6 +2163,150 @@ __global__ void __launch_bounds__(kFreqThreads, sizeof(typename P::S) == 4 ? (si
   freq_dispatch<P, G, PT>(v, blockIdx.x);
 }
 
+// ---------------------------------------- step 2 under the acceptance rule
+// Sec. 2.1 step 2 and its footnote: every cell subcycles its implicit
+// emission/absorption update.  A trial substep is accepted when the cell's
+// Lya energy density changes by |e'' - e'| / (e' + e_floor) < 0.1 (e_floor =
+// 4 pi J_floor / c, J_floor = 1e-15 erg cm^-2 s^-1 sr^-1); otherwise it is
+// halved and redone, until the accepted substeps fill the RT step.  Where the
+// paper gives only the halving: every cell starts with the whole step, an
+// accepted substep doubles the next trial (capped by what is left),
+// substeps are whole multiples of dt / 2^kSubLevels, one of that size is
+// accepted whatever the change, and once a cell has made kSubMaxTrials trials
+// every further trial is accepted (a bound on the loop that finite inputs do
+// not reach).  One thread per cell, in place on the post-transport state (the
+// view's input arrays, which the frequency step then reads); the force, the
+// emission and the absorption add up over the accepted substeps.  The
+// decision is taken in FP64 for every policy, the updates in the policy's
+// implicit type, with the operations in the order written (bit for bit the
+// oracle's under LYM1_FP64_DET).  Partial sums go to the frequency-step
+// partials of the same 128-cell block: emitted and absorbed, and, without a
+// frequency step, the energy and realisability slots.
+constexpr int kSubLevels = 40;
+constexpr int kSubMaxTrials = 1 << 16;
+constexpr double kJFloor = 1e-15;
+
+template <class P, int G, int TM>
+__device__ __forceinline__ void subcycle_block(const DeviceView& v, int blk) {
+  using S = typename P::S;
+  using I = typename P::I;
+  constexpr int NT = kFreqThreads;
+  __shared__ double red[NT / 32];
+  S* __restrict__ Js = static_cast<S*>(const_cast<void*>(v.J));
+  S* __restrict__ Hxs = static_cast<S*>(const_cast<void*>(v.Hx));
+  S* __restrict__ Hys = static_cast<S*>(const_cast<void*>(v.Hy));
+  const S* __restrict__ Hcs = static_cast<const S*>(v.Hc);
+  const S* __restrict__ Gcs = static_cast<const S*>(v.Gc);
+  const int nb = v.nb;
+  const long long nc = v.nc;
+  const long long cell = static_cast<long long>(blk) * NT + threadIdx.x;
+  const bool valid = cell < nc;
+  double wcell = 1.0;
+  if constexpr (G == 1)
+    if (valid) wcell = v.g_wv[cell % v.nx];
+  I em = I(0), ab = I(0), ax = I(0), ay = I(0);
+  double en = 0.0, mxf = 0.0, bad = 0.0;
+  if (valid) {
+    const I alpha = I(v.alpha[cell]), rho = I(v.rho[cell]), pd = I(v.pd[cell]);
+    const I kabs = I(v.kabs), kF = I(v.kF);
+    const double lum = v.lum[cell];
+    // temperature field with FP32 state: the emission factors are stored over
+    // the cell's maximum
+    const double gmc = (TM && sizeof(S) == 4) ? v.gmaxc[cell] : 1.0;
+    // FP32 implicit type: the source term c_tilde h j_k is formed in FP64 and
+    // rounded once (j_k alone falls below the FP32 range in the far wings), and
+    // the absorption sum takes c_tilde h kappa_k J'' (kappa_k J'' alone can)
+    constexpr bool F32 = sizeof(I) == 4;
+    auto coef = [&](int k, long long o, double chd, I& kap, I& aF, I& js) {
+      const I Hk = TM ? I(Hcs[o]) : I(v.t_H[k]);
+      const I aH = alpha * Hk;
+      kap = rho * kabs + pd * aH;
+      aF = aH + rho * kF;
+      const double jd = lum != 0.0 ? lum * (TM ? gmc * double(Gcs[o]) : v.t_gem[k]) : 0.0;
+      js = F32 ? I(chd * jd) : I(jd);
+    };
+    const long long full = 1LL << kSubLevels;
+    long long done = 0, size = full;
+    double e_cur = 0.0;
+    for (int k = 0; k < nb; ++k)
+      e_cur = e_cur + v.t_dnu[k] * double(Js[static_cast<long long>(k) * nc + cell]);
+    int trials = 0;
+    while (done < full) {
+      if (size > full - done) size = full - done;
+      const double h = v.dt * (double(size) / double(full));
+      const double chd = v.ct * h;
+      const I ch = I(chd);
+      ++trials;
+      double e_new = 0.0;
+      for (int k = 0; k < nb; ++k) {
+        const long long o = static_cast<long long>(k) * nc + cell;
+        I kap, aF, js;
+        coef(k, o, chd, kap, aF, js);
+        const I Jt = F32 ? (I(Js[o]) + js) / (I(1) + ch * kap)
+                         : (I(Js[o]) + ch * js) / (I(1) + ch * kap);
+        e_new = e_new + v.t_dnu[k] * double(Jt);
+      }
+      const double change = fabs(e_new - e_cur) / (e_cur + kJFloor);
+      if (!(change < 0.1) && size > 1 && trials <= kSubMaxTrials) {
+        size = size / 2;
+        continue;
+      }
+      for (int k = 0; k < nb; ++k) {
+        const long long o = static_cast<long long>(k) * nc + cell;
+        I kap, aF, js;
+        coef(k, o, chd, kap, aF, js);
+        const I J2 = F32 ? (I(Js[o]) + js) / (I(1) + ch * kap)
+                         : (I(Js[o]) + ch * js) / (I(1) + ch * kap);
+        const I hx = I(Hxs[o]), hy = I(Hys[o]);
+        const I Hx2 = hx / (I(1) + ch * aF);
+        const I Hy2 = hy / (I(1) + ch * aF);
+        const I dnu = I(v.t_dnu[k]);
+        ax = ax + dnu * (hx - Hx2);
+        ay = ay + dnu * (hy - Hy2);
+        em = em + dnu * (F32 ? js : ch * js);
+        ab = ab + dnu * (F32 ? (ch * kap) * J2 : ch * (kap * J2));
+        Js[o] = S(J2);
+        Hxs[o] = S(Hx2);
+        Hys[o] = S(Hy2);
+      }
+      e_cur = e_new;
+      done += size;
+      size = size * 2;
+    }
+    v.fx[cell] = v.fcoef * double(ax);
+    v.fy[cell] = v.fcoef * double(ay);
+    if (v.tdiag) {  // no frequency step follows: the energy and realisability here
+      for (int k = 0; k < nb; ++k) {
+        const long long o = static_cast<long long>(k) * nc + cell;
+        const double J = double(Js[o]), hx = double(Hxs[o]), hy = double(Hys[o]);
+        en = en + v.t_dnu[k] * J;
+        const double hn = sqrt(hx * hx + hy * hy);
+        if (J > 0.0) mxf = fmax(mxf, hn / J);
+        if (hn > J * 1.000001 && hn > 0.0) bad += 1.0;
+      }
+    }
+  }
+  double* part = v.partF + static_cast<long long>(blk) * kDiagSlots;
+  double s;
+  s = block_sum<NT>(double(em) * wcell, red);
+  if (threadIdx.x == 0) part[kSlotEmitted] = s;
+  s = block_sum<NT>(double(ab) * wcell, red);
+  if (threadIdx.x == 0) part[kSlotAbsorbed] = s;
+  if (v.tdiag) {
+    s = block_sum<NT>(en * wcell, red);
+    if (threadIdx.x == 0) part[kSlotEnergy] = s;
+    s = block_max<NT>(mxf, red);
+    if (threadIdx.x == 0) part[kSlotMaxF] = s;
+    s = block_sum<NT>(bad, red);
+    if (threadIdx.x == 0) part[kSlotBad] = s;
+  }
+}
+
+template <class P, int G, int TM>
+__global__ void __launch_bounds__(kFreqThreads) subcycle_kernel(DeviceView v) {
+  subcycle_block<P, G, TM>(v, blockIdx.x);
+}
+
 // ------------------------------------------------------------ batched launches
 // Persistent kernels over a work list that spans several contexts (clouds of
 // different sizes, one geometry and temperature mode): each item names a
@@ -2060,27 +2314,27 @@ __global__ void __launch_bounds__(kFreqThreads, sizeof(typename P::S) == 4 ? (si
 // walk the list with a grid stride.
 struct BatchItem {
   int ctx, x0, y0, blk;
+  int k0, k1, grp;  // transport: the bins of this item and its bin group
 };
 
-template <class P, int G, int PT>
-__global__ void __launch_bounds__(kTileX* kTileY) transport_batched(const DeviceView* views,
-                                                                    const BatchItem* items, int n) {
+template <class P, int G, int PT, int TS>
+__global__ void __launch_bounds__(TileShape<TS>::X* TileShape<TS>::Y) transport_batched(
+    const DeviceView* views, const BatchItem* items, int n) {
   for (int i = blockIdx.x; i < n; i += gridDim.x) {
     const BatchItem it = items[i];
     const DeviceView v = views[it.ctx];
-    transport_tile<P, G, PT>(v, it.x0, it.y0, it.blk);
+    transport_tile<P, G, PT, TS>(v, it.x0, it.y0, it.blk, it.k0, it.k1, it.grp);
     __syncthreads();
   }
 }
 
-template <class P, int G, int PT>
-__global__ void __launch_bounds__(kTileX* kTileY, tile_f32_min_blocks<P>()) transport_batched_f32(const DeviceView* views,
-                                                                           const BatchItem* items,
-                                                                           int n) {
+template <class P, int G, int PT, int TS>
+__global__ void __launch_bounds__(TileShape<TS>::X* TileShape<TS>::Y, tile_f32_min_blocks<P>())
+    transport_batched_f32(const DeviceView* views, const BatchItem* items, int n) {
   for (int i = blockIdx.x; i < n; i += gridDim.x) {
     const BatchItem it = items[i];
     const DeviceView v = views[it.ctx];
-    transport_tile_f32<P, G, PT>(v, it.x0, it.y0, it.blk);
+    transport_tile_f32<P, G, PT, TS>(v, it.x0, it.y0, it.blk, it.k0, it.k1, it.grp);
     __syncthreads();
   }
 }
@@ -2096,16 +2350,38 @@ __global__ void __launch_bounds__(kFreqThreads, sizeof(typename P::S) == 4 ? (si
   }
 }
 
-template <class P, int G, int PT>
-int launch_transport_batched_g(const DeviceView* views, const BatchItem* items, int n, int grid,
+template <class P, int G, int TM>
+__global__ void __launch_bounds__(kFreqThreads) subcycle_batched(const DeviceView* views,
+                                                                 const BatchItem* items, int n) {
+  for (int i = blockIdx.x; i < n; i += gridDim.x) {
+    const BatchItem it = items[i];
+    const DeviceView v = views[it.ctx];
+    subcycle_block<P, G, TM>(v, it.blk);
+    __syncthreads();
+  }
+}
+
+template <class P, int G, int PT, int TS>
+int launch_transport_batched_s(const DeviceView* views, const BatchItem* items, int n, int grid,
                                int nb_max, cudaStream_t st) {
+  const dim3 block(TileShape<TS>::X, TileShape<TS>::Y);
   if constexpr (sizeof(typename P::S) == 4) {
     const size_t smem = sizeof(float) * 4 * static_cast<size_t>(nb_max);
-    transport_batched_f32<P, G, PT><<<grid, dim3(kTileX, kTileY), smem, st>>>(views, items, n);
+    transport_batched_f32<P, G, PT, TS><<<grid, block, smem, st>>>(views, items, n);
   } else {
-    transport_batched<P, G, PT><<<grid, dim3(kTileX, kTileY), 0, st>>>(views, items, n);
+    transport_batched<P, G, PT, TS><<<grid, block, 0, st>>>(views, items, n);
   }
   return static_cast<int>(cudaGetLastError());
+}
+
+// tile shape 1 is instantiated for the plain table modes only (0, 1)
+template <class P, int G, int PT>
+int launch_transport_batched_g(const DeviceView* views, const BatchItem* items, int n, int grid,
+                               int nb_max, cudaStream_t st, int shape) {
+  if constexpr (PT == 0 || PT == 1)
+    if (shape == 1) return launch_transport_batched_s<P, G, PT, 1>(views, items, n, grid, nb_max, st);
+  if (shape != 0) return static_cast<int>(cudaErrorInvalidValue);
+  return launch_transport_batched_s<P, G, PT, 0>(views, items, n, grid, nb_max, st);
 }
 
 template <class P, int G, int PT>
@@ -2118,9 +2394,14 @@ int launch_freq_batched_g(const DeviceView* views, const BatchItem* items, int n
 
 // (geometry, temperature mode) -> template instance
 // transport: pt & 3 = 0 uniform temperature, 1 temperature field, 2 broad
-// bands; pt & 4 = active-bin pruning
+// bands; pt & 4 = active-bin pruning; pt & 8 = step 2 left to the subcycling
+// kernel of the acceptance rule (Lya only: not with broad bands)
 #define LYM1_PT_(F_, G_, ...)                                                   \
-  (pt == 6   ? F_<P, G_, 6>(__VA_ARGS__)                                        \
+  (pt == 13  ? F_<P, G_, 13>(__VA_ARGS__)                                       \
+   : pt == 12 ? F_<P, G_, 12>(__VA_ARGS__)                                      \
+   : pt == 9 ? F_<P, G_, 9>(__VA_ARGS__)                                        \
+   : pt == 8 ? F_<P, G_, 8>(__VA_ARGS__)                                        \
+   : pt == 6 ? F_<P, G_, 6>(__VA_ARGS__)                                        \
    : pt == 5 ? F_<P, G_, 5>(__VA_ARGS__)                                        \
    : pt == 4 ? F_<P, G_, 4>(__VA_ARGS__)                                        \
    : pt == 2 ? F_<P, G_, 2>(__VA_ARGS__)                                        \
@@ -2135,8 +2416,8 @@ int launch_freq_batched_g(const DeviceView* views, const BatchItem* items, int n
 
 template <class P>
 int launch_transport_batched_t(int geometry, int pt, const DeviceView* views, const BatchItem* items,
-                               int n, int grid, int nb_max, cudaStream_t st) {
-  return LYM1_GPT(launch_transport_batched_g, views, items, n, grid, nb_max, st);
+                               int n, int grid, int nb_max, cudaStream_t st, int shape = 0) {
+  return LYM1_GPT(launch_transport_batched_g, views, items, n, grid, nb_max, st, shape);
 }
 
 template <class P>
@@ -2157,17 +2438,23 @@ int launch_freq_batched_t(int geometry, int pt, const DeviceView* views, const B
 // bin) stay under the default at LYM1_MAX_BINS.
 constexpr size_t kFreqSmemMax = sizeof(double) * 7 * LYM1_MAX_BINS;
 
-template <class P, int G, int PT>
-int max_resident_transport_g(int nb_max) {
+template <class P, int G, int PT, int TS>
+int max_resident_transport_s(int nb_max) {
   int nblk = 0;
+  constexpr int NT = TileShape<TS>::X * TileShape<TS>::Y;
   if constexpr (sizeof(typename P::S) == 4)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nblk, transport_batched_f32<P, G, PT>,
-                                                  kTileX * kTileY,
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nblk, transport_batched_f32<P, G, PT, TS>, NT,
                                                   sizeof(float) * 4 * static_cast<size_t>(nb_max));
   else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nblk, transport_batched<P, G, PT>,
-                                                  kTileX * kTileY, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nblk, transport_batched<P, G, PT, TS>, NT, 0);
   return nblk < 1 ? 1 : nblk;
+}
+
+template <class P, int G, int PT>
+int max_resident_transport_g(int nb_max, int shape) {
+  if constexpr (PT == 0 || PT == 1)
+    if (shape == 1) return max_resident_transport_s<P, G, PT, 1>(nb_max);
+  return max_resident_transport_s<P, G, PT, 0>(nb_max);
 }
 
 template <class P, int G, int PT>
@@ -2181,8 +2468,8 @@ int max_resident_freq_g(int nb_max) {
 }
 
 template <class P>
-int max_resident_transport(int geometry, int pt, int nb_max) {
-  return LYM1_GPT(max_resident_transport_g, nb_max);
+int max_resident_transport(int geometry, int pt, int nb_max, int shape = 0) {
+  return LYM1_GPT(max_resident_transport_g, nb_max, shape);
 }
 
 template <class P>
@@ -2224,6 +2511,50 @@ int launch_freq_t(const DeviceView& v, cudaStream_t st) {
   const int geometry = v.geometry, pt = v.pt & 3;
   if (pt == 2) return static_cast<int>(cudaErrorInvalidValue);
   return LYM1_GPT_F(launch_freq_g, v, st);
+}
+
+// step 2 under the acceptance rule (Lya: uniform temperature or a
+// temperature field; pt & 3 == 2, broad bands, is refused)
+template <class P, int G, int TM>
+int launch_subcycle_g(const DeviceView& v, cudaStream_t st) {
+  subcycle_kernel<P, G, TM><<<freq_blocks(v.nc), kFreqThreads, 0, st>>>(v);
+  return static_cast<int>(cudaGetLastError());
+}
+
+template <class P>
+int launch_subcycle_t(const DeviceView& v, cudaStream_t st) {
+  const int geometry = v.geometry, pt = v.pt & 3;
+  if (pt == 2) return static_cast<int>(cudaErrorInvalidValue);
+  return LYM1_GPT_F(launch_subcycle_g, v, st);
+}
+
+template <class P, int G, int TM>
+int launch_subcycle_batched_g(const DeviceView* views, const BatchItem* items, int n, int grid,
+                              cudaStream_t st) {
+  subcycle_batched<P, G, TM><<<grid, kFreqThreads, 0, st>>>(views, items, n);
+  return static_cast<int>(cudaGetLastError());
+}
+
+template <class P>
+int launch_subcycle_batched_t(int geometry, int pt, const DeviceView* views, const BatchItem* items,
+                              int n, int grid, cudaStream_t st) {
+  pt &= 3;
+  if (pt == 2) return static_cast<int>(cudaErrorInvalidValue);
+  return LYM1_GPT_F(launch_subcycle_batched_g, views, items, n, grid, st);
+}
+
+template <class P, int G, int TM>
+int max_resident_subcycle_g(int) {
+  int nblk = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nblk, subcycle_batched<P, G, TM>, kFreqThreads, 0);
+  return nblk < 1 ? 1 : nblk;
+}
+
+template <class P>
+int max_resident_subcycle(int geometry, int pt) {
+  pt &= 3;
+  if (pt == 2) return 1;
+  return LYM1_GPT_F(max_resident_subcycle_g, 0);
 }
 
 }  // namespace lym1

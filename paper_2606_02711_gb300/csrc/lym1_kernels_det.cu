@@ -15,17 +15,24 @@ int launch_freq_det(const DeviceView& v, void* st) {
   return launch_freq_t<PolDet>(v, static_cast<cudaStream_t>(st));
 }
 
-int launch_batched_det(int kind, int geometry, int pt, const DeviceView* views, const void* items,
-                       int n, int grid, int nb_max, void* st) {
-  const cudaStream_t s = static_cast<cudaStream_t>(st);
-  const BatchItem* it = static_cast<const BatchItem*>(items);
-  if (kind == 0) return launch_transport_batched_t<PolDet>(geometry, pt, views, it, n, grid, nb_max, s);
-  return launch_freq_batched_t<PolDet>(geometry, pt, views, it, n, grid, nb_max, s);
+int launch_subcycle_det(const DeviceView& v, void* st) {
+  return launch_subcycle_t<PolDet>(v, static_cast<cudaStream_t>(st));
 }
 
-int resident_blocks_det(int kind, int geometry, int pt, int nb_max) {
-  return kind == 0 ? max_resident_transport<PolDet>(geometry, pt, nb_max)
-                   : max_resident_freq<PolDet>(geometry, pt, nb_max);
+int launch_batched_det(int kind, int geometry, int pt, const DeviceView* views, const void* items,
+                       int n, int grid, int nb_max, void* st, int shape) {
+  const cudaStream_t s = static_cast<cudaStream_t>(st);
+  const BatchItem* it = static_cast<const BatchItem*>(items);
+  if (kind == 0)
+    return launch_transport_batched_t<PolDet>(geometry, pt, views, it, n, grid, nb_max, s, shape);
+  if (kind == 1) return launch_freq_batched_t<PolDet>(geometry, pt, views, it, n, grid, nb_max, s);
+  return launch_subcycle_batched_t<PolDet>(geometry, pt, views, it, n, grid, s);
+}
+
+int resident_blocks_det(int kind, int geometry, int pt, int nb_max, int shape) {
+  if (kind == 0) return max_resident_transport<PolDet>(geometry, pt, nb_max, shape);
+  if (kind == 1) return max_resident_freq<PolDet>(geometry, pt, nb_max);
+  return max_resident_subcycle<PolDet>(geometry, pt);
 }
 
 
@@ -177,21 +184,28 @@ __device__ __forceinline__ void kahan_add(double* a, double v) {
 //               [8] energy after the substep, [9] max f, [10] unrealisable count,
 //               [11] substeps, [12] energy at the last reset, [13] energy unit
 // mode 0: substep (flows from partT, energy/max f from partE);
-// mode 1: reset (energy from partE; flows and counters zeroed).
+// mode 1: reset (energy from partE; flows and counters zeroed);
+// mode 2: substep whose step 2 ran in the subcycling kernel of the acceptance
+//         rule (emitted and absorbed also from partE).
 __device__ __forceinline__ void finalize_body(const double* partT, int nT, const double* partE,
                                               int nE, double* acc, int mode) {
   __shared__ double red[8];
   double v[kDiagSlots];
   for (int s = 0; s < kDiagSlots; ++s) v[s] = 0.0;
-  if (mode == 0)
+  const bool reset = (mode & 1) != 0;
+  if (!reset)
     for (int b = threadIdx.x; b < nT; b += 256)
       for (int s = 0; s < 4; ++s) v[s] += partT[static_cast<long long>(b) * kDiagSlots + s];
   for (int b = threadIdx.x; b < nE; b += 256) {
     const double* p = partE + static_cast<long long>(b) * kDiagSlots;
     v[kSlotEnergy] += p[kSlotEnergy];
-    if (mode == 0) {
+    if (!reset) {
       v[kSlotMaxF] = fmax(v[kSlotMaxF], p[kSlotMaxF]);
       v[kSlotBad] += p[kSlotBad];
+      if (mode & 2) {  // step 2 ran in the subcycling kernel: its flows
+        v[kSlotEmitted] += p[kSlotEmitted];
+        v[kSlotAbsorbed] += p[kSlotAbsorbed];
+      }
     }
   }
   double tot[kDiagSlots];
@@ -203,7 +217,7 @@ __device__ __forceinline__ void finalize_body(const double* partT, int nT, const
   }
   if (threadIdx.x == 0) {
     const double u = acc[13];
-    if (mode == 1) {
+    if (reset) {
       for (int i = 0; i < 8; ++i) acc[i] = 0.0;
       acc[8] = u * tot[kSlotEnergy];
       acc[9] = 0.0;
@@ -586,7 +600,7 @@ int launch_sum_cells(const double* a, long long n, double* work, void* st) {
 // one block per context: the per-substep reduction of finalize_kernel for a batch
 __global__ void __launch_bounds__(256) finalize_batched_kernel(const FinalizeJob* jobs) {
   const FinalizeJob j = jobs[blockIdx.x];
-  finalize_body(j.partT, j.nT, j.partE, j.nE, j.acc, 0);
+  finalize_body(j.partT, j.nT, j.partE, j.nE, j.acc, j.mode);
 }
 
 int launch_finalize_batched(const FinalizeJob* jobs, int n, void* st) {

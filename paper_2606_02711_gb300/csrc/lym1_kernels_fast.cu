@@ -1,56 +1,54 @@
-// lym1_kernels_fast.cu -- kernels of the LYM1_FP64, LYM1_MIXED and
-// LYM1_MIXED_FAST policies (FMA contraction allowed, hardware exp/expm1).
+// lym1_kernels_fast.cu -- dispatch to the kernels of the LYM1_FP64,
+// LYM1_MIXED and LYM1_MIXED_FAST policies (FMA contraction allowed, hardware
+// exp/expm1).  Each policy is instantiated in a translation unit of its own
+// (lym1_pol_f64.cu, lym1_pol_mix.cu, lym1_pol_mixf.cu), compiled in parallel.
 #include "lym1_kernels.cuh"
+#include "lym1_policies.h"
 
 namespace lym1 {
 
-using PolF64 = Policy<double, double, double, false>;
-using PolMix = Policy<float, float, double, false>;
-using PolMixFast = Policy<float, float, float, false>;
-
 int launch_transport_fast(int precision, const DeviceView& v, void* st) {
-  const cudaStream_t s = static_cast<cudaStream_t>(st);
   switch (precision) {
-    case 1: return launch_transport_t<PolF64>(v, s);
-    case 2: return launch_transport_t<PolMix>(v, s);
-    case 3: return launch_transport_t<PolMixFast>(v, s);
+    case 1: return pol_f64::transport(v, st);
+    case 2: return pol_mix::transport(v, st);
+    case 3: return pol_mixf::transport(v, st);
     default: return static_cast<int>(cudaErrorInvalidValue);
   }
 }
 
 int launch_freq_fast(int precision, const DeviceView& v, void* st) {
-  const cudaStream_t s = static_cast<cudaStream_t>(st);
   switch (precision) {
-    case 1: return launch_freq_t<PolF64>(v, s);
-    case 2: return launch_freq_t<PolMix>(v, s);
-    case 3: return launch_freq_t<PolMixFast>(v, s);
+    case 1: return pol_f64::freq(v, st);
+    case 2: return pol_mix::freq(v, st);
+    case 3: return pol_mixf::freq(v, st);
+    default: return static_cast<int>(cudaErrorInvalidValue);
+  }
+}
+
+int launch_subcycle_fast(int precision, const DeviceView& v, void* st) {
+  switch (precision) {
+    case 1: return pol_f64::subcycle(v, st);
+    case 2: return pol_mix::subcycle(v, st);
+    case 3: return pol_mixf::subcycle(v, st);
     default: return static_cast<int>(cudaErrorInvalidValue);
   }
 }
 
 int launch_batched_fast(int precision, int kind, int geometry, int pt, const DeviceView* views,
-                        const void* items, int n, int grid, int nb_max, void* st) {
-  const cudaStream_t s = static_cast<cudaStream_t>(st);
-  const BatchItem* it = static_cast<const BatchItem*>(items);
-  switch (precision * 2 + kind) {
-    case 2: return launch_transport_batched_t<PolF64>(geometry, pt, views, it, n, grid, nb_max, s);
-    case 3: return launch_freq_batched_t<PolF64>(geometry, pt, views, it, n, grid, nb_max, s);
-    case 4: return launch_transport_batched_t<PolMix>(geometry, pt, views, it, n, grid, nb_max, s);
-    case 5: return launch_freq_batched_t<PolMix>(geometry, pt, views, it, n, grid, nb_max, s);
-    case 6: return launch_transport_batched_t<PolMixFast>(geometry, pt, views, it, n, grid, nb_max, s);
-    case 7: return launch_freq_batched_t<PolMixFast>(geometry, pt, views, it, n, grid, nb_max, s);
+                        const void* items, int n, int grid, int nb_max, void* st, int shape) {
+  switch (precision) {
+    case 1: return pol_f64::batched(kind, geometry, pt, views, items, n, grid, nb_max, st, shape);
+    case 2: return pol_mix::batched(kind, geometry, pt, views, items, n, grid, nb_max, st, shape);
+    case 3: return pol_mixf::batched(kind, geometry, pt, views, items, n, grid, nb_max, st, shape);
     default: return static_cast<int>(cudaErrorInvalidValue);
   }
 }
 
-int resident_blocks_fast(int precision, int kind, int geometry, int pt, int nb_max) {
-  switch (precision * 2 + kind) {
-    case 2: return max_resident_transport<PolF64>(geometry, pt, nb_max);
-    case 3: return max_resident_freq<PolF64>(geometry, pt, nb_max);
-    case 4: return max_resident_transport<PolMix>(geometry, pt, nb_max);
-    case 5: return max_resident_freq<PolMix>(geometry, pt, nb_max);
-    case 6: return max_resident_transport<PolMixFast>(geometry, pt, nb_max);
-    case 7: return max_resident_freq<PolMixFast>(geometry, pt, nb_max);
+int resident_blocks_fast(int precision, int kind, int geometry, int pt, int nb_max, int shape) {
+  switch (precision) {
+    case 1: return pol_f64::resident(kind, geometry, pt, nb_max, shape);
+    case 2: return pol_mix::resident(kind, geometry, pt, nb_max, shape);
+    case 3: return pol_mixf::resident(kind, geometry, pt, nb_max, shape);
     default: return 1;
   }
 }

@@ -89,6 +89,7 @@ SIGNATURES = {
     "lym1_bands_update": (C.c_int, [C.c_void_p, _PD, _PD, _PD]),
     "lym1_set_temperature": (C.c_int, [C.c_void_p, _PD]),
     "lym1_set_pruning": (C.c_int, [C.c_void_p, C.c_double]),
+    "lym1_set_accept": (C.c_int, [C.c_void_p, C.c_int]),
     "lym1_dynamic_ctilde": (C.c_int, [C.c_void_p, _PD, C.c_double, C.c_double, _PD]),
     "lym1_create": (C.c_int, [C.POINTER(lym1_grid), C.POINTER(lym1_groups),
                               C.POINTER(lym1_opacities), C.POINTER(C.c_void_p)]),
@@ -114,6 +115,8 @@ SIGNATURES = {
     "lym1_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_void_p)]),
     "lym1_batch_substeps": (C.c_int, [C.c_void_p, C.c_int]),
     "lym1_batch_grid": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "lym1_batch_config": (C.c_int, [C.c_void_p] + [C.POINTER(C.c_int)] * 5),
+    "lym1_batch_configure": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int]),
     "lym1_batch_destroy": (None, [C.c_void_p]),
     "lym1_debug_expire_wait": (C.c_int, [C.c_void_p]),
     "lym1_debug_fp64_helpers": (C.c_int, [C.c_void_p, C.c_void_p, C.c_longlong, C.c_void_p,
@@ -256,6 +259,10 @@ class Context:
     def set_pruning(self, cut: float = 1e-10):
         """``lym1_set_pruning``: advect only bins above cut of the energy (0: all)."""
         _check(lib().lym1_set_pruning(self.handle, float(cut)), "lym1_set_pruning")
+
+    def set_accept(self, on: bool = True):
+        """``lym1_set_accept``: the substep acceptance rule of step 2 (Sec. 2.1)."""
+        _check(lib().lym1_set_accept(self.handle, int(bool(on))), "lym1_set_accept")
 
     def set_temperature(self, temp):
         """``lym1_set_temperature``: per-cell tables for new gas temperatures."""
@@ -482,6 +489,17 @@ class Batch:
         a, b = C.c_int(), C.c_int()
         _check(lib().lym1_batch_grid(self.handle, C.byref(a), C.byref(b)), "lym1_batch_grid")
         return a.value, b.value
+
+    def config(self) -> dict:
+        """``lym1_batch_config``: tile shape, bin groups and grids in use (0 until tuned)."""
+        v = [C.c_int() for _ in range(5)]
+        _check(lib().lym1_batch_config(self.handle, *[C.byref(x) for x in v]), "lym1_batch_config")
+        return dict(zip(("tile_x", "tile_y", "bin_groups", "grid_t", "grid_f"), [x.value for x in v]))
+
+    def configure(self, tile_shape=0, bin_groups=1, grid_t=0):
+        """``lym1_batch_configure``: fix the transport layout instead of tuning it."""
+        _check(lib().lym1_batch_configure(self.handle, int(tile_shape), int(bin_groups), int(grid_t)),
+               "lym1_batch_configure")
 
     def destroy(self):
         if getattr(self, "handle", None):

@@ -1,6 +1,11 @@
 """Batched substeps (one persistent launch per kernel over several clouds,
-CUDA-graph replay, tuned persistent grid) give every cloud exactly the result
-it gets alone."""
+CUDA-graph replay, tuned persistent grid and transport layout) give every
+cloud the result it gets alone: bit for bit under LYM1_FP64_DET, whose batches
+keep one 16 x 16 block per tile.  Under the other policies the tuner may pick
+another layout for a batch than for a cloud alone; J and H are still the same
+bit for bit, and the force and the transport's bookkeeping differ only in
+their summation order (FP64 sums: 1e-12; FP32 per-cell sums of
+LYM1_MIXED_FAST: 1e-6)."""
 import numpy as np
 import pytest
 
@@ -40,13 +45,20 @@ def test_batch_equals_individual_runs(L, precision):
     gt, gf = b.grid()
     assert gt > 0 and gf > 0
     b.destroy()
+    rel = 0.0 if precision == 0 else (1e-6 if precision == 3 else 1e-12)
     for ctx, ref in zip(ctxs, solo):
         got = ctx.get_state() + ctx.force()
-        for a, r in zip(got, ref[:5]):
+        for a, r in zip(got[:3], ref[:3]):
             assert np.array_equal(a, r)
+        for a, r in zip(got[3:], ref[3:5]):
+            if rel == 0.0:
+                assert np.array_equal(a, r)
+            else:
+                np.testing.assert_allclose(a, r, rtol=rel, atol=rel * np.abs(r).max())
         d = ctx.diagnostics()
-        for k in ("e_tot", "emitted", "absorbed", "outflow", "work", "substeps"):
-            assert d[k] == ref[5][k], k
+        assert d["e_tot"] == ref[5]["e_tot"] and d["substeps"] == ref[5]["substeps"]
+        for k in ("emitted", "absorbed", "outflow", "work"):
+            assert d[k] == pytest.approx(ref[5][k], rel=rel, abs=0.0), k
         ctx.destroy()
 
 
