@@ -50,6 +50,18 @@ ALGO_OPS_TRANSPORT = 2 * 110 + 75
 # FP32 lanes per SM on GB300 (one operation per lane per cycle)
 FP32_LANES_PER_SM = 128
 N_SM = 152
+# FP64 pipe of GB300: 2 FMA lanes per SM per cycle (1.25 TFLOP/s nominal at
+# 2070 MHz, counting an FMA as 2 flops).  Algorithmic FP64 flops per (cell,
+# bin) of the policies that keep the implicit steps in FP64 (FMA = 2 flops,
+# each +, -, *, / = 1), counted from the scheme as written:
+#   transport kernel, Sec. 2.1 step 2 and Sec. 2.3: kappa_k and alpha_F,k (4),
+#     1 + c dt kappa and 1 + c dt alpha_F (4), J'' = (J' + c dt j) / (.) (4),
+#     H''_x, H''_y (2), force dnu (H' - H'') for two components (6),
+#     absorbed dnu c dt kappa J'' (4), work dnu W (2): 26;
+#   frequency kernel, App. A elimination in margin form: E_k, r_k, D'_k (6),
+#     one reciprocal (1), g_k, h_k, q_k (3), back substitution (2), energy sum (2): 14.
+FP64_LANES_PER_SM = 2
+ALGO_FP64_FLOPS = {"transport": 26, "freq": 14}
 
 
 def _peaks():
@@ -119,7 +131,7 @@ class ClockSampler:
 
 def _kernel_hash() -> str:
     h = hashlib.sha256()
-    for f in ("lym1_kernels.cuh", "lym1_kernels_fast.cu", "lym1_kernels_det.cu"):
+    for f in ("lym1_kernels.cuh", "lym1_kernels_fast.cu", "lym1_kernels_det.cu", "lym1_pol_unit.cuh"):
         with open(os.path.join(ROOT, "paper_2606_02711_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -173,6 +185,41 @@ def cpu_baseline(cloud, seconds=10.0, crop=128):
                       f"({el:.1f} s wall)"}
 
 
+def serving_line(L, prec, args, rank, world):
+    """A bounded served stream (continuous batching, device-resident state,
+    admission by HBM budget): Poisson arrivals of cloud solves run to the
+    steady-state rule; p50/p99 latency from arrival to result, solves/s,
+    offered vs served load, cap hits.  Under torchrun each rank serves its
+    own shard of the stream."""
+    import workloads as wl
+    from paper_2606_02711_gb300 import serve as S
+    fp64 = prec in (L.FP64, L.FP64_DET)
+    n = args.serve_requests_fp64 if fp64 else args.serve_requests
+    lo, hi = (args.serve_side_fp64, args.serve_side_fp64) if fp64 else (args.serve_side_min,
+                                                                          args.serve_side_max)
+    arr = wl.poisson_arrivals(n, args.serve_rate, seed=7)
+    clouds = wl.batch_clouds(n, base_seed=5000, side_lo=lo, side_hi=hi, nh_lo=args.serve_nh_min,
+                             nh_hi=args.serve_nh_max, bc=(1, 1, 1, 1))
+    reqs = S.shard([S.Request(i, float(a), c) for i, (a, c) in enumerate(zip(arr, clouds))],
+                   rank, world)
+    be = S.Lym1Backend(prec)
+    srv = S.Server(be, hbm_budget=args.serve_hbm_gb * 1e9, max_active=64, check_every=50,
+                   tol=args.serve_tol, max_substeps=args.serve_cap)
+    t0 = time.perf_counter()
+    res = srv.run(reqs)
+    wall = time.perf_counter() - t0
+    out = S.summarize(res, wall, args.serve_rate / world)
+    out.update({"served_rate_per_s": out["solves_per_s"], "wall_s": wall, "rounds": srv.rounds,
+                "batches_built": be.batch_creations, "peak_resident_gb": srv.peak_bytes / 1e9,
+                "stream": {"requests": len(reqs), "arrivals": f"Poisson {args.serve_rate}/s",
+                           "sides": [lo, hi], "mean_nh": [args.serve_nh_min, args.serve_nh_max],
+                           "edges": "outflow into vacuum on all four sides",
+                           "L_sun": [1e4, 1e7], "Z_sun": [0, 1e-3, 1e-2],
+                           "steady_state": f"|E_n - E_n-50| / E_n / 50 < {args.serve_tol:g}",
+                           "cap_substeps": args.serve_cap, "hbm_budget_gb": args.serve_hbm_gb}})
+    return out
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -215,13 +262,25 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="mixed_fast", choices=list(NAMES.values()))
+    ap.add_argument("--precision", default="mixed", choices=list(NAMES.values()))
     ap.add_argument("--fp64-steps", type=int, default=8)
     ap.add_argument("--e2e-steps", type=int, default=40)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-crop", type=int, default=128)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="timed region only (for ncu)")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=40)
+    ap.add_argument("--serve-requests-fp64", type=int, default=8)
+    ap.add_argument("--serve-rate", type=float, default=50.0)
+    ap.add_argument("--serve-side-min", type=int, default=32)
+    ap.add_argument("--serve-side-max", type=int, default=64)
+    ap.add_argument("--serve-side-fp64", type=int, default=32)
+    ap.add_argument("--serve-nh-min", type=float, default=1e-2)
+    ap.add_argument("--serve-nh-max", type=float, default=1.0)
+    ap.add_argument("--serve-tol", type=float, default=1e-6)
+    ap.add_argument("--serve-cap", type=int, default=20000)
+    ap.add_argument("--serve-hbm-gb", type=float, default=150.0)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -290,21 +349,31 @@ def main():
     peak, peak_kind = _peaks()
     traffic, tsrc = _traffic_from_profiles(dom, NAMES[prec])
     share = {k: v[0] / max(ms, 1e-9) for k, v in kern.items()}
-    if dom == "transport" and prec == 3:
+    sm_mhz = ck.get("sm_mhz") or 2070.0
+    hbm_obj = {"achieved": hbm_gbs, "peak": peak, "unit": "GB/s", "frac": hbm_gbs / peak,
+               "algorithmic_bytes_per_launch": kbytes,
+               "peak_source": f"{peak_kind} MEASURED_PEAKS.json hbm_gbs"
+               if peak_kind == "measured" else "fallback 6.8 TB/s"}
+    if prec in (0, 1, 2):
+        # the FP64 implicit steps bind on GB300's FP64 pipe (~1/70 of the FP32
+        # rate): FP64-pipe roofline of the dominant kernel, HBM beside it
+        f64_peak = N_SM * FP64_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+        f64_ach = ALGO_FP64_FLOPS[dom] * nc * nb / avg_s / 1e12
+        roof = {"bound": "alu", "pipe": "fp64", "achieved": f64_ach, "peak": f64_peak,
+                "unit": "TFLOP/s", "frac": f64_ach / f64_peak, "traffic": traffic, "kernel": dom,
+                "peak_source": f"derived: {N_SM} SMs x {FP64_LANES_PER_SM} FP64 FMA lanes x 2 "
+                               f"flops x {sm_mhz:.0f} MHz",
+                "algorithmic_fp64_flops_per_cell_bin": ALGO_FP64_FLOPS[dom], "hbm": hbm_obj}
+    elif dom == "transport" and prec == 3:
         # FP32 transport is bound by instruction issue (ncu: DRAM bytes equal the
         # algorithmic bytes at ~14 % of DRAM peak, issue ~70 % active): FP32 ALU roofline
-        sm_mhz = ck.get("sm_mhz") or 2070.0
         alu_peak = N_SM * FP32_LANES_PER_SM * sm_mhz * 1e6 / 1e12
         alu_ach = ALGO_OPS_TRANSPORT * nc * nb / avg_s / 1e12
         roof = {"bound": "alu", "achieved": alu_ach, "peak": alu_peak, "unit": "TFLOP/s",
                 "frac": alu_ach / alu_peak, "traffic": traffic, "kernel": dom,
                 "peak_source": f"derived: {N_SM} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
                                f"{sm_mhz:.0f} MHz (one op per lane per cycle)",
-                "algorithmic_ops_per_cell_bin": ALGO_OPS_TRANSPORT,
-                "hbm": {"achieved": hbm_gbs, "peak": peak, "unit": "GB/s",
-                        "frac": hbm_gbs / peak, "algorithmic_bytes_per_launch": kbytes,
-                        "peak_source": f"{peak_kind} MEASURED_PEAKS.json hbm_gbs"
-                        if peak_kind == "measured" else "fallback 6.8 TB/s"}}
+                "algorithmic_ops_per_cell_bin": ALGO_OPS_TRANSPORT, "hbm": hbm_obj}
     else:
         roof = {"bound": "hbm", "achieved": hbm_gbs, "peak": peak, "unit": "GB/s",
                 "frac": hbm_gbs / peak, "traffic": traffic, "kernel": dom,
@@ -372,7 +441,11 @@ def main():
             b.record()
             torch.cuda.synchronize()
             m = a.elapsed_time(b)
-            cmp[NAMES[p]] = {"value": nc * n / (m * 1e-3), "ms_per_step": m / n, "steps": n}
+            cmp[NAMES[p]] = {"value": nc * n / (m * 1e-3), "ms_per_step": m / n, "steps": n,
+                             "dtype": DTYPES[p]}
+            if p == L.MIXED_FAST:
+                cmp[NAMES[p]]["note"] = ("extra: FP32 implicit steps and per-cell sums (not the "
+                                         "FP32-flux / FP64-source split of the headline)")
             c2.destroy()
         out["precisions"] = cmp
 
@@ -438,6 +511,10 @@ def main():
                                 "steps": n, "bands": c5.nb,
                                 "note": "cell-updates over 7 bands (IR, opt, FUV, LW, EUV1-3)"}
         c5.destroy()
+
+        if not args.no_serve:
+            out["serving"] = {NAMES[p]: serving_line(L, p, args, rank, world)
+                              for p in dict.fromkeys((prec, L.FP64))}
 
         if rank == 0 and world == 1 and not args.no_cpu:
             out["cpu_baseline"] = cpu_baseline(cloud, seconds=args.cpu_seconds)

@@ -1,8 +1,8 @@
 """Broad bands on the GPU (Sec. 3: the seven stellar and IR bands on the M1
 transport of Sec. 2.1 without frequency terms) through lym1_create_bands,
 against the oracle's band mode with the bars of test_gpu_parity (bit-exact
-LYM1_FP64_DET, 1e-10 LYM1_FP64, 1e-4 normwise per band plane for the mixed
-policies), in both geometries with vacuum sides, with emergent spectra, across
+LYM1_FP64_DET, 1e-10 LYM1_FP64, 1e-4 per element plus the n u S_n floor for
+the mixed policies), in both geometries with vacuum sides, with emergent spectra, across
 an update of the opacities, and reduced to the gray Lya group bit for bit.
 The thin-sphere force multiplier tau / 4 (Sec. 4.1, Test 1, thin limit, eta = 1
 for a band) is checked on the GPU too."""
@@ -13,7 +13,7 @@ import pytest
 
 import oracle
 import workloads as wl
-from test_gpu_parity import TOL, close, random_state
+from test_gpu_parity import TOL, check_outputs, close, force_weights, random_state
 
 pytestmark = pytest.mark.gpu
 
@@ -53,10 +53,9 @@ def run_pair(L, c, bands, precision, n, state):
 def test_seven_bands_match_oracle(L, precision, geometry):
     c, bands = band_cloud(45, 38, seed=101, geometry=geometry)
     st = random_state(7, 38, 45, 102, scale=1e-3)
-    ctx, _, got, ref, dg, diags = run_pair(L, c, bands, precision, 4, st)
+    ctx, O, got, ref, dg, diags = run_pair(L, c, bands, precision, 4, st)
     ctx.destroy()
-    for a, b, n in zip(got, ref, ("J", "Hx", "Hy", "fx", "fy")):
-        close(a, b, TOL[precision], n)
+    check_outputs(got, ref, TOL[precision], 4, st, force_weights(O, c.dx))
     rel = max(TOL[precision], 1e-12)
     assert dg["e_tot"] == pytest.approx(diags[-1]["e_after"], rel=rel)
     keys = ("emitted", "absorbed", "work", "outflow")
@@ -94,8 +93,7 @@ def test_band_update_and_spectrum(L, precision):
         O.spectrum_on()
         J, Hx, Hy, fx, fy, _ = O.substep(J, Hx, Hy)
         ref_spec = ref_spec + O.spectrum
-    for a, b, n in zip(got, (J, Hx, Hy, fx, fy), ("J", "Hx", "Hy", "fx", "fy")):
-        close(a, b, TOL[precision], n)
+    check_outputs(got, (J, Hx, Hy, fx, fy), TOL[precision], 4, st, force_weights(O1, c.dx))
     if precision == 0:
         np.testing.assert_array_equal(spec, ref_spec)
     else:

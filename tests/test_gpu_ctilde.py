@@ -10,7 +10,7 @@ import pytest
 
 import oracle
 import workloads as wl
-from test_gpu_parity import TOL, close, random_state
+from test_gpu_parity import TOL, check_outputs, close, force_weights, random_state
 
 pytestmark = pytest.mark.gpu
 
@@ -78,6 +78,7 @@ def test_substeps_follow_new_ctilde(L, edges, precision):
     ctx.substeps(2)
     for _ in range(2):
         J, Hx, Hy, fx, fy, _ = O.substep(J, Hx, Hy)
+    done = 2
     for set_ct in ("dynamic", 2.0e9):
         if set_ct == "dynamic":
             ct = ctx.dynamic_ctilde(ct_min=0.0)
@@ -88,11 +89,11 @@ def test_substeps_follow_new_ctilde(L, edges, precision):
             O.set_ctilde(set_ct)
         assert ctx.dt_cfl == O.dt_cfl
         ctx.substeps(3)
+        done += 3
         for _ in range(3):
             J, Hx, Hy, fx, fy, _ = O.substep(J, Hx, Hy)
         got = ctx.get_state() + ctx.force()
-        for a, b, n in zip(got, (J, Hx, Hy, fx, fy), ("J", "Hx", "Hy", "fx", "fy")):
-            close(a, b, TOL[precision], n)
+        check_outputs(got, (J, Hx, Hy, fx, fy), TOL[precision], done, st, force_weights(O, c.dx))
     ctx.destroy()
 
 

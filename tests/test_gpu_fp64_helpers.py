@@ -5,7 +5,8 @@ GB300 runs FP64 arithmetic and FP32 <-> FP64 conversions on a pipe of about
 pipe and refine the hardware reciprocal approximation by Newton-Raphson.
 Widening must be exact and narrowing correctly rounded (to nearest, ties to
 even) wherever the result is a binary32 normal number or infinity; both flush
-subnormals to zero.  The reciprocal must lie within one ulp of 1/x.  numpy's
+subnormals to zero.  The reciprocal must lie within one ulp of 1/x; the one-step reciprocal of the
+mixed steps (whose results are rounded to FP32) within 2^-38 of it.  numpy's
 conversions and division are the IEEE reference.
 """
 import ctypes as C
@@ -28,10 +29,12 @@ def _run(xf, xd):
     wide = torch.empty(n, dtype=torch.float64, device="cuda")
     narrow = torch.empty(n, dtype=torch.float32, device="cuda")
     rcp = torch.empty(n, dtype=torch.float64, device="cuda")
+    rcp1 = torch.empty(n, dtype=torch.float64, device="cuda")
     st = L.lib().lym1_debug_fp64_helpers(C.c_void_p(a.data_ptr()), C.c_void_p(b.data_ptr()), n,
                                          C.c_void_p(wide.data_ptr()), C.c_void_p(narrow.data_ptr()),
-                                         C.c_void_p(rcp.data_ptr()))
+                                         C.c_void_p(rcp.data_ptr()), C.c_void_p(rcp1.data_ptr()))
     assert st == 0
+    _run.rcp1 = rcp1.cpu().numpy()
     return wide.cpu().numpy(), narrow.cpu().numpy(), rcp.cpu().numpy()
 
 
@@ -101,3 +104,16 @@ def test_reciprocal_within_one_ulp():
     ulp = np.abs(_bits64(rcp).astype(np.int64) - _bits64(ref).astype(np.int64))
     assert ulp.max() <= 1
     assert np.mean(ulp == 0) > 0.9
+
+
+def test_one_step_reciprocal_within_2_pow_minus_38():
+    # the one Newton step squares the approximation's relative error: the
+    # bound the mixed source and elimination steps rely on, far below the FP32
+    # rounding (2^-24) their results then take
+    g = np.random.default_rng(4)
+    n = 1 << 20
+    xd = 10.0 ** g.uniform(-300.0, 300.0, n) * g.uniform(1.0, 10.0, n)
+    xd[:6] = [1.0, 2.0, 3.0, 1.0 + 2 ** -52, 1e300, 7.0]
+    _run(np.ones(n, dtype=np.float32), xd)
+    rel = np.abs(_run.rcp1 * xd - 1.0)
+    assert rel.max() <= 2.0 ** -38, f"max relative error 2^{np.log2(rel.max()):.1f}"

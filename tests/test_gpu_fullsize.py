@@ -1,22 +1,29 @@
 """GPU parity at the workloads' full sizes, in the launch configuration the
-benchmark times (one context, the default stream, CFL substeps).
+benchmark times (one context, the default stream, CFL substeps), with the
+per-element bars of test_gpu_parity:
 
 * uniform-gray 64x64: all 2000 substeps, FP64_DET, bit-exact;
-* lognormal-512 (512x512x194): FP64_DET bit-exact after 2 substeps and
-  MIXED_FAST (the benchmarked policy) within 1e-4 normwise after 5, against
-  the oracle on the full grid;
-* the seven stellar/IR bands on lognormal-512: FP64_DET bit-exact and
-  MIXED_FAST within 1e-4 normwise after 10 substeps, on the full grid;
+* lognormal-512 (512x512x194) from a populated realisable state (every cell
+  and bin holds radiation, |H| < J): FP64_DET bit-exact after 2 substeps,
+  MIXED and MIXED_FAST after 5, against the oracle on the full grid;
+* the seven stellar/IR bands on lognormal-512 from a populated state:
+  FP64_DET bit-exact and MIXED_FAST after 10 substeps, on the full grid;
+* a 128x128x194 crop of lognormal-512, MIXED and MIXED_FAST, 200 substeps
+  from a populated state and from the empty state (errors accumulated over
+  hundreds of substeps, as in steady-state and served runs);
 * lognormal-2048 (2048x2048x194), MIXED_FAST: 5 substeps from the empty
   state; the oracle computes the central 64x64 crop, which the radiation
   cannot leave in 5 substeps (the stencil reaches 2 cells per substep), so
   every crop cell is comparable.
 """
+import copy
+
 import numpy as np
 import pytest
 
 import oracle
 import workloads as wl
+from test_gpu_parity import TOL, check_outputs, force_weights, fw_of, random_state
 
 pytestmark = pytest.mark.gpu
 
@@ -28,13 +35,14 @@ def L():
     return L
 
 
-def _normwise(a, b, rtol, name):
-    A = a.reshape(a.shape[0], -1) if a.ndim == 3 else a.reshape(1, -1)
-    B = b.reshape(A.shape)
-    scale = np.abs(B).max(axis=1)
-    err = np.abs(A - B).max(axis=1)
-    bad = err > rtol * scale
-    assert not bad.any(), f"{name}: plane {int(np.argmax(bad))} err {err[bad][0]:.3e} scale {scale[bad][0]:.3e}"
+def crop(full, n):
+    """The central n x n cells of a cloud, as a cloud of its own."""
+    j0 = (full.ny - n) // 2
+    c = copy.copy(full)
+    for f in ("n_hi", "rho_d", "p_d", "ux", "uy", "lum"):
+        setattr(c, f, np.ascontiguousarray(getattr(full, f)[j0:j0 + n, j0:j0 + n]))
+    c.nx = c.ny = n
+    return c
 
 
 def test_uniform_gray_64_all_2000_substeps_bitexact(L):
@@ -51,31 +59,75 @@ def test_uniform_gray_64_all_2000_substeps_bitexact(L):
     ctx.destroy()
 
 
-def test_lognormal_512_fp64_det_bitexact(L):
+@pytest.fixture(scope="module")
+def lognormal_512():
     c = wl.config_lognormal_512()
+    return c, wl.populated_state(c, 194, seed=11)
+
+
+def test_lognormal_512_fp64_det_bitexact(L, lognormal_512):
+    c, st = lognormal_512
     ctx = L.from_cloud(c, precision=L.FP64_DET)
+    ctx.set_state(*st)
     ctx.substeps(2)
     got = ctx.get_state() + ctx.force()
     ctx.destroy()
     O = oracle.Oracle(edges=oracle.freq_grid(), **c.kwargs())
-    ref, _ = O.run(2)
+    ref, _ = O.run(2, st)
     for a, b, n in zip(got, ref, ("J", "Hx", "Hy", "fx", "fy")):
         assert np.array_equal(a, b), n
 
 
-def test_lognormal_512_mixed_fast(L):
-    c = wl.config_lognormal_512()
-    ctx = L.from_cloud(c, precision=L.MIXED_FAST)
+@pytest.mark.parametrize("precision", [2, 3])
+def test_lognormal_512_mixed_policies(L, lognormal_512, precision):
+    c, st = lognormal_512
+    ctx = L.from_cloud(c, precision=precision)
+    ctx.set_state(*st)
     ctx.substeps(5)
     got = ctx.get_state() + ctx.force()
     d = ctx.diagnostics()
     ctx.destroy()
     O = oracle.Oracle(edges=oracle.freq_grid(), **c.kwargs())
-    ref, diags = O.run(5)
-    for a, b, n in zip(got, ref, ("J", "Hx", "Hy", "fx", "fy")):
-        _normwise(a, b, 1e-4, n)
+    ref, diags = O.run(5, st)
+    check_outputs(got, ref, TOL[precision], 5, st, force_weights(O, c.dx))
     assert d["e_tot"] == pytest.approx(diags[-1]["e_after"], rel=1e-5)
     assert d["max_f"] < 2.0
+
+
+@pytest.fixture(scope="module")
+def crop_runs():
+    """Oracle results on the 128^2 crop after 1 and 200 substeps, from the
+    populated state and from the empty state."""
+    c = crop(wl.config_lognormal_512(), 128)
+    O = oracle.Oracle(edges=oracle.freq_grid(), **c.kwargs())
+    out = {}
+    for start in ("populated", "empty"):
+        st = wl.populated_state(c, 194, seed=12) if start == "populated" else None
+        r1, d1 = O.run(1, st)
+        r200, d200 = O.run(199, r1[:3])
+        out[start] = (st, {1: (r1, d1[-1]), 200: (r200, d200[-1])})
+    return c, out
+
+
+@pytest.mark.parametrize("start", ["populated", "empty"])
+@pytest.mark.parametrize("precision", [2, 3])
+def test_crop_128_200_substeps(L, crop_runs, precision, start):
+    c, out = crop_runs
+    st, refs = out[start]
+    ctx = L.from_cloud(c, precision=precision)
+    if st is not None:
+        ctx.set_state(*st)
+    done = 0
+    for n in (1, 200):
+        ctx.substeps(n - done)
+        done = n
+        ref, dref = refs[n]
+        check_outputs(ctx.get_state() + ctx.force(), ref, TOL[precision], n, st, fw_of(c))
+        d = ctx.diagnostics()
+        assert d["e_tot"] == pytest.approx(dref["e_after"], rel=1e-4)
+        if dref["force_abs"] > 0.0:
+            assert d["force_abs"] == pytest.approx(dref["force_abs"], rel=1e-4)
+    ctx.destroy()
 
 
 @pytest.mark.parametrize("precision", ["fp64_det", "mixed_fast"])
@@ -85,16 +137,19 @@ def test_seven_bands_lognormal_512(L, precision):
     c = wl.config_lognormal_512()
     aF, ka, je = wl.stellar_bands(c)
     kw = dict(nx=c.nx, ny=c.ny, dx=c.dx, ux=c.ux, uy=c.uy)
+    st = random_state(7, c.ny, c.nx, 21, scale=1e-3)
     ctx = L.Context.for_bands(alpha_F=aF, kappa=ka, emissivity=je, precision=precision, **kw)
+    ctx.set_state(*st)
     ctx.substeps(10)
     got = ctx.get_state() + ctx.force()
     ctx.destroy()
-    ref, _ = oracle.Oracle.for_bands(alpha_F=aF, kappa=ka, emissivity=je, **kw).run(10)
-    for a, b, n in zip(got, ref, ("J", "Hx", "Hy", "fx", "fy")):
-        if precision == "fp64_det":
+    O = oracle.Oracle.for_bands(alpha_F=aF, kappa=ka, emissivity=je, **kw)
+    ref, _ = O.run(10, st)
+    if precision == "fp64_det":
+        for a, b, n in zip(got, ref, ("J", "Hx", "Hy", "fx", "fy")):
             assert np.array_equal(a, b), n
-        else:
-            _normwise(a, b, 1e-4, n)
+    else:
+        check_outputs(got, ref, TOL[3], 10, st, force_weights(O, c.dx))
 
 
 def test_lognormal_2048_mixed_fast_central_crop(L):
@@ -114,10 +169,10 @@ def test_lognormal_2048_mixed_fast_central_crop(L):
     kw["nx"] = kw["ny"] = n
     O = oracle.Oracle(edges=oracle.freq_grid(), **kw)
     ref, _ = O.run(5, dt=dt)
-    got = (J[:, sl[0], sl[1]], Hx[:, sl[0], sl[1]], Hy[:, sl[0], sl[1]], fx[sl], fy[sl])
+    got = tuple(np.ascontiguousarray(x) for x in
+                (J[:, sl[0], sl[1]], Hx[:, sl[0], sl[1]], Hy[:, sl[0], sl[1]], fx[sl], fy[sl]))
     # the radiation has not reached the crop margin: outside it the GPU state is empty
     mask = np.ones(J.shape[1:], bool)
     mask[sl] = False
     assert not J[:, mask].any()
-    for a, b, nme in zip(got, ref, ("J", "Hx", "Hy", "fx", "fy")):
-        _normwise(np.ascontiguousarray(a), b, 1e-4, nme)
+    check_outputs(got, ref, TOL[3], 5, fw=force_weights(O, c.dx))

@@ -1,8 +1,8 @@
 """Active-bin pruning on the GPU (lym1_set_pruning, Sec. 2.2: bins holding no
 more than the cut, 1e-10 in the paper, of the domain energy skip step 1)
-against the oracle's pruning mode, with the bars of test_gpu_parity
-(bit-exact LYM1_FP64_DET, 1e-10 LYM1_FP64, 1e-4 normwise per bin plane for
-the mixed policies), in both geometries, through the graph-replayed and
+against the oracle's pruning mode, with the per-element bars of
+test_gpu_parity (bit-exact LYM1_FP64_DET, 1e-10 LYM1_FP64, 1e-4 plus the
+n u S_n floor for the mixed policies), in both geometries, through the graph-replayed and
 batched paths.  The states hold chosen bins at shares of ~1e-14, far from the
 cut, so that the two sides never face a borderline decision."""
 import numpy as np
@@ -10,7 +10,7 @@ import pytest
 
 import oracle
 import workloads as wl
-from test_gpu_parity import TOL, close
+from test_gpu_parity import TOL, check_outputs, close, fw_of
 
 pytestmark = pytest.mark.gpu
 
@@ -56,9 +56,9 @@ def run_pair(L, c, edges, precision, n, st, prune=CUT):
 def test_pruned_substeps_match_oracle(L, edges, precision):
     c = wl.lognormal_cloud(45, 38, seed=171, v_edge_kms=100.0, Z=0.2, p_d=1e-7)
     c.lum = 1e-6 * c.lum  # weak sources: the small bins stay below the cut
-    got, ref, dg, diags = run_pair(L, c, edges, precision, 3, state(194, 38, 45, 172))
-    for a, b, n in zip(got, ref, ("J", "Hx", "Hy", "fx", "fy")):
-        close(a, b, TOL[precision], n)
+    st = state(194, 38, 45, 172)
+    got, ref, dg, diags = run_pair(L, c, edges, precision, 3, st)
+    check_outputs(got, ref, TOL[precision], 3, st, fw_of(c, edges))
     rel = max(TOL[precision], 1e-12)
     assert dg["e_tot"] == pytest.approx(diags[-1]["e_after"], rel=rel)
     out = sum(x["outflow"] for x in diags)
@@ -70,9 +70,9 @@ def test_pruning_axisymmetric_vacuum(L, edges, precision):
     c = wl.lognormal_cloud(37, 29, seed=173, v_edge_kms=100.0)
     c.geometry, c.bc = 1, (0, 1, 0, 1)
     c.lum = 1e-6 * c.lum
-    got, ref, _, _ = run_pair(L, c, edges, precision, 2, state(194, 29, 37, 174))
-    for a, b, n in zip(got, ref, ("J", "Hx", "Hy", "fx", "fy")):
-        close(a, b, TOL[precision], n)
+    st = state(194, 29, 37, 174)
+    got, ref, _, _ = run_pair(L, c, edges, precision, 2, st)
+    check_outputs(got, ref, TOL[precision], 2, st, fw_of(c, edges))
 
 
 def test_pruned_bins_stay_put_in_vacuum(L, edges):

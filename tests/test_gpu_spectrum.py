@@ -1,6 +1,7 @@
 """Emergent spectra on the GPU (escaping energy per bin and outer face):
 parity with the oracle's per-substep spectra summed over substeps (bit-exact in
-FP64_DET, 1e-4 normwise per bin in mixed_fast) and the frequency scaling of
+FP64_DET; in mixed_fast 1e-4 per element plus n u times the bin's largest
+face value) and the frequency scaling of
 escaping photons, |nu - nu_Lya| ~ (a_v tau_0)^(1/3) dnu_D (Sec. 2.1), seen
 in the peaks of the emergent spectra of two thick spheres."""
 
@@ -55,8 +56,10 @@ def test_spectrum_matches_oracle(L, edges, case, precision):
     if precision == 0:
         np.testing.assert_array_equal(got, ref)
     else:
-        scale = np.abs(ref).max(axis=1, keepdims=True)
-        assert np.all(np.abs(got - ref) <= 1e-4 * scale + 1e-300)
+        # per face: 1e-4 relative plus n FP32 roundings of the bin's largest face value
+        floor = n * 2.0 ** -24 * np.abs(ref).max(axis=1, keepdims=True)
+        excess = np.abs(got - ref) - (1e-4 * np.abs(ref) + floor)
+        assert not np.any(excess > 0), f"{int(np.sum(excess > 0))} faces beyond the bar"
     assert got.sum() == pytest.approx(dg["outflow"], rel=1e-9 if precision == 0 else 1e-4)
     assert dg["outflow"] == pytest.approx(out, rel=1e-4 if precision else 1e-12)
 

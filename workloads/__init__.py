@@ -202,11 +202,13 @@ def config_lognormal_2048(seed=1):
                            name="lognormal-2048", substeps=5000)
 
 
-def batch_clouds(n=256, base_seed=1000, side_lo=64, side_hi=512, nh_lo=1e2, nh_hi=1e5):
+def batch_clouds(n=256, base_seed=1000, side_lo=64, side_hi=512, nh_lo=1e2, nh_hi=1e5,
+                 bc=(0, 0, 0, 0)):
     """Independent clouds for a batched sweep: side log-uniform in
     [side_lo, side_hi] rounded to a multiple of 16, mean n_H log-uniform
     [nh_lo, nh_hi] (default [1e2, 1e5]), L log-uniform [1e4, 1e7] L_sun,
-    Z in {0, 1e-3, 1e-2} Z_sun."""
+    Z in {0, 1e-3, 1e-2} Z_sun; bc: the outflow kind of the four sides
+    (0 zero gradient, 1 into vacuum)."""
     g = rng(base_seed)
     out = []
     for i in range(n):
@@ -215,8 +217,10 @@ def batch_clouds(n=256, base_seed=1000, side_lo=64, side_hi=512, nh_lo=1e2, nh_h
         mean = 10 ** g.uniform(math.log10(nh_lo), math.log10(nh_hi))
         L = 10 ** g.uniform(4, 7)
         Z = (0.0, 1e-3, 1e-2)[int(g.integers(0, 3))]
-        out.append(lognormal_cloud(side, side, mean_nh=mean, sigma_ln=1.0, Z=Z, L_sun=L,
-                                   seed=base_seed + 1 + i, name=f"batch-{i}", substeps=1000))
+        c = lognormal_cloud(side, side, mean_nh=mean, sigma_ln=1.0, Z=Z, L_sun=L,
+                            seed=base_seed + 1 + i, name=f"batch-{i}", substeps=1000)
+        c.bc = tuple(bc)
+        out.append(c)
     return out
 
 
