@@ -323,13 +323,15 @@ int lym1_debug_expire_wait(lym1_ctx *ctx);
  * pipe and refine a hardware reciprocal approximation by Newton-Raphson).
  * For i < n (device pointers, caller-owned): wide[i] = xf[i] widened to FP64,
  * narrow[i] = xd[i] narrowed to FP32 (round to nearest even), rcp[i] = 1 /
- * xd[i] (two Newton-Raphson steps) and rcp1[i] = 1 / xd[i] with the one step
- * the mixed steps take; both conversions flush subnormals to zero.  Runs on
+ * xd[i] (two Newton-Raphson steps), rcp1[i] = 1 / xd[i] with the one step
+ * the mixed elimination takes, and rcpf[i] = 1 / xd[i] seeded by the FP32
+ * reciprocal with one FP64 step, as the mixed source step takes it (xd[i] in
+ * the FP32 normal range); both conversions flush subnormals to zero.  Runs on
  * the legacy default stream and synchronises it.  LYM1_EINVAL for null
  * pointers or n < 0; LYM1_ECUDA if the launch fails.
  */
 int lym1_debug_fp64_helpers(const float *xf, const double *xd, long long n, double *wide,
-                            float *narrow, double *rcp, double *rcp1);
+                            float *narrow, double *rcp, double *rcp1, double *rcpf);
 int lym1_profile_read(lym1_ctx *ctx, lym1_profile *out, int reset);
 
 /*

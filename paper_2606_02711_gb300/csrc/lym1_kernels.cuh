@@ -800,6 +800,17 @@ __device__ __forceinline__ double drcp_nr(double x) {
   return fma(y, e, y);
 }
 
+// Reciprocal of an x within the FP32 normal range, seeded by the FP32 SFU
+// reciprocal (within 2 ulp, 2^-22 relative: the XU pipe, not the FP64 one)
+// and refined by one FP64 Newton-Raphson step, which squares the error
+// (2^-44; tested against IEEE division).  For the source step, whose
+// denominators (1 + c dt kappa)(1 + c dt alpha_F) lie in [1, 1e30].
+__device__ __forceinline__ double drcp_fs(double x) {
+  const double y = f2d_alu(__fdividef(1.0f, d2f_alu(x)));
+  const double e = fma(-x, y, 1.0);
+  return fma(y, e, y);
+}
+
 // One Newton-Raphson step: the relative error of the approximation squared
 // (2^-40 measured over the normal range against IEEE division, 2^-38 the
 // tested bound), for the FP64 steps of LYM1_MIXED whose results are rounded to
@@ -1043,6 +1054,7 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
   const float cdt_dx = float(v.cdt_dx);
   const I cdt = I(v.cdt), kabs = I(v.kabs), kF = I(v.kF), cdx = I(v.cdt_dx);
   const I wR = I(v.g_wR), wcol = I(wvf);
+  const float wRf = float(v.g_wR);
   // LYM1_MIXED (FP64 implicit step): the per-cell factors with c_tilde dt
   // folded in, c dt kappa_k = cA + cB <H>_k and c dt alpha_F,k = cD + cC <H>_k
   // (bands: c dt kappa_k from their kappa table, alpha = 1, rho_d = 0)
@@ -1094,8 +1106,7 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
   // LYM1_MIXED: the FP64 implicit step of bin k - 1 (Sec. 2.1 step 2) is
   // issued in the face phase of bin k, so that GB300's narrow FP64 pipe works
   // while the FP32 face fluxes are formed; pending values of the last bin are
-  // finished after the loop.  live = false on the first pass (nothing pending):
-  // the arithmetic runs on zeros and nothing is stored or summed.
+  // finished after the loop.
   float dJ1 = 0.0f, dHx1 = 0.0f, dHy1 = 0.0f, dW = 0.0f;
   RSum<float> fxs, fys;  // LYM1_MIXED: sum_k dnu_k (H' - H'') per component
   auto step2_mix = [&](bool live, int kk, long long kbase) {
@@ -1111,7 +1122,7 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
         ck = fma(cB, Hd, cA);
       const double caF = fma(cC, Hd, cD);
       const double d1 = 1.0 + ck, d2 = 1.0 + caF;
-      const double rp = drcp_nr1(d1 * d2);
+      const double rp = drcp_fs(d1 * d2);
       const double ra = d1 * rp;
       double num = f2d_alu(dJ1);
       double gk = 0.0;
@@ -1200,7 +1211,8 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
       }
     }
     __syncthreads();
-    if constexpr (MIX) step2_mix(k > k0, k > k0 ? k - 1 : k0, k > k0 ? base - nc : base);
+    if constexpr (MIX)
+      if (k > k0) step2_mix(true, k - 1, base - nc);  // a block-uniform branch
     auto xface = [&](int fi, int fj, float wf, float dl0, float dl1) {
       // between tile cells (fi-1, fj) and (fi, fj)
       const int r = fj + 2;
@@ -1319,19 +1331,24 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
           }
         }
       }
-      const I dnu = sizeof(I) == 8 ? I(v.t_dnu[k]) : I(tb.y);
       if (bnd) {
-        I o2 = 0;
+        // the escaping flux of the cell's outer faces, formed in FP32 (the face
+        // fluxes are FP32) and added to the outflow sum once per bin
+        float o2 = 0.0f;
         if constexpr (G == 1) {
-          if (gx == nx - 1) o2 += wR * I(xr.x);
-          if (gy == ny - 1) o2 += wcol * I(yt.x);
+          if (gx == nx - 1) o2 += wRf * xr.x;
+          if (gy == ny - 1) o2 += wvf * yt.x;
         } else {
-          if (gx == 0) o2 -= I(xl.x);
-          if (gx == nx - 1) o2 += I(xr.x);
-          if (gy == 0) o2 -= I(yb.x);
-          if (gy == ny - 1) o2 += I(yt.x);
+          if (gx == 0) o2 -= xl.x;
+          if (gx == nx - 1) o2 += xr.x;
+          if (gy == 0) o2 -= yb.x;
+          if (gy == ny - 1) o2 += yt.x;
         }
-        out += dnu * (cdx * o2);
+        const I dnu = sizeof(I) == 8 ? I(v.t_dnu[k]) : I(tb.y);
+        if constexpr (sizeof(I) == 8)
+          out = fma(dnu * cdx, f2d_alu(o2), out);
+        else
+          out += dnu * (cdx * o2);
         if (v.spec) {  // emergent spectrum: the escaping energy of each outer face
           double* sp = v.spec + static_cast<long long>(k) * v.nf;
           const double dxd = v.dx;
@@ -1350,7 +1367,8 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
     }
     base = nbase;
   }
-  if constexpr (MIX) step2_mix(k1 > k0, k1 - 1, base - nc);
+  if constexpr (MIX)
+    if (k1 > k0) step2_mix(true, k1 - 1, base - nc);
   if (valid && !DF) {
     if constexpr (MIX)
       store_force(v, cell, grp, fxs.value(), fys.value());

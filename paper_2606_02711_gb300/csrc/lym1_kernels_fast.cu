@@ -54,25 +54,26 @@ int resident_blocks_fast(int precision, int kind, int geometry, int pt, int nb_m
 }
 
 __global__ void fp64_helpers_kernel(const float* xf, const double* xd, long long n, double* wide,
-                                    float* narrow, double* rcp, double* rcp1) {
+                                    float* narrow, double* rcp, double* rcp1, double* rcpf) {
   const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= n) return;
   wide[i] = f2d_alu(xf[i]);
   narrow[i] = d2f_alu(xd[i]);
   rcp[i] = drcp_nr(xd[i]);
   rcp1[i] = drcp_nr1(xd[i]);
+  rcpf[i] = drcp_fs(xd[i]);
 }
 
 }  // namespace lym1
 
 extern "C" int lym1_debug_fp64_helpers(const float* xf, const double* xd, long long n, double* wide,
-                                       float* narrow, double* rcp, double* rcp1) {
-  if (!xf || !xd || !wide || !narrow || !rcp || !rcp1 || n < 0) return LYM1_EINVAL;
+                                       float* narrow, double* rcp, double* rcp1, double* rcpf) {
+  if (!xf || !xd || !wide || !narrow || !rcp || !rcp1 || !rcpf || n < 0) return LYM1_EINVAL;
   if (n == 0) return LYM1_OK;
   const long long blocks = (n + 255) / 256;
   if (blocks > 0x7fffffffLL) return LYM1_EINVAL;
   lym1::fp64_helpers_kernel<<<static_cast<unsigned>(blocks), 256>>>(xf, xd, n, wide, narrow, rcp,
-                                                                     rcp1);
+                                                                     rcp1, rcpf);
   if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
     cudaGetLastError();
     return LYM1_ECUDA;

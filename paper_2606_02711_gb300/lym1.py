@@ -120,7 +120,7 @@ SIGNATURES = {
     "lym1_batch_destroy": (None, [C.c_void_p]),
     "lym1_debug_expire_wait": (C.c_int, [C.c_void_p]),
     "lym1_debug_fp64_helpers": (C.c_int, [C.c_void_p, C.c_void_p, C.c_longlong, C.c_void_p,
-                                          C.c_void_p, C.c_void_p, C.c_void_p]),
+                                          C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "lym1_energy_noalloc": (C.c_int, [_PD, _PD, C.c_int, C.c_longlong, C.c_double, _PD,
                                       C.c_void_p]),
 }

@@ -6,7 +6,8 @@ pipe and refine the hardware reciprocal approximation by Newton-Raphson.
 Widening must be exact and narrowing correctly rounded (to nearest, ties to
 even) wherever the result is a binary32 normal number or infinity; both flush
 subnormals to zero.  The reciprocal must lie within one ulp of 1/x; the one-step reciprocal of the
-mixed steps (whose results are rounded to FP32) within 2^-38 of it.  numpy's
+mixed elimination (whose results are rounded to FP32) within 2^-38 of it, and
+the FP32-seeded one of the mixed source step within 2^-40 over [1, 1e30].  numpy's
 conversions and division are the IEEE reference.
 """
 import ctypes as C
@@ -30,11 +31,14 @@ def _run(xf, xd):
     narrow = torch.empty(n, dtype=torch.float32, device="cuda")
     rcp = torch.empty(n, dtype=torch.float64, device="cuda")
     rcp1 = torch.empty(n, dtype=torch.float64, device="cuda")
+    rcpf = torch.empty(n, dtype=torch.float64, device="cuda")
     st = L.lib().lym1_debug_fp64_helpers(C.c_void_p(a.data_ptr()), C.c_void_p(b.data_ptr()), n,
                                          C.c_void_p(wide.data_ptr()), C.c_void_p(narrow.data_ptr()),
-                                         C.c_void_p(rcp.data_ptr()), C.c_void_p(rcp1.data_ptr()))
+                                         C.c_void_p(rcp.data_ptr()), C.c_void_p(rcp1.data_ptr()),
+                                         C.c_void_p(rcpf.data_ptr()))
     assert st == 0
     _run.rcp1 = rcp1.cpu().numpy()
+    _run.rcpf = rcpf.cpu().numpy()
     return wide.cpu().numpy(), narrow.cpu().numpy(), rcp.cpu().numpy()
 
 
@@ -117,3 +121,15 @@ def test_one_step_reciprocal_within_2_pow_minus_38():
     _run(np.ones(n, dtype=np.float32), xd)
     rel = np.abs(_run.rcp1 * xd - 1.0)
     assert rel.max() <= 2.0 ** -38, f"max relative error 2^{np.log2(rel.max()):.1f}"
+
+
+def test_fp32_seeded_reciprocal_within_2_pow_minus_40():
+    # the source step's denominators (1 + c dt kappa)(1 + c dt alpha_F) lie in
+    # [1, 1e30]: an FP32 SFU seed (2 ulp) and one FP64 Newton step
+    g = np.random.default_rng(5)
+    n = 1 << 20
+    xd = 10.0 ** g.uniform(0.0, 30.0, n) * g.uniform(1.0, 10.0, n) / 10.0
+    xd[:6] = [1.0, 1.0 + 2 ** -52, 2.0, 3.0, 1e30, 7.0]
+    _run(np.ones(n, dtype=np.float32), np.maximum(xd, 1.0))
+    rel = np.abs(_run.rcpf * np.maximum(xd, 1.0) - 1.0)
+    assert rel.max() <= 2.0 ** -40, f"max relative error 2^{np.log2(rel.max()):.1f}"
