@@ -344,7 +344,7 @@ def main():
             "freq": (prof["freq_ms"], prof["freq_launches"], nc * (6.0 * nb * selem + 32.0))}
     dom = max(kern, key=lambda k: kern[k][0])
     kms, kl, kbytes = kern[dom]
-    avg_s = kms / max(kl, 1) * 1e-3
+    avg_s = max(kms / max(kl, 1) * 1e-3, 1e-12)  # no profiled launch: a null roofline
     hbm_gbs = kbytes / avg_s / 1e9
     peak, peak_kind = _peaks()
     traffic, tsrc = _traffic_from_profiles(dom, NAMES[prec])

@@ -1435,12 +1435,14 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
   }
 }
 
-// blocks per SM the FP32 tile is register-budgeted for: 3 (80 registers);
-// LYM1_MIXED's FP64 step holds more live values and is bound by the FP64
-// pipe, not by latency, so it takes 2 blocks of up to 128 registers
+// blocks per SM the FP32 tile is register-budgeted for: 3 (80 registers).
+// LYM1_MIXED's FP64 step holds more live values: at 3 blocks it spills
+// ~60 bytes a thread, yet the third block's warps hide enough of the FP64
+// pipe's latency to win (512^2 x 194: 2.47 ms at 2 blocks of 128 registers,
+// 2.19 ms at 3, 2.38 ms at 4 with 190 bytes of spills)
 template <class P>
 __host__ __device__ constexpr int tile_f32_min_blocks() {
-  return sizeof(typename P::I) == 8 ? 2 : 3;
+  return 3;
 }
 
 template <class P, int G, int PT>
