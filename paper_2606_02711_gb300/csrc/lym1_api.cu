@@ -64,6 +64,7 @@ struct lym1_ctx {
   void* B[3] = {nullptr, nullptr, nullptr};  // ping-pong partner
   double *alpha = nullptr, *rho = nullptr, *pd = nullptr, *ux = nullptr, *uy = nullptr;
   double *gxx = nullptr, *gyy = nullptr, *gsh = nullptr, *lum = nullptr;
+  double *t_dH = nullptr;
   double *t_dnu = nullptr, *t_H = nullptr, *t_gem = nullptr, *t_half = nullptr, *t_R = nullptr,
          *t_nbc = nullptr;
   double *fx = nullptr, *fy = nullptr, *partT = nullptr, *partF = nullptr, *acc = nullptr;
@@ -179,6 +180,7 @@ DeviceView make_view(const lym1_ctx* c, double dt) {
   v.t_half = c->t_half;
   v.t_R = c->t_R;
   v.t_nbc = c->t_nbc;
+  v.t_dH = c->t_dH;
   v.fx = c->fx;
   v.fy = c->fy;
   v.partT = c->partT;
@@ -832,7 +834,7 @@ static int create_impl(const lym1_grid* grid, const lym1_groups* groups, const l
                             &c->gyy,   &c->gsh, &c->lum, &c->fx, &c->fy, &c->staging};
   for (double** p : cell_arrays)
     if (rc == LYM1_OK) rc = dalloc_t(c, p, plane);
-  double** bin_arrays[] = {&c->t_dnu, &c->t_H, &c->t_gem, &c->t_half, &c->t_R, &c->t_nbc};
+  double** bin_arrays[] = {&c->t_dnu, &c->t_H, &c->t_gem, &c->t_half, &c->t_R, &c->t_nbc, &c->t_dH};
   for (double** p : bin_arrays)
     if (rc == LYM1_OK) rc = dalloc_t(c, p, static_cast<size_t>(c->nb));
   if (rc == LYM1_OK) rc = dalloc_t(c, &c->partT, static_cast<size_t>(transport_blocks(c->nx, c->ny)) * kDiagSlots);
@@ -992,6 +994,12 @@ static int create_impl(const lym1_grid* grid, const lym1_groups* groups, const l
     if (cudaMemcpyAsync(dtabs[i], tabs[i]->data(), sizeof(double) * c->nb, cudaMemcpyHostToDevice, s) !=
         cudaSuccess)
       return fail(LYM1_ECUDA);
+  {  // dnu_k <H>_k (the destruction part of the mixed step's absorbed energy)
+    std::vector<double> dH(c->nb);
+    for (int k = 0; k < c->nb; ++k) dH[k] = c->tab.dnu[k] * c->tab.Havg[k];
+    if (cudaMemcpy(c->t_dH, dH.data(), sizeof(double) * c->nb, cudaMemcpyHostToDevice) != cudaSuccess)
+      return fail(LYM1_ECUDA);
+  }
   // FP32 table copies (the emissivity factor scaled by its maximum)
   std::vector<float> fh[6];
   for (int k = 0; k < c->nb; ++k) {

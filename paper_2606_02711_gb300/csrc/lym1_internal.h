@@ -123,6 +123,7 @@ struct DeviceView {
   const double* t_half = nullptr;
   const double* t_R = nullptr;
   const double* t_nbc = nullptr;
+  const double* t_dH = nullptr;  // dnu_k <H>_k
   // outputs
   double* fx = nullptr;
   double* fy = nullptr;

@@ -800,13 +800,42 @@ __device__ __forceinline__ double drcp_nr(double x) {
   return fma(y, e, y);
 }
 
-// Reciprocal of an x within the FP32 normal range, seeded by the FP32 SFU
-// reciprocal (within 2 ulp, 2^-22 relative: the XU pipe, not the FP64 one)
-// and refined by one FP64 Newton-Raphson step, which squares the error
-// (2^-44; tested against IEEE division).  For the source step, whose
-// denominators (1 + c dt kappa)(1 + c dt alpha_F) lie in [1, 1e30].
+// Seed of 1/x for a binary64 normal x > 0 below 2^1020, without the FP64 pipe:
+// x = m 2^q with m in [1, 2); the top 23 bits of m's fraction form a binary32
+// m' in [1, 2) (truncated, within 2^-23 of m), whose SFU reciprocal r lies in
+// (1/2, 1] (XU pipe); r widened to binary64 and its exponent lowered by q is
+// the seed, within ~2^-22 of 1/x.  Integer-pipe bit operations otherwise.
+// Also returns q and r's bits, from which the binary32 seed follows.
+__device__ __forceinline__ double rcp_seed(double x, int& q, unsigned& rb) {
+  const unsigned hi = static_cast<unsigned>(__double2hiint(x));
+  const unsigned lo = static_cast<unsigned>(__double2loint(x));
+  const unsigned mb = 0x3f800000u | ((hi & 0x000fffffu) << 3) | (lo >> 29);
+  rb = __float_as_uint(__fdividef(1.0f, __uint_as_float(mb)));
+  q = static_cast<int>(hi >> 20) - 1023;
+  const unsigned yhi = ((rb >> 3) + 0x38000000u) - (static_cast<unsigned>(q) << 20);
+  return __hiloint2double(static_cast<int>(yhi), static_cast<int>(rb << 29));
+}
+
+__device__ __forceinline__ double rcp_seed(double x) {
+  int q;
+  unsigned rb;
+  return rcp_seed(x, q, rb);
+}
+
+// binary64 -> binary32 by truncation, for small correction terms: |x| below
+// 2^127; results below the binary32 normal range flush to signed zero
+__device__ __forceinline__ float d2f_trunc(double x) {
+  const unsigned hi = static_cast<unsigned>(__double2hiint(x));
+  const unsigned lo = static_cast<unsigned>(__double2loint(x));
+  const unsigned a = hi & 0x7fffffffu;
+  const unsigned f = a < 0x38100000u ? 0u : (((a - 0x38000000u) << 3) | (lo >> 29));
+  return __uint_as_float((hi & 0x80000000u) | f);
+}
+
+// Reciprocal of x > 0 from that seed and one FP64 Newton-Raphson step, which
+// squares the error (2^-44; tested against IEEE division).
 __device__ __forceinline__ double drcp_fs(double x) {
-  const double y = f2d_alu(__fdividef(1.0f, d2f_alu(x)));
+  const double y = rcp_seed(x);
   const double e = fma(-x, y, 1.0);
   return fma(y, e, y);
 }
@@ -1060,6 +1089,10 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
   // (bands: c dt kappa_k from their kappa table, alpha = 1, rho_d = 0)
   constexpr bool MIX = sizeof(I) == 8 && !DF;
   double cA = 0.0, cB = 0.0, cC = 0.0, cD = 0.0, cjs = 0.0;
+  // 1 + cA and 1 + cD (the denominators of step 2 in one FMA each) and FP32
+  // copies of cC, cD for the force weight
+  double cA1 = 1.0, cD1 = 1.0;
+  float cCf = 0.0f, cDf = 0.0f;
   // emission of a uniform-temperature cell over this block's bins k0..k1-1:
   // c dt L_cell sum_k dnu_k gem_k
   double sgk = 0.0;
@@ -1070,6 +1103,10 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
     cC = cd * double(alpha_c);
     cD = cd * (double(rho_c) * v.kF);
     cjs = cd * lum_d;
+    cA1 = 1.0 + cA;
+    cD1 = 1.0 + cD;
+    cCf = d2f_alu(cC);
+    cDf = d2f_alu(cD);
     if constexpr (TM == 0)
       if (lum_d != 0.0)
         for (int k = k0; k < k1; ++k) sgk = fma(v.t_dnu[k], v.t_gem[k], sgk);
@@ -1079,6 +1116,9 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
   // enough at 194 terms) for LYM1_MIXED, plain FP32 for LYM1_MIXED_FAST; the
   // sums over cells are FP64 in both
   I em = 0, ab = 0, out = 0, wk = 0, en = 0;
+  // LYM1_MIXED, Lya table modes: the absorbed energy sum_k dnu_k c dt kappa_k J''_k
+  // as cA sum_k dnu_k J''_k + cB sum_k dnu_k <H>_k J''_k (c dt kappa_k = cA + cB <H>_k)
+  double sJ = 0.0, sHJ = 0.0;
   float mxf2 = 0.0f;
   int bad = 0;
   // source term c_tilde dt j_k = (c_tilde dt L_cell gem_max) (gem_k / gem_max):
@@ -1109,53 +1149,70 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
   // finished after the loop.
   float dJ1 = 0.0f, dHx1 = 0.0f, dHy1 = 0.0f, dW = 0.0f;
   RSum<float> fxs, fys;  // LYM1_MIXED: sum_k dnu_k (H' - H'') per component
-  auto step2_mix = [&](bool live, int kk, long long kbase) {
+  auto step2_mix = [&](int kk, long long kbase) {
     if constexpr (MIX) {
-      // one shared reciprocal: r = 1 / (d1 d2) gives 1/d1 = d2 r and
-      // 1/d2 = d1 r, with d1 = 1 + c dt kappa_k and d2 = 1 + c dt alpha_F,k
+      // d1 = 1 + c dt kappa_k and d2 = 1 + c dt alpha_F,k, each in one FMA
       const double Hd = TM ? f2d_alu(Hcf[kbase + cell]) : v.t_H[kk];
       const double dnud = v.t_dnu[kk];
-      double ck;
-      if constexpr (TM == 2)
+      double ck = 0.0, d1;
+      if constexpr (TM == 2) {
         ck = v.cdt * f2d_alu(Kbf[kbase + cell]);
-      else
-        ck = fma(cB, Hd, cA);
-      const double caF = fma(cC, Hd, cD);
-      const double d1 = 1.0 + ck, d2 = 1.0 + caF;
-      const double rp = drcp_fs(d1 * d2);
-      const double ra = d1 * rp;
+        d1 = 1.0 + ck;
+      } else {
+        d1 = fma(cB, Hd, cA1);
+      }
+      const double d2 = fma(cC, Hd, cD1);
       double num = f2d_alu(dJ1);
       double gk = 0.0;
       if (src) {
         gk = TM ? gmax_c * f2d_alu(Gcf[kbase + cell]) : v.t_gem[kk];
         num = fma(cjs, gk, num);
       }
-      const double J2d = num * (d2 * rp);
+      // J'' = num / d1 in FP64: the FP32 seed y of 1/d1 (d1 >= 1) and one
+      // Newton-Raphson step folded into the product, num y (1 + e) with the
+      // FP64 residual e = 1 - d1 y (relative error e^2 ~ 2^-44)
+      const double y1 = rcp_seed(d1);
+      const double e1 = fma(-d1, y1, 1.0);
+      const double t1 = num * y1;
+      const double J2d = fma(t1, e1, t1);
       const float J2 = d2f_alu(J2d);
-      // H'' = H' / d2 with the FP64 factor (H is FP32 state); the force term
-      // dnu_k (H' - H'') = dnu_k (c dt alpha_F / d2) H' has no cancellation
-      const float raf = d2f_alu(ra);
+      // H'' = H' / d2 with the factor 1/d2 rounded to the FP32 of the state:
+      // the FP32 seed corrected by its FP64 residual (the correction itself,
+      // ~2^-22 of the seed, needs no more than FP32)
+      int q2;
+      unsigned rb2;
+      const double y2d = rcp_seed(d2, q2, rb2);
+      const double e2 = fma(-d2, y2d, 1.0);
+      // the same seed in binary32 (d2 >= 1, so q2 >= 0; 1/d2 below the binary32
+      // normal range flushes to zero, as the state's FP32 arithmetic would)
+      const float y2 = q2 < 126 ? __uint_as_float(rb2 - (static_cast<unsigned>(q2) << 23)) : 0.0f;
+      const float raf = fmaf(y2, d2f_trunc(e2), y2);
       const float Hx2 = dHx1 * raf, Hy2 = dHy1 * raf;
-      if (live && valid) {
+      if (valid) {
         (Jout + kbase)[cell32] = J2;
         (Hxout + kbase)[cell32] = Hx2;
         (Hyout + kbase)[cell32] = Hy2;
       }
-      // dnu_k c dt alpha_F / d2 (the force weight, summed in FP32 below)
-      const float wq = tab4[kk].y * (d2f_alu(caF) * raf);
-      // A7 bookkeeping in FP64 (c_tilde dt is in ck; 1/c and the energy units
-      // once per substep); the force, not a conservation sum, in compensated
-      // FP32 (off the FP64 pipe)
+      // the force term dnu_k (H' - H'') = dnu_k (c dt alpha_F / d2) H' has no
+      // cancellation; its weight dnu_k c dt alpha_F / d2 is FP32 (the force is
+      // summed in compensated FP32, off the FP64 pipe)
+      const float caFf = fmaf(cCf, TM ? Hcf[kbase + cell] : tab4[kk].x, cDf);
+      const float wq = tab4[kk].y * (caFf * raf);
+      // A7 bookkeeping in FP64 (c_tilde dt is in the factors; 1/c and the
+      // energy units once per substep)
       const double twk = f2d_alu(tab4[kk].y * dW);
-      if (live) {
-        fxs.add(wq * dHx1);
-        fys.add(wq * dHy1);
+      fxs.add(wq * dHx1);
+      fys.add(wq * dHy1);
+      if constexpr (TM == 2) {
+        ab = fma(dnud * ck, J2d, ab);
+      } else {
+        sJ = fma(dnud, J2d, sJ);
+        sHJ = fma(TM ? dnud * Hd : v.t_dH[kk], J2d, sHJ);
       }
-      ab = fma(live ? dnud * ck : 0.0, J2d, ab);
-      wk = live ? wk + twk : wk;
-      if constexpr (TM != 0) em = live ? fma(dnud, gk, em) : em;
-      if (tdiag && live) {  // the frequency step recomputes these when it follows
-        en = fma(dnud, J2d, en);
+      wk = wk + twk;
+      if constexpr (TM != 0) em = fma(dnud, gk, em);
+      if (tdiag) {  // the frequency step recomputes these when it follows
+        if constexpr (TM == 2) en = fma(dnud, J2d, en);
         const float h2 = Hx2 * Hx2 + Hy2 * Hy2, jj = J2 * J2;
         if ((G == 1 ? J2 * wvf : J2) > tab4[kk].w) {
           mxf2 = fmaxf(mxf2, fdiv(h2, jj));
@@ -1212,7 +1269,7 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
     }
     __syncthreads();
     if constexpr (MIX)
-      if (k > k0) step2_mix(true, k - 1, base - nc);  // a block-uniform branch
+      if (k > k0) step2_mix(k - 1, base - nc);  // a block-uniform branch
     auto xface = [&](int fi, int fj, float wf, float dl0, float dl1) {
       // between tile cells (fi-1, fj) and (fi, fj)
       const int r = fj + 2;
@@ -1367,8 +1424,13 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
     }
     base = nbase;
   }
-  if constexpr (MIX)
-    if (k1 > k0) step2_mix(true, k1 - 1, base - nc);
+  if constexpr (MIX) {
+    if (k1 > k0) step2_mix(k1 - 1, base - nc);
+    if constexpr (TM != 2) {
+      ab = fma(cA, sJ, cB * sHJ);
+      en = sJ;
+    }
+  }
   if (valid && !DF) {
     if constexpr (MIX)
       store_force(v, cell, grp, fxs.value(), fys.value());
@@ -1474,7 +1536,7 @@ template <class P>
 __device__ __forceinline__ typename P::I rcp_elim(typename P::I x) {
   using I = typename P::I;
   if constexpr (sizeof(I) == 4) return frcp(x);
-  else if constexpr (freq_mix<P>()) return drcp_nr1(x);
+  else if constexpr (freq_mix<P>()) return drcp_fs(x);
   else return I(1) / x;
 }
 // Exponential of the frequency-step coefficients: the FP64 policies' own
@@ -1932,6 +1994,9 @@ __device__ __forceinline__ void freq_block_bulk(const DeviceView& v, int blk) {
   I* tact = tdi + nb;
   float* tactf = reinterpret_cast<float*>(tact);
   I* tsk = MIX ? tact + nb : nullptr;
+  // LYM1_MIXED: s_k in FP32 in the spare half of tact (the right-hand side s_k J_k
+  // is formed in FP32, like the other coefficients)
+  float* tskf = tactf + nb;
   T* tabs = reinterpret_cast<T*>(MIX ? tsk + nb : tact + nb);
   T* tH = tabs;
   T* tR = tabs + nb;
@@ -1951,6 +2016,7 @@ __device__ __forceinline__ void freq_block_bulk(const DeviceView& v, int blk) {
     if constexpr (MIX) {
       tactf[i] = fmaxf(thr, 1e-30f) / v.f_dnu[i];
       tsk[i] = v.t_dnu[i] * v.rcdt;
+      tskf[i] = d2f_alu(tsk[i]);
     } else {
       tact[i] = I(fmaxf(thr, 1e-30f) / v.f_dnu[i]);
     }
@@ -2072,7 +2138,11 @@ __device__ __forceinline__ void freq_block_bulk(const DeviceView& v, int blk) {
           E = (k == 1) ? sk : sk + Bprev * qprev;
         else
           E = (k == 1) ? sk : sk + hprev * Eprev;
-        const I r = (k == 1) ? sk * Jp : sk * Jp + Aprev * gprev;
+        I r;
+        if constexpr (MIX)  // Jp holds s_{k-1} J_{k-1}
+          r = (k == 1) ? Jp : fma(Aprev, gprev, Jp);
+        else
+          r = (k == 1) ? sk * Jp : sk * Jp + Aprev * gprev;
         const I Dp = E + A;
         const I inv = rcp_elim<P>(Dp);
         const I g = r * inv;
@@ -2091,7 +2161,10 @@ __device__ __forceinline__ void freq_block_bulk(const DeviceView& v, int blk) {
       Pp = Pk;
       ap = ak;
       ep = ek;
-      Jp = to_elim<P>(Jc);
+      if constexpr (MIX)
+        Jp = f2d_alu(tskf[k] * Jc);
+      else
+        Jp = to_elim<P>(Jc);
     }
     if (__syncthreads_or(okF ? 0 : 1)) {  // stage s consumed (or a wait ran out)
       give_up(barF, nb < k + D ? nb : k + D, k);
@@ -2112,7 +2185,11 @@ __device__ __forceinline__ void freq_block_bulk(const DeviceView& v, int blk) {
       E = (nb == 1) ? sk : sk + Bprev * qprev;
     else
       E = (nb == 1) ? sk : sk + hprev * Eprev;
-    const I r = (nb == 1) ? sk * Jp : sk * Jp + Aprev * gprev;
+    I r;
+    if constexpr (MIX)
+      r = (nb == 1) ? Jp : fma(Aprev, gprev, Jp);
+    else
+      r = (nb == 1) ? sk * Jp : sk * Jp + Aprev * gprev;
     const I inv = rcp_elim<P>(E);
     const long long o = static_cast<long long>(nb - 1) * nc + cell;
     Jout[o] = to_state<P>(r * inv);
@@ -2147,14 +2224,14 @@ __device__ __forceinline__ void freq_block_bulk(const DeviceView& v, int blk) {
         Jout[o] = Jnf;
         Hxout[o] = Hx2;
         Hyout[o] = Hy2;
-        en.add(I(tdi[k] * Jn));
+        if constexpr (MIX) en.s = fma(tdi[k], Jn, en.s);
       } else if (MIX) {
         float Hxi = Xo, Hyi = Yo;
         causal_stats_f32(Jo, Hxi, Hyi, wf, tactf[k], mxf2, bad);
         Jout[o] = Jo;
         Hxout[o] = Hxi;
         Hyout[o] = Hyi;
-        en.add(I(tdi[k] * f2d_alu(Jo)));
+        if constexpr (MIX) en.s = fma(tdi[k], f2d_alu(Jo), en.s);
       } else if (act) {
         const I g = I(ring[s][0][tid]), h = I(ring[s][1][tid]);
         const I Jn = (j == 0) ? g : g + h * Jnext;

@@ -5,9 +5,9 @@ GB300 runs FP64 arithmetic and FP32 <-> FP64 conversions on a pipe of about
 pipe and refine the hardware reciprocal approximation by Newton-Raphson.
 Widening must be exact and narrowing correctly rounded (to nearest, ties to
 even) wherever the result is a binary32 normal number or infinity; both flush
-subnormals to zero.  The reciprocal must lie within one ulp of 1/x; the one-step reciprocal of the
-mixed elimination (whose results are rounded to FP32) within 2^-38 of it, and
-the FP32-seeded one of the mixed source step within 2^-40 over [1, 1e30].  numpy's
+subnormals to zero.  The reciprocal must lie within one ulp of 1/x; the one-step reciprocal
+(whose results are rounded to FP32) within 2^-38 of it, and the FP32-seeded one
+of the mixed source step and elimination within 2^-40 over the normal range.  numpy's
 conversions and division are the IEEE reference.
 """
 import ctypes as C
@@ -124,12 +124,15 @@ def test_one_step_reciprocal_within_2_pow_minus_38():
 
 
 def test_fp32_seeded_reciprocal_within_2_pow_minus_40():
-    # the source step's denominators (1 + c dt kappa)(1 + c dt alpha_F) lie in
-    # [1, 1e30]: an FP32 SFU seed (2 ulp) and one FP64 Newton step
+    # the mixed source step's denominators 1 + c dt kappa, 1 + c dt alpha_F and
+    # the elimination's pivots: the seed is the FP32 SFU reciprocal of the
+    # significand (exponent handled apart, so any normal x below 2^1020), and
+    # one FP64 Newton step squares its error
     g = np.random.default_rng(5)
     n = 1 << 20
-    xd = 10.0 ** g.uniform(0.0, 30.0, n) * g.uniform(1.0, 10.0, n) / 10.0
-    xd[:6] = [1.0, 1.0 + 2 ** -52, 2.0, 3.0, 1e30, 7.0]
-    _run(np.ones(n, dtype=np.float32), np.maximum(xd, 1.0))
-    rel = np.abs(_run.rcpf * np.maximum(xd, 1.0) - 1.0)
+    xd = 10.0 ** g.uniform(-300.0, 300.0, n) * g.uniform(1.0, 10.0, n)
+    xd[:12] = [1.0, 1.0 + 2 ** -52, 2.0 - 2 ** -52, 2.0, 3.0, 1e30, 7.0, 2.0 ** 1019,
+               2.0 ** -1021, 1.5 * 2.0 ** -1000, np.nextafter(1.0, 0.0), 1e-5]
+    _run(np.ones(n, dtype=np.float32), xd)
+    rel = np.abs(_run.rcpf * xd - 1.0)
     assert rel.max() <= 2.0 ** -40, f"max relative error 2^{np.log2(rel.max()):.1f}"
