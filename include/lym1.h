@@ -183,6 +183,32 @@ int lym1_set_state(lym1_ctx *ctx, const double *J, const double *Hx, const doubl
 int lym1_get_state(lym1_ctx *ctx, double *J, double *Hx, double *Hy);
 
 /*
+ * Halo rows of a y-slab decomposition of one grid over several GPUs (the
+ * multi-GPU form of the substep; the paper's own code parallelises with
+ * threads on one machine, Sec. 2.2).  The substep's stencil reaches two cells
+ * each way (the MinMod face states of Sec. 2.1 step 1) and steps 2 and 3 are
+ * cell-local, so a slab rank needs only its neighbours' two edge rows before
+ * each substep: these calls move whole rows in the state's own element type,
+ * without the FP64 conversion of lym1_get_state / lym1_set_state.
+ *
+ * lym1_state_elem_size: *bytes = 4 under LYM1_MIXED and LYM1_MIXED_FAST, else 8.
+ * lym1_get_rows copies rows [y0, y0 + n_rows) of every bin of J, Hx, Hy into
+ * caller buffers laid out [nb][n_rows][nx] of that element type; lym1_set_rows
+ * copies such buffers into those rows.  Buffers are host or device memory
+ * (unified addressing), owned by the caller.  Both calls only enqueue the
+ * copies on the context's stream (one strided copy per array): read a host
+ * buffer, or hand a device buffer to another stream, after lym1_synchronize;
+ * the buffers of lym1_set_rows must stay unchanged until the stream has
+ * passed the copy.  lym1_set_rows leaves the diagnostic counters running.
+ * LYM1_EINVAL for a null pointer, n_rows < 0 or rows outside [0, ny);
+ * n_rows = 0 copies nothing.
+ */
+int lym1_state_elem_size(lym1_ctx *ctx, int *bytes);
+int lym1_get_rows(lym1_ctx *ctx, int y0, int n_rows, void *J, void *Hx, void *Hy);
+int lym1_set_rows(lym1_ctx *ctx, int y0, int n_rows, const void *J, const void *Hx,
+                  const void *Hy);
+
+/*
  * Enqueues n substeps of length dt_s on the context's stream (dt_s <= 0 means
  * the CFL step dt_RT).  Asynchronous: returns after the launches; errors of
  * the kernels themselves surface at the next synchronising call.

@@ -440,7 +440,7 @@ double plan_context_bytes(long long nx, long long ny, long long nb, size_t selem
   const double nstate = plane * static_cast<double>(nb), ncol = static_cast<double>(nx);
   const double tb = static_cast<double>(transport_blocks(static_cast<int>(nx), static_cast<int>(ny)));
   const double fb = static_cast<double>(freq_blocks(static_cast<long long>(plane)));
-  double t = 6.0 * a(nstate * selem) + 12.0 * a(plane * 8) + 6.0 * a(nb * 8.0);
+  double t = 6.0 * a(nstate * selem) + 12.0 * a(plane * 8) + 7.0 * a(nb * 8.0);
   t += a(tb * kDiagSlots * 8) + a(fb * kDiagSlots * 8) + a(16 * 8) + a(2.0 * kForceBlocks * 8);
   t += a(4 * sizeof(int)) + a(2 * sizeof(unsigned long long)) + a(kSumWork * 8) + 6.0 * a(nb * 4.0);
   if (mode == 2) t += 3.0 * a(nstate * selem) + 2.0 * a(plane * 8);
@@ -1135,6 +1135,39 @@ int lym1_get_state(lym1_ctx* c, double* J, double* Hx, double* Hy) {
   if (rc == LYM1_OK) rc = state_out(c, c->A[2], Hy, 1.0);
   if (rc != LYM1_OK) return rc;
   LYM1_TRY(cudaStreamSynchronize(c->stream));
+  return LYM1_OK;
+}
+
+int lym1_state_elem_size(lym1_ctx* c, int* bytes) {
+  if (!c || !bytes) return LYM1_EINVAL;
+  *bytes = static_cast<int>(c->selem);
+  return LYM1_OK;
+}
+
+int lym1_get_rows(lym1_ctx* c, int y0, int n_rows, void* J, void* Hx, void* Hy) {
+  if (!c || !J || !Hx || !Hy || y0 < 0 || n_rows < 0 || y0 > c->ny - n_rows) return LYM1_EINVAL;
+  if (n_rows == 0) return LYM1_OK;
+  // every bin's rows [y0, y0 + n_rows) are contiguous: one strided copy per array
+  const size_t w = static_cast<size_t>(n_rows) * c->nx * c->selem;
+  const size_t off = static_cast<size_t>(y0) * c->nx * c->selem;
+  const size_t pitch = static_cast<size_t>(c->nc) * c->selem;
+  void* dst[3] = {J, Hx, Hy};
+  for (int i = 0; i < 3; ++i)
+    LYM1_TRY(cudaMemcpy2DAsync(dst[i], w, static_cast<const char*>(c->A[i]) + off, pitch, w,
+                               static_cast<size_t>(c->nb), cudaMemcpyDefault, c->stream));
+  return LYM1_OK;
+}
+
+int lym1_set_rows(lym1_ctx* c, int y0, int n_rows, const void* J, const void* Hx, const void* Hy) {
+  if (!c || !J || !Hx || !Hy || y0 < 0 || n_rows < 0 || y0 > c->ny - n_rows) return LYM1_EINVAL;
+  if (n_rows == 0) return LYM1_OK;
+  const size_t w = static_cast<size_t>(n_rows) * c->nx * c->selem;
+  const size_t off = static_cast<size_t>(y0) * c->nx * c->selem;
+  const size_t pitch = static_cast<size_t>(c->nc) * c->selem;
+  const void* src[3] = {J, Hx, Hy};
+  for (int i = 0; i < 3; ++i)
+    LYM1_TRY(cudaMemcpy2DAsync(static_cast<char*>(c->A[i]) + off, pitch, src[i], w, w,
+                               static_cast<size_t>(c->nb), cudaMemcpyDefault, c->stream));
   return LYM1_OK;
 }
 

@@ -1656,6 +1656,7 @@ __device__ __forceinline__ void freq_block(const DeviceView& v, int blk) {
   // LYM1_MIXED: the threshold in FP32, and dnu_k / (c dt) in FP64
   float* tactf = reinterpret_cast<float*>(tact);
   I* tsk = MIX ? tact + nb : nullptr;
+  float* tskf = tactf + nb;  // LYM1_MIXED: s_k in FP32 (the spare half of tact)
   T* tabs = reinterpret_cast<T*>(MIX ? tsk + nb : tact + nb);
   T* tH = tabs;
   T* tR = tabs + nb;
@@ -1668,6 +1669,7 @@ __device__ __forceinline__ void freq_block(const DeviceView& v, int blk) {
       if constexpr (MIX) {
         tactf[i] = fmaxf(thr, 1e-30f) / v.f_dnu[i];
         tsk[i] = v.t_dnu[i] * v.rcdt;
+        tskf[i] = d2f_alu(tsk[i]);
       } else {
         tact[i] = I(fmaxf(thr, 1e-30f) / v.f_dnu[i]);
       }
@@ -1741,7 +1743,8 @@ __device__ __forceinline__ void freq_block(const DeviceView& v, int blk) {
       const float rcdt = float(1.0 / v.cdt);
       (void)rcdt;
       F P0, a0, e0, P1 = F(0), a1 = F(0), e1 = F(0);
-      I Jin0 = to_elim<P>(F(Jin[cell]));
+      // LYM1_MIXED: Jin0, Jin1 hold s_k J_k formed in FP32 (as the bulk-copy sweep)
+      I Jin0 = MIX ? f2d_alu(tskf[0] * float(Jin[cell])) : to_elim<P>(F(Jin[cell]));
       I Jin1 = 0;
       freq_coef<P, G>(F(Jin[cell]), F(Hxin[cell]), F(Hyin[cell]), Kc, gxx, gyy, gsh, gphi, H0, R0,
                       tn, th, 0, P0, a0, e0);
@@ -1766,7 +1769,10 @@ __device__ __forceinline__ void freq_block(const DeviceView& v, int blk) {
             nX = Hxin[o2];
             nY = Hyin[o2];
           }
-          Jin1 = to_elim<P>(F(Jr));
+          if constexpr (MIX)
+            Jin1 = f2d_alu(tskf[k + 1] * float(Jr));
+          else
+            Jin1 = to_elim<P>(F(Jr));
           F H1, R1;
           HR(k + 1, H1, R1);
           freq_coef<P, G>(F(Jr), F(Xr), F(Yr), Kc, gxx, gyy, gsh, gphi, H1, R1, tn, th, k + 1, P1,
@@ -1797,12 +1803,17 @@ __device__ __forceinline__ void freq_block(const DeviceView& v, int blk) {
           s = tdi[k] / cdt;
         else
           s = tdi[k] * (I(1) / cdt);
-        I E;
+        I E, r;
         if constexpr (P::DET)
           E = (k == 0) ? s : s + Bprev * qprev;
+        else if constexpr (MIX)
+          E = (k == 0) ? s : fma(hprev, Eprev, s);
         else
           E = (k == 0) ? s : s + hprev * Eprev;
-        const I r = (k == 0) ? s * Jin0 : s * Jin0 + Aprev * gprev;
+        if constexpr (MIX)
+          r = (k == 0) ? Jin0 : fma(Aprev, gprev, Jin0);
+        else
+          r = (k == 0) ? s * Jin0 : s * Jin0 + Aprev * gprev;
         const I Dp = E + A;
         const I inv = rcp_elim<P>(Dp);
         const I g = r * inv;
@@ -1847,7 +1858,7 @@ __device__ __forceinline__ void freq_block(const DeviceView& v, int blk) {
           Jout[oc] = Jnf;
           Hxout[oc] = Hx2;
           Hyout[oc] = Hy2;
-          en.add(tdi[k] * Jn);
+          en.s = fma(tdi[k], Jn, en.s);
           continue;
         }
         const I g = I(gS), h = I(hS);
@@ -1882,7 +1893,7 @@ __device__ __forceinline__ void freq_block(const DeviceView& v, int blk) {
           Jout[o] = J;
           Hxout[o] = Hxi;
           Hyout[o] = Hyi;
-          en.add(tdi[k] * f2d_alu(J));
+          en.s = fma(tdi[k], f2d_alu(J), en.s);
           continue;
         }
         const I Ji = I(J);
@@ -2136,6 +2147,8 @@ __device__ __forceinline__ void freq_block_bulk(const DeviceView& v, int blk) {
         I E;  // as in freq_block
         if constexpr (P::DET)
           E = (k == 1) ? sk : sk + Bprev * qprev;
+        else if constexpr (MIX)
+          E = (k == 1) ? sk : fma(hprev, Eprev, sk);
         else
           E = (k == 1) ? sk : sk + hprev * Eprev;
         I r;
@@ -2183,6 +2196,8 @@ __device__ __forceinline__ void freq_block_bulk(const DeviceView& v, int blk) {
     I E;
     if constexpr (P::DET)
       E = (nb == 1) ? sk : sk + Bprev * qprev;
+    else if constexpr (MIX)
+      E = (nb == 1) ? sk : fma(hprev, Eprev, sk);
     else
       E = (nb == 1) ? sk : sk + hprev * Eprev;
     I r;

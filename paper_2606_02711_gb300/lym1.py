@@ -97,6 +97,9 @@ SIGNATURES = {
     "lym1_set_sources": (C.c_int, [C.c_void_p, _PD]),
     "lym1_set_state": (C.c_int, [C.c_void_p, _PD, _PD, _PD]),
     "lym1_get_state": (C.c_int, [C.c_void_p, _PD, _PD, _PD]),
+    "lym1_state_elem_size": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
+    "lym1_get_rows": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "lym1_set_rows": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "lym1_substeps": (C.c_int, [C.c_void_p, C.c_int, C.c_double]),
     "lym1_step": (C.c_int, [C.c_void_p, C.c_double, C.POINTER(C.c_int)]),
     "lym1_moments": (C.c_int, [C.c_void_p, _PD, _PD, _PD]),
@@ -320,6 +323,54 @@ class Context:
         _check(lib().lym1_get_state(self.handle, _out_ptr(J), _out_ptr(Hx), _out_ptr(Hy)),
                "lym1_get_state")
         return J, Hx, Hy
+
+    def state_itemsize(self) -> int:
+        """Bytes per state element: 4 under the mixed policies, 8 under the FP64 ones."""
+        b = C.c_int()
+        _check(lib().lym1_state_elem_size(self.handle, C.byref(b)), "lym1_state_elem_size")
+        return b.value
+
+    def _row_ptrs(self, arrays, n, writable):
+        """Pointers to three [nb][n][nx] arrays (numpy) or tensors (torch, any
+        device) of the state's element type, contiguous."""
+        size = self.state_itemsize()
+        want = np.float32 if size == 4 else np.float64
+        ptrs = []
+        for a in arrays:
+            if hasattr(a, "data_ptr"):
+                if a.element_size() != size or not a.is_floating_point() or not a.is_contiguous():
+                    raise TypeError(f"row buffers must be contiguous {np.dtype(want).name} tensors")
+                if a.numel() != self.nb * n * self.nx:
+                    raise ValueError("row buffers must hold nb * n_rows * nx elements")
+                ptrs.append(C.c_void_p(a.data_ptr()))
+            else:
+                if not (isinstance(a, np.ndarray) and a.dtype == want and a.flags.c_contiguous
+                        and (a.flags.writeable or not writable)):
+                    raise TypeError(f"row arrays must be C-contiguous {np.dtype(want).name}")
+                if a.size != self.nb * n * self.nx:
+                    raise ValueError("row arrays must hold nb * n_rows * nx elements")
+                ptrs.append(C.c_void_p(a.ctypes.data))
+        return ptrs
+
+    def get_rows(self, y0, n, out=None):
+        """Rows [y0, y0 + n) of J, Hx, Hy ([nb][n][nx] each) in the state's own
+        element type, into ``out`` (three arrays or tensors, host or device) or
+        new numpy arrays; the copies are complete when this returns."""
+        if out is None:
+            dt = np.float32 if self.state_itemsize() == 4 else np.float64
+            out = tuple(np.empty((self.nb, int(n), self.nx), dtype=dt) for _ in range(3))
+        p = self._row_ptrs(out, int(n), True)
+        _check(lib().lym1_get_rows(self.handle, int(y0), int(n), *p), "lym1_get_rows")
+        self.synchronize()
+        return out
+
+    def set_rows(self, y0, J, Hx, Hy):
+        """Writes rows [y0, y0 + n) of the state from three [nb][n][nx] arrays or
+        tensors of the state's element type; complete when this returns."""
+        n = (J.numel() if hasattr(J, "numel") else J.size) // max(self.nb * self.nx, 1)
+        p = self._row_ptrs((J, Hx, Hy), n, False)
+        _check(lib().lym1_set_rows(self.handle, int(y0), int(n), *p), "lym1_set_rows")
+        self.synchronize()
 
     def substeps(self, n, dt=0.0):
         _check(lib().lym1_substeps(self.handle, int(n), float(dt)), "lym1_substeps")

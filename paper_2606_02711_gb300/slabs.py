@@ -18,8 +18,9 @@ keep it off.
 
 The module is solver-agnostic: state arrays are [nb][rows][nx] numpy arrays
 or torch tensors (CPU with gloo, CUDA with NCCL); the caller advances its
-slab with whatever it uses (a lym1 context through set_state / substeps /
-get_state, for instance).
+slab with whatever it uses.  A lym1 context swaps only its halo rows, in
+its own element type and on the device, with exchange_ctx (lym1_get_rows /
+lym1_set_rows), so no full state leaves the GPU between substeps.
 """
 import numpy as np
 import torch
@@ -83,6 +84,48 @@ def exchange(arrays, ny: int, world: int, rank: int, group=None):
                 a[:, rows].copy_(buf)
             else:
                 a[:, rows] = buf.numpy()
+
+
+def exchange_ctx(ctx, ny: int, world: int, rank: int, group=None, device=None):
+    """Swap the halo rows of a slab solver in place through its row calls:
+    ``ctx`` holds this rank's extended rows [e0, e1) and offers
+    ``get_rows(y0, n, out)`` / ``set_rows(y0, J, Hx, Hy)`` over [nb][n][nx]
+    buffers of its state's element type (a lym1 context: lym1_get_rows /
+    lym1_set_rows, ``ctx.state_itemsize()`` bytes per element).  Only the
+    2 x HALO edge rows travel: this rank's lowest and highest HALO own rows go
+    to the ranks below and above, whose edge rows land in this rank's halo.
+    ``device``: where the row buffers live (a CUDA device for NCCL, the CPU
+    for gloo); the row calls copy between it and the solver's state."""
+    if world == 1:
+        return
+    y0, y1 = slab_rows(ny, world, rank)
+    e0, e1 = extended_rows(ny, world, rank)
+    lo, hi = y0 - e0, y1 - e0  # own rows, relative to the extended slab
+    dtype = torch.float32 if ctx.state_itemsize() == 4 else torch.float64
+    dev = torch.device("cpu") if device is None else torch.device(device)
+
+    def buf(n):
+        return tuple(torch.empty((ctx.nb, n, ctx.nx), dtype=dtype, device=dev) for _ in range(3))
+
+    reqs, recvs = [], []
+    if rank > 0:
+        send = ctx.get_rows(lo, HALO, buf(HALO))
+        reqs += [dist.isend(t, rank - 1, group=group) for t in send]
+        r = buf(lo)
+        reqs += [dist.irecv(t, rank - 1, group=group) for t in r]
+        recvs.append((0, r))
+    if rank < world - 1:
+        send = ctx.get_rows(hi - HALO, HALO, buf(HALO))
+        reqs += [dist.isend(t, rank + 1, group=group) for t in send]
+        r = buf(e1 - e0 - hi)
+        reqs += [dist.irecv(t, rank + 1, group=group) for t in r]
+        recvs.append((hi, r))
+    for q in reqs:
+        q.wait()
+    if dev.type == "cuda":
+        torch.cuda.current_stream(dev).synchronize()  # the received rows, before the solver's stream reads them
+    for row0, (J, Hx, Hy) in recvs:
+        ctx.set_rows(row0, J, Hx, Hy)
 
 
 def global_ctilde(local_ctilde: float, group=None) -> float:

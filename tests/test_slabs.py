@@ -161,6 +161,66 @@ def test_exchange_fills_every_halo_row_from_its_owner(ny, world):
         np.testing.assert_array_equal(t, want)
 
 
+class _RowCtx:
+    """A stand-in for a slab context's row calls (lym1_get_rows /
+    lym1_set_rows) over numpy state arrays of one element type."""
+
+    def __init__(self, arrays):
+        self.a = arrays
+        self.nb, _, self.nx = arrays[0].shape
+
+    def state_itemsize(self):
+        return self.a[0].dtype.itemsize
+
+    def get_rows(self, y0, n, out):
+        import torch
+        for o, a in zip(out, self.a):
+            o.copy_(torch.from_numpy(np.ascontiguousarray(a[:, y0:y0 + n])))
+        return out
+
+    def set_rows(self, y0, J, Hx, Hy):
+        for a, t in zip(self.a, (J, Hx, Hy)):
+            a[:, y0:y0 + t.shape[1]] = t.numpy()
+
+
+def _worker_ctx_rows(rank, world, port, ny, out):
+    # the row-call exchange in both element types: each rank's own rows hold
+    # their global row index (halo rows -1) before the swap
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    y0, y1 = slabs.slab_rows(ny, world, rank)
+    e0, e1 = slabs.extended_rows(ny, world, rank)
+    rows = np.arange(e0, e1, dtype=np.float64)
+    res = []
+    for dt in (np.float32, np.float64):
+        a = [(np.where((rows >= y0) & (rows < y1), rows, -1.0)[None, :, None] * np.ones((3, 1, 5)) *
+              (i + 1)).astype(dt) for i in range(3)]
+        slabs.exchange_ctx(_RowCtx(a), ny, world, rank)
+        res.append(a)
+    out.put((rank, res, rows))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("ny,world", [(9, 4), (17, 3), (4, 2)])
+def test_row_call_exchange_fills_every_halo_row_from_its_owner(ny, world):
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker_ctx_rows, args=(r, world, port, ny, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = [q.get(timeout=120) for _ in range(world)]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, per_type, rows in res:
+        for a in per_type:
+            for i, arr in enumerate(a):
+                want = np.broadcast_to(rows[None, :, None] * (i + 1), arr.shape).astype(arr.dtype)
+                np.testing.assert_array_equal(arr, want)
+
+
 def test_split_is_a_balanced_partition():
     for ny in (4, 17, 512, 2048):
         for world in (1, 2, 3, 8):
