@@ -37,6 +37,11 @@ NAMES = {0: "fp64_det", 1: "fp64", 2: "mixed", 3: "mixed_fast"}
 WORKLOAD = ("lognormal-512: 512x512 cells x 194 bins, sigma_ln=1.0, mean n_H=1e3 cm^-3, "
             "Z=0.01 Z_sun dust, v~r (10 km/s at 1 pc), 1e6 L_sun central source, T=1e4 K, "
             "2 pc box, outflow boundaries")
+# the single large solve (timed on request with --workload lognormal-2048; the
+# default line is the 512^2 workload above)
+WORKLOAD_2048 = ("lognormal-2048: 2048x2048 cells x 194 bins, sigma_ln=1.5, mean n_H=1e4 cm^-3, "
+                 "Z=0.001 Z_sun dust, v~r (10 km/s at 1 pc), 1e7 L_sun central source, T=1e4 K, "
+                 "2 pc box, outflow boundaries")
 
 
 # Algorithmic FP32 operations per (cell, bin) of the transport + source kernel,
@@ -263,6 +268,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=list(NAMES.values()))
+    ap.add_argument("--workload", default="lognormal-512", choices=["lognormal-512", "lognormal-2048"],
+                    help="lognormal-2048: the single large solve, timed region only (with --no-extras)")
     ap.add_argument("--fp64-steps", type=int, default=8)
     ap.add_argument("--e2e-steps", type=int, default=40)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
@@ -306,7 +313,8 @@ def main():
             dist.barrier()
 
     prec = L.PRECISIONS[args.precision]
-    cloud = wl.config_lognormal_512(seed=1 + rank)
+    big = args.workload == "lognormal-2048"
+    cloud = (wl.config_lognormal_2048 if big else wl.config_lognormal_512)(seed=1 + rank)
     nc = cloud.nx * cloud.ny
     ctx = L.from_cloud(cloud, precision=prec)
     nb = ctx.nb
@@ -387,7 +395,7 @@ def main():
            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[prec],
            "data": "synthetic (seeded lognormal cloud, no dataset)",
-           "config": {"workload": WORKLOAD, "cells": nc, "bins": nb, "precision": NAMES[prec],
+           "config": {"workload": WORKLOAD_2048 if big else WORKLOAD, "cells": nc, "bins": nb, "precision": NAMES[prec],
                       "substep_dt_s": ctx.dt_cfl, "per_rank_clouds": 1,
                       "l2": "inputs larger than L2: state "
                             f"{3 * nb * nc * selem / 1e6:.0f} MB per copy > 129 MB L2",

@@ -14,7 +14,7 @@ import time
 
 
 def run(n_clouds=256, substeps=20, precisions=("mixed_fast", "fp64"), base_seed=1000,
-        side_lo=64, side_hi=512, loop_substeps=None):
+        side_lo=64, side_hi=512, loop_substeps=None, fp64_substeps=None):
     import torch
     import workloads as wl
     import paper_2606_02711_gb300.lym1 as L
@@ -24,7 +24,7 @@ def run(n_clouds=256, substeps=20, precisions=("mixed_fast", "fp64"), base_seed=
            "sides": [min(c.nx for c in clouds), max(c.nx for c in clouds)], "modes": {}}
     for pname in precisions:
         p = L.PRECISIONS[pname]
-        n = substeps if p >= 2 else max(2, substeps // 10)
+        n = substeps if p >= 2 else (fp64_substeps or max(2, substeps // 10))
         ctxs = [L.from_cloud(c, precision=p) for c in clouds]
         dev_gb = sum(x.info()["device_bytes"] for x in ctxs) / 1e9
         b = L.Batch(ctxs)
@@ -67,8 +67,13 @@ def main():
     ap.add_argument("--clouds", type=int, default=256)
     ap.add_argument("--substeps", type=int, default=20)
     ap.add_argument("--precisions", default="mixed_fast,mixed,fp64")
+    ap.add_argument("--fp64-substeps", type=int, default=None,
+                    help="substeps of the FP64 policies (default: a tenth of --substeps)")
+    ap.add_argument("--loop-substeps", type=int, default=None,
+                    help="substeps of the one-context-at-a-time comparison (default: half)")
     args = ap.parse_args()
-    print(json.dumps(run(args.clouds, args.substeps, tuple(args.precisions.split(",")))))
+    print(json.dumps(run(args.clouds, args.substeps, tuple(args.precisions.split(",")),
+                         loop_substeps=args.loop_substeps, fp64_substeps=args.fp64_substeps)))
 
 
 if __name__ == "__main__":
