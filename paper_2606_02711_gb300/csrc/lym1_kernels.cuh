@@ -951,9 +951,25 @@ __device__ __forceinline__ void face_flux_f32(float Jm, float nm, float tm, floa
 // distances) of a thread's faces do not depend on the bin and stay in
 // registers.  The implicit source step runs in type I (FP64 for LYM1_MIXED,
 // FP32 for LYM1_MIXED_FAST).
-template <class P, int G, int PT, int TS = 0>
-__device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, int y0, int blk,
-                                                   int k0, int k1, int grp) {
+// The FP32 tile's static shared buffers, declared once per kernel (the tile
+// body is instantiated twice under LYM1_MIXED, see transport_tile_f32_any)
+template <int TS>
+struct TileSmemF32 {
+  static constexpr int TX = TileShape<TS>::X, TY = TileShape<TS>::Y, SX = TX + 4, SY = TY + 4;
+  float4 sq[2][SY][SX];  // (J, f_x, f_y, alpha_F of the bin)
+  float sHx[2][SY][SX], sHy[2][SY][SX];
+  // face fluxes (J, normal K, tangential K, -): x faces (J, K_xx, K_xy), y faces
+  // (J, K_yy, K_yx)
+  float4 xF[TY][TX + 1];
+  float4 yF[TY + 1][TX];
+  double red[2 * (TX * TY / 32)];  // the last pair of reductions uses both halves
+};
+
+// SRC = false: no cell of the tile holds a source (LYM1_MIXED's step 2 then
+// compiles without the emission term; decided per tile by the kernel wrapper)
+template <class P, int G, int PT, int TS = 0, bool SRC = true>
+__device__ __forceinline__ void transport_tile_f32(TileSmemF32<TS>& sm, const DeviceView& v, int x0,
+                                                   int y0, int blk, int k0, int k1, int grp) {
   // table mode (0 uniform T, 1 temperature field, 2 broad bands) and, in bit 4,
   // active-bin pruning: without it the tile compiles with no pruning code
   constexpr int TM = PT & 3;
@@ -965,13 +981,12 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
   constexpr int NT = TX * TY;
   static_assert(SX * SY <= 2 * NT, "two halo entries per thread at most");
   static_assert(TX + TY <= 64, "the extra faces are the first two warps' work at most");
-  __shared__ float4 sq[2][SY][SX];  // (J, f_x, f_y, alpha_F of the bin)
-  __shared__ float sHx[2][SY][SX], sHy[2][SY][SX];
-  // face fluxes (J, normal K, tangential K, -): x faces (J, K_xx, K_xy), y faces
-  // (J, K_yy, K_yx)
-  __shared__ float4 xF[TY][TX + 1];
-  __shared__ float4 yF[TY + 1][TX];
-  __shared__ double red[2 * (NT / 32)];  // the last pair of reductions uses both halves
+  auto& sq = sm.sq;
+  auto& sHx = sm.sHx;
+  auto& sHy = sm.sHy;
+  auto& xF = sm.xF;
+  auto& yF = sm.yF;
+  auto& red = sm.red;
   extern __shared__ float4 tab4[];  // per bin (<H>_k, dnu_k, gem_k / gem_max, J_act,k) as FP32
 
   const float* __restrict__ Jin = static_cast<const float*>(v.J);
@@ -1164,10 +1179,11 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
       const double d2 = fma(cC, Hd, cD1);
       double num = f2d_alu(dJ1);
       double gk = 0.0;
-      if (src) {
-        gk = TM ? gmax_c * f2d_alu(Gcf[kbase + cell]) : v.t_gem[kk];
-        num = fma(cjs, gk, num);
-      }
+      if constexpr (SRC)
+        if (src) {
+          gk = TM ? gmax_c * f2d_alu(Gcf[kbase + cell]) : v.t_gem[kk];
+          num = fma(cjs, gk, num);
+        }
       // J'' = num / d1 in FP64: the FP32 seed y of 1/d1 (d1 >= 1) and one
       // Newton-Raphson step folded into the product, num y (1 + e) with the
       // FP64 residual e = 1 - d1 y (relative error e^2 ~ 2^-44)
@@ -1221,6 +1237,7 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
       }
     }
   };
+
   for (int k = k0; k < k1; ++k) {
     const int b = k & 1;
     const float4 tb = tab4[k];  // (<H>_k, dnu_k, gem_k / gem_max, J_act,k)
@@ -1497,6 +1514,29 @@ __device__ __forceinline__ void transport_tile_f32(const DeviceView& v, int x0, 
   }
 }
 
+// The FP32 tile for any tile: under LYM1_MIXED (FP64 step 2 in the tile) the
+// tiles without a source cell, nearly all of them, take the variant without
+// the emission term.  A per-cell branch inside step 2 costs GB300's narrow
+// FP64 pipe two issue slots per cell-bin even where no cell takes it, and a
+// per-tile branch inside the bin loop keeps the compiler from interleaving
+// step 2 with the face fluxes; a whole-tile choice costs neither.
+template <class P, int G, int PT, int TS>
+__device__ __forceinline__ void transport_tile_f32_any(const DeviceView& v, int x0, int y0, int blk,
+                                                       int k0, int k1, int grp) {
+  __shared__ TileSmemF32<TS> sm;
+  if constexpr (sizeof(typename P::I) == 8 && (PT & 8) == 0) {
+    const int gx = x0 + static_cast<int>(threadIdx.x), gy = y0 + static_cast<int>(threadIdx.y);
+    const bool s = gx < v.nx && gy < v.ny && v.lum[static_cast<long long>(gy) * v.nx + gx] != 0.0;
+    if (__syncthreads_or(s ? 1 : 0)) {
+      transport_tile_f32<P, G, PT, TS, true>(sm, v, x0, y0, blk, k0, k1, grp);
+      return;
+    }
+    transport_tile_f32<P, G, PT, TS, false>(sm, v, x0, y0, blk, k0, k1, grp);
+  } else {
+    transport_tile_f32<P, G, PT, TS, true>(sm, v, x0, y0, blk, k0, k1, grp);
+  }
+}
+
 // blocks per SM the FP32 tile is register-budgeted for: 3 (80 registers).
 // LYM1_MIXED's FP64 step holds more live values: at 3 blocks it spills
 // ~60 bytes a thread, yet the third block's warps hide enough of the FP64
@@ -1509,8 +1549,8 @@ __host__ __device__ constexpr int tile_f32_min_blocks() {
 
 template <class P, int G, int PT>
 __global__ void __launch_bounds__(kTileX* kTileY, tile_f32_min_blocks<P>()) transport_kernel_f32(DeviceView v) {
-  transport_tile_f32<P, G, PT>(v, blockIdx.x * kTileX, blockIdx.y * kTileY,
-                               blockIdx.y * gridDim.x + blockIdx.x, 0, v.nb, 0);
+  transport_tile_f32_any<P, G, PT, 0>(v, blockIdx.x * kTileX, blockIdx.y * kTileY,
+                                      blockIdx.y * gridDim.x + blockIdx.x, 0, v.nb, 0);
 }
 
 // ------------------------------------------------------------ frequency kernel
@@ -2496,7 +2536,7 @@ __global__ void __launch_bounds__(TileShape<TS>::X* TileShape<TS>::Y, tile_f32_m
   for (int i = blockIdx.x; i < n; i += gridDim.x) {
     const BatchItem it = items[i];
     const DeviceView v = views[it.ctx];
-    transport_tile_f32<P, G, PT, TS>(v, it.x0, it.y0, it.blk, it.k0, it.k1, it.grp);
+    transport_tile_f32_any<P, G, PT, TS>(v, it.x0, it.y0, it.blk, it.k0, it.k1, it.grp);
     __syncthreads();
   }
 }
