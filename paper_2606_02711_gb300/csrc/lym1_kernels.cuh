@@ -791,6 +791,20 @@ __device__ __forceinline__ float d2f_alu(double x) {
   return __uint_as_float(s | f);
 }
 
+// The per-tile FP32 constants of the FP32 tile are narrowed from their FP64
+// inputs on the integer pipe: under register pressure the compiler re-forms
+// such values inside the bin loop, and a hardware FP64 -> FP32 conversion there
+// costs GB300's narrow FP64 pipe an issue slot per cell-bin (measured: two
+// slots per cell-bin, 6 % of LYM1_MIXED's transport).  Same result as the
+// conversion for every FP32-normal value.
+template <class T>
+__device__ __forceinline__ T narrow_to(double x) {
+  if constexpr (sizeof(T) == 4)
+    return d2f_alu(x);
+  else
+    return x;
+}
+
 __device__ __forceinline__ double drcp_nr(double x) {
   double y;
   asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
@@ -1059,7 +1073,7 @@ __device__ __forceinline__ void transport_tile_f32(TileSmemF32<TS>& sm, const De
                : 0.5f * (wcell(x0 + xfi, y0 + TY - 1, false) + wcell(x0 + xfi, y0 + TY, false));
   // face optical depth = aF_0 dl_0 + aF_1 dl_1 (centroid distances, geometry
   // 1) or (aF_0 + aF_1) dx/2 (geometry 0)
-  const float half_dx = 0.5f * float(v.dx);
+  const float half_dx = 0.5f * d2f_alu(v.dx);
   float dlA0 = half_dx, dlA1 = half_dx, dlB0 = half_dx, dlB1 = half_dx;
   if constexpr (G == 1) {
     const int fa = gx <= nx ? gx : nx;
@@ -1077,28 +1091,29 @@ __device__ __forceinline__ void transport_tile_f32(TileSmemF32<TS>& sm, const De
   float r0c = 0, r1c = 0, hoopc = 0, wvf = 1.0f;
   double lum_d = 0.0;
   if (valid) {
-    alpha_c = I(v.alpha[cell]);
-    rho_c = I(v.rho[cell]);
-    pd_c = I(v.pd[cell]);
+    alpha_c = narrow_to<I>(v.alpha[cell]);
+    rho_c = narrow_to<I>(v.rho[cell]);
+    pd_c = narrow_to<I>(v.pd[cell]);
     lum_d = v.lum[cell];
     // velocity gradients times c_tilde dt / c: W below is then the step-1
     // change of J itself, (c_tilde dt / c) D : grad u J, which stays in the
     // FP32 range where J does (W / c alone is ~1e-20 J)
-    gxx = float(v.gxx[cell] * v.cdt_c);
-    gyy = float(v.gyy[cell] * v.cdt_c);
-    gsh = float(v.gsh[cell] * v.cdt_c);
+    gxx = d2f_alu(v.gxx[cell] * v.cdt_c);
+    gyy = d2f_alu(v.gyy[cell] * v.cdt_c);
+    gsh = d2f_alu(v.gsh[cell] * v.cdt_c);
     if constexpr (G == 1) {
-      gphi = float(v.gphi[cell] * v.cdt_c);
+      gphi = d2f_alu(v.gphi[cell] * v.cdt_c);
       r0c = v.gf_r0[gx];
       r1c = v.gf_r1[gx];
       hoopc = v.gf_hoop[gx];
       wvf = v.gf_wv[gx];
     }
   }
-  const float cdt_dx = float(v.cdt_dx);
-  const I cdt = I(v.cdt), kabs = I(v.kabs), kF = I(v.kF), cdx = I(v.cdt_dx);
-  const I wR = I(v.g_wR), wcol = I(wvf);
-  const float wRf = float(v.g_wR);
+  const float cdt_dx = d2f_alu(v.cdt_dx);
+  const I cdt = narrow_to<I>(v.cdt), kabs = narrow_to<I>(v.kabs), kF = narrow_to<I>(v.kF),
+          cdx = narrow_to<I>(v.cdt_dx);
+  const I wR = narrow_to<I>(v.g_wR), wcol = I(wvf);
+  const float wRf = d2f_alu(v.g_wR);
   // LYM1_MIXED (FP64 implicit step): the per-cell factors with c_tilde dt
   // folded in, c dt kappa_k = cA + cB <H>_k and c dt alpha_F,k = cD + cC <H>_k
   // (bands: c dt kappa_k from their kappa table, alpha = 1, rho_d = 0)
@@ -1141,7 +1156,7 @@ __device__ __forceinline__ void transport_tile_f32(TileSmemF32<TS>& sm, const De
   // (~1e-75) alone, or j_k itself in the far wings (~1e-38)
   const bool src = lum_d != 0.0;
   const double gmax_c = TM ? (valid ? v.gmaxc[cell] : 1.0) : v.gem_max;
-  const float cjsc = float(v.cdt * (lum_d * gmax_c));
+  const float cjsc = d2f_alu(v.cdt * (lum_d * gmax_c));
   const bool bnd = valid && (G == 1 ? (gx == nx - 1 || gy == ny - 1)
                                      : (gx == 0 || gx == nx - 1 || gy == 0 || gy == ny - 1));
 
@@ -1753,25 +1768,27 @@ __device__ __forceinline__ void freq_block(const DeviceView& v, int blk) {
   if constexpr (G == 1)
     if (cell < nc) wcell = v.g_wv[cell % v.nx];
   const I wI = I(wcell);
-  const float wf = float(wcell);
+  const float wf = d2f_alu(wcell);
   if (cell < nc) {
     combine_force_groups(v, cell);
     const double alpha = v.alpha[cell];
     if (v.freq_step && alpha > 0.0) {
-      const F Kc = PT ? F(v.Kcc[cell] * alpha) : F(v.Kc * alpha);
-      const F gxx = F(v.gxx[cell]), gyy = F(v.gyy[cell]), gsh = F(v.gsh[cell]);
-      const F gphi = G == 1 ? F(v.gphi[cell]) : F(0);
+      const F Kc = narrow_to<F>(PT ? v.Kcc[cell] * alpha : v.Kc * alpha);
+      const F gxx = narrow_to<F>(v.gxx[cell]), gyy = narrow_to<F>(v.gyy[cell]),
+              gsh = narrow_to<F>(v.gsh[cell]);
+      const F gphi = G == 1 ? narrow_to<F>(v.gphi[cell]) : F(0);
       // <H>_k and the recoil factor R_k of bin kk: per-bin tables, or the
       // cell's own under a temperature field
       const S* __restrict__ Hcs = static_cast<const S*>(v.Hc);
       const double hkT_c = PT ? v.hkTc[cell] : 0.0;
+      const float hkT_f = d2f_alu(hkT_c);
       auto HR = [&](int kk, F& Hk, F& Rk) {
         if constexpr (PT) {
           Hk = F(Hcs[static_cast<long long>(kk) * nc + cell]);
           if constexpr (sizeof(F) == 8)
             Rk = F(hkT_c - v.t_2nu[kk]);
           else
-            Rk = float(hkT_c) - v.f_2nu[kk];
+            Rk = hkT_f - v.f_2nu[kk];
         } else {
           Hk = tH[kk];
           Rk = tR[kk];
@@ -2095,17 +2112,17 @@ __device__ __forceinline__ void freq_block_bulk(const DeviceView& v, int blk) {
   const bool valid = tid < ncell;
   const double alpha = valid ? v.alpha[cell] : 0.0;
   const bool act = valid && alpha > 0.0;
-  const F Kc = PT ? F((valid ? v.Kcc[cell] : 0.0) * alpha) : F(v.Kc * alpha);
+  const F Kc = narrow_to<F>(PT ? (valid ? v.Kcc[cell] : 0.0) * alpha : v.Kc * alpha);
   // temperature field: <H>_k rides the forward ring as a fourth row
   const float* __restrict__ Hcf = static_cast<const float*>(v.Hc);
-  const float hkT_c = PT ? float(valid ? v.hkTc[cell] : 0.0) : 0.0f;
-  const F gxx = valid ? F(v.gxx[cell]) : F(0), gyy = valid ? F(v.gyy[cell]) : F(0),
-          gsh = valid ? F(v.gsh[cell]) : F(0);
+  const float hkT_c = PT ? d2f_alu(valid ? v.hkTc[cell] : 0.0) : 0.0f;
+  const F gxx = valid ? narrow_to<F>(v.gxx[cell]) : F(0), gyy = valid ? narrow_to<F>(v.gyy[cell]) : F(0),
+          gsh = valid ? narrow_to<F>(v.gsh[cell]) : F(0);
   F gphi = F(0);
   double wcell = 1.0;  // axisymmetric grid: energy weight of the cell's column
   if constexpr (G == 1)
     if (valid) {
-      gphi = F(v.gphi[cell]);
+      gphi = narrow_to<F>(v.gphi[cell]);
       wcell = v.g_wv[cell % v.nx];
     }
   const I wI = I(wcell);
@@ -2260,7 +2277,7 @@ __device__ __forceinline__ void freq_block_bulk(const DeviceView& v, int blk) {
   float mxf2 = 0.0f;  // LYM1_MIXED: max |H|^2 / J^2
   int bad = 0;
   I Jnext = 0;
-  const float wf = G == 1 ? float(wcell) : 1.0f;
+  const float wf = G == 1 ? d2f_alu(wcell) : 1.0f;
   long long obw = static_cast<long long>(nb - 1) * nc + cell;  // plane offset of row k
   for (int j = 0; j < nb; ++j, obw -= nc) {
     const int s = j % D, k = nb - 1 - j;
