@@ -797,6 +797,18 @@ __device__ __forceinline__ float d2f_alu(double x) {
 // costs GB300's narrow FP64 pipe an issue slot per cell-bin (measured: two
 // slots per cell-bin, 6 % of LYM1_MIXED's transport).  Same result as the
 // conversion for every FP32-normal value.
+// x != 0 and x > 0 for a binary64 x, decided on its bits (integer pipe): a
+// per-cell predicate that the compiler re-forms inside a bin loop from the
+// double itself would otherwise be an FP64 compare there.  Same truth values
+// as the comparisons, NaN included.
+__device__ __forceinline__ bool nonzero_bits(double x) {
+  return (static_cast<unsigned long long>(__double_as_longlong(x)) << 1) != 0ull;
+}
+__device__ __forceinline__ bool positive_bits(double x) {
+  const long long b = __double_as_longlong(x);
+  return b > 0 && b <= 0x7ff0000000000000LL;
+}
+
 template <class T>
 __device__ __forceinline__ T narrow_to(double x) {
   if constexpr (sizeof(T) == 4)
@@ -1154,7 +1166,7 @@ __device__ __forceinline__ void transport_tile_f32(TileSmemF32<TS>& sm, const De
   // source term c_tilde dt j_k = (c_tilde dt L_cell gem_max) (gem_k / gem_max):
   // both factors lie in the FP32 range, unlike L_cell (~1e39 erg/s) and gem_k
   // (~1e-75) alone, or j_k itself in the far wings (~1e-38)
-  const bool src = lum_d != 0.0;
+  const bool src = nonzero_bits(lum_d);
   const double gmax_c = TM ? (valid ? v.gmaxc[cell] : 1.0) : v.gem_max;
   const float cjsc = d2f_alu(v.cdt * (lum_d * gmax_c));
   const bool bnd = valid && (G == 1 ? (gx == nx - 1 || gy == ny - 1)
@@ -2111,7 +2123,7 @@ __device__ __forceinline__ void freq_block_bulk(const DeviceView& v, int blk) {
   const long long cell = c0 + tid;
   const bool valid = tid < ncell;
   const double alpha = valid ? v.alpha[cell] : 0.0;
-  const bool act = valid && alpha > 0.0;
+  const bool act = valid && positive_bits(alpha);
   const F Kc = narrow_to<F>(PT ? (valid ? v.Kcc[cell] : 0.0) * alpha : v.Kc * alpha);
   // temperature field: <H>_k rides the forward ring as a fourth row
   const float* __restrict__ Hcf = static_cast<const float*>(v.Hc);
