@@ -53,8 +53,10 @@ extern "C" {
 /* Arithmetic of the substep. */
 #define LYM1_FP64_DET 0    /* FP64, fixed operation order, no FMA contraction, own exp/expm1 */
 #define LYM1_FP64 1        /* FP64 with FMA and hardware exp/expm1 */
-#define LYM1_MIXED 2       /* FP32 state, transport and closure; FP64 implicit steps 2-3 and force */
-#define LYM1_MIXED_FAST 3  /* FP32 everywhere but the per-cell FP64 sums; subtraction-free solve */
+#define LYM1_MIXED 2       /* FP32 state, transport and closure; FP64 implicit steps 2-3 and
+                              conservation sums (the force sum: compensated FP32) */
+#define LYM1_MIXED_FAST 3  /* FP32 throughout (compensated FP32 sums per cell, FP64 across
+                              cells); subtraction-free solve */
 
 typedef struct lym1_ctx lym1_ctx;
 
@@ -349,10 +351,11 @@ int lym1_debug_expire_wait(lym1_ctx *ctx);
  * pipe and refine a hardware reciprocal approximation by Newton-Raphson).
  * For i < n (device pointers, caller-owned): wide[i] = xf[i] widened to FP64,
  * narrow[i] = xd[i] narrowed to FP32 (round to nearest even), rcp[i] = 1 /
- * xd[i] (two Newton-Raphson steps), rcp1[i] = 1 / xd[i] with the one step
- * the mixed elimination takes, and rcpf[i] = 1 / xd[i] seeded by the FP32
- * reciprocal with one FP64 step, as the mixed source step takes it (xd[i] in
- * the FP32 normal range); both conversions flush subnormals to zero.  Runs on
+ * xd[i] (two Newton-Raphson steps), rcp1[i] = 1 / xd[i] from the hardware
+ * approximation with one step, and rcpf[i] = 1 / xd[i] as the mixed source
+ * step and elimination take it: the FP32 reciprocal of the significand seeds
+ * it (exponent in integer bits, any normal xd[i] below 2^1020) and one FP64
+ * step refines it; both conversions flush subnormals to zero.  Runs on
  * the legacy default stream and synchronises it.  LYM1_EINVAL for null
  * pointers or n < 0; LYM1_ECUDA if the launch fails.
  */
